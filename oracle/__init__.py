@@ -1,0 +1,271 @@
+"""Python access to the FP64 CPU oracle (plain C, see ``oracle.h``).
+
+TEST INFRASTRUCTURE ONLY: the oracle is the independent, slow, obviously
+correct restatement of the paper's method that the CUDA library is checked
+against. Only the tests, ``__graft_entry__.smoke()`` and the benchmark's
+CPU-baseline / reference leg may import this package. It shares no code with
+the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SOURCES = ["rng_sample.c", "locate.c", "transfer.c", "clip.c", "mlp.c"]
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# plain ISO C, one rounding per operation: no contraction into FMA, no fast-math
+CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+          "-fno-unsafe-math-optimizations", "-Wall"]
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` with gcc (seconds)."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES if os.path.exists(os.path.join(_HERE, s))]
+    newest = max(os.path.getmtime(s) for s in srcs + [os.path.join(_HERE, "oracle.h")])
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", *CFLAGS, *srcs, "-o", tmp, "-lm"], check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            _lib = ctypes.CDLL(_LIB_PATH)
+            _declare(_lib)
+        return _lib
+
+
+_i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+_u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+_f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("samples_per_elem", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("stream", ctypes.c_uint32),
+                ("alpha", ctypes.c_double), ("grid_scale_L", ctypes.c_double),
+                ("cg_tol", ctypes.c_double), ("cg_max_iter", ctypes.c_int)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("cg_iters", ctypes.c_int), ("cg_rel_resid", ctypes.c_double),
+                ("fallback_queries", ctypes.c_int64), ("empty_queries", ctypes.c_int64)]
+
+
+def _declare(L):
+    L.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+    L.orc_u01_f32.argtypes = [ctypes.c_uint32]
+    L.orc_u01_f32.restype = ctypes.c_float
+    L.orc_u01_f64.argtypes = [ctypes.c_uint32]
+    L.orc_u01_f64.restype = ctypes.c_double
+    L.orc_sample_element.argtypes = [_int, _int, ctypes.c_uint64, ctypes.c_uint32, _i64,
+                                     ctypes.c_int32, _f64p, _f64p, _f64p]
+    L.orc_grid_build.argtypes = [_int, _int, _i64, _f64p, _i64, _i32p, ctypes.c_double]
+    L.orc_grid_build.restype = _vp
+    L.orc_grid_free.argtypes = [_vp]
+    L.orc_grid_shape.argtypes = [_vp, _i32p, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
+    L.orc_grid_csr.argtypes = [_vp, _i64p, _i32p]
+    L.orc_grid_locate.argtypes = [_vp, _i64, _f64p, _i32p, _i32p]
+    L.orc_brute_locate.argtypes = [_int, _int, _i64, _f64p, _i64, _i32p, _i64, _f64p,
+                                   _i32p, _i32p]
+    L.orc_eval_p1.argtypes = [_int, _f64p, _i32p, _int, _i64, _f64p, ctypes.c_int32,
+                              _f64p, _f64p]
+    L.orc_mass_nnz.argtypes = [_int, _i64, _i64, _i32p]
+    L.orc_mass_nnz.restype = _i64
+    L.orc_mass_csr.argtypes = [_int, _i64, _f64p, _i64, _i32p, _i64p, _i32p, _f64p]
+    L.orc_lumped_mass.argtypes = [_int, _i64, _f64p, _i64, _i32p, _f64p]
+    L.orc_pcg.argtypes = [_i64, _i64p, _i32p, _f64p, _f64p, _f64p, ctypes.c_double, _int,
+                          ctypes.POINTER(ctypes.c_double)]
+    L.orc_pcg.restype = _int
+    L.orc_transfer.argtypes = [_int, ctypes.POINTER(_Params),
+                               _i64, _f64p, _i64, _i32p, _int, _f64p,
+                               _i64, _f64p, _i64, _i32p,
+                               _f64p, _f64p, _f64p, _f64p, _f64p, _vp,
+                               ctypes.POINTER(_Stats)]
+    L.orc_integral_p1.argtypes = [_int, _i64, _f64p, _i64, _i32p, _f64p]
+    L.orc_integral_p1.restype = ctypes.c_double
+    L.orc_mi_load_vector_2d.argtypes = [_i64, _f64p, _i64, _i32p, _f64p, _i64, _f64p, _i64,
+                                        _i32p, _f64p]
+    L.orc_l2_error_2d.argtypes = [_i64, _f64p, _i64, _i32p, _f64p, _i64, _f64p, _i64, _i32p,
+                                  _f64p, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double)]
+    if hasattr(L, "orc_mlp_forward"):
+        _declare_mlp(L)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+# ---------------------------------------------------------------------------
+def philox4x32_10(ctr, key) -> np.ndarray:
+    out = np.zeros(4, np.uint32)
+    lib().orc_philox4x32_10(np.ascontiguousarray(ctr, np.uint32),
+                            np.ascontiguousarray(key, np.uint32), out)
+    return out
+
+
+def u01(x: int, prec: int) -> float:
+    return float(lib().orc_u01_f32(x) if prec == 1 else lib().orc_u01_f64(x))
+
+
+def sample_element(prec, dim, seed, stream, t, nsamp, node_xyz):
+    lam = np.zeros((nsamp, dim + 1))
+    X = np.zeros((nsamp, dim))
+    lib().orc_sample_element(prec, dim, seed, stream, t, nsamp, _f64(node_xyz), lam, X)
+    return lam, X
+
+
+class Grid:
+    """The oracle's uniform grid over a source mesh (build + locate)."""
+
+    def __init__(self, prec, coords, conn, grid_scale_L=1.0):
+        self.coords = _f64(coords)
+        self.conn = _i32(conn)
+        self.dim = self.coords.shape[1]
+        self.prec = prec
+        self._h = lib().orc_grid_build(prec, self.dim, self.coords.shape[0], self.coords,
+                                       self.conn.shape[0], self.conn, grid_scale_L)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().orc_grid_free(self._h)
+            self._h = None
+
+    def shape(self):
+        n = np.zeros(3, np.int32)
+        nc, ni = _i64(), _i64()
+        lib().orc_grid_shape(self._h, n, ctypes.byref(nc), ctypes.byref(ni))
+        return n, nc.value, ni.value
+
+    def csr(self):
+        _, nc, ni = self.shape()
+        start = np.zeros(nc + 1, np.int64)
+        items = np.zeros(max(ni, 1), np.int32)
+        lib().orc_grid_csr(self._h, start, items)
+        return start, items[:ni]
+
+    def locate(self, pts):
+        pts = _f64(pts).reshape(-1, self.dim)
+        e = np.zeros(pts.shape[0], np.int32)
+        st = np.zeros(pts.shape[0], np.int32)
+        lib().orc_grid_locate(self._h, pts.shape[0], pts, e, st)
+        return e, st
+
+
+def brute_locate(prec, coords, conn, pts):
+    coords, conn = _f64(coords), _i32(conn)
+    dim = coords.shape[1]
+    pts = _f64(pts).reshape(-1, dim)
+    e = np.zeros(pts.shape[0], np.int32)
+    st = np.zeros(pts.shape[0], np.int32)
+    lib().orc_brute_locate(prec, dim, coords.shape[0], coords, conn.shape[0], conn,
+                           pts.shape[0], pts, e, st)
+    return e, st
+
+
+def eval_p1(coords, conn, values, e, X):
+    coords, conn, values = _f64(coords), _i32(conn), _f64(np.atleast_2d(values))
+    out = np.zeros(values.shape[0])
+    lib().orc_eval_p1(coords.shape[1], coords, conn, values.shape[0], coords.shape[0], values,
+                      int(e), _f64(X), out)
+    return out
+
+
+def mass_csr(coords, conn):
+    coords, conn = _f64(coords), _i32(conn)
+    dim, nv = coords.shape[1], coords.shape[0]
+    nnz = lib().orc_mass_nnz(dim, nv, conn.shape[0], conn)
+    rp = np.zeros(nv + 1, np.int64)
+    col = np.zeros(nnz, np.int32)
+    val = np.zeros(nnz)
+    lib().orc_mass_csr(dim, nv, coords, conn.shape[0], conn, rp, col, val)
+    return rp, col, val
+
+
+def lumped_mass(coords, conn):
+    coords, conn = _f64(coords), _i32(conn)
+    m = np.zeros(coords.shape[0])
+    lib().orc_lumped_mass(coords.shape[1], coords.shape[0], coords, conn.shape[0], conn, m)
+    return m
+
+
+def pcg(rp, col, val, b, tol=1e-12, max_iter=1000):
+    b = _f64(b)
+    x = np.zeros_like(b)
+    rr = ctypes.c_double()
+    it = lib().orc_pcg(b.shape[0], np.ascontiguousarray(rp, np.int64), _i32(col), _f64(val),
+                       b, x, tol, max_iter, ctypes.byref(rr))
+    return x, it, rr.value
+
+
+def transfer(src, tgt, prec, samples_per_elem, seed=0, stream=0, alpha=1.0, grid_scale_L=1.0,
+             cg_tol=1e-12, cg_max_iter=1000, want_sample_elem=False):
+    """Steps 1-7 of Sec. 4 on the CPU; returns a dict of FP64 arrays."""
+    sc, sconn, sv = _f64(src.coords), _i32(src.conn), _f64(src.values)
+    tc, tconn = _f64(tgt.coords), _i32(tgt.conn)
+    dim, nf = sc.shape[1], sv.shape[0]
+    nvt, net = tc.shape[0], tconn.shape[0]
+    p = _Params(prec, samples_per_elem, seed, stream, alpha, grid_scale_L, cg_tol, cg_max_iter)
+    st = _Stats()
+    out = {k: np.zeros((nf, nvt)) for k in ("g", "b_g", "b_res", "b", "u")}
+    se = np.zeros((net, samples_per_elem), np.int32) if want_sample_elem else None
+    lib().orc_transfer(dim, ctypes.byref(p), sc.shape[0], sc, sconn.shape[0], sconn, nf, sv,
+                       nvt, tc, net, tconn, out["g"], out["b_g"], out["b_res"], out["b"],
+                       out["u"], None if se is None else se.ctypes.data_as(_vp),
+                       ctypes.byref(st))
+    out.update(cg_iters=st.cg_iters, cg_rel_resid=st.cg_rel_resid,
+               fallback_queries=st.fallback_queries, empty_queries=st.empty_queries)
+    if se is not None:
+        out["sample_elem"] = se
+    return out
+
+
+def integral_p1(coords, conn, values):
+    coords, conn = _f64(coords), _i32(conn)
+    return lib().orc_integral_p1(coords.shape[1], coords.shape[0], coords, conn.shape[0],
+                                 conn, _f64(values))
+
+
+def mi_load_vector_2d(src, tgt, field=0):
+    sc, tc = _f64(src.coords), _f64(tgt.coords)
+    b = np.zeros(tc.shape[0])
+    lib().orc_mi_load_vector_2d(sc.shape[0], sc, src.conn.shape[0], _i32(src.conn),
+                                _f64(src.values[field]), tc.shape[0], tc, tgt.conn.shape[0],
+                                _i32(tgt.conn), b)
+    return b
+
+
+def l2_error_2d(src, tgt, tgt_values, field=0):
+    sc, tc = _f64(src.coords), _f64(tgt.coords)
+    e, n = ctypes.c_double(), ctypes.c_double()
+    lib().orc_l2_error_2d(sc.shape[0], sc, src.conn.shape[0], _i32(src.conn),
+                          _f64(src.values[field]), tc.shape[0], tc, tgt.conn.shape[0],
+                          _i32(tgt.conn), _f64(tgt_values), ctypes.byref(e), ctypes.byref(n))
+    return e.value, n.value
+
+
+def _declare_mlp(L):
+    pass

@@ -1,0 +1,333 @@
+/*
+ * Oracle: point location of the black-box source query (Sec. 4, step 4) in a
+ * uniform grid (Sec. 5.3: nx = ny = int(L sqrt(#elements))), and P1
+ * evaluation of the source field. TEST INFRASTRUCTURE ONLY (see oracle.h).
+ *
+ * Reading of the unstated parts:
+ *   - cells per axis: the largest n >= 1 with n^d <= L^d * #elements (2D:
+ *     int(L sqrt(#elements)) as in the paper; 3D: the cube-root analogue);
+ *   - grid box: min/max of the source node coordinates; per-axis scale
+ *     inv = n / (max - min) in FP64, rounded once to the path precision P;
+ *   - cell of a coordinate x: clamp(floor((x - min) * inv), 0, n - 1) in P.
+ *     It is monotone in x, so a point inside an element's bounding box falls
+ *     in one of the cells the element is registered in;
+ *   - each element is registered in every cell its bounding box overlaps;
+ *     a cell lists its elements in ascending id;
+ *   - predicate: barycentric coordinates mu from the element's inverse affine
+ *     map. The map coefficients are formed in FP64 from the vertex
+ *     coordinates and rounded to P once; mu is then evaluated in P with fused
+ *     multiply-adds in a fixed order. The point is accepted when all mu >= 0;
+ *   - the first accepting candidate (ascending id) wins; if none accepts, the
+ *     candidate with the largest min(mu) wins (ties to the lower id); an empty
+ *     cell yields -1.
+ */
+#include "oracle.h"
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+struct orc_grid {
+    int prec, dim;
+    int32_t n[3];
+    double lo[3];      /* grid box minimum (a P value) */
+    double inv[3];     /* n / extent rounded to P */
+    int64_t ncells, nitems;
+    int64_t* start;
+    int32_t* items;
+    /* source mesh (coordinates rounded to P) */
+    int64_t nv, ne;
+    double* coords;
+    const int32_t* conn;
+};
+
+static double to_prec(int prec, double x) { return prec == 1 ? (double)(float)x : x; }
+
+static int32_t cells_per_axis(int dim, int64_t ne, double L)
+{
+    const double target = (dim == 2 ? L * L : L * L * L) * (double)ne;
+    double r = dim == 2 ? sqrt(target) : cbrt(target);
+    int64_t n = (int64_t)floor(r);
+    if (n < 1) n = 1;
+    /* exact fix-up of the floating-point root */
+    for (;;) {
+        double nn = (double)(n + 1);
+        double p = dim == 2 ? nn * nn : nn * nn * nn;
+        if (p <= target) ++n; else break;
+    }
+    for (;;) {
+        double nn = (double)n;
+        double p = dim == 2 ? nn * nn : nn * nn * nn;
+        if (n > 1 && p > target) --n; else break;
+    }
+    return (int32_t)n;
+}
+
+static int32_t cell_axis(const orc_grid* g, int a, double x)
+{
+    double fl;
+    if (g->prec == 1) {
+        float d = (float)x - (float)g->lo[a];
+        float s = d * (float)g->inv[a];
+        fl = (double)floorf(s);
+    } else {
+        double d = x - g->lo[a];
+        double s = d * g->inv[a];
+        fl = floor(s);
+    }
+    if (!(fl >= 0.0)) return 0;
+    if (fl > (double)(g->n[a] - 1)) return g->n[a] - 1;
+    return (int32_t)fl;
+}
+
+/* barycentric coordinates of X in element e, evaluated in precision P from
+ * the element's inverse affine map (coefficients formed in FP64, rounded). */
+static void predicate_mu(int prec, int dim, const double* coords, const int32_t* conn,
+                         int32_t e, const double* X, double* mu)
+{
+    const int k = dim + 1;
+    const double* a = coords + (int64_t)conn[(int64_t)e * k + 0] * dim;
+    if (dim == 2) {
+        const double* b = coords + (int64_t)conn[(int64_t)e * k + 1] * dim;
+        const double* c = coords + (int64_t)conn[(int64_t)e * k + 2] * dim;
+        const double e1x = b[0] - a[0], e1y = b[1] - a[1];
+        const double e2x = c[0] - a[0], e2y = c[1] - a[1];
+        const double det = e1x * e2y - e2x * e1y;
+        const double i00 = e2y / det, i01 = -e2x / det;
+        const double i10 = -e1y / det, i11 = e1x / det;
+        if (prec == 1) {
+            const float dx = (float)X[0] - (float)a[0], dy = (float)X[1] - (float)a[1];
+            const float m1 = fmaf((float)i01, dy, (float)i00 * dx);
+            const float m2 = fmaf((float)i11, dy, (float)i10 * dx);
+            const float m0 = (1.0f - m1) - m2;
+            mu[0] = m0; mu[1] = m1; mu[2] = m2;
+        } else {
+            const double dx = X[0] - a[0], dy = X[1] - a[1];
+            const double m1 = fma(i01, dy, i00 * dx);
+            const double m2 = fma(i11, dy, i10 * dx);
+            mu[0] = (1.0 - m1) - m2; mu[1] = m1; mu[2] = m2;
+        }
+    } else {
+        const double* b = coords + (int64_t)conn[(int64_t)e * k + 1] * dim;
+        const double* c = coords + (int64_t)conn[(int64_t)e * k + 2] * dim;
+        const double* d = coords + (int64_t)conn[(int64_t)e * k + 3] * dim;
+        const double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+        const double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+        const double e3[3] = {d[0] - a[0], d[1] - a[1], d[2] - a[2]};
+        /* rows of the inverse Jacobian: (e2 x e3, e3 x e1, e1 x e2) / det */
+        const double c23[3] = {e2[1] * e3[2] - e2[2] * e3[1], e2[2] * e3[0] - e2[0] * e3[2],
+                               e2[0] * e3[1] - e2[1] * e3[0]};
+        const double c31[3] = {e3[1] * e1[2] - e3[2] * e1[1], e3[2] * e1[0] - e3[0] * e1[2],
+                               e3[0] * e1[1] - e3[1] * e1[0]};
+        const double c12[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                               e1[0] * e2[1] - e1[1] * e2[0]};
+        const double det = (e1[0] * c23[0] + e1[1] * c23[1]) + e1[2] * c23[2];
+        double r[3][3];
+        for (int q = 0; q < 3; ++q) {
+            r[0][q] = c23[q] / det; r[1][q] = c31[q] / det; r[2][q] = c12[q] / det;
+        }
+        if (prec == 1) {
+            const float dx = (float)X[0] - (float)a[0], dy = (float)X[1] - (float)a[1],
+                        dz = (float)X[2] - (float)a[2];
+            float m[3];
+            for (int q = 0; q < 3; ++q)
+                m[q] = fmaf((float)r[q][2], dz, fmaf((float)r[q][1], dy, (float)r[q][0] * dx));
+            mu[0] = ((1.0f - m[0]) - m[1]) - m[2];
+            mu[1] = m[0]; mu[2] = m[1]; mu[3] = m[2];
+        } else {
+            const double dx = X[0] - a[0], dy = X[1] - a[1], dz = X[2] - a[2];
+            double m[3];
+            for (int q = 0; q < 3; ++q)
+                m[q] = fma(r[q][2], dz, fma(r[q][1], dy, r[q][0] * dx));
+            mu[0] = ((1.0 - m[0]) - m[1]) - m[2];
+            mu[1] = m[0]; mu[2] = m[1]; mu[3] = m[2];
+        }
+    }
+}
+
+/* scan candidates in the given order; returns status 0/1/2 */
+static int scan_candidates(int prec, int dim, const double* coords, const int32_t* conn,
+                           const int32_t* cand, int64_t ncand, const double* X, int32_t* elem)
+{
+    int32_t best = -1;
+    double best_score = -INFINITY;
+    for (int64_t q = 0; q < ncand; ++q) {
+        const int32_t e = cand[q];
+        double mu[4];
+        predicate_mu(prec, dim, coords, conn, e, X, mu);
+        double mn = mu[0];
+        for (int m = 1; m <= dim; ++m) if (mu[m] < mn) mn = mu[m];
+        if (mn >= 0.0) { *elem = e; return 0; }
+        if (best < 0 || mn > best_score) { best = e; best_score = mn; }
+    }
+    *elem = best;
+    return best < 0 ? 2 : 1;
+}
+
+static double* rounded_coords(int prec, int dim, int64_t nv, const double* coords)
+{
+    double* c = (double*)malloc(sizeof(double) * (size_t)(nv * dim));
+    for (int64_t i = 0; i < nv * dim; ++i) c[i] = to_prec(prec, coords[i]);
+    return c;
+}
+
+orc_grid* orc_grid_build(int prec, int dim, int64_t nv, const double* coords,
+                         int64_t ne, const int32_t* conn, double grid_scale_L)
+{
+    orc_grid* g = (orc_grid*)calloc(1, sizeof(orc_grid));
+    const int k = dim + 1;
+    g->prec = prec; g->dim = dim; g->nv = nv; g->ne = ne; g->conn = conn;
+    g->coords = rounded_coords(prec, dim, nv, coords);
+    const int32_t n = cells_per_axis(dim, ne, grid_scale_L);
+    g->ncells = 1;
+    for (int a = 0; a < 3; ++a) g->n[a] = 1;
+    for (int a = 0; a < dim; ++a) {
+        double lo = INFINITY, hi = -INFINITY;
+        for (int64_t i = 0; i < nv; ++i) {
+            const double x = g->coords[i * dim + a];
+            if (x < lo) lo = x;
+            if (x > hi) hi = x;
+        }
+        g->n[a] = n;
+        g->lo[a] = lo;
+        g->inv[a] = to_prec(prec, (double)n / (hi - lo));
+        g->ncells *= n;
+    }
+    /* pass 1: count registrations per cell; pass 2: fill in element order */
+    int64_t* count = (int64_t*)calloc((size_t)g->ncells + 1, sizeof(int64_t));
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int64_t e = 0; e < ne; ++e) {
+            int32_t c0[3] = {0, 0, 0}, c1[3] = {0, 0, 0};
+            for (int a = 0; a < dim; ++a) {
+                double lo = INFINITY, hi = -INFINITY;
+                for (int m = 0; m < k; ++m) {
+                    const double x = g->coords[(int64_t)conn[e * k + m] * dim + a];
+                    if (x < lo) lo = x;
+                    if (x > hi) hi = x;
+                }
+                c0[a] = cell_axis(g, a, lo);
+                c1[a] = cell_axis(g, a, hi);
+            }
+            for (int32_t iz = c0[2]; iz <= c1[2]; ++iz)
+                for (int32_t iy = c0[1]; iy <= c1[1]; ++iy)
+                    for (int32_t ix = c0[0]; ix <= c1[0]; ++ix) {
+                        const int64_t cell = ((int64_t)iz * g->n[1] + iy) * g->n[0] + ix;
+                        if (pass == 0) count[cell + 1]++;
+                        else g->items[g->start[cell] + count[cell]++] = (int32_t)e;
+                    }
+        }
+        if (pass == 0) {
+            g->start = (int64_t*)malloc(sizeof(int64_t) * (size_t)(g->ncells + 1));
+            g->start[0] = 0;
+            for (int64_t c = 0; c < g->ncells; ++c) g->start[c + 1] = g->start[c] + count[c + 1];
+            g->nitems = g->start[g->ncells];
+            g->items = (int32_t*)malloc(sizeof(int32_t) * (size_t)(g->nitems > 0 ? g->nitems : 1));
+            memset(count, 0, sizeof(int64_t) * (size_t)(g->ncells + 1));
+        }
+    }
+    free(count);
+    return g;
+}
+
+void orc_grid_free(orc_grid* g)
+{
+    if (!g) return;
+    free(g->start); free(g->items); free(g->coords); free(g);
+}
+
+void orc_grid_shape(const orc_grid* g, int32_t n_out[3], int64_t* ncells, int64_t* nitems)
+{
+    for (int a = 0; a < 3; ++a) n_out[a] = g->n[a];
+    *ncells = g->ncells;
+    *nitems = g->nitems;
+}
+
+void orc_grid_csr(const orc_grid* g, int64_t* start, int32_t* items)
+{
+    memcpy(start, g->start, sizeof(int64_t) * (size_t)(g->ncells + 1));
+    memcpy(items, g->items, sizeof(int32_t) * (size_t)g->nitems);
+}
+
+static int locate_one(const orc_grid* g, const double* Xin, int32_t* elem)
+{
+    double X[3] = {0, 0, 0};
+    for (int a = 0; a < g->dim; ++a) X[a] = to_prec(g->prec, Xin[a]);
+    int32_t ci[3] = {0, 0, 0};
+    for (int a = 0; a < g->dim; ++a) ci[a] = cell_axis(g, a, X[a]);
+    const int64_t cell = ((int64_t)ci[2] * g->n[1] + ci[1]) * g->n[0] + ci[0];
+    return scan_candidates(g->prec, g->dim, g->coords, g->conn, g->items + g->start[cell],
+                           g->start[cell + 1] - g->start[cell], X, elem);
+}
+
+void orc_grid_locate(const orc_grid* g, int64_t npts, const double* pts,
+                     int32_t* elem_out, int32_t* status_out)
+{
+    for (int64_t i = 0; i < npts; ++i) {
+        int32_t e;
+        int st = locate_one(g, pts + i * g->dim, &e);
+        elem_out[i] = e;
+        if (status_out) status_out[i] = st;
+    }
+}
+
+void orc_brute_locate(int prec, int dim, int64_t nv, const double* coords, int64_t ne,
+                      const int32_t* conn, int64_t npts, const double* pts,
+                      int32_t* elem_out, int32_t* status_out)
+{
+    double* c = rounded_coords(prec, dim, nv, coords);
+    int32_t* all = (int32_t*)malloc(sizeof(int32_t) * (size_t)(ne > 0 ? ne : 1));
+    for (int64_t e = 0; e < ne; ++e) all[e] = (int32_t)e;
+    for (int64_t i = 0; i < npts; ++i) {
+        double X[3] = {0, 0, 0};
+        for (int a = 0; a < dim; ++a) X[a] = to_prec(prec, pts[i * dim + a]);
+        int32_t e;
+        int st = scan_candidates(prec, dim, c, conn, all, ne, X, &e);
+        elem_out[i] = e;
+        if (status_out) status_out[i] = st;
+    }
+    free(all); free(c);
+}
+
+/* P1 evaluation in FP64: barycentric coordinates by Cramer's rule (ratios of
+ * signed areas / volumes), then sum_m mu_m f_m. */
+void orc_eval_p1(int dim, const double* coords, const int32_t* conn, int nf, int64_t nv,
+                 const double* values, int32_t e, const double* X, double* f_out)
+{
+    const int k = dim + 1;
+    const int32_t* v = conn + (int64_t)e * k;
+    double mu[4];
+    if (dim == 2) {
+        const double* a = coords + (int64_t)v[0] * 2;
+        const double* b = coords + (int64_t)v[1] * 2;
+        const double* c = coords + (int64_t)v[2] * 2;
+        const double bax = b[0] - a[0], bay = b[1] - a[1], cax = c[0] - a[0], cay = c[1] - a[1];
+        const double pax = X[0] - a[0], pay = X[1] - a[1];
+        const double area = bax * cay - cax * bay;
+        mu[1] = (pax * cay - cax * pay) / area;
+        mu[2] = (bax * pay - pax * bay) / area;
+        mu[0] = 1.0 - mu[1] - mu[2];
+    } else {
+        const double* p[4];
+        for (int m = 0; m < 4; ++m) p[m] = coords + (int64_t)v[m] * 3;
+        double E[3][3], Q[3];
+        for (int q = 0; q < 3; ++q) {
+            E[0][q] = p[1][q] - p[0][q];
+            E[1][q] = p[2][q] - p[0][q];
+            E[2][q] = p[3][q] - p[0][q];
+            Q[q] = X[q] - p[0][q];
+        }
+#define DET3(A, B, C) ((A)[0] * ((B)[1] * (C)[2] - (B)[2] * (C)[1]) \
+                     - (A)[1] * ((B)[0] * (C)[2] - (B)[2] * (C)[0]) \
+                     + (A)[2] * ((B)[0] * (C)[1] - (B)[1] * (C)[0]))
+        const double vol = DET3(E[0], E[1], E[2]);
+        mu[1] = DET3(Q, E[1], E[2]) / vol;
+        mu[2] = DET3(E[0], Q, E[2]) / vol;
+        mu[3] = DET3(E[0], E[1], Q) / vol;
+#undef DET3
+        mu[0] = 1.0 - mu[1] - mu[2] - mu[3];
+    }
+    for (int f = 0; f < nf; ++f) {
+        double s = 0.0;
+        for (int m = 0; m < k; ++m) s += mu[m] * values[(int64_t)f * nv + v[m]];
+        f_out[f] = s;
+    }
+}

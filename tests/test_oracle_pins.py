@@ -1,0 +1,451 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics
+(closed forms, invariants, textbook special cases, brute force), not against
+the oracle itself. CPU only."""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_two_tri():
+    rows = {}
+    with open(os.path.join(GOLDEN, "two_triangle_square.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            key, *vals = line.split()
+            rows[key] = [float(v) for v in vals]
+    coords = np.array(rows["nodes"]).reshape(-1, 2)
+    conn = np.array(rows["tris"], dtype=np.int32).reshape(-1, 3)
+    return coords, conn, rows
+
+
+# --------------------------------------------------------------------------
+# random numbers
+# --------------------------------------------------------------------------
+def _philox_block(orc, n, key=(0x1234, 0xABCD), word2=7):
+    out = np.zeros((n, 4), np.uint32)
+    for i in range(n):
+        out[i] = orc.philox4x32_10([i, i >> 3, word2, 0], key)
+    return out
+
+
+def test_philox_uniform_bytes_chi2(orc):
+    w = _philox_block(orc, 4096)
+    byts = w.view(np.uint8).ravel()
+    cnt = np.bincount(byts, minlength=256)
+    exp = byts.size / 256
+    chi2 = ((cnt - exp) ** 2 / exp).sum()
+    # chi2 with 255 dof: mean 255, sd 22.6; 6 sd bounds
+    assert 255 - 6 * 22.6 < chi2 < 255 + 6 * 22.6
+
+
+def test_philox_avalanche(orc):
+    """Flipping any single counter or key bit flips each output bit with
+    probability 1/2 (a reduced-round or mis-wired Philox fails this)."""
+    rng = np.random.default_rng(0)
+    trials = 48
+    worst = 0.0
+    for bit in list(range(0, 128, 5)) + [127]:
+        flips = np.zeros(128)
+        for _ in range(trials):
+            ctr = rng.integers(0, 2 ** 32, 4, dtype=np.uint64).astype(np.uint32)
+            key = rng.integers(0, 2 ** 32, 2, dtype=np.uint64).astype(np.uint32)
+            a = orc.philox4x32_10(ctr, key)
+            c2 = ctr.copy()
+            c2[bit // 32] ^= np.uint32(1 << (bit % 32))
+            b = orc.philox4x32_10(c2, key)
+            x = np.bitwise_xor(a, b)
+            flips += np.unpackbits(x.view(np.uint8))
+        frac = flips.sum() / (128 * trials)
+        worst = max(worst, abs(frac - 0.5))
+    assert worst < 0.03
+
+
+def test_philox_distinct_counters_distinct_outputs(orc):
+    w = _philox_block(orc, 20000)
+    keys = set(map(bytes, w))
+    assert len(keys) == w.shape[0]
+
+
+def test_uniform_conversion_exact_open_interval(orc):
+    for x in [0, 1, 255, 256, 2 ** 31, 2 ** 32 - 1]:
+        u32 = orc.u01(x, 1)
+        u64 = orc.u01(x, 0)
+        assert 0.0 < u32 < 1.0 and 0.0 < u64 < 1.0
+        assert u32 == ((x >> 8) | 1) / 2 ** 24
+        assert u64 == (x + 0.5) / 2 ** 32
+
+
+# --------------------------------------------------------------------------
+# sample map (Sec. 4 step 3; Osada et al. 2002 in 2D, simplex spacings in 3D)
+# --------------------------------------------------------------------------
+REF = {2: np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]]),
+       3: np.array([[0.0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]])}
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_sample_moments_and_uniformity(orc, dim, prec):
+    """E[lambda_i] = 1/(d+1), E[lambda_i lambda_j] = (1+delta_ij)/((d+1)(d+2))
+    (Dirichlet(1,...,1) moments of the uniform law on the simplex); the 2^d
+    congruent sub-simplices of a midpoint split (corners: lambda_m >= 1/2)
+    each receive probability 1/2^d."""
+    k = dim + 1
+    lam_all = []
+    for t in range(200):
+        lam, X = orc.sample_element(prec, dim, 11, 0, t, 512, REF[dim])
+        lam_all.append(lam)
+        assert np.all(lam >= 0.0)
+        assert np.allclose(lam.sum(1), 1.0, atol=1e-6 if prec else 1e-15)
+        assert np.allclose(X, lam @ REF[dim], atol=1e-6 if prec else 1e-15)
+    lam = np.concatenate(lam_all)
+    n = lam.shape[0]
+    m1 = lam.mean(0)
+    sd1 = math.sqrt(dim / ((dim + 1) ** 2 * (dim + 2)) / n)
+    assert np.all(np.abs(m1 - 1 / k) < 6 * sd1)
+    second = lam.T @ lam / n
+    expect = (np.ones((k, k)) + np.eye(k)) / (k * (k + 1))
+    assert np.all(np.abs(second - expect) < 6 * 0.3 / math.sqrt(n))
+    corner = [(lam[:, m] >= 0.5).mean() for m in range(k)]
+    p = 1.0 / 2 ** dim
+    for c in corner:
+        assert abs(c - p) < 6 * math.sqrt(p * (1 - p) / n)
+
+
+def test_sample_map_osada_formula(orc):
+    """Hand check of the 2D map for one Philox draw: (xi, eta) -> (1-s, s(1-eta), s eta)."""
+    w = orc.philox4x32_10([0, 5, 3, 0], [9, 0])
+    lam, X = orc.sample_element(0, 2, 9, 3, 5, 2, REF[2])
+    xi0, eta0 = (w[0] + 0.5) / 2 ** 32, (w[1] + 0.5) / 2 ** 32
+    xi1, eta1 = (w[2] + 0.5) / 2 ** 32, (w[3] + 0.5) / 2 ** 32
+    for j, (xi, eta) in enumerate([(xi0, eta0), (xi1, eta1)]):
+        s = math.sqrt(xi)
+        assert np.allclose(lam[j], [1 - s, s * (1 - eta), s * eta], rtol=0, atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# point location
+# --------------------------------------------------------------------------
+def test_golden_two_triangle_locate_eval_mass(orc):
+    coords, conn, rows = _golden_two_tri()
+    loc = np.array(rows["locate"]).reshape(-1, 3)
+    for prec in (0, 1):
+        g = orc.Grid(prec, coords, conn)
+        e, st = g.locate(loc[:, :2])
+        assert list(e) == [int(v) for v in loc[:, 2]]
+        assert np.all(st == 0)
+    vals = np.array([[0.0, 1.0, 3.0, 2.0]])
+    ex, ey, fexp = rows["eval"]
+    assert orc.eval_p1(coords, conn, vals, 0, [ex, ey])[0] == pytest.approx(fexp, abs=1e-15)
+    rp, col, val = orc.mass_csr(coords, conn)
+    dense = np.zeros((4, 4))
+    for i in range(4):
+        dense[i, col[rp[i]:rp[i + 1]]] = val[rp[i]:rp[i + 1]]
+    assert np.allclose(dense * 24, np.array(rows["M24"]).reshape(4, 4), atol=1e-14)
+
+
+def _exact_bary(coords, conn, e, p):
+    P = [[Fraction(float(c)) for c in coords[v]] for v in conn[e]]
+    X = [Fraction(float(c)) for c in p]
+    d = len(X)
+    if d == 2:
+        (ax, ay), (bx, by), (cx, cy) = P
+        det = (bx - ax) * (cy - ay) - (cx - ax) * (by - ay)
+        m1 = ((X[0] - ax) * (cy - ay) - (cx - ax) * (X[1] - ay)) / det
+        m2 = ((bx - ax) * (X[1] - ay) - (X[0] - ax) * (by - ay)) / det
+        return [1 - m1 - m2, m1, m2]
+    a = P[0]
+    E = [[P[i][q] - a[q] for q in range(3)] for i in (1, 2, 3)]
+    Q = [X[q] - a[q] for q in range(3)]
+
+    def det3(A, B, C):
+        return (A[0] * (B[1] * C[2] - B[2] * C[1]) - A[1] * (B[0] * C[2] - B[2] * C[0])
+                + A[2] * (B[0] * C[1] - B[1] * C[0]))
+    v = det3(*E)
+    m = [det3(Q, E[1], E[2]) / v, det3(E[0], Q, E[2]) / v, det3(E[0], E[1], Q) / v]
+    return [1 - sum(m)] + m
+
+
+@pytest.mark.parametrize("dim,prec", [(2, 0), (2, 1), (3, 0), (3, 1)])
+def test_grid_locate_equals_brute_force_and_exact_containment(orc, dim, prec):
+    """The grid answer equals a scan of every element with the same rule; the
+    accepted element contains the point in exact rational arithmetic up to the
+    predicate's rounding."""
+    src = W.jittered_tri_mesh(7, 3) if dim == 2 else W.jittered_kuhn_mesh(3, 3)
+    coords = src.coords.astype(np.float32).astype(np.float64) if prec else src.coords
+    rng = np.random.default_rng(1)
+    pts = rng.random((3000, dim))
+    # add mesh vertices and edge midpoints: the tie cases
+    pts = np.concatenate([pts, coords, coords[src.conn[:, :2]].mean(1)])
+    if prec:
+        pts = pts.astype(np.float32).astype(np.float64)
+    g = orc.Grid(prec, coords, src.conn)
+    eg, sg = g.locate(pts)
+    eb, sb = orc.brute_locate(prec, coords, src.conn, pts)
+    tol = 1e-5 if prec else 1e-12
+    mism = 0
+    for i in range(pts.shape[0]):
+        assert eg[i] >= 0
+        mu = _exact_bary(coords, src.conn, eg[i], pts[i])
+        assert min(mu) >= -tol, (i, mu)
+        if eg[i] != eb[i]:
+            # both candidates must contain the point up to rounding (a tie on a
+            # shared face); otherwise the grid dropped a candidate
+            mism += 1
+            mu_b = _exact_bary(coords, src.conn, eb[i], pts[i])
+            assert min(mu_b) >= -tol
+            assert abs(min(mu)) <= tol or abs(min(mu_b)) <= tol
+    assert mism <= pts.shape[0] // 50
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_grid_structure(orc, dim):
+    src = W.jittered_tri_mesh(9, 2) if dim == 2 else W.jittered_kuhn_mesh(3, 2)
+    g = orc.Grid(0, src.coords, src.conn, 1.0)
+    n, nc, ni = g.shape()
+    E = src.nelems
+    expect_n = int(math.isqrt(E)) if dim == 2 else max(k for k in range(1, 200) if k ** 3 <= E)
+    assert n[0] == expect_n and nc == expect_n ** dim
+    start, items = g.csr()
+    assert start[0] == 0 and start[-1] == ni and np.all(np.diff(start) >= 0)
+    for c in range(nc):
+        seg = items[start[c]:start[c + 1]]
+        assert np.all(np.diff(seg) > 0)          # ascending element ids
+    # every element appears in exactly the cells of its bounding box
+    lo = src.coords.min(0)
+    hi = src.coords.max(0)
+    counts = np.bincount(items, minlength=E)
+    for e in range(E):
+        bb0 = src.coords[src.conn[e]].min(0)
+        bb1 = src.coords[src.conn[e]].max(0)
+        c0 = np.clip(np.floor((bb0 - lo) * (expect_n / (hi - lo))), 0, expect_n - 1)
+        c1 = np.clip(np.floor((bb1 - lo) * (expect_n / (hi - lo))), 0, expect_n - 1)
+        assert counts[e] == int(np.prod(c1 - c0 + 1))
+
+
+# --------------------------------------------------------------------------
+# mass matrix and solve (Eqs. mass_matrix, galerkin_system)
+# --------------------------------------------------------------------------
+def _dense(rp, col, val, n):
+    A = np.zeros((n, n))
+    for i in range(n):
+        A[i, col[rp[i]:rp[i + 1]]] += val[rp[i]:rp[i + 1]]
+    return A
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_mass_matrix_closed_forms(orc, dim):
+    """u^T M u = int (P1 interpolant)^2; for nodal values of a linear field
+    L = a + b.x on the unit square/cube this equals the closed form
+    a^2 + a sum(b) + sum(b^2)/3 + sum_{i<j} b_i b_j / 2."""
+    m = W.delaunay_tri_mesh(60, 5, 4) if dim == 2 else W.jittered_kuhn_mesh(3, 4)
+    rp, col, val = orc.mass_csr(m.coords, m.conn)
+    A = _dense(rp, col, val, m.nnodes)
+    assert np.allclose(A, A.T, atol=1e-17)
+    assert np.all(np.linalg.eigvalsh(A) > 0)
+    assert A.sum() == pytest.approx(1.0, abs=1e-13)
+    assert np.allclose(A.sum(1), orc.lumped_mass(m.coords, m.conn), atol=1e-16)
+    coef = np.array([0.7, -1.3, 2.1, 0.4][: dim + 1])
+    u = coef[0] + m.coords @ coef[1:]
+    a, b = coef[0], coef[1:]
+    cross = sum(b[i] * b[j] for i in range(dim) for j in range(i + 1, dim))
+    exact = a * a + a * b.sum() + (b ** 2).sum() / 3 + cross / 2
+    assert u @ A @ u == pytest.approx(exact, rel=1e-12)
+
+
+def test_pcg_matches_dense_solve(orc):
+    m = W.delaunay_tri_mesh(150, 6, 5)
+    rp, col, val = orc.mass_csr(m.coords, m.conn)
+    A = _dense(rp, col, val, m.nnodes)
+    b = np.random.default_rng(2).standard_normal(m.nnodes)
+    x, it, rr = orc.pcg(rp, col, val, b, tol=1e-13, max_iter=1000)
+    assert rr <= 1e-13 and 0 < it < 200
+    xd = np.linalg.solve(A, b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-11
+
+
+# --------------------------------------------------------------------------
+# the transfer (Sec. 4)
+# --------------------------------------------------------------------------
+def _pair(dim, ns=6, seed=0):
+    if dim == 2:
+        return W.jittered_tri_mesh(ns, seed), W.delaunay_tri_mesh(40, 4, seed + 1)
+    return W.jittered_kuhn_mesh(3, seed), W.morton_reorder(W.jittered_kuhn_mesh(2, seed + 1))
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_linear_field_is_reproduced(orc, dim, prec):
+    """f linear and alpha = 1: f^s - g vanishes identically (both are the same
+    linear function), so the residual estimate is zero up to rounding, b equals
+    M f(nodes) and u equals f(nodes) (Eq. cv_load_expanded)."""
+    s, t = _pair(dim)
+    if prec:
+        s, t = W.as_precision(s, np.float32), W.as_precision(t, np.float32)
+    f = W.linear_field([1.5, 0.3, -0.7, 0.2][: dim + 1])
+    s = W.with_values(s, [f], np.float64)
+    r = orc.transfer(s, t, prec, 12, seed=3, cg_tol=1e-14)
+    fn = f(t.coords.astype(np.float64))
+    rp, col, val = orc.mass_csr(t.coords, t.conn)
+    Mf = _dense(rp, col, val, t.nnodes) @ fn
+    tol = 1e-6 if prec else 1e-13
+    assert np.linalg.norm(r["b"][0] - Mf) / np.linalg.norm(Mf) < tol
+    assert np.linalg.norm(r["u"][0] - fn) / np.linalg.norm(fn) < (1e-6 if prec else 1e-11)
+    assert np.abs(r["b_res"][0]).max() < (1e-6 if prec else 1e-14)
+
+
+@pytest.mark.parametrize("alpha", [0.0, 0.3, 1.0])
+def test_constant_field_sum_b(orc, alpha):
+    """f = c: every estimate of int c psi_i sums to c |Omega| (partition of
+    unity of the target basis)."""
+    s, t = _pair(2)
+    s = W.with_values(s, [lambda x: np.full(x.shape[0], 2.5)], np.float64)
+    r = orc.transfer(s, t, 0, 8, seed=1, alpha=alpha)
+    assert r["b"][0].sum() == pytest.approx(2.5, abs=1e-13)
+
+
+def test_load_vector_sum_identity(orc):
+    """sum_i b_i = alpha int g + sum_t |T|/N sum_j (f^s - alpha g)(X_j)
+    (partition of unity applied to Eq. cv_load_expanded), recomputed here
+    from the oracle's separate sampling / location / evaluation entry points."""
+    s, t = _pair(2)
+    s = W.with_values(s, [W.paper_f3])
+    N, alpha, seed = 6, 0.7, 4
+    r = orc.transfer(s, t, 0, N, seed=seed, alpha=alpha)
+    grid = orc.Grid(0, s.coords, s.conn)
+    g = r["g"][0]
+    assert r["b_g"][0].sum() == pytest.approx(alpha * orc.integral_p1(t.coords, t.conn, g), rel=1e-13)
+    total = 0.0
+    for e in range(t.nelems):
+        xyz = t.coords[t.conn[e]]
+        vol = 0.5 * np.linalg.det(np.array([xyz[1] - xyz[0], xyz[2] - xyz[0]]))
+        lam, X = orc.sample_element(0, 2, seed, 0, e, N, xyz)
+        el, _ = grid.locate(X)
+        acc = 0.0
+        for j in range(N):
+            fs = orc.eval_p1(s.coords, s.conn, s.values, el[j], X[j])[0]
+            acc += fs - alpha * lam[j] @ g[t.conn[e]]
+        total += vol / N * acc
+    assert r["b_res"][0].sum() == pytest.approx(total, rel=1e-11, abs=1e-14)
+
+
+def test_mesh_intersection_judge_closed_forms(orc):
+    """The clipping judge: exact for a linear source (b = M f(nodes)), sums to
+    int f^s for any P1 source, and equals M_s f when both meshes coincide."""
+    s, t = _pair(2)
+    lin = W.linear_field([1.0, 2.0, -3.0])
+    sl = W.with_values(s, [lin])
+    b = orc.mi_load_vector_2d(sl, t)
+    rp, col, val = orc.mass_csr(t.coords, t.conn)
+    Mf = _dense(rp, col, val, t.nnodes) @ lin(t.coords)
+    assert np.allclose(b, Mf, rtol=0, atol=1e-13)
+    sf = W.with_values(s, [W.paper_f2])
+    b2 = orc.mi_load_vector_2d(sf, t)
+    assert b2.sum() == pytest.approx(orc.integral_p1(s.coords, s.conn, sf.values[0]), rel=1e-13)
+    b3 = orc.mi_load_vector_2d(sf, s)
+    rp, col, val = orc.mass_csr(s.coords, s.conn)
+    assert np.allclose(b3, _dense(rp, col, val, s.nnodes) @ sf.values[0], atol=1e-13)
+    # supermesh L2 error: zero for an exactly represented field, one against 0
+    e, n = orc.l2_error_2d(sf, s, sf.values[0])
+    assert e / n < 1e-12
+    e, n = orc.l2_error_2d(sf, t, np.zeros(t.nnodes))
+    assert e / n == pytest.approx(1.0, rel=1e-12)
+
+
+def test_unbiased_against_mesh_intersection(orc):
+    """E[b_hat] = b (Eq. cv_load_unbiased): the mean over R seeds of the
+    estimate approaches the exact mesh-intersection load vector within a few
+    standard errors, for alpha = 0 and alpha = 1."""
+    s, t = _pair(2, ns=5)
+    s = W.with_values(s, [W.field_sincos])
+    b_mi = orc.mi_load_vector_2d(s, t)
+    for alpha in (0.0, 1.0):
+        bs = np.stack([orc.transfer(s, t, 0, 8, seed=sd, alpha=alpha, cg_max_iter=1)["b"][0]
+                       for sd in range(300)])
+        mean, se = bs.mean(0), bs.std(0, ddof=1) / math.sqrt(bs.shape[0])
+        # entries whose estimate has (almost) no variance are compared at the
+        # FP64 rounding level instead
+        se = np.sqrt(se ** 2 + (1e-13 * np.abs(b_mi).max()) ** 2)
+        z = (mean - b_mi) / se
+        assert np.abs(z).max() < 5.0
+        assert abs(z.mean()) < 5.0 / math.sqrt(z.size)
+
+
+def test_error_decays_as_inverse_sqrt_N(orc):
+    """RMS load-vector error ~ N^{-1/2} (Monte Carlo variance ~ 1/N)."""
+    s, t = _pair(2, ns=5)
+    s = W.with_values(s, [W.field_sincos])
+    b_mi = orc.mi_load_vector_2d(s, t)
+    Ns = [4, 16, 64, 256]
+    rms = []
+    for N in Ns:
+        errs = [np.linalg.norm(orc.transfer(s, t, 0, N, seed=sd, alpha=0.0, cg_max_iter=1)["b"][0]
+                               - b_mi) for sd in range(40)]
+        rms.append(math.sqrt(np.mean(np.square(errs))))
+    slope = np.polyfit(np.log(Ns), np.log(rms), 1)[0]
+    assert -0.56 < slope < -0.44
+
+
+def test_alpha_reduces_error(orc):
+    """Both errors decrease as alpha goes from 0 to 1 (Sec. 5.1, alpha study)."""
+    s, t = _pair(2, ns=8)
+    s = W.with_values(s, [W.paper_f3])
+    b_mi = orc.mi_load_vector_2d(s, t)
+    Is = orc.integral_p1(s.coords, s.conn, s.values[0])
+    err, cons = [], []
+    for alpha in (0.0, 0.5, 1.0):
+        e_b, e_c = [], []
+        for sd in range(30):
+            r = orc.transfer(s, t, 0, 20, seed=sd, alpha=alpha, cg_max_iter=1)
+            e_b.append(np.linalg.norm(r["b"][0] - b_mi))
+            e_c.append(r["b"][0].sum() - Is)
+        err.append(np.sqrt(np.mean(np.square(e_b))))
+        cons.append(np.sqrt(np.mean(np.square(e_c))))
+    assert err[0] > err[1] > err[2]
+    assert cons[0] > cons[1] > cons[2]
+
+
+@pytest.mark.slow
+def test_convergence_rates_in_h(orc):
+    """At alpha = 1, N = 20: E_L2 ~ h^2 and the RMS conservation error
+    ~ h^3 / sqrt(N) in 2D (Eqs. accuracy_bound_interpretation and
+    conservation_bound_interpretation)."""
+    el2, econs, hs = [], [], []
+    for n in (6, 12, 24, 48):
+        s = W.with_values(W.jittered_tri_mesh(n, 10), [W.paper_f3])
+        side = int(round(n * 0.9))
+        t = W.delaunay_tri_mesh((side - 1) ** 2, side - 1, 11)
+        Is = orc.integral_p1(s.coords, s.conn, s.values[0])
+        c, e = [], []
+        for sd in range(12):
+            r = orc.transfer(s, t, 0, 20, seed=sd, cg_tol=1e-13)
+            It = orc.lumped_mass(t.coords, t.conn) @ r["u"][0]
+            c.append((It - Is) / Is)
+            if sd < 2:
+                err, nrm = orc.l2_error_2d(s, t, r["u"][0])
+                e.append(err / nrm)
+        hs.append(1.0 / n)
+        el2.append(np.mean(e))
+        econs.append(math.sqrt(np.mean(np.square(c))))
+    s_l2 = np.polyfit(np.log(hs), np.log(el2), 1)[0]
+    s_c = np.polyfit(np.log(hs), np.log(econs), 1)[0]
+    assert 1.6 < s_l2 < 2.4
+    assert 2.4 < s_c < 3.6
+
+
+def test_conservation_at_convergence(orc):
+    """int f^t = sum_i u_i m_i = sum_i b_i once M u = b is solved (Sec. 2,
+    Eq. conservation with 1 in V_t)."""
+    s, t = _pair(2)
+    s = W.with_values(s, [W.paper_f1, W.paper_f2])
+    r = orc.transfer(s, t, 0, 10, seed=2, cg_tol=1e-14)
+    m = orc.lumped_mass(t.coords, t.conn)
+    for q in range(2):
+        assert m @ r["u"][q] == pytest.approx(r["b"][q].sum(), rel=1e-12)
