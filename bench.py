@@ -1,0 +1,413 @@
+"""Benchmark of the stochastic conservative field transfer on one GB300.
+
+A step is one pass of the whole path on one synthetic workload: build the
+source location grid and the target mass matrix, compute the control values,
+run the fused Monte Carlo assembly, solve M u = b in FP64 and evaluate the
+conservation error, i.e. sft_source_create + sft_target_create +
+sft_transfer + sft_conservation_error (+ destroy), with the meshes already
+resident in device memory when the timed region starts.
+
+Default workload ("tri4m"): 3,998,792-triangle jittered source mesh with the
+Gaussian + jump field in FP32, 2,000,000-triangle Delaunay target, N = 64
+samples per element, FP32 sampling with compensated partials, FP64 CG to 1e-10.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 launch with torchrun; every rank runs an independent replica of the
+workload (the single transfer is not sharded), and rank 0 reports the sum of
+the ranks' queries over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "source queries/s and transfer ms at fixed L2 + conservation error, vs roofline"
+WORKLOADS = {
+    "tri4m": "2D: 3,998,792-triangle jittered source (f = exp(-|x-c|^2/0.01) + 0.5 sign(x-0.5), FP32 "
+             "coords) -> 2,000,000-triangle Delaunay target, N = 64, FP32 sampling + compensated partials, "
+             "FP64 load vector and CG to 1e-10",
+    "tet5m": "3D: 4,983,504-tet jittered Kuhn source (8 Gaussians + jump at z = 0.4, FP32) -> 2,958,234-tet "
+             "target, N = 32, FP32 sampling + compensated partials, FP64 CG to 1e-10",
+}
+# algorithmic HBM bytes of the assembly kernel (minimum a black-box P1 query
+# and a target element must move): per query cell range 8 B + one candidate
+# id 4 B + the containing element record (2D 36 B, 3D 64 B); per target
+# element conn + coords + g + b read-modify-write (2D 72 B, 3D 112 B)
+BYTES_PER_QUERY = {2: 48, 3: 76}
+BYTES_PER_ELEM = {2: 72, 3: 112}
+KERNEL_FILES = ["paper_2603_00538_gb300/csrc/assemble.cu", "paper_2603_00538_gb300/csrc/common.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "assemble_traffic.txt")
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_FILES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str):
+    """DRAM bytes per launch of the assembly kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    for line in open(TRAFFIC_FILE):
+        parts = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        if parts.get("workload") == workload and parts.get("kernel_hash") == kernel_hash():
+            try:
+                return float(parts["dram_bytes_per_launch"])
+            except (KeyError, ValueError):
+                return None
+    return None
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self._stop = threading.Event()
+        self._proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self._proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
+                                           "--format=csv,noheader,nounits", "-lms", "200"],
+                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (OSError, FileNotFoundError):
+            self._proc = None
+        return self
+
+    def _read(self):
+        for line in self._proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self._proc:
+            time.sleep(0.25)
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self._proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def make_workload(name: str):
+    src, tgt, p = W.config_meshes(name)
+    return src, tgt, p
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import paper_2603_00538_gb300 as sft
+
+    rank, world, local = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    src, tgt, p = make_workload(args.workload)
+    N, tol = p["samples_per_elem"], p["cg_tol"]
+    dim = src.dim
+    prec = sft.SFT_PREC_FP32
+    stream = torch.cuda.current_stream()
+    sc, sk, sv = (torch.as_tensor(np.ascontiguousarray(a)).to(dev) for a in (src.coords, src.conn, src.values))
+    tc, tk = (torch.as_tensor(np.ascontiguousarray(a)).to(dev) for a in (tgt.coords, tgt.conn))
+    u = torch.zeros((src.nfields, tgt.nnodes), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+
+    stats_last = {}
+    cons_last = [None]
+
+    def step():
+        s = sft.sft_source_create(sc, sk, sv)
+        t = sft.sft_target_create(tc, tk)
+        _, st, _ = sft.sft_transfer(s, t, N, prec, seed=0, cg_tol=tol, u_out=u)
+        cons_last[0] = sft.sft_conservation_error(s, t, u[0])
+        stats_last.update(st)
+        s.close()
+        t.close()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    asm_ms, solve_ms, setup_ms = [], [], []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(float(k))          # evict L2 between steps (untimed)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+            asm_ms.append(stats_last["ms_assembly"])
+            solve_ms.append(stats_last["ms_solve"])
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    queries = int(stats_last["queries"])
+    ms_per_step = total_ms / args.steps
+    value = queries * world / (ms_per_step / 1e3)
+
+    # kernels launched per step (profiled once, outside the timed region)
+    launches_per_step = count_launches(step)
+
+    # end to end through the public API with host (pinned) buffers
+    e2e = run_e2e(args, src, tgt, N, tol, prec) if rank == 0 else None
+
+    # errors at which the throughput is measured
+    e_mass = cons_last[0][0]
+    e_l2, e_l2_se = estimate_l2(src, tgt, u[0].cpu().numpy(), dev) if rank == 0 else (None, None)
+
+    if rank == 0:
+        hbm, which = peaks()
+        mean_asm = float(np.mean(asm_ms))
+        alg_bytes = BYTES_PER_QUERY[dim] * tgt.nelems * N + BYTES_PER_ELEM[dim] * tgt.nelems
+        achieved = alg_bytes / (mean_asm / 1e3) / 1e9
+        traffic = measured_traffic(args.workload)
+        cpu = cpu_baseline(args, src, tgt, p) if not args.skip_cpu else None
+        line = {
+            "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}",
+                       "queries_per_step": queries, "target_elements": tgt.nelems, "samples_per_elem": N,
+                       "source_elements": src.nelems, "l2": "flushed between steps (256 MB write)",
+                       "accumulation": "FP64 load vector, CG and reductions",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "breakdown_ms": {"assembly_kernel": mean_asm, "solve": float(np.mean(solve_ms)),
+                             "step_min": min(step_ms), "step_max": max(step_ms),
+                             "transfer_call": stats_last["ms_total"], "control": stats_last["ms_control"]},
+            "assembly_queries_per_s": tgt.nelems * N / (mean_asm / 1e3),
+            "accuracy": {"E_mass": e_mass, "E_L2_estimate": e_l2, "E_L2_stderr": e_l2_se,
+                         "cg_iters": stats_last["cg_iters"], "cg_rel_resid": stats_last["cg_rel_resid"],
+                         "fallback_queries": stats_last["fallback_queries"]},
+            "roofline": {"kernel": "sft::k_assemble", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                         "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                         "peak_source": which, "algorithmic_bytes": alg_bytes},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk.summary(),
+            "gpu_launches": launches_per_step * args.steps if launches_per_step else None,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def count_launches(step):
+    try:
+        import torch
+        from torch.profiler import ProfilerActivity, profile
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            step()
+            torch.cuda.synchronize()
+        n = 0
+        for evt in prof.events():
+            name = evt.name or ""
+            if "sft" in name and ("k_" in name or "sft::" in name):
+                n += 1
+        return n or None
+    except Exception:
+        return None
+
+
+def run_e2e(args, src, tgt, N, tol, prec):
+    import torch
+    import paper_2603_00538_gb300 as sft
+    pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    sc, sk, sv, tc, tk = (pin(a) for a in (src.coords, src.conn, src.values, tgt.coords, tgt.conn))
+    u = torch.zeros((src.nfields, tgt.nnodes), dtype=torch.float64).pin_memory()
+    h2d = sum(x.numel() * x.element_size() for x in (sc, sk, sv, tc, tk))
+    d2h = u.numel() * u.element_size() + 8
+
+    def step():
+        s = sft.sft_source_create(sc, sk, sv)
+        t = sft.sft_target_create(tc, tk)
+        _, st, _ = sft.sft_transfer(s, t, N, prec, seed=0, cg_tol=tol, u_out=u)
+        e = sft.sft_conservation_error(s, t, u[0])
+        s.close()
+        t.close()
+        return st["queries"], e
+
+    for _ in range(max(1, min(args.warmup, 3))):
+        step()
+    torch.cuda.synchronize()
+    k = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    q = 0
+    for _ in range(k):
+        q, _ = step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / k
+    return {"value": q / dt, "unit": "queries/s", "ms_per_step": dt * 1e3, "steps": k,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "timing": "host wall clock around sft_* calls with pinned host buffers"}
+
+
+def estimate_l2(src, tgt, u, dev, npts=1 << 22):
+    """E_L2 estimate (not exact): both meshes queried at the same uniform
+    random points of the unit domain through sft_locate."""
+    import torch
+    import paper_2603_00538_gb300 as sft
+    rng = np.random.default_rng(12345)
+    pts = torch.as_tensor(rng.random((npts, src.dim))).to(dev)
+    s = sft.mesh_source(src, device=dev)
+    tsrc = sft.sft_source_create(torch.as_tensor(tgt.coords.astype(np.float64)).to(dev),
+                                 torch.as_tensor(tgt.conn).to(dev), torch.as_tensor(u[None, :]).to(dev))
+    fs = torch.zeros((1, npts), dtype=torch.float64, device=dev)
+    ft = torch.zeros_like(fs)
+    es = torch.zeros(npts, dtype=torch.int32, device=dev)
+    et = torch.zeros_like(es)
+    sft.sft_locate(s, pts, sft.SFT_PREC_FP64, elem_out=es, val_out=fs)
+    sft.sft_locate(tsrc, pts, sft.SFT_PREC_FP64, elem_out=et, val_out=ft)
+    d2 = ((fs - ft) ** 2).cpu().numpy()[0]
+    f2 = (fs ** 2).cpu().numpy()[0]
+    e = math.sqrt(d2.mean() / f2.mean())
+    se = 0.5 * e * math.sqrt(d2.var() / npts) / max(d2.mean(), 1e-300)
+    s.close()
+    tsrc.close()
+    return e, se
+
+
+# ---------------------------------------------------------------------------
+# the oracle: CPU baseline and the reference arm
+# ---------------------------------------------------------------------------
+def _sample_target(tgt, frac):
+    """The first `frac` of the target elements (Morton order: a compact patch),
+    nodes renumbered."""
+    ne = max(1, int(tgt.nelems * frac))
+    conn = tgt.conn[:ne]
+    used = np.unique(conn)
+    remap = -np.ones(tgt.nnodes, np.int64)
+    remap[used] = np.arange(used.size)
+    return W.Mesh(tgt.coords[used], remap[conn].astype(np.int32))
+
+
+def oracle_step(src, tgt_s, p):
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.transfer(src, tgt_s, 1, p["samples_per_elem"], seed=0, cg_tol=p["cg_tol"], cg_max_iter=1000)
+    dt = time.perf_counter() - t0
+    return (tgt_s.nelems * p["samples_per_elem"] + tgt_s.nnodes) / dt, dt, r
+
+
+def cpu_baseline(args, src, tgt, p):
+    frac = args.cpu_frac
+    tgt_s = _sample_target(tgt, frac)
+    v, dt, _ = oracle_step(src, tgt_s, p)
+    return {"value": v, "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "seconds": dt,
+            "sample": f"full source mesh (grid build included) and the first {tgt_s.nelems} target "
+                      f"elements in Morton order ({frac:.3g} of the workload), one full oracle transfer"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    src, tgt, p = make_workload(args.workload)
+    tgt_s = _sample_target(tgt, args.cpu_frac)
+    for _ in range(args.warmup):
+        oracle_step(src, tgt_s, p)
+    times, q = [], 0
+    for _ in range(args.steps):
+        v, dt, _ = oracle_step(src, tgt_s, p)
+        times.append(dt)
+        q = tgt_s.nelems * p["samples_per_elem"] + tgt_s.nnodes
+    ms = 1e3 * float(np.mean(times))
+    value = q / (ms / 1e3)
+    sample = (f"full source mesh and the first {tgt_s.nelems} target elements (Morton order, "
+              f"{args.cpu_frac:.3g} of the workload) per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s",
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "queries/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="tri4m")
+    ap.add_argument("--cpu-frac", type=float, default=0.05)
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * sft.h -- C ABI of libsft, a GB300 (sm_103a) implementation of the
+ * stochastic conservative field transfer: the control-variate Monte Carlo
+ * approximation of the Galerkin projection (paper Sec. 4), with the source
+ * field queried pointwise as a black box (here: P1 point location in a
+ * uniform-grid-bucketed source mesh, Sec. 5.3) and the target mass-matrix
+ * system solved in FP64.
+ *
+ * Conventions shared by every entry point
+ *  - Plain pointers and sizes only. A pointer is device memory when the
+ *    matching `device_ptrs` / `out_device` flag is 1, host memory otherwise.
+ *  - Handles own every device buffer they allocate; the caller owns its
+ *    input arrays, which are copied at create time, and its output arrays.
+ *  - Work is ordered on the CUDA stream given in the descriptor/options
+ *    (NULL = the legacy default stream). Calls that return results to the
+ *    host (statistics, status of the solve) synchronise that stream.
+ *  - Errors are returned as sft_status; sft_last_error() gives a message for
+ *    the calling thread. No C++ exception crosses the ABI.
+ *  - Index types: int32 connectivity and element ids, int64 sizes.
+ */
+#ifndef SFT_H
+#define SFT_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sft_source_s* sft_source;
+typedef struct sft_target_s* sft_target;
+
+typedef enum {
+    SFT_OK = 0,
+    SFT_ERR_ARG = 1,            /* invalid argument (null, size, enum) */
+    SFT_ERR_MESH = 2,           /* invalid mesh: connectivity, orientation, non-finite value */
+    SFT_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+    SFT_ERR_OOM = 4,            /* device allocation failed */
+    SFT_ERR_NOT_CONVERGED = 5,  /* CG reached cg_max_iter; u is the last iterate */
+    SFT_ERR_OUTSIDE = 6,        /* strict mode: a query fell in an empty grid cell */
+    SFT_ERR_DEVICE_STATUS = 7,  /* a kernel reported an error (bounded wait expired, bad index) */
+    SFT_ERR_UNSUPPORTED = 8     /* valid request this build does not implement */
+} sft_status;
+
+/* Arithmetic of the sampling / location / residual part of a transfer.
+ * FP32: samples, containment predicate, source evaluation and residual in
+ * FP32 with compensated (two-sum) per-element partials; load vector, CG and
+ * global reductions in FP64. FP64: everything in FP64. */
+typedef enum { SFT_PREC_FP64 = 0, SFT_PREC_FP32 = 1 } sft_precision;
+
+/* element type of coordinate / value arrays */
+typedef enum { SFT_F32 = 0, SFT_F64 = 1 } sft_dtype;
+
+/* A P1 simplex mesh (Sec. 2: the target FE space V_t; the source P1 field
+ * "interpolated onto the source mesh" of Sec. 5.1). */
+typedef struct {
+    int32_t dim;            /* 2 (triangles) or 3 (tetrahedra) */
+    int32_t nfields;        /* source: nodal fields carried (1..8); target: 0 */
+    int64_t nnodes;
+    int64_t nelems;
+    const void* coords;     /* [nnodes][dim] of `dtype`, row-major */
+    const int32_t* conn;    /* [nelems][dim+1], positively oriented */
+    const void* values;     /* source: [nfields][nnodes] of `dtype`; target: NULL */
+    int32_t dtype;          /* sft_dtype of coords and values */
+    int32_t device_ptrs;    /* 1: coords/conn/values are device pointers */
+    double grid_scale_L;    /* source: grid cells per axis = int(L * nelems^(1/dim)); <= 0 means 1 */
+    void* cuda_stream;      /* cudaStream_t for the setup work */
+} sft_mesh_desc;
+
+/* Options of one transfer (Sec. 4 steps 1-7). */
+typedef struct {
+    int32_t samples_per_elem;   /* N >= 1 samples per target element */
+    int32_t precision;          /* sft_precision */
+    uint64_t seed;              /* Philox key */
+    uint32_t stream_id;         /* Philox counter word 2 (independent sample streams) */
+    int32_t cg_max_iter;        /* >= 0; 0 skips the solve (u = 0) */
+    double alpha;               /* control-variate parameter (Eq. cv_centered_integrand); 1 recommended */
+    double cg_tol;              /* stop when ||b - M u||_2 <= cg_tol ||b||_2 */
+    int32_t strict_inside;      /* 1: SFT_ERR_OUTSIDE when a query lands in an empty grid cell */
+    int32_t out_device;         /* 1: u_out, b_out, g_out, sample_elem_out are device pointers */
+    void* cuda_stream;          /* cudaStream_t */
+    int32_t* sample_elem_out;   /* optional [nelems][N]: source element located for every sample */
+} sft_options;
+
+typedef struct {
+    int32_t cg_iters;           /* largest iteration count over the fields */
+    int32_t reserved;
+    double cg_rel_resid;        /* largest final ||r||/||b|| over the fields */
+    int64_t queries;            /* source queries issued: nodes (control) + nelems * N */
+    int64_t fallback_queries;   /* queries no candidate accepted (nearest candidate used) */
+    int64_t empty_queries;      /* queries that landed in an empty cell (value 0) */
+    float ms_setup;             /* lazily built source/target structures inside this call */
+    float ms_control;           /* step 1: control values g at the target nodes */
+    float ms_assembly;          /* steps 2-6: fused sample / query / control / scatter kernel */
+    float ms_solve;             /* step 7: CG */
+    float ms_total;
+    float reserved2;
+} sft_stats;
+
+/* Copy a source mesh and its nodal fields to the device and build the
+ * uniform-grid point-location structure (Sec. 5.3: nx = ny = int(L sqrt(#elements)),
+ * extended to 3D with the cube root) for the precision matching `dtype`
+ * (F32 -> FP32 location, F64 -> FP64 location); the other precision is built
+ * on first use. Also computes int f^s (exact P1 integral) per field.
+ * Errors: SFT_ERR_ARG (null/size/dim/nfields), SFT_ERR_MESH (index out of
+ * range, non-positive element, non-finite coordinate), SFT_ERR_OOM, SFT_ERR_CUDA. */
+sft_status sft_source_create(const sft_mesh_desc* desc, sft_source* out);
+
+/* Copy a target P1 mesh to the device and assemble its FP64 mass matrix
+ * M_ki = int psi_k psi_i (Eq. mass_matrix; exact P1 quadrature, Sec. 2) in
+ * CSR form, its Jacobi diagonal and lumped masses m_i = sum_k M_ik.
+ * Errors as for sft_source_create. */
+sft_status sft_target_create(const sft_mesh_desc* desc, sft_target* out);
+
+void sft_source_destroy(sft_source src);
+void sft_target_destroy(sft_target tgt);
+
+/* One transfer, Sec. 4 steps 1-7 (Eqs. cv_load_expanded and cv_galerkin_system):
+ *   g   = source evaluated at the target nodes (step 1);
+ *   b_i = alpha int g psi_i  +  sum_t |T|/N sum_j (f^s - alpha g)(X_tj) psi_i(X_tj)
+ *         with X_tj uniform in t from Philox4x32-10 (steps 2-6);
+ *   M u = b by Jacobi-preconditioned CG from u = 0 (step 7).
+ * u_out [nfields][nnodes_target] FP64 (required); b_out, g_out same shape,
+ * optional (NULL). u_out is written on SFT_OK and SFT_ERR_NOT_CONVERGED.
+ * stats may be NULL. Synchronises opt->cuda_stream before returning. */
+sft_status sft_transfer(sft_source src, sft_target tgt, const sft_options* opt,
+                        double* u_out, double* b_out, double* g_out, sft_stats* stats);
+
+/* Relative conservation error (Eq. relative_conservation_error) of a target
+ * field u [nnodes_target] (FP64; device pointer if u_on_device):
+ *   out3[0] = |int f^s - int f^t| / |int f^s|, out3[1] = int f^s (field `field`
+ *   of the source, exact P1 integral), out3[2] = int f^t = sum_i m_i u_i.
+ * out3 is a host array of 3 doubles. Synchronises `cuda_stream`. */
+sft_status sft_conservation_error(sft_source src, sft_target tgt, const double* u,
+                                  int32_t u_on_device, int32_t field, void* cuda_stream,
+                                  double* out3);
+
+/* Black-box source query at arbitrary points (the step-4 query on its own):
+ * pts [n][dim] FP64 (rounded to FP32 first when precision = FP32);
+ * elem_out [n] located source element (-1: empty cell), val_out [nfields][n]
+ * FP64 P1 value (may be NULL). Pointers are device memory if device_ptrs. */
+sft_status sft_locate(sft_source src, int32_t precision, int64_t n, const double* pts,
+                      int32_t device_ptrs, int32_t* elem_out, double* val_out,
+                      void* cuda_stream);
+
+/* Solve M u = b on the target (step 7 alone) for nrhs right-hand sides
+ * b [nrhs][nnodes] -> u [nrhs][nnodes], FP64, Jacobi-PCG from u = 0.
+ * iters_out / rel_resid_out (host, may be NULL) get the worst field. */
+sft_status sft_mass_solve(sft_target tgt, int32_t nrhs, const double* b, double* u,
+                          int32_t device_ptrs, double tol, int32_t max_iter, void* cuda_stream,
+                          int32_t* iters_out, double* rel_resid_out);
+
+/* Inspection of the built structures (host copies; any output may be NULL).
+ * Source grid for `precision`: cells per axis n[3], cell count, registration
+ * count, CSR start [ncells+1] and items [nitems]. */
+sft_status sft_source_grid(sft_source src, int32_t precision, int32_t n_out[3],
+                           int64_t* ncells_out, int64_t* nitems_out,
+                           int64_t* start_out, int32_t* items_out);
+/* Target mass matrix: nnz, row_ptr [nnodes+1] (int64), col [nnz], val [nnz],
+ * lumped masses [nnodes]. */
+sft_status sft_target_mass(sft_target tgt, int64_t* nnz_out, int64_t* row_ptr_out,
+                           int32_t* col_out, double* val_out, double* lumped_out);
+
+const char* sft_status_str(sft_status s);
+const char* sft_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFT_H */

@@ -1,0 +1,344 @@
+"""Python binding of libsft (include/sft.h): argument marshalling only.
+
+Every step of the transfer runs in the CUDA library. The functions carry the
+names of the C entry points. Arrays may be numpy arrays (host memory) or torch
+tensors (host or CUDA); CUDA tensors are passed to the library as device
+pointers on the current torch stream.
+
+The library is required: importing works without it (so the build step can
+run), but every call raises ``SftUnavailable`` when ``libsft.so`` is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsft.so")
+
+SFT_OK, SFT_ERR_NOT_CONVERGED = 0, 5
+SFT_PREC_FP64, SFT_PREC_FP32 = 0, 1
+SFT_F32, SFT_F64 = 0, 1
+
+
+class SftUnavailable(RuntimeError):
+    pass
+
+
+class SftError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: status {status} ({msg})")
+        self.status = status
+
+
+class sft_mesh_desc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("nfields", ctypes.c_int32), ("nnodes", ctypes.c_int64),
+                ("nelems", ctypes.c_int64), ("coords", ctypes.c_void_p), ("conn", ctypes.c_void_p),
+                ("values", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("device_ptrs", ctypes.c_int32),
+                ("grid_scale_L", ctypes.c_double), ("cuda_stream", ctypes.c_void_p)]
+
+
+class sft_options(ctypes.Structure):
+    _fields_ = [("samples_per_elem", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint32), ("cg_max_iter", ctypes.c_int32),
+                ("alpha", ctypes.c_double), ("cg_tol", ctypes.c_double), ("strict_inside", ctypes.c_int32),
+                ("out_device", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
+                ("sample_elem_out", ctypes.c_void_p)]
+
+
+class sft_stats(ctypes.Structure):
+    _fields_ = [("cg_iters", ctypes.c_int32), ("reserved", ctypes.c_int32), ("cg_rel_resid", ctypes.c_double),
+                ("queries", ctypes.c_int64), ("fallback_queries", ctypes.c_int64),
+                ("empty_queries", ctypes.c_int64), ("ms_setup", ctypes.c_float), ("ms_control", ctypes.c_float),
+                ("ms_assembly", ctypes.c_float), ("ms_solve", ctypes.c_float), ("ms_total", ctypes.c_float),
+                ("reserved2", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
+
+
+_vp, _i32, _i64, _d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+_SIGS = {
+    "sft_source_create": ([ctypes.POINTER(sft_mesh_desc), ctypes.POINTER(_vp)], _i32),
+    "sft_target_create": ([ctypes.POINTER(sft_mesh_desc), ctypes.POINTER(_vp)], _i32),
+    "sft_source_destroy": ([_vp], None),
+    "sft_target_destroy": ([_vp], None),
+    "sft_transfer": ([_vp, _vp, ctypes.POINTER(sft_options), _vp, _vp, _vp, ctypes.POINTER(sft_stats)], _i32),
+    "sft_conservation_error": ([_vp, _vp, _vp, _i32, _i32, _vp, _vp], _i32),
+    "sft_locate": ([_vp, _i32, _i64, _vp, _i32, _vp, _vp, _vp], _i32),
+    "sft_mass_solve": ([_vp, _i32, _vp, _vp, _i32, _d, _i32, _vp, _vp, _vp], _i32),
+    "sft_source_grid": ([_vp, _i32, _vp, _vp, _vp, _vp, _vp], _i32),
+    "sft_target_mass": ([_vp, _vp, _vp, _vp, _vp, _vp], _i32),
+    "sft_status_str": ([_i32], ctypes.c_char_p),
+    "sft_last_error": ([], ctypes.c_char_p),
+}
+EXPORTS = tuple(_SIGS)
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsft.so (raises SftUnavailable if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise SftUnavailable(f"libsft.so not built (expected at {LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(status: int, where: str, allow=(SFT_OK,)):
+    if status not in allow:
+        raise SftError(status, where, lib().sft_last_error().decode())
+    return status
+
+
+# --------------------------------------------------------------------------
+# array marshalling (no arithmetic)
+# --------------------------------------------------------------------------
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """(pointer, on_device, keepalive) of a numpy array or torch tensor."""
+    if x is None:
+        return None, False, None
+    if _is_torch(x):
+        x = x.contiguous()
+        return x.data_ptr(), bool(x.is_cuda), x
+    x = np.ascontiguousarray(x)
+    return x.ctypes.data, False, x
+
+
+def _dtype_code(x):
+    name = str(x.dtype)
+    if name.endswith("float64"):
+        return SFT_F64
+    if name.endswith("float32"):
+        return SFT_F32
+    raise TypeError(f"coordinates must be float32 or float64, got {x.dtype}")
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+def _int32(x):
+    if _is_torch(x):
+        import torch
+        return x.to(torch.int32).contiguous()
+    return np.ascontiguousarray(x, dtype=np.int32)
+
+
+class _Handle:
+    def __init__(self, h, destroy, keep):
+        self.h = h
+        self._destroy = destroy
+        self._keep = keep
+
+    def close(self):
+        if self.h:
+            self._destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Source(_Handle):
+    pass
+
+
+class Target(_Handle):
+    pass
+
+
+def _desc(coords, conn, values, grid_scale_L, stream):
+    conn = _int32(conn)
+    cp, cdev, ck = _ptr(coords)
+    kp, kdev, kk = _ptr(conn)
+    vp, vdev, vk = _ptr(values)
+    if values is not None and _dtype_code(values) != _dtype_code(coords):
+        raise TypeError("values must have the coordinates' dtype")
+    if len({cdev, kdev} | ({vdev} if values is not None else set())) != 1:
+        raise ValueError("coords, conn and values must all be host or all device arrays")
+    d = sft_mesh_desc()
+    d.dim = int(coords.shape[1])
+    d.nfields = 0 if values is None else int(values.shape[0])
+    d.nnodes = int(coords.shape[0])
+    d.nelems = int(conn.shape[0])
+    d.coords, d.conn, d.values = cp, kp, vp
+    d.dtype = _dtype_code(coords)
+    d.device_ptrs = int(cdev)
+    d.grid_scale_L = float(grid_scale_L)
+    d.cuda_stream = stream if stream is not None else (_current_stream() if cdev else None)
+    return d, (ck, kk, vk)
+
+
+def sft_source_create(coords, conn, values, grid_scale_L=1.0, stream=None) -> Source:
+    """Source mesh + nodal fields -> handle with its point-location grid."""
+    d, keep = _desc(coords, conn, values, grid_scale_L, stream)
+    h = _vp()
+    _check(lib().sft_source_create(ctypes.byref(d), ctypes.byref(h)), "sft_source_create")
+    return Source(h.value, lib().sft_source_destroy, keep)
+
+
+def sft_target_create(coords, conn, stream=None) -> Target:
+    """Target mesh -> handle with its FP64 CSR mass matrix."""
+    d, keep = _desc(coords, conn, None, 1.0, stream)
+    h = _vp()
+    _check(lib().sft_target_create(ctypes.byref(d), ctypes.byref(h)), "sft_target_create")
+    return Target(h.value, lib().sft_target_destroy, keep)
+
+
+def sft_source_destroy(src: Source):
+    src.close()
+
+
+def sft_target_destroy(tgt: Target):
+    tgt.close()
+
+
+def sft_transfer(src: Source, tgt: Target, samples_per_elem: int, precision: int = SFT_PREC_FP32,
+                 seed: int = 0, stream_id: int = 0, alpha: float = 1.0, cg_tol: float = 1e-10,
+                 cg_max_iter: int = 1000, strict_inside: bool = False, u_out=None, b_out=None, g_out=None,
+                 sample_elem_out=None, stream=None, allow_not_converged: bool = False):
+    """Run one transfer. Outputs are caller-provided arrays (numpy for host,
+    torch CUDA tensors for device); when u_out is None a host array
+    [nfields, nnodes] is allocated. Returns (status, stats dict, u_out)."""
+    nf = _nf(src)
+    if u_out is None:
+        u_out = np.zeros((nf, _nv(tgt)), np.float64)
+    up, udev, _ = _ptr(u_out)
+    bp, bdev, _ = _ptr(b_out)
+    gp, gdev, _ = _ptr(g_out)
+    sp, sdev, _ = _ptr(sample_elem_out)
+    for p, dv in ((bp, bdev), (gp, gdev), (sp, sdev)):
+        if p is not None and dv != udev:
+            raise ValueError("all outputs must be host arrays or all device tensors")
+    o = sft_options()
+    o.samples_per_elem = int(samples_per_elem)
+    o.precision = int(precision)
+    o.seed = int(seed)
+    o.stream_id = int(stream_id)
+    o.cg_max_iter = int(cg_max_iter)
+    o.alpha = float(alpha)
+    o.cg_tol = float(cg_tol)
+    o.strict_inside = int(bool(strict_inside))
+    o.out_device = int(udev)
+    o.cuda_stream = stream if stream is not None else _current_stream()
+    o.sample_elem_out = sp
+    st = sft_stats()
+    allow = (SFT_OK, SFT_ERR_NOT_CONVERGED) if allow_not_converged else (SFT_OK,)
+    status = _check(lib().sft_transfer(src.h, tgt.h, ctypes.byref(o), up, bp, gp, ctypes.byref(st)),
+                    "sft_transfer", allow)
+    return status, st.as_dict(), u_out
+
+
+def sft_conservation_error(src: Source, tgt: Target, u, field: int = 0, stream=None):
+    """(E_mass, int f^s, int f^t) for one target field u [nnodes]."""
+    p, dev, _ = _ptr(u)
+    out = (ctypes.c_double * 3)()
+    _check(lib().sft_conservation_error(src.h, tgt.h, p, int(dev), int(field),
+                                        stream if stream is not None else _current_stream(), out),
+           "sft_conservation_error")
+    return out[0], out[1], out[2]
+
+
+def sft_locate(src: Source, pts, precision: int = SFT_PREC_FP32, elem_out=None, val_out=None, stream=None):
+    """Locate FP64 points [n, dim]; returns (elem [n], values [nfields, n])."""
+    n = int(pts.shape[0])
+    pp, dev, _ = _ptr(pts)
+    if elem_out is None:
+        elem_out = np.zeros(n, np.int32)
+    if val_out is None:
+        val_out = np.zeros((_nf(src), n), np.float64)
+    ep, _, _ = _ptr(elem_out)
+    vp, _, _ = _ptr(val_out)
+    _check(lib().sft_locate(src.h, int(precision), n, pp, int(dev), ep, vp,
+                            stream if stream is not None else _current_stream()), "sft_locate")
+    return elem_out, val_out
+
+
+def sft_mass_solve(tgt: Target, b, tol=1e-12, max_iter=1000, u_out=None, stream=None):
+    """Solve M u = b for b [nrhs, nnodes]; returns (u, iters, rel_resid)."""
+    b2 = b if _is_torch(b) else np.ascontiguousarray(np.atleast_2d(b), np.float64)
+    nrhs = int(b2.shape[0]) if b2.ndim == 2 else 1
+    bp, dev, keep = _ptr(b2)
+    if u_out is None:
+        u_out = np.zeros((nrhs, _nv(tgt)), np.float64)
+    up, _, _ = _ptr(u_out)
+    it = ctypes.c_int32()
+    rr = ctypes.c_double()
+    _check(lib().sft_mass_solve(tgt.h, nrhs, bp, up, int(dev), float(tol), int(max_iter),
+                                stream if stream is not None else _current_stream(),
+                                ctypes.byref(it), ctypes.byref(rr)), "sft_mass_solve")
+    return u_out, it.value, rr.value
+
+
+def sft_source_grid(src: Source, precision: int):
+    """(n[3], cell start [ncells+1] int64, cell items [nitems] int32)."""
+    n = (ctypes.c_int32 * 3)()
+    nc, ni = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().sft_source_grid(src.h, int(precision), n, ctypes.byref(nc), ctypes.byref(ni), None, None),
+           "sft_source_grid")
+    start = np.zeros(nc.value + 1, np.int64)
+    items = np.zeros(max(ni.value, 1), np.int32)
+    _check(lib().sft_source_grid(src.h, int(precision), None, None, None, start.ctypes.data, items.ctypes.data),
+           "sft_source_grid")
+    return np.array(list(n)), start, items[:ni.value]
+
+
+def sft_target_mass(tgt: Target):
+    """(row_ptr int64, col int32, val float64, lumped float64) of the mass matrix."""
+    nnz = ctypes.c_int64()
+    _check(lib().sft_target_mass(tgt.h, ctypes.byref(nnz), None, None, None, None), "sft_target_mass")
+    nv = _nv(tgt)
+    rp = np.zeros(nv + 1, np.int64)
+    col = np.zeros(nnz.value, np.int32)
+    val = np.zeros(nnz.value, np.float64)
+    lump = np.zeros(nv, np.float64)
+    _check(lib().sft_target_mass(tgt.h, None, rp.ctypes.data, col.ctypes.data, val.ctypes.data,
+                                 lump.ctypes.data), "sft_target_mass")
+    return rp, col, val, lump
+
+
+def _nf(src: Source) -> int:
+    return int(src._keep[2].shape[0])
+
+
+def _nv(tgt: Target) -> int:
+    return int(tgt._keep[0].shape[0])
+
+
+def mesh_source(mesh, grid_scale_L=1.0, device=None):
+    """Convenience: a ``workloads.Mesh``-like object (coords, conn, values)."""
+    c, k, v = mesh.coords, mesh.conn, mesh.values
+    if device is not None:
+        import torch
+        c, k, v = (torch.as_tensor(np.ascontiguousarray(a)).to(device) for a in (c, k, v))
+    return sft_source_create(c, k, v, grid_scale_L)
+
+
+def mesh_target(mesh, device=None):
+    c, k = mesh.coords, mesh.conn
+    if device is not None:
+        import torch
+        c, k = (torch.as_tensor(np.ascontiguousarray(a)).to(device) for a in (c, k))
+    return sft_target_create(c, k)

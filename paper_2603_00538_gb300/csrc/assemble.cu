@@ -1,0 +1,239 @@
+// The fused control-variate Monte Carlo assembly (Sec. 4, steps 2-6;
+// Eq. cv_element_load_residual_operator summed as in Eq. cv_load_expanded):
+//
+//   b_i += alpha int_t g psi_i                       (exact P1 mass, FP64)
+//        + |T|/N sum_j (f^s - alpha g)(X_tj) psi_i(X_tj)
+//
+// Work mapping: a warp owns whole target elements. The unit of work is one
+// Philox call: two samples in 2D, one in 3D. With U units per element,
+// U >= 32 gives one element per warp (lanes stride over units), U < 32 packs
+// floor(32/U) elements into a warp (lane -> element lane/U). Per sample a lane
+// maps the draw into the element (psi_i(X) are the barycentric weights used
+// to build X), locates X in the source grid, evaluates every field, forms the
+// residual against the P1 control and accumulates r psi_i. FP32 partials are
+// compensated (TwoSum). A segmented suffix scan over lanes combines the
+// partials of each element; the segment head adds the deterministic control
+// term and scatters k*nf FP64 atomics into b.
+#include "internal.hpp"
+#include "util.cuh"
+
+namespace sft {
+
+template <typename P> struct Acc;
+template <> struct Acc<float> {
+  float s = 0.f, e = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float t, err;
+    two_sum(s, x, t, err);
+    s = t;
+    e = __fadd_rn(e, err);
+  }
+  __device__ __forceinline__ void combine(float s2, float e2) {
+    float t, err;
+    two_sum(s, s2, t, err);
+    s = t;
+    e = __fadd_rn(__fadd_rn(e, e2), err);
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)e; }
+};
+template <> struct Acc<double> {
+  double s = 0.0, e = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ void combine(double s2, double) { s += s2; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+struct AsmParams {
+  int64_t nv, ne, nes;
+  int nf, N, U, G;
+  int64_t ntasks;
+  PhiloxKey key;
+  uint32_t stream_id;
+  double alpha;
+};
+
+template <int D, typename P, int NF, bool DBG>
+__global__ void __launch_bounds__(256) k_assemble(const P* __restrict__ tx, const int32_t* __restrict__ tconn,
+                                                  const double* __restrict__ vol, const P* __restrict__ g,
+                                                  const GridP<P>* __restrict__ gp,
+                                                  const int32_t* __restrict__ cell_start,
+                                                  const int32_t* __restrict__ cell_items,
+                                                  const P* __restrict__ recs, const P* __restrict__ vals,
+                                                  AsmParams p, double* __restrict__ b,
+                                                  int32_t* __restrict__ sample_elem,
+                                                  int64_t* __restrict__ counters) {
+  using A = Ar<P>;
+  constexpr int K = D + 1;
+  constexpr int SPU = D == 2 ? 2 : 1;  // samples per Philox call
+  const GridP<P> gr = *gp;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const P alphaP = (P)p.alpha;
+  int n_fallback = 0, n_empty = 0;
+
+  for (int64_t task = warp0; task < p.ntasks; task += nwarps) {
+    int64_t t;
+    int u0, ustep, seg_lo, seg_hi;
+    bool active;
+    if (p.G == 1) {
+      t = task;
+      u0 = lane;
+      ustep = 32;
+      seg_lo = 0;
+      seg_hi = 32;
+      active = true;
+    } else {
+      const int slot = lane / p.U;
+      t = task * p.G + slot;
+      u0 = lane - slot * p.U;
+      ustep = p.U;
+      seg_lo = slot * p.U;
+      seg_hi = seg_lo + p.U;
+      active = slot < p.G;
+    }
+    active = active && t < p.ne;
+
+    int32_t v[K];
+    P xv[K][D];
+    P gl[NF][K];
+    Acc<P> acc[NF][K];
+    if (active) {
+#pragma unroll
+      for (int m = 0; m < K; ++m) {
+        v[m] = __ldg(tconn + t * K + m);
+#pragma unroll
+        for (int a = 0; a < D; ++a) xv[m][a] = __ldg(tx + (int64_t)v[m] * D + a);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) gl[f][m] = f < p.nf ? __ldg(g + (int64_t)f * p.nv + v[m]) : P(0);
+      }
+    }
+
+    for (int u = u0; active && u < p.U; u += ustep) {
+      const uint4 w = philox4x32_10(make_uint4((uint32_t)u, (uint32_t)t, p.stream_id, 0u), p.key);
+#pragma unroll
+      for (int s = 0; s < SPU; ++s) {
+        const int j = SPU * u + s;
+        if (j >= p.N) break;
+        P lam[K];
+        if constexpr (D == 2) {
+          if (s == 0) osada_weights<P>(w.x, w.y, lam);
+          else osada_weights<P>(w.z, w.w, lam);
+        } else {
+          spacing_weights<P>(w.x, w.y, w.z, lam);
+        }
+        P X[D];
+        map_point<D, P>(lam, xv, X);
+        P mu[K];
+        int status;
+        const int32_t e = locate_point<D, P>(gr, cell_start, cell_items, recs, X, mu, status);
+        n_fallback += status == 1;
+        n_empty += status == 2;
+        if (DBG) sample_elem[t * p.N + j] = e;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          if (f >= p.nf) break;
+          const P fs = e >= 0 ? eval_p1<D, P>(vals, p.nes, f, e, mu) : P(0);
+          P gX = A::mul(gl[f][0], lam[0]);
+#pragma unroll
+          for (int m = 1; m < K; ++m) gX = A::fma(gl[f][m], lam[m], gX);
+          const P r = A::sub(fs, A::mul(alphaP, gX));
+#pragma unroll
+          for (int i = 0; i < K; ++i) acc[f][i].add(A::mul(r, lam[i]));
+        }
+      }
+    }
+
+    // segmented suffix combine: lane seg_lo ends with its element's totals
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const bool take = lane + o < seg_hi;
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          const P s2 = __shfl_down_sync(0xffffffffu, acc[f][i].s, o);
+          const P e2 = __shfl_down_sync(0xffffffffu, acc[f][i].e, o);
+          if (take) acc[f][i].combine(s2, e2);
+        }
+    }
+
+    if (active && lane == seg_lo) {
+      const double w = __ldg(vol + t);
+      const double cdet = p.alpha * w / (double)((D + 1) * (D + 2));
+      const double cmc = w / (double)p.N;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        if (f >= p.nf) break;
+        double gsum = 0.0;
+#pragma unroll
+        for (int m = 0; m < K; ++m) gsum += (double)gl[f][m];
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          const double contrib = cdet * (gsum + (double)gl[f][i]) + cmc * acc[f][i].value();
+          atomicAdd(b + (int64_t)f * p.nv + v[i], contrib);
+        }
+      }
+    }
+  }
+  const int fb = warp_sum<int>(n_fallback), em = warp_sum<int>(n_empty);
+  if (lane == 0 && counters) {
+    if (fb) atomicAdd(reinterpret_cast<unsigned long long*>(counters), (unsigned long long)fb);
+    if (em) atomicAdd(reinterpret_cast<unsigned long long*>(counters + 1), (unsigned long long)em);
+  }
+}
+
+template <int D, typename P, int NF>
+static void launch_t(sft_source_s* s, sft_target_s* t, const AssembleArgs& a, const AsmParams& p, cudaStream_t st) {
+  const Locator& L = s->loc[a.prec];
+  const int threads = 256;
+  const int64_t warps_needed = p.ntasks;
+  int64_t blocks = (warps_needed + (threads / 32) - 1) / (threads / 32);
+  if (blocks > (1 << 20)) blocks = 1 << 20;
+  if (blocks < 1) blocks = 1;
+  auto args = [&](auto kern) {
+    kern<<<(unsigned)blocks, threads, 0, st>>>((const P*)t->coordsP[a.prec], t->conn, t->vol, (const P*)a.g,
+                                               (const GridP<P>*)L.grid, L.cell_start, L.cell_items,
+                                               (const P*)L.recs, (const P*)L.vals, p, a.b, a.sample_elem,
+                                               a.counters);
+  };
+  if (a.sample_elem) args(k_assemble<D, P, NF, true>);
+  else args(k_assemble<D, P, NF, false>);
+}
+
+template <int D, typename P>
+static void launch_nf(sft_source_s* s, sft_target_s* t, const AssembleArgs& a, const AsmParams& p, cudaStream_t st) {
+  if (a.nf <= 1) launch_t<D, P, 1>(s, t, a, p, st);
+  else if (a.nf <= 2) launch_t<D, P, 2>(s, t, a, p, st);
+  else if (a.nf <= 4) launch_t<D, P, 4>(s, t, a, p, st);
+  else launch_t<D, P, 8>(s, t, a, p, st);
+}
+
+sft_status launch_assembly(sft_source_s* s, sft_target_s* t, const AssembleArgs& a, cudaStream_t st) {
+  if (t->ne == 0) return SFT_OK;
+  AsmParams p;
+  p.nv = t->nv;
+  p.ne = t->ne;
+  p.nes = s->ne;
+  p.nf = a.nf;
+  p.N = a.N;
+  const int spu = t->dim == 2 ? 2 : 1;
+  p.U = (a.N + spu - 1) / spu;
+  p.G = p.U >= 32 ? 1 : 32 / p.U;
+  p.ntasks = (t->ne + p.G - 1) / p.G;
+  p.key.k0 = (uint32_t)a.seed;
+  p.key.k1 = (uint32_t)(a.seed >> 32);
+  p.stream_id = a.stream_id;
+  p.alpha = a.alpha;
+  if (t->dim == 2) {
+    if (a.prec == SFT_PREC_FP32) launch_nf<2, float>(s, t, a, p, st);
+    else launch_nf<2, double>(s, t, a, p, st);
+  } else {
+    if (a.prec == SFT_PREC_FP32) launch_nf<3, float>(s, t, a, p, st);
+    else launch_nf<3, double>(s, t, a, p, st);
+  }
+  SFT_CUDA(cudaGetLastError());
+  return SFT_OK;
+}
+
+}  // namespace sft

@@ -1,0 +1,278 @@
+// Device primitives of the transfer path: counter-based random numbers, the
+// element sample map (Sec. 4, step 3), the uniform-grid cell index and the
+// point-location predicate (Sec. 5.3 grid search), P1 evaluation.
+//
+// The arithmetic that decides an integer (a located element) is written with
+// explicit round-to-nearest intrinsics (__fmul_rn, __fmaf_rn, ...) so no
+// compiler contraction changes it: the same operation sequence evaluated in
+// IEEE arithmetic gives the same element on any conforming implementation.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sft {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+// as 1, 2, 3", SC'11): 10 rounds of two 32x32->64 multiplies; the key advances
+// by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+struct PhiloxKey { uint32_t k0, k1; };
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, PhiloxKey k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.k0, lo1, hi0 ^ c.w ^ k.k1, lo0);
+    k.k0 += 0x9E3779B9u;
+    k.k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Uniform(0,1) from one 32-bit word, exact in the target precision:
+// FP32 odd multiples of 2^-24, FP64 (x + 1/2) 2^-32.
+__device__ __forceinline__ float u01f(uint32_t x) {
+  return __fmul_rn(__uint2float_rn((x >> 8) | 1u), 0x1p-24f);
+}
+__device__ __forceinline__ double u01d(uint32_t x) {
+  return __dmul_rn(__dadd_rn(__uint2double_rn(x), 0.5), 0x1p-32);
+}
+
+// ---------------------------------------------------------------------------
+// rounding-explicit arithmetic in precision P
+// ---------------------------------------------------------------------------
+template <typename P> struct Ar;
+template <> struct Ar<float> {
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+  static __device__ __forceinline__ float sqrt(float a) { return __fsqrt_rn(a); }
+  static __device__ __forceinline__ float u01(uint32_t x) { return u01f(x); }
+  static __device__ __forceinline__ float from_d(double x) { return __double2float_rn(x); }
+  static __device__ __forceinline__ float floor(float x) { return floorf(x); }
+};
+template <> struct Ar<double> {
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+  static __device__ __forceinline__ double sqrt(double a) { return __dsqrt_rn(a); }
+  static __device__ __forceinline__ double u01(uint32_t x) { return u01d(x); }
+  static __device__ __forceinline__ double from_d(double x) { return x; }
+  static __device__ __forceinline__ double floor(double x) { return ::floor(x); }
+};
+
+// ---------------------------------------------------------------------------
+// Sample map (Sec. 4 step 3). 2D: Osada et al. (2002),
+// (xi, eta) -> (1 - sqrt(xi), sqrt(xi)(1 - eta), sqrt(xi) eta).
+// 3D: spacings of three sorted uniforms (uniform on the simplex).
+// Counter layout: 2D one Philox call per sample pair q = j/2, counter
+// (q, t, stream, 0), sample j uses words 2(j%2), 2(j%2)+1; 3D one call per
+// sample, counter (j, t, stream, 0), words 0..2.
+// ---------------------------------------------------------------------------
+template <typename P>
+__device__ __forceinline__ void osada_weights(uint32_t wx, uint32_t wy, P lam[3]) {
+  using A = Ar<P>;
+  const P xi = A::u01(wx), eta = A::u01(wy);
+  const P s = A::sqrt(xi);
+  lam[0] = A::sub(P(1), s);
+  lam[1] = A::mul(s, A::sub(P(1), eta));
+  lam[2] = A::mul(s, eta);
+}
+
+template <typename P>
+__device__ __forceinline__ void spacing_weights(uint32_t w0, uint32_t w1, uint32_t w2, P lam[4]) {
+  using A = Ar<P>;
+  P v0 = A::u01(w0), v1 = A::u01(w1), v2 = A::u01(w2), s;
+  if (v1 < v0) { s = v0; v0 = v1; v1 = s; }
+  if (v2 < v1) { s = v1; v1 = v2; v2 = s; }
+  if (v1 < v0) { s = v0; v0 = v1; v1 = s; }
+  lam[0] = v0;
+  lam[1] = A::sub(v1, v0);
+  lam[2] = A::sub(v2, v1);
+  lam[3] = A::sub(P(1), v2);
+}
+
+// X = sum_m lam_m x_m, accumulated left to right, one rounding per operation
+template <int D, typename P>
+__device__ __forceinline__ void map_point(const P lam[D + 1], const P xv[D + 1][D], P X[D]) {
+  using A = Ar<P>;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    P x = A::mul(lam[0], xv[0][a]);
+#pragma unroll
+    for (int m = 1; m <= D; ++m) x = A::add(x, A::mul(lam[m], xv[m][a]));
+    X[a] = x;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Uniform grid (Sec. 5.3): per axis origin lo, scale inv = n / extent (rounded
+// to P once), n cells. cell(x) = clamp(floor((x - lo) * inv), 0, n - 1) is
+// monotone in x.
+// ---------------------------------------------------------------------------
+template <typename P> struct GridP {
+  P lo[3];
+  P inv[3];
+  int32_t n[3];
+};
+
+template <typename P>
+__device__ __forceinline__ int32_t cell_axis(P x, P lo, P inv, int32_t n) {
+  using A = Ar<P>;
+  const P f = A::floor(A::mul(A::sub(x, lo), inv));
+  if (!(f >= P(0))) return 0;
+  if (f > P(n - 1)) return n - 1;
+  return (int32_t)f;
+}
+
+template <int D, typename P>
+__device__ __forceinline__ int32_t cell_of(const GridP<P>& g, const P X[D]) {
+  int32_t c = cell_axis<P>(X[D - 1], g.lo[D - 1], g.inv[D - 1], g.n[D - 1]);
+#pragma unroll
+  for (int a = D - 2; a >= 0; --a) c = c * g.n[a] + cell_axis<P>(X[a], g.lo[a], g.inv[a], g.n[a]);
+  return c;
+}
+
+// ---------------------------------------------------------------------------
+// Location record of a source element in precision P: the first vertex a and
+// the rows of the inverse affine map (formed in FP64, rounded to P once).
+// 2D: {ax, ay, i00, i01, i10, i11, 0, 0}; 3D: {ax, ay, az, r00..r22}.
+// mu_1.. = J^-1 (X - a), mu_0 = 1 - sum; accept when min(mu) >= 0.
+// ---------------------------------------------------------------------------
+template <int D> struct RecLen { static constexpr int value = D == 2 ? 8 : 12; };
+
+template <int D, typename P>
+__device__ __forceinline__ void bary_from_record(const P* __restrict__ rec, const P X[D], P mu[D + 1]) {
+  using A = Ar<P>;
+  if constexpr (D == 2) {
+    const P dx = A::sub(X[0], rec[0]), dy = A::sub(X[1], rec[1]);
+    const P m1 = A::fma(rec[3], dy, A::mul(rec[2], dx));
+    const P m2 = A::fma(rec[5], dy, A::mul(rec[4], dx));
+    mu[0] = A::sub(A::sub(P(1), m1), m2);
+    mu[1] = m1;
+    mu[2] = m2;
+  } else {
+    const P dx = A::sub(X[0], rec[0]), dy = A::sub(X[1], rec[1]), dz = A::sub(X[2], rec[2]);
+    P m[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      m[q] = A::fma(rec[3 + 3 * q + 2], dz, A::fma(rec[3 + 3 * q + 1], dy, A::mul(rec[3 + 3 * q], dx)));
+    mu[0] = A::sub(A::sub(A::sub(P(1), m[0]), m[1]), m[2]);
+    mu[1] = m[0];
+    mu[2] = m[1];
+    mu[3] = m[2];
+  }
+}
+
+// vectorised record load (records are 16-byte aligned)
+template <int D, typename P>
+__device__ __forceinline__ void load_record(const P* __restrict__ recs, int32_t e, P r[RecLen<D>::value]) {
+  constexpr int L = RecLen<D>::value;
+  if constexpr (sizeof(P) == 4) {
+    const float4* p = reinterpret_cast<const float4*>(recs + (int64_t)e * L);
+#pragma unroll
+    for (int q = 0; q < L / 4; ++q) {
+      const float4 v = __ldg(p + q);
+      r[4 * q] = v.x; r[4 * q + 1] = v.y; r[4 * q + 2] = v.z; r[4 * q + 3] = v.w;
+    }
+  } else {
+    const double2* p = reinterpret_cast<const double2*>(recs + (int64_t)e * L);
+#pragma unroll
+    for (int q = 0; q < L / 2; ++q) {
+      const double2 v = __ldg(p + q);
+      r[2 * q] = v.x; r[2 * q + 1] = v.y;
+    }
+  }
+}
+
+// Locate X: scan the candidates of its cell in ascending element id, return
+// the first whose predicate accepts; if none accepts, the candidate with the
+// largest min(mu) (first in order on ties); -1 for an empty cell.
+// status: 0 accepted, 1 nearest candidate, 2 empty cell. mu is the returned
+// element's barycentric vector.
+template <int D, typename P>
+__device__ __forceinline__ int32_t locate_point(const GridP<P>& g, const int32_t* __restrict__ cell_start,
+                                                const int32_t* __restrict__ cell_items,
+                                                const P* __restrict__ recs, const P X[D], P mu[D + 1],
+                                                int& status) {
+  constexpr int L = RecLen<D>::value;
+  const int32_t c = cell_of<D, P>(g, X);
+  const int32_t p0 = __ldg(cell_start + c), p1 = __ldg(cell_start + c + 1);
+  int32_t best = -1;
+  P best_score = P(0);
+  for (int32_t p = p0; p < p1; ++p) {
+    const int32_t e = __ldg(cell_items + p);
+    P r[L];
+    load_record<D, P>(recs, e, r);
+    P m[D + 1];
+    bary_from_record<D, P>(r, X, m);
+    P mn = m[0];
+#pragma unroll
+    for (int q = 1; q <= D; ++q) mn = m[q] < mn ? m[q] : mn;
+    if (mn >= P(0)) {
+#pragma unroll
+      for (int q = 0; q <= D; ++q) mu[q] = m[q];
+      status = 0;
+      return e;
+    }
+    if (best < 0 || mn > best_score) { best = e; best_score = mn; }
+  }
+  if (best < 0) {
+    status = 2;
+#pragma unroll
+    for (int q = 0; q <= D; ++q) mu[q] = P(0);
+    return -1;
+  }
+  status = 1;
+  P r[L];
+  load_record<D, P>(recs, best, r);
+  bary_from_record<D, P>(r, X, mu);
+  return best;
+}
+
+// P1 value of field f in element e from the per-element copy of its nodal
+// values (vals: [nf][ne][4] in P; slot 3 unused in 2D)
+template <int D, typename P>
+__device__ __forceinline__ P eval_p1(const P* __restrict__ vals, int64_t ne, int f, int32_t e, const P mu[D + 1]) {
+  using A = Ar<P>;
+  const P* v = vals + ((int64_t)f * ne + e) * 4;
+  P fv[4];
+  if constexpr (sizeof(P) == 4) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(v));
+    fv[0] = q.x; fv[1] = q.y; fv[2] = q.z; fv[3] = q.w;
+  } else {
+    const double2 q0 = __ldg(reinterpret_cast<const double2*>(v));
+    const double2 q1 = __ldg(reinterpret_cast<const double2*>(v) + 1);
+    fv[0] = q0.x; fv[1] = q0.y; fv[2] = q1.x; fv[3] = q1.y;
+  }
+  P s = A::mul(mu[0], fv[0]);
+#pragma unroll
+  for (int m = 1; m <= D; ++m) s = A::fma(mu[m], fv[m], s);
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// error-free transformation: Knuth's TwoSum
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  const float ap = __fsub_rn(s, bp);
+  e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+// device error words (kernel-side status reported to the host)
+enum DevErr : int32_t {
+  DEV_OK = 0,
+  DEV_BARRIER_TIMEOUT = 1,
+  DEV_BAD_INDEX = 2,
+  DEV_VALENCE = 3,
+  DEV_BAD_ELEMENT = 4,
+  DEV_NONFINITE = 5
+};
+
+}  // namespace sft

@@ -1,0 +1,114 @@
+// Internal declarations shared by the translation units of libsft.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <cuda_runtime.h>
+#include "../../include/sft.h"
+#include "common.cuh"
+
+namespace sft {
+
+constexpr int kMaxFields = 8;
+
+// thread-local error message + status helpers (api.cu)
+void set_last_error(const std::string& msg);
+sft_status fail(sft_status s, const std::string& msg);
+sft_status cuda_fail(cudaError_t e, const char* what);
+
+#define SFT_CUDA(call)                                                   \
+  do {                                                                   \
+    cudaError_t _e = (call);                                             \
+    if (_e != cudaSuccess) return ::sft::cuda_fail(_e, #call);           \
+  } while (0)
+
+// stream-ordered device allocation
+template <typename T>
+cudaError_t dalloc(T** p, size_t count, cudaStream_t s) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMallocAsync(reinterpret_cast<void**>(p), sizeof(T) * count, s);
+}
+template <typename T>
+void dfree(T*& p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+  p = nullptr;
+}
+
+// location structure of a source mesh in one precision
+struct Locator {
+  bool built = false;
+  int32_t n[3] = {1, 1, 1};
+  int64_t ncells = 0, nitems = 0;
+  void* grid = nullptr;          // device GridP<P>
+  int32_t* cell_start = nullptr;  // [ncells + 1]
+  int32_t* cell_items = nullptr;  // [nitems]
+  void* recs = nullptr;           // [ne][RecLen] P
+  void* vals = nullptr;           // [nf][ne][4] P
+  void* coordsP = nullptr;        // [nv][dim] P
+};
+
+}  // namespace sft
+
+struct sft_source_s {
+  int dim = 2, nf = 1;
+  int64_t nv = 0, ne = 0;
+  int dtype = SFT_F64;
+  double L = 1.0;
+  cudaStream_t stream = nullptr;
+  void* coords = nullptr;       // [nv][dim] input dtype
+  int32_t* conn = nullptr;      // [ne][dim+1]
+  void* values = nullptr;       // [nf][nv] input dtype
+  double integral[sft::kMaxFields] = {0};
+  sft::Locator loc[2];          // index = sft_precision (0 FP64, 1 FP32)
+};
+
+struct sft_target_s {
+  int dim = 2;
+  int64_t nv = 0, ne = 0;
+  int dtype = SFT_F64;
+  cudaStream_t stream = nullptr;
+  void* coords = nullptr;       // [nv][dim] input dtype
+  int32_t* conn = nullptr;      // [ne][dim+1]
+  void* coordsP[2] = {nullptr, nullptr};  // per precision copy (lazy)
+  double* vol = nullptr;        // [ne] FP64 measures
+  // mass matrix, CSR FP64
+  int64_t nnz = 0;
+  int32_t* row_ptr = nullptr;   // [nv+1]
+  int32_t* col = nullptr;       // [nnz]
+  double* val = nullptr;        // [nnz]
+  double* dinv = nullptr;       // [nv]
+  double* lumped = nullptr;     // [nv]
+};
+
+namespace sft {
+// locate.cu
+sft_status build_locator(sft_source_s* s, int prec, cudaStream_t st, int32_t* d_err);
+sft_status locate_points(sft_source_s* s, int prec, int64_t n, const void* pts, int pts_are_double,
+                         int32_t* elem_out, void* val_out, int val_is_double, int64_t val_stride,
+                         int64_t* d_counters, cudaStream_t st);
+sft_status source_integrals(sft_source_s* s, cudaStream_t st);
+// target.cu
+sft_status build_target(sft_target_s* t, cudaStream_t st, int32_t* d_err);
+sft_status target_coordsP(sft_target_s* t, int prec, cudaStream_t st);
+// assemble.cu
+struct AssembleArgs {
+  int prec;
+  int nf;
+  int N;
+  uint64_t seed;
+  uint32_t stream_id;
+  double alpha;
+  const void* g;          // [nf][nv_t] P
+  double* b;              // [nf][nv_t] FP64 (accumulated)
+  int32_t* sample_elem;   // optional [ne_t][N]
+  int64_t* counters;      // [2]: fallback, empty
+};
+sft_status launch_assembly(sft_source_s* s, sft_target_s* t, const AssembleArgs& a, cudaStream_t st);
+// solve.cu
+struct SolveResult { int iters; double rel_resid; int converged; };
+sft_status mass_solve(sft_target_s* t, int nrhs, const double* b, double* x, double tol, int max_iter,
+                      cudaStream_t st, int32_t* d_err, SolveResult* res);
+sft_status weighted_sum(const double* w, const double* u, int64_t n, double* out_host, cudaStream_t st);
+// conversions
+sft_status convert_coords(const void* in, int in_dtype, void* out, int out_prec, int64_t n, cudaStream_t st);
+}  // namespace sft

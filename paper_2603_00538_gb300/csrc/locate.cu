@@ -1,0 +1,502 @@
+// Source side of the transfer: the uniform-grid point-location structure
+// (Sec. 5.3 grid search; cells per axis int(L sqrt(#elements)) in 2D, the
+// cube-root analogue in 3D), built on the GPU by a counting sort of
+// (cell, element) registrations, and the standalone point-query kernel used
+// for the control values g (Sec. 4 step 1) and the query entry point.
+//
+// Layout in HBM per precision P:
+//   recs  [ne][8 | 12] P  : first vertex + inverse affine map (16-B aligned rows)
+//   vals  [nf][ne][4]  P  : per-element copy of the nodal values (one 16/32-B load)
+//   cell_start [ncells+1], cell_items [nitems] int32: elements of each cell in
+//   ascending id (the order the first-accepting-candidate rule scans).
+#include <cmath>
+#include <vector>
+#include "internal.hpp"
+#include "util.cuh"
+
+namespace sft {
+
+// cells per axis: the largest n >= 1 with n^d <= L^d * ne
+static int32_t cells_per_axis(int dim, int64_t ne, double L) {
+  const double target = (dim == 2 ? L * L : L * L * L) * (double)ne;
+  int64_t n = (int64_t)std::floor(dim == 2 ? std::sqrt(target) : std::cbrt(target));
+  if (n < 1) n = 1;
+  auto pw = [dim](double x) { return dim == 2 ? x * x : x * x * x; };
+  while (pw((double)(n + 1)) <= target) ++n;
+  while (n > 1 && pw((double)n) > target) --n;
+  return (int32_t)n;
+}
+
+template <typename TI, typename TO>
+__global__ void k_convert(const TI* __restrict__ in, TO* __restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (sizeof(TO) == 4 && sizeof(TI) == 8) out[i] = __double2float_rn(in[i]);
+    else out[i] = (TO)in[i];
+  }
+}
+
+sft_status convert_coords(const void* in, int in_dtype, void* out, int out_prec, int64_t n, cudaStream_t st) {
+  if (n <= 0) return SFT_OK;
+  const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 65535 * 8);
+  if (in_dtype == SFT_F64 && out_prec == SFT_PREC_FP32)
+    k_convert<double, float><<<blocks, 256, 0, st>>>((const double*)in, (float*)out, n);
+  else if (in_dtype == SFT_F64)
+    k_convert<double, double><<<blocks, 256, 0, st>>>((const double*)in, (double*)out, n);
+  else if (out_prec == SFT_PREC_FP32)
+    k_convert<float, float><<<blocks, 256, 0, st>>>((const float*)in, (float*)out, n);
+  else
+    k_convert<float, double><<<blocks, 256, 0, st>>>((const float*)in, (double*)out, n);
+  SFT_CUDA(cudaGetLastError());
+  return SFT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// grid box: per-block min/max, then one block combines and forms GridP
+// ---------------------------------------------------------------------------
+template <int D, typename P>
+__global__ void k_bbox_partial(const P* __restrict__ x, int64_t nv, P* __restrict__ part) {
+  P lo[D], hi[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) { lo[a] = P(INFINITY); hi[a] = P(-INFINITY); }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const P v = x[i * D + a];
+      lo[a] = v < lo[a] ? v : lo[a];
+      hi[a] = v > hi[a] ? v : hi[a];
+    }
+  }
+  __shared__ P slo[D][256], shi[D][256];
+#pragma unroll
+  for (int a = 0; a < D; ++a) { slo[a][threadIdx.x] = lo[a]; shi[a][threadIdx.x] = hi[a]; }
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const P l2 = slo[a][threadIdx.x + s], h2 = shi[a][threadIdx.x + s];
+        if (l2 < slo[a][threadIdx.x]) slo[a][threadIdx.x] = l2;
+        if (h2 > shi[a][threadIdx.x]) shi[a][threadIdx.x] = h2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) { part[blockIdx.x * 2 * D + a] = slo[a][0]; part[blockIdx.x * 2 * D + D + a] = shi[a][0]; }
+  }
+}
+
+template <int D, typename P>
+__global__ void k_grid_params(const P* __restrict__ part, int nblocks, int32_t n, GridP<P>* __restrict__ g,
+                              int32_t* err) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  GridP<P> r;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) { r.lo[a] = P(0); r.inv[a] = P(0); r.n[a] = 1; }
+  for (int a = 0; a < D; ++a) {
+    P lo = part[a], hi = part[D + a];
+    for (int b = 1; b < nblocks; ++b) {
+      const P l2 = part[b * 2 * D + a], h2 = part[b * 2 * D + D + a];
+      lo = l2 < lo ? l2 : lo;
+      hi = h2 > hi ? h2 : hi;
+    }
+    if (!(hi > lo)) set_error(err, DEV_BAD_ELEMENT);
+    r.lo[a] = lo;
+    r.inv[a] = Ar<P>::from_d(__ddiv_rn((double)n, __dsub_rn((double)hi, (double)lo)));
+    r.n[a] = n;
+  }
+  *g = r;
+}
+
+// ---------------------------------------------------------------------------
+// per-element location records + per-element value copies
+// ---------------------------------------------------------------------------
+template <int D, typename P>
+__device__ __forceinline__ void elem_vertices(const P* __restrict__ x, const int32_t* __restrict__ conn, int64_t e,
+                                              P xv[D + 1][D]) {
+#pragma unroll
+  for (int m = 0; m <= D; ++m) {
+    const int32_t v = conn[e * (D + 1) + m];
+#pragma unroll
+    for (int a = 0; a < D; ++a) xv[m][a] = x[(int64_t)v * D + a];
+  }
+}
+
+template <int D, typename P>
+__device__ __forceinline__ int64_t elem_cell_range(const GridP<P>& g, const P xv[D + 1][D], int32_t c0[3], int32_t c1[3]) {
+  int64_t cnt = 1;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) { c0[a] = 0; c1[a] = 0; }
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    P lo = xv[0][a], hi = xv[0][a];
+#pragma unroll
+    for (int m = 1; m <= D; ++m) {
+      lo = xv[m][a] < lo ? xv[m][a] : lo;
+      hi = xv[m][a] > hi ? xv[m][a] : hi;
+    }
+    c0[a] = cell_axis<P>(lo, g.lo[a], g.inv[a], g.n[a]);
+    c1[a] = cell_axis<P>(hi, g.lo[a], g.inv[a], g.n[a]);
+    cnt *= (int64_t)(c1[a] - c0[a] + 1);
+  }
+  return cnt;
+}
+
+template <int D, typename P, typename TV>
+__global__ void k_records(const P* __restrict__ x, const int32_t* __restrict__ conn, const TV* __restrict__ values,
+                          int64_t nv, int64_t ne, int nf, const GridP<P>* __restrict__ gp, P* __restrict__ recs,
+                          P* __restrict__ vals, int32_t* __restrict__ counts, int32_t* err) {
+  constexpr int L = RecLen<D>::value;
+  const GridP<P> g = *gp;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v[D + 1];
+    bool ok = true;
+#pragma unroll
+    for (int m = 0; m <= D; ++m) {
+      v[m] = conn[e * (D + 1) + m];
+      ok = ok && v[m] >= 0 && v[m] < nv;
+    }
+    if (!ok) {
+      set_error(err, DEV_BAD_INDEX);
+      counts[e] = 0;
+      continue;
+    }
+    P xv[D + 1][D];
+    elem_vertices<D, P>(x, conn, e, xv);
+    P r[L];
+#pragma unroll
+    for (int q = 0; q < L; ++q) r[q] = P(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) r[a] = xv[0][a];
+    if constexpr (D == 2) {
+      const double ax = xv[0][0], ay = xv[0][1];
+      const double e1x = __dsub_rn((double)xv[1][0], ax), e1y = __dsub_rn((double)xv[1][1], ay);
+      const double e2x = __dsub_rn((double)xv[2][0], ax), e2y = __dsub_rn((double)xv[2][1], ay);
+      const double det = __dsub_rn(__dmul_rn(e1x, e2y), __dmul_rn(e2x, e1y));
+      if (!(det > 0.0)) set_error(err, DEV_BAD_ELEMENT);
+      r[2] = Ar<P>::from_d(__ddiv_rn(e2y, det));
+      r[3] = Ar<P>::from_d(__ddiv_rn(-e2x, det));
+      r[4] = Ar<P>::from_d(__ddiv_rn(-e1y, det));
+      r[5] = Ar<P>::from_d(__ddiv_rn(e1x, det));
+    } else {
+      double e1[3], e2[3], e3[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        e1[a] = __dsub_rn((double)xv[1][a], (double)xv[0][a]);
+        e2[a] = __dsub_rn((double)xv[2][a], (double)xv[0][a]);
+        e3[a] = __dsub_rn((double)xv[3][a], (double)xv[0][a]);
+      }
+      auto crs = [](const double* u, const double* w, double* o) {
+        o[0] = __dsub_rn(__dmul_rn(u[1], w[2]), __dmul_rn(u[2], w[1]));
+        o[1] = __dsub_rn(__dmul_rn(u[2], w[0]), __dmul_rn(u[0], w[2]));
+        o[2] = __dsub_rn(__dmul_rn(u[0], w[1]), __dmul_rn(u[1], w[0]));
+      };
+      double c23[3], c31[3], c12[3];
+      crs(e2, e3, c23);
+      crs(e3, e1, c31);
+      crs(e1, e2, c12);
+      const double det = __dadd_rn(__dadd_rn(__dmul_rn(e1[0], c23[0]), __dmul_rn(e1[1], c23[1])), __dmul_rn(e1[2], c23[2]));
+      if (!(det > 0.0)) set_error(err, DEV_BAD_ELEMENT);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        r[3 + q] = Ar<P>::from_d(__ddiv_rn(c23[q], det));
+        r[6 + q] = Ar<P>::from_d(__ddiv_rn(c31[q], det));
+        r[9 + q] = Ar<P>::from_d(__ddiv_rn(c12[q], det));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < L; ++q) recs[e * L + q] = r[q];
+    for (int f = 0; f < nf; ++f) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+        vals[((int64_t)f * ne + e) * 4 + m] = m <= D ? P(values[(int64_t)f * nv + v[m]]) : P(0);
+    }
+    int32_t c0[3], c1[3];
+    counts[e] = (int32_t)elem_cell_range<D, P>(g, xv, c0, c1);
+  }
+}
+
+// one registration per (element, cell): count or fill
+template <int D, typename P, bool FILL>
+__global__ void k_register(const P* __restrict__ x, const int32_t* __restrict__ conn, int64_t ne,
+                           const GridP<P>* __restrict__ gp, int32_t* __restrict__ cell_count,
+                           const int32_t* __restrict__ cell_start, int32_t* __restrict__ items) {
+  const GridP<P> g = *gp;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+    P xv[D + 1][D];
+    elem_vertices<D, P>(x, conn, e, xv);
+    int32_t c0[3], c1[3];
+    elem_cell_range<D, P>(g, xv, c0, c1);
+    for (int32_t iz = c0[2]; iz <= c1[2]; ++iz)
+      for (int32_t iy = c0[1]; iy <= c1[1]; ++iy)
+        for (int32_t ix = c0[0]; ix <= c1[0]; ++ix) {
+          const int64_t c = ((int64_t)iz * g.n[1] + iy) * g.n[0] + ix;
+          const int32_t pos = atomicAdd(cell_count + c, 1);
+          if (FILL) items[cell_start[c] + pos] = (int32_t)e;
+        }
+  }
+}
+
+// ascending element order inside each cell (insertion sort; cells are short)
+__global__ void k_sort_cells(const int32_t* __restrict__ cell_start, int32_t* __restrict__ items, int64_t ncells) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t p0 = cell_start[c], p1 = cell_start[c + 1];
+    for (int32_t i = p0 + 1; i < p1; ++i) {
+      const int32_t key = items[i];
+      int32_t j = i - 1;
+      while (j >= p0 && items[j] > key) {
+        items[j + 1] = items[j];
+        --j;
+      }
+      items[j + 1] = key;
+    }
+  }
+}
+
+static unsigned grid_for(int64_t n, int threads = 256) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > 152 * 64) b = 152 * 64;
+  return (unsigned)b;
+}
+
+template <int D, typename P>
+static sft_status build_locator_t(sft_source_s* s, int prec, cudaStream_t st, int32_t* d_err) {
+  Locator& L = s->loc[prec];
+  constexpr int RL = RecLen<D>::value;
+  // coordinates in P
+  P* xP = nullptr;
+  SFT_CUDA(dalloc(&xP, (size_t)s->nv * D, st));
+  L.coordsP = xP;
+  if (sft_status r = convert_coords(s->coords, s->dtype, xP, prec, s->nv * D, st)) return r;
+  // grid box and parameters
+  const int32_t n = cells_per_axis(D, s->ne, s->L);
+  L.n[0] = L.n[1] = L.n[2] = 1;
+  L.ncells = 1;
+  for (int a = 0; a < D; ++a) { L.n[a] = n; L.ncells *= n; }
+  const unsigned nb = 256;
+  P* part = nullptr;
+  SFT_CUDA(dalloc(&part, (size_t)nb * 2 * D, st));
+  k_bbox_partial<D, P><<<nb, 256, 0, st>>>(xP, s->nv, part);
+  GridP<P>* g = nullptr;
+  SFT_CUDA(dalloc(&g, 1, st));
+  L.grid = g;
+  k_grid_params<D, P><<<1, 32, 0, st>>>(part, nb, n, g, d_err);
+  SFT_CUDA(cudaGetLastError());
+  dfree(part, st);
+  // records, value copies, per-element registration counts
+  P* recs = nullptr;
+  P* vals = nullptr;
+  int32_t* counts = nullptr;
+  SFT_CUDA(dalloc(&recs, (size_t)s->ne * RL, st));
+  SFT_CUDA(dalloc(&vals, (size_t)s->nf * s->ne * 4, st));
+  SFT_CUDA(dalloc(&counts, (size_t)s->ne, st));
+  L.recs = recs;
+  L.vals = vals;
+  if (s->dtype == SFT_F64)
+    k_records<D, P, double><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, (const double*)s->values, s->nv, s->ne,
+                                                             s->nf, g, recs, vals, counts, d_err);
+  else
+    k_records<D, P, float><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, (const float*)s->values, s->nv, s->ne,
+                                                            s->nf, g, recs, vals, counts, d_err);
+  SFT_CUDA(cudaGetLastError());
+  int32_t herr = 0;
+  SFT_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  // total registrations (int64) -> check that int32 offsets suffice
+  int64_t* eoff = nullptr;
+  SFT_CUDA(dalloc(&eoff, (size_t)s->ne + 1, st));
+  SFT_CUDA(exclusive_scan_i32_to_i64(counts, eoff, s->ne, st));
+  int64_t total = 0;
+  SFT_CUDA(cudaMemcpyAsync(&total, eoff + s->ne, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  SFT_CUDA(cudaStreamSynchronize(st));
+  dfree(eoff, st);
+  dfree(counts, st);
+  if (herr != 0)
+    return fail(SFT_ERR_MESH, herr == DEV_BAD_INDEX ? "source connectivity index out of range"
+                                                    : "source mesh has a non-positive element or a degenerate box");
+  if (total >= (int64_t)INT32_MAX) return fail(SFT_ERR_UNSUPPORTED, "grid registrations exceed 2^31");
+  L.nitems = total;
+  // counting sort by cell
+  int32_t* cell_count = nullptr;
+  int64_t* start64 = nullptr;
+  SFT_CUDA(dalloc(&cell_count, (size_t)L.ncells, st));
+  SFT_CUDA(dalloc(&start64, (size_t)L.ncells + 1, st));
+  SFT_CUDA(dalloc(&L.cell_start, (size_t)L.ncells + 1, st));
+  SFT_CUDA(dalloc(&L.cell_items, (size_t)total, st));
+  SFT_CUDA(cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * L.ncells, st));
+  k_register<D, P, false><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, s->ne, g, cell_count, nullptr, nullptr);
+  SFT_CUDA(cudaGetLastError());
+  SFT_CUDA(exclusive_scan_i32_to_i64(cell_count, start64, L.ncells, st));
+  SFT_CUDA(narrow_i64_to_i32(start64, L.cell_start, L.ncells + 1, st));
+  SFT_CUDA(cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * L.ncells, st));
+  k_register<D, P, true><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, s->ne, g, cell_count, L.cell_start, L.cell_items);
+  SFT_CUDA(cudaGetLastError());
+  k_sort_cells<<<grid_for(L.ncells), 256, 0, st>>>(L.cell_start, L.cell_items, L.ncells);
+  SFT_CUDA(cudaGetLastError());
+  dfree(cell_count, st);
+  dfree(start64, st);
+  L.built = true;
+  return SFT_OK;
+}
+
+sft_status build_locator(sft_source_s* s, int prec, cudaStream_t st, int32_t* d_err) {
+  if (s->loc[prec].built) return SFT_OK;
+  if (s->dim == 2)
+    return prec == SFT_PREC_FP32 ? build_locator_t<2, float>(s, prec, st, d_err) : build_locator_t<2, double>(s, prec, st, d_err);
+  return prec == SFT_PREC_FP32 ? build_locator_t<3, float>(s, prec, st, d_err) : build_locator_t<3, double>(s, prec, st, d_err);
+}
+
+// ---------------------------------------------------------------------------
+// point queries: location + P1 evaluation of all fields
+// ---------------------------------------------------------------------------
+template <int D, typename P, typename TIn, typename TOut>
+__global__ void __launch_bounds__(256) k_locate_points(const TIn* __restrict__ pts, int64_t n,
+                                                       const GridP<P>* __restrict__ gp,
+                                                       const int32_t* __restrict__ cell_start,
+                                                       const int32_t* __restrict__ cell_items,
+                                                       const P* __restrict__ recs, const P* __restrict__ vals,
+                                                       int64_t ne, int nf, int32_t* __restrict__ elem_out,
+                                                       TOut* __restrict__ val_out, int64_t val_stride,
+                                                       int64_t* __restrict__ counters) {
+  const GridP<P> g = *gp;
+  int n_fallback = 0, n_empty = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    P X[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      if constexpr (sizeof(P) == 4 && sizeof(TIn) == 8) X[a] = __double2float_rn(pts[i * D + a]);
+      else X[a] = (P)pts[i * D + a];
+    }
+    P mu[D + 1];
+    int status;
+    const int32_t e = locate_point<D, P>(g, cell_start, cell_items, recs, X, mu, status);
+    n_fallback += status == 1;
+    n_empty += status == 2;
+    if (elem_out) elem_out[i] = e;
+    if (val_out) {
+      for (int f = 0; f < nf; ++f)
+        val_out[(int64_t)f * val_stride + i] = e >= 0 ? (TOut)eval_p1<D, P>(vals, ne, f, e, mu) : TOut(0);
+    }
+  }
+  if (counters) {
+    const int fb = warp_sum<int>(n_fallback), em = warp_sum<int>(n_empty);
+    if ((threadIdx.x & 31) == 0) {
+      if (fb) atomicAdd(reinterpret_cast<unsigned long long*>(counters), (unsigned long long)fb);
+      if (em) atomicAdd(reinterpret_cast<unsigned long long*>(counters + 1), (unsigned long long)em);
+    }
+  }
+}
+
+template <int D, typename P>
+static void launch_locate(sft_source_s* s, const Locator& L, int64_t n, const void* pts, int pts_are_double,
+                          int32_t* elem_out, void* val_out, int val_is_double, int64_t val_stride,
+                          int64_t* counters, cudaStream_t st) {
+  const unsigned blocks = grid_for(n);
+  const GridP<P>* g = (const GridP<P>*)L.grid;
+  const P* recs = (const P*)L.recs;
+  const P* vals = (const P*)L.vals;
+#define SFT_LOC(TIN, TOUT)                                                                                      \
+  k_locate_points<D, P, TIN, TOUT><<<blocks, 256, 0, st>>>((const TIN*)pts, n, g, L.cell_start, L.cell_items, \
+                                                           recs, vals, s->ne, s->nf, elem_out, (TOUT*)val_out,  \
+                                                           val_stride, counters)
+  if (pts_are_double) {
+    if (val_is_double) SFT_LOC(double, double); else SFT_LOC(double, P);
+  } else {
+    if (val_is_double) SFT_LOC(P, double); else SFT_LOC(P, P);
+  }
+#undef SFT_LOC
+}
+
+sft_status locate_points(sft_source_s* s, int prec, int64_t n, const void* pts, int pts_are_double,
+                         int32_t* elem_out, void* val_out, int val_is_double, int64_t val_stride,
+                         int64_t* d_counters, cudaStream_t st) {
+  const Locator& L = s->loc[prec];
+  if (!L.built) return fail(SFT_ERR_ARG, "locator not built");
+  if (n <= 0) return SFT_OK;
+  if (s->dim == 2) {
+    if (prec == SFT_PREC_FP32) launch_locate<2, float>(s, L, n, pts, pts_are_double, elem_out, val_out, val_is_double, val_stride, d_counters, st);
+    else launch_locate<2, double>(s, L, n, pts, pts_are_double, elem_out, val_out, val_is_double, val_stride, d_counters, st);
+  } else {
+    if (prec == SFT_PREC_FP32) launch_locate<3, float>(s, L, n, pts, pts_are_double, elem_out, val_out, val_is_double, val_stride, d_counters, st);
+    else launch_locate<3, double>(s, L, n, pts, pts_are_double, elem_out, val_out, val_is_double, val_stride, d_counters, st);
+  }
+  SFT_CUDA(cudaGetLastError());
+  return SFT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// exact P1 integral of every source field: sum_e |e| mean(f over vertices)
+// ---------------------------------------------------------------------------
+template <int D, typename TI>
+__global__ void k_p1_integral_partial(const TI* __restrict__ x, const int32_t* __restrict__ conn,
+                                      const TI* __restrict__ values, int64_t nv, int64_t ne, int nf,
+                                      double* __restrict__ part) {
+  double acc[kMaxFields];
+  for (int f = 0; f < kMaxFields; ++f) acc[f] = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+    double xv[D + 1][D];
+    int32_t v[D + 1];
+#pragma unroll
+    for (int m = 0; m <= D; ++m) {
+      v[m] = conn[e * (D + 1) + m];
+#pragma unroll
+      for (int a = 0; a < D; ++a) xv[m][a] = (double)x[(int64_t)v[m] * D + a];
+    }
+    double vol;
+    if constexpr (D == 2) {
+      vol = 0.5 * ((xv[1][0] - xv[0][0]) * (xv[2][1] - xv[0][1]) - (xv[2][0] - xv[0][0]) * (xv[1][1] - xv[0][1]));
+    } else {
+      double e1[3], e2[3], e3[3];
+      for (int a = 0; a < 3; ++a) { e1[a] = xv[1][a] - xv[0][a]; e2[a] = xv[2][a] - xv[0][a]; e3[a] = xv[3][a] - xv[0][a]; }
+      vol = (e1[0] * (e2[1] * e3[2] - e2[2] * e3[1]) - e1[1] * (e2[0] * e3[2] - e2[2] * e3[0]) +
+             e1[2] * (e2[0] * e3[1] - e2[1] * e3[0])) / 6.0;
+    }
+    for (int f = 0; f < nf; ++f) {
+      double m = 0.0;
+#pragma unroll
+      for (int q = 0; q <= D; ++q) m += (double)values[(int64_t)f * nv + v[q]];
+      acc[f] += vol * m / (double)(D + 1);
+    }
+  }
+  __shared__ double sh[kMaxFields][8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int f = 0; f < nf; ++f) {
+    const double w = warp_sum<double>(acc[f]);
+    if (lane == 0) sh[f][warp] = w;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int f = 0; f < nf; ++f) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += sh[f][w];
+      part[(int64_t)blockIdx.x * kMaxFields + f] = t;
+    }
+  }
+}
+
+sft_status source_integrals(sft_source_s* s, cudaStream_t st) {
+  const unsigned nb = 256;
+  double* part = nullptr;
+  SFT_CUDA(dalloc(&part, (size_t)nb * kMaxFields, st));
+  if (s->dim == 2) {
+    if (s->dtype == SFT_F64) k_p1_integral_partial<2, double><<<nb, 256, 0, st>>>((const double*)s->coords, s->conn, (const double*)s->values, s->nv, s->ne, s->nf, part);
+    else k_p1_integral_partial<2, float><<<nb, 256, 0, st>>>((const float*)s->coords, s->conn, (const float*)s->values, s->nv, s->ne, s->nf, part);
+  } else {
+    if (s->dtype == SFT_F64) k_p1_integral_partial<3, double><<<nb, 256, 0, st>>>((const double*)s->coords, s->conn, (const double*)s->values, s->nv, s->ne, s->nf, part);
+    else k_p1_integral_partial<3, float><<<nb, 256, 0, st>>>((const float*)s->coords, s->conn, (const float*)s->values, s->nv, s->ne, s->nf, part);
+  }
+  SFT_CUDA(cudaGetLastError());
+  std::vector<double> h((size_t)nb * kMaxFields);
+  SFT_CUDA(cudaMemcpyAsync(h.data(), part, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
+  SFT_CUDA(cudaStreamSynchronize(st));
+  dfree(part, st);
+  for (int f = 0; f < s->nf; ++f) {
+    double t = 0.0;
+    for (unsigned b = 0; b < nb; ++b) t += h[(size_t)b * kMaxFields + f];
+    s->integral[f] = t;
+  }
+  return SFT_OK;
+}
+
+}  // namespace sft

@@ -1,0 +1,298 @@
+// Step 7 of Sec. 4: solve the target Galerkin system M u = b (Eq.
+// cv_galerkin_system) in FP64 with Jacobi-preconditioned CG from u = 0,
+// stopping at ||b - M u||_2 <= tol ||b||_2 (the paper does not name its
+// solver; see the design notes).
+//
+// One cooperative (co-resident) kernel runs the whole iteration: no host round
+// trip per step. Each iteration has two grid barriers:
+//   A: p_new = z + beta p_old (own rows) and q = M p_new, with the neighbours'
+//      p_new recomputed on the fly from z and p_old (double-buffered p), and
+//      the partial dot p_new.q;
+//   B: u += a p_new, r -= a q, z = D^-1 r, partial dots r.r and r.z.
+// Dot products are reduced deterministically: per-block partials, then every
+// block sums all partials in the same fixed order, so all blocks take the
+// same convergence decision. The barrier wait is bounded (error flag on
+// timeout; the kernel then returns).
+#include <algorithm>
+#include <vector>
+#include "internal.hpp"
+#include "util.cuh"
+
+namespace sft {
+
+constexpr int kSolveThreads = 256;
+
+struct PcgCtl {
+  GridBarrier bar;
+  int32_t err;
+  int32_t iters[kMaxFields];
+  double rel[kMaxFields];
+  int32_t conv[kMaxFields];
+};
+
+// sum the per-block partials [nblocks][nrhs][2] -> tot[nrhs][2] (identical in all blocks)
+__device__ __forceinline__ void reduce_partials(const double* part, int nblocks, int nrhs, double* sh_tot) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int f = 0; f < nrhs; ++f) {
+      for (int c = 0; c < 2; ++c) {
+        double s = 0.0;
+        for (int bidx = lane; bidx < nblocks; bidx += 32) s += __ldcg(part + ((int64_t)bidx * nrhs + f) * 2 + c);
+        s = warp_sum<double>(s);
+        if (lane == 0) sh_tot[f * 2 + c] = s;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void block_partials(double v[kMaxFields][2], int nrhs, double* part) {
+  __shared__ double sh[kSolveThreads / 32][kMaxFields][2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int f = 0; f < nrhs; ++f)
+    for (int c = 0; c < 2; ++c) {
+      const double w = warp_sum<double>(v[f][c]);
+      if (lane == 0) sh[warp][f][c] = w;
+    }
+  __syncthreads();
+  if (threadIdx.x < nrhs * 2) {
+    const int f = threadIdx.x >> 1, c = threadIdx.x & 1;
+    double s = 0.0;
+    for (int w = 0; w < kSolveThreads / 32; ++w) s += sh[w][f][c];
+    part[((int64_t)blockIdx.x * nrhs + f) * 2 + c] = s;
+  }
+  __syncthreads();
+}
+
+template <int TPR>
+__global__ void __launch_bounds__(kSolveThreads) k_pcg(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                       const double* __restrict__ val, const double* __restrict__ dinv,
+                                                       int64_t n, int nrhs, const double* __restrict__ b,
+                                                       double* __restrict__ x, double* r, double* z, double* pA,
+                                                       double* pB, double* q, double* part, PcgCtl* ctl, double tol,
+                                                       int max_iter) {
+  __shared__ double tot[kMaxFields * 2];
+  __shared__ double bnorm[kMaxFields], rz[kMaxFields], beta[kMaxFields], alpha[kMaxFields];
+  __shared__ int conv[kMaxFields];
+  const unsigned nb = gridDim.x;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  double v[kMaxFields][2];
+
+  // init: x = 0, r = b, z = D^-1 r, p_old = 0
+  for (int f = 0; f < kMaxFields; ++f) v[f][0] = v[f][1] = 0.0;
+  for (int64_t i = tid; i < n; i += nthreads) {
+    const double di = dinv[i];
+    for (int f = 0; f < nrhs; ++f) {
+      const int64_t k = (int64_t)f * n + i;
+      const double bi = b[k];
+      x[k] = 0.0;
+      r[k] = bi;
+      z[k] = di * bi;
+      pA[k] = 0.0;
+      v[f][0] += bi * bi;
+      v[f][1] += bi * di * bi;
+    }
+  }
+  block_partials(v, nrhs, part);
+  if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+  reduce_partials(part, nb, nrhs, tot);
+  if (threadIdx.x == 0) {
+    for (int f = 0; f < nrhs; ++f) {
+      bnorm[f] = sqrt(tot[f * 2]);
+      rz[f] = tot[f * 2 + 1];
+      beta[f] = 0.0;
+      conv[f] = bnorm[f] == 0.0;
+    }
+  }
+  __syncthreads();
+
+  int it = 0;
+  double* pold = pA;
+  double* pnew = pB;
+  constexpr int kRowsPerWarp = 32 / TPR;
+  const int lane = threadIdx.x & 31;
+  const int lane_in_row = lane % TPR;
+  const int64_t warp_id = tid >> 5, nwarps = nthreads >> 5;
+  for (;;) {
+    bool all = true;
+    for (int f = 0; f < nrhs; ++f) all = all && conv[f];
+    if (all || it >= max_iter) break;
+    // phase A (warp-uniform loop: each warp owns 32/TPR consecutive rows)
+    for (int f = 0; f < kMaxFields; ++f) v[f][0] = v[f][1] = 0.0;
+    for (int64_t base = warp_id * kRowsPerWarp; base < n; base += nwarps * kRowsPerWarp) {
+      const int64_t row = base + lane / TPR;
+      const bool valid = row < n;
+      int32_t q0 = 0, q1 = 0;
+      if (valid) {
+        q0 = __ldg(rp + row);
+        q1 = __ldg(rp + row + 1);
+      }
+      for (int f = 0; f < nrhs; ++f) {
+        if (conv[f]) continue;
+        const double bt = beta[f];
+        const double* zf = z + (int64_t)f * n;
+        const double* pf = pold + (int64_t)f * n;
+        double s = 0.0;
+        for (int32_t k = q0 + lane_in_row; k < q1; k += TPR) {
+          const int32_t j = __ldg(col + k);
+          s += __ldg(val + k) * (__ldcg(zf + j) + bt * __ldcg(pf + j));
+        }
+#pragma unroll
+        for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, TPR);
+        if (valid && lane_in_row == 0) {
+          const double pn = __ldcg(zf + row) + bt * __ldcg(pf + row);
+          pnew[(int64_t)f * n + row] = pn;
+          q[(int64_t)f * n + row] = s;
+          v[f][0] += pn * s;
+        }
+      }
+    }
+    block_partials(v, nrhs, part);
+    if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+    reduce_partials(part, nb, nrhs, tot);
+    if (threadIdx.x == 0)
+      for (int f = 0; f < nrhs; ++f) alpha[f] = conv[f] ? 0.0 : rz[f] / tot[f * 2];
+    __syncthreads();
+    // phase B
+    for (int f = 0; f < kMaxFields; ++f) v[f][0] = v[f][1] = 0.0;
+    for (int64_t i = tid; i < n; i += nthreads) {
+      const double di = dinv[i];
+      for (int f = 0; f < nrhs; ++f) {
+        if (conv[f]) continue;
+        const int64_t k = (int64_t)f * n + i;
+        const double a = alpha[f];
+        x[k] = __ldcg(x + k) + a * __ldcg(pnew + k);
+        const double ri = __ldcg(r + k) - a * __ldcg(q + k);
+        r[k] = ri;
+        const double zi = di * ri;
+        z[k] = zi;
+        v[f][0] += ri * ri;
+        v[f][1] += ri * zi;
+      }
+    }
+    block_partials(v, nrhs, part);
+    if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+    reduce_partials(part, nb, nrhs, tot);
+    ++it;
+    if (threadIdx.x == 0) {
+      for (int f = 0; f < nrhs; ++f) {
+        if (conv[f]) continue;
+        const double rn = sqrt(tot[f * 2]);
+        ctl->iters[f] = it;  // identical in every block
+        ctl->rel[f] = rn / bnorm[f];
+        if (rn <= tol * bnorm[f]) conv[f] = 1;
+        beta[f] = tot[f * 2 + 1] / rz[f];
+        rz[f] = tot[f * 2 + 1];
+      }
+    }
+    __syncthreads();
+    double* tmp = pold;
+    pold = pnew;
+    pnew = tmp;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int f = 0; f < nrhs; ++f) {
+      ctl->conv[f] = conv[f];
+      if (bnorm[f] == 0.0) { ctl->iters[f] = 0; ctl->rel[f] = 0.0; }
+    }
+  }
+}
+
+sft_status mass_solve(sft_target_s* t, int nrhs, const double* b, double* x, double tol, int max_iter,
+                      cudaStream_t st, int32_t* d_err, SolveResult* res) {
+  (void)d_err;
+  res->iters = 0;
+  res->rel_resid = 0.0;
+  res->converged = 1;
+  const int64_t n = t->nv;
+  if (n == 0 || nrhs == 0) return SFT_OK;
+  if (nrhs > kMaxFields) return fail(SFT_ERR_ARG, "at most 8 right-hand sides");
+  if (max_iter <= 0) {
+    SFT_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n * nrhs, st));
+    res->converged = 0;
+    return SFT_OK;
+  }
+  int dev = 0, sms = 0, coop = 0;
+  SFT_CUDA(cudaGetDevice(&dev));
+  SFT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  SFT_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) return fail(SFT_ERR_UNSUPPORTED, "device lacks cooperative launch");
+  const bool wide = t->dim == 3;
+  int per_sm = 0;
+  if (wide) SFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<16>, kSolveThreads, 0));
+  else SFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<8>, kSolveThreads, 0));
+  if (per_sm < 1) return fail(SFT_ERR_CUDA, "solver kernel cannot be resident");
+  per_sm = std::min(per_sm, 4);
+  const int64_t want = (n * (wide ? 16 : 8) + kSolveThreads - 1) / kSolveThreads;
+  const unsigned nblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, want));
+
+  double *r = nullptr, *z = nullptr, *pA = nullptr, *pB = nullptr, *q = nullptr, *part = nullptr;
+  PcgCtl* ctl = nullptr;
+  const size_t vec = (size_t)n * nrhs;
+  SFT_CUDA(dalloc(&r, vec, st));
+  SFT_CUDA(dalloc(&z, vec, st));
+  SFT_CUDA(dalloc(&pA, vec, st));
+  SFT_CUDA(dalloc(&pB, vec, st));
+  SFT_CUDA(dalloc(&q, vec, st));
+  SFT_CUDA(dalloc(&part, (size_t)nblocks * nrhs * 2, st));
+  SFT_CUDA(dalloc(&ctl, 1, st));
+  SFT_CUDA(cudaMemsetAsync(ctl, 0, sizeof(PcgCtl), st));
+  const int32_t* rp = t->row_ptr;
+  const int32_t* col = t->col;
+  const double* val = t->val;
+  const double* dinv = t->dinv;
+  void* args[] = {(void*)&rp, (void*)&col, (void*)&val, (void*)&dinv, (void*)&n, (void*)&nrhs, (void*)&b,
+                  (void*)&x, (void*)&r, (void*)&z, (void*)&pA, (void*)&pB, (void*)&q, (void*)&part,
+                  (void*)&ctl, (void*)&tol, (void*)&max_iter};
+  cudaError_t le;
+  if (wide) le = cudaLaunchCooperativeKernel((const void*)k_pcg<16>, nblocks, kSolveThreads, args, 0, st);
+  else le = cudaLaunchCooperativeKernel((const void*)k_pcg<8>, nblocks, kSolveThreads, args, 0, st);
+  if (le != cudaSuccess) return cuda_fail(le, "cudaLaunchCooperativeKernel(k_pcg)");
+  PcgCtl h;
+  SFT_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
+  SFT_CUDA(cudaStreamSynchronize(st));
+  dfree(r, st); dfree(z, st); dfree(pA, st); dfree(pB, st); dfree(q, st); dfree(part, st); dfree(ctl, st);
+  if (h.err != 0) return fail(SFT_ERR_DEVICE_STATUS, "CG kernel: grid barrier wait expired");
+  for (int f = 0; f < nrhs; ++f) {
+    res->iters = std::max(res->iters, (int)h.iters[f]);
+    res->rel_resid = std::max(res->rel_resid, h.rel[f]);
+    if (!h.conv[f]) res->converged = 0;
+  }
+  return SFT_OK;
+}
+
+// deterministic FP64 sum of w_i u_i (the integral of a P1 target field with lumped masses)
+__global__ void k_wsum_partial(const double* __restrict__ w, const double* __restrict__ u, int64_t n,
+                               double* __restrict__ part) {
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += w[i] * u[i];
+  __shared__ double sh[8];
+  s = warp_sum<double>(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x / 32); ++k) t += sh[k];
+    part[blockIdx.x] = t;
+  }
+}
+
+sft_status weighted_sum(const double* w, const double* u, int64_t n, double* out_host, cudaStream_t st) {
+  const unsigned nb = 304;
+  double* part = nullptr;
+  SFT_CUDA(dalloc(&part, nb, st));
+  k_wsum_partial<<<nb, 256, 0, st>>>(w, u, n, part);
+  SFT_CUDA(cudaGetLastError());
+  std::vector<double> h(nb);
+  SFT_CUDA(cudaMemcpyAsync(h.data(), part, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+  SFT_CUDA(cudaStreamSynchronize(st));
+  dfree(part, st);
+  double t = 0.0;
+  for (unsigned k = 0; k < nb; ++k) t += h[k];
+  *out_host = t;
+  return SFT_OK;
+}
+
+}  // namespace sft

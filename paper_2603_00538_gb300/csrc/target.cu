@@ -1,0 +1,212 @@
+// Target side: element measures |T| and the FP64 P1 mass matrix
+// M_ki = int psi_k psi_i (Eq. mass_matrix). P1 x P1 is degree 2, so exact
+// quadrature gives the closed form |T| (1 + delta_ij) / ((d+1)(d+2)).
+//
+// CSR build without a global sort: node -> element incidence lists by a
+// counting sort (atomics + per-node insertion sort, ascending element id);
+// then one thread per row merges the vertices of its incident elements into a
+// sorted, de-duplicated column list, summing contributions in ascending
+// element order (deterministic values).
+#include <vector>
+#include "internal.hpp"
+#include "util.cuh"
+
+namespace sft {
+
+constexpr int kMaxRow = 64;  // distinct neighbours (incl. self) per node
+
+template <int D, typename TI>
+__global__ void k_volumes(const TI* __restrict__ x, const int32_t* __restrict__ conn, int64_t nv, int64_t ne,
+                          double* __restrict__ vol, int32_t* __restrict__ inc_count, int32_t* err) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v[D + 1];
+    bool ok = true;
+#pragma unroll
+    for (int m = 0; m <= D; ++m) {
+      v[m] = conn[e * (D + 1) + m];
+      ok = ok && v[m] >= 0 && v[m] < nv;
+    }
+    if (!ok) {
+      set_error(err, DEV_BAD_INDEX);
+      vol[e] = 0.0;
+      continue;
+    }
+    double xv[D + 1][D];
+#pragma unroll
+    for (int m = 0; m <= D; ++m)
+#pragma unroll
+      for (int a = 0; a < D; ++a) xv[m][a] = (double)x[(int64_t)v[m] * D + a];
+    double w;
+    if constexpr (D == 2) {
+      w = 0.5 * ((xv[1][0] - xv[0][0]) * (xv[2][1] - xv[0][1]) - (xv[2][0] - xv[0][0]) * (xv[1][1] - xv[0][1]));
+    } else {
+      double e1[3], e2[3], e3[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) { e1[a] = xv[1][a] - xv[0][a]; e2[a] = xv[2][a] - xv[0][a]; e3[a] = xv[3][a] - xv[0][a]; }
+      w = (e1[0] * (e2[1] * e3[2] - e2[2] * e3[1]) - e1[1] * (e2[0] * e3[2] - e2[2] * e3[0]) +
+           e1[2] * (e2[0] * e3[1] - e2[1] * e3[0])) / 6.0;
+    }
+    if (!(w > 0.0) || !isfinite(w)) set_error(err, DEV_BAD_ELEMENT);
+    vol[e] = w;
+#pragma unroll
+    for (int m = 0; m <= D; ++m) atomicAdd(inc_count + v[m], 1);
+  }
+}
+
+template <int D>
+__global__ void k_inc_fill(const int32_t* __restrict__ conn, int64_t ne, const int32_t* __restrict__ inc_start,
+                           int32_t* __restrict__ cursor, int32_t* __restrict__ inc) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int m = 0; m <= D; ++m) {
+      const int32_t v = conn[e * (D + 1) + m];
+      inc[inc_start[v] + atomicAdd(cursor + v, 1)] = (int32_t)e;
+    }
+  }
+}
+
+__global__ void k_inc_sort(const int32_t* __restrict__ inc_start, int32_t* __restrict__ inc, int64_t nv) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t p0 = inc_start[i], p1 = inc_start[i + 1];
+    for (int32_t a = p0 + 1; a < p1; ++a) {
+      const int32_t key = inc[a];
+      int32_t b = a - 1;
+      while (b >= p0 && inc[b] > key) { inc[b + 1] = inc[b]; --b; }
+      inc[b + 1] = key;
+    }
+  }
+}
+
+// Row i of M: FILL=false writes the row length, FILL=true writes columns,
+// values, the Jacobi inverse diagonal and the lumped mass.
+template <int D, bool FILL>
+__global__ void k_mass_rows(const int32_t* __restrict__ conn, const double* __restrict__ vol,
+                            const int32_t* __restrict__ inc_start, const int32_t* __restrict__ inc, int64_t nv,
+                            int32_t* __restrict__ row_len, const int32_t* __restrict__ row_ptr,
+                            int32_t* __restrict__ col, double* __restrict__ val, double* __restrict__ dinv,
+                            double* __restrict__ lumped, int32_t* err) {
+  constexpr double kDen = (double)((D + 1) * (D + 2));
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t cols[kMaxRow];
+    double vals[kMaxRow];
+    int cnt = 0;
+    bool overflow = false;
+    double lump = 0.0;
+    for (int32_t p = inc_start[i]; p < inc_start[i + 1]; ++p) {
+      const int32_t e = inc[p];
+      const double w = vol[e];
+      lump += w / (double)(D + 1);
+#pragma unroll
+      for (int m = 0; m <= D; ++m) {
+        const int32_t j = conn[(int64_t)e * (D + 1) + m];
+        const double c = w * (j == i ? 2.0 : 1.0) / kDen;
+        int q = 0;
+        while (q < cnt && cols[q] < j) ++q;
+        if (q < cnt && cols[q] == j) {
+          vals[q] += c;
+        } else if (cnt < kMaxRow) {
+          for (int r = cnt; r > q; --r) { cols[r] = cols[r - 1]; vals[r] = vals[r - 1]; }
+          cols[q] = j;
+          vals[q] = c;
+          ++cnt;
+        } else {
+          overflow = true;
+        }
+      }
+    }
+    if (overflow) set_error(err, DEV_VALENCE);
+    if (!FILL) {
+      row_len[i] = cnt;
+    } else {
+      const int32_t base = row_ptr[i];
+      double diag = 0.0;
+      for (int q = 0; q < cnt; ++q) {
+        col[base + q] = cols[q];
+        val[base + q] = vals[q];
+        if (cols[q] == i) diag = vals[q];
+      }
+      dinv[i] = diag > 0.0 ? 1.0 / diag : 0.0;
+      lumped[i] = lump;
+    }
+  }
+}
+
+static unsigned blocks_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b < 1) b = 1;
+  if (b > 152 * 64) b = 152 * 64;
+  return (unsigned)b;
+}
+
+template <int D>
+static sft_status build_target_t(sft_target_s* t, cudaStream_t st, int32_t* d_err) {
+  SFT_CUDA(dalloc(&t->vol, (size_t)t->ne, st));
+  int32_t *inc_count = nullptr, *inc_start = nullptr, *inc = nullptr, *row_len = nullptr;
+  int64_t* off64 = nullptr;
+  SFT_CUDA(dalloc(&inc_count, (size_t)t->nv, st));
+  SFT_CUDA(cudaMemsetAsync(inc_count, 0, sizeof(int32_t) * t->nv, st));
+  if (t->dtype == SFT_F64)
+    k_volumes<D, double><<<blocks_for(t->ne), 256, 0, st>>>((const double*)t->coords, t->conn, t->nv, t->ne, t->vol, inc_count, d_err);
+  else
+    k_volumes<D, float><<<blocks_for(t->ne), 256, 0, st>>>((const float*)t->coords, t->conn, t->nv, t->ne, t->vol, inc_count, d_err);
+  SFT_CUDA(cudaGetLastError());
+  int32_t herr = 0;
+  SFT_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  SFT_CUDA(cudaStreamSynchronize(st));
+  if (herr) {
+    dfree(inc_count, st);
+    return fail(SFT_ERR_MESH, herr == DEV_BAD_INDEX ? "target connectivity index out of range"
+                                                    : "target mesh has a non-positive element");
+  }
+  SFT_CUDA(dalloc(&off64, (size_t)t->nv + 1, st));
+  SFT_CUDA(dalloc(&inc_start, (size_t)t->nv + 1, st));
+  SFT_CUDA(dalloc(&inc, (size_t)t->ne * (D + 1), st));
+  SFT_CUDA(exclusive_scan_i32_to_i64(inc_count, off64, t->nv, st));
+  SFT_CUDA(narrow_i64_to_i32(off64, inc_start, t->nv + 1, st));
+  SFT_CUDA(cudaMemsetAsync(inc_count, 0, sizeof(int32_t) * t->nv, st));
+  k_inc_fill<D><<<blocks_for(t->ne), 256, 0, st>>>(t->conn, t->ne, inc_start, inc_count, inc);
+  SFT_CUDA(cudaGetLastError());
+  k_inc_sort<<<blocks_for(t->nv), 256, 0, st>>>(inc_start, inc, t->nv);
+  SFT_CUDA(cudaGetLastError());
+  row_len = inc_count;  // reuse
+  k_mass_rows<D, false><<<blocks_for(t->nv), 256, 0, st>>>(t->conn, t->vol, inc_start, inc, t->nv, row_len, nullptr,
+                                                           nullptr, nullptr, nullptr, nullptr, d_err);
+  SFT_CUDA(cudaGetLastError());
+  SFT_CUDA(exclusive_scan_i32_to_i64(row_len, off64, t->nv, st));
+  int64_t nnz = 0;
+  SFT_CUDA(cudaMemcpyAsync(&nnz, off64 + t->nv, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  SFT_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  SFT_CUDA(cudaStreamSynchronize(st));
+  if (herr) return fail(SFT_ERR_MESH, "target node belongs to more elements than supported");
+  if (nnz >= (int64_t)INT32_MAX) return fail(SFT_ERR_UNSUPPORTED, "mass matrix nnz exceeds 2^31");
+  t->nnz = nnz;
+  SFT_CUDA(dalloc(&t->row_ptr, (size_t)t->nv + 1, st));
+  SFT_CUDA(narrow_i64_to_i32(off64, t->row_ptr, t->nv + 1, st));
+  SFT_CUDA(dalloc(&t->col, (size_t)nnz, st));
+  SFT_CUDA(dalloc(&t->val, (size_t)nnz, st));
+  SFT_CUDA(dalloc(&t->dinv, (size_t)t->nv, st));
+  SFT_CUDA(dalloc(&t->lumped, (size_t)t->nv, st));
+  k_mass_rows<D, true><<<blocks_for(t->nv), 256, 0, st>>>(t->conn, t->vol, inc_start, inc, t->nv, nullptr, t->row_ptr,
+                                                          t->col, t->val, t->dinv, t->lumped, d_err);
+  SFT_CUDA(cudaGetLastError());
+  dfree(off64, st);
+  dfree(inc_start, st);
+  dfree(inc, st);
+  dfree(inc_count, st);
+  return SFT_OK;
+}
+
+sft_status build_target(sft_target_s* t, cudaStream_t st, int32_t* d_err) {
+  return t->dim == 2 ? build_target_t<2>(t, st, d_err) : build_target_t<3>(t, st, d_err);
+}
+
+sft_status target_coordsP(sft_target_s* t, int prec, cudaStream_t st) {
+  if (t->coordsP[prec]) return SFT_OK;
+  const size_t esz = prec == SFT_PREC_FP32 ? 4 : 8;
+  void* p = nullptr;
+  SFT_CUDA(cudaMallocAsync(&p, esz * (size_t)(t->nv * t->dim > 0 ? t->nv * t->dim : 1), st));
+  t->coordsP[prec] = p;
+  return convert_coords(t->coords, t->dtype, p, prec, t->nv * t->dim, st);
+}
+
+}  // namespace sft

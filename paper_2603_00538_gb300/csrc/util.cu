@@ -1,0 +1,96 @@
+// Device-wide exclusive scan (three phases: per-block scan, recursive scan of
+// the block totals, add-back) and small conversion kernels.
+#include "util.cuh"
+
+namespace sft {
+
+namespace {
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;                         // per thread
+constexpr int kScanTile = kScanThreads * kScanItems;  // per block
+
+template <typename TIn>
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const TIn* __restrict__ in, int64_t* __restrict__ out,
+                                                             int64_t n, int64_t* __restrict__ tile_sums) {
+  __shared__ int64_t warp_tot[kScanThreads / kWarp];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int64_t v[kScanItems];
+  int64_t run = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const int64_t idx = base + i;
+    v[i] = idx < n ? (int64_t)in[idx] : 0;
+    run += v[i];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t incl = warp_inclusive_scan<int64_t>(run, lane);
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t w = lane < kScanThreads / kWarp ? warp_tot[lane] : 0;
+    w = warp_inclusive_scan<int64_t>(w, lane);
+    if (lane < kScanThreads / kWarp) warp_tot[lane] = w;
+  }
+  __syncthreads();
+  int64_t pre = (warp > 0 ? warp_tot[warp - 1] : 0) + incl - run;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const int64_t idx = base + i;
+    if (idx < n) out[idx] = pre;
+    pre += v[i];
+  }
+  if (threadIdx.x == kScanThreads - 1) tile_sums[blockIdx.x] = warp_tot[kScanThreads / kWarp - 1];
+}
+
+__global__ void k_add_tile_offsets(int64_t* __restrict__ out, int64_t n, const int64_t* __restrict__ offs) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] += offs[i / kScanTile];
+}
+
+__global__ void k_narrow(const int64_t* __restrict__ in, int32_t* __restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (int32_t)in[i];
+}
+
+// exclusive scan of n values into out[0..n) plus total at out[n]
+template <typename TIn>
+cudaError_t scan_rec(const TIn* in, int64_t* out, int64_t n, cudaStream_t s) {
+  const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+  if (tiles == 0) return cudaMemsetAsync(out, 0, sizeof(int64_t), s);
+  int64_t* sums = nullptr;
+  cudaError_t e = cudaMallocAsync(&sums, sizeof(int64_t) * (tiles + 1), s);
+  if (e != cudaSuccess) return e;
+  k_scan_tiles<TIn><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, sums);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (tiles == 1) {
+    // out[n] = tile total; offsets are zero
+    e = cudaMemcpyAsync(out + n, sums, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+  } else {
+    int64_t* sums_scan = nullptr;
+    e = cudaMallocAsync(&sums_scan, sizeof(int64_t) * (tiles + 1), s);
+    if (e != cudaSuccess) return e;
+    e = scan_rec<int64_t>(sums, sums_scan, tiles, s);
+    if (e == cudaSuccess) {
+      k_add_tile_offsets<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, n, sums_scan);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out + n, sums_scan + tiles, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+    cudaFreeAsync(sums_scan, s);
+  }
+  cudaFreeAsync(sums, s);
+  return e;
+}
+}  // namespace
+
+cudaError_t exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s) {
+  return scan_rec<int32_t>(in, out, n, s);
+}
+
+cudaError_t narrow_i64_to_i32(const int64_t* in, int32_t* out, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_narrow<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace sft

@@ -1,0 +1,88 @@
+// Shared device utilities: warp/block reductions and scans, a grid-wide
+// barrier with a bounded wait (for cooperative launches), error-flag helpers.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "common.cuh"
+
+namespace sft {
+
+constexpr int kWarp = 32;
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void set_error(int32_t* err, int32_t code) {
+  if (err) atomicCAS(err, 0, code);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// inclusive warp scan
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_scan(T v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  return v;
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).
+// Sense by generation counter; the wait gives up after `timeout_ns`, sets
+// DEV_BARRIER_TIMEOUT in *err and returns false (callers then return).
+struct GridBarrier {
+  unsigned int count;
+  unsigned int gen;
+};
+
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned int nblocks, int32_t* err,
+                                          uint64_t timeout_ns = 2000000000ull) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned int* vgen = &bar->gen;
+    const unsigned int g = *vgen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&bar->count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      const uint64_t t0 = globaltimer_ns();
+      while (*vgen == g) {
+        if (*reinterpret_cast<volatile int32_t*>(err) != 0) { ok = 0; break; }
+        if (globaltimer_ns() - t0 > timeout_ns) {
+          set_error(err, DEV_BARRIER_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+}  // namespace sft
+
+// host-side helpers implemented in util.cu
+namespace sft {
+// exclusive scan of int32 counts [n] into int64 offsets [n+1] (out[n] = total)
+cudaError_t exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
+// narrow int64 -> int32 (caller checked the range)
+cudaError_t narrow_i64_to_i32(const int64_t* in, int32_t* out, int64_t n, cudaStream_t s);
+}  // namespace sft

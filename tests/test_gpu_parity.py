@@ -1,0 +1,290 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 oracle.
+
+Bar: integer results (grid cells, located elements, per-sample source
+elements, CSR pattern) bit-exact; FP64 paths within rounding; FP32 paths:
+b within 1e-5 relative (2-norm), the rest within the bounds derived in the
+design notes (FP32 evaluation error ~1e-7 relative, amplified at most by the
+mass matrix condition number)."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2603_00538_gb300 as sft  # noqa: E402
+
+DEV = torch.device("cuda:0")
+FP64, FP32 = sft.SFT_PREC_FP64, sft.SFT_PREC_FP32
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def _run(src, tgt, prec, N, seed=0, alpha=1.0, tol=1e-13, device=True, stream_id=0, L=1.0, maxit=2000):
+    s = sft.mesh_source(src, grid_scale_L=L, device=DEV if device else None)
+    t = sft.mesh_target(tgt, device=DEV if device else None)
+    nf = src.nfields
+    if device:
+        u = torch.zeros((nf, tgt.nnodes), dtype=torch.float64, device=DEV)
+        b, g = torch.zeros_like(u), torch.zeros_like(u)
+        se = torch.zeros((tgt.nelems, N), dtype=torch.int32, device=DEV)
+    else:
+        u = np.zeros((nf, tgt.nnodes))
+        b, g = np.zeros_like(u), np.zeros_like(u)
+        se = np.zeros((tgt.nelems, N), np.int32)
+    _, stats, _ = sft.sft_transfer(s, t, N, prec, seed=seed, stream_id=stream_id, alpha=alpha, cg_tol=tol,
+                                   cg_max_iter=maxit, u_out=u, b_out=b, g_out=g, sample_elem_out=se)
+    cv = lambda x: x.cpu().numpy() if device else x  # noqa: E731
+    return dict(u=cv(u), b=cv(b), g=cv(g), sample_elem=cv(se), stats=stats, s=s, t=t)
+
+
+# --------------------------------------------------------------------------
+# location and grid
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,prec", [(2, FP64), (2, FP32), (3, FP64), (3, FP32)])
+def test_grid_bit_exact(orc, dim, prec):
+    m = W.jittered_tri_mesh(23, 5) if dim == 2 else W.jittered_kuhn_mesh(7, 5)
+    m = W.with_values(m, [W.paper_f2], np.float32 if prec == FP32 else np.float64)
+    if prec == FP32:
+        m = W.as_precision(m, np.float32)
+    s = sft.mesh_source(m, device=DEV)
+    n, start, items = sft.sft_source_grid(s, prec)
+    g = orc.Grid(1 if prec == FP32 else 0, m.coords, m.conn)
+    n_o, nc_o, _ = g.shape()
+    start_o, items_o = g.csr()
+    assert list(n) == list(n_o)
+    assert np.array_equal(start, start_o)
+    assert np.array_equal(items, items_o)
+
+
+@pytest.mark.parametrize("dim,prec", [(2, FP64), (2, FP32), (3, FP64), (3, FP32)])
+def test_locate_bit_exact(orc, dim, prec):
+    m = W.jittered_tri_mesh(31, 6) if dim == 2 else W.jittered_kuhn_mesh(9, 6)
+    dt = np.float32 if prec == FP32 else np.float64
+    m = W.as_precision(W.with_values(m, [W.paper_f1, W.paper_f3], np.float64), dt)
+    rng = np.random.default_rng(3)
+    pts = np.concatenate([rng.random((20000, dim)), m.coords.astype(np.float64),
+                          m.coords[m.conn[:, :2]].astype(np.float64).mean(1),
+                          rng.random((500, dim)) * 1.2 - 0.1])  # some points outside the box
+    s = sft.mesh_source(m, device=DEV)
+    e_gpu, v_gpu = sft.sft_locate(s, pts, prec)
+    p_o = 1 if prec == FP32 else 0
+    e_o, st_o = orc.Grid(p_o, m.coords, m.conn).locate(pts)
+    assert np.array_equal(e_gpu, e_o)
+    # values: FP64 path to rounding; FP32 path to single-precision evaluation error
+    x = pts.astype(np.float32).astype(np.float64) if prec == FP32 else pts
+    ref = np.stack([orc.eval_p1(m.coords, m.conn, m.values, e, xi) for e, xi in zip(e_o[:3000], x[:3000])], 1)
+    tol = 2e-6 if prec == FP32 else 1e-13
+    assert np.max(np.abs(v_gpu[:, :3000] - ref)) <= tol * np.max(np.abs(ref))
+
+
+def test_locate_host_pointers_match_device(orc):
+    m = W.with_values(W.jittered_tri_mesh(12, 1), [W.paper_f3])
+    pts = np.random.default_rng(0).random((777, 2))
+    s_h = sft.mesh_source(m)                 # host inputs
+    s_d = sft.mesh_source(m, device=DEV)     # device inputs
+    e1, v1 = sft.sft_locate(s_h, pts, FP64)
+    e2, v2 = sft.sft_locate(s_d, pts, FP64)
+    assert np.array_equal(e1, e2) and np.array_equal(v1, v2)
+
+
+# --------------------------------------------------------------------------
+# mass matrix and solve
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dim", [2, 3])
+def test_mass_matrix_parity(orc, dim):
+    m = W.delaunay_tri_mesh(900, 12, 8) if dim == 2 else W.morton_reorder(W.jittered_kuhn_mesh(6, 8))
+    t = sft.mesh_target(m, device=DEV)
+    rp, col, val, lump = sft.sft_target_mass(t)
+    rp_o, col_o, val_o = orc.mass_csr(m.coords, m.conn)
+    assert np.array_equal(rp, rp_o) and np.array_equal(col, col_o)
+    assert np.max(np.abs(val - val_o)) <= 1e-15 * np.max(np.abs(val_o))
+    assert np.max(np.abs(lump - orc.lumped_mass(m.coords, m.conn))) <= 1e-15
+
+
+@pytest.mark.parametrize("dim,nrhs", [(2, 1), (2, 3), (3, 2)])
+def test_mass_solve_parity(orc, dim, nrhs):
+    """Given the same b, the FP64 CG solutions agree to 1e-10 (tol 1e-13)."""
+    m = W.delaunay_tri_mesh(3000, 20, 9) if dim == 2 else W.morton_reorder(W.jittered_kuhn_mesh(8, 9))
+    t = sft.mesh_target(m, device=DEV)
+    b = np.random.default_rng(4).standard_normal((nrhs, m.nnodes))
+    u, it, rr = sft.sft_mass_solve(t, b, tol=1e-13, max_iter=2000)
+    assert rr <= 1e-13
+    rp, col, val = orc.mass_csr(m.coords, m.conn)
+    for f in range(nrhs):
+        uo, _, _ = orc.pcg(rp, col, val, b[f], tol=1e-13, max_iter=2000)
+        assert _rel(u[f], uo) < 1e-10
+
+
+def test_mass_solve_not_converged_is_reported():
+    m = W.delaunay_tri_mesh(400, 8, 2)
+    t = sft.mesh_target(m, device=DEV)
+    b = np.random.default_rng(1).standard_normal((1, m.nnodes))
+    with pytest.raises(sft.SftError) as ei:
+        sft.sft_mass_solve(t, b, tol=1e-15, max_iter=2)
+    assert ei.value.status == 5
+
+
+# --------------------------------------------------------------------------
+# the transfer
+# --------------------------------------------------------------------------
+CASES = [
+    # name, scale, precision, N
+    ("tri2k", 1.0, FP64, 16),
+    ("tri2k", 1.0, FP32, 16),
+    ("tri4m", 3e-3, FP32, 64),
+    ("tri4m", 3e-3, FP64, 64),
+    ("tet5m", 2e-3, FP32, 32),
+    ("tet5m", 2e-3, FP64, 32),
+]
+
+
+@pytest.mark.parametrize("name,scale,prec,N", CASES)
+def test_transfer_parity(orc, name, scale, prec, N):
+    src, tgt, _ = W.config_meshes(name, scale)
+    r = _run(src, tgt, prec, N)
+    o = orc.transfer(src, tgt, 1 if prec == FP32 else 0, N, cg_tol=1e-13, cg_max_iter=2000,
+                     want_sample_elem=True)
+    assert np.array_equal(r["sample_elem"], o["sample_elem"])
+    assert r["stats"]["fallback_queries"] == o["fallback_queries"]
+    assert r["stats"]["empty_queries"] == o["empty_queries"] == 0
+    if prec == FP64:
+        assert _rel(r["g"], o["g"]) < 1e-13
+        assert _rel(r["b"], o["b"]) < 1e-13
+        assert _rel(r["u"], o["u"]) < 1e-10
+    else:
+        assert _rel(r["g"], o["g"]) < 2e-6
+        assert _rel(r["b"], o["b"]) < 1e-5
+        assert _rel(r["u"], o["u"]) < 1e-4
+
+
+@pytest.mark.parametrize("dim,N,nf,alpha", [
+    (2, 1, 1, 1.0), (2, 7, 1, 1.0), (2, 20, 1, 0.5), (2, 33, 1, 1.0), (2, 128, 2, 1.0),
+    (3, 1, 1, 1.0), (3, 5, 3, 0.0), (3, 40, 1, 1.0), (2, 16, 8, 1.0), (3, 8, 5, 0.7),
+])
+def test_transfer_edge_shapes(orc, dim, N, nf, alpha):
+    """Ragged unit counts, packed and long warp modes, odd N in 2D, several
+    fields (masked template widths), alpha = 0."""
+    fields = [W.paper_f1, W.paper_f2, W.paper_f3, W.field_sincos, W.linear_field([1, 2, 3, 4])][:nf]
+    fields = (fields * 2)[:nf]
+    if dim == 2:
+        src = W.with_values(W.jittered_tri_mesh(9, 11), fields)
+        tgt = W.delaunay_tri_mesh(53, 5, 12)
+    else:
+        src = W.with_values(W.jittered_kuhn_mesh(4, 11), [lambda x, f=f: f(x[:, :2]) + x[:, 2] for f in fields])
+        tgt = W.morton_reorder(W.jittered_kuhn_mesh(3, 12))
+    for prec in (FP64, FP32):
+        r = _run(src, tgt, prec, N, seed=5, alpha=alpha, stream_id=3)
+        o = orc.transfer(src, tgt, 1 if prec == FP32 else 0, N, seed=5, stream=3, alpha=alpha,
+                         cg_tol=1e-13, cg_max_iter=2000, want_sample_elem=True)
+        assert np.array_equal(r["sample_elem"], o["sample_elem"])
+        lim_b = 1e-13 if prec == FP64 else 1e-5
+        for f in range(nf):
+            assert _rel(r["b"][f], o["b"][f]) < lim_b
+            assert _rel(r["u"][f], o["u"][f]) < (1e-10 if prec == FP64 else 1e-4)
+
+
+def test_host_buffers_equal_device_buffers():
+    src, tgt, _ = W.config_meshes("tri2k")
+    a = _run(src, tgt, FP64, 16, device=True)
+    b = _run(src, tgt, FP64, 16, device=False)
+    assert np.array_equal(a["sample_elem"], b["sample_elem"])
+    assert _rel(a["u"], b["u"]) < 1e-13
+
+
+def test_seeds_and_streams_change_samples():
+    src, tgt, _ = W.config_meshes("tri2k")
+    a = _run(src, tgt, FP64, 16, seed=1)
+    b = _run(src, tgt, FP64, 16, seed=2)
+    c = _run(src, tgt, FP64, 16, seed=1, stream_id=9)
+    assert not np.array_equal(a["sample_elem"], b["sample_elem"])
+    assert not np.array_equal(a["sample_elem"], c["sample_elem"])
+
+
+def test_conservation_api(orc):
+    src, tgt, _ = W.config_meshes("tri2k")
+    r = _run(src, tgt, FP64, 16)
+    e, i_s, i_t = sft.sft_conservation_error(r["s"], r["t"], r["u"][0])
+    assert i_s == pytest.approx(orc.integral_p1(src.coords, src.conn, src.values[0]), rel=1e-13)
+    assert i_t == pytest.approx(orc.lumped_mass(tgt.coords, tgt.conn) @ r["u"][0], rel=1e-13)
+    assert i_t == pytest.approx(r["b"][0].sum(), rel=1e-11)
+    assert e == pytest.approx(abs(i_s - i_t) / abs(i_s), rel=1e-9)
+
+
+def test_empty_cells_and_strict_mode():
+    """An L-shaped source leaves grid cells empty; queries there return -1
+    and value 0, and strict mode reports SFT_ERR_OUTSIDE."""
+    m = W.jittered_tri_mesh(8, 0)
+    cen = m.coords[m.conn].mean(1)
+    keep = ~((cen[:, 0] > 0.5) & (cen[:, 1] > 0.5))
+    used = np.unique(m.conn[keep])
+    remap = -np.ones(m.nnodes, np.int64)
+    remap[used] = np.arange(used.size)
+    src = W.with_values(W.Mesh(m.coords[used], remap[m.conn[keep]].astype(np.int32)), [W.paper_f2])
+    s = sft.mesh_source(src, device=DEV)
+    e, v = sft.sft_locate(s, np.array([[0.9, 0.9], [0.1, 0.1]]), FP64)
+    assert e[0] == -1 and v[0, 0] == 0.0 and e[1] >= 0
+    tgt = W.delaunay_tri_mesh(50, 4, 3)
+    t = sft.mesh_target(tgt, device=DEV)
+    with pytest.raises(sft.SftError) as ei:
+        sft.sft_transfer(s, t, 8, FP64, strict_inside=True)
+    assert ei.value.status == 6
+
+
+def test_invalid_meshes_rejected():
+    m = W.with_values(W.jittered_tri_mesh(4, 0), [W.paper_f1])
+    bad = m.conn.copy()
+    bad[3, 1] = m.nnodes + 5
+    with pytest.raises(sft.SftError) as ei:
+        sft.sft_source_create(m.coords, bad, m.values)
+    assert ei.value.status == 2
+    flip = m.conn.copy()
+    flip[0, [1, 2]] = flip[0, [2, 1]]
+    with pytest.raises(sft.SftError) as ei:
+        sft.sft_target_create(m.coords, flip)
+    assert ei.value.status == 2
+    nanc = m.coords.copy()
+    nanc[2, 0] = np.nan
+    with pytest.raises(sft.SftError) as ei:
+        sft.sft_source_create(nanc, m.conn, m.values)
+    assert ei.value.status == 2
+
+
+# --------------------------------------------------------------------------
+# full size, in the benchmark's launch configuration: sampled outputs
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["tri4m", "tet5m"])
+def test_full_size_sampled(orc, name):
+    src, tgt, p = W.config_meshes(name)
+    N = p["samples_per_elem"]
+    r = _run(src, tgt, FP32, N, tol=p["cg_tol"])
+    # every sample lands in an element (the meshes cover the same domain)
+    assert r["stats"]["empty_queries"] == 0
+    assert (r["sample_elem"] >= 0).all()
+    # sampled target elements: samples and their source elements, one by one
+    rng = np.random.default_rng(0)
+    pick = np.sort(rng.choice(tgt.nelems, 400, replace=False))
+    grid = orc.Grid(1, src.coords, src.conn)
+    d = tgt.dim
+    for e in pick:
+        xyz = tgt.coords[tgt.conn[e]].astype(np.float64)
+        lam, X = orc.sample_element(1, d, 0, 0, int(e), N, xyz)
+        el, _ = grid.locate(X)
+        assert np.array_equal(el, r["sample_elem"][e])
+    # control values at sampled nodes
+    nodes = rng.choice(tgt.nnodes, 2000, replace=False)
+    X = tgt.coords[nodes].astype(np.float64)
+    el, _ = grid.locate(X)
+    gref = np.array([orc.eval_p1(src.coords, src.conn, src.values, e, x)[0] for e, x in zip(el, X)])
+    assert np.max(np.abs(r["g"][0][nodes] - gref)) <= 2e-6 * np.max(np.abs(gref))
+    # properties: partition of unity of the control term and convergence of M u = b
+    e_mass, i_s, i_t = sft.sft_conservation_error(r["s"], r["t"], r["u"][0])
+    assert i_t == pytest.approx(r["b"][0].sum(), rel=1e-8)
+    assert r["stats"]["cg_rel_resid"] <= p["cg_tol"]
+    assert e_mass < 1e-3
