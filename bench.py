@@ -86,7 +86,7 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+    """nvidia-smi samples (every 100 ms) while the timed region runs."""
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
@@ -100,7 +100,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_power_cap")
         try:
             self._proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
-                                           "--format=csv,noheader,nounits", "-lms", "200"],
+                                           "--format=csv,noheader,nounits", "-lms", "100"],
                                           stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             threading.Thread(target=self._read, daemon=True).start()
         except (OSError, FileNotFoundError):
@@ -144,8 +144,8 @@ def dist_init():
     return rank, world, local
 
 
-def make_workload(name: str):
-    src, tgt, p = W.config_meshes(name)
+def make_workload(name: str, scale: float = 1.0):
+    src, tgt, p = W.config_meshes(name, scale)
     return src, tgt, p
 
 
@@ -159,7 +159,7 @@ def run_ours(args):
     rank, world, local = dist_init()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    src, tgt, p = make_workload(args.workload)
+    src, tgt, p = make_workload(args.workload, args.scale)
     N, tol = p["samples_per_elem"], p["cg_tol"]
     dim = src.dim
     prec = sft.SFT_PREC_FP32
@@ -226,12 +226,13 @@ def run_ours(args):
         alg_bytes = BYTES_PER_QUERY[dim] * tgt.nelems * N + BYTES_PER_ELEM[dim] * tgt.nelems
         achieved = alg_bytes / (mean_asm / 1e3) / 1e9
         traffic = measured_traffic(args.workload)
-        cpu = cpu_baseline(args, src, tgt, p) if not args.skip_cpu else None
+        cpu = cpu_baseline(args, src, tgt, p, args.cpu_frac_baseline) if not args.skip_cpu else None
         line = {
             "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}",
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}"
+                                   + ("" if args.scale == 1.0 else f" (element counts x{args.scale})"),
                        "queries_per_step": queries, "target_elements": tgt.nelems, "samples_per_elem": N,
                        "source_elements": src.nelems, "l2": "flushed between steps (256 MB write)",
                        "accumulation": "FP64 load vector, CG and reductions",
@@ -257,20 +258,13 @@ def run_ours(args):
 
 
 def count_launches(step):
-    try:
-        import torch
-        from torch.profiler import ProfilerActivity, profile
-        with profile(activities=[ProfilerActivity.CUDA]) as prof:
-            step()
-            torch.cuda.synchronize()
-        n = 0
-        for evt in prof.events():
-            name = evt.name or ""
-            if "sft" in name and ("k_" in name or "sft::" in name):
-                n += 1
-        return n or None
-    except Exception:
-        return None
+    """Kernels libsft launches in one step (its own launch counter)."""
+    import torch
+    import paper_2603_00538_gb300 as sft
+    n0 = sft.sft_kernel_launches()
+    step()
+    torch.cuda.synchronize()
+    return sft.sft_kernel_launches() - n0
 
 
 def run_e2e(args, src, tgt, N, tol, prec):
@@ -353,8 +347,7 @@ def oracle_step(src, tgt_s, p):
     return (tgt_s.nelems * p["samples_per_elem"] + tgt_s.nnodes) / dt, dt, r
 
 
-def cpu_baseline(args, src, tgt, p):
-    frac = args.cpu_frac
+def cpu_baseline(args, src, tgt, p, frac):
     tgt_s = _sample_target(tgt, frac)
     v, dt, _ = oracle_step(src, tgt_s, p)
     return {"value": v, "unit": "queries/s", "cores": 1, "kind": "oracle",
@@ -367,7 +360,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    src, tgt, p = make_workload(args.workload)
+    src, tgt, p = make_workload(args.workload, args.scale)
     tgt_s = _sample_target(tgt, args.cpu_frac)
     for _ in range(args.warmup):
         oracle_step(src, tgt_s, p)
@@ -394,12 +387,17 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="tri4m")
-    ap.add_argument("--cpu-frac", type=float, default=0.05)
+    ap.add_argument("--cpu-frac", type=float, default=0.05,
+                    help="fraction of the target elements per reference-arm step")
+    ap.add_argument("--cpu-frac-baseline", type=float, default=0.4,
+                    help="fraction of the target elements in the cpu_baseline sample")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="element-count scale of the workload (1 = the named workload)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -161,7 +161,11 @@ sft_status sft_target_mass(sft_target tgt, int64_t* nnz_out, int64_t* row_ptr_ou
                            int32_t* col_out, double* val_out, double* lumped_out);
 
 const char* sft_status_str(sft_status s);
+/* Message of the last error on the calling thread (empty if none). */
 const char* sft_last_error(void);
+/* Number of CUDA kernels this library has launched in this process
+ * (diagnostics; monotone, thread-safe). */
+int64_t sft_kernel_launches(void);
 
 #ifdef __cplusplus
 }

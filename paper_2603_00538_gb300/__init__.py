@@ -73,6 +73,7 @@ _SIGS = {
     "sft_target_mass": ([_vp, _vp, _vp, _vp, _vp, _vp], _i32),
     "sft_status_str": ([_i32], ctypes.c_char_p),
     "sft_last_error": ([], ctypes.c_char_p),
+    "sft_kernel_launches": ([], _i64),
 }
 EXPORTS = tuple(_SIGS)
 _lib = None
@@ -317,6 +318,11 @@ def sft_target_mass(tgt: Target):
     _check(lib().sft_target_mass(tgt.h, None, rp.ctypes.data, col.ctypes.data, val.ctypes.data,
                                  lump.ctypes.data), "sft_target_mass")
     return rp, col, val, lump
+
+
+def sft_kernel_launches() -> int:
+    """Kernels launched by libsft in this process so far."""
+    return int(lib().sft_kernel_launches())
 
 
 def _nf(src: Source) -> int:

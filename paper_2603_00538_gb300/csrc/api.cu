@@ -3,6 +3,7 @@
 // host staging of host-memory outputs, timing events and status mapping.
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -12,6 +13,9 @@
 namespace sft {
 
 static thread_local std::string g_last_error;
+static std::atomic<int64_t> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 
@@ -137,6 +141,8 @@ const char* sft_status_str(sft_status s) {
 
 const char* sft_last_error(void) { return g_last_error.c_str(); }
 
+int64_t sft_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
 void sft_source_destroy(sft_source s) {
   if (!s) return;
   cudaStream_t st = s->stream;
@@ -150,7 +156,7 @@ void sft_source_destroy(sft_source s) {
 void sft_target_destroy(sft_target t) {
   if (!t) return;
   cudaStream_t st = t->stream;
-  void* bufs[] = {t->coords, t->conn, t->coordsP[0], t->coordsP[1], t->vol, t->row_ptr, t->col, t->val, t->dinv, t->lumped};
+  void* bufs[] = {t->coords, t->conn, t->coordsP[0], t->coordsP[1], t->vol, t->vol32, t->row_ptr, t->col, t->val, t->dinv, t->lumped};
   for (void* p : bufs)
     if (p) cudaFreeAsync(p, st);
   delete t;

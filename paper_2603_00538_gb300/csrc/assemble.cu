@@ -50,11 +50,34 @@ struct AsmParams {
   PhiloxKey key;
   uint32_t stream_id;
   double alpha;
+  double c_det;   // alpha / ((d+1)(d+2)): exact P1 mass factor of the control term
+  double inv_n;   // 1 / N
+};
+
+// Per-element epilogue: b_i += |T| c_det (sum_m g_m + g_i) + |T|/N P_i.
+// On this GPU the FP64 pipe retires one warp instruction per 16 cycles, and
+// the epilogue runs on one lane per element, so the FP32 path keeps it in
+// FP32 (error ~1e-7 relative, below the FP32 evaluation error of g) and only
+// converts the final value for the FP64 atomic.
+template <typename P> struct Epi;
+template <> struct Epi<float> {
+  static __device__ __forceinline__ double contrib(float volf, double, float cdet, float cmc, float gsum,
+                                                   float gi, const Acc<float>& a) {
+    const float mc = __fadd_rn(a.s, a.e);
+    return (double)__fmaf_rn(__fmul_rn(volf, cdet), __fadd_rn(gsum, gi), __fmul_rn(__fmul_rn(volf, cmc), mc));
+  }
+};
+template <> struct Epi<double> {
+  static __device__ __forceinline__ double contrib(float, double vol, double cdet, double cmc, double gsum,
+                                                   double gi, const Acc<double>& a) {
+    return vol * cdet * (gsum + gi) + vol * cmc * a.value();
+  }
 };
 
 template <int D, typename P, int NF, bool DBG>
 __global__ void __launch_bounds__(256) k_assemble(const P* __restrict__ tx, const int32_t* __restrict__ tconn,
-                                                  const double* __restrict__ vol, const P* __restrict__ g,
+                                                  const double* __restrict__ vol, const float* __restrict__ vol32,
+                                                  const P* __restrict__ g,
                                                   const GridP<P>* __restrict__ gp,
                                                   const int32_t* __restrict__ cell_start,
                                                   const int32_t* __restrict__ cell_items,
@@ -159,20 +182,18 @@ __global__ void __launch_bounds__(256) k_assemble(const P* __restrict__ tx, cons
     }
 
     if (active && lane == seg_lo) {
-      const double w = __ldg(vol + t);
-      const double cdet = p.alpha * w / (double)((D + 1) * (D + 2));
-      const double cmc = w / (double)p.N;
+      const double w = sizeof(P) == 8 ? __ldg(vol + t) : 0.0;
+      const float wf = sizeof(P) == 4 ? __ldg(vol32 + t) : 0.f;
+      const P cdet = (P)p.c_det, cmc = (P)p.inv_n;
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         if (f >= p.nf) break;
-        double gsum = 0.0;
+        P gsum = gl[f][0];
 #pragma unroll
-        for (int m = 0; m < K; ++m) gsum += (double)gl[f][m];
+        for (int m = 1; m < K; ++m) gsum = A::add(gsum, gl[f][m]);
 #pragma unroll
-        for (int i = 0; i < K; ++i) {
-          const double contrib = cdet * (gsum + (double)gl[f][i]) + cmc * acc[f][i].value();
-          atomicAdd(b + (int64_t)f * p.nv + v[i], contrib);
-        }
+        for (int i = 0; i < K; ++i)
+          atomicAdd(b + (int64_t)f * p.nv + v[i], Epi<P>::contrib(wf, w, cdet, cmc, gsum, gl[f][i], acc[f][i]));
       }
     }
   }
@@ -192,7 +213,7 @@ static void launch_t(sft_source_s* s, sft_target_s* t, const AssembleArgs& a, co
   if (blocks > (1 << 20)) blocks = 1 << 20;
   if (blocks < 1) blocks = 1;
   auto args = [&](auto kern) {
-    kern<<<(unsigned)blocks, threads, 0, st>>>((const P*)t->coordsP[a.prec], t->conn, t->vol, (const P*)a.g,
+    ::sft::note_launch(), kern<<<(unsigned)blocks, threads, 0, st>>>((const P*)t->coordsP[a.prec], t->conn, t->vol, t->vol32, (const P*)a.g,
                                                (const GridP<P>*)L.grid, L.cell_start, L.cell_items,
                                                (const P*)L.recs, (const P*)L.vals, p, a.b, a.sample_elem,
                                                a.counters);
@@ -225,6 +246,8 @@ sft_status launch_assembly(sft_source_s* s, sft_target_s* t, const AssembleArgs&
   p.key.k1 = (uint32_t)(a.seed >> 32);
   p.stream_id = a.stream_id;
   p.alpha = a.alpha;
+  p.c_det = a.alpha / (double)((t->dim + 1) * (t->dim + 2));
+  p.inv_n = 1.0 / (double)a.N;
   if (t->dim == 2) {
     if (a.prec == SFT_PREC_FP32) launch_nf<2, float>(s, t, a, p, st);
     else launch_nf<2, double>(s, t, a, p, st);

@@ -32,12 +32,18 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, PhiloxKey k) {
 }
 
 // Uniform(0,1) from one 32-bit word, exact in the target precision:
-// FP32 odd multiples of 2^-24, FP64 (x + 1/2) 2^-32.
+// FP32 odd multiples of 2^-24, u = ((x >> 8) | 1) 2^-24; FP64 (x + 1/2) 2^-32.
+// Formed from the bit pattern (1 + m 2^-23 has mantissa m) with exact
+// subtract/add, so no int->float conversion instruction is issued: on this
+// GPU conversions share the narrow FP64 pipe. Value-identical to the
+// definition above.
 __device__ __forceinline__ float u01f(uint32_t x) {
-  return __fmul_rn(__uint2float_rn((x >> 8) | 1u), 0x1p-24f);
+  const float one_m = __uint_as_float(0x3F800000u | (x >> 9));  // 1 + (x>>9) 2^-23
+  return __fadd_rn(__fsub_rn(one_m, 1.0f), 0x1p-24f);           // (2 (x>>9) + 1) 2^-24
 }
 __device__ __forceinline__ double u01d(uint32_t x) {
-  return __dmul_rn(__dadd_rn(__uint2double_rn(x), 0.5), 0x1p-32);
+  const double one_m = __longlong_as_double((long long)(0x3FF0000000000000ull | ((uint64_t)x << 20)));
+  return __dadd_rn(__dsub_rn(one_m, 1.0), 0x1p-33);              // (2x + 1) 2^-33
 }
 
 // ---------------------------------------------------------------------------
@@ -120,13 +126,31 @@ template <typename P> struct GridP {
   int32_t n[3];
 };
 
+// cell_axis(x) = clamp(floor((x - lo) * inv), 0, n - 1). The floor is taken
+// without a conversion instruction: for 0 <= s <= 2^22 (2^51 in FP64),
+// s + 2^23 (2^52) rounded toward zero is 2^23 + floor(s), whose bit pattern
+// minus that of 2^23 is floor(s). NaN and negative s clamp to 0 (fmax
+// returns the non-NaN operand), large s to n - 1 (n < 2^22 is checked on
+// the host). Same result as floor + clamp.
 template <typename P>
-__device__ __forceinline__ int32_t cell_axis(P x, P lo, P inv, int32_t n) {
-  using A = Ar<P>;
-  const P f = A::floor(A::mul(A::sub(x, lo), inv));
-  if (!(f >= P(0))) return 0;
-  if (f > P(n - 1)) return n - 1;
-  return (int32_t)f;
+__device__ __forceinline__ int32_t cell_axis(P x, P lo, P inv, int32_t n);
+
+template <>
+__device__ __forceinline__ int32_t cell_axis<float>(float x, float lo, float inv, int32_t n) {
+  float s = __fmul_rn(__fsub_rn(x, lo), inv);
+  s = fminf(fmaxf(s, 0.0f), 4194304.0f);
+  const float t = __fadd_rz(s, 8388608.0f);
+  const int32_t c = (int32_t)(__float_as_uint(t) - 0x4B000000u);
+  return c < n - 1 ? c : n - 1;
+}
+
+template <>
+__device__ __forceinline__ int32_t cell_axis<double>(double x, double lo, double inv, int32_t n) {
+  double s = __dmul_rn(__dsub_rn(x, lo), inv);
+  s = fmin(fmax(s, 0.0), 2251799813685248.0);
+  const double t = __dadd_rz(s, 4503599627370496.0);
+  const int64_t c = (int64_t)((uint64_t)__double_as_longlong(t) - 0x4330000000000000ull);
+  return c < (int64_t)(n - 1) ? (int32_t)c : n - 1;
 }
 
 template <int D, typename P>

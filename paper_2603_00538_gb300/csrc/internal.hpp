@@ -71,6 +71,7 @@ struct sft_target_s {
   int32_t* conn = nullptr;      // [ne][dim+1]
   void* coordsP[2] = {nullptr, nullptr};  // per precision copy (lazy)
   double* vol = nullptr;        // [ne] FP64 measures
+  float* vol32 = nullptr;       // [ne] FP32 copy (the FP32 assembly epilogue)
   // mass matrix, CSR FP64
   int64_t nnz = 0;
   int32_t* row_ptr = nullptr;   // [nv+1]

@@ -39,13 +39,13 @@ sft_status convert_coords(const void* in, int in_dtype, void* out, int out_prec,
   if (n <= 0) return SFT_OK;
   const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 65535 * 8);
   if (in_dtype == SFT_F64 && out_prec == SFT_PREC_FP32)
-    k_convert<double, float><<<blocks, 256, 0, st>>>((const double*)in, (float*)out, n);
+    ::sft::note_launch(), k_convert<double, float><<<blocks, 256, 0, st>>>((const double*)in, (float*)out, n);
   else if (in_dtype == SFT_F64)
-    k_convert<double, double><<<blocks, 256, 0, st>>>((const double*)in, (double*)out, n);
+    ::sft::note_launch(), k_convert<double, double><<<blocks, 256, 0, st>>>((const double*)in, (double*)out, n);
   else if (out_prec == SFT_PREC_FP32)
-    k_convert<float, float><<<blocks, 256, 0, st>>>((const float*)in, (float*)out, n);
+    ::sft::note_launch(), k_convert<float, float><<<blocks, 256, 0, st>>>((const float*)in, (float*)out, n);
   else
-    k_convert<float, double><<<blocks, 256, 0, st>>>((const float*)in, (double*)out, n);
+    ::sft::note_launch(), k_convert<float, double><<<blocks, 256, 0, st>>>((const float*)in, (double*)out, n);
   SFT_CUDA(cudaGetLastError());
   return SFT_OK;
 }
@@ -238,10 +238,33 @@ __global__ void k_register(const P* __restrict__ x, const int32_t* __restrict__ 
   }
 }
 
-// ascending element order inside each cell (insertion sort; cells are short)
+// ascending element order inside each cell. Cells of up to 16 entries (the
+// common case) are sorted in registers by an odd-even transposition network
+// (static indices only); longer cells by an insertion sort in memory.
 __global__ void k_sort_cells(const int32_t* __restrict__ cell_start, int32_t* __restrict__ items, int64_t ncells) {
+  constexpr int R = 16;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x) {
     const int32_t p0 = cell_start[c], p1 = cell_start[c + 1];
+    const int32_t len = p1 - p0;
+    if (len <= 1) continue;
+    if (len <= R) {
+      int32_t k[R];
+#pragma unroll
+      for (int i = 0; i < R; ++i) k[i] = i < len ? items[p0 + i] : INT32_MAX;
+#pragma unroll
+      for (int phase = 0; phase < R; ++phase) {
+#pragma unroll
+        for (int i = phase & 1; i + 1 < R; i += 2) {
+          const int32_t a = min(k[i], k[i + 1]), b = max(k[i], k[i + 1]);
+          k[i] = a;
+          k[i + 1] = b;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < R; ++i)
+        if (i < len) items[p0 + i] = k[i];
+      continue;
+    }
     for (int32_t i = p0 + 1; i < p1; ++i) {
       const int32_t key = items[i];
       int32_t j = i - 1;
@@ -272,17 +295,18 @@ static sft_status build_locator_t(sft_source_s* s, int prec, cudaStream_t st, in
   if (sft_status r = convert_coords(s->coords, s->dtype, xP, prec, s->nv * D, st)) return r;
   // grid box and parameters
   const int32_t n = cells_per_axis(D, s->ne, s->L);
+  if (n >= (1 << 22)) return fail(SFT_ERR_UNSUPPORTED, "grid too fine (cells per axis >= 2^22)");
   L.n[0] = L.n[1] = L.n[2] = 1;
   L.ncells = 1;
   for (int a = 0; a < D; ++a) { L.n[a] = n; L.ncells *= n; }
   const unsigned nb = 256;
   P* part = nullptr;
   SFT_CUDA(dalloc(&part, (size_t)nb * 2 * D, st));
-  k_bbox_partial<D, P><<<nb, 256, 0, st>>>(xP, s->nv, part);
+  ::sft::note_launch(), k_bbox_partial<D, P><<<nb, 256, 0, st>>>(xP, s->nv, part);
   GridP<P>* g = nullptr;
   SFT_CUDA(dalloc(&g, 1, st));
   L.grid = g;
-  k_grid_params<D, P><<<1, 32, 0, st>>>(part, nb, n, g, d_err);
+  ::sft::note_launch(), k_grid_params<D, P><<<1, 32, 0, st>>>(part, nb, n, g, d_err);
   SFT_CUDA(cudaGetLastError());
   dfree(part, st);
   // records, value copies, per-element registration counts
@@ -295,10 +319,10 @@ static sft_status build_locator_t(sft_source_s* s, int prec, cudaStream_t st, in
   L.recs = recs;
   L.vals = vals;
   if (s->dtype == SFT_F64)
-    k_records<D, P, double><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, (const double*)s->values, s->nv, s->ne,
+    ::sft::note_launch(), k_records<D, P, double><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, (const double*)s->values, s->nv, s->ne,
                                                              s->nf, g, recs, vals, counts, d_err);
   else
-    k_records<D, P, float><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, (const float*)s->values, s->nv, s->ne,
+    ::sft::note_launch(), k_records<D, P, float><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, (const float*)s->values, s->nv, s->ne,
                                                             s->nf, g, recs, vals, counts, d_err);
   SFT_CUDA(cudaGetLastError());
   int32_t herr = 0;
@@ -325,14 +349,14 @@ static sft_status build_locator_t(sft_source_s* s, int prec, cudaStream_t st, in
   SFT_CUDA(dalloc(&L.cell_start, (size_t)L.ncells + 1, st));
   SFT_CUDA(dalloc(&L.cell_items, (size_t)total, st));
   SFT_CUDA(cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * L.ncells, st));
-  k_register<D, P, false><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, s->ne, g, cell_count, nullptr, nullptr);
+  ::sft::note_launch(), k_register<D, P, false><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, s->ne, g, cell_count, nullptr, nullptr);
   SFT_CUDA(cudaGetLastError());
   SFT_CUDA(exclusive_scan_i32_to_i64(cell_count, start64, L.ncells, st));
   SFT_CUDA(narrow_i64_to_i32(start64, L.cell_start, L.ncells + 1, st));
   SFT_CUDA(cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * L.ncells, st));
-  k_register<D, P, true><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, s->ne, g, cell_count, L.cell_start, L.cell_items);
+  ::sft::note_launch(), k_register<D, P, true><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, s->ne, g, cell_count, L.cell_start, L.cell_items);
   SFT_CUDA(cudaGetLastError());
-  k_sort_cells<<<grid_for(L.ncells), 256, 0, st>>>(L.cell_start, L.cell_items, L.ncells);
+  ::sft::note_launch(), k_sort_cells<<<grid_for(L.ncells), 256, 0, st>>>(L.cell_start, L.cell_items, L.ncells);
   SFT_CUDA(cudaGetLastError());
   dfree(cell_count, st);
   dfree(start64, st);
@@ -397,7 +421,7 @@ static void launch_locate(sft_source_s* s, const Locator& L, int64_t n, const vo
   const P* recs = (const P*)L.recs;
   const P* vals = (const P*)L.vals;
 #define SFT_LOC(TIN, TOUT)                                                                                      \
-  k_locate_points<D, P, TIN, TOUT><<<blocks, 256, 0, st>>>((const TIN*)pts, n, g, L.cell_start, L.cell_items, \
+  ::sft::note_launch(), k_locate_points<D, P, TIN, TOUT><<<blocks, 256, 0, st>>>((const TIN*)pts, n, g, L.cell_start, L.cell_items, \
                                                            recs, vals, s->ne, s->nf, elem_out, (TOUT*)val_out,  \
                                                            val_stride, counters)
   if (pts_are_double) {
@@ -480,11 +504,11 @@ sft_status source_integrals(sft_source_s* s, cudaStream_t st) {
   double* part = nullptr;
   SFT_CUDA(dalloc(&part, (size_t)nb * kMaxFields, st));
   if (s->dim == 2) {
-    if (s->dtype == SFT_F64) k_p1_integral_partial<2, double><<<nb, 256, 0, st>>>((const double*)s->coords, s->conn, (const double*)s->values, s->nv, s->ne, s->nf, part);
-    else k_p1_integral_partial<2, float><<<nb, 256, 0, st>>>((const float*)s->coords, s->conn, (const float*)s->values, s->nv, s->ne, s->nf, part);
+    if (s->dtype == SFT_F64) ::sft::note_launch(), k_p1_integral_partial<2, double><<<nb, 256, 0, st>>>((const double*)s->coords, s->conn, (const double*)s->values, s->nv, s->ne, s->nf, part);
+    else ::sft::note_launch(), k_p1_integral_partial<2, float><<<nb, 256, 0, st>>>((const float*)s->coords, s->conn, (const float*)s->values, s->nv, s->ne, s->nf, part);
   } else {
-    if (s->dtype == SFT_F64) k_p1_integral_partial<3, double><<<nb, 256, 0, st>>>((const double*)s->coords, s->conn, (const double*)s->values, s->nv, s->ne, s->nf, part);
-    else k_p1_integral_partial<3, float><<<nb, 256, 0, st>>>((const float*)s->coords, s->conn, (const float*)s->values, s->nv, s->ne, s->nf, part);
+    if (s->dtype == SFT_F64) ::sft::note_launch(), k_p1_integral_partial<3, double><<<nb, 256, 0, st>>>((const double*)s->coords, s->conn, (const double*)s->values, s->nv, s->ne, s->nf, part);
+    else ::sft::note_launch(), k_p1_integral_partial<3, float><<<nb, 256, 0, st>>>((const float*)s->coords, s->conn, (const float*)s->values, s->nv, s->ne, s->nf, part);
   }
   SFT_CUDA(cudaGetLastError());
   std::vector<double> h((size_t)nb * kMaxFields);

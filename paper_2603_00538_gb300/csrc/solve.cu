@@ -5,10 +5,12 @@
 //
 // One cooperative (co-resident) kernel runs the whole iteration: no host round
 // trip per step. Each iteration has two grid barriers:
-//   A: p_new = z + beta p_old (own rows) and q = M p_new, with the neighbours'
-//      p_new recomputed on the fly from z and p_old (double-buffered p), and
-//      the partial dot p_new.q;
-//   B: u += a p_new, r -= a q, z = D^-1 r, partial dots r.r and r.z.
+//   A: w = M z (SpMV), then for the own row p = z + beta p and
+//      q = w + beta q (= M p by linearity, one FP64 FMA per nonzero instead of
+//      two), and the partial dot p.q;
+//   B: u += a p, r -= a q, z = D^-1 r, partial dots r.r and r.z.
+// FP64 throughput is the scarce resource on this GPU, so the iteration is
+// written to minimise FP64 operations per row.
 // Dot products are reduced deterministically: per-block partials, then every
 // block sums all partials in the same fixed order, so all blocks take the
 // same convergence decision. The barrier wait is bounded (error flag on
@@ -68,8 +70,8 @@ template <int TPR>
 __global__ void __launch_bounds__(kSolveThreads) k_pcg(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
                                                        const double* __restrict__ val, const double* __restrict__ dinv,
                                                        int64_t n, int nrhs, const double* __restrict__ b,
-                                                       double* __restrict__ x, double* r, double* z, double* pA,
-                                                       double* pB, double* q, double* part, PcgCtl* ctl, double tol,
+                                                       double* __restrict__ x, double* r, double* z, double* p,
+                                                       double* q, double* part, PcgCtl* ctl, double tol,
                                                        int max_iter) {
   __shared__ double tot[kMaxFields * 2];
   __shared__ double bnorm[kMaxFields], rz[kMaxFields], beta[kMaxFields], alpha[kMaxFields];
@@ -89,7 +91,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_pcg(const int32_t* __restrict
       x[k] = 0.0;
       r[k] = bi;
       z[k] = di * bi;
-      pA[k] = 0.0;
+      p[k] = 0.0;
+      q[k] = 0.0;
       v[f][0] += bi * bi;
       v[f][1] += bi * di * bi;
     }
@@ -108,8 +111,6 @@ __global__ void __launch_bounds__(kSolveThreads) k_pcg(const int32_t* __restrict
   __syncthreads();
 
   int it = 0;
-  double* pold = pA;
-  double* pnew = pB;
   constexpr int kRowsPerWarp = 32 / TPR;
   const int lane = threadIdx.x & 31;
   const int lane_in_row = lane % TPR;
@@ -130,21 +131,21 @@ __global__ void __launch_bounds__(kSolveThreads) k_pcg(const int32_t* __restrict
       }
       for (int f = 0; f < nrhs; ++f) {
         if (conv[f]) continue;
-        const double bt = beta[f];
         const double* zf = z + (int64_t)f * n;
-        const double* pf = pold + (int64_t)f * n;
         double s = 0.0;
-        for (int32_t k = q0 + lane_in_row; k < q1; k += TPR) {
-          const int32_t j = __ldg(col + k);
-          s += __ldg(val + k) * (__ldcg(zf + j) + bt * __ldcg(pf + j));
-        }
+        for (int32_t k = q0 + lane_in_row; k < q1; k += TPR) s += __ldg(val + k) * __ldcg(zf + __ldg(col + k));
+        if constexpr (TPR > 1) {
 #pragma unroll
-        for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, TPR);
+          for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, TPR);
+        }
         if (valid && lane_in_row == 0) {
-          const double pn = __ldcg(zf + row) + bt * __ldcg(pf + row);
-          pnew[(int64_t)f * n + row] = pn;
-          q[(int64_t)f * n + row] = s;
-          v[f][0] += pn * s;
+          const double bt = beta[f];
+          const int64_t k = (int64_t)f * n + row;
+          const double pn = __ldcg(zf + row) + bt * __ldcg(p + k);
+          const double qn = s + bt * __ldcg(q + k);
+          p[k] = pn;
+          q[k] = qn;
+          v[f][0] += pn * qn;
         }
       }
     }
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_pcg(const int32_t* __restrict
         if (conv[f]) continue;
         const int64_t k = (int64_t)f * n + i;
         const double a = alpha[f];
-        x[k] = __ldcg(x + k) + a * __ldcg(pnew + k);
+        x[k] = __ldcg(x + k) + a * __ldcg(p + k);
         const double ri = __ldcg(r + k) - a * __ldcg(q + k);
         r[k] = ri;
         const double zi = di * ri;
@@ -187,9 +188,6 @@ __global__ void __launch_bounds__(kSolveThreads) k_pcg(const int32_t* __restrict
       }
     }
     __syncthreads();
-    double* tmp = pold;
-    pold = pnew;
-    pnew = tmp;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (int f = 0; f < nrhs; ++f) {
@@ -218,22 +216,22 @@ sft_status mass_solve(sft_target_s* t, int nrhs, const double* b, double* x, dou
   SFT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   SFT_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
   if (!coop) return fail(SFT_ERR_UNSUPPORTED, "device lacks cooperative launch");
-  const bool wide = t->dim == 3;
+  // one thread per row: the FP64 pipe (1 warp instruction / 16 cycles / SM
+  // here) is the limiter, and a row-per-thread SpMV issues one DFMA warp
+  // instruction per nonzero for 32 rows, with no shuffle reductions
   int per_sm = 0;
-  if (wide) SFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<16>, kSolveThreads, 0));
-  else SFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<8>, kSolveThreads, 0));
+  SFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<1>, kSolveThreads, 0));
   if (per_sm < 1) return fail(SFT_ERR_CUDA, "solver kernel cannot be resident");
   per_sm = std::min(per_sm, 4);
-  const int64_t want = (n * (wide ? 16 : 8) + kSolveThreads - 1) / kSolveThreads;
+  const int64_t want = (n + kSolveThreads - 1) / kSolveThreads;
   const unsigned nblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, want));
 
-  double *r = nullptr, *z = nullptr, *pA = nullptr, *pB = nullptr, *q = nullptr, *part = nullptr;
+  double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *part = nullptr;
   PcgCtl* ctl = nullptr;
   const size_t vec = (size_t)n * nrhs;
   SFT_CUDA(dalloc(&r, vec, st));
   SFT_CUDA(dalloc(&z, vec, st));
-  SFT_CUDA(dalloc(&pA, vec, st));
-  SFT_CUDA(dalloc(&pB, vec, st));
+  SFT_CUDA(dalloc(&p, vec, st));
   SFT_CUDA(dalloc(&q, vec, st));
   SFT_CUDA(dalloc(&part, (size_t)nblocks * nrhs * 2, st));
   SFT_CUDA(dalloc(&ctl, 1, st));
@@ -243,16 +241,15 @@ sft_status mass_solve(sft_target_s* t, int nrhs, const double* b, double* x, dou
   const double* val = t->val;
   const double* dinv = t->dinv;
   void* args[] = {(void*)&rp, (void*)&col, (void*)&val, (void*)&dinv, (void*)&n, (void*)&nrhs, (void*)&b,
-                  (void*)&x, (void*)&r, (void*)&z, (void*)&pA, (void*)&pB, (void*)&q, (void*)&part,
+                  (void*)&x, (void*)&r, (void*)&z, (void*)&p, (void*)&q, (void*)&part,
                   (void*)&ctl, (void*)&tol, (void*)&max_iter};
   cudaError_t le;
-  if (wide) le = cudaLaunchCooperativeKernel((const void*)k_pcg<16>, nblocks, kSolveThreads, args, 0, st);
-  else le = cudaLaunchCooperativeKernel((const void*)k_pcg<8>, nblocks, kSolveThreads, args, 0, st);
+  le = (::sft::note_launch(), cudaLaunchCooperativeKernel((const void*)k_pcg<1>, nblocks, kSolveThreads, args, 0, st));
   if (le != cudaSuccess) return cuda_fail(le, "cudaLaunchCooperativeKernel(k_pcg)");
   PcgCtl h;
   SFT_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
   SFT_CUDA(cudaStreamSynchronize(st));
-  dfree(r, st); dfree(z, st); dfree(pA, st); dfree(pB, st); dfree(q, st); dfree(part, st); dfree(ctl, st);
+  dfree(r, st); dfree(z, st); dfree(p, st); dfree(q, st); dfree(part, st); dfree(ctl, st);
   if (h.err != 0) return fail(SFT_ERR_DEVICE_STATUS, "CG kernel: grid barrier wait expired");
   for (int f = 0; f < nrhs; ++f) {
     res->iters = std::max(res->iters, (int)h.iters[f]);
@@ -283,7 +280,7 @@ sft_status weighted_sum(const double* w, const double* u, int64_t n, double* out
   const unsigned nb = 304;
   double* part = nullptr;
   SFT_CUDA(dalloc(&part, nb, st));
-  k_wsum_partial<<<nb, 256, 0, st>>>(w, u, n, part);
+  ::sft::note_launch(), k_wsum_partial<<<nb, 256, 0, st>>>(w, u, n, part);
   SFT_CUDA(cudaGetLastError());
   std::vector<double> h(nb);
   SFT_CUDA(cudaMemcpyAsync(h.data(), part, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));

@@ -17,7 +17,8 @@ constexpr int kMaxRow = 64;  // distinct neighbours (incl. self) per node
 
 template <int D, typename TI>
 __global__ void k_volumes(const TI* __restrict__ x, const int32_t* __restrict__ conn, int64_t nv, int64_t ne,
-                          double* __restrict__ vol, int32_t* __restrict__ inc_count, int32_t* err) {
+                          double* __restrict__ vol, float* __restrict__ vol32, int32_t* __restrict__ inc_count,
+                          int32_t* err) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
     int32_t v[D + 1];
     bool ok = true;
@@ -29,6 +30,7 @@ __global__ void k_volumes(const TI* __restrict__ x, const int32_t* __restrict__ 
     if (!ok) {
       set_error(err, DEV_BAD_INDEX);
       vol[e] = 0.0;
+      vol32[e] = 0.f;
       continue;
     }
     double xv[D + 1][D];
@@ -48,6 +50,7 @@ __global__ void k_volumes(const TI* __restrict__ x, const int32_t* __restrict__ 
     }
     if (!(w > 0.0) || !isfinite(w)) set_error(err, DEV_BAD_ELEMENT);
     vol[e] = w;
+    vol32[e] = __double2float_rn(w);
 #pragma unroll
     for (int m = 0; m <= D; ++m) atomicAdd(inc_count + v[m], 1);
   }
@@ -96,10 +99,12 @@ __global__ void k_mass_rows(const int32_t* __restrict__ conn, const double* __re
       const int32_t e = inc[p];
       const double w = vol[e];
       lump += w / (double)(D + 1);
+      // one division per incident element: 2 RN(w/den) == RN(2w/den)
+      const double wd = w / kDen;
 #pragma unroll
       for (int m = 0; m <= D; ++m) {
         const int32_t j = conn[(int64_t)e * (D + 1) + m];
-        const double c = w * (j == i ? 2.0 : 1.0) / kDen;
+        const double c = j == i ? 2.0 * wd : wd;
         int q = 0;
         while (q < cnt && cols[q] < j) ++q;
         if (q < cnt && cols[q] == j) {
@@ -141,14 +146,15 @@ static unsigned blocks_for(int64_t n) {
 template <int D>
 static sft_status build_target_t(sft_target_s* t, cudaStream_t st, int32_t* d_err) {
   SFT_CUDA(dalloc(&t->vol, (size_t)t->ne, st));
+  SFT_CUDA(dalloc(&t->vol32, (size_t)t->ne, st));
   int32_t *inc_count = nullptr, *inc_start = nullptr, *inc = nullptr, *row_len = nullptr;
   int64_t* off64 = nullptr;
   SFT_CUDA(dalloc(&inc_count, (size_t)t->nv, st));
   SFT_CUDA(cudaMemsetAsync(inc_count, 0, sizeof(int32_t) * t->nv, st));
   if (t->dtype == SFT_F64)
-    k_volumes<D, double><<<blocks_for(t->ne), 256, 0, st>>>((const double*)t->coords, t->conn, t->nv, t->ne, t->vol, inc_count, d_err);
+    ::sft::note_launch(), k_volumes<D, double><<<blocks_for(t->ne), 256, 0, st>>>((const double*)t->coords, t->conn, t->nv, t->ne, t->vol, t->vol32, inc_count, d_err);
   else
-    k_volumes<D, float><<<blocks_for(t->ne), 256, 0, st>>>((const float*)t->coords, t->conn, t->nv, t->ne, t->vol, inc_count, d_err);
+    ::sft::note_launch(), k_volumes<D, float><<<blocks_for(t->ne), 256, 0, st>>>((const float*)t->coords, t->conn, t->nv, t->ne, t->vol, t->vol32, inc_count, d_err);
   SFT_CUDA(cudaGetLastError());
   int32_t herr = 0;
   SFT_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -164,12 +170,12 @@ static sft_status build_target_t(sft_target_s* t, cudaStream_t st, int32_t* d_er
   SFT_CUDA(exclusive_scan_i32_to_i64(inc_count, off64, t->nv, st));
   SFT_CUDA(narrow_i64_to_i32(off64, inc_start, t->nv + 1, st));
   SFT_CUDA(cudaMemsetAsync(inc_count, 0, sizeof(int32_t) * t->nv, st));
-  k_inc_fill<D><<<blocks_for(t->ne), 256, 0, st>>>(t->conn, t->ne, inc_start, inc_count, inc);
+  ::sft::note_launch(), k_inc_fill<D><<<blocks_for(t->ne), 256, 0, st>>>(t->conn, t->ne, inc_start, inc_count, inc);
   SFT_CUDA(cudaGetLastError());
-  k_inc_sort<<<blocks_for(t->nv), 256, 0, st>>>(inc_start, inc, t->nv);
+  ::sft::note_launch(), k_inc_sort<<<blocks_for(t->nv), 256, 0, st>>>(inc_start, inc, t->nv);
   SFT_CUDA(cudaGetLastError());
   row_len = inc_count;  // reuse
-  k_mass_rows<D, false><<<blocks_for(t->nv), 256, 0, st>>>(t->conn, t->vol, inc_start, inc, t->nv, row_len, nullptr,
+  ::sft::note_launch(), k_mass_rows<D, false><<<blocks_for(t->nv), 256, 0, st>>>(t->conn, t->vol, inc_start, inc, t->nv, row_len, nullptr,
                                                            nullptr, nullptr, nullptr, nullptr, d_err);
   SFT_CUDA(cudaGetLastError());
   SFT_CUDA(exclusive_scan_i32_to_i64(row_len, off64, t->nv, st));
@@ -186,7 +192,7 @@ static sft_status build_target_t(sft_target_s* t, cudaStream_t st, int32_t* d_er
   SFT_CUDA(dalloc(&t->val, (size_t)nnz, st));
   SFT_CUDA(dalloc(&t->dinv, (size_t)t->nv, st));
   SFT_CUDA(dalloc(&t->lumped, (size_t)t->nv, st));
-  k_mass_rows<D, true><<<blocks_for(t->nv), 256, 0, st>>>(t->conn, t->vol, inc_start, inc, t->nv, nullptr, t->row_ptr,
+  ::sft::note_launch(), k_mass_rows<D, true><<<blocks_for(t->nv), 256, 0, st>>>(t->conn, t->vol, inc_start, inc, t->nv, nullptr, t->row_ptr,
                                                           t->col, t->val, t->dinv, t->lumped, d_err);
   SFT_CUDA(cudaGetLastError());
   dfree(off64, st);

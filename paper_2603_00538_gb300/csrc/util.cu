@@ -60,7 +60,7 @@ cudaError_t scan_rec(const TIn* in, int64_t* out, int64_t n, cudaStream_t s) {
   int64_t* sums = nullptr;
   cudaError_t e = cudaMallocAsync(&sums, sizeof(int64_t) * (tiles + 1), s);
   if (e != cudaSuccess) return e;
-  k_scan_tiles<TIn><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, sums);
+  ::sft::note_launch(), k_scan_tiles<TIn><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, sums);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (tiles == 1) {
     // out[n] = tile total; offsets are zero
@@ -71,7 +71,7 @@ cudaError_t scan_rec(const TIn* in, int64_t* out, int64_t n, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     e = scan_rec<int64_t>(sums, sums_scan, tiles, s);
     if (e == cudaSuccess) {
-      k_add_tile_offsets<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, n, sums_scan);
+      ::sft::note_launch(), k_add_tile_offsets<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, n, sums_scan);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess)
@@ -89,7 +89,7 @@ cudaError_t exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n
 
 cudaError_t narrow_i64_to_i32(const int64_t* in, int32_t* out, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_narrow<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, out, n);
+  ::sft::note_launch(), k_narrow<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, out, n);
   return cudaGetLastError();
 }
 
