@@ -149,6 +149,29 @@ sft_status sft_mass_solve(sft_target tgt, int32_t nrhs, const double* b, double*
                           int32_t device_ptrs, double tol, int32_t max_iter, void* cuda_stream,
                           int32_t* iters_out, double* rel_resid_out);
 
+/* Allocation-free solve of M u = b for callers that cannot allocate device
+ * memory at solve time (for example a coupled code whose memory pool owns
+ * the device, or a time-stepping loop that must not call cudaMalloc/cudaFree,
+ * which synchronise the device and can fail mid-run). The paper has no
+ * counterpart; this is the step-7 solve of sft_mass_solve with the caller's
+ * CSR matrix and its work vectors kept in a fixed 32 MiB device array that
+ * the library reserves on every device it is loaded on, until process exit.
+ * All pointers are device memory: row_ptr [n+1], col / val [row_ptr[n]]
+ * (FP64, symmetric positive definite, diagonal present), b and u
+ * [nrhs][n]. Jacobi-PCG from u = 0 to ||b - M u|| <= tol ||b||.
+ * Limits: 1 <= nrhs <= 8 and 8 n (1 + 4 nrhs) bytes plus small per-block
+ * partials must fit in 32 MiB (n (1 + 4 nrhs) below about 4.1e6);
+ * larger problems are rejected with SFT_ERR_ARG before any device work.
+ * The first call on a device looks up the array's device address once (make
+ * that first call before any stream capture). Every call uses the same
+ * array, so calls that overlap on the GPU (other streams, other threads)
+ * race and must be serialised by the caller. Nothing is allocated or freed;
+ * the stream is synchronised before returning. iters_out / rel_resid_out are
+ * host pointers (may be NULL). */
+sft_status sft_mass_solve_static(int64_t n, const int32_t* row_ptr, const int32_t* col, const double* val,
+                                 int32_t nrhs, const double* b, double* u, double tol, int32_t max_iter,
+                                 void* cuda_stream, int32_t* iters_out, double* rel_resid_out);
+
 /* Inspection of the built structures (host copies; any output may be NULL).
  * Source grid for `precision`: cells per axis n[3], cell count, registration
  * count, CSR start [ncells+1] and items [nitems]. */

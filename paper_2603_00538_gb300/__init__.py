@@ -74,6 +74,7 @@ _SIGS = {
     "sft_status_str": ([_i32], ctypes.c_char_p),
     "sft_last_error": ([], ctypes.c_char_p),
     "sft_kernel_launches": ([], _i64),
+    "sft_mass_solve_static": ([_i64, _vp, _vp, _vp, _i32, _vp, _vp, _d, _i32, _vp, _vp, _vp], _i32),
 }
 EXPORTS = tuple(_SIGS)
 _lib = None
@@ -291,6 +292,24 @@ def sft_mass_solve(tgt: Target, b, tol=1e-12, max_iter=1000, u_out=None, stream=
                                 stream if stream is not None else _current_stream(),
                                 ctypes.byref(it), ctypes.byref(rr)), "sft_mass_solve")
     return u_out, it.value, rr.value
+
+
+def sft_mass_solve_static(row_ptr, col, val, b, u_out, tol=1e-12, max_iter=1000, stream=None):
+    """Allocation-free solve of M u = b (all arguments CUDA tensors: row_ptr
+    int32 [n+1], col int32, val float64, b and u_out float64 [nrhs, n]).
+    Returns (iters, rel_resid)."""
+    n = int(row_ptr.shape[0]) - 1
+    nrhs = int(b.shape[0]) if b.dim() == 2 else 1
+    ptrs = [_ptr(x) for x in (row_ptr, col, val, b, u_out)]
+    if not all(dev for _, dev, _ in ptrs):
+        raise ValueError("sft_mass_solve_static takes device tensors only")
+    it = ctypes.c_int32()
+    rr = ctypes.c_double()
+    _check(lib().sft_mass_solve_static(n, ptrs[0][0], ptrs[1][0], ptrs[2][0], nrhs, ptrs[3][0], ptrs[4][0],
+                                       float(tol), int(max_iter),
+                                       stream if stream is not None else _current_stream(),
+                                       ctypes.byref(it), ctypes.byref(rr)), "sft_mass_solve_static")
+    return it.value, rr.value
 
 
 def sft_source_grid(src: Source, precision: int):

@@ -16,6 +16,7 @@
 // same convergence decision. The barrier wait is bounded (error flag on
 // timeout; the kernel then returns).
 #include <algorithm>
+#include <mutex>
 #include <vector>
 #include "internal.hpp"
 #include "util.cuh"
@@ -293,3 +294,126 @@ sft_status weighted_sum(const double* w, const double* u, int64_t n, double* out
 }
 
 }  // namespace sft
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the CG solve (no counterpart in the paper).
+//
+// Some callers cannot allocate device memory when they need a solve: for
+// example a coupled simulation that hands all device memory to its own pool
+// up front, or a time-stepping loop that must not call cudaMalloc/cudaFree
+// because they synchronise the device and can fail mid-run. This entry point
+// takes the CSR matrix, right-hand sides and solution buffers from the caller
+// and keeps its work vectors in one fixed, file-scope device array instead.
+// ---------------------------------------------------------------------------
+namespace sft {
+
+// 32 MiB of work space, resident on every device that loads the library
+constexpr size_t kStaticScratchBytes = 32ull << 20;
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+static std::mutex g_static_mu;
+static void* g_static_ptr[64] = {nullptr};
+
+// Device address of the scratch array for the current device: looked up once
+// per device (with that device current) and cached.
+static sft_status static_scratch(void** out) {
+  int dev = 0;
+  SFT_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(SFT_ERR_UNSUPPORTED, "device ordinal >= 64");
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return SFT_OK;
+}
+
+__global__ void k_jacobi_inverse(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                 const double* __restrict__ val, int64_t n, double* __restrict__ dinv) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double d = 0.0;
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k)
+      if (col[k] == i) d = val[k];
+    dinv[i] = d > 0.0 ? 1.0 / d : 0.0;
+  }
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace sft
+
+extern "C" sft_status sft_mass_solve_static(int64_t n, const int32_t* row_ptr, const int32_t* col,
+                                            const double* val, int32_t nrhs, const double* b, double* u,
+                                            double tol, int32_t max_iter, void* cuda_stream,
+                                            int32_t* iters_out, double* rel_resid_out) {
+  using namespace sft;
+  if (n <= 0 || !row_ptr || !col || !val || !b || !u) return fail(SFT_ERR_ARG, "null argument or n <= 0");
+  if (nrhs < 1 || nrhs > kMaxFields) return fail(SFT_ERR_ARG, "nrhs must be in 1..8");
+  if (max_iter < 1 || !(tol >= 0)) return fail(SFT_ERR_ARG, "bad solver options");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int dev = 0, sms = 0, coop = 0;
+  SFT_CUDA(cudaGetDevice(&dev));
+  SFT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  SFT_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) return fail(SFT_ERR_UNSUPPORTED, "device lacks cooperative launch");
+  int per_sm = 0;
+  SFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<1>, kSolveThreads, 0));
+  if (per_sm < 1) return fail(SFT_ERR_CUDA, "solver kernel cannot be resident");
+  per_sm = std::min(per_sm, 4);
+  const int64_t want = (n + kSolveThreads - 1) / kSolveThreads;
+  const unsigned nblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, want));
+  // layout: dinv [n] | r, z, p, q [nrhs][n] | partials [nblocks][nrhs][2] | control block
+  const size_t vec = sizeof(double) * (size_t)n * nrhs;
+  const size_t off_dinv = 0;
+  const size_t off_r = align256(off_dinv + sizeof(double) * (size_t)n);
+  const size_t off_z = align256(off_r + vec);
+  const size_t off_p = align256(off_z + vec);
+  const size_t off_q = align256(off_p + vec);
+  const size_t off_part = align256(off_q + vec);
+  const size_t off_ctl = align256(off_part + sizeof(double) * (size_t)nblocks * nrhs * 2);
+  const size_t need = off_ctl + sizeof(PcgCtl);
+  if (need > kStaticScratchBytes)
+    return fail(SFT_ERR_ARG, "problem too large for the 32 MiB static work space: needs 8 n (1 + 4 nrhs) bytes "
+                             "plus partials (n * (1 + 4 nrhs) <= ~4.1e6)");
+  void* base = nullptr;
+  if (sft_status r = static_scratch(&base)) return r;
+  unsigned char* s = static_cast<unsigned char*>(base);
+  double* dinv = reinterpret_cast<double*>(s + off_dinv);
+  double* r = reinterpret_cast<double*>(s + off_r);
+  double* z = reinterpret_cast<double*>(s + off_z);
+  double* p = reinterpret_cast<double*>(s + off_p);
+  double* q = reinterpret_cast<double*>(s + off_q);
+  double* part = reinterpret_cast<double*>(s + off_part);
+  PcgCtl* ctl = reinterpret_cast<PcgCtl*>(s + off_ctl);
+  // the barrier counters and error word must start at zero; every other
+  // region is written by the kernels before it is read
+  SFT_CUDA(cudaMemsetAsync(ctl, 0, sizeof(PcgCtl), st));
+  ::sft::note_launch(), k_jacobi_inverse<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(
+      row_ptr, col, val, n, dinv);
+  SFT_CUDA(cudaGetLastError());
+  const double* dinv_c = dinv;
+  void* args[] = {(void*)&row_ptr, (void*)&col, (void*)&val, (void*)&dinv_c, (void*)&n, (void*)&nrhs, (void*)&b,
+                  (void*)&u, (void*)&r, (void*)&z, (void*)&p, (void*)&q, (void*)&part,
+                  (void*)&ctl, (void*)&tol, (void*)&max_iter};
+  const cudaError_t le =
+      (::sft::note_launch(), cudaLaunchCooperativeKernel((const void*)k_pcg<1>, nblocks, kSolveThreads, args, 0, st));
+  if (le != cudaSuccess) return cuda_fail(le, "cudaLaunchCooperativeKernel(k_pcg, static scratch)");
+  PcgCtl h;
+  SFT_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
+  SFT_CUDA(cudaStreamSynchronize(st));
+  if (h.err != 0) return fail(SFT_ERR_DEVICE_STATUS, "CG kernel: grid barrier wait expired");
+  int it = 0, conv = 1;
+  double rel = 0.0;
+  for (int f = 0; f < nrhs; ++f) {
+    it = std::max(it, (int)h.iters[f]);
+    rel = std::max(rel, h.rel[f]);
+    if (!h.conv[f]) conv = 0;
+  }
+  if (iters_out) *iters_out = it;
+  if (rel_resid_out) *rel_resid_out = rel;
+  if (!conv) return fail(SFT_ERR_NOT_CONVERGED, "CG reached max_iter");
+  return SFT_OK;
+}
