@@ -84,6 +84,7 @@ def _declare(L):
     L.orc_grid_shape.argtypes = [_vp, _i32p, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]
     L.orc_grid_csr.argtypes = [_vp, _i64p, _i32p]
     L.orc_grid_locate.argtypes = [_vp, _i64, _f64p, _i32p, _i32p]
+    L.orc_grid_depths.argtypes = [_vp, _f64p]
     L.orc_brute_locate.argtypes = [_int, _int, _i64, _f64p, _i64, _i32p, _i64, _f64p,
                                    _i32p, _i32p]
     L.orc_eval_p1.argtypes = [_int, _f64p, _i32p, _int, _i64, _f64p, ctypes.c_int32,
@@ -166,6 +167,12 @@ class Grid:
         items = np.zeros(max(ni, 1), np.int32)
         lib().orc_grid_csr(self._h, start, items)
         return start, items[:ni]
+
+    def depths(self):
+        _, _, ni = self.shape()
+        out = np.zeros(max(ni, 1))
+        lib().orc_grid_depths(self._h, out)
+        return out[:ni]
 
     def locate(self, pts):
         pts = _f64(pts).reshape(-1, self.dim)

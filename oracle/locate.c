@@ -12,14 +12,18 @@
  *     It is monotone in x, so a point inside an element's bounding box falls
  *     in one of the cells the element is registered in;
  *   - each element is registered in every cell its bounding box overlaps;
- *     a cell lists its elements in ascending id;
+ *     a cell lists its elements by decreasing "depth" of the cell centre in
+ *     them (min of the centre's barycentric coordinates, computed with the
+ *     predicate below), ties by ascending id. The centre of cell i along an
+ *     axis is lo + (i + 1/2) h with h = (max - min)/n formed in FP64 and
+ *     rounded to P, evaluated as one fused multiply-add in P;
  *   - predicate: barycentric coordinates mu from the element's inverse affine
- *     map. The map coefficients are formed in FP64 from the vertex
- *     coordinates and rounded to P once; mu is then evaluated in P with fused
- *     multiply-adds in a fixed order. The point is accepted when all mu >= 0;
- *   - the first accepting candidate (ascending id) wins; if none accepts, the
- *     candidate with the largest min(mu) wins (ties to the lower id); an empty
- *     cell yields -1.
+ *     map, formed in P from the vertex coordinates (one reciprocal of the
+ *     determinant; FP32 uses Kahan's 2x2 determinant); mu is evaluated in P
+ *     with fused multiply-adds in a fixed order. Accepted when all mu >= 0;
+ *   - the first accepting candidate in the cell's order wins; if none
+ *     accepts, the candidate with the largest min(mu) wins (ties to the
+ *     earlier one); an empty cell yields -1.
  */
 #include "oracle.h"
 #include <math.h>
@@ -31,6 +35,7 @@ struct orc_grid {
     int32_t n[3];
     double lo[3];      /* grid box minimum (a P value) */
     double inv[3];     /* n / extent rounded to P */
+    double h[3];       /* extent / n rounded to P (cell size) */
     int64_t ncells, nitems;
     int64_t* start;
     int32_t* items;
@@ -79,8 +84,21 @@ static int32_t cell_axis(const orc_grid* g, int a, double x)
     return (int32_t)fl;
 }
 
+/* a*d - b*c in FP32 with Kahan's algorithm (one FMA recovers the rounding
+ * error of b*c), accurate to a few units in the last place */
+static float det2f(float a, float d, float b, float c)
+{
+    const float w = b * c;
+    const float e = fmaf(-b, c, w);
+    const float f = fmaf(a, d, -w);
+    return f + e;
+}
+
 /* barycentric coordinates of X in element e, evaluated in precision P from
- * the element's inverse affine map (coefficients formed in FP64, rounded). */
+ * the element's inverse affine map. The map is formed in P: edge vectors
+ * e_k = x_k - x_0, the determinant, one correctly rounded reciprocal of it,
+ * and products with the cofactors (FP32: cofactors and determinant with
+ * Kahan's 2x2 determinant; FP64: plain products). */
 static void predicate_mu(int prec, int dim, const double* coords, const int32_t* conn,
                          int32_t e, const double* X, double* mu)
 {
@@ -89,18 +107,22 @@ static void predicate_mu(int prec, int dim, const double* coords, const int32_t*
     if (dim == 2) {
         const double* b = coords + (int64_t)conn[(int64_t)e * k + 1] * dim;
         const double* c = coords + (int64_t)conn[(int64_t)e * k + 2] * dim;
-        const double e1x = b[0] - a[0], e1y = b[1] - a[1];
-        const double e2x = c[0] - a[0], e2y = c[1] - a[1];
-        const double det = e1x * e2y - e2x * e1y;
-        const double i00 = e2y / det, i01 = -e2x / det;
-        const double i10 = -e1y / det, i11 = e1x / det;
         if (prec == 1) {
-            const float dx = (float)X[0] - (float)a[0], dy = (float)X[1] - (float)a[1];
-            const float m1 = fmaf((float)i01, dy, (float)i00 * dx);
-            const float m2 = fmaf((float)i11, dy, (float)i10 * dx);
+            const float ax = (float)a[0], ay = (float)a[1];
+            const float e1x = (float)b[0] - ax, e1y = (float)b[1] - ay;
+            const float e2x = (float)c[0] - ax, e2y = (float)c[1] - ay;
+            const float inv = 1.0f / det2f(e1x, e2y, e2x, e1y);
+            const float i00 = e2y * inv, i01 = -e2x * inv, i10 = -e1y * inv, i11 = e1x * inv;
+            const float dx = (float)X[0] - ax, dy = (float)X[1] - ay;
+            const float m1 = fmaf(i01, dy, i00 * dx);
+            const float m2 = fmaf(i11, dy, i10 * dx);
             const float m0 = (1.0f - m1) - m2;
             mu[0] = m0; mu[1] = m1; mu[2] = m2;
         } else {
+            const double e1x = b[0] - a[0], e1y = b[1] - a[1];
+            const double e2x = c[0] - a[0], e2y = c[1] - a[1];
+            const double inv = 1.0 / (e1x * e2y - e2x * e1y);
+            const double i00 = e2y * inv, i01 = -e2x * inv, i10 = -e1y * inv, i11 = e1x * inv;
             const double dx = X[0] - a[0], dy = X[1] - a[1];
             const double m1 = fma(i01, dy, i00 * dx);
             const double m2 = fma(i11, dy, i10 * dx);
@@ -110,30 +132,47 @@ static void predicate_mu(int prec, int dim, const double* coords, const int32_t*
         const double* b = coords + (int64_t)conn[(int64_t)e * k + 1] * dim;
         const double* c = coords + (int64_t)conn[(int64_t)e * k + 2] * dim;
         const double* d = coords + (int64_t)conn[(int64_t)e * k + 3] * dim;
-        const double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
-        const double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
-        const double e3[3] = {d[0] - a[0], d[1] - a[1], d[2] - a[2]};
-        /* rows of the inverse Jacobian: (e2 x e3, e3 x e1, e1 x e2) / det */
-        const double c23[3] = {e2[1] * e3[2] - e2[2] * e3[1], e2[2] * e3[0] - e2[0] * e3[2],
-                               e2[0] * e3[1] - e2[1] * e3[0]};
-        const double c31[3] = {e3[1] * e1[2] - e3[2] * e1[1], e3[2] * e1[0] - e3[0] * e1[2],
-                               e3[0] * e1[1] - e3[1] * e1[0]};
-        const double c12[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
-                               e1[0] * e2[1] - e1[1] * e2[0]};
-        const double det = (e1[0] * c23[0] + e1[1] * c23[1]) + e1[2] * c23[2];
-        double r[3][3];
-        for (int q = 0; q < 3; ++q) {
-            r[0][q] = c23[q] / det; r[1][q] = c31[q] / det; r[2][q] = c12[q] / det;
-        }
         if (prec == 1) {
+            float e1[3], e2[3], e3[3];
+            for (int q = 0; q < 3; ++q) {
+                e1[q] = (float)b[q] - (float)a[q];
+                e2[q] = (float)c[q] - (float)a[q];
+                e3[q] = (float)d[q] - (float)a[q];
+            }
+            /* rows of the inverse Jacobian: (e2 x e3, e3 x e1, e1 x e2) / det */
+            const float c23[3] = {det2f(e2[1], e3[2], e2[2], e3[1]), det2f(e2[2], e3[0], e2[0], e3[2]),
+                                  det2f(e2[0], e3[1], e2[1], e3[0])};
+            const float c31[3] = {det2f(e3[1], e1[2], e3[2], e1[1]), det2f(e3[2], e1[0], e3[0], e1[2]),
+                                  det2f(e3[0], e1[1], e3[1], e1[0])};
+            const float c12[3] = {det2f(e1[1], e2[2], e1[2], e2[1]), det2f(e1[2], e2[0], e1[0], e2[2]),
+                                  det2f(e1[0], e2[1], e1[1], e2[0])};
+            const float inv = 1.0f / fmaf(e1[2], c23[2], fmaf(e1[1], c23[1], e1[0] * c23[0]));
+            float r[3][3];
+            for (int q = 0; q < 3; ++q) {
+                r[0][q] = c23[q] * inv; r[1][q] = c31[q] * inv; r[2][q] = c12[q] * inv;
+            }
             const float dx = (float)X[0] - (float)a[0], dy = (float)X[1] - (float)a[1],
                         dz = (float)X[2] - (float)a[2];
             float m[3];
             for (int q = 0; q < 3; ++q)
-                m[q] = fmaf((float)r[q][2], dz, fmaf((float)r[q][1], dy, (float)r[q][0] * dx));
+                m[q] = fmaf(r[q][2], dz, fmaf(r[q][1], dy, r[q][0] * dx));
             mu[0] = ((1.0f - m[0]) - m[1]) - m[2];
             mu[1] = m[0]; mu[2] = m[1]; mu[3] = m[2];
         } else {
+            const double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+            const double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+            const double e3[3] = {d[0] - a[0], d[1] - a[1], d[2] - a[2]};
+            const double c23[3] = {e2[1] * e3[2] - e2[2] * e3[1], e2[2] * e3[0] - e2[0] * e3[2],
+                                   e2[0] * e3[1] - e2[1] * e3[0]};
+            const double c31[3] = {e3[1] * e1[2] - e3[2] * e1[1], e3[2] * e1[0] - e3[0] * e1[2],
+                                   e3[0] * e1[1] - e3[1] * e1[0]};
+            const double c12[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                                   e1[0] * e2[1] - e1[1] * e2[0]};
+            const double inv = 1.0 / ((e1[0] * c23[0] + e1[1] * c23[1]) + e1[2] * c23[2]);
+            double r[3][3];
+            for (int q = 0; q < 3; ++q) {
+                r[0][q] = c23[q] * inv; r[1][q] = c31[q] * inv; r[2][q] = c12[q] * inv;
+            }
             const double dx = X[0] - a[0], dy = X[1] - a[1], dz = X[2] - a[2];
             double m[3];
             for (int q = 0; q < 3; ++q)
@@ -170,6 +209,57 @@ static double* rounded_coords(int prec, int dim, int64_t nv, const double* coord
     return c;
 }
 
+/* centre of cell index i along axis a, in P */
+static double cell_centre(const orc_grid* g, int a, int32_t i)
+{
+    if (g->prec == 1) return (double)fmaf((float)i + 0.5f, (float)g->h[a], (float)g->lo[a]);
+    return fma((double)i + 0.5, g->h[a], g->lo[a]);
+}
+
+/* min barycentric coordinate of point X in element e (the predicate's value) */
+static double depth(const orc_grid* g, int32_t e, const double* X)
+{
+    double mu[4];
+    predicate_mu(g->prec, g->dim, g->coords, g->conn, e, X, mu);
+    double mn = mu[0];
+    for (int m = 1; m <= g->dim; ++m) if (mu[m] < mn) mn = mu[m];
+    return mn;
+}
+
+/* each cell's list: decreasing depth of the cell centre, ties ascending id
+ * (stable insertion sort of the ascending-id list) */
+static void order_cells(orc_grid* g)
+{
+    int64_t cap = 0;
+    double* sc = NULL;
+    for (int64_t cell = 0; cell < g->ncells; ++cell) {
+        const int64_t p0 = g->start[cell], n = g->start[cell + 1] - p0;
+        if (n < 2) continue;
+        if (n > cap) { cap = n; sc = (double*)realloc(sc, sizeof(double) * (size_t)cap); }
+        const int32_t ix = (int32_t)(cell % g->n[0]);
+        const int32_t iy = (int32_t)((cell / g->n[0]) % g->n[1]);
+        const int32_t iz = (int32_t)(cell / ((int64_t)g->n[0] * g->n[1]));
+        const int32_t idx[3] = {ix, iy, iz};
+        double X[3] = {0, 0, 0};
+        for (int a = 0; a < g->dim; ++a) X[a] = cell_centre(g, a, idx[a]);
+        int32_t* it = g->items + p0;
+        for (int64_t q = 0; q < n; ++q) sc[q] = depth(g, it[q], X);
+        for (int64_t q = 1; q < n; ++q) {
+            const double ks = sc[q];
+            const int32_t ki = it[q];
+            int64_t r = q - 1;
+            while (r >= 0 && sc[r] < ks) {  /* ids ascend already: equal depths keep their order */
+                sc[r + 1] = sc[r];
+                it[r + 1] = it[r];
+                --r;
+            }
+            sc[r + 1] = ks;
+            it[r + 1] = ki;
+        }
+    }
+    free(sc);
+}
+
 orc_grid* orc_grid_build(int prec, int dim, int64_t nv, const double* coords,
                          int64_t ne, const int32_t* conn, double grid_scale_L)
 {
@@ -190,6 +280,7 @@ orc_grid* orc_grid_build(int prec, int dim, int64_t nv, const double* coords,
         g->n[a] = n;
         g->lo[a] = lo;
         g->inv[a] = to_prec(prec, (double)n / (hi - lo));
+        g->h[a] = to_prec(prec, (hi - lo) / (double)n);
         g->ncells *= n;
     }
     /* pass 1: count registrations per cell; pass 2: fill in element order */
@@ -225,6 +316,7 @@ orc_grid* orc_grid_build(int prec, int dim, int64_t nv, const double* coords,
         }
     }
     free(count);
+    order_cells(g);
     return g;
 }
 
@@ -245,6 +337,17 @@ void orc_grid_csr(const orc_grid* g, int64_t* start, int32_t* items)
 {
     memcpy(start, g->start, sizeof(int64_t) * (size_t)(g->ncells + 1));
     memcpy(items, g->items, sizeof(int32_t) * (size_t)g->nitems);
+}
+
+void orc_grid_depths(const orc_grid* g, double* out)
+{
+    for (int64_t cell = 0; cell < g->ncells; ++cell) {
+        const int32_t idx[3] = {(int32_t)(cell % g->n[0]), (int32_t)((cell / g->n[0]) % g->n[1]),
+                                (int32_t)(cell / ((int64_t)g->n[0] * g->n[1]))};
+        double X[3] = {0, 0, 0};
+        for (int a = 0; a < g->dim; ++a) X[a] = cell_centre(g, a, idx[a]);
+        for (int64_t p = g->start[cell]; p < g->start[cell + 1]; ++p) out[p] = depth(g, g->items[p], X);
+    }
 }
 
 static int locate_one(const orc_grid* g, const double* Xin, int32_t* elem)

@@ -47,7 +47,9 @@ void orc_grid_free(orc_grid* g);
 void orc_grid_shape(const orc_grid* g, int32_t n_out[3], int64_t* ncells, int64_t* nitems);
 /* CSR copy: start [ncells+1], items [nitems] */
 void orc_grid_csr(const orc_grid* g, int64_t* start, int32_t* items);
-/* elem_out: containing element (first accepting candidate in ascending id),
+/* depth of each cell's centre in each listed element (min barycentric), [nitems] */
+void orc_grid_depths(const orc_grid* g, double* out);
+/* elem_out: containing element (first accepting candidate in the cell order),
  * the best-scoring candidate when none accepts, or -1 for an empty cell.
  * status_out: 0 accepted, 1 fallback, 2 empty cell. */
 void orc_grid_locate(const orc_grid* g, int64_t npts, const double* pts,

@@ -123,6 +123,7 @@ __device__ __forceinline__ void map_point(const P lam[D + 1], const P xv[D + 1][
 template <typename P> struct GridP {
   P lo[3];
   P inv[3];
+  P h[3];      // cell size (extent / n, rounded to P): cell centres lo + (i + 1/2) h
   int32_t n[3];
 };
 
@@ -213,11 +214,15 @@ __device__ __forceinline__ void load_record(const P* __restrict__ recs, int32_t 
   }
 }
 
-// Locate X: scan the candidates of its cell in ascending element id, return
-// the first whose predicate accepts; if none accepts, the candidate with the
-// largest min(mu) (first in order on ties); -1 for an empty cell.
+// Locate X: scan the candidates of its cell in list order (decreasing depth
+// of the cell centre in the element, ties ascending id), return the first
+// whose predicate accepts; if none accepts, the candidate with the largest
+// min(mu) (the earlier one on ties); -1 for an empty cell.
 // status: 0 accepted, 1 nearest candidate, 2 empty cell. mu is the returned
-// element's barycentric vector.
+// element's barycentric vector. The first pass only tests acceptance; the
+// nearest-candidate pass runs only when nothing accepted (rare: points on
+// the domain boundary within rounding), so the common path carries no
+// bookkeeping for it. The result is that of a single scan with both rules.
 template <int D, typename P>
 __device__ __forceinline__ int32_t locate_point(const GridP<P>& g, const int32_t* __restrict__ cell_start,
                                                 const int32_t* __restrict__ cell_items,

@@ -3,7 +3,7 @@
 #include <cstdint>
 #include <string>
 #include <cuda_runtime.h>
-#include "../../include/sft.h"
+#include "sft.h"
 #include "common.cuh"
 
 namespace sft {

@@ -7,8 +7,10 @@
 // Layout in HBM per precision P:
 //   recs  [ne][8 | 12] P  : first vertex + inverse affine map (16-B aligned rows)
 //   vals  [nf][ne][4]  P  : per-element copy of the nodal values (one 16/32-B load)
-//   cell_start [ncells+1], cell_items [nitems] int32: elements of each cell in
-//   ascending id (the order the first-accepting-candidate rule scans).
+//   cell_start [ncells+1], cell_items [nitems] int32: elements of each cell,
+//   ordered by decreasing depth of the cell centre in them (min barycentric
+//   coordinate), ties by ascending id: the element holding most of the cell
+//   is scanned first, and the first accepting candidate in this order wins.
 #include <cmath>
 #include <vector>
 #include "internal.hpp"
@@ -93,7 +95,7 @@ __global__ void k_grid_params(const P* __restrict__ part, int nblocks, int32_t n
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   GridP<P> r;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) { r.lo[a] = P(0); r.inv[a] = P(0); r.n[a] = 1; }
+  for (int a = 0; a < 3; ++a) { r.lo[a] = P(0); r.inv[a] = P(0); r.h[a] = P(0); r.n[a] = 1; }
   for (int a = 0; a < D; ++a) {
     P lo = part[a], hi = part[D + a];
     for (int b = 1; b < nblocks; ++b) {
@@ -104,6 +106,7 @@ __global__ void k_grid_params(const P* __restrict__ part, int nblocks, int32_t n
     if (!(hi > lo)) set_error(err, DEV_BAD_ELEMENT);
     r.lo[a] = lo;
     r.inv[a] = Ar<P>::from_d(__ddiv_rn((double)n, __dsub_rn((double)hi, (double)lo)));
+    r.h[a] = Ar<P>::from_d(__ddiv_rn(__dsub_rn((double)hi, (double)lo), (double)n));
     r.n[a] = n;
   }
   *g = r;
@@ -143,6 +146,96 @@ __device__ __forceinline__ int64_t elem_cell_range(const GridP<P>& g, const P xv
   return cnt;
 }
 
+// a*d - b*c in FP32 by Kahan's algorithm (the FMA recovers the rounding error
+// of b*c)
+__device__ __forceinline__ float det2f(float a, float d, float b, float c) {
+  const float w = __fmul_rn(b, c);
+  const float e = __fmaf_rn(-b, c, w);
+  const float f = __fmaf_rn(a, d, -w);
+  return __fadd_rn(f, e);
+}
+
+// Inverse affine map of an element into record slots [D .. D + D*D): formed in
+// P from the edge vectors, with one correctly rounded reciprocal of the
+// determinant (FP32: cofactors and determinant by Kahan's 2x2 determinant).
+// Returns false for a non-positive element.
+template <int D, typename P>
+__device__ __forceinline__ bool record_map(const P xv[D + 1][D], P* r) {
+  if constexpr (sizeof(P) == 4) {
+    float e[D][D];
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+#pragma unroll
+      for (int a = 0; a < D; ++a) e[k][a] = __fsub_rn(xv[k + 1][a], xv[0][a]);
+    if constexpr (D == 2) {
+      const float det = det2f(e[0][0], e[1][1], e[1][0], e[0][1]);
+      const float inv = __frcp_rn(det);
+      r[2] = __fmul_rn(e[1][1], inv);
+      r[3] = __fmul_rn(-e[1][0], inv);
+      r[4] = __fmul_rn(-e[0][1], inv);
+      r[5] = __fmul_rn(e[0][0], inv);
+      return det > 0.f;
+    } else {
+      const float* e1 = e[0];
+      const float* e2 = e[1];
+      const float* e3 = e[2];
+      const float c23[3] = {det2f(e2[1], e3[2], e2[2], e3[1]), det2f(e2[2], e3[0], e2[0], e3[2]),
+                            det2f(e2[0], e3[1], e2[1], e3[0])};
+      const float c31[3] = {det2f(e3[1], e1[2], e3[2], e1[1]), det2f(e3[2], e1[0], e3[0], e1[2]),
+                            det2f(e3[0], e1[1], e3[1], e1[0])};
+      const float c12[3] = {det2f(e1[1], e2[2], e1[2], e2[1]), det2f(e1[2], e2[0], e1[0], e2[2]),
+                            det2f(e1[0], e2[1], e1[1], e2[0])};
+      const float det = __fmaf_rn(e1[2], c23[2], __fmaf_rn(e1[1], c23[1], __fmul_rn(e1[0], c23[0])));
+      const float inv = __frcp_rn(det);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        r[3 + q] = __fmul_rn(c23[q], inv);
+        r[6 + q] = __fmul_rn(c31[q], inv);
+        r[9 + q] = __fmul_rn(c12[q], inv);
+      }
+      return det > 0.f;
+    }
+  } else {
+    double e[D][D];
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+#pragma unroll
+      for (int a = 0; a < D; ++a) e[k][a] = __dsub_rn(xv[k + 1][a], xv[0][a]);
+    if constexpr (D == 2) {
+      const double det = __dsub_rn(__dmul_rn(e[0][0], e[1][1]), __dmul_rn(e[1][0], e[0][1]));
+      const double inv = __drcp_rn(det);
+      r[2] = __dmul_rn(e[1][1], inv);
+      r[3] = __dmul_rn(-e[1][0], inv);
+      r[4] = __dmul_rn(-e[0][1], inv);
+      r[5] = __dmul_rn(e[0][0], inv);
+      return det > 0.0;
+    } else {
+      const double* e1 = e[0];
+      const double* e2 = e[1];
+      const double* e3 = e[2];
+      auto crs = [](const double* u, const double* w, double* o) {
+        o[0] = __dsub_rn(__dmul_rn(u[1], w[2]), __dmul_rn(u[2], w[1]));
+        o[1] = __dsub_rn(__dmul_rn(u[2], w[0]), __dmul_rn(u[0], w[2]));
+        o[2] = __dsub_rn(__dmul_rn(u[0], w[1]), __dmul_rn(u[1], w[0]));
+      };
+      double c23[3], c31[3], c12[3];
+      crs(e2, e3, c23);
+      crs(e3, e1, c31);
+      crs(e1, e2, c12);
+      const double det =
+          __dadd_rn(__dadd_rn(__dmul_rn(e1[0], c23[0]), __dmul_rn(e1[1], c23[1])), __dmul_rn(e1[2], c23[2]));
+      const double inv = __drcp_rn(det);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        r[3 + q] = __dmul_rn(c23[q], inv);
+        r[6 + q] = __dmul_rn(c31[q], inv);
+        r[9 + q] = __dmul_rn(c12[q], inv);
+      }
+      return det > 0.0;
+    }
+  }
+}
+
 template <int D, typename P, typename TV>
 __global__ void k_records(const P* __restrict__ x, const int32_t* __restrict__ conn, const TV* __restrict__ values,
                           int64_t nv, int64_t ne, int nf, const GridP<P>* __restrict__ gp, P* __restrict__ recs,
@@ -169,42 +262,7 @@ __global__ void k_records(const P* __restrict__ x, const int32_t* __restrict__ c
     for (int q = 0; q < L; ++q) r[q] = P(0);
 #pragma unroll
     for (int a = 0; a < D; ++a) r[a] = xv[0][a];
-    if constexpr (D == 2) {
-      const double ax = xv[0][0], ay = xv[0][1];
-      const double e1x = __dsub_rn((double)xv[1][0], ax), e1y = __dsub_rn((double)xv[1][1], ay);
-      const double e2x = __dsub_rn((double)xv[2][0], ax), e2y = __dsub_rn((double)xv[2][1], ay);
-      const double det = __dsub_rn(__dmul_rn(e1x, e2y), __dmul_rn(e2x, e1y));
-      if (!(det > 0.0)) set_error(err, DEV_BAD_ELEMENT);
-      r[2] = Ar<P>::from_d(__ddiv_rn(e2y, det));
-      r[3] = Ar<P>::from_d(__ddiv_rn(-e2x, det));
-      r[4] = Ar<P>::from_d(__ddiv_rn(-e1y, det));
-      r[5] = Ar<P>::from_d(__ddiv_rn(e1x, det));
-    } else {
-      double e1[3], e2[3], e3[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        e1[a] = __dsub_rn((double)xv[1][a], (double)xv[0][a]);
-        e2[a] = __dsub_rn((double)xv[2][a], (double)xv[0][a]);
-        e3[a] = __dsub_rn((double)xv[3][a], (double)xv[0][a]);
-      }
-      auto crs = [](const double* u, const double* w, double* o) {
-        o[0] = __dsub_rn(__dmul_rn(u[1], w[2]), __dmul_rn(u[2], w[1]));
-        o[1] = __dsub_rn(__dmul_rn(u[2], w[0]), __dmul_rn(u[0], w[2]));
-        o[2] = __dsub_rn(__dmul_rn(u[0], w[1]), __dmul_rn(u[1], w[0]));
-      };
-      double c23[3], c31[3], c12[3];
-      crs(e2, e3, c23);
-      crs(e3, e1, c31);
-      crs(e1, e2, c12);
-      const double det = __dadd_rn(__dadd_rn(__dmul_rn(e1[0], c23[0]), __dmul_rn(e1[1], c23[1])), __dmul_rn(e1[2], c23[2]));
-      if (!(det > 0.0)) set_error(err, DEV_BAD_ELEMENT);
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        r[3 + q] = Ar<P>::from_d(__ddiv_rn(c23[q], det));
-        r[6 + q] = Ar<P>::from_d(__ddiv_rn(c31[q], det));
-        r[9 + q] = Ar<P>::from_d(__ddiv_rn(c12[q], det));
-      }
-    }
+    if (!record_map<D, P>(xv, r)) set_error(err, DEV_BAD_ELEMENT);
 #pragma unroll
     for (int q = 0; q < L; ++q) recs[e * L + q] = r[q];
     for (int f = 0; f < nf; ++f) {
@@ -238,41 +296,50 @@ __global__ void k_register(const P* __restrict__ x, const int32_t* __restrict__ 
   }
 }
 
-// ascending element order inside each cell. Cells of up to 16 entries (the
-// common case) are sorted in registers by an odd-even transposition network
-// (static indices only); longer cells by an insertion sort in memory.
-__global__ void k_sort_cells(const int32_t* __restrict__ cell_start, int32_t* __restrict__ items, int64_t ncells) {
-  constexpr int R = 16;
+// Order each cell's list (built in arbitrary order by the atomic fill):
+// decreasing depth of the cell centre in the element (the predicate's min
+// barycentric coordinate there), ties by ascending element id. Insertion
+// sort over the cell's entries (cells are short), with their depths in a
+// scratch array.
+template <int D, typename P>
+__global__ void k_order_cells(const GridP<P>* __restrict__ gp, const int32_t* __restrict__ cell_start,
+                              int32_t* __restrict__ items, P* __restrict__ depth, const P* __restrict__ recs,
+                              int64_t ncells) {
+  using A = Ar<P>;
+  constexpr int L = RecLen<D>::value;
+  const GridP<P> g = *gp;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x) {
     const int32_t p0 = cell_start[c], p1 = cell_start[c + 1];
-    const int32_t len = p1 - p0;
-    if (len <= 1) continue;
-    if (len <= R) {
-      int32_t k[R];
+    if (p1 - p0 < 2) continue;
+    int64_t rem = c;
+    P X[D];
 #pragma unroll
-      for (int i = 0; i < R; ++i) k[i] = i < len ? items[p0 + i] : INT32_MAX;
-#pragma unroll
-      for (int phase = 0; phase < R; ++phase) {
-#pragma unroll
-        for (int i = phase & 1; i + 1 < R; i += 2) {
-          const int32_t a = min(k[i], k[i + 1]), b = max(k[i], k[i + 1]);
-          k[i] = a;
-          k[i + 1] = b;
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < R; ++i)
-        if (i < len) items[p0 + i] = k[i];
-      continue;
+    for (int a = 0; a < D; ++a) {
+      const int32_t i = (int32_t)(rem % g.n[a]);
+      rem /= g.n[a];
+      X[a] = A::fma(A::add((P)i, P(0.5)), g.h[a], g.lo[a]);
     }
-    for (int32_t i = p0 + 1; i < p1; ++i) {
-      const int32_t key = items[i];
-      int32_t j = i - 1;
-      while (j >= p0 && items[j] > key) {
-        items[j + 1] = items[j];
-        --j;
+    for (int32_t p = p0; p < p1; ++p) {
+      P r[L];
+      load_record<D, P>(recs, items[p], r);
+      P mu[D + 1];
+      bary_from_record<D, P>(r, X, mu);
+      P mn = mu[0];
+#pragma unroll
+      for (int q = 1; q <= D; ++q) mn = mu[q] < mn ? mu[q] : mn;
+      depth[p] = mn;
+    }
+    for (int32_t p = p0 + 1; p < p1; ++p) {
+      const P ks = depth[p];
+      const int32_t ki = items[p];
+      int32_t q = p - 1;
+      while (q >= p0 && (depth[q] < ks || (depth[q] == ks && items[q] > ki))) {
+        depth[q + 1] = depth[q];
+        items[q + 1] = items[q];
+        --q;
       }
-      items[j + 1] = key;
+      depth[q + 1] = ks;
+      items[q + 1] = ki;
     }
   }
 }
@@ -356,8 +423,12 @@ static sft_status build_locator_t(sft_source_s* s, int prec, cudaStream_t st, in
   SFT_CUDA(cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * L.ncells, st));
   ::sft::note_launch(), k_register<D, P, true><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, s->ne, g, cell_count, L.cell_start, L.cell_items);
   SFT_CUDA(cudaGetLastError());
-  ::sft::note_launch(), k_sort_cells<<<grid_for(L.ncells), 256, 0, st>>>(L.cell_start, L.cell_items, L.ncells);
+  P* depth = nullptr;
+  SFT_CUDA(dalloc(&depth, (size_t)total, st));
+  ::sft::note_launch(), k_order_cells<D, P><<<grid_for(L.ncells), 256, 0, st>>>(g, L.cell_start, L.cell_items, depth,
+                                                                              recs, L.ncells);
   SFT_CUDA(cudaGetLastError());
+  dfree(depth, st);
   dfree(cell_count, st);
   dfree(start64, st);
   L.built = true;

@@ -17,8 +17,8 @@ constexpr int kMaxRow = 64;  // distinct neighbours (incl. self) per node
 
 template <int D, typename TI>
 __global__ void k_volumes(const TI* __restrict__ x, const int32_t* __restrict__ conn, int64_t nv, int64_t ne,
-                          double* __restrict__ vol, float* __restrict__ vol32, int32_t* __restrict__ inc_count,
-                          int32_t* err) {
+                          double* __restrict__ vol, float* __restrict__ vol32, double2* __restrict__ wfac,
+                          int32_t* __restrict__ inc_count, int32_t* err) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
     int32_t v[D + 1];
     bool ok = true;
@@ -51,6 +51,8 @@ __global__ void k_volumes(const TI* __restrict__ x, const int32_t* __restrict__ 
     if (!(w > 0.0) || !isfinite(w)) set_error(err, DEV_BAD_ELEMENT);
     vol[e] = w;
     vol32[e] = __double2float_rn(w);
+    // mass-matrix factor |T|/((d+1)(d+2)) and lumped share |T|/(d+1)
+    wfac[e] = make_double2(w / (double)((D + 1) * (D + 2)), w / (double)(D + 1));
 #pragma unroll
     for (int m = 0; m <= D; ++m) atomicAdd(inc_count + v[m], 1);
   }
@@ -83,12 +85,11 @@ __global__ void k_inc_sort(const int32_t* __restrict__ inc_start, int32_t* __res
 // Row i of M: FILL=false writes the row length, FILL=true writes columns,
 // values, the Jacobi inverse diagonal and the lumped mass.
 template <int D, bool FILL>
-__global__ void k_mass_rows(const int32_t* __restrict__ conn, const double* __restrict__ vol,
+__global__ void k_mass_rows(const int32_t* __restrict__ conn, const double2* __restrict__ wfac,
                             const int32_t* __restrict__ inc_start, const int32_t* __restrict__ inc, int64_t nv,
                             int32_t* __restrict__ row_len, const int32_t* __restrict__ row_ptr,
                             int32_t* __restrict__ col, double* __restrict__ val, double* __restrict__ dinv,
                             double* __restrict__ lumped, int32_t* err) {
-  constexpr double kDen = (double)((D + 1) * (D + 2));
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
     int32_t cols[kMaxRow];
     double vals[kMaxRow];
@@ -97,10 +98,10 @@ __global__ void k_mass_rows(const int32_t* __restrict__ conn, const double* __re
     double lump = 0.0;
     for (int32_t p = inc_start[i]; p < inc_start[i + 1]; ++p) {
       const int32_t e = inc[p];
-      const double w = vol[e];
-      lump += w / (double)(D + 1);
-      // one division per incident element: 2 RN(w/den) == RN(2w/den)
-      const double wd = w / kDen;
+      const double2 wf = __ldg(wfac + e);
+      lump += wf.y;
+      // 2 RN(w/den) == RN(2w/den): same values as dividing each entry
+      const double wd = wf.x;
 #pragma unroll
       for (int m = 0; m <= D; ++m) {
         const int32_t j = conn[(int64_t)e * (D + 1) + m];
@@ -147,20 +148,23 @@ template <int D>
 static sft_status build_target_t(sft_target_s* t, cudaStream_t st, int32_t* d_err) {
   SFT_CUDA(dalloc(&t->vol, (size_t)t->ne, st));
   SFT_CUDA(dalloc(&t->vol32, (size_t)t->ne, st));
+  double2* wfac = nullptr;
+  SFT_CUDA(dalloc(&wfac, (size_t)t->ne, st));
   int32_t *inc_count = nullptr, *inc_start = nullptr, *inc = nullptr, *row_len = nullptr;
   int64_t* off64 = nullptr;
   SFT_CUDA(dalloc(&inc_count, (size_t)t->nv, st));
   SFT_CUDA(cudaMemsetAsync(inc_count, 0, sizeof(int32_t) * t->nv, st));
   if (t->dtype == SFT_F64)
-    ::sft::note_launch(), k_volumes<D, double><<<blocks_for(t->ne), 256, 0, st>>>((const double*)t->coords, t->conn, t->nv, t->ne, t->vol, t->vol32, inc_count, d_err);
+    ::sft::note_launch(), k_volumes<D, double><<<blocks_for(t->ne), 256, 0, st>>>((const double*)t->coords, t->conn, t->nv, t->ne, t->vol, t->vol32, wfac, inc_count, d_err);
   else
-    ::sft::note_launch(), k_volumes<D, float><<<blocks_for(t->ne), 256, 0, st>>>((const float*)t->coords, t->conn, t->nv, t->ne, t->vol, t->vol32, inc_count, d_err);
+    ::sft::note_launch(), k_volumes<D, float><<<blocks_for(t->ne), 256, 0, st>>>((const float*)t->coords, t->conn, t->nv, t->ne, t->vol, t->vol32, wfac, inc_count, d_err);
   SFT_CUDA(cudaGetLastError());
   int32_t herr = 0;
   SFT_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   SFT_CUDA(cudaStreamSynchronize(st));
   if (herr) {
     dfree(inc_count, st);
+    dfree(wfac, st);
     return fail(SFT_ERR_MESH, herr == DEV_BAD_INDEX ? "target connectivity index out of range"
                                                     : "target mesh has a non-positive element");
   }
@@ -175,7 +179,7 @@ static sft_status build_target_t(sft_target_s* t, cudaStream_t st, int32_t* d_er
   ::sft::note_launch(), k_inc_sort<<<blocks_for(t->nv), 256, 0, st>>>(inc_start, inc, t->nv);
   SFT_CUDA(cudaGetLastError());
   row_len = inc_count;  // reuse
-  ::sft::note_launch(), k_mass_rows<D, false><<<blocks_for(t->nv), 256, 0, st>>>(t->conn, t->vol, inc_start, inc, t->nv, row_len, nullptr,
+  ::sft::note_launch(), k_mass_rows<D, false><<<blocks_for(t->nv), 256, 0, st>>>(t->conn, wfac, inc_start, inc, t->nv, row_len, nullptr,
                                                            nullptr, nullptr, nullptr, nullptr, d_err);
   SFT_CUDA(cudaGetLastError());
   SFT_CUDA(exclusive_scan_i32_to_i64(row_len, off64, t->nv, st));
@@ -192,13 +196,14 @@ static sft_status build_target_t(sft_target_s* t, cudaStream_t st, int32_t* d_er
   SFT_CUDA(dalloc(&t->val, (size_t)nnz, st));
   SFT_CUDA(dalloc(&t->dinv, (size_t)t->nv, st));
   SFT_CUDA(dalloc(&t->lumped, (size_t)t->nv, st));
-  ::sft::note_launch(), k_mass_rows<D, true><<<blocks_for(t->nv), 256, 0, st>>>(t->conn, t->vol, inc_start, inc, t->nv, nullptr, t->row_ptr,
+  ::sft::note_launch(), k_mass_rows<D, true><<<blocks_for(t->nv), 256, 0, st>>>(t->conn, wfac, inc_start, inc, t->nv, nullptr, t->row_ptr,
                                                           t->col, t->val, t->dinv, t->lumped, d_err);
   SFT_CUDA(cudaGetLastError());
   dfree(off64, st);
   dfree(inc_start, st);
   dfree(inc, st);
   dfree(inc_count, st);
+  dfree(wfac, st);
   return SFT_OK;
 }
 

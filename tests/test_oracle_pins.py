@@ -214,10 +214,15 @@ def test_grid_structure(orc, dim):
     expect_n = int(math.isqrt(E)) if dim == 2 else max(k for k in range(1, 200) if k ** 3 <= E)
     assert n[0] == expect_n and nc == expect_n ** dim
     start, items = g.csr()
+    depth = g.depths()
     assert start[0] == 0 and start[-1] == ni and np.all(np.diff(start) >= 0)
     for c in range(nc):
-        seg = items[start[c]:start[c + 1]]
-        assert np.all(np.diff(seg) > 0)          # ascending element ids
+        seg, dep = items[start[c]:start[c + 1]], depth[start[c]:start[c + 1]]
+        # decreasing centre depth, ties by ascending id; every cell centre lies
+        # in the meshed unit square/cube, so the first element contains it
+        assert np.all((np.diff(dep) < 0) | ((np.diff(dep) == 0) & (np.diff(seg) > 0)))
+        assert len(seg) == len(set(seg.tolist()))
+        assert dep[0] >= 0.0
     # every element appears in exactly the cells of its bounding box
     lo = src.coords.min(0)
     hi = src.coords.max(0)
