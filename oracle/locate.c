@@ -11,8 +11,9 @@
  *   - cell of a coordinate x: clamp(floor((x - min) * inv), 0, n - 1) in P.
  *     It is monotone in x, so a point inside an element's bounding box falls
  *     in one of the cells the element is registered in;
- *   - each element is registered in every cell its bounding box overlaps;
- *     a cell lists its elements by decreasing "depth" of the cell centre in
+ *   - each element is registered in the cells its bounding box overlaps,
+ *     except those that one of its face planes separates from it (see
+ *     cell_may_hold); a cell lists its elements by decreasing "depth" of the cell centre in
  *     them (min of the centre's barycentric coordinates, computed with the
  *     predicate below), ties by ascending id. The centre of cell i along an
  *     axis is lo + (i + 1/2) h with h = (max - min)/n formed in FP64 and
@@ -94,16 +95,18 @@ static float det2f(float a, float d, float b, float c)
     return f + e;
 }
 
-/* barycentric coordinates of X in element e, evaluated in precision P from
- * the element's inverse affine map. The map is formed in P: edge vectors
- * e_k = x_k - x_0, the determinant, one correctly rounded reciprocal of it,
- * and products with the cofactors (FP32: cofactors and determinant with
- * Kahan's 2x2 determinant; FP64: plain products). */
-static void predicate_mu(int prec, int dim, const double* coords, const int32_t* conn,
-                         int32_t e, const double* X, double* mu)
+/* The element's inverse affine map in precision P: first vertex x0[dim] and
+ * rows R[m][a] (m, a < dim) with mu_{m+1}(X) = R[m] . (X - x0). Formed in P
+ * from the edge vectors e_k = x_k - x_0 with one correctly rounded reciprocal
+ * of the determinant (FP32: cofactors and determinant by Kahan's 2x2
+ * determinant; FP64: plain products). Values are stored as doubles holding
+ * P values. */
+static void inverse_map(int prec, int dim, const double* coords, const int32_t* conn, int32_t e,
+                        double x0[3], double R[3][3])
 {
     const int k = dim + 1;
     const double* a = coords + (int64_t)conn[(int64_t)e * k + 0] * dim;
+    for (int q = 0; q < dim; ++q) x0[q] = a[q];
     if (dim == 2) {
         const double* b = coords + (int64_t)conn[(int64_t)e * k + 1] * dim;
         const double* c = coords + (int64_t)conn[(int64_t)e * k + 2] * dim;
@@ -112,21 +115,12 @@ static void predicate_mu(int prec, int dim, const double* coords, const int32_t*
             const float e1x = (float)b[0] - ax, e1y = (float)b[1] - ay;
             const float e2x = (float)c[0] - ax, e2y = (float)c[1] - ay;
             const float inv = 1.0f / det2f(e1x, e2y, e2x, e1y);
-            const float i00 = e2y * inv, i01 = -e2x * inv, i10 = -e1y * inv, i11 = e1x * inv;
-            const float dx = (float)X[0] - ax, dy = (float)X[1] - ay;
-            const float m1 = fmaf(i01, dy, i00 * dx);
-            const float m2 = fmaf(i11, dy, i10 * dx);
-            const float m0 = (1.0f - m1) - m2;
-            mu[0] = m0; mu[1] = m1; mu[2] = m2;
+            R[0][0] = e2y * inv; R[0][1] = -e2x * inv; R[1][0] = -e1y * inv; R[1][1] = e1x * inv;
         } else {
             const double e1x = b[0] - a[0], e1y = b[1] - a[1];
             const double e2x = c[0] - a[0], e2y = c[1] - a[1];
             const double inv = 1.0 / (e1x * e2y - e2x * e1y);
-            const double i00 = e2y * inv, i01 = -e2x * inv, i10 = -e1y * inv, i11 = e1x * inv;
-            const double dx = X[0] - a[0], dy = X[1] - a[1];
-            const double m1 = fma(i01, dy, i00 * dx);
-            const double m2 = fma(i11, dy, i10 * dx);
-            mu[0] = (1.0 - m1) - m2; mu[1] = m1; mu[2] = m2;
+            R[0][0] = e2y * inv; R[0][1] = -e2x * inv; R[1][0] = -e1y * inv; R[1][1] = e1x * inv;
         }
     } else {
         const double* b = coords + (int64_t)conn[(int64_t)e * k + 1] * dim;
@@ -147,17 +141,9 @@ static void predicate_mu(int prec, int dim, const double* coords, const int32_t*
             const float c12[3] = {det2f(e1[1], e2[2], e1[2], e2[1]), det2f(e1[2], e2[0], e1[0], e2[2]),
                                   det2f(e1[0], e2[1], e1[1], e2[0])};
             const float inv = 1.0f / fmaf(e1[2], c23[2], fmaf(e1[1], c23[1], e1[0] * c23[0]));
-            float r[3][3];
             for (int q = 0; q < 3; ++q) {
-                r[0][q] = c23[q] * inv; r[1][q] = c31[q] * inv; r[2][q] = c12[q] * inv;
+                R[0][q] = c23[q] * inv; R[1][q] = c31[q] * inv; R[2][q] = c12[q] * inv;
             }
-            const float dx = (float)X[0] - (float)a[0], dy = (float)X[1] - (float)a[1],
-                        dz = (float)X[2] - (float)a[2];
-            float m[3];
-            for (int q = 0; q < 3; ++q)
-                m[q] = fmaf(r[q][2], dz, fmaf(r[q][1], dy, r[q][0] * dx));
-            mu[0] = ((1.0f - m[0]) - m[1]) - m[2];
-            mu[1] = m[0]; mu[2] = m[1]; mu[3] = m[2];
         } else {
             const double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
             const double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
@@ -169,17 +155,95 @@ static void predicate_mu(int prec, int dim, const double* coords, const int32_t*
             const double c12[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
                                    e1[0] * e2[1] - e1[1] * e2[0]};
             const double inv = 1.0 / ((e1[0] * c23[0] + e1[1] * c23[1]) + e1[2] * c23[2]);
-            double r[3][3];
             for (int q = 0; q < 3; ++q) {
-                r[0][q] = c23[q] * inv; r[1][q] = c31[q] * inv; r[2][q] = c12[q] * inv;
+                R[0][q] = c23[q] * inv; R[1][q] = c31[q] * inv; R[2][q] = c12[q] * inv;
             }
-            const double dx = X[0] - a[0], dy = X[1] - a[1], dz = X[2] - a[2];
-            double m[3];
-            for (int q = 0; q < 3; ++q)
-                m[q] = fma(r[q][2], dz, fma(r[q][1], dy, r[q][0] * dx));
-            mu[0] = ((1.0 - m[0]) - m[1]) - m[2];
-            mu[1] = m[0]; mu[2] = m[1]; mu[3] = m[2];
         }
+    }
+}
+
+/* barycentric coordinates of X in element e, evaluated in precision P with
+ * fused multiply-adds in a fixed order from the inverse map above */
+static void predicate_mu(int prec, int dim, const double* coords, const int32_t* conn,
+                         int32_t e, const double* X, double* mu)
+{
+    double x0[3], R[3][3];
+    inverse_map(prec, dim, coords, conn, e, x0, R);
+    if (prec == 1) {
+        float dx[3], m[3];
+        for (int q = 0; q < dim; ++q) dx[q] = (float)X[q] - (float)x0[q];
+        float s = 1.0f;
+        for (int r = 0; r < dim; ++r) {
+            float t = (float)R[r][0] * dx[0];
+            for (int q = 1; q < dim; ++q) t = fmaf((float)R[r][q], dx[q], t);
+            m[r] = t;
+            s = s - t;
+        }
+        mu[0] = s;
+        for (int r = 0; r < dim; ++r) mu[r + 1] = m[r];
+    } else {
+        double dx[3], m[3];
+        for (int q = 0; q < dim; ++q) dx[q] = X[q] - x0[q];
+        double s = 1.0;
+        for (int r = 0; r < dim; ++r) {
+            double t = R[r][0] * dx[0];
+            for (int q = 1; q < dim; ++q) t = fma(R[r][q], dx[q], t);
+            m[r] = t;
+            s = s - t;
+        }
+        mu[0] = s;
+        for (int r = 0; r < dim; ++r) mu[r + 1] = m[r];
+    }
+}
+
+/* Registration test: can the cell box (centre c, half widths w, P values)
+ * contain a point of element e? For each barycentric coordinate, which is an
+ * affine function, its largest value over the box is its value at the
+ * centre plus sum_a |gradient_a| w_a; the element is left out of the cell
+ * when that largest value is below -2^-10 for some coordinate (the box lies
+ * outside that face plane by a margin far above the rounding of the
+ * predicate). Evaluated in P in a fixed order. */
+static int cell_may_hold(const orc_grid* g, int32_t e, const double* c, const double* w)
+{
+    const int dim = g->dim;
+    double x0[3], R[3][3];
+    inverse_map(g->prec, dim, g->coords, g->conn, e, x0, R);
+    if (g->prec == 1) {
+        const float eps = 0x1p-10f;
+        float d[3], s[3] = {0, 0, 0}, tsum = 0.0f;
+        for (int a = 0; a < dim; ++a) d[a] = (float)c[a] - (float)x0[a];
+        for (int m = 0; m < dim; ++m) {
+            float t = (float)R[m][0] * d[0];
+            float sp = fabsf((float)R[m][0]) * (float)w[0];
+            for (int a = 1; a < dim; ++a) {
+                t = fmaf((float)R[m][a], d[a], t);
+                sp = fmaf(fabsf((float)R[m][a]), (float)w[a], sp);
+            }
+            if (t + sp < -eps) return 0;
+            tsum = m == 0 ? t : tsum + t;
+            for (int a = 0; a < dim; ++a) s[a] = m == 0 ? (float)R[m][a] : s[a] + (float)R[m][a];
+        }
+        float S = fabsf(s[0]) * (float)w[0];
+        for (int a = 1; a < dim; ++a) S = fmaf(fabsf(s[a]), (float)w[a], S);
+        return !((1.0f - tsum) + S < -eps);
+    } else {
+        const double eps = 0x1p-10;
+        double d[3], s[3] = {0, 0, 0}, tsum = 0.0;
+        for (int a = 0; a < dim; ++a) d[a] = c[a] - x0[a];
+        for (int m = 0; m < dim; ++m) {
+            double t = R[m][0] * d[0];
+            double sp = fabs(R[m][0]) * w[0];
+            for (int a = 1; a < dim; ++a) {
+                t = fma(R[m][a], d[a], t);
+                sp = fma(fabs(R[m][a]), w[a], sp);
+            }
+            if (t + sp < -eps) return 0;
+            tsum = m == 0 ? t : tsum + t;
+            for (int a = 0; a < dim; ++a) s[a] = m == 0 ? R[m][a] : s[a] + R[m][a];
+        }
+        double S = fabs(s[0]) * w[0];
+        for (int a = 1; a < dim; ++a) S = fma(fabs(s[a]), w[a], S);
+        return !((1.0 - tsum) + S < -eps);
     }
 }
 
@@ -301,6 +365,13 @@ orc_grid* orc_grid_build(int prec, int dim, int64_t nv, const double* coords,
             for (int32_t iz = c0[2]; iz <= c1[2]; ++iz)
                 for (int32_t iy = c0[1]; iy <= c1[1]; ++iy)
                     for (int32_t ix = c0[0]; ix <= c1[0]; ++ix) {
+                        const int32_t idx[3] = {ix, iy, iz};
+                        double cc[3] = {0, 0, 0}, ww[3] = {0, 0, 0};
+                        for (int a = 0; a < dim; ++a) {
+                            cc[a] = cell_centre(g, a, idx[a]);
+                            ww[a] = 0.5 * g->h[a];
+                        }
+                        if (!cell_may_hold(g, (int32_t)e, cc, ww)) continue;
                         const int64_t cell = ((int64_t)iz * g->n[1] + iy) * g->n[0] + ix;
                         if (pass == 0) count[cell + 1]++;
                         else g->items[g->start[cell] + count[cell]++] = (int32_t)e;

@@ -75,7 +75,7 @@ template <> struct Epi<double> {
 };
 
 template <int D, typename P, int NF, bool DBG>
-__global__ void __launch_bounds__(256) k_assemble(const P* __restrict__ tx, const int32_t* __restrict__ tconn,
+__global__ void __launch_bounds__(256, D == 2 ? 4 : 3) k_assemble(const P* __restrict__ tx, const int32_t* __restrict__ tconn,
                                                   const double* __restrict__ vol, const float* __restrict__ vol32,
                                                   const P* __restrict__ g,
                                                   const GridP<P>* __restrict__ gp,

@@ -238,10 +238,9 @@ __device__ __forceinline__ bool record_map(const P xv[D + 1][D], P* r) {
 
 template <int D, typename P, typename TV>
 __global__ void k_records(const P* __restrict__ x, const int32_t* __restrict__ conn, const TV* __restrict__ values,
-                          int64_t nv, int64_t ne, int nf, const GridP<P>* __restrict__ gp, P* __restrict__ recs,
-                          P* __restrict__ vals, int32_t* __restrict__ counts, int32_t* err) {
+                          int64_t nv, int64_t ne, int nf, P* __restrict__ recs, P* __restrict__ vals, int32_t* err) {
   constexpr int L = RecLen<D>::value;
-  const GridP<P> g = *gp;
+  
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
     int32_t v[D + 1];
     bool ok = true;
@@ -252,7 +251,6 @@ __global__ void k_records(const P* __restrict__ x, const int32_t* __restrict__ c
     }
     if (!ok) {
       set_error(err, DEV_BAD_INDEX);
-      counts[e] = 0;
       continue;
     }
     P xv[D + 1][D];
@@ -270,77 +268,140 @@ __global__ void k_records(const P* __restrict__ x, const int32_t* __restrict__ c
       for (int m = 0; m < 4; ++m)
         vals[((int64_t)f * ne + e) * 4 + m] = m <= D ? P(values[(int64_t)f * nv + v[m]]) : P(0);
     }
-    int32_t c0[3], c1[3];
-    counts[e] = (int32_t)elem_cell_range<D, P>(g, xv, c0, c1);
   }
 }
 
-// one registration per (element, cell): count or fill
+// centre of cell index i along axis a: lo + (i + 1/2) h as one FMA in P
+template <typename P>
+__device__ __forceinline__ P cell_centre(const GridP<P>& g, int a, int32_t i) {
+  return Ar<P>::fma(Ar<P>::add((P)i, P(0.5)), g.h[a], g.lo[a]);
+}
+
+// Can the cell box (centre c, half widths w) hold a point of the element with
+// location record r? Each barycentric coordinate is affine; its largest value
+// over the box is its value at the centre plus sum_a |gradient_a| w_a. The
+// element is left out when that value is below -2^-10 for some coordinate
+// (the box lies outside a face plane by a margin far above the predicate's
+// rounding, so the test never drops an element a point of the cell could be
+// accepted by). Fixed evaluation order in P.
+template <int D, typename P>
+__device__ __forceinline__ bool cell_may_hold(const P* r, const P c[D], const P w[D]) {
+  using A = Ar<P>;
+  const P eps = P(0.0009765625);
+  P d[D], s[D], tsum = P(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) d[a] = A::sub(c[a], r[a]);
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    const P* row = r + D + m * D;
+    P t = A::mul(row[0], d[0]);
+    P sp = A::mul(row[0] < P(0) ? -row[0] : row[0], w[0]);
+#pragma unroll
+    for (int a = 1; a < D; ++a) {
+      t = A::fma(row[a], d[a], t);
+      sp = A::fma(row[a] < P(0) ? -row[a] : row[a], w[a], sp);
+    }
+    if (A::add(t, sp) < -eps) return false;
+    tsum = m == 0 ? t : A::add(tsum, t);
+#pragma unroll
+    for (int a = 0; a < D; ++a) s[a] = m == 0 ? row[a] : A::add(s[a], row[a]);
+  }
+  P S = A::mul(s[0] < P(0) ? -s[0] : s[0], w[0]);
+#pragma unroll
+  for (int a = 1; a < D; ++a) S = A::fma(s[a] < P(0) ? -s[a] : s[a], w[a], S);
+  return !(A::add(A::sub(P(1), tsum), S) < -eps);
+}
+
+// one registration per (element, cell) that passes cell_may_hold: count, or
+// fill the element id and the cell id
 template <int D, typename P, bool FILL>
-__global__ void k_register(const P* __restrict__ x, const int32_t* __restrict__ conn, int64_t ne,
-                           const GridP<P>* __restrict__ gp, int32_t* __restrict__ cell_count,
-                           const int32_t* __restrict__ cell_start, int32_t* __restrict__ items) {
+__global__ void k_register(const P* __restrict__ x, const int32_t* __restrict__ conn, const P* __restrict__ recs,
+                           int64_t nv, int64_t ne, const GridP<P>* __restrict__ gp, int32_t* __restrict__ cell_count,
+                           const int32_t* __restrict__ cell_start, int32_t* __restrict__ items,
+                           int32_t* __restrict__ item_cell) {
+  constexpr int RL = RecLen<D>::value;
   const GridP<P> g = *gp;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+    bool ok = true;
+#pragma unroll
+    for (int m = 0; m <= D; ++m) {
+      const int32_t v = conn[e * (D + 1) + m];
+      ok = ok && v >= 0 && v < nv;
+    }
+    if (!ok) continue;  // reported by k_records; never read out of range
     P xv[D + 1][D];
     elem_vertices<D, P>(x, conn, e, xv);
     int32_t c0[3], c1[3];
     elem_cell_range<D, P>(g, xv, c0, c1);
+    P r[RL];
+    load_record<D, P>(recs, (int32_t)e, r);
+    P w[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) w[a] = Ar<P>::mul(g.h[a], P(0.5));
     for (int32_t iz = c0[2]; iz <= c1[2]; ++iz)
       for (int32_t iy = c0[1]; iy <= c1[1]; ++iy)
         for (int32_t ix = c0[0]; ix <= c1[0]; ++ix) {
+          const int32_t idx[3] = {ix, iy, iz};
+          P cc[D];
+#pragma unroll
+          for (int a = 0; a < D; ++a) cc[a] = cell_centre<P>(g, a, idx[a]);
+          if (!cell_may_hold<D, P>(r, cc, w)) continue;
           const int64_t c = ((int64_t)iz * g.n[1] + iy) * g.n[0] + ix;
           const int32_t pos = atomicAdd(cell_count + c, 1);
-          if (FILL) items[cell_start[c] + pos] = (int32_t)e;
+          if (FILL) {
+            items[cell_start[c] + pos] = (int32_t)e;
+            item_cell[cell_start[c] + pos] = (int32_t)c;
+          }
         }
   }
 }
 
-// Order each cell's list (built in arbitrary order by the atomic fill):
-// decreasing depth of the cell centre in the element (the predicate's min
-// barycentric coordinate there), ties by ascending element id. Insertion
-// sort over the cell's entries (cells are short), with their depths in a
-// scratch array.
+// Order of each cell's list (the atomic fill leaves it arbitrary): decreasing
+// depth of the cell centre in the element (its min barycentric coordinate
+// there), ties by ascending element id. One thread per registration computes
+// its depth, then its rank among the cell's entries, and scatters itself.
 template <int D, typename P>
-__global__ void k_order_cells(const GridP<P>* __restrict__ gp, const int32_t* __restrict__ cell_start,
-                              int32_t* __restrict__ items, P* __restrict__ depth, const P* __restrict__ recs,
-                              int64_t ncells) {
-  using A = Ar<P>;
+__global__ void k_item_depth(const GridP<P>* __restrict__ gp, const int32_t* __restrict__ items,
+                             const int32_t* __restrict__ item_cell, const P* __restrict__ recs, int64_t nitems,
+                             P* __restrict__ depth) {
   constexpr int L = RecLen<D>::value;
   const GridP<P> g = *gp;
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t p0 = cell_start[c], p1 = cell_start[c + 1];
-    if (p1 - p0 < 2) continue;
-    int64_t rem = c;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nitems; p += (int64_t)gridDim.x * blockDim.x) {
+    int64_t rem = item_cell[p];
     P X[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       const int32_t i = (int32_t)(rem % g.n[a]);
       rem /= g.n[a];
-      X[a] = A::fma(A::add((P)i, P(0.5)), g.h[a], g.lo[a]);
+      X[a] = cell_centre<P>(g, a, i);
     }
-    for (int32_t p = p0; p < p1; ++p) {
-      P r[L];
-      load_record<D, P>(recs, items[p], r);
-      P mu[D + 1];
-      bary_from_record<D, P>(r, X, mu);
-      P mn = mu[0];
+    P r[L];
+    load_record<D, P>(recs, items[p], r);
+    P mu[D + 1];
+    bary_from_record<D, P>(r, X, mu);
+    P mn = mu[0];
 #pragma unroll
-      for (int q = 1; q <= D; ++q) mn = mu[q] < mn ? mu[q] : mn;
-      depth[p] = mn;
+    for (int q = 1; q <= D; ++q) mn = mu[q] < mn ? mu[q] : mn;
+    depth[p] = mn;
+  }
+}
+
+template <typename P>
+__global__ void k_item_rank(const int32_t* __restrict__ cell_start, const int32_t* __restrict__ item_cell,
+                            const int32_t* __restrict__ items, const P* __restrict__ depth, int64_t nitems,
+                            int32_t* __restrict__ out) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nitems; p += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = item_cell[p];
+    const int32_t p0 = cell_start[c], p1 = cell_start[c + 1];
+    const P dp = depth[p];
+    const int32_t ip = items[p];
+    int32_t rank = 0;
+    for (int32_t q = p0; q < p1; ++q) {
+      const P dq = depth[q];
+      const int32_t iq = items[q];
+      rank += (dq > dp) || (dq == dp && iq < ip);
     }
-    for (int32_t p = p0 + 1; p < p1; ++p) {
-      const P ks = depth[p];
-      const int32_t ki = items[p];
-      int32_t q = p - 1;
-      while (q >= p0 && (depth[q] < ks || (depth[q] == ks && items[q] > ki))) {
-        depth[q + 1] = depth[q];
-        items[q + 1] = items[q];
-        --q;
-      }
-      depth[q + 1] = ks;
-      items[q + 1] = ki;
-    }
+    out[p0 + rank] = ip;
   }
 }
 
@@ -376,61 +437,66 @@ static sft_status build_locator_t(sft_source_s* s, int prec, cudaStream_t st, in
   ::sft::note_launch(), k_grid_params<D, P><<<1, 32, 0, st>>>(part, nb, n, g, d_err);
   SFT_CUDA(cudaGetLastError());
   dfree(part, st);
-  // records, value copies, per-element registration counts
+  // location records and value copies
   P* recs = nullptr;
   P* vals = nullptr;
-  int32_t* counts = nullptr;
   SFT_CUDA(dalloc(&recs, (size_t)s->ne * RL, st));
   SFT_CUDA(dalloc(&vals, (size_t)s->nf * s->ne * 4, st));
-  SFT_CUDA(dalloc(&counts, (size_t)s->ne, st));
   L.recs = recs;
   L.vals = vals;
   if (s->dtype == SFT_F64)
     ::sft::note_launch(), k_records<D, P, double><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, (const double*)s->values, s->nv, s->ne,
-                                                             s->nf, g, recs, vals, counts, d_err);
+                                                             s->nf, recs, vals, d_err);
   else
     ::sft::note_launch(), k_records<D, P, float><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, (const float*)s->values, s->nv, s->ne,
-                                                            s->nf, g, recs, vals, counts, d_err);
+                                                            s->nf, recs, vals, d_err);
   SFT_CUDA(cudaGetLastError());
-  int32_t herr = 0;
-  SFT_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  // total registrations (int64) -> check that int32 offsets suffice
-  int64_t* eoff = nullptr;
-  SFT_CUDA(dalloc(&eoff, (size_t)s->ne + 1, st));
-  SFT_CUDA(exclusive_scan_i32_to_i64(counts, eoff, s->ne, st));
-  int64_t total = 0;
-  SFT_CUDA(cudaMemcpyAsync(&total, eoff + s->ne, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-  SFT_CUDA(cudaStreamSynchronize(st));
-  dfree(eoff, st);
-  dfree(counts, st);
-  if (herr != 0)
-    return fail(SFT_ERR_MESH, herr == DEV_BAD_INDEX ? "source connectivity index out of range"
-                                                    : "source mesh has a non-positive element or a degenerate box");
-  if (total >= (int64_t)INT32_MAX) return fail(SFT_ERR_UNSUPPORTED, "grid registrations exceed 2^31");
-  L.nitems = total;
-  // counting sort by cell
+  // count registrations per cell, then total (int64) -> int32 offsets must suffice
   int32_t* cell_count = nullptr;
   int64_t* start64 = nullptr;
   SFT_CUDA(dalloc(&cell_count, (size_t)L.ncells, st));
   SFT_CUDA(dalloc(&start64, (size_t)L.ncells + 1, st));
-  SFT_CUDA(dalloc(&L.cell_start, (size_t)L.ncells + 1, st));
-  SFT_CUDA(dalloc(&L.cell_items, (size_t)total, st));
   SFT_CUDA(cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * L.ncells, st));
-  ::sft::note_launch(), k_register<D, P, false><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, s->ne, g, cell_count, nullptr, nullptr);
+  ::sft::note_launch(), k_register<D, P, false><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, recs, s->nv, s->ne, g, cell_count,
+                                                                               nullptr, nullptr, nullptr);
   SFT_CUDA(cudaGetLastError());
   SFT_CUDA(exclusive_scan_i32_to_i64(cell_count, start64, L.ncells, st));
+  int32_t herr = 0;
+  int64_t total = 0;
+  SFT_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  SFT_CUDA(cudaMemcpyAsync(&total, start64 + L.ncells, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  SFT_CUDA(cudaStreamSynchronize(st));
+  if (herr != 0) {
+    dfree(cell_count, st);
+    dfree(start64, st);
+    return fail(SFT_ERR_MESH, herr == DEV_BAD_INDEX ? "source connectivity index out of range"
+                                                    : "source mesh has a non-positive element or a degenerate box");
+  }
+  if (total >= (int64_t)INT32_MAX) return fail(SFT_ERR_UNSUPPORTED, "grid registrations exceed 2^31");
+  L.nitems = total;
+  SFT_CUDA(dalloc(&L.cell_start, (size_t)L.ncells + 1, st));
   SFT_CUDA(narrow_i64_to_i32(start64, L.cell_start, L.ncells + 1, st));
-  SFT_CUDA(cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * L.ncells, st));
-  ::sft::note_launch(), k_register<D, P, true><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, s->ne, g, cell_count, L.cell_start, L.cell_items);
-  SFT_CUDA(cudaGetLastError());
-  P* depth = nullptr;
-  SFT_CUDA(dalloc(&depth, (size_t)total, st));
-  ::sft::note_launch(), k_order_cells<D, P><<<grid_for(L.ncells), 256, 0, st>>>(g, L.cell_start, L.cell_items, depth,
-                                                                              recs, L.ncells);
-  SFT_CUDA(cudaGetLastError());
-  dfree(depth, st);
-  dfree(cell_count, st);
   dfree(start64, st);
+  // fill (arbitrary order within a cell), then order each cell
+  int32_t *items = nullptr, *item_cell = nullptr;
+  P* depth = nullptr;
+  SFT_CUDA(dalloc(&items, (size_t)total, st));
+  SFT_CUDA(dalloc(&item_cell, (size_t)total, st));
+  SFT_CUDA(dalloc(&depth, (size_t)total, st));
+  SFT_CUDA(dalloc(&L.cell_items, (size_t)total, st));
+  SFT_CUDA(cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * L.ncells, st));
+  ::sft::note_launch(), k_register<D, P, true><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, recs, s->nv, s->ne, g, cell_count,
+                                                                              L.cell_start, items, item_cell);
+  SFT_CUDA(cudaGetLastError());
+  ::sft::note_launch(), k_item_depth<D, P><<<grid_for(total), 256, 0, st>>>(g, items, item_cell, recs, total, depth);
+  SFT_CUDA(cudaGetLastError());
+  ::sft::note_launch(), k_item_rank<P><<<grid_for(total), 256, 0, st>>>(L.cell_start, item_cell, items, depth, total,
+                                                                       L.cell_items);
+  SFT_CUDA(cudaGetLastError());
+  dfree(cell_count, st);
+  dfree(items, st);
+  dfree(item_cell, st);
+  dfree(depth, st);
   L.built = true;
   return SFT_OK;
 }

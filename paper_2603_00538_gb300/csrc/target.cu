@@ -58,27 +58,31 @@ __global__ void k_volumes(const TI* __restrict__ x, const int32_t* __restrict__ 
   }
 }
 
+// node -> element incidence, filled in arbitrary order (atomic cursor) with
+// the node of every entry, then put in ascending element order by rank
 template <int D>
 __global__ void k_inc_fill(const int32_t* __restrict__ conn, int64_t ne, const int32_t* __restrict__ inc_start,
-                           int32_t* __restrict__ cursor, int32_t* __restrict__ inc) {
+                           int32_t* __restrict__ cursor, int32_t* __restrict__ inc, int32_t* __restrict__ inc_node) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
     for (int m = 0; m <= D; ++m) {
       const int32_t v = conn[e * (D + 1) + m];
-      inc[inc_start[v] + atomicAdd(cursor + v, 1)] = (int32_t)e;
+      const int32_t pos = inc_start[v] + atomicAdd(cursor + v, 1);
+      inc[pos] = (int32_t)e;
+      inc_node[pos] = v;
     }
   }
 }
 
-__global__ void k_inc_sort(const int32_t* __restrict__ inc_start, int32_t* __restrict__ inc, int64_t nv) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t p0 = inc_start[i], p1 = inc_start[i + 1];
-    for (int32_t a = p0 + 1; a < p1; ++a) {
-      const int32_t key = inc[a];
-      int32_t b = a - 1;
-      while (b >= p0 && inc[b] > key) { inc[b + 1] = inc[b]; --b; }
-      inc[b + 1] = key;
-    }
+__global__ void k_inc_rank(const int32_t* __restrict__ inc_start, const int32_t* __restrict__ inc,
+                           const int32_t* __restrict__ inc_node, int64_t n, int32_t* __restrict__ out) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = inc_node[p];
+    const int32_t p0 = inc_start[v], p1 = inc_start[v + 1];
+    const int32_t e = inc[p];
+    int32_t rank = 0;
+    for (int32_t q = p0; q < p1; ++q) rank += inc[q] < e;
+    out[p0 + rank] = e;
   }
 }
 
@@ -171,13 +175,20 @@ static sft_status build_target_t(sft_target_s* t, cudaStream_t st, int32_t* d_er
   SFT_CUDA(dalloc(&off64, (size_t)t->nv + 1, st));
   SFT_CUDA(dalloc(&inc_start, (size_t)t->nv + 1, st));
   SFT_CUDA(dalloc(&inc, (size_t)t->ne * (D + 1), st));
+  int32_t *inc_raw = nullptr, *inc_node = nullptr;
+  SFT_CUDA(dalloc(&inc_raw, (size_t)t->ne * (D + 1), st));
+  SFT_CUDA(dalloc(&inc_node, (size_t)t->ne * (D + 1), st));
   SFT_CUDA(exclusive_scan_i32_to_i64(inc_count, off64, t->nv, st));
   SFT_CUDA(narrow_i64_to_i32(off64, inc_start, t->nv + 1, st));
   SFT_CUDA(cudaMemsetAsync(inc_count, 0, sizeof(int32_t) * t->nv, st));
-  ::sft::note_launch(), k_inc_fill<D><<<blocks_for(t->ne), 256, 0, st>>>(t->conn, t->ne, inc_start, inc_count, inc);
+  ::sft::note_launch(), k_inc_fill<D><<<blocks_for(t->ne), 256, 0, st>>>(t->conn, t->ne, inc_start, inc_count, inc_raw,
+                                                                       inc_node);
   SFT_CUDA(cudaGetLastError());
-  ::sft::note_launch(), k_inc_sort<<<blocks_for(t->nv), 256, 0, st>>>(inc_start, inc, t->nv);
+  ::sft::note_launch(), k_inc_rank<<<blocks_for(t->ne * (D + 1)), 256, 0, st>>>(inc_start, inc_raw, inc_node,
+                                                                               t->ne * (D + 1), inc);
   SFT_CUDA(cudaGetLastError());
+  dfree(inc_raw, st);
+  dfree(inc_node, st);
   row_len = inc_count;  // reuse
   ::sft::note_launch(), k_mass_rows<D, false><<<blocks_for(t->nv), 256, 0, st>>>(t->conn, wfac, inc_start, inc, t->nv, row_len, nullptr,
                                                            nullptr, nullptr, nullptr, nullptr, d_err);

@@ -223,16 +223,44 @@ def test_grid_structure(orc, dim):
         assert np.all((np.diff(dep) < 0) | ((np.diff(dep) == 0) & (np.diff(seg) > 0)))
         assert len(seg) == len(set(seg.tolist()))
         assert dep[0] >= 0.0
-    # every element appears in exactly the cells of its bounding box
+    # registration: listed cells lie in the element's bounding-box range; a
+    # bounding-box cell is left out only if a face plane separates it from
+    # the element (checked exactly at the box corners); random points of the
+    # element land in cells that list it
     lo = src.coords.min(0)
     hi = src.coords.max(0)
-    counts = np.bincount(items, minlength=E)
+    h = (hi - lo) / expect_n
+    cell_of_item = np.repeat(np.arange(nc), np.diff(start))
+    listed = {}
+    for c, e in zip(cell_of_item, items):
+        listed.setdefault(int(e), set()).add(int(c))
+    rng = np.random.default_rng(5)
+    import itertools
     for e in range(E):
         bb0 = src.coords[src.conn[e]].min(0)
         bb1 = src.coords[src.conn[e]].max(0)
-        c0 = np.clip(np.floor((bb0 - lo) * (expect_n / (hi - lo))), 0, expect_n - 1)
-        c1 = np.clip(np.floor((bb1 - lo) * (expect_n / (hi - lo))), 0, expect_n - 1)
-        assert counts[e] == int(np.prod(c1 - c0 + 1))
+        c0 = np.clip(np.floor((bb0 - lo) * (expect_n / (hi - lo))), 0, expect_n - 1).astype(int)
+        c1 = np.clip(np.floor((bb1 - lo) * (expect_n / (hi - lo))), 0, expect_n - 1).astype(int)
+        box_cells = set()
+        for idx in itertools.product(*[range(c0[a], c1[a] + 1) for a in range(dim)]):
+            flat = 0
+            for a in reversed(range(dim)):
+                flat = flat * expect_n + idx[a]
+            box_cells.add(flat)
+            if flat in listed.get(e, set()):
+                continue
+            corners = [lo + (np.array(idx) + np.array(off)) * h for off in itertools.product((0, 1), repeat=dim)]
+            mus = np.array([_exact_bary(src.coords, src.conn, e, x) for x in corners], dtype=object)
+            assert any(all(mus[:, m] < 0) for m in range(dim + 1)), (e, idx)
+        assert listed.get(e, set()) <= box_cells
+        w = rng.dirichlet(np.ones(dim + 1), 20)
+        pts = w @ src.coords[src.conn[e]]
+        ci = np.clip(np.floor((pts - lo) / h), 0, expect_n - 1).astype(int)
+        for row in ci:
+            flat = 0
+            for a in reversed(range(dim)):
+                flat = flat * expect_n + row[a]
+            assert flat in listed[e]
 
 
 # --------------------------------------------------------------------------
