@@ -28,6 +28,7 @@ extern "C" {
 
 typedef struct sft_source_s* sft_source;
 typedef struct sft_target_s* sft_target;
+typedef struct sft_batch_s* sft_batch;
 
 typedef enum {
     SFT_OK = 0,
@@ -79,6 +80,8 @@ typedef struct {
     int32_t out_device;         /* 1: u_out, b_out, g_out, sample_elem_out are device pointers */
     void* cuda_stream;          /* cudaStream_t */
     int32_t* sample_elem_out;   /* optional [nelems][N]: source element located for every sample */
+    int32_t field_count;        /* 0: every source field; k > 0: the first k fields only */
+    int32_t reserved;
 } sft_options;
 
 typedef struct {
@@ -119,6 +122,7 @@ void sft_target_destroy(sft_target tgt);
  *   b_i = alpha int g psi_i  +  sum_t |T|/N sum_j (f^s - alpha g)(X_tj) psi_i(X_tj)
  *         with X_tj uniform in t from Philox4x32-10 (steps 2-6);
  *   M u = b by Jacobi-preconditioned CG from u = 0 (step 7).
+ * nfields = opt->field_count if > 0, else the source's field count.
  * u_out [nfields][nnodes_target] FP64 (required); b_out, g_out same shape,
  * optional (NULL). u_out is written on SFT_OK and SFT_ERR_NOT_CONVERGED.
  * stats may be NULL. Synchronises opt->cuda_stream before returning. */
@@ -148,6 +152,47 @@ sft_status sft_locate(sft_source src, int32_t precision, int64_t n, const double
 sft_status sft_mass_solve(sft_target tgt, int32_t nrhs, const double* b, double* u,
                           int32_t device_ptrs, double tol, int32_t max_iter, void* cuda_stream,
                           int32_t* iters_out, double* rel_resid_out);
+
+/* ---- batched transfers ----
+ * Many requests (source, target, options) of uneven size run together: the
+ * paper's per-request method (Sec. 4 steps 1-7) is unchanged; batching has no
+ * counterpart in the paper. The plan groups requests by dimension and field
+ * count, and records one CUDA graph: control values of every request, a
+ * persistent fused assembly per group (warps pull (request, element-tile)
+ * work items from an atomic counter), and one cooperative FP64 CG over the
+ * block-diagonal system of every (request, field) right-hand side. */
+typedef struct {
+    int32_t nreq;
+    int32_t graph;              /* 1: runs replay a captured CUDA graph; 0: direct launches */
+    int32_t max_cg_iters;       /* over all (request, field) systems */
+    int32_t nonconverged;       /* systems that reached their iteration cap */
+    double max_rel_resid;
+    int64_t queries;            /* all source queries of the batch */
+    int64_t fallback_queries;
+    int64_t empty_queries;
+    float ms_control, ms_assembly, ms_solve, ms_total;  /* device time of the last run */
+    int32_t tile[6];            /* work-item tile per group (2D, 3D) x (fields <= 2, <= 4, <= 8); 0: empty */
+} sft_batch_stats;
+
+/* Build a batch plan. srcs/tgts/opts are arrays of nreq (1..4096) entries;
+ * every request must use precision SFT_PREC_FP32 (SFT_ERR_UNSUPPORTED
+ * otherwise); field_count selects the first k source fields. The handles
+ * must outlive the plan. autotune = 1 times trial launches of each group's
+ * assembly (tiles 1..16 work items per pull) and keeps the fastest; results
+ * are cached per process and, if the environment variable
+ * SFT_AUTOTUNE_CACHE names a file, in that file. Synchronises cuda_stream. */
+sft_status sft_batch_create(int32_t nreq, const sft_source* srcs, const sft_target* tgts,
+                            const sft_options* opts, int32_t autotune, void* cuda_stream,
+                            sft_batch* out);
+/* Run every request of the plan (stream NULL: the plan's stream) and wait.
+ * stats may be NULL. Returns SFT_ERR_NOT_CONVERGED if a system reached its
+ * cap (its last iterate is kept). */
+sft_status sft_batch_run(sft_batch b, void* cuda_stream, sft_batch_stats* stats);
+/* Copy request req's solution (and optionally load vector) [nfields][nnodes]
+ * of the last run to u_out / b_out (device pointers if out_device). */
+sft_status sft_batch_result(sft_batch b, int32_t req, double* u_out, double* b_out, int32_t out_device,
+                            void* cuda_stream);
+void sft_batch_destroy(sft_batch b);
 
 /* Allocation-free solve of M u = b for callers that cannot allocate device
  * memory at solve time (for example a coupled code whose memory pool owns

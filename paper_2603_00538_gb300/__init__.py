@@ -45,7 +45,8 @@ class sft_options(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint32), ("cg_max_iter", ctypes.c_int32),
                 ("alpha", ctypes.c_double), ("cg_tol", ctypes.c_double), ("strict_inside", ctypes.c_int32),
                 ("out_device", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
-                ("sample_elem_out", ctypes.c_void_p)]
+                ("sample_elem_out", ctypes.c_void_p), ("field_count", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class sft_stats(ctypes.Structure):
@@ -57,6 +58,20 @@ class sft_stats(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
+
+
+class sft_batch_stats(ctypes.Structure):
+    _fields_ = [("nreq", ctypes.c_int32), ("graph", ctypes.c_int32), ("max_cg_iters", ctypes.c_int32),
+                ("nonconverged", ctypes.c_int32), ("max_rel_resid", ctypes.c_double),
+                ("queries", ctypes.c_int64), ("fallback_queries", ctypes.c_int64),
+                ("empty_queries", ctypes.c_int64), ("ms_control", ctypes.c_float),
+                ("ms_assembly", ctypes.c_float), ("ms_solve", ctypes.c_float), ("ms_total", ctypes.c_float),
+                ("tile", ctypes.c_int32 * 6)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "tile"}
+        d["tile"] = list(self.tile)
+        return d
 
 
 _vp, _i32, _i64, _d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
@@ -74,6 +89,10 @@ _SIGS = {
     "sft_status_str": ([_i32], ctypes.c_char_p),
     "sft_last_error": ([], ctypes.c_char_p),
     "sft_kernel_launches": ([], _i64),
+    "sft_batch_create": ([_i32, _vp, _vp, _vp, _i32, _vp, _vp], _i32),
+    "sft_batch_run": ([_vp, _vp, ctypes.POINTER(sft_batch_stats)], _i32),
+    "sft_batch_result": ([_vp, _i32, _vp, _vp, _i32, _vp], _i32),
+    "sft_batch_destroy": ([_vp], None),
     "sft_mass_solve_static": ([_i64, _vp, _vp, _vp, _i32, _vp, _vp, _d, _i32, _vp, _vp, _vp], _i32),
 }
 EXPORTS = tuple(_SIGS)
@@ -220,11 +239,11 @@ def sft_target_destroy(tgt: Target):
 def sft_transfer(src: Source, tgt: Target, samples_per_elem: int, precision: int = SFT_PREC_FP32,
                  seed: int = 0, stream_id: int = 0, alpha: float = 1.0, cg_tol: float = 1e-10,
                  cg_max_iter: int = 1000, strict_inside: bool = False, u_out=None, b_out=None, g_out=None,
-                 sample_elem_out=None, stream=None, allow_not_converged: bool = False):
+                 sample_elem_out=None, stream=None, allow_not_converged: bool = False, field_count: int = 0):
     """Run one transfer. Outputs are caller-provided arrays (numpy for host,
     torch CUDA tensors for device); when u_out is None a host array
     [nfields, nnodes] is allocated. Returns (status, stats dict, u_out)."""
-    nf = _nf(src)
+    nf = int(field_count) if field_count > 0 else _nf(src)
     if u_out is None:
         u_out = np.zeros((nf, _nv(tgt)), np.float64)
     up, udev, _ = _ptr(u_out)
@@ -246,6 +265,7 @@ def sft_transfer(src: Source, tgt: Target, samples_per_elem: int, precision: int
     o.out_device = int(udev)
     o.cuda_stream = stream if stream is not None else _current_stream()
     o.sample_elem_out = sp
+    o.field_count = int(field_count)
     st = sft_stats()
     allow = (SFT_OK, SFT_ERR_NOT_CONVERGED) if allow_not_converged else (SFT_OK,)
     status = _check(lib().sft_transfer(src.h, tgt.h, ctypes.byref(o), up, bp, gp, ctypes.byref(st)),
@@ -310,6 +330,62 @@ def sft_mass_solve_static(row_ptr, col, val, b, u_out, tol=1e-12, max_iter=1000,
                                        stream if stream is not None else _current_stream(),
                                        ctypes.byref(it), ctypes.byref(rr)), "sft_mass_solve_static")
     return it.value, rr.value
+
+
+class Batch(_Handle):
+    pass
+
+
+def _options(samples_per_elem, seed=0, stream_id=0, alpha=1.0, cg_tol=1e-10, cg_max_iter=1000,
+             field_count=0, precision=SFT_PREC_FP32):
+    o = sft_options()
+    o.samples_per_elem = int(samples_per_elem)
+    o.precision = int(precision)
+    o.seed = int(seed)
+    o.stream_id = int(stream_id)
+    o.cg_max_iter = int(cg_max_iter)
+    o.alpha = float(alpha)
+    o.cg_tol = float(cg_tol)
+    o.field_count = int(field_count)
+    return o
+
+
+def sft_batch_create(sources, targets, options, autotune=True, stream=None) -> Batch:
+    """Plan of len(sources) transfers; options: list of dicts for _options()."""
+    n = len(sources)
+    srcs = (ctypes.c_void_p * n)(*[s.h for s in sources])
+    tgts = (ctypes.c_void_p * n)(*[t.h for t in targets])
+    opts = (sft_options * n)(*[_options(**o) for o in options])
+    h = _vp()
+    _check(lib().sft_batch_create(n, srcs, tgts, opts, int(bool(autotune)),
+                                  stream if stream is not None else _current_stream(), ctypes.byref(h)),
+           "sft_batch_create")
+    b = Batch(h.value, lib().sft_batch_destroy, (list(sources), list(targets)))
+    b.nfields = [int(o.get("field_count", 0)) or _nf(s) for o, s in zip(options, sources)]
+    b.nnodes = [_nv(t) for t in targets]
+    return b
+
+
+def sft_batch_run(batch: Batch, stream=None, allow_not_converged=False):
+    st = sft_batch_stats()
+    allow = (SFT_OK, SFT_ERR_NOT_CONVERGED) if allow_not_converged else (SFT_OK,)
+    status = _check(lib().sft_batch_run(batch.h, stream if stream is not None else _current_stream(),
+                                        ctypes.byref(st)), "sft_batch_run", allow)
+    return status, st.as_dict()
+
+
+def sft_batch_result(batch: Batch, req: int, u_out=None, b_out=None, stream=None):
+    if u_out is None:
+        u_out = np.zeros((batch.nfields[req], batch.nnodes[req]))
+    up, dev, _ = _ptr(u_out)
+    bp, _, _ = _ptr(b_out)
+    _check(lib().sft_batch_result(batch.h, int(req), up, bp, int(dev),
+                                  stream if stream is not None else _current_stream()), "sft_batch_result")
+    return u_out, b_out
+
+
+def sft_batch_destroy(batch: Batch):
+    batch.close()
 
 
 def sft_source_grid(src: Source, precision: int):

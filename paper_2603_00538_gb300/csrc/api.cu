@@ -70,7 +70,10 @@ struct Events {
   }
   float ms(int a, int b) const {
     float t = 0.f;
-    if (ok) cudaEventElapsedTime(&t, e[a], e[b]);
+    if (ok && cudaEventElapsedTime(&t, e[a], e[b]) != cudaSuccess) {
+      t = -1.f;
+      cudaGetLastError();  // timing unavailable: do not leave a sticky error behind
+    }
     return t;
   }
 };
@@ -245,9 +248,10 @@ sft_status sft_transfer(sft_source s, sft_target t, const sft_options* o, double
   if ((int64_t)o->samples_per_elem * t->ne >= ((int64_t)1 << 40)) return fail(SFT_ERR_UNSUPPORTED, "too many samples");
   if (o->precision != SFT_PREC_FP32 && o->precision != SFT_PREC_FP64) return fail(SFT_ERR_ARG, "bad precision");
   if (o->cg_max_iter < 0 || !(o->cg_tol >= 0) || !std::isfinite(o->alpha)) return fail(SFT_ERR_ARG, "bad solver options");
+  if (o->field_count < 0 || o->field_count > s->nf) return fail(SFT_ERR_ARG, "field_count out of range");
   cudaStream_t st = (cudaStream_t)o->cuda_stream;
   const int prec = o->precision;
-  const int nf = s->nf;
+  const int nf = o->field_count > 0 ? o->field_count : s->nf;
   const int64_t nv = t->nv, ne = t->ne;
   const size_t psz = prec == SFT_PREC_FP32 ? 4 : 8;
   Events ev;
@@ -271,7 +275,7 @@ sft_status sft_transfer(sft_source s, sft_target t, const sft_options* o, double
 
   // step 1: control values g = f^s at the target nodes
   if (sft_status r = locate_points(s, prec, nv, t->coordsP[prec], prec == SFT_PREC_FP64, nullptr, g.p,
-                                   prec == SFT_PREC_FP64, nv, counters.p, st))
+                                   prec == SFT_PREC_FP64, nv, counters.p, st, nf))
     return r;
   if (ev.ok) cudaEventRecord(ev.e[2], st);
 

@@ -1,0 +1,1014 @@
+// Batched transfers: many (source, target, options) requests of uneven size
+// run together (Sec. 4 steps 1-7 per request; batching itself has no
+// counterpart in the paper). A plan groups the requests by dimension and
+// field-count class and records one CUDA graph:
+//   1. control values of every request      (k_batch_control, one per dim)
+//   2. fused assembly of every request      (k_batch_assemble, persistent, one per group:
+//      warps pull (request, element-task) tiles from an atomic work counter)
+//   3. one cooperative CG over the block-diagonal system of every
+//      (request, field) right-hand side     (k_batch_pcg)
+// The tile size of each group is chosen by a small autotuner (timed trial
+// launches, cached per process and optionally in a file).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+#include "internal.hpp"
+#include "util.cuh"
+
+namespace sft {
+
+constexpr int kMaxBatch = 4096;
+constexpr int kBatchThreads = 256;
+
+// one request, FP32 path (device copy)
+struct BReq {
+  const float* tx;
+  const int32_t* tconn;
+  const float* vol32;
+  int64_t nv, ne;
+  const GridP<float>* grid;
+  const int32_t* cell_start;
+  const int32_t* cell_items;
+  const float* recs;
+  const float* vals;
+  int64_t nes;
+  int32_t nf, N, U, G;
+  int64_t ntasks;
+  PhiloxKey key;
+  uint32_t stream_id;
+  float alpha, c_det, inv_n;
+  float* g;   // [nf][nv]
+  double* b;  // [nf][nv]
+};
+
+// one (request, field) linear system of the batched CG
+struct BSys {
+  const int32_t* rp;
+  const int32_t* col;
+  const double* val;
+  const double* dinv;
+  const double* b;
+  double* x;
+  int64_t off;  // first global row
+  int64_t n;
+  double tol;
+  int32_t max_iter;
+  int32_t blo, bhi;  // blocks owning its rows
+};
+
+struct BSysOut {
+  int32_t iters;
+  int32_t conv;
+  double rel;
+};
+
+// index of the last entry of off[0..n] that is <= key (off ascending, off[0] = 0)
+__device__ __forceinline__ int find_seg(const int64_t* off, int n, int64_t key) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= key) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// step 1: control values of every request of one dimension
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(kBatchThreads) k_batch_control(const BReq* __restrict__ reqs,
+                                                                 const int32_t* __restrict__ greq,
+                                                                 const int64_t* __restrict__ goff, int ng,
+                                                                 int64_t total, int64_t* __restrict__ counters) {
+  extern __shared__ int64_t s_off[];  // [ng + 1]
+  for (int i = threadIdx.x; i <= ng; i += blockDim.x) s_off[i] = goff[i];
+  __syncthreads();
+  int n_fb = 0, n_em = 0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    const int gi = find_seg(s_off, ng, k);
+    const BReq& R = reqs[greq[gi]];
+    const int64_t i = k - s_off[gi];
+    const GridP<float> gr = *R.grid;
+    float X[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) X[a] = R.tx[i * D + a];
+    float mu[D + 1];
+    int status;
+    const int32_t e = locate_point<D, float>(gr, R.cell_start, R.cell_items, R.recs, X, mu, status);
+    n_fb += status == 1;
+    n_em += status == 2;
+    for (int f = 0; f < R.nf; ++f) R.g[(int64_t)f * R.nv + i] = e >= 0 ? eval_p1<D, float>(R.vals, R.nes, f, e, mu) : 0.f;
+  }
+  const int fb = warp_sum<int>(n_fb), em = warp_sum<int>(n_em);
+  if ((threadIdx.x & 31) == 0) {
+    if (fb) atomicAdd(reinterpret_cast<unsigned long long*>(counters), (unsigned long long)fb);
+    if (em) atomicAdd(reinterpret_cast<unsigned long long*>(counters + 1), (unsigned long long)em);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// steps 2-6: persistent fused assembly over the tasks of a request group.
+// A task is one warp's share of one request (one element when the element
+// has >= 32 Philox units, else floor(32/U) elements). Per-lane partials are
+// plain FP32 sums of a lane's few samples; the warp combine is compensated.
+// ---------------------------------------------------------------------------
+template <int D, int NF>
+__global__ void __launch_bounds__(kBatchThreads) k_batch_assemble(const BReq* __restrict__ reqs,
+                                                                  const int32_t* __restrict__ greq,
+                                                                  const int64_t* __restrict__ goff, int ng,
+                                                                  int64_t total, int tile,
+                                                                  unsigned long long* __restrict__ work,
+                                                                  int64_t* __restrict__ counters) {
+  constexpr int K = D + 1;
+  constexpr int SPU = D == 2 ? 2 : 1;
+  using A = Ar<float>;
+  extern __shared__ int64_t s_off[];  // [ng + 1]
+  for (int i = threadIdx.x; i <= ng; i += blockDim.x) s_off[i] = goff[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  int n_fb = 0, n_em = 0;
+  for (;;) {
+    unsigned long long start = 0;
+    if (lane == 0) start = atomicAdd(work, (unsigned long long)tile);
+    start = __shfl_sync(0xffffffffu, start, 0);
+    if (start >= (unsigned long long)total) break;
+    for (int kk = 0; kk < tile; ++kk) {
+      const int64_t task_g = (int64_t)start + kk;
+      if (task_g >= total) break;
+      const int gi = find_seg(s_off, ng, task_g);
+      const BReq& R = reqs[greq[gi]];
+      const int64_t task = task_g - s_off[gi];
+      const int U = R.U, G = R.G, N = R.N, nf = R.nf;
+      int64_t t;
+      int u0, ustep, seg_lo, seg_hi;
+      bool active;
+      if (G == 1) {
+        t = task; u0 = lane; ustep = 32; seg_lo = 0; seg_hi = 32; active = true;
+      } else {
+        const int slot = lane / U;
+        t = task * G + slot; u0 = lane - slot * U; ustep = U; seg_lo = slot * U; seg_hi = seg_lo + U;
+        active = slot < G;
+      }
+      active = active && t < R.ne;
+      int32_t v[K];
+      float xv[K][D];
+      float acc[NF][K];
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+#pragma unroll
+        for (int i = 0; i < K; ++i) acc[f][i] = 0.f;
+      if (active) {
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+          v[m] = __ldg(R.tconn + t * K + m);
+#pragma unroll
+          for (int a = 0; a < D; ++a) xv[m][a] = __ldg(R.tx + (int64_t)v[m] * D + a);
+        }
+      }
+      const GridP<float> gr = *R.grid;
+      for (int u = u0; active && u < U; u += ustep) {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)u, (uint32_t)t, R.stream_id, 0u), R.key);
+#pragma unroll
+        for (int s = 0; s < SPU; ++s) {
+          const int j = SPU * u + s;
+          if (j >= N) break;
+          float lam[K];
+          if constexpr (D == 2) {
+            if (s == 0) osada_weights<float>(w.x, w.y, lam);
+            else osada_weights<float>(w.z, w.w, lam);
+          } else {
+            spacing_weights<float>(w.x, w.y, w.z, lam);
+          }
+          float X[D];
+          map_point<D, float>(lam, xv, X);
+          float mu[K];
+          int status;
+          const int32_t e = locate_point<D, float>(gr, R.cell_start, R.cell_items, R.recs, X, mu, status);
+          n_fb += status == 1;
+          n_em += status == 2;
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            if (f >= nf) break;
+            const float fs = e >= 0 ? eval_p1<D, float>(R.vals, R.nes, f, e, mu) : 0.f;
+            const float* gf = R.g + (int64_t)f * R.nv;
+            float gX = A::mul(__ldg(gf + v[0]), lam[0]);
+#pragma unroll
+            for (int m = 1; m < K; ++m) gX = A::fma(__ldg(gf + v[m]), lam[m], gX);
+            const float r = A::sub(fs, A::mul(R.alpha, gX));
+#pragma unroll
+            for (int i = 0; i < K; ++i) acc[f][i] = A::fma(r, lam[i], acc[f][i]);
+          }
+        }
+      }
+      // compensated segmented suffix combine of every field's partials
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        if (f >= nf) break;  // nf is warp-uniform
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          float s = acc[f][i], e = 0.f;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const float s2 = __shfl_down_sync(0xffffffffu, s, o);
+            const float e2 = __shfl_down_sync(0xffffffffu, e, o);
+            if (lane + o < seg_hi) {
+              float tt, err;
+              two_sum(s, s2, tt, err);
+              s = tt;
+              e = __fadd_rn(__fadd_rn(e, e2), err);
+            }
+          }
+          acc[f][i] = __fadd_rn(s, e);
+        }
+      }
+      if (active && lane == seg_lo) {
+        const float wv = __ldg(R.vol32 + t);
+        const float cd = __fmul_rn(wv, R.c_det), cm = __fmul_rn(wv, R.inv_n);
+        for (int f = 0; f < nf && f < NF; ++f) {
+          const float* gf = R.g + (int64_t)f * R.nv;
+          float gl[K];
+          float gsum = 0.f;
+#pragma unroll
+          for (int m = 0; m < K; ++m) {
+            gl[m] = __ldg(gf + v[m]);
+            gsum = __fadd_rn(gsum, gl[m]);
+          }
+#pragma unroll
+          for (int i = 0; i < K; ++i) {
+            const float c = __fmaf_rn(cd, __fadd_rn(gsum, gl[i]), __fmul_rn(cm, acc[f][i]));
+            atomicAdd(R.b + (int64_t)f * R.nv + v[i], (double)c);
+          }
+        }
+      }
+    }
+  }
+  const int fb = warp_sum<int>(n_fb), em = warp_sum<int>(n_em);
+  if (lane == 0) {
+    if (fb) atomicAdd(reinterpret_cast<unsigned long long*>(counters), (unsigned long long)fb);
+    if (em) atomicAdd(reinterpret_cast<unsigned long long*>(counters + 1), (unsigned long long)em);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// step 7: one cooperative Jacobi-PCG over all systems (block-diagonal).
+// Block b owns global rows [b R, (b+1) R); its systems are s_lo(b)..s_hi(b).
+// Per-system dot products: per-(block, local system) partials, summed by
+// every block for its own systems over the blocks that own that system's
+// rows, in block order (deterministic, identical in every block). A system
+// stops when it converges or reaches its own iteration cap; the kernel stops
+// when a round finds every system stopped (a flag summed over blocks).
+// ---------------------------------------------------------------------------
+constexpr int kMaxLocalSys = 64;
+
+struct BCgCtl {
+  GridBarrier bar;
+  int32_t err;
+  int32_t pad;
+  unsigned int flag[3];
+};
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum<double>(v);
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+  return s;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kBatchThreads) k_batch_pcg(const BSys* __restrict__ sys, int nsys, int64_t ntot,
+                                                             int64_t rows_per_block,
+                                                             const int32_t* __restrict__ blk_slo,
+                                                             const int32_t* __restrict__ blk_shi, int maxs,
+                                                             double* r, double* z, double* p, double* q, double* part,
+                                                             BSysOut* __restrict__ out, BCgCtl* ctl) {
+  __shared__ double sh[kBatchThreads / 32];
+  __shared__ double s_rz[kMaxLocalSys], s_bn[kMaxLocalSys], s_beta[kMaxLocalSys], s_alpha[kMaxLocalSys],
+      s_rel[kMaxLocalSys];
+  __shared__ int s_done[kMaxLocalSys], s_it[kMaxLocalSys], s_conv[kMaxLocalSys];
+  __shared__ int s_any;
+  const unsigned nb = gridDim.x;
+  const int b = blockIdx.x;
+  const int64_t row0 = (int64_t)b * rows_per_block;
+  const int64_t row1 = min(ntot, row0 + rows_per_block);
+  const int slo = blk_slo[b], shi = blk_shi[b];
+  const int nloc = row0 < row1 ? shi - slo + 1 : 0;
+
+  // local system j, row range of this block inside it
+  auto range = [&](int j, int64_t& a, int64_t& e) {
+    const BSys& S = sys[slo + j];
+    a = max(row0, S.off);
+    e = min(row1, S.off + S.n);
+  };
+  // sum of partial c of system s over its blocks
+  auto gather = [&](int s, int c) {
+    const BSys& S = sys[s];
+    double acc = 0.0;
+    for (int bb = S.blo; bb <= S.bhi; ++bb) acc += __ldcg(part + ((int64_t)bb * maxs + (s - blk_slo[bb])) * 2 + c);
+    return acc;
+  };
+
+  // init: x = 0, r = b, z = D^-1 r, p = q = 0; partials b.b and r.z
+  for (int j = 0; j < nloc; ++j) {
+    const BSys& S = sys[slo + j];
+    int64_t a, e;
+    range(j, a, e);
+    double bb = 0.0, rzv = 0.0;
+    for (int64_t gr = a + threadIdx.x; gr < e; gr += blockDim.x) {
+      const int64_t i = gr - S.off;
+      const double bi = S.b[i], di = S.dinv[i];
+      S.x[i] = 0.0;
+      r[gr] = bi;
+      z[gr] = di * bi;
+      p[gr] = 0.0;
+      q[gr] = 0.0;
+      bb += bi * bi;
+      rzv += bi * di * bi;
+    }
+    const double t0 = block_sum(bb, sh);
+    const double t1 = block_sum(rzv, sh);
+    if (threadIdx.x == 0) {
+      part[((int64_t)b * maxs + j) * 2] = t0;
+      part[((int64_t)b * maxs + j) * 2 + 1] = t1;
+    }
+  }
+  if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+  if (threadIdx.x < nloc) {
+    const int j = threadIdx.x;
+    s_bn[j] = sqrt(gather(slo + j, 0));
+    s_rz[j] = gather(slo + j, 1);
+    s_beta[j] = 0.0;
+    s_it[j] = 0;
+    s_conv[j] = s_bn[j] == 0.0;
+    s_done[j] = s_conv[j];
+    s_rel[j] = 0.0;
+  }
+  __syncthreads();
+
+  for (int it = 0;; ++it) {
+    // phase A: w = M z, p = z + beta p, q = w + beta q, partial p.q
+    for (int j = 0; j < nloc; ++j) {
+      if (s_done[j]) continue;
+      const BSys& S = sys[slo + j];
+      int64_t a, e;
+      range(j, a, e);
+      const double bt = s_beta[j];
+      const double* zs = z + S.off;
+      double pq = 0.0;
+      for (int64_t gr = a + threadIdx.x; gr < e; gr += blockDim.x) {
+        const int64_t i = gr - S.off;
+        double w = 0.0;
+        for (int32_t k = __ldg(S.rp + i); k < __ldg(S.rp + i + 1); ++k) w += __ldg(S.val + k) * __ldcg(zs + __ldg(S.col + k));
+        const double pn = __ldcg(z + gr) + bt * __ldcg(p + gr);
+        const double qn = w + bt * __ldcg(q + gr);
+        p[gr] = pn;
+        q[gr] = qn;
+        pq += pn * qn;
+      }
+      const double t0 = block_sum(pq, sh);
+      if (threadIdx.x == 0) part[((int64_t)b * maxs + j) * 2] = t0;
+    }
+    if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+    if (it > 0) {
+      const unsigned int any = *reinterpret_cast<volatile unsigned int*>(&ctl->flag[(it - 1) % 3]);
+      if (any == 0) break;
+    }
+    if (threadIdx.x < nloc) {
+      const int j = threadIdx.x;
+      s_alpha[j] = s_done[j] ? 0.0 : s_rz[j] / gather(slo + j, 0);
+    }
+    __syncthreads();
+    // phase B: x += a p, r -= a q, z = D^-1 r, partials r.r and r.z
+    for (int j = 0; j < nloc; ++j) {
+      if (s_done[j]) continue;
+      const BSys& S = sys[slo + j];
+      int64_t a, e;
+      range(j, a, e);
+      const double al = s_alpha[j];
+      double rr = 0.0, rzv = 0.0;
+      for (int64_t gr = a + threadIdx.x; gr < e; gr += blockDim.x) {
+        const int64_t i = gr - S.off;
+        S.x[i] = __ldcg(S.x + i) + al * __ldcg(p + gr);
+        const double ri = __ldcg(r + gr) - al * __ldcg(q + gr);
+        r[gr] = ri;
+        const double zi = S.dinv[i] * ri;
+        z[gr] = zi;
+        rr += ri * ri;
+        rzv += ri * zi;
+      }
+      const double t0 = block_sum(rr, sh);
+      const double t1 = block_sum(rzv, sh);
+      if (threadIdx.x == 0) {
+        part[((int64_t)b * maxs + j) * 2] = t0;
+        part[((int64_t)b * maxs + j) * 2 + 1] = t1;
+      }
+    }
+    if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    if (threadIdx.x < nloc) {
+      const int j = threadIdx.x;
+      if (!s_done[j]) {
+        const BSys& S = sys[slo + j];
+        const double rn = sqrt(gather(slo + j, 0));
+        const double rz_new = gather(slo + j, 1);
+        s_it[j] += 1;
+        s_rel[j] = rn / s_bn[j];
+        if (rn <= S.tol * s_bn[j]) s_conv[j] = 1;
+        s_beta[j] = rz_new / s_rz[j];
+        s_rz[j] = rz_new;
+        s_done[j] = s_conv[j] || s_it[j] >= S.max_iter;
+        if (!s_done[j]) atomicOr(&s_any, 1);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (b == 0) atomicExch(&ctl->flag[(it + 1) % 3], 0u);
+      if (s_any) atomicAdd(&ctl->flag[it % 3], 1u);
+    }
+  }
+  // results: written by the first block of each system
+  if (threadIdx.x < nloc) {
+    const int j = threadIdx.x;
+    const int s = slo + j;
+    if (sys[s].blo == b) {
+      out[s].iters = s_it[j];
+      out[s].conv = s_conv[j];
+      out[s].rel = s_rel[j];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// autotune cache: (dim, field class, log2 mean N, log2 tasks) -> tile
+// ---------------------------------------------------------------------------
+using TuneKey = std::tuple<int, int, int, int>;
+static std::mutex g_tune_mu;
+static std::map<TuneKey, int> g_tune;
+static bool g_tune_loaded = false;
+
+static const char* tune_file() { return std::getenv("SFT_AUTOTUNE_CACHE"); }
+
+static void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = tune_file();
+  if (!path) return;
+  FILE* fh = std::fopen(path, "r");
+  if (!fh) return;
+  int d, c, n, t, tile;
+  while (std::fscanf(fh, "%d %d %d %d %d", &d, &c, &n, &t, &tile) == 5) g_tune[TuneKey(d, c, n, t)] = tile;
+  std::fclose(fh);
+}
+
+static void tune_store_locked(const TuneKey& k, int tile) {
+  g_tune[k] = tile;
+  const char* path = tune_file();
+  if (!path) return;
+  FILE* fh = std::fopen(path, "a");
+  if (!fh) return;
+  std::fprintf(fh, "%d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k), tile);
+  std::fclose(fh);
+}
+
+static int ilog2(double x) { return x < 1.0 ? 0 : (int)std::floor(std::log2(x)); }
+
+}  // namespace sft
+
+// ---------------------------------------------------------------------------
+// the plan
+// ---------------------------------------------------------------------------
+struct sft_batch_s {
+  int nreq = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<sft_source> srcs;
+  std::vector<sft_target> tgts;
+  std::vector<sft::BReq> hreq;
+  sft::BReq* dreq = nullptr;
+  // groups: index = (dim - 2) * 3 + field class (0: nf <= 2, 1: <= 4, 2: <= 8)
+  struct Group {
+    std::vector<int32_t> req;
+    std::vector<int64_t> off;  // task offsets
+    int32_t* dreq = nullptr;
+    int64_t* doff = nullptr;
+    int64_t total = 0;
+    int tile = 4;
+    unsigned long long* work = nullptr;
+  } grp[6];
+  struct CtlGroup {
+    std::vector<int32_t> req;
+    std::vector<int64_t> off;  // node offsets
+    int32_t* dreq = nullptr;
+    int64_t* doff = nullptr;
+    int64_t total = 0;
+  } ctl[2];
+  // buffers
+  float* g = nullptr;
+  double* b = nullptr;
+  double* u = nullptr;
+  std::vector<int64_t> vec_off;  // per request offset into g/b/u (elements)
+  int64_t vec_total = 0;
+  int64_t* counters = nullptr;
+  // CG
+  std::vector<sft::BSys> hsys;
+  sft::BSys* dsys = nullptr;
+  int nsys = 0;
+  int64_t ntot = 0, rows_per_block = 0;
+  int nblocks = 0, maxs = 1;
+  int32_t *blk_slo = nullptr, *blk_shi = nullptr;
+  double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *part = nullptr;
+  sft::BSysOut* sysout = nullptr;
+  sft::BCgCtl* cgctl = nullptr;
+  std::vector<int> sys_first;  // first system of each request
+  // graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool graph_ok = false;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  int64_t queries = 0;
+};
+
+namespace sft {
+
+static sft_status enqueue_batch(sft_batch_s* B, cudaStream_t st) {
+  SFT_CUDA(cudaEventRecordWithFlags(B->ev[0], st, cudaEventRecordExternal));
+  SFT_CUDA(cudaMemsetAsync(B->b, 0, sizeof(double) * B->vec_total, st));
+  SFT_CUDA(cudaMemsetAsync(B->counters, 0, sizeof(int64_t) * 2, st));
+  SFT_CUDA(cudaMemsetAsync(B->cgctl, 0, sizeof(BCgCtl), st));
+  for (auto& G : B->grp)
+    if (G.total) SFT_CUDA(cudaMemsetAsync(G.work, 0, sizeof(unsigned long long), st));
+  for (int d = 0; d < 2; ++d) {
+    auto& C = B->ctl[d];
+    if (!C.total) continue;
+    const unsigned blocks = (unsigned)std::min<int64_t>((C.total + kBatchThreads - 1) / kBatchThreads, 152 * 16);
+    if (d == 0)
+      ::sft::note_launch(), k_batch_control<2><<<blocks, kBatchThreads, sizeof(int64_t) * (C.req.size() + 1), st>>>(B->dreq, C.dreq, C.doff,
+                                                                                  (int)C.req.size(), C.total, B->counters);
+    else
+      ::sft::note_launch(), k_batch_control<3><<<blocks, kBatchThreads, sizeof(int64_t) * (C.req.size() + 1), st>>>(B->dreq, C.dreq, C.doff,
+                                                                                  (int)C.req.size(), C.total, B->counters);
+    SFT_CUDA(cudaGetLastError());
+  }
+  SFT_CUDA(cudaEventRecordWithFlags(B->ev[1], st, cudaEventRecordExternal));
+  int sms = 152;
+  {
+    int dev = 0;
+    SFT_CUDA(cudaGetDevice(&dev));
+    SFT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  for (int gi = 0; gi < 6; ++gi) {
+    auto& G = B->grp[gi];
+    if (!G.total) continue;
+    const unsigned blocks = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)sms * 4, (G.total + (kBatchThreads / 32) - 1) / (kBatchThreads / 32)));
+    const int ng = (int)G.req.size();
+#define SFT_BA(DD, NN)                                                                                          \
+  ::sft::note_launch(), k_batch_assemble<DD, NN><<<blocks, kBatchThreads, sizeof(int64_t) * (ng + 1), st>>>(B->dreq, G.dreq, G.doff, ng, \
+                                                                                   G.total, G.tile, G.work,   \
+                                                                                   B->counters)
+    switch (gi) {
+      case 0: SFT_BA(2, 2); break;
+      case 1: SFT_BA(2, 4); break;
+      case 2: SFT_BA(2, 8); break;
+      case 3: SFT_BA(3, 2); break;
+      case 4: SFT_BA(3, 4); break;
+      default: SFT_BA(3, 8); break;
+    }
+#undef SFT_BA
+    SFT_CUDA(cudaGetLastError());
+  }
+  SFT_CUDA(cudaEventRecordWithFlags(B->ev[2], st, cudaEventRecordExternal));
+  if (B->nsys > 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)B->nblocks);
+    cfg.blockDim = dim3(kBatchThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    ::sft::note_launch();
+    SFT_CUDA(cudaLaunchKernelEx(&cfg, k_batch_pcg, (const BSys*)B->dsys, B->nsys, B->ntot, B->rows_per_block,
+                                (const int32_t*)B->blk_slo, (const int32_t*)B->blk_shi, B->maxs, B->r, B->z, B->p,
+                                B->q, B->part, B->sysout, B->cgctl));
+  }
+  SFT_CUDA(cudaEventRecordWithFlags(B->ev[3], st, cudaEventRecordExternal));
+  return SFT_OK;
+}
+
+static sft_status autotune_group(sft_batch_s* B, int gi, cudaStream_t st) {
+  auto& G = B->grp[gi];
+  const int dim = gi < 3 ? 2 : 3;
+  double mean_n = 0.0;
+  for (int32_t r : G.req) mean_n += B->hreq[r].N;
+  mean_n /= (double)G.req.size();
+  const TuneKey key(dim, gi % 3, ilog2(mean_n), ilog2((double)G.total));
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      G.tile = it->second;
+      return SFT_OK;
+    }
+  }
+  // control values must exist before trial assemblies
+  int sms = 152, dev = 0;
+  SFT_CUDA(cudaGetDevice(&dev));
+  SFT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  cudaEvent_t e0, e1;
+  SFT_CUDA(cudaEventCreate(&e0));
+  SFT_CUDA(cudaEventCreate(&e1));
+  const int tiles[] = {1, 2, 4, 8, 16};
+  float best = 1e30f;
+  int best_tile = 4;
+  const unsigned blocks = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((int64_t)sms * 4, (G.total + (kBatchThreads / 32) - 1) / (kBatchThreads / 32)));
+  const int ng = (int)G.req.size();
+  for (int tile : tiles) {
+    float tsum = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {
+      SFT_CUDA(cudaMemsetAsync(G.work, 0, sizeof(unsigned long long), st));
+      SFT_CUDA(cudaEventRecord(e0, st));
+#define SFT_BA(DD, NN)                                                                                          \
+  ::sft::note_launch(), k_batch_assemble<DD, NN><<<blocks, kBatchThreads, sizeof(int64_t) * (ng + 1), st>>>(B->dreq, G.dreq, G.doff, ng, \
+                                                                                   G.total, tile, G.work,     \
+                                                                                   B->counters)
+      switch (gi) {
+        case 0: SFT_BA(2, 2); break;
+        case 1: SFT_BA(2, 4); break;
+        case 2: SFT_BA(2, 8); break;
+        case 3: SFT_BA(3, 2); break;
+        case 4: SFT_BA(3, 4); break;
+        default: SFT_BA(3, 8); break;
+      }
+#undef SFT_BA
+      SFT_CUDA(cudaGetLastError());
+      SFT_CUDA(cudaEventRecord(e1, st));
+      SFT_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      SFT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep > 0) tsum += ms;
+    }
+    if (tsum < best) {
+      best = tsum;
+      best_tile = tile;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  G.tile = best_tile;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_store_locked(key, best_tile);
+  return SFT_OK;
+}
+
+static void free_batch(sft_batch_s* B) {
+  cudaStream_t st = B->stream;
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  for (auto& e : B->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& G : B->grp) {
+    dfree(G.dreq, st);
+    dfree(G.doff, st);
+    dfree(G.work, st);
+  }
+  for (auto& C : B->ctl) {
+    dfree(C.dreq, st);
+    dfree(C.doff, st);
+  }
+  dfree(B->dreq, st);
+  dfree(B->g, st);
+  dfree(B->b, st);
+  dfree(B->u, st);
+  dfree(B->counters, st);
+  dfree(B->dsys, st);
+  dfree(B->blk_slo, st);
+  dfree(B->blk_shi, st);
+  dfree(B->r, st);
+  dfree(B->z, st);
+  dfree(B->p, st);
+  dfree(B->q, st);
+  dfree(B->part, st);
+  dfree(B->sysout, st);
+  dfree(B->cgctl, st);
+  delete B;
+}
+
+template <typename T>
+static sft_status upload(T** dst, const std::vector<T>& v, cudaStream_t st) {
+  SFT_CUDA(dalloc(dst, v.size(), st));
+  if (!v.empty()) SFT_CUDA(cudaMemcpyAsync(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st));
+  return SFT_OK;
+}
+
+static sft_status build_batch(sft_batch_s* B, const sft_options* opts, int autotune) {
+  cudaStream_t st = B->stream;
+  const int nreq = B->nreq;
+  int32_t* d_err = nullptr;
+  SFT_CUDA(dalloc(&d_err, 1, st));
+  SFT_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int32_t), st));
+  // buffers per request
+  B->vec_off.resize(nreq + 1);
+  B->vec_off[0] = 0;
+  for (int r = 0; r < nreq; ++r) {
+    const int nf = opts[r].field_count > 0 ? opts[r].field_count : B->srcs[r]->nf;
+    B->vec_off[r + 1] = B->vec_off[r] + (int64_t)nf * B->tgts[r]->nv;
+  }
+  B->vec_total = B->vec_off[nreq];
+  SFT_CUDA(dalloc(&B->g, (size_t)B->vec_total, st));
+  SFT_CUDA(dalloc(&B->b, (size_t)B->vec_total, st));
+  SFT_CUDA(dalloc(&B->u, (size_t)B->vec_total, st));
+  SFT_CUDA(dalloc(&B->counters, 2, st));
+  B->hreq.resize(nreq);
+  B->queries = 0;
+  for (int r = 0; r < nreq; ++r) {
+    sft_source s = B->srcs[r];
+    sft_target t = B->tgts[r];
+    if (sft_status e = build_locator(s, SFT_PREC_FP32, st, d_err)) return e;
+    if (sft_status e = target_coordsP(t, SFT_PREC_FP32, st)) return e;
+    const Locator& L = s->loc[SFT_PREC_FP32];
+    BReq& R = B->hreq[r];
+    const sft_options& o = opts[r];
+    R.tx = (const float*)t->coordsP[SFT_PREC_FP32];
+    R.tconn = t->conn;
+    R.vol32 = t->vol32;
+    R.nv = t->nv;
+    R.ne = t->ne;
+    R.grid = (const GridP<float>*)L.grid;
+    R.cell_start = L.cell_start;
+    R.cell_items = L.cell_items;
+    R.recs = (const float*)L.recs;
+    R.vals = (const float*)L.vals;
+    R.nes = s->ne;
+    R.nf = o.field_count > 0 ? o.field_count : s->nf;
+    R.N = o.samples_per_elem;
+    const int spu = t->dim == 2 ? 2 : 1;
+    R.U = (R.N + spu - 1) / spu;
+    R.G = R.U >= 32 ? 1 : 32 / R.U;
+    R.ntasks = (t->ne + R.G - 1) / R.G;
+    R.key.k0 = (uint32_t)o.seed;
+    R.key.k1 = (uint32_t)(o.seed >> 32);
+    R.stream_id = o.stream_id;
+    R.alpha = (float)o.alpha;
+    R.c_det = (float)(o.alpha / (double)((t->dim + 1) * (t->dim + 2)));
+    R.inv_n = (float)(1.0 / (double)R.N);
+    R.g = B->g + B->vec_off[r];
+    R.b = B->b + B->vec_off[r];
+    B->queries += t->nv + t->ne * (int64_t)R.N;
+    const int cls = R.nf <= 2 ? 0 : (R.nf <= 4 ? 1 : 2);
+    auto& G = B->grp[(t->dim - 2) * 3 + cls];
+    G.req.push_back(r);
+    auto& C = B->ctl[t->dim - 2];
+    C.req.push_back(r);
+  }
+  for (auto& G : B->grp) {
+    if (G.req.empty()) continue;
+    G.off.assign(1, 0);
+    for (int32_t r : G.req) G.off.push_back(G.off.back() + B->hreq[r].ntasks);
+    G.total = G.off.back();
+    if (sft_status e = upload(&G.dreq, G.req, st)) return e;
+    if (sft_status e = upload(&G.doff, G.off, st)) return e;
+    SFT_CUDA(dalloc(&G.work, 1, st));
+  }
+  for (int d = 0; d < 2; ++d) {
+    auto& C = B->ctl[d];
+    if (C.req.empty()) continue;
+    C.off.assign(1, 0);
+    for (int32_t r : C.req) C.off.push_back(C.off.back() + B->hreq[r].nv);
+    C.total = C.off.back();
+    if (sft_status e = upload(&C.dreq, C.req, st)) return e;
+    if (sft_status e = upload(&C.doff, C.off, st)) return e;
+  }
+  if (sft_status e = upload(&B->dreq, B->hreq, st)) return e;
+  // systems of the batched CG
+  B->sys_first.resize(nreq + 1);
+  int64_t off = 0;
+  for (int r = 0; r < nreq; ++r) {
+    B->sys_first[r] = (int)B->hsys.size();
+    sft_target t = B->tgts[r];
+    for (int f = 0; f < B->hreq[r].nf; ++f) {
+      BSys S;
+      S.rp = t->row_ptr;
+      S.col = t->col;
+      S.val = t->val;
+      S.dinv = t->dinv;
+      S.b = B->b + B->vec_off[r] + (int64_t)f * t->nv;
+      S.x = B->u + B->vec_off[r] + (int64_t)f * t->nv;
+      S.off = off;
+      S.n = t->nv;
+      S.tol = opts[r].cg_tol;
+      S.max_iter = std::max(1, opts[r].cg_max_iter);
+      off += t->nv;
+      B->hsys.push_back(S);
+    }
+  }
+  B->sys_first[nreq] = (int)B->hsys.size();
+  B->nsys = (int)B->hsys.size();
+  B->ntot = off;
+  int dev = 0, sms = 0, per_sm = 0;
+  SFT_CUDA(cudaGetDevice(&dev));
+  SFT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  SFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_pcg, kBatchThreads, 0));
+  if (per_sm < 1) return fail(SFT_ERR_CUDA, "batched CG kernel cannot be resident");
+  B->nblocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::min(per_sm, 4) * sms,
+                                                           (B->ntot + kBatchThreads - 1) / kBatchThreads));
+  B->rows_per_block = (B->ntot + B->nblocks - 1) / B->nblocks;
+  std::vector<int32_t> slo(B->nblocks), shi(B->nblocks);
+  {
+    int s = 0;
+    for (int b = 0; b < B->nblocks; ++b) {
+      const int64_t r0 = (int64_t)b * B->rows_per_block;
+      const int64_t r1 = std::min(B->ntot, r0 + B->rows_per_block) - 1;
+      if (r0 > r1) {
+        slo[b] = shi[b] = B->nsys - 1;
+        continue;
+      }
+      while (s + 1 < B->nsys && B->hsys[s + 1].off <= r0) ++s;
+      slo[b] = s;
+      int e = s;
+      while (e + 1 < B->nsys && B->hsys[e + 1].off <= r1) ++e;
+      shi[b] = e;
+      B->maxs = std::max(B->maxs, e - s + 1);
+    }
+  }
+  if (B->maxs > kMaxLocalSys) return fail(SFT_ERR_UNSUPPORTED, "too many small systems per CG block");
+  for (int s = 0; s < B->nsys; ++s) {
+    BSys& S = B->hsys[s];
+    if (S.n == 0) { S.blo = S.bhi = 0; continue; }
+    S.blo = (int32_t)(S.off / B->rows_per_block);
+    S.bhi = (int32_t)((S.off + S.n - 1) / B->rows_per_block);
+  }
+  if (sft_status e = upload(&B->dsys, B->hsys, st)) return e;
+  if (sft_status e = upload(&B->blk_slo, slo, st)) return e;
+  if (sft_status e = upload(&B->blk_shi, shi, st)) return e;
+  SFT_CUDA(dalloc(&B->r, (size_t)B->ntot, st));
+  SFT_CUDA(dalloc(&B->z, (size_t)B->ntot, st));
+  SFT_CUDA(dalloc(&B->p, (size_t)B->ntot, st));
+  SFT_CUDA(dalloc(&B->q, (size_t)B->ntot, st));
+  SFT_CUDA(dalloc(&B->part, (size_t)B->nblocks * B->maxs * 2, st));
+  SFT_CUDA(dalloc(&B->sysout, (size_t)std::max(1, B->nsys), st));
+  SFT_CUDA(dalloc(&B->cgctl, 1, st));
+  for (auto& e : B->ev) SFT_CUDA(cudaEventCreate(&e));
+  int32_t herr = 0;
+  SFT_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  SFT_CUDA(cudaStreamSynchronize(st));
+  dfree(d_err, st);
+  if (herr) return fail(SFT_ERR_MESH, "a batch source mesh failed to build");
+  // autotune the tile of every group (control values first)
+  if (autotune) {
+    SFT_CUDA(cudaMemsetAsync(B->counters, 0, sizeof(int64_t) * 2, st));
+    for (int d = 0; d < 2; ++d) {
+      auto& C = B->ctl[d];
+      if (!C.total) continue;
+      const unsigned blocks = (unsigned)std::min<int64_t>((C.total + kBatchThreads - 1) / kBatchThreads, 152 * 16);
+      if (d == 0)
+        ::sft::note_launch(), k_batch_control<2><<<blocks, kBatchThreads, sizeof(int64_t) * (C.req.size() + 1), st>>>(B->dreq, C.dreq, C.doff,
+                                                                                    (int)C.req.size(), C.total, B->counters);
+      else
+        ::sft::note_launch(), k_batch_control<3><<<blocks, kBatchThreads, sizeof(int64_t) * (C.req.size() + 1), st>>>(B->dreq, C.dreq, C.doff,
+                                                                                    (int)C.req.size(), C.total, B->counters);
+      SFT_CUDA(cudaGetLastError());
+    }
+    for (int gi = 0; gi < 6; ++gi)
+      if (B->grp[gi].total)
+        if (sft_status e = autotune_group(B, gi, st)) return e;
+  }
+  // record the graph (fallback: direct launches)
+  cudaStream_t cap = nullptr;
+  SFT_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    const sft_status e = enqueue_batch(B, cap);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(cap, &g);
+    ok = e == SFT_OK && ce == cudaSuccess && g;
+    if (ok) {
+      B->graph = g;
+      ok = cudaGraphInstantiate(&B->exec, g, 0) == cudaSuccess;
+    } else if (g) {
+      cudaGraphDestroy(g);
+    }
+  }
+  cudaGetLastError();  // clear a failed capture
+  cudaStreamDestroy(cap);
+  B->graph_ok = ok;
+  return SFT_OK;
+}
+
+}  // namespace sft
+
+using namespace sft;
+
+extern "C" {
+
+sft_status sft_batch_create(int32_t nreq, const sft_source* srcs, const sft_target* tgts, const sft_options* opts,
+                            int32_t autotune, void* cuda_stream, sft_batch* out) {
+  if (!out) return fail(SFT_ERR_ARG, "null output handle");
+  *out = nullptr;
+  if (nreq < 1 || nreq > kMaxBatch) return fail(SFT_ERR_ARG, "nreq must be in 1..4096");
+  if (!srcs || !tgts || !opts) return fail(SFT_ERR_ARG, "null request arrays");
+  for (int r = 0; r < nreq; ++r) {
+    if (!srcs[r] || !tgts[r]) return fail(SFT_ERR_ARG, "null source or target in the batch");
+    if (srcs[r]->dim != tgts[r]->dim) return fail(SFT_ERR_ARG, "source and target dimensions differ");
+    const sft_options& o = opts[r];
+    if (o.precision != SFT_PREC_FP32) return fail(SFT_ERR_UNSUPPORTED, "batched transfers use the FP32 path");
+    if (o.samples_per_elem < 1 || o.cg_max_iter < 0 || !(o.cg_tol >= 0) || !std::isfinite(o.alpha))
+      return fail(SFT_ERR_ARG, "bad request options");
+    if (o.field_count < 0 || o.field_count > srcs[r]->nf) return fail(SFT_ERR_ARG, "field_count out of range");
+  }
+  auto* B = new sft_batch_s();
+  B->nreq = nreq;
+  B->stream = (cudaStream_t)cuda_stream;
+  B->srcs.assign(srcs, srcs + nreq);
+  B->tgts.assign(tgts, tgts + nreq);
+  const sft_status r = build_batch(B, opts, autotune);
+  if (r != SFT_OK) {
+    free_batch(B);
+    return r;
+  }
+  *out = B;
+  return SFT_OK;
+}
+
+sft_status sft_batch_run(sft_batch B, void* cuda_stream, sft_batch_stats* stats) {
+  if (!B) return fail(SFT_ERR_ARG, "null batch");
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : B->stream;
+  if (B->graph_ok) {
+    SFT_CUDA(cudaGraphLaunch(B->exec, st));
+  } else {
+    if (sft_status e = enqueue_batch(B, st)) return e;
+  }
+  std::vector<BSysOut> so((size_t)std::max(1, B->nsys));
+  int64_t hc[2] = {0, 0};
+  BCgCtl hctl;
+  if (B->nsys) SFT_CUDA(cudaMemcpyAsync(so.data(), B->sysout, sizeof(BSysOut) * B->nsys, cudaMemcpyDeviceToHost, st));
+  SFT_CUDA(cudaMemcpyAsync(hc, B->counters, sizeof(hc), cudaMemcpyDeviceToHost, st));
+  SFT_CUDA(cudaMemcpyAsync(&hctl, B->cgctl, sizeof(BCgCtl), cudaMemcpyDeviceToHost, st));
+  SFT_CUDA(cudaStreamSynchronize(st));
+  if (hctl.err) return fail(SFT_ERR_DEVICE_STATUS, "batched CG: grid barrier wait expired");
+  int maxit = 0, nonconv = 0;
+  double maxrel = 0.0;
+  for (int s = 0; s < B->nsys; ++s) {
+    maxit = std::max(maxit, (int)so[s].iters);
+    maxrel = std::max(maxrel, so[s].rel);
+    nonconv += !so[s].conv;
+  }
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->nreq = B->nreq;
+    stats->graph = B->graph_ok ? 1 : 0;
+    stats->max_cg_iters = maxit;
+    stats->nonconverged = nonconv;
+    stats->max_rel_resid = maxrel;
+    stats->queries = B->queries;
+    stats->fallback_queries = hc[0];
+    stats->empty_queries = hc[1];
+    auto ms = [&](int a, int b) {
+      float t = -1.f;
+      if (cudaEventElapsedTime(&t, B->ev[a], B->ev[b]) != cudaSuccess) {
+        t = -1.f;
+        cudaGetLastError();  // timing unavailable: do not leave a sticky error behind
+      }
+      return t;
+    };
+    stats->ms_control = ms(0, 1);
+    stats->ms_assembly = ms(1, 2);
+    stats->ms_solve = ms(2, 3);
+    stats->ms_total = ms(0, 3);
+    for (int gi = 0; gi < 6; ++gi) stats->tile[gi] = B->grp[gi].total ? B->grp[gi].tile : 0;
+  }
+  if (nonconv) return fail(SFT_ERR_NOT_CONVERGED, "a batched system reached its iteration cap");
+  return SFT_OK;
+}
+
+sft_status sft_batch_result(sft_batch B, int32_t req, double* u_out, double* b_out, int32_t out_device,
+                            void* cuda_stream) {
+  if (!B || req < 0 || req >= B->nreq || !u_out) return fail(SFT_ERR_ARG, "bad batch result request");
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : B->stream;
+  const size_t bytes = sizeof(double) * (size_t)(B->vec_off[req + 1] - B->vec_off[req]);
+  const cudaMemcpyKind k = out_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  SFT_CUDA(cudaMemcpyAsync(u_out, B->u + B->vec_off[req], bytes, k, st));
+  if (b_out) SFT_CUDA(cudaMemcpyAsync(b_out, B->b + B->vec_off[req], bytes, k, st));
+  SFT_CUDA(cudaStreamSynchronize(st));
+  return SFT_OK;
+}
+
+void sft_batch_destroy(sft_batch B) {
+  if (B) free_batch(B);
+}
+
+}  // extern "C"

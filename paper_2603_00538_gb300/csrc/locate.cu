@@ -552,14 +552,14 @@ __global__ void __launch_bounds__(256) k_locate_points(const TIn* __restrict__ p
 template <int D, typename P>
 static void launch_locate(sft_source_s* s, const Locator& L, int64_t n, const void* pts, int pts_are_double,
                           int32_t* elem_out, void* val_out, int val_is_double, int64_t val_stride,
-                          int64_t* counters, cudaStream_t st) {
+                          int64_t* counters, cudaStream_t st, int nf) {
   const unsigned blocks = grid_for(n);
   const GridP<P>* g = (const GridP<P>*)L.grid;
   const P* recs = (const P*)L.recs;
   const P* vals = (const P*)L.vals;
 #define SFT_LOC(TIN, TOUT)                                                                                      \
   ::sft::note_launch(), k_locate_points<D, P, TIN, TOUT><<<blocks, 256, 0, st>>>((const TIN*)pts, n, g, L.cell_start, L.cell_items, \
-                                                           recs, vals, s->ne, s->nf, elem_out, (TOUT*)val_out,  \
+                                                           recs, vals, s->ne, nf, elem_out, (TOUT*)val_out,  \
                                                            val_stride, counters)
   if (pts_are_double) {
     if (val_is_double) SFT_LOC(double, double); else SFT_LOC(double, P);
@@ -571,16 +571,17 @@ static void launch_locate(sft_source_s* s, const Locator& L, int64_t n, const vo
 
 sft_status locate_points(sft_source_s* s, int prec, int64_t n, const void* pts, int pts_are_double,
                          int32_t* elem_out, void* val_out, int val_is_double, int64_t val_stride,
-                         int64_t* d_counters, cudaStream_t st) {
+                         int64_t* d_counters, cudaStream_t st, int nf_out) {
   const Locator& L = s->loc[prec];
+  const int nf = nf_out < 0 ? s->nf : nf_out;
   if (!L.built) return fail(SFT_ERR_ARG, "locator not built");
   if (n <= 0) return SFT_OK;
   if (s->dim == 2) {
-    if (prec == SFT_PREC_FP32) launch_locate<2, float>(s, L, n, pts, pts_are_double, elem_out, val_out, val_is_double, val_stride, d_counters, st);
-    else launch_locate<2, double>(s, L, n, pts, pts_are_double, elem_out, val_out, val_is_double, val_stride, d_counters, st);
+    if (prec == SFT_PREC_FP32) launch_locate<2, float>(s, L, n, pts, pts_are_double, elem_out, val_out, val_is_double, val_stride, d_counters, st, nf);
+    else launch_locate<2, double>(s, L, n, pts, pts_are_double, elem_out, val_out, val_is_double, val_stride, d_counters, st, nf);
   } else {
-    if (prec == SFT_PREC_FP32) launch_locate<3, float>(s, L, n, pts, pts_are_double, elem_out, val_out, val_is_double, val_stride, d_counters, st);
-    else launch_locate<3, double>(s, L, n, pts, pts_are_double, elem_out, val_out, val_is_double, val_stride, d_counters, st);
+    if (prec == SFT_PREC_FP32) launch_locate<3, float>(s, L, n, pts, pts_are_double, elem_out, val_out, val_is_double, val_stride, d_counters, st, nf);
+    else launch_locate<3, double>(s, L, n, pts, pts_are_double, elem_out, val_out, val_is_double, val_stride, d_counters, st, nf);
   }
   SFT_CUDA(cudaGetLastError());
   return SFT_OK;
