@@ -114,6 +114,13 @@ sft_status sft_source_create(const sft_mesh_desc* desc, sft_source* out);
  * Errors as for sft_source_create. */
 sft_status sft_target_create(const sft_mesh_desc* desc, sft_target* out);
 
+/* Replace the nodal values of every field of a source (same shape and dtype
+ * as at create: [nfields][nnodes]; device pointer if device_ptrs) keeping its
+ * mesh and location grid: the per-coupling-step update of a fixed mesh
+ * (the paper's online cost, Sec. 5.3). Ordered on cuda_stream; synchronises
+ * it to refresh the source integrals. */
+sft_status sft_source_set_values(sft_source src, const void* values, int32_t device_ptrs, void* cuda_stream);
+
 void sft_source_destroy(sft_source src);
 void sft_target_destroy(sft_target tgt);
 

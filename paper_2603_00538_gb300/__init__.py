@@ -79,6 +79,7 @@ _SIGS = {
     "sft_source_create": ([ctypes.POINTER(sft_mesh_desc), ctypes.POINTER(_vp)], _i32),
     "sft_target_create": ([ctypes.POINTER(sft_mesh_desc), ctypes.POINTER(_vp)], _i32),
     "sft_source_destroy": ([_vp], None),
+    "sft_source_set_values": ([_vp, _vp, _i32, _vp], _i32),
     "sft_target_destroy": ([_vp], None),
     "sft_transfer": ([_vp, _vp, ctypes.POINTER(sft_options), _vp, _vp, _vp, ctypes.POINTER(sft_stats)], _i32),
     "sft_conservation_error": ([_vp, _vp, _vp, _i32, _i32, _vp, _vp], _i32),
@@ -226,6 +227,13 @@ def sft_target_create(coords, conn, stream=None) -> Target:
     h = _vp()
     _check(lib().sft_target_create(ctypes.byref(d), ctypes.byref(h)), "sft_target_create")
     return Target(h.value, lib().sft_target_destroy, keep)
+
+
+def sft_source_set_values(src: Source, values, stream=None):
+    """Replace the source's nodal values [nfields, nnodes] (same dtype)."""
+    vp, dev, keep = _ptr(values)
+    _check(lib().sft_source_set_values(src.h, vp, int(dev), stream if stream is not None else _current_stream()),
+           "sft_source_set_values")
 
 
 def sft_source_destroy(src: Source):

@@ -203,6 +203,16 @@ sft_status sft_source_create(const sft_mesh_desc* d, sft_source* out) {
   return SFT_OK;
 }
 
+sft_status sft_source_set_values(sft_source s, const void* values, int32_t device_ptrs, void* cuda_stream) {
+  if (!s || !values) return fail(SFT_ERR_ARG, "null argument");
+  (void)device_ptrs;  // cudaMemcpyDefault resolves host or device memory
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const size_t esz = s->dtype == SFT_F64 ? 8 : 4;
+  SFT_CUDA(cudaMemcpyAsync(s->values, values, esz * s->nv * s->nf, cudaMemcpyDefault, st));
+  if (sft_status r = refresh_value_copies(s, st)) return r;
+  return source_integrals(s, st);
+}
+
 sft_status sft_target_create(const sft_mesh_desc* d, sft_target* out) {
   if (!out) return fail(SFT_ERR_ARG, "null output handle");
   *out = nullptr;

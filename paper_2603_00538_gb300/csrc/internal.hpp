@@ -88,6 +88,7 @@ sft_status locate_points(sft_source_s* s, int prec, int64_t n, const void* pts, 
                          int32_t* elem_out, void* val_out, int val_is_double, int64_t val_stride,
                          int64_t* d_counters, cudaStream_t st, int nf_out = -1);
 sft_status source_integrals(sft_source_s* s, cudaStream_t st);
+sft_status refresh_value_copies(sft_source_s* s, cudaStream_t st);
 // target.cu
 sft_status build_target(sft_target_s* t, cudaStream_t st, int32_t* d_err);
 sft_status target_coordsP(sft_target_s* t, int prec, cudaStream_t st);

@@ -508,6 +508,41 @@ sft_status build_locator(sft_source_s* s, int prec, cudaStream_t st, int32_t* d_
   return prec == SFT_PREC_FP32 ? build_locator_t<3, float>(s, prec, st, d_err) : build_locator_t<3, double>(s, prec, st, d_err);
 }
 
+// per-element value copies from the nodal values (after a value update)
+template <int D, typename P, typename TV>
+__global__ void k_value_copies(const int32_t* __restrict__ conn, const TV* __restrict__ values, int64_t nv,
+                               int64_t ne, int nf, P* __restrict__ vals) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v[D + 1];
+#pragma unroll
+    for (int m = 0; m <= D; ++m) v[m] = conn[e * (D + 1) + m];
+    for (int f = 0; f < nf; ++f)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) vals[((int64_t)f * ne + e) * 4 + m] = m <= D ? P(values[(int64_t)f * nv + v[m]]) : P(0);
+  }
+}
+
+sft_status refresh_value_copies(sft_source_s* s, cudaStream_t st) {
+  for (int prec = 0; prec < 2; ++prec) {
+    Locator& L = s->loc[prec];
+    if (!L.built) continue;
+    const unsigned blocks = grid_for(s->ne);
+#define SFT_VC(DD, PP, TT)                                                                                  \
+  ::sft::note_launch(), k_value_copies<DD, PP, TT><<<blocks, 256, 0, st>>>(s->conn, (const TT*)s->values, s->nv, \
+                                                                          s->ne, s->nf, (PP*)L.vals)
+    if (s->dim == 2) {
+      if (prec == SFT_PREC_FP32) { if (s->dtype == SFT_F64) SFT_VC(2, float, double); else SFT_VC(2, float, float); }
+      else { if (s->dtype == SFT_F64) SFT_VC(2, double, double); else SFT_VC(2, double, float); }
+    } else {
+      if (prec == SFT_PREC_FP32) { if (s->dtype == SFT_F64) SFT_VC(3, float, double); else SFT_VC(3, float, float); }
+      else { if (s->dtype == SFT_F64) SFT_VC(3, double, double); else SFT_VC(3, double, float); }
+    }
+#undef SFT_VC
+    SFT_CUDA(cudaGetLastError());
+  }
+  return SFT_OK;
+}
+
 // ---------------------------------------------------------------------------
 // point queries: location + P1 evaluation of all fields
 // ---------------------------------------------------------------------------

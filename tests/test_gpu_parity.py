@@ -288,3 +288,20 @@ def test_full_size_sampled(orc, name):
     assert i_t == pytest.approx(r["b"][0].sum(), rel=1e-8)
     assert r["stats"]["cg_rel_resid"] <= p["cg_tol"]
     assert e_mass < 1e-3
+
+
+def test_set_values_equals_recreate(orc):
+    """Updating a source's values in place gives the transfer of a source
+    created with those values (same mesh, same grid)."""
+    src, tgt, _ = W.config_meshes("tri4m", 2e-3)
+    s = sft.mesh_source(src, device=DEV)
+    t = sft.mesh_target(tgt, device=DEV)
+    new = W.as_precision(W.with_values(src, [W.paper_f3], np.float64), np.float32)
+    sft.sft_source_set_values(s, torch.as_tensor(new.values).to(DEV))
+    _, _, u1 = sft.sft_transfer(s, t, 16, FP32, cg_tol=1e-12)
+    s2 = sft.mesh_source(new, device=DEV)
+    _, _, u2 = sft.sft_transfer(s2, t, 16, FP32, cg_tol=1e-12)
+    assert np.array_equal(u1, u2)
+    e1 = sft.sft_conservation_error(s, t, u1[0])
+    e2 = sft.sft_conservation_error(s2, t, u2[0])
+    assert e1 == e2

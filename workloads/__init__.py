@@ -306,6 +306,44 @@ def config_meshes(name: str, scale: float = 1.0):
     raise KeyError(name)
 
 
+BATCH_FIELDS_2D = [paper_f1, paper_f2, paper_f3, field_sincos, field_gauss_jump_2d,
+                   linear_field([1.0, 2.0, -1.0]), lambda x: np.cos(3 * x[:, 0]) + x[:, 1],
+                   lambda x: x[:, 0] * x[:, 1]]
+
+
+def batch_workload(nreq: int = 256, seed: int = 5, scale: float = 1.0):
+    """The batched workload: three sources carrying 8 fields each (the small
+    and the large 2D source meshes, the 3D source mesh) and ``nreq`` requests
+    from ``batch_requests``. 2D requests alternate between the two 2D
+    sources, 3D requests use the 3D source. Targets are jittered structured
+    meshes of the requested size (2 n^2 triangles or 6 n^3 tetrahedra; a
+    Delaunay build for 32 M elements would dominate the run)."""
+    f3 = [lambda x, f=f: f(x[:, :2]) + 0.5 * np.sign(x[:, 2] - 0.4) for f in BATCH_FIELDS_2D]
+    n_small = max(2, int(round(32 * math.sqrt(scale))))
+    n_big = max(2, int(round(1414 * math.sqrt(scale))))
+    n_3d = max(2, int(round(94 * scale ** (1 / 3))))
+    sources = [
+        as_precision(with_values(jittered_tri_mesh(n_small, seed=0), BATCH_FIELDS_2D, np.float64), np.float32),
+        as_precision(with_values(jittered_tri_mesh(n_big, seed=0), BATCH_FIELDS_2D, np.float64), np.float32),
+        as_precision(with_values(jittered_kuhn_mesh(n_3d, seed=0), f3, np.float64), np.float32),
+    ]
+    reqs = batch_requests(nreq, seed, emin=1e4 * scale, emax=5e5 * scale)
+    out = []
+    k2 = 0
+    for r, q in enumerate(reqs):
+        if q["dim"] == 2:
+            n = max(2, int(round(math.sqrt(q["elems"] / 2))))
+            tgt = as_precision(jittered_tri_mesh(n, seed=1000 + r), np.float32)
+            src = k2 % 2
+            k2 += 1
+        else:
+            n = max(2, int(round((q["elems"] / 6) ** (1 / 3))))
+            tgt = as_precision(jittered_kuhn_mesh(n, seed=1000 + r), np.float32)
+            src = 2
+        out.append(dict(q, source=src, target=tgt, elems=tgt.nelems))
+    return sources, out
+
+
 def batch_requests(nreq: int = 256, seed: int = 5, emin: float = 1e4, emax: float = 5e5):
     """The batched-transfer request list: per request the target dimension
     (50/50), the element count (log-uniform in [emin, emax]), the number of
