@@ -275,4 +275,53 @@ def l2_error_2d(src, tgt, tgt_values, field=0):
 
 
 def _declare_mlp(L):
-    pass
+    L.orc_mlp_nparam.restype = _i64
+    L.orc_bf16_round.argtypes = [ctypes.c_double]
+    L.orc_bf16_round.restype = ctypes.c_double
+    L.orc_mlp_forward.argtypes = [_f64p, _i64, _f64p, _int, _f64p]
+    L.orc_mlp_loss_grad.argtypes = [_f64p, _i64, _f64p, _f64p, _int, _f64p]
+    L.orc_mlp_loss_grad.restype = ctypes.c_double
+    L.orc_adam_step.argtypes = [_i64, _f64p, _f64p, _f64p, _f64p, _i64, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_double]
+
+
+MLP_H = 256
+
+
+def mlp_nparam() -> int:
+    return int(lib().orc_mlp_nparam())
+
+
+def mlp_split(params):
+    """Views of the parameter vector: W1 [256,3], c1, W2, c2, W3, c3, W4, c4, w5 [256], c5 [1]."""
+    H = MLP_H
+    sizes = [H * 3, H, H * H, H, H * H, H, H * H, H, H, 1]
+    shapes = [(H, 3), (H,), (H, H), (H,), (H, H), (H,), (H, H), (H,), (H,), (1,)]
+    out, o = [], 0
+    for n, sh in zip(sizes, shapes):
+        out.append(params[o:o + n].reshape(sh))
+        o += n
+    return out
+
+
+def bf16_round(x: float) -> float:
+    return float(lib().orc_bf16_round(float(x)))
+
+
+def mlp_forward(params, X, act_bf16=False):
+    X = _f64(X).reshape(-1, 3)
+    y = np.zeros(X.shape[0])
+    lib().orc_mlp_forward(_f64(params), X.shape[0], X, int(act_bf16), y)
+    return y
+
+
+def mlp_loss_grad(params, X, t, act_bf16=False):
+    X = _f64(X).reshape(-1, 3)
+    g = np.zeros(mlp_nparam())
+    loss = lib().orc_mlp_loss_grad(_f64(params), X.shape[0], X, _f64(t), int(act_bf16), g)
+    return loss, g
+
+
+def adam_step(params, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """In place on params, m, v (float64 arrays)."""
+    lib().orc_adam_step(params.size, params, _f64(grad), m, v, int(t), lr, beta1, beta2, eps)

@@ -117,6 +117,15 @@ void orc_l2_error_2d(int64_t nvs, const double* src_coords, int64_t nes,
                      const int32_t* tgt_conn, const double* tgt_values,
                      double* err_out, double* norm_out);
 
+/* ---- the surrogate network (see mlp.c for the parameter layout) ---- */
+int64_t orc_mlp_nparam(void);
+double orc_bf16_round(double x);
+void orc_mlp_forward(const double* params, int64_t n, const double* X, int act_bf16, double* y_out);
+double orc_mlp_loss_grad(const double* params, int64_t n, const double* X, const double* t, int act_bf16,
+                         double* grad);
+void orc_adam_step(int64_t np, double* params, const double* grad, double* m, double* v, int64_t t,
+                   double lr, double beta1, double beta2, double eps);
+
 #ifdef __cplusplus
 }
 #endif

@@ -482,3 +482,62 @@ def test_conservation_at_convergence(orc):
     m = orc.lumped_mass(t.coords, t.conn)
     for q in range(2):
         assert m @ r["u"][q] == pytest.approx(r["b"][q].sum(), rel=1e-12)
+
+
+# --------------------------------------------------------------------------
+# the surrogate network (FP64)
+# --------------------------------------------------------------------------
+def _mlp_params(seed, scale=1.0):
+    import workloads as W_
+    return W_.mlp_init(seed) * scale
+
+
+def test_bf16_rounding_hand_cases(orc):
+    """bfloat16 keeps 8 significant bits, ties to even (worked by hand)."""
+    assert orc.bf16_round(1.0) == 1.0
+    assert orc.bf16_round(1.0 + 2 ** -8) == 1.0                 # tie -> even (1.0)
+    assert orc.bf16_round(1.0 + 3 * 2 ** -8) == 1.0 + 2 ** -6   # tie -> even (1 + 2^-6)
+    assert orc.bf16_round(1.0 + 2 ** -8 + 2 ** -12) == 1.0 + 2 ** -7
+    assert orc.bf16_round(-3.0) == -3.0
+    assert orc.bf16_round(0.1) == 0.10009765625
+
+
+def test_mlp_zero_weights_and_silu(orc):
+    p = np.zeros(orc.mlp_nparam())
+    p[-1] = 0.75                        # c5
+    X = np.random.default_rng(0).random((5, 3))
+    assert np.allclose(orc.mlp_forward(p, X), 0.75)
+    # one active path: W1[0] = e_x, w5[0] = 1 and identity-free hidden layers
+    # give y = silu(x) only if later layers pass it through; use c's instead:
+    q = np.zeros(orc.mlp_nparam())
+    W1, c1, W2, c2, W3, c3, W4, c4, w5, c5 = orc.mlp_split(q)
+    c4[0] = 2.0
+    w5[0] = 1.0
+    y = orc.mlp_forward(q, X)
+    assert np.allclose(y, 2.0 / (1.0 + np.exp(-2.0)))   # silu(2)
+
+
+def test_mlp_gradient_matches_finite_differences(orc):
+    p = _mlp_params(3)
+    rng = np.random.default_rng(4)
+    X = rng.random((6, 3))
+    t = rng.standard_normal(6)
+    loss, g = orc.mlp_loss_grad(p, X, t)
+    idx = rng.choice(p.size, 40, replace=False)
+    idx = np.concatenate([idx, [0, 767, 768, p.size - 257, p.size - 1]])   # W1, c1, w5, c5 entries
+    for i in idx:
+        h = 1e-6 * max(1.0, abs(p[i]))
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (orc.mlp_loss_grad(pp, X, t)[0] - orc.mlp_loss_grad(pm, X, t)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1e-3, abs(g[i])) + 1e-10, (i, fd, g[i])
+
+
+def test_adam_first_step_closed_form(orc):
+    """From m = v = 0 the bias-corrected first step is lr g / (|g| + eps)."""
+    p = np.array([1.0, -2.0, 0.5])
+    g = np.array([0.3, -4.0, 0.0])
+    m, v = np.zeros(3), np.zeros(3)
+    orc.adam_step(p, g, m, v, 1, lr=0.01)
+    assert np.allclose(p, np.array([1.0, -2.0, 0.5]) - 0.01 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)

@@ -344,6 +344,28 @@ def batch_workload(nreq: int = 256, seed: int = 5, scale: float = 1.0):
     return sources, out
 
 
+MLP_HIDDEN = 256
+MLP_NPARAM = MLP_HIDDEN * 3 + MLP_HIDDEN + 3 * (MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN) + MLP_HIDDEN + 1
+
+
+def mlp_init(seed: int = 0) -> np.ndarray:
+    """Seeded initial parameters of the surrogate network 3->256->256->256->256->1
+    (layout: W1 [256][3], c1, W2 [256][256], c2, W3, c3, W4, c4, w5 [256], c5):
+    uniform weights with He-uniform bounds sqrt(6/fan_in) (the first layer
+    scaled up for the unit-box inputs), uniform first-layer biases, zero
+    other biases."""
+    rng = np.random.default_rng(seed)
+    H = MLP_HIDDEN
+    parts = [rng.uniform(-1, 1, (H, 3)) * 6.0,
+             rng.uniform(-1, 1, H) * 3.0]
+    for _ in range(3):
+        parts += [rng.uniform(-1, 1, (H, H)) * math.sqrt(6.0 / H), np.zeros(H)]
+    parts += [rng.uniform(-1, 1, H) * math.sqrt(3.0 / H), np.zeros(1)]
+    out = np.concatenate([x.ravel() for x in parts])
+    assert out.size == MLP_NPARAM
+    return out
+
+
 def batch_requests(nreq: int = 256, seed: int = 5, emin: float = 1e4, emax: float = 5e5):
     """The batched-transfer request list: per request the target dimension
     (50/50), the element count (log-uniform in [emin, emax]), the number of
