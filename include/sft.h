@@ -29,6 +29,7 @@ extern "C" {
 typedef struct sft_source_s* sft_source;
 typedef struct sft_target_s* sft_target;
 typedef struct sft_batch_s* sft_batch;
+typedef struct sft_mlp_s* sft_mlp;
 
 typedef enum {
     SFT_OK = 0,
@@ -200,6 +201,24 @@ sft_status sft_batch_run(sft_batch b, void* cuda_stream, sft_batch_stats* stats)
 sft_status sft_batch_result(sft_batch b, int32_t req, double* u_out, double* b_out, int32_t out_device,
                             void* cuda_stream);
 void sft_batch_destroy(sft_batch b);
+
+/* ---- learned surrogate source (spec item 4; no counterpart in the
+ * paper beyond its motivation: black-box sources "such as machine-learned
+ * surrogates") ----
+ * Network x in R^3 -> 256 -> 256 -> 256 -> 256 -> 1, SiLU after each hidden
+ * layer, FP32 parameters with BF16 copies of the three 256x256 weight
+ * matrices (run on the tensor cores), BF16 hidden activations, FP32
+ * accumulation. Parameter vector (sft_mlp_nparam() floats): W1 [256][3],
+ * c1 [256], W2 [256][256], c2, W3, c3, W4, c4, w5 [256], c5; weights [out][in]. */
+int64_t sft_mlp_nparam(void);
+/* params: host or device FP32 vector (copied). */
+sft_status sft_mlp_create(const float* params, int32_t device_ptrs, void* cuda_stream, sft_mlp* out);
+/* Current FP32 parameters to out (device pointer if out_device). */
+sft_status sft_mlp_params(sft_mlp m, float* out, int32_t out_device, void* cuda_stream);
+/* Surrogate query: out[i] = network(pts[i]) for pts [n][3] FP32. */
+sft_status sft_mlp_forward(sft_mlp m, int64_t n, const float* pts, float* out, int32_t device_ptrs,
+                           void* cuda_stream);
+void sft_mlp_destroy(sft_mlp m);
 
 /* Allocation-free solve of M u = b for callers that cannot allocate device
  * memory at solve time (for example a coupled code whose memory pool owns

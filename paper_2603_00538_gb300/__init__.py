@@ -94,6 +94,11 @@ _SIGS = {
     "sft_batch_run": ([_vp, _vp, ctypes.POINTER(sft_batch_stats)], _i32),
     "sft_batch_result": ([_vp, _i32, _vp, _vp, _i32, _vp], _i32),
     "sft_batch_destroy": ([_vp], None),
+    "sft_mlp_nparam": ([], _i64),
+    "sft_mlp_create": ([_vp, _i32, _vp, _vp], _i32),
+    "sft_mlp_params": ([_vp, _vp, _i32, _vp], _i32),
+    "sft_mlp_forward": ([_vp, _i64, _vp, _vp, _i32, _vp], _i32),
+    "sft_mlp_destroy": ([_vp], None),
     "sft_mass_solve_static": ([_i64, _vp, _vp, _vp, _i32, _vp, _vp, _d, _i32, _vp, _vp, _vp], _i32),
 }
 EXPORTS = tuple(_SIGS)
@@ -394,6 +399,45 @@ def sft_batch_result(batch: Batch, req: int, u_out=None, b_out=None, stream=None
 
 def sft_batch_destroy(batch: Batch):
     batch.close()
+
+
+class Mlp(_Handle):
+    pass
+
+
+def sft_mlp_nparam() -> int:
+    return int(lib().sft_mlp_nparam())
+
+
+def sft_mlp_create(params, stream=None) -> Mlp:
+    """Network handle from an FP32 parameter vector (numpy or torch)."""
+    p = params if _is_torch(params) else np.ascontiguousarray(params, np.float32)
+    pp, dev, keep = _ptr(p)
+    h = _vp()
+    _check(lib().sft_mlp_create(pp, int(dev), stream if stream is not None else _current_stream(),
+                                ctypes.byref(h)), "sft_mlp_create")
+    return Mlp(h.value, lib().sft_mlp_destroy, None)
+
+
+def sft_mlp_params(m: Mlp, out=None, stream=None):
+    if out is None:
+        out = np.zeros(sft_mlp_nparam(), np.float32)
+    op, dev, _ = _ptr(out)
+    _check(lib().sft_mlp_params(m.h, op, int(dev), stream if stream is not None else _current_stream()),
+           "sft_mlp_params")
+    return out
+
+
+def sft_mlp_forward(m: Mlp, pts, out=None, stream=None):
+    """Network values at pts [n, 3] (float32, numpy or CUDA tensor)."""
+    n = int(pts.shape[0])
+    if out is None:
+        out = np.zeros(n, np.float32)
+    pp, dev, _ = _ptr(pts if _is_torch(pts) else np.ascontiguousarray(pts, np.float32))
+    op, _, _ = _ptr(out)
+    _check(lib().sft_mlp_forward(m.h, n, pp, op, int(dev), stream if stream is not None else _current_stream()),
+           "sft_mlp_forward")
+    return out
 
 
 def sft_source_grid(src: Source, precision: int):
