@@ -218,6 +218,20 @@ sft_status sft_mlp_params(sft_mlp m, float* out, int32_t out_device, void* cuda_
 /* Surrogate query: out[i] = network(pts[i]) for pts [n][3] FP32. */
 sft_status sft_mlp_forward(sft_mlp m, int64_t n, const float* pts, float* out, int32_t device_ptrs,
                            void* cuda_stream);
+/* Gradient of the mean squared error 1/n sum (net(pts_i) - targets_i)^2 with
+ * respect to every parameter (grad_out [nparam] FP32) and the loss value
+ * (host double); all arrays device memory. Hand-written BF16 forward and
+ * backward on the tensor cores (activations and activation gradients in
+ * BF16, FP32 accumulation, FP32 gradient). */
+sft_status sft_mlp_loss_grad(sft_mlp m, int64_t n, const float* pts, const float* targets, float* grad_out,
+                             double* loss_out, int32_t device_ptrs, void* cuda_stream);
+/* Adam training (beta 0.9 / 0.999, eps 1e-8) on device data: `epochs` passes
+ * over the n points in minibatches of `batch` (rounded to 128), learning rate
+ * decaying geometrically from lr to lr_final; loss_history [epochs] (host,
+ * may be NULL) gets each epoch's mean loss. */
+sft_status sft_mlp_train(sft_mlp m, int64_t n, const float* pts, const float* targets, int32_t epochs,
+                         int32_t batch, float lr, float lr_final, double* loss_history, int32_t device_ptrs,
+                         void* cuda_stream);
 void sft_mlp_destroy(sft_mlp m);
 
 /* Allocation-free solve of M u = b for callers that cannot allocate device

@@ -99,6 +99,8 @@ _SIGS = {
     "sft_mlp_params": ([_vp, _vp, _i32, _vp], _i32),
     "sft_mlp_forward": ([_vp, _i64, _vp, _vp, _i32, _vp], _i32),
     "sft_mlp_destroy": ([_vp], None),
+    "sft_mlp_loss_grad": ([_vp, _i64, _vp, _vp, _vp, _vp, _i32, _vp], _i32),
+    "sft_mlp_train": ([_vp, _i64, _vp, _vp, _i32, _i32, ctypes.c_float, ctypes.c_float, _vp, _i32, _vp], _i32),
     "sft_mass_solve_static": ([_i64, _vp, _vp, _vp, _i32, _vp, _vp, _d, _i32, _vp, _vp, _vp], _i32),
 }
 EXPORTS = tuple(_SIGS)
@@ -438,6 +440,35 @@ def sft_mlp_forward(m: Mlp, pts, out=None, stream=None):
     _check(lib().sft_mlp_forward(m.h, n, pp, op, int(dev), stream if stream is not None else _current_stream()),
            "sft_mlp_forward")
     return out
+
+
+def _cuda_f32(x, name):
+    if not (_is_torch(x) and x.is_cuda and str(x.dtype).endswith("float32") and x.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    return x.data_ptr()
+
+
+def sft_mlp_loss_grad(m: Mlp, pts, targets, grad_out, stream=None):
+    """Mean squared error of the network on (pts [n,3], targets [n]) and its
+    gradient, written into grad_out [nparam]; all contiguous float32 CUDA
+    tensors. Returns the loss."""
+    n = int(pts.shape[0])
+    loss = ctypes.c_double()
+    _check(lib().sft_mlp_loss_grad(m.h, n, _cuda_f32(pts, "pts"), _cuda_f32(targets, "targets"),
+                                   _cuda_f32(grad_out, "grad_out"), ctypes.byref(loss), 1,
+                                   stream if stream is not None else _current_stream()), "sft_mlp_loss_grad")
+    return loss.value
+
+
+def sft_mlp_train(m: Mlp, pts, targets, epochs=10, batch=16384, lr=2e-3, lr_final=1e-4, stream=None):
+    """Adam training on (pts [n,3], targets [n]) contiguous float32 CUDA
+    tensors; returns the per-epoch mean losses."""
+    n = int(pts.shape[0])
+    hist = np.zeros(int(epochs))
+    _check(lib().sft_mlp_train(m.h, n, _cuda_f32(pts, "pts"), _cuda_f32(targets, "targets"), int(epochs),
+                               int(batch), float(lr), float(lr_final), hist.ctypes.data, 1,
+                               stream if stream is not None else _current_stream()), "sft_mlp_train")
+    return hist
 
 
 def sft_source_grid(src: Source, precision: int):
