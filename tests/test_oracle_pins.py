@@ -541,3 +541,96 @@ def test_adam_first_step_closed_form(orc):
     m, v = np.zeros(3), np.zeros(3)
     orc.adam_step(p, g, m, v, 1, lr=0.01)
     assert np.allclose(p, np.array([1.0, -2.0, 0.5]) - 0.01 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# surrogate-source transfer oracle (network as the black box, exact fallback)
+# ---------------------------------------------------------------------------
+def _const_net(orc, c):
+    """A network whose output is the constant c (all weights zero, c5 = c)."""
+    p = np.zeros(orc.mlp_nparam())
+    p[-1] = c
+    return p
+
+
+def _sur_meshes():
+    import workloads as W_
+    tgt = W_.jittered_kuhn_mesh(3, seed=2)
+    src = W_.with_values(W_.jittered_tri_mesh(6, seed=3), [W_.linear_field([0.3, 1.5, -0.7])])
+    return src, tgt
+
+
+def test_surrogate_constant_network_gives_mass_times_constant(orc):
+    """alpha = 1 and a constant source c: every residual vanishes, so b is the
+    control term alone, b_i = c * int psi_i (the lumped mass), and u = c."""
+    from oracle import surrogate as S
+    _, tgt = _sur_meshes()
+    out = S.surrogate_transfer(_const_net(orc, 0.75), tgt.coords, tgt.conn, N=8, seed=4)
+    m = orc.lumped_mass(tgt.coords, tgt.conn)
+    assert np.allclose(out["g"], 0.75, rtol=0, atol=1e-15)
+    assert np.allclose(out["b"], 0.75 * m, rtol=1e-12, atol=0)
+    assert np.allclose(out["u"], 0.75, atol=1e-9)
+
+
+def test_surrogate_alpha_zero_conserves_total(orc):
+    """alpha = 0: b is the plain Monte Carlo load vector; the barycentric
+    weights sum to one, so sum_i b_i = c * |Omega| exactly (up to rounding)."""
+    from oracle import surrogate as S
+    _, tgt = _sur_meshes()
+    out = S.surrogate_transfer(_const_net(orc, -1.25), tgt.coords, tgt.conn, N=5, seed=9, alpha=0.0)
+    assert abs(out["b"].sum() - (-1.25) * 1.0) < 1e-6   # the jittered cube keeps volume 1
+
+
+def test_surrogate_exact_only_reproduces_linear_field(orc):
+    """No network: every query exact. A linear field of (x, y) is reproduced
+    by the 2D source, the residuals vanish (alpha = 1) and u equals the field
+    at the 3D target's nodes (the source extruded along z)."""
+    from oracle import surrogate as S
+    src, tgt = _sur_meshes()
+    out = S.surrogate_transfer(None, tgt.coords, tgt.conn, N=6, seed=1,
+                               exact=(src.coords, src.conn, src.values[0]))
+    ref = 0.3 + 1.5 * tgt.coords[:, 0] - 0.7 * tgt.coords[:, 1]
+    assert out["fallback"].all()
+    assert np.abs(out["u"] - ref).max() < 2e-6
+
+
+def test_surrogate_fallback_margin_closed_form(orc):
+    """Constant network c against the linear exact field l: the margin of an
+    element is max_{j<s} |c - l(X_j)| over its first s sample points, and the
+    element falls back exactly when that exceeds tau. Fallback elements then
+    carry the exact field, the others the constant."""
+    from oracle import surrogate as S
+    src, tgt = _sur_meshes()
+    c, N, s, seed = 0.9, 8, 3, 6
+    tau = 0.35
+    out = S.surrogate_transfer(_const_net(orc, c), tgt.coords, tgt.conn, N=N, seed=seed,
+                               exact=(src.coords, src.conn, src.values[0]), tau=tau, s=s)
+    ref_margin = np.zeros(len(tgt.conn))
+    for t in range(len(tgt.conn)):
+        _, X = orc.sample_element(1, 3, seed, 0, t, N, tgt.coords[tgt.conn[t]])
+        lX = 0.3 + 1.5 * X[:s, 0] - 0.7 * X[:s, 1]
+        ref_margin[t] = np.abs(c - lX).max()
+        lall = 0.3 + 1.5 * X[:, 0] - 0.7 * X[:, 1]
+        expect = lall if ref_margin[t] > tau else np.full(N, c)
+        assert np.allclose(out["f"][t], expect, atol=2e-6)
+    assert np.allclose(out["margin"], ref_margin, atol=2e-6)
+    assert np.array_equal(out["fallback"], ref_margin > tau)
+    assert 0 < out["fallback"].sum() < len(tgt.conn)
+
+
+def test_surrogate_dataset_points_and_values(orc):
+    """Training points lie in the box, are uniform (mean within 5 standard
+    errors of the centre) and carry the exact (x, y) field, here linear, so
+    it is reproduced exactly by the P1 source."""
+    from oracle import surrogate as S
+    src, _ = _sur_meshes()
+    pts, f, e = S.surrogate_dataset(src.coords, src.conn, src.values[0], 3000, seed=11,
+                                    box_lo=(0, 0, 0.25), box_hi=(1, 1, 0.75))
+    assert pts.dtype == np.float32
+    assert (pts[:, :2] > 0).all() and (pts[:, :2] < 1).all()
+    assert (pts[:, 2] > 0.25).all() and (pts[:, 2] < 0.75).all()
+    se = np.array([1, 1, 0.5]) / np.sqrt(12 * 3000)
+    assert np.all(np.abs(pts.mean(axis=0) - [0.5, 0.5, 0.5]) < 5 * se)
+    assert (e >= 0).all()
+    ref = 0.3 + 1.5 * pts[:, 0].astype(np.float64) - 0.7 * pts[:, 1].astype(np.float64)
+    assert np.abs(f - ref).max() < 1e-12
