@@ -234,6 +234,64 @@ sft_status sft_mlp_train(sft_mlp m, int64_t n, const float* pts, const float* ta
                          void* cuda_stream);
 void sft_mlp_destroy(sft_mlp m);
 
+/* ---- Surrogate source: the network as the black-box query ----
+ *
+ * The transfer of Sec. 4 (steps 1-7) with the source queried through a
+ * trained surrogate network (the learned black-box source the paper's
+ * introduction motivates) instead of a mesh location. Network inputs are the
+ * 3 coordinates of a sample point (z = 0 for a 2D target). An optional exact
+ * source mesh, of dimension d_s <= the target's, backs it: an exact query
+ * locates the point's first d_s coordinates. */
+typedef struct {
+    int32_t exact_field;   /* field of the exact source answering exact queries */
+    int32_t subsample;     /* s in 0..min(N,128): the first s samples of every element are also
+                              queried exactly; 0 disables the fallback */
+    float tau;             /* >= 0: an element whose subsample has max |f_net - f_exact| > tau
+                              (or a non-finite difference) uses exact queries for all N samples */
+    int32_t reserved;
+    int32_t* fallback_out; /* optional [nelems]: 1 where the element used exact queries */
+    float* sample_f_out;   /* optional [nelems][N]: the source value used at every sample */
+} sft_surrogate_opts;
+
+typedef struct {
+    int32_t cg_iters;
+    int32_t reserved;
+    double cg_rel_resid;
+    int64_t net_queries;     /* network evaluations: target nodes + nelems * N */
+    int64_t exact_queries;   /* exact mesh queries (subsample + fallback elements) */
+    int64_t fallback_elems;  /* elements that used exact queries */
+    int64_t empty_queries;   /* exact queries that landed in an empty grid cell (value 0) */
+    float ms_control;        /* step 1: control values at the target nodes */
+    float ms_assembly;       /* steps 2-6: fused sample / network / fallback / scatter kernel */
+    float ms_solve;          /* step 7 */
+    float ms_total;
+} sft_surrogate_stats;
+
+/* Transfer with the surrogate `net` (may be NULL: every query exact, the
+ * plain mesh-query transfer of a d_s-dimensional source onto the target) and
+ * the exact source `exact` (may be NULL: no fallback). opt->precision must be
+ * SFT_PREC_FP32 (else SFT_ERR_UNSUPPORTED); opt->field_count and
+ * sample_elem_out are ignored; one field. Control values g at the target
+ * nodes come from the network (exact source without one). Outputs as
+ * sft_transfer: u_out, b_out, g_out [nnodes] FP64, fallback_out and
+ * sample_f_out host or device per opt->out_device. Samples are those of
+ * sft_transfer with the same seed / stream_id / N (Philox counters of the
+ * target dimension), so both paths see identical points. */
+sft_status sft_transfer_surrogate(sft_mlp net, sft_source exact, sft_target tgt, const sft_options* opt,
+                                  const sft_surrogate_opts* sopt, double* u_out, double* b_out, double* g_out,
+                                  sft_surrogate_stats* stats);
+
+/* Training set for the surrogate: n points in the box [box_lo, box_hi]
+ * (host float[3] each), point j = lo + u * (hi - lo) per axis in FP32 (one
+ * rounded product, one rounded sum), u = Philox4x32-10(key = seed, counter =
+ * (j_lo32, j_hi32, stream_id, 1)) words 0..2 mapped as the FP32 sampler's
+ * uniforms; f = the exact source's field `field` at the point's first d_s
+ * coordinates (FP32 location; 0 in an empty cell). pts_out [n][3] and f_out
+ * [n] are device memory; *max_abs_out (host, may be NULL) = max |f|. */
+sft_status sft_surrogate_dataset(sft_source src, int32_t field, int64_t n, uint64_t seed, uint32_t stream_id,
+                                 const float* box_lo, const float* box_hi, float* pts_out, float* f_out,
+                                 float* max_abs_out, void* cuda_stream);
+
 /* Allocation-free solve of M u = b for callers that cannot allocate device
  * memory at solve time (for example a coupled code whose memory pool owns
  * the device, or a time-stepping loop that must not call cudaMalloc/cudaFree,

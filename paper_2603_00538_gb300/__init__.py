@@ -18,7 +18,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsft.so")
 
-SFT_OK, SFT_ERR_NOT_CONVERGED = 0, 5
+(SFT_OK, SFT_ERR_ARG, SFT_ERR_MESH, SFT_ERR_CUDA, SFT_ERR_OOM, SFT_ERR_NOT_CONVERGED, SFT_ERR_OUTSIDE,
+ SFT_ERR_DEVICE_STATUS, SFT_ERR_UNSUPPORTED) = range(9)
 SFT_PREC_FP64, SFT_PREC_FP32 = 0, 1
 SFT_F32, SFT_F64 = 0, 1
 
@@ -74,6 +75,22 @@ class sft_batch_stats(ctypes.Structure):
         return d
 
 
+class sft_surrogate_opts(ctypes.Structure):
+    _fields_ = [("exact_field", ctypes.c_int32), ("subsample", ctypes.c_int32), ("tau", ctypes.c_float),
+                ("reserved", ctypes.c_int32), ("fallback_out", ctypes.c_void_p), ("sample_f_out", ctypes.c_void_p)]
+
+
+class sft_surrogate_stats(ctypes.Structure):
+    _fields_ = [("cg_iters", ctypes.c_int32), ("reserved", ctypes.c_int32), ("cg_rel_resid", ctypes.c_double),
+                ("net_queries", ctypes.c_int64), ("exact_queries", ctypes.c_int64),
+                ("fallback_elems", ctypes.c_int64), ("empty_queries", ctypes.c_int64),
+                ("ms_control", ctypes.c_float), ("ms_assembly", ctypes.c_float), ("ms_solve", ctypes.c_float),
+                ("ms_total", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
+
+
 _vp, _i32, _i64, _d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
 _SIGS = {
     "sft_source_create": ([ctypes.POINTER(sft_mesh_desc), ctypes.POINTER(_vp)], _i32),
@@ -101,6 +118,9 @@ _SIGS = {
     "sft_mlp_destroy": ([_vp], None),
     "sft_mlp_loss_grad": ([_vp, _i64, _vp, _vp, _vp, _vp, _i32, _vp], _i32),
     "sft_mlp_train": ([_vp, _i64, _vp, _vp, _i32, _i32, ctypes.c_float, ctypes.c_float, _vp, _i32, _vp], _i32),
+    "sft_transfer_surrogate": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i32),
+    "sft_surrogate_dataset": ([_vp, _i32, _i64, ctypes.c_uint64, ctypes.c_uint32, _vp, _vp, _vp, _vp, _vp, _vp],
+                              _i32),
     "sft_mass_solve_static": ([_i64, _vp, _vp, _vp, _i32, _vp, _vp, _d, _i32, _vp, _vp, _vp], _i32),
 }
 EXPORTS = tuple(_SIGS)
@@ -469,6 +489,59 @@ def sft_mlp_train(m: Mlp, pts, targets, epochs=10, batch=16384, lr=2e-3, lr_fina
                                int(batch), float(lr), float(lr_final), hist.ctypes.data, 1,
                                stream if stream is not None else _current_stream()), "sft_mlp_train")
     return hist
+
+
+def sft_surrogate_dataset(src: Source, n: int, seed: int = 0, stream_id: int = 0, box_lo=(0.0, 0.0, 0.0),
+                          box_hi=(1.0, 1.0, 1.0), field: int = 0, pts_out=None, f_out=None, stream=None):
+    """Training set of the surrogate on the device: (pts [n,3], f [n] float32
+    CUDA tensors, max |f|)."""
+    import torch
+    n = int(n)
+    if pts_out is None:
+        pts_out = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    if f_out is None:
+        f_out = torch.empty(n, dtype=torch.float32, device="cuda")
+    lo = (ctypes.c_float * 3)(*[float(x) for x in box_lo])
+    hi = (ctypes.c_float * 3)(*[float(x) for x in box_hi])
+    mx = ctypes.c_float()
+    _check(lib().sft_surrogate_dataset(src.h, int(field), n, int(seed), int(stream_id), lo, hi,
+                                       _cuda_f32(pts_out, "pts_out"), _cuda_f32(f_out, "f_out"), ctypes.byref(mx),
+                                       stream if stream is not None else _current_stream()), "sft_surrogate_dataset")
+    return pts_out, f_out, mx.value
+
+
+def sft_transfer_surrogate(net, exact, tgt: Target, samples_per_elem: int, seed: int = 0, stream_id: int = 0,
+                           alpha: float = 1.0, cg_tol: float = 1e-10, cg_max_iter: int = 1000, subsample: int = 4,
+                           tau: float = 0.0, exact_field: int = 0, u_out=None, b_out=None, g_out=None,
+                           fallback_out=None, sample_f_out=None, strict_inside: bool = False, stream=None,
+                           allow_not_converged: bool = False):
+    """Transfer with the surrogate network `net` (Mlp or None) backed by the
+    exact source `exact` (Source or None). Outputs as sft_transfer (numpy for
+    host, CUDA tensors for device). Returns (status, stats dict, u_out)."""
+    if u_out is None:
+        u_out = np.zeros(_nv(tgt), np.float64)
+    up, udev, _ = _ptr(u_out)
+    ptrs = [_ptr(x) for x in (b_out, g_out, fallback_out, sample_f_out)]
+    for p, dv, _ in ptrs:
+        if p is not None and dv != udev:
+            raise ValueError("all outputs must be host arrays or all device tensors")
+    o = _options(samples_per_elem, seed, stream_id, alpha, cg_tol, cg_max_iter)
+    o.strict_inside = int(bool(strict_inside))
+    o.out_device = int(udev)
+    o.cuda_stream = stream if stream is not None else _current_stream()
+    so = sft_surrogate_opts()
+    so.exact_field = int(exact_field)
+    so.subsample = int(subsample)
+    so.tau = float(tau)
+    so.fallback_out = ptrs[2][0]
+    so.sample_f_out = ptrs[3][0]
+    st = sft_surrogate_stats()
+    allow = (SFT_OK, SFT_ERR_NOT_CONVERGED) if allow_not_converged else (SFT_OK,)
+    status = _check(lib().sft_transfer_surrogate(net.h if net is not None else None,
+                                                 exact.h if exact is not None else None, tgt.h, ctypes.byref(o),
+                                                 ctypes.byref(so), up, ptrs[0][0], ptrs[1][0], ctypes.byref(st)),
+                    "sft_transfer_surrogate", allow)
+    return status, st.as_dict(), u_out
 
 
 def sft_source_grid(src: Source, precision: int):

@@ -47,37 +47,6 @@ static sft_status init_device_pool() {
   return SFT_OK;
 }
 
-// RAII device scratch on a stream
-template <typename T>
-struct DevBuf {
-  T* p = nullptr;
-  cudaStream_t s = nullptr;
-  explicit DevBuf(cudaStream_t st) : s(st) {}
-  cudaError_t alloc(size_t n) { return dalloc(&p, n, s); }
-  ~DevBuf() { dfree(p, s); }
-};
-
-struct Events {
-  cudaEvent_t e[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  bool ok = false;
-  Events() {
-    ok = true;
-    for (auto& x : e) ok = ok && cudaEventCreate(&x) == cudaSuccess;
-  }
-  ~Events() {
-    for (auto& x : e)
-      if (x) cudaEventDestroy(x);
-  }
-  float ms(int a, int b) const {
-    float t = 0.f;
-    if (ok && cudaEventElapsedTime(&t, e[a], e[b]) != cudaSuccess) {
-      t = -1.f;
-      cudaGetLastError();  // timing unavailable: do not leave a sticky error behind
-    }
-    return t;
-  }
-};
-
 static sft_status check_desc(const sft_mesh_desc* d, bool source) {
   if (!d) return fail(SFT_ERR_ARG, "null mesh descriptor");
   if (d->dim != 2 && d->dim != 3) return fail(SFT_ERR_ARG, "dim must be 2 or 3");

@@ -34,6 +34,37 @@ void dfree(T*& p, cudaStream_t s) {
   p = nullptr;
 }
 
+// RAII device scratch on a stream
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  cudaStream_t s = nullptr;
+  explicit DevBuf(cudaStream_t st) : s(st) {}
+  cudaError_t alloc(size_t n) { return dalloc(&p, n, s); }
+  ~DevBuf() { dfree(p, s); }
+};
+
+struct Events {
+  cudaEvent_t e[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool ok = false;
+  Events() {
+    ok = true;
+    for (auto& x : e) ok = ok && cudaEventCreate(&x) == cudaSuccess;
+  }
+  ~Events() {
+    for (auto& x : e)
+      if (x) cudaEventDestroy(x);
+  }
+  float ms(int a, int b) const {
+    float t = 0.f;
+    if (ok && cudaEventElapsedTime(&t, e[a], e[b]) != cudaSuccess) {
+      t = -1.f;
+      cudaGetLastError();  // timing unavailable: do not leave a sticky error behind
+    }
+    return t;
+  }
+};
+
 // location structure of a source mesh in one precision
 struct Locator {
   bool built = false;

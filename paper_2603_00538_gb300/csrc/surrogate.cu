@@ -1,0 +1,555 @@
+// The learned surrogate source: the control-variate Monte Carlo assembly of
+// Sec. 4 (steps 1-7) with the black-box query of step 4 answered by the
+// surrogate network instead of a mesh location, plus a per-element exact
+// fallback, and the training set drawn from the exact source.
+//
+// Fused assembly kernel, one 128-thread CTA per SM, persistent over tiles of
+// 128 samples (thread r owns sample row r):
+//   Philox -> barycentrics -> X (FP32)  ->  network on the tensor cores
+//   (tcgen05, FP32 accumulation in tensor memory)  ->  exact subsample test
+//   ->  residual r = f - alpha sum_m g_m lambda_m  ->  r lambda_i partials
+//   ->  warp-segmented compensated sums  ->  per-element epilogue + FP64
+//   atomics into b.
+// Tiles hold EPB = floor(128/N) whole elements when N <= 128; an element with
+// N > 128 samples spans ceil(N/128) consecutive tiles of one CTA.
+//
+// Fallback: the first s samples of every element are also queried exactly
+// (a location of X's first d_s coordinates in the exact source mesh). If any
+// of them differs from the network by more than tau (or is not finite), the
+// whole element uses exact queries for all N samples.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include "accum.cuh"
+#include "mlp.cuh"
+
+namespace sft {
+
+struct SurParams {
+  int64_t nv, ne, nes;   // target nodes, target elements, exact-source elements
+  int64_t nunits;        // work units: element groups (N <= 128) or elements (N > 128)
+  int N, EPB, nsub, s;   // samples per element, elements per tile, tiles per element, subsample
+  int exact_field;
+  int has_exact;
+  PhiloxKey key;
+  uint32_t stream_id;
+  float alpha, tau, cdet, cmc;
+};
+
+// shared memory: [network tile (NET only)] + per-row partial pieces +
+// per-element fallback flags
+constexpr uint32_t kSmemPieces = kTileM * 8 * 4 + kTileM * 4;
+constexpr uint32_t kSmemSur = kSmemFwd + kSmemPieces;
+
+template <int DS>
+__device__ __forceinline__ float exact_value(const GridP<float>& gr, const int32_t* __restrict__ cell_start,
+                                             const int32_t* __restrict__ cell_items, const float* __restrict__ recs,
+                                             const float* __restrict__ vals, int64_t nes, int field, const float* X,
+                                             int& n_empty) {
+  float Xs[DS];
+#pragma unroll
+  for (int a = 0; a < DS; ++a) Xs[a] = X[a];
+  float mu[DS + 1];
+  int status;
+  const int32_t e = locate_point<DS, float>(gr, cell_start, cell_items, recs, Xs, mu, status);
+  n_empty += status == 2;
+  return e >= 0 ? eval_p1<DS, float>(vals, nes, field, e, mu) : 0.f;
+}
+
+// NET = false: every query exact (the plain mesh-query transfer on the same
+// sampler and launch shape, the comparison point of the surrogate).
+template <int DT, int DS, bool NET>
+__global__ void __launch_bounds__(128, 1) k_surrogate_assemble(
+    const float* __restrict__ P, const __nv_bfloat16* __restrict__ W2, const __nv_bfloat16* __restrict__ W3,
+    const __nv_bfloat16* __restrict__ W4, const float* __restrict__ tx, const int32_t* __restrict__ tconn,
+    const float* __restrict__ vol32, const float* __restrict__ g, const GridP<float>* __restrict__ gp,
+    const int32_t* __restrict__ cell_start, const int32_t* __restrict__ cell_items, const float* __restrict__ recs,
+    const float* __restrict__ vals, SurParams p, double* __restrict__ b, int32_t* __restrict__ fb_out,
+    float* __restrict__ sample_f, int64_t* __restrict__ counters, int32_t* err) {
+  constexpr int K = DT + 1;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  MlpSmem S = mlp_smem(sm);
+  constexpr uint32_t off = NET ? kSmemFwd : 0;
+  float(*piece)[8] = reinterpret_cast<float(*)[8]>(sm + off);  // [row][s_i, e_i]
+  int* s_flag = reinterpret_cast<int*>(sm + off + kTileM * 8 * 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t taddr = 0;
+  if (NET) {
+    if (warp == 0) {
+      tc::tmem_alloc(S.slot, kH);
+      tc::tmem_relinquish();
+    }
+    if (threadIdx.x == 0) tc::mbar_init(S.bar, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    taddr = *S.slot;
+  }
+  GridP<float> gr;
+  if (p.has_exact) gr = *gp;
+  uint32_t phase = 0;
+  bool ok = true;
+  int64_t n_exact = 0, n_fb = 0;
+  int n_empty = 0;
+  Acc<float> acc_long;  // N > 128: thread i < K carries node i's sum over the element's tiles
+  const int row = threadIdx.x;
+
+  for (int64_t unit = blockIdx.x; ok && unit < p.nunits; unit += gridDim.x) {
+    s_flag[row] = NET ? 0 : 1;
+    acc_long = Acc<float>();
+    __syncthreads();
+    for (int c = 0; c < p.nsub; ++c) {
+      int el, j;
+      int64_t t;
+      bool valid;
+      if (p.nsub == 1) {
+        el = row / p.N;
+        j = row - el * p.N;
+        t = unit * p.EPB + el;
+        valid = el < p.EPB && t < p.ne;
+      } else {
+        el = 0;
+        j = c * kTileM + row;
+        t = unit;
+        valid = j < p.N;
+      }
+      float lam[K], X[DT];
+      int32_t v[K];
+#pragma unroll
+      for (int m = 0; m < K; ++m) { lam[m] = 0.f; v[m] = 0; }
+#pragma unroll
+      for (int a = 0; a < DT; ++a) X[a] = 0.f;
+      if (valid) {
+        float xv[K][DT];
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+          v[m] = __ldg(tconn + t * K + m);
+#pragma unroll
+          for (int a = 0; a < DT; ++a) xv[m][a] = __ldg(tx + (int64_t)v[m] * DT + a);
+        }
+        if constexpr (DT == 2) {
+          const uint4 w = philox4x32_10(make_uint4((uint32_t)(j >> 1), (uint32_t)t, p.stream_id, 0u), p.key);
+          if (j & 1) osada_weights<float>(w.z, w.w, lam);
+          else osada_weights<float>(w.x, w.y, lam);
+        } else {
+          const uint4 w = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)t, p.stream_id, 0u), p.key);
+          spacing_weights<float>(w.x, w.y, w.z, lam);
+        }
+        map_point<DT, float>(lam, xv, X);
+      }
+      // exact subsample (or every query when the network is off)
+      float fe = 0.f;
+      const bool sub = p.has_exact && valid && (!NET || j < p.s);
+      if (sub) {
+        fe = exact_value<DS>(gr, cell_start, cell_items, recs, vals, p.nes, p.exact_field, X, n_empty);
+        ++n_exact;
+      }
+      float f = fe;
+      if (NET) {
+        const float x3[3] = {X[0], X[1], DT == 3 ? X[DT - 1] : 0.f};
+        float y = 0.f;
+        ok = mlp_tile(S, P, W2, W3, W4, x3, taddr, phase, err, y);
+        if (!ok) break;
+        if (sub && !(fabsf(y - fe) <= p.tau)) s_flag[el] = 1;
+        __syncthreads();
+        const bool fb = s_flag[el] != 0;
+        if (fb && valid && !sub) {
+          fe = exact_value<DS>(gr, cell_start, cell_items, recs, vals, p.nes, p.exact_field, X, n_empty);
+          ++n_exact;
+        }
+        f = fb ? fe : y;
+        if (valid && c == 0 && j == 0) {
+          n_fb += fb;
+          if (fb_out) fb_out[t] = fb ? 1 : 0;
+        }
+      } else if (valid && c == 0 && j == 0 && fb_out) {
+        fb_out[t] = 1;
+      }
+      if (valid && sample_f) sample_f[t * p.N + j] = f;
+
+      // residual against the P1 control and its basis-weighted partials
+      Acc<float> a[K];
+      if (valid) {
+        float gX = __fmul_rn(__ldg(g + v[0]), lam[0]);
+#pragma unroll
+        for (int m = 1; m < K; ++m) gX = __fmaf_rn(__ldg(g + v[m]), lam[m], gX);
+        const float r = __fsub_rn(f, __fmul_rn(p.alpha, gX));
+#pragma unroll
+        for (int i = 0; i < K; ++i) a[i].add(__fmul_rn(r, lam[i]));
+      }
+      // warp-segmented suffix combine over rows of the same element
+      const int seg = valid ? el : -1;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int seg2 = __shfl_down_sync(0xffffffffu, seg, o);
+        const bool take = lane + o < 32 && seg2 == seg;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          const float s2 = __shfl_down_sync(0xffffffffu, a[i].s, o);
+          const float e2 = __shfl_down_sync(0xffffffffu, a[i].e, o);
+          if (take) a[i].combine(s2, e2);
+        }
+      }
+      const int seg_prev = __shfl_up_sync(0xffffffffu, seg, 1);
+      const bool head = valid && (lane == 0 || seg_prev != seg);
+      if (head) {
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          piece[row][2 * i] = a[i].s;
+          piece[row][2 * i + 1] = a[i].e;
+        }
+      }
+      __syncthreads();
+      // combine the pieces of each element (heads at its first row and at
+      // every warp boundary inside it), in row order
+      if (p.nsub == 1) {
+        for (int q = threadIdx.x; q < p.EPB * K; q += blockDim.x) {
+          const int e2 = q / K, i = q - e2 * K;
+          const int64_t t2 = unit * p.EPB + e2;
+          if (t2 >= p.ne) continue;
+          const int r0 = e2 * p.N, r1 = r0 + p.N;
+          Acc<float> acc;
+          for (int hr = r0; hr < r1; hr = (hr & ~31) + 32) acc.combine(piece[hr][2 * i], piece[hr][2 * i + 1]);
+          int32_t vv[K];
+          float gv[K];
+#pragma unroll
+          for (int m = 0; m < K; ++m) {
+            vv[m] = __ldg(tconn + t2 * K + m);
+            gv[m] = __ldg(g + vv[m]);
+          }
+          float gsum = gv[0];
+#pragma unroll
+          for (int m = 1; m < K; ++m) gsum = __fadd_rn(gsum, gv[m]);
+          float gi = gv[0];
+#pragma unroll
+          for (int m = 1; m < K; ++m) gi = i == m ? gv[m] : gi;
+          int32_t vi = vv[0];
+#pragma unroll
+          for (int m = 1; m < K; ++m) vi = i == m ? vv[m] : vi;
+          atomicAdd(b + vi, Epi<float>::contrib(__ldg(vol32 + t2), 0.0, p.cdet, p.cmc, gsum, gi, acc));
+        }
+      } else if (threadIdx.x < K) {
+        const int i = threadIdx.x;
+        const int nrow = min(kTileM, p.N - c * kTileM);
+        for (int hr = 0; hr < nrow; hr += 32) acc_long.combine(piece[hr][2 * i], piece[hr][2 * i + 1]);
+        if (c == p.nsub - 1) {
+          int32_t vv[K];
+          float gv[K];
+#pragma unroll
+          for (int m = 0; m < K; ++m) {
+            vv[m] = __ldg(tconn + unit * K + m);
+            gv[m] = __ldg(g + vv[m]);
+          }
+          float gsum = gv[0];
+#pragma unroll
+          for (int m = 1; m < K; ++m) gsum = __fadd_rn(gsum, gv[m]);
+          atomicAdd(b + vv[i], Epi<float>::contrib(__ldg(vol32 + unit), 0.0, p.cdet, p.cmc, gsum, gv[i], acc_long));
+        }
+      }
+      __syncthreads();  // pieces and flags are reused by the next tile
+    }
+  }
+  if (counters) {
+    const int64_t e1 = warp_sum<int64_t>(n_exact), f1 = warp_sum<int64_t>(n_fb);
+    const int m1 = warp_sum<int>(n_empty);
+    if (lane == 0) {
+      if (e1) atomicAdd(reinterpret_cast<unsigned long long*>(counters), (unsigned long long)e1);
+      if (f1) atomicAdd(reinterpret_cast<unsigned long long*>(counters + 1), (unsigned long long)f1);
+      if (m1) atomicAdd(reinterpret_cast<unsigned long long*>(counters + 2), (unsigned long long)m1);
+    }
+  }
+  if (NET) {
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(taddr, kH);
+  }
+}
+
+// target nodes [nv][d] -> network inputs [nv][3] (z = 0 in 2D)
+__global__ void k_pad3(const float* __restrict__ x, int64_t nv, int d, float* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+    out[i * 3] = x[i * d];
+    out[i * 3 + 1] = x[i * d + 1];
+    out[i * 3 + 2] = d == 3 ? x[i * d + 2] : 0.f;
+  }
+}
+
+// control values from the exact source (network off): FP32 g at target nodes
+template <int DS>
+__global__ void k_exact_nodes(const float* __restrict__ x, int64_t nv, int d, const GridP<float>* __restrict__ gp,
+                              const int32_t* __restrict__ cell_start, const int32_t* __restrict__ cell_items,
+                              const float* __restrict__ recs, const float* __restrict__ vals, int64_t nes, int field,
+                              float* __restrict__ out, int64_t* __restrict__ counters) {
+  const GridP<float> gr = *gp;
+  int n_empty = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+    float X[3] = {x[i * d], x[i * d + 1], d == 3 ? x[i * d + 2] : 0.f};
+    out[i] = exact_value<DS>(gr, cell_start, cell_items, recs, vals, nes, field, X, n_empty);
+  }
+  const int m1 = warp_sum<int>(n_empty);
+  if ((threadIdx.x & 31) == 0 && m1) atomicAdd(reinterpret_cast<unsigned long long*>(counters + 2), (unsigned long long)m1);
+}
+
+// Training set: point j = lo + u * (hi - lo) per axis, u from Philox counter
+// (j_lo, j_hi, stream, 1) words 0..2 (FP32: one rounded product, one rounded
+// sum); value = exact source at the point's first d_s coordinates.
+template <int DS>
+__global__ void k_dataset(int64_t n, PhiloxKey key, uint32_t stream_id, float3 lo, float3 w,
+                          const GridP<float>* __restrict__ gp, const int32_t* __restrict__ cell_start,
+                          const int32_t* __restrict__ cell_items, const float* __restrict__ recs,
+                          const float* __restrict__ vals, int64_t nes, int field, float* __restrict__ pts,
+                          float* __restrict__ f, unsigned int* __restrict__ maxabs, int64_t* __restrict__ counters) {
+  const GridP<float> gr = *gp;
+  int n_empty = 0;
+  float mx = 0.f;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)(j >> 32), stream_id, 1u), key);
+    float X[3];
+    X[0] = __fadd_rn(lo.x, __fmul_rn(u01f(r.x), w.x));
+    X[1] = __fadd_rn(lo.y, __fmul_rn(u01f(r.y), w.y));
+    X[2] = __fadd_rn(lo.z, __fmul_rn(u01f(r.z), w.z));
+    const float v = exact_value<DS>(gr, cell_start, cell_items, recs, vals, nes, field, X, n_empty);
+    pts[j * 3] = X[0];
+    pts[j * 3 + 1] = X[1];
+    pts[j * 3 + 2] = X[2];
+    f[j] = v;
+    mx = fmaxf(mx, fabsf(v));
+  }
+  for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const int m1 = warp_sum<int>(n_empty);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(maxabs, __float_as_uint(mx));  // non-negative floats order as their bit patterns
+    if (m1) atomicAdd(reinterpret_cast<unsigned long long*>(counters), (unsigned long long)m1);
+  }
+}
+
+template <int DT, int DS, bool NET>
+static sft_status launch_sur(sft_mlp_s* m, sft_source_s* s, sft_target_s* t, const SurParams& p, const float* g,
+                             double* b, int32_t* fb, float* sf, int64_t* counters, int32_t* err, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    SFT_CUDA(cudaFuncSetAttribute(k_surrogate_assemble<DT, DS, NET>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kSmemSur));
+    attr = true;
+  }
+  int dev = 0, sms = 0;
+  SFT_CUDA(cudaGetDevice(&dev));
+  SFT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(p.nunits, sms));
+  const Locator* L = s ? &s->loc[SFT_PREC_FP32] : nullptr;
+  ::sft::note_launch(), k_surrogate_assemble<DT, DS, NET><<<grid, 128, NET ? kSmemSur : kSmemPieces, st>>>(
+      m ? m->P : nullptr, m ? m->W[0] : nullptr, m ? m->W[1] : nullptr, m ? m->W[2] : nullptr,
+      (const float*)t->coordsP[SFT_PREC_FP32], t->conn, t->vol32, g, L ? (const GridP<float>*)L->grid : nullptr,
+      L ? L->cell_start : nullptr, L ? L->cell_items : nullptr, L ? (const float*)L->recs : nullptr,
+      L ? (const float*)L->vals : nullptr, p, b, fb, sf, counters, err);
+  SFT_CUDA(cudaGetLastError());
+  return SFT_OK;
+}
+
+}  // namespace sft
+
+using namespace sft;
+
+extern "C" {
+
+sft_status sft_surrogate_dataset(sft_source s, int32_t field, int64_t n, uint64_t seed, uint32_t stream_id,
+                                 const float* box_lo, const float* box_hi, float* pts_out, float* f_out,
+                                 float* max_abs_out, void* cuda_stream) {
+  if (!s || !box_lo || !box_hi || (n > 0 && (!pts_out || !f_out))) return fail(SFT_ERR_ARG, "null argument");
+  if (field < 0 || field >= s->nf) return fail(SFT_ERR_ARG, "field out of range");
+  if (n < 0) return fail(SFT_ERR_ARG, "n < 0");
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(box_lo[a]) || !std::isfinite(box_hi[a]) || !(box_hi[a] >= box_lo[a]))
+      return fail(SFT_ERR_ARG, "bad box");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  DevBuf<int32_t> d_err(st);
+  DevBuf<int64_t> counters(st);
+  DevBuf<unsigned int> mx(st);
+  SFT_CUDA(d_err.alloc(1));
+  SFT_CUDA(counters.alloc(1));
+  SFT_CUDA(mx.alloc(1));
+  SFT_CUDA(cudaMemsetAsync(d_err.p, 0, sizeof(int32_t), st));
+  SFT_CUDA(cudaMemsetAsync(counters.p, 0, sizeof(int64_t), st));
+  SFT_CUDA(cudaMemsetAsync(mx.p, 0, sizeof(unsigned int), st));
+  if (sft_status r = build_locator(s, SFT_PREC_FP32, st, d_err.p)) return r;
+  const Locator& L = s->loc[SFT_PREC_FP32];
+  PhiloxKey key{(uint32_t)seed, (uint32_t)(seed >> 32)};
+  const float3 lo = make_float3(box_lo[0], box_lo[1], box_lo[2]);
+  const float3 w = make_float3(box_hi[0] - box_lo[0], box_hi[1] - box_lo[1], box_hi[2] - box_lo[2]);
+  if (n > 0) {
+    const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16);
+#define SFT_DS(DSV)                                                                                               \
+  ::sft::note_launch(), k_dataset<DSV><<<blocks, 256, 0, st>>>(n, key, stream_id, lo, w, (const GridP<float>*)L.grid, \
+                                                              L.cell_start, L.cell_items, (const float*)L.recs,   \
+                                                              (const float*)L.vals, s->ne, field, pts_out, f_out, \
+                                                              mx.p, counters.p)
+    if (s->dim == 2) SFT_DS(2); else SFT_DS(3);
+#undef SFT_DS
+    SFT_CUDA(cudaGetLastError());
+  }
+  unsigned int hm = 0;
+  int32_t herr = 0;
+  SFT_CUDA(cudaMemcpyAsync(&hm, mx.p, sizeof(hm), cudaMemcpyDeviceToHost, st));
+  SFT_CUDA(cudaMemcpyAsync(&herr, d_err.p, sizeof(herr), cudaMemcpyDeviceToHost, st));
+  SFT_CUDA(cudaStreamSynchronize(st));
+  if (herr) return fail(SFT_ERR_DEVICE_STATUS, "source location structure build failed");
+  if (max_abs_out) std::memcpy(max_abs_out, &hm, sizeof(float));
+  return SFT_OK;
+}
+
+sft_status sft_transfer_surrogate(sft_mlp net, sft_source exact, sft_target t, const sft_options* o,
+                                  const sft_surrogate_opts* so, double* u_out, double* b_out, double* g_out,
+                                  sft_surrogate_stats* stats) {
+  if (!t || !o || !so || !u_out) return fail(SFT_ERR_ARG, "null argument");
+  if (!net && !exact) return fail(SFT_ERR_ARG, "need a network, an exact source or both");
+  if (o->precision != SFT_PREC_FP32) return fail(SFT_ERR_UNSUPPORTED, "the surrogate path computes in FP32 (BF16 network)");
+  if (o->samples_per_elem < 1) return fail(SFT_ERR_ARG, "samples_per_elem must be >= 1");
+  if ((int64_t)o->samples_per_elem * t->ne >= ((int64_t)1 << 40)) return fail(SFT_ERR_UNSUPPORTED, "too many samples");
+  if (o->cg_max_iter < 0 || !(o->cg_tol >= 0) || !std::isfinite(o->alpha)) return fail(SFT_ERR_ARG, "bad solver options");
+  if (exact) {
+    if (exact->dim > t->dim) return fail(SFT_ERR_ARG, "exact source dimension exceeds the target's");
+    if (so->exact_field < 0 || so->exact_field >= exact->nf) return fail(SFT_ERR_ARG, "exact_field out of range");
+  }
+  if (net && exact && (so->subsample < 0 || so->subsample > std::min(o->samples_per_elem, kTileM)))
+    return fail(SFT_ERR_ARG, "subsample must be in 0..min(N, 128)");
+  if (net && exact && !(so->tau >= 0.f)) return fail(SFT_ERR_ARG, "tau must be >= 0");
+  cudaStream_t st = (cudaStream_t)o->cuda_stream;
+  const int64_t nv = t->nv, ne = t->ne;
+  const int N = o->samples_per_elem;
+  Events ev;
+  if (ev.ok) cudaEventRecord(ev.e[0], st);
+  DevBuf<int32_t> d_err(st), fb_tmp(st);
+  DevBuf<float> g(st), pts3(st), sf_tmp(st);
+  DevBuf<double> b(st), u_tmp(st);
+  DevBuf<int64_t> counters(st);
+  SFT_CUDA(d_err.alloc(1));
+  SFT_CUDA(cudaMemsetAsync(d_err.p, 0, sizeof(int32_t), st));
+  if (exact) {
+    if (sft_status r = build_locator(exact, SFT_PREC_FP32, st, d_err.p)) return r;
+  }
+  if (sft_status r = target_coordsP(t, SFT_PREC_FP32, st)) return r;
+  SFT_CUDA(g.alloc((size_t)nv));
+  SFT_CUDA(b.alloc((size_t)nv));
+  SFT_CUDA(counters.alloc(3));
+  SFT_CUDA(cudaMemsetAsync(b.p, 0, sizeof(double) * nv, st));
+  SFT_CUDA(cudaMemsetAsync(counters.p, 0, sizeof(int64_t) * 3, st));
+  const float* tx = (const float*)t->coordsP[SFT_PREC_FP32];
+  if (ev.ok) cudaEventRecord(ev.e[1], st);
+
+  // step 1: control values at the target nodes (network, or exact without one)
+  const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nv + 255) / 256, 152 * 16));
+  if (net) {
+    SFT_CUDA(pts3.alloc((size_t)nv * 3));
+    ::sft::note_launch(), k_pad3<<<nb, 256, 0, st>>>(tx, nv, t->dim, pts3.p);
+    SFT_CUDA(cudaGetLastError());
+    if (sft_status r = mlp_forward_dev(net, nv, pts3.p, g.p, st, d_err.p)) return r;
+  } else {
+    const Locator& L = exact->loc[SFT_PREC_FP32];
+#define SFT_EN(DSV)                                                                                             \
+  ::sft::note_launch(), k_exact_nodes<DSV><<<nb, 256, 0, st>>>(tx, nv, t->dim, (const GridP<float>*)L.grid,     \
+                                                              L.cell_start, L.cell_items, (const float*)L.recs, \
+                                                              (const float*)L.vals, exact->ne, so->exact_field, \
+                                                              g.p, counters.p)
+    if (exact->dim == 2) SFT_EN(2); else SFT_EN(3);
+#undef SFT_EN
+    SFT_CUDA(cudaGetLastError());
+  }
+  if (ev.ok) cudaEventRecord(ev.e[2], st);
+
+  // steps 2-6: fused sample / network / fallback / scatter
+  SurParams p{};
+  p.nv = nv;
+  p.ne = ne;
+  p.nes = exact ? exact->ne : 0;
+  p.N = N;
+  if (N <= kTileM) {
+    p.EPB = kTileM / N;
+    p.nsub = 1;
+    p.nunits = (ne + p.EPB - 1) / p.EPB;
+  } else {
+    p.EPB = 1;
+    p.nsub = (N + kTileM - 1) / kTileM;
+    p.nunits = ne;
+  }
+  p.s = (net && exact) ? so->subsample : 0;
+  p.exact_field = so->exact_field;
+  p.has_exact = exact && (!net || p.s > 0) ? 1 : 0;
+  p.key.k0 = (uint32_t)o->seed;
+  p.key.k1 = (uint32_t)(o->seed >> 32);
+  p.stream_id = o->stream_id;
+  p.alpha = (float)o->alpha;
+  p.tau = so->tau;
+  p.cdet = (float)(o->alpha / (double)((t->dim + 1) * (t->dim + 2)));
+  p.cmc = (float)(1.0 / (double)N);
+  int32_t* fb = nullptr;
+  float* sf = nullptr;
+  if (so->fallback_out) {
+    if (o->out_device) fb = so->fallback_out;
+    else { SFT_CUDA(fb_tmp.alloc((size_t)ne)); fb = fb_tmp.p; }
+  }
+  if (so->sample_f_out) {
+    if (o->out_device) sf = so->sample_f_out;
+    else { SFT_CUDA(sf_tmp.alloc((size_t)ne * N)); sf = sf_tmp.p; }
+  }
+  const int ds = exact ? exact->dim : 2;
+  sft_status lr = SFT_OK;
+  if (net) {
+    if (t->dim == 2) lr = launch_sur<2, 2, true>(net, exact, t, p, g.p, b.p, fb, sf, counters.p, d_err.p, st);
+    else if (ds == 2) lr = launch_sur<3, 2, true>(net, exact, t, p, g.p, b.p, fb, sf, counters.p, d_err.p, st);
+    else lr = launch_sur<3, 3, true>(net, exact, t, p, g.p, b.p, fb, sf, counters.p, d_err.p, st);
+  } else {
+    if (t->dim == 2) lr = launch_sur<2, 2, false>(nullptr, exact, t, p, g.p, b.p, fb, sf, counters.p, d_err.p, st);
+    else if (ds == 2) lr = launch_sur<3, 2, false>(nullptr, exact, t, p, g.p, b.p, fb, sf, counters.p, d_err.p, st);
+    else lr = launch_sur<3, 3, false>(nullptr, exact, t, p, g.p, b.p, fb, sf, counters.p, d_err.p, st);
+  }
+  if (lr) return lr;
+  if (ev.ok) cudaEventRecord(ev.e[3], st);
+
+  // step 7: M u = b
+  double* u_dev = u_out;
+  if (!o->out_device) {
+    SFT_CUDA(u_tmp.alloc((size_t)nv));
+    u_dev = u_tmp.p;
+  }
+  SolveResult sr;
+  if (sft_status r = mass_solve(t, 1, b.p, u_dev, o->cg_tol, o->cg_max_iter, st, d_err.p, &sr)) return r;
+  if (ev.ok) cudaEventRecord(ev.e[4], st);
+
+  const cudaMemcpyKind d2o = o->out_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (!o->out_device) SFT_CUDA(cudaMemcpyAsync(u_out, u_dev, sizeof(double) * nv, d2o, st));
+  if (b_out) SFT_CUDA(cudaMemcpyAsync(b_out, b.p, sizeof(double) * nv, d2o, st));
+  DevBuf<double> g64(st);
+  if (g_out) {
+    SFT_CUDA(g64.alloc((size_t)nv));
+    if (sft_status r = convert_coords(g.p, SFT_F32, g64.p, SFT_PREC_FP64, nv, st)) return r;
+    SFT_CUDA(cudaMemcpyAsync(g_out, g64.p, sizeof(double) * nv, d2o, st));
+  }
+  if (fb && !o->out_device) SFT_CUDA(cudaMemcpyAsync(so->fallback_out, fb, sizeof(int32_t) * ne, d2o, st));
+  if (sf && !o->out_device) SFT_CUDA(cudaMemcpyAsync(so->sample_f_out, sf, sizeof(float) * ne * N, d2o, st));
+  int64_t hc[3] = {0, 0, 0};
+  int32_t herr = 0;
+  SFT_CUDA(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
+  SFT_CUDA(cudaMemcpyAsync(&herr, d_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  if (ev.ok) cudaEventRecord(ev.e[5], st);
+  SFT_CUDA(cudaStreamSynchronize(st));
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->cg_iters = sr.iters;
+    stats->cg_rel_resid = sr.rel_resid;
+    stats->net_queries = net ? nv + ne * (int64_t)N : 0;
+    stats->exact_queries = hc[0] + (net ? 0 : nv);
+    stats->fallback_elems = net ? hc[1] : ne;
+    stats->empty_queries = hc[2];
+    stats->ms_control = ev.ms(1, 2);
+    stats->ms_assembly = ev.ms(2, 3);
+    stats->ms_solve = ev.ms(3, 4);
+    stats->ms_total = ev.ms(0, 5);
+  }
+  if (herr) return fail(SFT_ERR_DEVICE_STATUS, "a surrogate kernel reported an error");
+  if (o->strict_inside && hc[2] > 0) return fail(SFT_ERR_OUTSIDE, "an exact query fell in an empty grid cell");
+  if (!sr.converged && o->cg_max_iter > 0) return fail(SFT_ERR_NOT_CONVERGED, "CG reached cg_max_iter");
+  return SFT_OK;
+}
+
+}  // extern "C"
