@@ -43,6 +43,11 @@ WORKLOADS = {
              "FP64 load vector and CG to 1e-10",
     "tet5m": "3D: 4,983,504-tet jittered Kuhn source (8 Gaussians + jump at z = 0.4, FP32) -> 2,958,234-tet "
              "target, N = 32, FP32 sampling + compensated partials, FP64 CG to 1e-10",
+    "sur3d": "surrogate source: the tri4m source field (3,998,792 triangles, Gaussian + jump, FP32) extruded "
+             "along z, learned by the 3-256-256-256-256-1 SiLU network (BF16 weights/activations, FP32 "
+             "accumulation) from 2,000,000 seeded exact queries, transferred onto the tet5m target "
+             "(2,958,234 tets) with N = 64; per-element exact fallback on the first 4 samples at "
+             "tau = 1e-2 max|f|; FP64 load vector and CG to 1e-10",
     "batch256": "256 batched requests, 2D/3D 50/50, 1e4..5e5 target elements (log-uniform, seeded), 1..8 fields, "
                 "N in {8,16,32,64,128}; 2D sources: 2,048- and 3,998,792-triangle meshes, 3D source: "
                 "4,983,504 tets, 8 fields each; one graph-replayed plan per step (control, persistent "
@@ -399,6 +404,202 @@ def run_batch(args):
         torch.distributed.destroy_process_group()
 
 
+# FLOPs of one network query: 2 * (3*256 + 3*256^2 + 256) multiply-adds
+NET_FLOP_PER_QUERY = 2 * (3 * 256 + 3 * 256 * 256 + 256)
+SUR_KERNEL_FILES = ["paper_2603_00538_gb300/csrc/surrogate.cu", "paper_2603_00538_gb300/csrc/mlp.cuh",
+                    "paper_2603_00538_gb300/csrc/tc.cuh"]
+
+
+def run_surrogate(args):
+    """Surrogate workload: the network is trained once (timed separately); a
+    step is one sft_transfer_surrogate (control at the target nodes from the
+    network, fused sampling / network / fallback / scatter kernel, FP64 CG)
+    plus the conservation error. Compared with the exact-only transfer of the
+    same source on the same samples (every query a mesh location)."""
+    import torch
+    import paper_2603_00538_gb300 as sft
+
+    rank, world, local = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    src, tgt, p = make_workload("sur3d", args.scale)
+    N, tol = p["samples_per_elem"], p["cg_tol"]
+    S = sft.mesh_source(src, device=dev)
+    T = sft.mesh_target(tgt, device=dev)
+    stream = torch.cuda.current_stream()
+    # training set and training (outside the timed region)
+    t0 = time.perf_counter()
+    pts, f, fmax = sft.sft_surrogate_dataset(S, p["train_points"], seed=1, stream_id=0)
+    torch.cuda.synchronize()
+    data_s = time.perf_counter() - t0
+    net = sft.sft_mlp_create(W.mlp_init(0).astype(np.float32))
+    t0 = time.perf_counter()
+    hist = sft.sft_mlp_train(net, pts, f, epochs=args.sur_epochs, batch=16384, lr=2e-3, lr_final=1e-4)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    tau = p["tau_rel"] * fmax
+    u = torch.zeros(tgt.nnodes, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    last = {}
+
+    def step():
+        _, st, _ = sft.sft_transfer_surrogate(net, S, T, N, seed=0, cg_tol=tol, subsample=p["subsample"], tau=tau,
+                                              u_out=u)
+        last["cons"] = sft.sft_conservation_error(S, T, u)
+        last.update(st)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    asm_ms = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+            asm_ms.append(last["ms_assembly"])
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+        torch.distributed.barrier()
+    ms_per_step = total_ms / args.steps
+    queries = int(last["net_queries"])
+    value = queries * world / (ms_per_step / 1e3)
+    launches = count_launches(step)
+    stats_sur = dict(last)
+    u_sur = u.clone()
+
+    # the same transfer with every query exact (no network)
+    ue = torch.zeros_like(u)
+    ex = {}
+    for _ in range(2):
+        _, ex, _ = sft.sft_transfer_surrogate(None, S, T, N, seed=0, cg_tol=tol, u_out=ue)
+    ex_ms = []
+    for k in range(max(3, min(args.steps, 10))):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, ex, _ = sft.sft_transfer_surrogate(None, S, T, N, seed=0, cg_tol=tol, u_out=ue)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ex_ms.append(a.elapsed_time(b))
+    cons_ex = sft.sft_conservation_error(S, T, ue)
+    m = torch.as_tensor(_lumped_mass(tgt)).to(dev)
+    rel_diff = float(torch.sqrt((m * (u_sur - ue) ** 2).sum() / (m * ue ** 2).sum()).item())
+
+    # end to end: target mesh from pinned host memory, u back to pinned memory
+    pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    tc_h, tk_h = pin(tgt.coords), pin(tgt.conn)
+    u_h = torch.zeros(tgt.nnodes, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        t_ = sft.sft_target_create(tc_h, tk_h)
+        sft.sft_transfer_surrogate(net, S, t_, N, seed=0, cg_tol=tol, subsample=p["subsample"], tau=tau, u_out=u_h)
+        t_.close()
+
+    e2e_step()
+    torch.cuda.synchronize()
+    k_e2e = max(1, min(args.steps, 3))
+    t1 = time.perf_counter()
+    for _ in range(k_e2e):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t1) * 1e3 / k_e2e
+
+    if rank == 0:
+        mean_asm = float(np.mean(asm_ms))
+        flops = NET_FLOP_PER_QUERY * tgt.nelems * N
+        achieved = flops / (mean_asm / 1e3) / 1e12
+        peak, which = tensor_peak()
+        cpu = None if args.skip_cpu else sur_cpu_baseline(src, tgt, p, net, tau)
+        line = {
+            "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "sur3d: " + WORKLOADS["sur3d"]
+                                   + ("" if args.scale == 1.0 else f" (element counts x{args.scale})"),
+                       "queries_per_step": queries, "target_elements": tgt.nelems, "samples_per_elem": N,
+                       "source_elements": src.nelems, "train_points": p["train_points"],
+                       "train_epochs": args.sur_epochs, "train_s": train_s, "dataset_s": data_s,
+                       "train_loss_first_last": [float(hist[0]), float(hist[-1])], "tau": tau,
+                       "l2": "flushed between steps (256 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "breakdown_ms": {"assembly_kernel": mean_asm, "control": stats_sur["ms_control"],
+                             "solve": stats_sur["ms_solve"], "transfer_call": stats_sur["ms_total"],
+                             "step_min": min(step_ms), "step_max": max(step_ms)},
+            "fallback": {"elements": int(stats_sur["fallback_elems"]),
+                         "fraction": stats_sur["fallback_elems"] / tgt.nelems,
+                         "exact_queries": int(stats_sur["exact_queries"])},
+            "accuracy": {"E_mass": last["cons"][0], "E_mass_exact_path": cons_ex[0],
+                         "rel_diff_u_vs_exact_path": rel_diff, "cg_iters": stats_sur["cg_iters"]},
+            "exact_path": {"ms_per_step": float(np.mean(ex_ms)), "assembly_ms": ex["ms_assembly"],
+                           "queries_per_s": (tgt.nelems * N + tgt.nnodes) / (float(np.mean(ex_ms)) / 1e3),
+                           "surrogate_over_exact_time": ms_per_step / float(np.mean(ex_ms))},
+            "roofline": {"kernel": "sft::k_surrogate_assemble", "bound": "tensor", "achieved": achieved,
+                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak_source": which, "algorithmic_flops": flops},
+            "cpu_baseline": cpu,
+            "e2e": {"value": queries / (e2e_ms / 1e3), "unit": "queries/s", "ms_per_step": e2e_ms, "steps": k_e2e,
+                    "h2d_bytes_per_step": int(tc_h.numel() * tc_h.element_size() + tk_h.numel() * tk_h.element_size()),
+                    "d2h_bytes_per_step": int(u_h.numel() * u_h.element_size()),
+                    "timing": "host wall clock: target mesh H2D + target setup, surrogate transfer, u D2H"},
+            "clocks": clk.summary(),
+            "gpu_launches": launches * args.steps if launches else None,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def tensor_peak():
+    """Dense BF16 tensor peak: the sustained (seconds-long) measurement, the
+    kernel runs inside a long step."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), "measured (sustained)"
+    return 1700.0, "fallback (sustained)"
+
+
+def _lumped_mass(mesh):
+    x = mesh.coords.astype(np.float64)[mesh.conn]
+    if mesh.conn.shape[1] == 3:
+        e1, e2 = x[:, 1] - x[:, 0], x[:, 2] - x[:, 0]
+        vol = 0.5 * (e1[:, 0] * e2[:, 1] - e1[:, 1] * e2[:, 0])
+    else:
+        vol = np.linalg.det(x[:, 1:] - x[:, :1]) / 6.0
+    m = np.zeros(mesh.coords.shape[0])
+    np.add.at(m, mesh.conn.ravel(), np.repeat(vol / mesh.conn.shape[1], mesh.conn.shape[1]))
+    return m
+
+
+def sur_cpu_baseline(src, tgt, p, net, tau, nelem=256):
+    """The oracle's surrogate transfer (FP64 network, FP32 sampler and
+    location) on the first `nelem` target elements (Morton order) with the
+    trained weights and the full exact source."""
+    import paper_2603_00538_gb300 as sft
+    from oracle import surrogate as OS
+    params = sft.sft_mlp_params(net).astype(np.float64)
+    tgt_s = _sample_target(tgt, nelem / tgt.nelems)
+    t0 = time.perf_counter()
+    OS.surrogate_transfer(params, tgt_s.coords, tgt_s.conn, p["samples_per_elem"],
+                          exact=(src.coords, src.conn, src.values[0]), tau=tau, s=p["subsample"])
+    dt = time.perf_counter() - t0
+    q = tgt_s.nelems * p["samples_per_elem"] + tgt_s.nnodes
+    return {"value": q / dt, "unit": "queries/s", "cores": 1, "kind": "oracle", "seconds": dt,
+            "sample": f"the first {tgt_s.nelems} target elements (Morton order) with the trained network and "
+                      f"the full exact source (grid build included), one oracle surrogate transfer"}
+
+
 def count_launches(step):
     """Kernels libsft launches in one step (its own launch counter)."""
     import torch
@@ -502,19 +703,48 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    src, tgt, p = make_workload(args.workload, args.scale)
-    tgt_s = _sample_target(tgt, args.cpu_frac)
-    for _ in range(args.warmup):
-        oracle_step(src, tgt_s, p)
-    times, q = [], 0
-    for _ in range(args.steps):
-        v, dt, _ = oracle_step(src, tgt_s, p)
-        times.append(dt)
+    if args.workload == "batch256":
+        import oracle
+        srcm, reqs = W.batch_workload(scale=args.scale)
+        q0 = [q for q in reqs if q["source"] == 0][:4]
+
+        def one():
+            t0 = time.perf_counter()
+            for q in q0:
+                oracle.transfer(W.Mesh(srcm[0].coords, srcm[0].conn, srcm[0].values[:q["nfields"]]),
+                                q["target"], 1, q["samples_per_elem"], cg_tol=1e-10)
+            return time.perf_counter() - t0
+        q = sum(q["elems"] * q["samples_per_elem"] + q["target"].nnodes for q in q0)
+        sample = f"the first {len(q0)} requests on the 2,048-triangle source per step, full oracle transfers"
+    elif args.workload == "sur3d":
+        from oracle import surrogate as OS
+        src, tgt, p = make_workload(args.workload, args.scale)
+        tgt_s = _sample_target(tgt, min(1.0, 64 / tgt.nelems))
+        params = W.mlp_init(0).astype(np.float32).astype(np.float64)
+        tau = p["tau_rel"] * float(np.abs(src.values[0]).max())
+
+        def one():
+            t0 = time.perf_counter()
+            OS.surrogate_transfer(params, tgt_s.coords, tgt_s.conn, p["samples_per_elem"],
+                                  exact=(src.coords, src.conn, src.values[0]), tau=tau, s=p["subsample"])
+            return time.perf_counter() - t0
         q = tgt_s.nelems * p["samples_per_elem"] + tgt_s.nnodes
+        sample = (f"the first {tgt_s.nelems} target elements (Morton order) per step, the initial network "
+                  f"weights, the full exact source (grid build included)")
+    else:
+        src, tgt, p = make_workload(args.workload, args.scale)
+        tgt_s = _sample_target(tgt, args.cpu_frac)
+
+        def one():
+            return oracle_step(src, tgt_s, p)[1]
+        q = tgt_s.nelems * p["samples_per_elem"] + tgt_s.nnodes
+        sample = (f"full source mesh and the first {tgt_s.nelems} target elements (Morton order, "
+                  f"{args.cpu_frac:.3g} of the workload) per step")
+    for _ in range(args.warmup):
+        one()
+    times = [one() for _ in range(args.steps)]
     ms = 1e3 * float(np.mean(times))
     value = q / (ms / 1e3)
-    sample = (f"full source mesh and the first {tgt_s.nelems} target elements (Morton order, "
-              f"{args.cpu_frac:.3g} of the workload) per step")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s",
         "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
@@ -538,6 +768,7 @@ def main():
     ap.add_argument("--cpu-frac-baseline", type=float, default=0.4,
                     help="fraction of the target elements in the cpu_baseline sample")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--sur-epochs", type=int, default=40, help="training epochs of the surrogate (sur3d)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="element-count scale of the workload (1 = the named workload)")
     args = ap.parse_args()
@@ -547,6 +778,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch256":
         run_batch(args)
+    elif args.workload == "sur3d":
+        run_surrogate(args)
     else:
         run_ours(args)
 

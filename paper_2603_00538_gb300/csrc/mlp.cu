@@ -75,10 +75,6 @@ struct GemmEpi {
 constexpr uint32_t kGemmA = kTileM * kKC * 2;   // 16 KiB per A chunk
 constexpr uint32_t kSmemGemm = 2 * kGemmA + 2 * kSmemB + 64;
 
-__device__ __forceinline__ float silu_grad(float z) {
-  const float sg = __fdividef(1.0f, 1.0f + __expf(-z));
-  return sg * (1.0f + z * (1.0f - sg));
-}
 
 template <int EPI>
 __global__ void __launch_bounds__(128, 1) k_gemm_tn(int64_t M, int64_t K, int64_t klen,

@@ -28,7 +28,16 @@ constexpr uint32_t kSmemB = kH * kKC * 2;           // 32 KiB
 constexpr uint32_t kSmemFwd = kSmemA + 2 * kSmemB + 64;
 constexpr uint32_t kIdesc = tc::idesc_bf16_f32(kTileM, kH);
 
+// SiLU z sigma(z), sigma(z) = 1 / (1 + e^-z): one exponential and one
+// reciprocal on the special-function unit. (The one-operation form
+// u + u tanh(u), u = z/2, loses accuracy to cancellation for z << 0: its
+// absolute error |u| 2^-11 exceeds the BF16 rounding of the activation.)
 __device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
+// d silu / dz = sigma(z) (1 + z (1 - sigma(z)))
+__device__ __forceinline__ float silu_grad(float z) {
+  const float sg = __fdividef(1.0f, 1.0f + __expf(-z));
+  return sg * __fmaf_rn(z, 1.0f - sg, 1.0f);
+}
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
 __device__ __forceinline__ void store_bf16x8(unsigned char* dst, const float* v) {

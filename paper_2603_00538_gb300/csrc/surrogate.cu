@@ -59,7 +59,7 @@ __device__ __forceinline__ float exact_value(const GridP<float>& gr, const int32
 // NET = false: every query exact (the plain mesh-query transfer on the same
 // sampler and launch shape, the comparison point of the surrogate).
 template <int DT, int DS, bool NET>
-__global__ void __launch_bounds__(128, 1) k_surrogate_assemble(
+__global__ void __launch_bounds__(128, NET ? 1 : 8) k_surrogate_assemble(
     const float* __restrict__ P, const __nv_bfloat16* __restrict__ W2, const __nv_bfloat16* __restrict__ W3,
     const __nv_bfloat16* __restrict__ W4, const float* __restrict__ tx, const int32_t* __restrict__ tconn,
     const float* __restrict__ vol32, const float* __restrict__ g, const GridP<float>* __restrict__ gp,
@@ -336,7 +336,9 @@ static sft_status launch_sur(sft_mlp_s* m, sft_source_s* s, sft_target_s* t, con
   int dev = 0, sms = 0;
   SFT_CUDA(cudaGetDevice(&dev));
   SFT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(p.nunits, sms));
+  // network on: one CTA per SM (all of shared memory, 256 TMEM columns);
+  // exact queries only: latency-bound location work, many CTAs per SM
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(p.nunits, (int64_t)sms * (NET ? 1 : 16)));
   const Locator* L = s ? &s->loc[SFT_PREC_FP32] : nullptr;
   ::sft::note_launch(), k_surrogate_assemble<DT, DS, NET><<<grid, 128, NET ? kSmemSur : kSmemPieces, st>>>(
       m ? m->P : nullptr, m ? m->W[0] : nullptr, m ? m->W[1] : nullptr, m ? m->W[2] : nullptr,

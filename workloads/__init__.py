@@ -282,6 +282,10 @@ def config_meshes(name: str, scale: float = 1.0):
       float32 coords; 2,000,000-triangle Delaunay target; N = 64.
     * ``tet5m``:   4,983,504-tet source (94^3 x 6), 8 Gaussians + jump;
       2,958,234-tet target (79^3 x 6, independent jitter); N = 32; float32.
+    * ``sur3d``:   the tri4m source field extruded along z, F(x,y,z) = f(x,y),
+      learned by the surrogate network from 2,000,000 seeded points, onto the
+      tet5m target with N = 64; exact fallback subsample s = 4,
+      tau = 1e-2 max |f| over the training set.
     """
     if name == "tri2k":
         n = max(2, int(round(32 * math.sqrt(scale))))
@@ -303,6 +307,15 @@ def config_meshes(name: str, scale: float = 1.0):
                                        [lambda x: field_gauss8_jump_3d(x, 0)]), np.float32)
         tgt = as_precision(morton_reorder(jittered_kuhn_mesh(nt, seed=1)), np.float32)
         return src, tgt, dict(samples_per_elem=32, dtype="float32", cg_tol=1e-10)
+    if name == "sur3d":
+        # the 2D source of tri4m, extruded along z, learned by the surrogate
+        # network and transferred onto the 3D target of tet5m with N = 64
+        n = max(2, int(round(1414 * math.sqrt(scale))))
+        src = as_precision(with_values(jittered_tri_mesh(n, seed=0), [field_gauss_jump_2d]), np.float32)
+        nt = max(2, int(round(79 * scale ** (1 / 3))))
+        tgt = as_precision(morton_reorder(jittered_kuhn_mesh(nt, seed=1)), np.float32)
+        return src, tgt, dict(samples_per_elem=64, dtype="float32", cg_tol=1e-10,
+                              train_points=max(4096, int(round(2_000_000 * scale))), subsample=4, tau_rel=1e-2)
     raise KeyError(name)
 
 
