@@ -15,28 +15,22 @@
 namespace sft {
 
 // Forward of the network on n points (x,y,z) [n][3] FP32 -> out [n] FP32.
-// One CTA of 128 threads per SM; thread i owns row i of each 128-point tile.
-__global__ void __launch_bounds__(128, 1) k_mlp_forward(const float* __restrict__ P, const __nv_bfloat16* __restrict__ W2,
-                                                        const __nv_bfloat16* __restrict__ W3,
-                                                        const __nv_bfloat16* __restrict__ W4, int64_t n,
-                                                        const float* __restrict__ pts, float* __restrict__ out,
-                                                        int32_t* err) {
+// Persistent CTAs of 256 threads (two per SM): each 128-point tile is
+// shared by the two column halves (mlp_tile).
+__global__ void __launch_bounds__(kTPR * kTileM, 2) k_mlp_forward(const float* __restrict__ P,
+                                                                  const __nv_bfloat16* __restrict__ W2,
+                                                                  const __nv_bfloat16* __restrict__ W3,
+                                                                  const __nv_bfloat16* __restrict__ W4, int64_t n,
+                                                                  const float* __restrict__ pts,
+                                                                  float* __restrict__ out, int32_t* err) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  MlpSmem S = mlp_smem(sm);
-  const int warp = threadIdx.x >> 5;
-  if (warp == 0) {
-    tc::tmem_alloc(S.slot, kH);
-    tc::tmem_relinquish();
-  }
-  if (threadIdx.x == 0) tc::mbar_init(S.bar, 1);
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  const uint32_t taddr = *S.slot;
+  const MlpSmem S = mlp_smem(sm);
+  const uint32_t taddr = mlp_setup(S, P);
   uint32_t phase = 0;
   bool ok = true;
+  const int row = threadIdx.x & (kTileM - 1);
   for (int64_t tile = blockIdx.x; ok && tile * kTileM < n; tile += gridDim.x) {
-    const int64_t gi = tile * kTileM + threadIdx.x;
+    const int64_t gi = tile * kTileM + row;
     float x[3] = {0.f, 0.f, 0.f};
     if (gi < n) {
       x[0] = pts[gi * 3];
@@ -45,12 +39,9 @@ __global__ void __launch_bounds__(128, 1) k_mlp_forward(const float* __restrict_
     }
     float y = 0.f;
     ok = mlp_tile(S, P, W2, W3, W4, x, taddr, phase, err, y);
-    if (ok && gi < n) out[gi] = y;
+    if (ok && gi < n && threadIdx.x < kTileM) out[gi] = y;
   }
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  if (warp == 0) tc::tmem_dealloc(taddr, kH);
+  mlp_teardown(taddr);
 }
 
 // ---------------------------------------------------------------------------
@@ -427,8 +418,9 @@ sft_status mlp_forward_dev(sft_mlp_s* m, int64_t n, const float* pts, float* out
   SFT_CUDA(cudaGetDevice(&dev));
   SFT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int64_t tiles = (n + kTileM - 1) / kTileM;
-  const unsigned grid = (unsigned)std::min<int64_t>(tiles, sms);
-  ::sft::note_launch(), k_mlp_forward<<<grid, 128, kSmemFwd, st>>>(m->P, m->W[0], m->W[1], m->W[2], n, pts, out, d_err);
+  const unsigned grid = (unsigned)std::min<int64_t>(tiles, 2 * (int64_t)sms);
+  ::sft::note_launch(), k_mlp_forward<<<grid, kTPR * kTileM, kSmemFwd, st>>>(m->P, m->W[0], m->W[1], m->W[2], n, pts,
+                                                                             out, d_err);
   SFT_CUDA(cudaGetLastError());
   return SFT_OK;
 }

@@ -59,7 +59,7 @@ __device__ __forceinline__ float exact_value(const GridP<float>& gr, const int32
 // NET = false: every query exact (the plain mesh-query transfer on the same
 // sampler and launch shape, the comparison point of the surrogate).
 template <int DT, int DS, bool NET>
-__global__ void __launch_bounds__(128, NET ? 1 : 8) k_surrogate_assemble(
+__global__ void __launch_bounds__(NET ? kTPR * kTileM : kTileM, NET ? 2 : 8) k_surrogate_assemble(
     const float* __restrict__ P, const __nv_bfloat16* __restrict__ W2, const __nv_bfloat16* __restrict__ W3,
     const __nv_bfloat16* __restrict__ W4, const float* __restrict__ tx, const int32_t* __restrict__ tconn,
     const float* __restrict__ vol32, const float* __restrict__ g, const GridP<float>* __restrict__ gp,
@@ -72,19 +72,9 @@ __global__ void __launch_bounds__(128, NET ? 1 : 8) k_surrogate_assemble(
   constexpr uint32_t off = NET ? kSmemFwd : 0;
   float(*piece)[8] = reinterpret_cast<float(*)[8]>(sm + off);  // [row][s_i, e_i]
   int* s_flag = reinterpret_cast<int*>(sm + off + kTileM * 8 * 4);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31;
   uint32_t taddr = 0;
-  if (NET) {
-    if (warp == 0) {
-      tc::tmem_alloc(S.slot, kH);
-      tc::tmem_relinquish();
-    }
-    if (threadIdx.x == 0) tc::mbar_init(S.bar, 1);
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    taddr = *S.slot;
-  }
+  if (NET) taddr = mlp_setup(S, P);
   GridP<float> gr;
   if (p.has_exact) gr = *gp;
   uint32_t phase = 0;
@@ -92,10 +82,13 @@ __global__ void __launch_bounds__(128, NET ? 1 : 8) k_surrogate_assemble(
   int64_t n_exact = 0, n_fb = 0;
   int n_empty = 0;
   Acc<float> acc_long;  // N > 128: thread i < K carries node i's sum over the element's tiles
-  const int row = threadIdx.x;
+  // with the network on, threads 128..255 only help with the network (the
+  // second column half); the sample rows belong to threads 0..127
+  const int row = threadIdx.x & (kTileM - 1);
+  const bool lead = threadIdx.x < kTileM;
 
   for (int64_t unit = blockIdx.x; ok && unit < p.nunits; unit += gridDim.x) {
-    s_flag[row] = NET ? 0 : 1;
+    if (lead) s_flag[row] = NET ? 0 : 1;
     acc_long = Acc<float>();
     __syncthreads();
     for (int c = 0; c < p.nsub; ++c) {
@@ -139,7 +132,7 @@ __global__ void __launch_bounds__(128, NET ? 1 : 8) k_surrogate_assemble(
       }
       // exact subsample (or every query when the network is off)
       float fe = 0.f;
-      const bool sub = p.has_exact && valid && (!NET || j < p.s);
+      const bool sub = lead && p.has_exact && valid && (!NET || j < p.s);
       if (sub) {
         fe = exact_value<DS>(gr, cell_start, cell_items, recs, vals, p.nes, p.exact_field, X, n_empty);
         ++n_exact;
@@ -153,23 +146,24 @@ __global__ void __launch_bounds__(128, NET ? 1 : 8) k_surrogate_assemble(
         if (sub && !(fabsf(y - fe) <= p.tau)) s_flag[el] = 1;
         __syncthreads();
         const bool fb = s_flag[el] != 0;
-        if (fb && valid && !sub) {
+        if (fb && lead && valid && !sub) {
           fe = exact_value<DS>(gr, cell_start, cell_items, recs, vals, p.nes, p.exact_field, X, n_empty);
           ++n_exact;
         }
         f = fb ? fe : y;
-        if (valid && c == 0 && j == 0) {
+        if (lead && valid && c == 0 && j == 0) {
           n_fb += fb;
           if (fb_out) fb_out[t] = fb ? 1 : 0;
         }
       } else if (valid && c == 0 && j == 0 && fb_out) {
         fb_out[t] = 1;
       }
-      if (valid && sample_f) sample_f[t * p.N + j] = f;
+      if (lead && valid && sample_f) sample_f[t * p.N + j] = f;
 
       // residual against the P1 control and its basis-weighted partials
       Acc<float> a[K];
-      if (valid) {
+      const bool mine = lead && valid;
+      if (mine) {
         float gX = __fmul_rn(__ldg(g + v[0]), lam[0]);
 #pragma unroll
         for (int m = 1; m < K; ++m) gX = __fmaf_rn(__ldg(g + v[m]), lam[m], gX);
@@ -178,7 +172,7 @@ __global__ void __launch_bounds__(128, NET ? 1 : 8) k_surrogate_assemble(
         for (int i = 0; i < K; ++i) a[i].add(__fmul_rn(r, lam[i]));
       }
       // warp-segmented suffix combine over rows of the same element
-      const int seg = valid ? el : -1;
+      const int seg = mine ? el : -1;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const int seg2 = __shfl_down_sync(0xffffffffu, seg, o);
@@ -191,7 +185,7 @@ __global__ void __launch_bounds__(128, NET ? 1 : 8) k_surrogate_assemble(
         }
       }
       const int seg_prev = __shfl_up_sync(0xffffffffu, seg, 1);
-      const bool head = valid && (lane == 0 || seg_prev != seg);
+      const bool head = mine && (lane == 0 || seg_prev != seg);
       if (head) {
 #pragma unroll
         for (int i = 0; i < K; ++i) {
@@ -258,12 +252,7 @@ __global__ void __launch_bounds__(128, NET ? 1 : 8) k_surrogate_assemble(
       if (m1) atomicAdd(reinterpret_cast<unsigned long long*>(counters + 2), (unsigned long long)m1);
     }
   }
-  if (NET) {
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(taddr, kH);
-  }
+  if (NET) mlp_teardown(taddr);
 }
 
 // target nodes [nv][d] -> network inputs [nv][3] (z = 0 in 2D)
@@ -336,11 +325,12 @@ static sft_status launch_sur(sft_mlp_s* m, sft_source_s* s, sft_target_s* t, con
   int dev = 0, sms = 0;
   SFT_CUDA(cudaGetDevice(&dev));
   SFT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  // network on: one CTA per SM (all of shared memory, 256 TMEM columns);
+  // network on: two CTAs per SM (about 106 KB of shared memory and 256 TMEM
+  // columns each);
   // exact queries only: latency-bound location work, many CTAs per SM
-  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(p.nunits, (int64_t)sms * (NET ? 1 : 16)));
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(p.nunits, (int64_t)sms * (NET ? 2 : 16)));
   const Locator* L = s ? &s->loc[SFT_PREC_FP32] : nullptr;
-  ::sft::note_launch(), k_surrogate_assemble<DT, DS, NET><<<grid, 128, NET ? kSmemSur : kSmemPieces, st>>>(
+  ::sft::note_launch(), k_surrogate_assemble<DT, DS, NET><<<grid, NET ? kTPR * kTileM : kTileM, NET ? kSmemSur : kSmemPieces, st>>>(
       m ? m->P : nullptr, m ? m->W[0] : nullptr, m ? m->W[1] : nullptr, m ? m->W[2] : nullptr,
       (const float*)t->coordsP[SFT_PREC_FP32], t->conn, t->vol32, g, L ? (const GridP<float>*)L->grid : nullptr,
       L ? L->cell_start : nullptr, L ? L->cell_items : nullptr, L ? (const float*)L->recs : nullptr,
