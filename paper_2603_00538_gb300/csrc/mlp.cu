@@ -18,14 +18,16 @@ namespace sft {
 // Persistent CTAs of 256 threads (two per SM): each 128-point tile is
 // shared by the two column halves (mlp_tile).
 __global__ void __launch_bounds__(kTPR * kTileM, 2) k_mlp_forward(const float* __restrict__ P,
-                                                                  const __nv_bfloat16* __restrict__ W2,
-                                                                  const __nv_bfloat16* __restrict__ W3,
-                                                                  const __nv_bfloat16* __restrict__ W4, int64_t n,
+                                                                  const unsigned char* __restrict__ W2,
+                                                                  const unsigned char* __restrict__ W3,
+                                                                  const unsigned char* __restrict__ W4, int64_t n,
                                                                   const float* __restrict__ pts,
                                                                   float* __restrict__ out, int32_t* err) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const MlpSmem S = mlp_smem(sm);
-  const uint32_t taddr = mlp_setup(S, P);
+  const unsigned char* const Wc[3] = {W2, W3, W4};
+  WStream ws;
+  const uint32_t taddr = mlp_setup(S, P, Wc, cta_tiles((n + kTileM - 1) / kTileM), ws);
   uint32_t phase = 0;
   bool ok = true;
   const int row = threadIdx.x & (kTileM - 1);
@@ -38,10 +40,10 @@ __global__ void __launch_bounds__(kTPR * kTileM, 2) k_mlp_forward(const float* _
       x[2] = pts[gi * 3 + 2];
     }
     float y = 0.f;
-    ok = mlp_tile(S, P, W2, W3, W4, x, taddr, phase, err, y);
+    ok = mlp_tile(S, P, Wc, ws, x, taddr, phase, err, y);
     if (ok && gi < n && threadIdx.x < kTileM) out[gi] = y;
   }
-  mlp_teardown(taddr);
+  mlp_teardown(S, taddr, ws, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -281,21 +283,23 @@ __global__ void k_adam(float* __restrict__ P, const float* __restrict__ g, float
   }
 }
 
-// BF16 copies W (K-major [out][in]) and W^T ([in][out]) of a 256x256 layer
+// BF16 copies of a 256x256 layer: W (K-major [out][in]), W^T ([in][out])
+// and the forward tile's chunked layout
 __global__ void k_weights_bf16(const float* __restrict__ Wf, __nv_bfloat16* __restrict__ W,
-                               __nv_bfloat16* __restrict__ WT) {
+                               __nv_bfloat16* __restrict__ WT, unsigned char* __restrict__ Wc) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < kH * kH; k += gridDim.x * blockDim.x) {
     const int o = k / kH, i = k % kH;
     const __nv_bfloat16 v = __float2bfloat16_rn(Wf[k]);
     W[k] = v;
     if (WT) WT[i * kH + o] = v;
+    *reinterpret_cast<__nv_bfloat16*>(Wc + wchunk_offset(o, i)) = v;
   }
 }
 
 static sft_status refresh_bf16(sft_mlp_s* m, cudaStream_t st) {
   const int64_t offW[3] = {kOffW2, kOffW3, kOffW4};
   for (int l = 0; l < 3; ++l) {
-    ::sft::note_launch(), k_weights_bf16<<<64, 256, 0, st>>>(m->P + offW[l], m->W[l], m->WT[l]);
+    ::sft::note_launch(), k_weights_bf16<<<64, 256, 0, st>>>(m->P + offW[l], m->W[l], m->WT[l], m->Wc[l]);
     SFT_CUDA(cudaGetLastError());
   }
   return SFT_OK;
@@ -419,8 +423,8 @@ sft_status mlp_forward_dev(sft_mlp_s* m, int64_t n, const float* pts, float* out
   SFT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int64_t tiles = (n + kTileM - 1) / kTileM;
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, 2 * (int64_t)sms);
-  ::sft::note_launch(), k_mlp_forward<<<grid, kTPR * kTileM, kSmemFwd, st>>>(m->P, m->W[0], m->W[1], m->W[2], n, pts,
-                                                                             out, d_err);
+  ::sft::note_launch(), k_mlp_forward<<<grid, kTPR * kTileM, kSmemFwd, st>>>(m->P, m->Wc[0], m->Wc[1], m->Wc[2], n,
+                                                                             pts, out, d_err);
   SFT_CUDA(cudaGetLastError());
   return SFT_OK;
 }
@@ -449,6 +453,7 @@ sft_status sft_mlp_create(const float* params, int32_t device_ptrs, void* cuda_s
     for (int l = 0; l < 3 && e == cudaSuccess; ++l) {
       e = dalloc(&m->W[l], (size_t)kH * kH, st);
       if (e == cudaSuccess) e = dalloc(&m->WT[l], (size_t)kH * kH, st);
+      if (e == cudaSuccess) e = dalloc(&m->Wc[l], (size_t)kH * kH * 2, st);
     }
     if (e != cudaSuccess) { r = cuda_fail(e, "alloc"); break; }
     if (r) break;
@@ -469,6 +474,7 @@ void sft_mlp_destroy(sft_mlp m) {
   dfree(m->P, m->stream);
   for (auto& w : m->W) dfree(w, m->stream);
   for (auto& w : m->WT) dfree(w, m->stream);
+  for (auto& w : m->Wc) dfree(w, m->stream);
   dfree(m->grad, m->stream);
   dfree(m->m1, m->stream);
   dfree(m->m2, m->stream);

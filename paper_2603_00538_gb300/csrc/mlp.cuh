@@ -16,33 +16,59 @@ namespace sft {
 constexpr int kH = 256;
 constexpr int kTileM = 128;
 constexpr int kKC = 64;  // K chunk of a streamed weight block (training GEMM)
-constexpr int kKF = 32;  // K chunk of a streamed weight block (forward tile)
+constexpr int kKF = 16;  // K chunk of a streamed weight block (forward tile): one MMA
+constexpr int kStages = 4;  // weight chunk buffers of the forward tile
 constexpr int kTPR = 2;  // forward tile: threads per activation row (each owns half the columns)
 constexpr int64_t kOffW1 = 0, kOffC1 = kH * 3, kOffW2 = kOffC1 + kH, kOffC2 = kOffW2 + kH * kH,
                   kOffW3 = kOffC2 + kH, kOffC3 = kOffW3 + kH * kH, kOffW4 = kOffC3 + kH,
                   kOffC4 = kOffW4 + kH * kH, kOffW5 = kOffC4 + kH, kOffC5 = kOffW5 + kH,
                   kNParam = kOffC5 + 1;
 
-// shared memory of a forward tile: activation tile (128 x 256 BF16), two
-// weight chunks (256 x 32 BF16), the first layer as float4 {w0, w1, w2, c}
-// per output, the two halves' partial outputs, one mbarrier, the TMEM
-// address slot and a status word. About 101 KB: two CTAs fit on one SM.
+// shared memory of a forward tile: activation tile (128 x 256 BF16),
+// kStages weight chunks (256 x 16 BF16), the first layer as float4
+// {w0, w1, w2, c} per output, the two halves' partial outputs, the
+// mbarriers, the TMEM address slot and a status word. About 101 KB: two
+// CTAs fit on one SM.
 constexpr uint32_t kSmemA = kTileM * kH * 2;        // 64 KiB
 constexpr uint32_t kSmemB = kH * kKC * 2;           // 32 KiB (training GEMM chunk)
-constexpr uint32_t kSmemBF = kH * kKF * 2;          // 16 KiB
+constexpr uint32_t kSmemBF = kH * kKF * 2;          // 8 KiB
 constexpr uint32_t kSmemW1 = kH * 16;               // 4 KiB
 constexpr uint32_t kSmemY = kTPR * kTileM * 4;      // 1 KiB
-constexpr uint32_t kSmemFwd = kSmemA + 2 * kSmemBF + kSmemW1 + kSmemY + 64;
+constexpr uint32_t kSmemBar = 128;                  // 2 kStages + 1 mbarriers, slot, status
+constexpr uint32_t kSmemFwd = kSmemA + kStages * kSmemBF + kSmemW1 + kSmemY + kSmemBar;
+constexpr int kChunksPerLayer = kH / kKF;
+
+// byte offset of weight (n, k) of a 256x256 layer in the chunked layout the
+// forward tile streams: chunk k / kKF is one contiguous [256][kKF] block in
+// the no-swizzle K-major core-matrix order of its shared-memory image
+__host__ __device__ constexpr uint32_t wchunk_offset(int n, int k) {
+  return (uint32_t)(k / kKF) * kSmemBF + tc::kmajor_offset(n, k % kKF, kKF);
+}
 constexpr uint32_t kIdesc = tc::idesc_bf16_f32(kTileM, kH);
 
-// SiLU z sigma(z), sigma(z) = 1 / (1 + e^-z): one exponential and one
-// reciprocal on the special-function unit. (The one-operation form
+// special-function-unit approximations (PTX ex2.approx / rcp.approx):
+// relative errors near 2^-22, far below the BF16 rounding of an activation
+__device__ __forceinline__ float ex2_sfu(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_sfu(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+constexpr float kNegLog2e = -1.4426950408889634f;
+// sigma(z) = 1 / (1 + 2^(-z log2 e)); the limits are exact: 2^(+big) = inf
+// gives 1/inf = 0, 2^(-big) = 0 gives 1. (The one-operation form
 // u + u tanh(u), u = z/2, loses accuracy to cancellation for z << 0: its
 // absolute error |u| 2^-11 exceeds the BF16 rounding of the activation.)
-__device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
+__device__ __forceinline__ float sigmoid_f(float z) { return rcp_sfu(1.0f + ex2_sfu(kNegLog2e * z)); }
+// SiLU z sigma(z): two special-function operations per activation
+__device__ __forceinline__ float silu_f(float z) { return z * sigmoid_f(z); }
 // d silu / dz = sigma(z) (1 + z (1 - sigma(z)))
 __device__ __forceinline__ float silu_grad(float z) {
-  const float sg = __fdividef(1.0f, 1.0f + __expf(-z));
+  const float sg = sigmoid_f(z);
   return sg * __fmaf_rn(z, 1.0f - sg, 1.0f);
 }
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
@@ -54,108 +80,109 @@ __device__ __forceinline__ void store_bf16x8(unsigned char* dst, const float* v)
   *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(h);
 }
 
-// stage rows n = 0..255, k = kc*kKF .. kc*kKF+kKF-1 of a [256][256] BF16
-// weight matrix (K-major) into a no-swizzle K-major smem block (K = kKF)
-__device__ __forceinline__ void load_weight_chunk(unsigned char* dst, const __nv_bfloat16* __restrict__ W, int kc) {
-  constexpr int Q = kKF / 8;  // 16-byte pieces per row
-  for (int c = threadIdx.x; c < kH * Q; c += blockDim.x) {
-    const int n = c / Q, kq = c - n * Q;
-    tc::cp_async16(dst + tc::kmajor_offset(n, kq * 8, kKF), W + (int64_t)n * kH + kc * kKF + kq * 8);
-  }
-  tc::cp_async_commit();
+// The weight stream of a forward CTA: chunk g (g = 0, 1, ... over the
+// CTA's tiles, 3 layers of kChunksPerLayer chunks each) goes to buffer
+// g % kStages by one bulk copy whose bytes complete full[b]; its MMA commits
+// to mdone[b]. Thread 0 consumes chunk g (wait full, MMA, commit), then waits
+// for chunk g-1's MMA (its buffer is the one chunk g+kStages-1 goes to; the
+// MMA of chunk g stays queued behind it, so the tensor pipe does not idle)
+// and issues that copy. The next layer's first chunks thus load during the
+// current layer's epilogue. Every commit to mdone[b] is waited exactly once,
+// before its buffer is refilled; parity of the k-th use of a buffer is k & 1.
+struct WStream {
+  int64_t next_use = 0, next_copy = 0, total = 0;
+};
+
+__device__ __forceinline__ const unsigned char* wchunk_src(const unsigned char* const Wc[3], int64_t g) {
+  const int64_t per_tile = 3 * kChunksPerLayer;
+  const int l = (int)((g % per_tile) / kChunksPerLayer);
+  const int kc = (int)(g % kChunksPerLayer);
+  return Wc[l] + (size_t)kc * kSmemBF;
 }
 
-// One hidden 256x256 layer on the tensor cores: TMEM[128 x 256] = A (smem,
-// 128 x 256) * W^T, W streamed in kKF-wide K chunks through two buffers.
-// Thread 0 issues chunk kc's MMAs and commits them to mbarrier kc % 2; the
-// buffer of chunk kc+1 is refilled once the MMAs of chunk kc-1 (its last
-// reader) have completed, so chunk kc's MMAs run while chunk kc+1 loads.
-// At most one commit per barrier is outstanding; `phase` holds the parity
-// bit of each barrier. Only thread 0 polls (bounded); the CTA then meets at
-// a barrier, so every thread takes the same branch. Returns false if a wait
-// expired (error recorded in *err); TMEM holds the layer's accumulators on
-// true.
-__device__ __forceinline__ bool tc_layer(unsigned char* A, unsigned char* B0, unsigned char* B1, uint64_t* bar,
-                                         uint32_t& phase, uint32_t taddr, const __nv_bfloat16* __restrict__ W,
-                                         int32_t* err, int* s_ok) {
-  constexpr int NK = kH / kKF;
-  unsigned char* Bb[2] = {B0, B1};
-  load_weight_chunk(Bb[0], W, 0);
-  for (int kc = 0; kc < NK; ++kc) {
-    tc::cp_async_wait_all();
-    tc::fence_async_smem();
-    __syncthreads();
-    const bool refill = kc + 1 < NK;
-    const int rb = (kc + 1) & 1;           // buffer of chunk kc+1 (last read by chunk kc-1)
-    if (threadIdx.x == 0) {
-      tc::fence_after_sync();
-#pragma unroll
-      for (int kk = 0; kk < kKF / 16; ++kk) {
-        const uint64_t ad = tc::smem_desc(tc::smem_addr(A) + (uint32_t)((kc * kKF + kk * 16) / 8) * 128u, 128u,
-                                          (uint32_t)kH * 16u);
-        const uint64_t bd = tc::smem_desc(tc::smem_addr(Bb[kc & 1]) + (uint32_t)kk * 256u, 128u, (uint32_t)kKF * 16u);
-        tc::mma_bf16(taddr, ad, bd, kIdesc, (kc | kk) != 0);
+// thread 0: copy chunk ws.next_copy (buffer free: its previous reader's MMA
+// was waited by the caller, or the buffer is unused yet)
+__device__ __forceinline__ void ws_copy(WStream& ws, unsigned char* B, uint64_t* full,
+                                        const unsigned char* const Wc[3]) {
+  const int64_t g = ws.next_copy++;
+  const int b = (int)(g % kStages);
+  tc::mbar_arrive_expect_tx(full + b, kSmemBF);
+  tc::bulk_g2s(B + (size_t)b * kSmemBF, wchunk_src(Wc, g), kSmemBF, full + b);
+}
+
+// one 256x256 layer: TMEM[128 x 256] = A (smem, 128 x 256) * W^T. Only
+// thread 0 works; ends with a commit to lbar and a bounded wait on it.
+// Returns false if a wait expired (error recorded in *err).
+__device__ __forceinline__ bool tc_layer_issue(WStream& ws, unsigned char* A, unsigned char* B, uint64_t* full,
+                                               uint64_t* mdone, uint64_t* lbar, uint32_t& lphase,
+                                               const unsigned char* const Wc[3], uint32_t taddr, int32_t* err) {
+  tc::fence_after_sync();
+  for (int kc = 0; kc < kChunksPerLayer; ++kc) {
+    const int64_t g = ws.next_use++;
+    const int b = (int)(g % kStages);
+    if (!tc::mbar_wait(full + b, (uint32_t)((g / kStages) & 1), err)) return false;
+    const uint64_t ad = tc::smem_desc(tc::smem_addr(A) + (uint32_t)(kc * kKF / 8) * 128u, 128u, (uint32_t)kH * 16u);
+    const uint64_t bd = tc::smem_desc(tc::smem_addr(B + (size_t)b * kSmemBF), 128u, (uint32_t)kKF * 16u);
+    tc::mma_bf16(taddr, ad, bd, kIdesc, kc != 0);
+    tc::mma_commit(mdone + b);
+    if (ws.next_copy < ws.total) {
+      if (g >= 1) {
+        const int64_t gp = g - 1;  // last reader of the buffer chunk next_copy goes to
+        if (!tc::mbar_wait(mdone + (gp % kStages), (uint32_t)((gp / kStages) & 1), err)) return false;
       }
-      tc::mma_commit(bar + (kc & 1));
-      bool ok = true;
-      if (refill && kc >= 1) {
-        ok = tc::mbar_wait(bar + rb, (phase >> rb) & 1u, err);
-      } else if (!refill) {
-        // end of the layer: the last two commits (chunks NK-2 and NK-1)
-        ok = tc::mbar_wait(bar + rb, (phase >> rb) & 1u, err);
-        ok = ok && tc::mbar_wait(bar + (kc & 1), (phase >> (kc & 1)) & 1u, err);
-      }
-      *s_ok = ok ? 1 : 0;
+      ws_copy(ws, B, full, Wc);
     }
-    if (refill && kc >= 1) phase ^= 1u << rb;
-    if (!refill) phase ^= 3u;
-    if (kc >= 1 || !refill) {
-      __syncthreads();
-      tc::fence_after_sync();
-      if (!*s_ok) {
-        tc::cp_async_wait_all();
-        return false;
-      }
-    }
-    if (refill) load_weight_chunk(Bb[rb], W, kc + 1);
   }
-  return true;
+  tc::mma_commit(lbar);
+  const bool ok = tc::mbar_wait(lbar, lphase, err);
+  lphase ^= 1u;
+  return ok;
 }
 
 // shared-memory carve-up of one 128-row network tile
 struct MlpSmem {
   unsigned char* A;   // activation tile [128][256] BF16, K-major core matrices
-  unsigned char* B0;  // weight chunk buffers [256][kKF] BF16
-  unsigned char* B1;
+  unsigned char* B;   // kStages weight chunk buffers [256][kKF] BF16
   float4* w1;         // first layer: {W1[o][0], W1[o][1], W1[o][2], c1[o]}
   float* ypart;       // [kTPR][128] partial outputs of the column halves
-  uint64_t* bar;      // two MMA completion mbarriers (one per weight buffer)
+  uint64_t* full;     // [kStages] chunk landed (bulk-copy transaction bytes)
+  uint64_t* mdone;    // [kStages] MMAs reading the chunk completed
+  uint64_t* lbar;     // all MMAs of a layer completed
   uint32_t* slot;     // TMEM base address
-  int* s_ok;          // result of thread 0's bounded wait
+  int* s_ok;          // result of thread 0's bounded waits
 };
 __device__ __forceinline__ MlpSmem mlp_smem(unsigned char* sm) {
   MlpSmem S;
   S.A = sm;
-  S.B0 = sm + kSmemA;
-  S.B1 = S.B0 + kSmemBF;
-  S.w1 = reinterpret_cast<float4*>(S.B1 + kSmemBF);
-  S.ypart = reinterpret_cast<float*>(S.B1 + kSmemBF + kSmemW1);
-  S.bar = reinterpret_cast<uint64_t*>(S.B1 + kSmemBF + kSmemW1 + kSmemY);
-  S.slot = reinterpret_cast<uint32_t*>(S.bar + 2);
+  S.B = sm + kSmemA;
+  S.w1 = reinterpret_cast<float4*>(S.B + kStages * kSmemBF);
+  S.ypart = reinterpret_cast<float*>(S.B + kStages * kSmemBF + kSmemW1);
+  S.full = reinterpret_cast<uint64_t*>(S.B + kStages * kSmemBF + kSmemW1 + kSmemY);
+  S.mdone = S.full + kStages;
+  S.lbar = S.mdone + kStages;
+  S.slot = reinterpret_cast<uint32_t*>(S.lbar + 1);
   S.s_ok = reinterpret_cast<int*>(S.slot + 1);
   return S;
 }
 
-// Per-CTA setup of a network tile loop: TMEM allocation (256 columns), the
-// mbarrier and the first-layer table. Every thread calls it.
-__device__ __forceinline__ uint32_t mlp_setup(const MlpSmem& S, const float* __restrict__ P) {
+// Per-CTA setup of a network tile loop over `ntiles` tiles: TMEM allocation
+// (256 columns), the mbarriers, the first-layer table and the first
+// kStages - 1 weight chunk copies. Every thread calls it.
+__device__ __forceinline__ uint32_t mlp_setup(const MlpSmem& S, const float* __restrict__ P,
+                                              const unsigned char* const Wc[3], int64_t ntiles, WStream& ws) {
   if ((threadIdx.x >> 5) == 0) {
     tc::tmem_alloc(S.slot, kH);
     tc::tmem_relinquish();
   }
+  ws.total = ntiles * 3 * kChunksPerLayer;
   if (threadIdx.x == 0) {
-    tc::mbar_init(S.bar, 1);
-    tc::mbar_init(S.bar + 1, 1);
+    for (int b = 0; b < kStages; ++b) {
+      tc::mbar_init(S.full + b, 1);
+      tc::mbar_init(S.mdone + b, 1);
+    }
+    tc::mbar_init(S.lbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    while (ws.next_copy < ws.total && ws.next_copy < kStages - 1) ws_copy(ws, S.B, S.full, Wc);
   }
   for (int o = threadIdx.x; o < kH; o += blockDim.x)
     S.w1[o] = make_float4(__ldg(P + kOffW1 + o * 3), __ldg(P + kOffW1 + o * 3 + 1), __ldg(P + kOffW1 + o * 3 + 2),
@@ -165,11 +192,22 @@ __device__ __forceinline__ uint32_t mlp_setup(const MlpSmem& S, const float* __r
   tc::fence_after_sync();
   return *S.slot;
 }
-__device__ __forceinline__ void mlp_teardown(uint32_t taddr) {
+// End of the tile loop: thread 0 waits (bounded) for copies it issued that
+// no MMA consumed (after an expired wait), then TMEM is released.
+__device__ __forceinline__ void mlp_teardown(const MlpSmem& S, uint32_t taddr, WStream& ws, int32_t* err) {
+  if (threadIdx.x == 0) {
+    for (int64_t g = ws.next_use; g < ws.next_copy; ++g)
+      if (!tc::mbar_wait(S.full + (g % kStages), (uint32_t)((g / kStages) & 1), err, 200000000ull)) break;
+  }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(taddr, kH);
+}
+
+// tiles a persistent CTA visits (tile = blockIdx.x + k gridDim.x < ntiles)
+__device__ __forceinline__ int64_t cta_tiles(int64_t ntiles) {
+  return blockIdx.x < ntiles ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
 }
 
 // The whole network on one 128-row tile with kTPR * 128 threads: thread t
@@ -180,9 +218,8 @@ __device__ __forceinline__ void mlp_teardown(uint32_t taddr) {
 // the last layer (256 -> 1) as FMA dots over each half, the halves added in
 // a fixed order. False if a tensor-core wait expired.
 __device__ __forceinline__ bool mlp_tile(const MlpSmem& S, const float* __restrict__ P,
-                                         const __nv_bfloat16* __restrict__ W2, const __nv_bfloat16* __restrict__ W3,
-                                         const __nv_bfloat16* __restrict__ W4, const float x[3], uint32_t taddr,
-                                         uint32_t& phase, int32_t* err, float& y_out) {
+                                         const unsigned char* const Wc[3], WStream& ws, const float x[3],
+                                         uint32_t taddr, uint32_t& phase, int32_t* err, float& y_out) {
   constexpr int kCols = kH / kTPR;
   const int row = threadIdx.x & (kTileM - 1);
   const int half = threadIdx.x / kTileM;
@@ -199,11 +236,13 @@ __device__ __forceinline__ bool mlp_tile(const MlpSmem& S, const float* __restri
   }
   tc::fence_async_smem();
   __syncthreads();
-  const __nv_bfloat16* Ws[3] = {W2, W3, W4};
   const int64_t offC[3] = {kOffC2, kOffC3, kOffC4};
   float y = 0.f;
   for (int l = 0; l < 3; ++l) {
-    if (!tc_layer(S.A, S.B0, S.B1, S.bar, phase, taddr, Ws[l], err, S.s_ok)) return false;
+    if (threadIdx.x == 0) *S.s_ok = tc_layer_issue(ws, S.A, S.B, S.full, S.mdone, S.lbar, phase, Wc, taddr, err);
+    __syncthreads();
+    tc::fence_after_sync();
+    if (!*S.s_ok) return false;
     // epilogue: bias + SiLU from TMEM, this thread's row and column half
     for (int cc = c0; cc < c0 + kCols; cc += 32) {
       float v[32];
@@ -251,6 +290,7 @@ struct sft_mlp_s {
   float* P = nullptr;                                  // FP32 parameters (master)
   __nv_bfloat16* W[3] = {nullptr, nullptr, nullptr};   // BF16 copies of W2, W3, W4 ([out][in])
   __nv_bfloat16* WT[3] = {nullptr, nullptr, nullptr};  // BF16 transposes ([in][out]) for the backward pass
+  unsigned char* Wc[3] = {nullptr, nullptr, nullptr};  // BF16 in the forward tile's chunked layout
   float* grad = nullptr;                               // FP32 gradient of the mean loss
   float* m1 = nullptr;                                 // Adam moments
   float* m2 = nullptr;

@@ -60,8 +60,8 @@ __device__ __forceinline__ float exact_value(const GridP<float>& gr, const int32
 // sampler and launch shape, the comparison point of the surrogate).
 template <int DT, int DS, bool NET>
 __global__ void __launch_bounds__(NET ? kTPR * kTileM : kTileM, NET ? 2 : 8) k_surrogate_assemble(
-    const float* __restrict__ P, const __nv_bfloat16* __restrict__ W2, const __nv_bfloat16* __restrict__ W3,
-    const __nv_bfloat16* __restrict__ W4, const float* __restrict__ tx, const int32_t* __restrict__ tconn,
+    const float* __restrict__ P, const unsigned char* __restrict__ W2, const unsigned char* __restrict__ W3,
+    const unsigned char* __restrict__ W4, const float* __restrict__ tx, const int32_t* __restrict__ tconn,
     const float* __restrict__ vol32, const float* __restrict__ g, const GridP<float>* __restrict__ gp,
     const int32_t* __restrict__ cell_start, const int32_t* __restrict__ cell_items, const float* __restrict__ recs,
     const float* __restrict__ vals, SurParams p, double* __restrict__ b, int32_t* __restrict__ fb_out,
@@ -74,7 +74,9 @@ __global__ void __launch_bounds__(NET ? kTPR * kTileM : kTileM, NET ? 2 : 8) k_s
   int* s_flag = reinterpret_cast<int*>(sm + off + kTileM * 8 * 4);
   const int lane = threadIdx.x & 31;
   uint32_t taddr = 0;
-  if (NET) taddr = mlp_setup(S, P);
+  const unsigned char* const Wc[3] = {W2, W3, W4};
+  WStream ws;
+  if (NET) taddr = mlp_setup(S, P, Wc, cta_tiles(p.nunits) * p.nsub, ws);
   GridP<float> gr;
   if (p.has_exact) gr = *gp;
   uint32_t phase = 0;
@@ -141,7 +143,7 @@ __global__ void __launch_bounds__(NET ? kTPR * kTileM : kTileM, NET ? 2 : 8) k_s
       if (NET) {
         const float x3[3] = {X[0], X[1], DT == 3 ? X[DT - 1] : 0.f};
         float y = 0.f;
-        ok = mlp_tile(S, P, W2, W3, W4, x3, taddr, phase, err, y);
+        ok = mlp_tile(S, P, Wc, ws, x3, taddr, phase, err, y);
         if (!ok) break;
         if (sub && !(fabsf(y - fe) <= p.tau)) s_flag[el] = 1;
         __syncthreads();
@@ -252,7 +254,7 @@ __global__ void __launch_bounds__(NET ? kTPR * kTileM : kTileM, NET ? 2 : 8) k_s
       if (m1) atomicAdd(reinterpret_cast<unsigned long long*>(counters + 2), (unsigned long long)m1);
     }
   }
-  if (NET) mlp_teardown(taddr);
+  if (NET) mlp_teardown(S, taddr, ws, err);
 }
 
 // target nodes [nv][d] -> network inputs [nv][3] (z = 0 in 2D)
@@ -331,7 +333,7 @@ static sft_status launch_sur(sft_mlp_s* m, sft_source_s* s, sft_target_s* t, con
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(p.nunits, (int64_t)sms * (NET ? 2 : 16)));
   const Locator* L = s ? &s->loc[SFT_PREC_FP32] : nullptr;
   ::sft::note_launch(), k_surrogate_assemble<DT, DS, NET><<<grid, NET ? kTPR * kTileM : kTileM, NET ? kSmemSur : kSmemPieces, st>>>(
-      m ? m->P : nullptr, m ? m->W[0] : nullptr, m ? m->W[1] : nullptr, m ? m->W[2] : nullptr,
+      m ? m->P : nullptr, m ? m->Wc[0] : nullptr, m ? m->Wc[1] : nullptr, m ? m->Wc[2] : nullptr,
       (const float*)t->coordsP[SFT_PREC_FP32], t->conn, t->vol32, g, L ? (const GridP<float>*)L->grid : nullptr,
       L ? L->cell_start : nullptr, L ? L->cell_items : nullptr, L ? (const float*)L->recs : nullptr,
       L ? (const float*)L->vals : nullptr, p, b, fb, sf, counters, err);
