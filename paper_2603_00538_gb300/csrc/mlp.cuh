@@ -34,8 +34,9 @@ constexpr uint32_t kSmemB = kH * kKC * 2;           // 32 KiB (training GEMM chu
 constexpr uint32_t kSmemBF = kH * kKF * 2;          // 8 KiB
 constexpr uint32_t kSmemW1 = kH * 16;               // 4 KiB
 constexpr uint32_t kSmemY = kTPR * kTileM * 4;      // 1 KiB
+constexpr uint32_t kSmemBias = 4 * kH * 4;          // 4 KiB: c2, c3, c4, w5
 constexpr uint32_t kSmemBar = 128;                  // 2 kStages + 1 mbarriers, slot, status
-constexpr uint32_t kSmemFwd = kSmemA + kStages * kSmemBF + kSmemW1 + kSmemY + kSmemBar;
+constexpr uint32_t kSmemFwd = kSmemA + kStages * kSmemBF + kSmemW1 + kSmemBias + kSmemY + kSmemBar;
 constexpr int kChunksPerLayer = kH / kKF;
 
 // byte offset of weight (n, k) of a 256x256 layer in the chunked layout the
@@ -144,6 +145,7 @@ struct MlpSmem {
   unsigned char* A;   // activation tile [128][256] BF16, K-major core matrices
   unsigned char* B;   // kStages weight chunk buffers [256][kKF] BF16
   float4* w1;         // first layer: {W1[o][0], W1[o][1], W1[o][2], c1[o]}
+  float* bias;        // [4][256]: c2, c3, c4 and the output weights w5
   float* ypart;       // [kTPR][128] partial outputs of the column halves
   uint64_t* full;     // [kStages] chunk landed (bulk-copy transaction bytes)
   uint64_t* mdone;    // [kStages] MMAs reading the chunk completed
@@ -156,8 +158,9 @@ __device__ __forceinline__ MlpSmem mlp_smem(unsigned char* sm) {
   S.A = sm;
   S.B = sm + kSmemA;
   S.w1 = reinterpret_cast<float4*>(S.B + kStages * kSmemBF);
-  S.ypart = reinterpret_cast<float*>(S.B + kStages * kSmemBF + kSmemW1);
-  S.full = reinterpret_cast<uint64_t*>(S.B + kStages * kSmemBF + kSmemW1 + kSmemY);
+  S.bias = reinterpret_cast<float*>(S.B + kStages * kSmemBF + kSmemW1);
+  S.ypart = reinterpret_cast<float*>(S.B + kStages * kSmemBF + kSmemW1 + kSmemBias);
+  S.full = reinterpret_cast<uint64_t*>(S.B + kStages * kSmemBF + kSmemW1 + kSmemBias + kSmemY);
   S.mdone = S.full + kStages;
   S.lbar = S.mdone + kStages;
   S.slot = reinterpret_cast<uint32_t*>(S.lbar + 1);
@@ -184,9 +187,14 @@ __device__ __forceinline__ uint32_t mlp_setup(const MlpSmem& S, const float* __r
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     while (ws.next_copy < ws.total && ws.next_copy < kStages - 1) ws_copy(ws, S.B, S.full, Wc);
   }
-  for (int o = threadIdx.x; o < kH; o += blockDim.x)
+  for (int o = threadIdx.x; o < kH; o += blockDim.x) {
     S.w1[o] = make_float4(__ldg(P + kOffW1 + o * 3), __ldg(P + kOffW1 + o * 3 + 1), __ldg(P + kOffW1 + o * 3 + 2),
                           __ldg(P + kOffC1 + o));
+    S.bias[o] = __ldg(P + kOffC2 + o);
+    S.bias[kH + o] = __ldg(P + kOffC3 + o);
+    S.bias[2 * kH + o] = __ldg(P + kOffC4 + o);
+    S.bias[3 * kH + o] = __ldg(P + kOffW5 + o);
+  }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -208,6 +216,37 @@ __device__ __forceinline__ void mlp_teardown(const MlpSmem& S, uint32_t taddr, W
 // tiles a persistent CTA visits (tile = blockIdx.x + k gridDim.x < ntiles)
 __device__ __forceinline__ int64_t cta_tiles(int64_t ntiles) {
   return blockIdx.x < ntiles ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+}
+
+// 32 columns cc .. cc+31 of hidden layer l (accumulators in r) for this
+// thread's row: bias + SiLU, then into the activation tile (l < 2) or the
+// output dot product y
+__device__ __forceinline__ void tile_columns(const MlpSmem& S, int l, int row, int cc, const uint32_t (&r)[32],
+                                             float& y) {
+  const float4* b4 = reinterpret_cast<const float4*>(S.bias + l * kH + cc);
+  float v[32];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float4 b = b4[i];
+    v[4 * i] = silu_f(__uint_as_float(r[4 * i]) + b.x);
+    v[4 * i + 1] = silu_f(__uint_as_float(r[4 * i + 1]) + b.y);
+    v[4 * i + 2] = silu_f(__uint_as_float(r[4 * i + 2]) + b.z);
+    v[4 * i + 3] = silu_f(__uint_as_float(r[4 * i + 3]) + b.w);
+  }
+  if (l < 2) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) store_bf16x8(S.A + tc::kmajor_offset(row, cc + q * 8, kH), v + q * 8);
+  } else {
+    const float4* w4 = reinterpret_cast<const float4*>(S.bias + 3 * kH + cc);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float4 w = w4[i];
+      y = __fmaf_rn(bf16r(v[4 * i]), w.x, y);
+      y = __fmaf_rn(bf16r(v[4 * i + 1]), w.y, y);
+      y = __fmaf_rn(bf16r(v[4 * i + 2]), w.z, y);
+      y = __fmaf_rn(bf16r(v[4 * i + 3]), w.w, y);
+    }
+  }
 }
 
 // The whole network on one 128-row tile with kTPR * 128 threads: thread t
@@ -236,40 +275,26 @@ __device__ __forceinline__ bool mlp_tile(const MlpSmem& S, const float* __restri
   }
   tc::fence_async_smem();
   __syncthreads();
-  const int64_t offC[3] = {kOffC2, kOffC3, kOffC4};
   float y = 0.f;
   for (int l = 0; l < 3; ++l) {
     if (threadIdx.x == 0) *S.s_ok = tc_layer_issue(ws, S.A, S.B, S.full, S.mdone, S.lbar, phase, Wc, taddr, err);
     __syncthreads();
     tc::fence_after_sync();
     if (!*S.s_ok) return false;
-    // epilogue: bias + SiLU from TMEM, this thread's row and column half
-    for (int cc = c0; cc < c0 + kCols; cc += 32) {
-      float v[32];
-      tc::tmem_ld32(trow + (uint32_t)cc, v);
-      const float4* b4 = reinterpret_cast<const float4*>(P + offC[l] + cc);
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const float4 b = __ldg(b4 + i);
-        v[4 * i] = silu_f(v[4 * i] + b.x);
-        v[4 * i + 1] = silu_f(v[4 * i + 1] + b.y);
-        v[4 * i + 2] = silu_f(v[4 * i + 2] + b.z);
-        v[4 * i + 3] = silu_f(v[4 * i + 3] + b.w);
-      }
-      if (l < 2) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) store_bf16x8(S.A + tc::kmajor_offset(row, cc + q * 8, kH), v + q * 8);
-      } else {
-        const float4* w4 = reinterpret_cast<const float4*>(P + kOffW5 + cc);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const float4 w = __ldg(w4 + i);
-          y = __fmaf_rn(bf16r(v[4 * i]), w.x, y);
-          y = __fmaf_rn(bf16r(v[4 * i + 1]), w.y, y);
-          y = __fmaf_rn(bf16r(v[4 * i + 2]), w.z, y);
-          y = __fmaf_rn(bf16r(v[4 * i + 3]), w.w, y);
-        }
-      }
+    // epilogue: bias + SiLU from TMEM, this thread's row and column half;
+    // TMEM loads double buffered (the next 32 columns load while the
+    // current ones are processed)
+    uint32_t ra[32], rb[32];
+    tc::tmem_ld32_issue(trow + (uint32_t)c0, ra);
+    tc::tmem_ld_wait();
+#pragma unroll 1
+    for (int cc = c0; cc < c0 + kCols; cc += 64) {
+      tc::tmem_ld32_issue(trow + (uint32_t)(cc + 32), rb);
+      tile_columns(S, l, row, cc, ra, y);
+      tc::tmem_ld_wait();
+      if (cc + 64 < c0 + kCols) tc::tmem_ld32_issue(trow + (uint32_t)(cc + 64), ra);
+      tile_columns(S, l, row, cc + 32, rb, y);
+      tc::tmem_ld_wait();
     }
     if (l == 2) S.ypart[half * kTileM + row] = y;
     tc::fence_async_smem();
