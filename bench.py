@@ -59,7 +59,8 @@ WORKLOADS = {
 # element conn + coords + g + b read-modify-write (2D 72 B, 3D 112 B)
 BYTES_PER_QUERY = {2: 48, 3: 76}
 BYTES_PER_ELEM = {2: 72, 3: 112}
-KERNEL_FILES = ["paper_2603_00538_gb300/csrc/assemble.cu", "paper_2603_00538_gb300/csrc/common.cuh"]
+KERNEL_FILES = ["paper_2603_00538_gb300/csrc/assemble.cu", "paper_2603_00538_gb300/csrc/common.cuh",
+                "paper_2603_00538_gb300/csrc/accum.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "assemble_traffic.txt")
 
 
@@ -153,6 +154,20 @@ def dist_init():
     return rank, world, local
 
 
+def aggregate(total_ms: float, units: float, world: int, dev=None):
+    """Whole-job timing over ranks (every rank calls it): the slowest rank's
+    elapsed time and the sum of the units all ranks processed."""
+    if world <= 1:
+        return float(total_ms), float(units)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=dev)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def make_workload(name: str, scale: float = 1.0):
     src, tgt, p = W.config_meshes(name, scale)
     return src, tgt, p
@@ -210,14 +225,10 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
     queries = int(stats_last["queries"])
+    total_ms, all_queries = aggregate(float(sum(step_ms)), queries * args.steps, world, dev)
     ms_per_step = total_ms / args.steps
-    value = queries * world / (ms_per_step / 1e3)
+    value = all_queries / (total_ms / 1e3)
 
     # kernels launched per step (profiled once, outside the timed region)
     launches_per_step = count_launches(step)
@@ -302,15 +313,12 @@ def run_batch(args):
             b.record(stream)
             torch.cuda.synchronize()
             times.append(a.elapsed_time(b))
-    total_ms = float(sum(times))
+    queries = int(stats["queries"])
+    total_ms, all_queries = aggregate(float(sum(times)), queries * args.steps, world, dev)
     if world > 1:
-        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
         torch.distributed.barrier()
     ms_per_step = total_ms / args.steps
-    queries = int(stats["queries"])
-    value = queries * world / (ms_per_step / 1e3)
+    value = all_queries / (total_ms / 1e3)
     launches = count_launches(lambda: sft.sft_batch_run(plan))
     # sequential plain launches of the same requests
     seq_ms = []
@@ -465,15 +473,12 @@ def run_surrogate(args):
             asm_ms.append(last["ms_assembly"])
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(step_ms))
+    queries = int(last["net_queries"])
+    total_ms, all_queries = aggregate(float(sum(step_ms)), queries * args.steps, world, dev)
     if world > 1:
-        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
         torch.distributed.barrier()
     ms_per_step = total_ms / args.steps
-    queries = int(last["net_queries"])
-    value = queries * world / (ms_per_step / 1e3)
+    value = all_queries / (total_ms / 1e3)
     launches = count_launches(step)
     stats_sur = dict(last)
     u_sur = u.clone()
