@@ -259,13 +259,20 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_assemble(const BReq* __
 // ---------------------------------------------------------------------------
 // step 7: one cooperative Jacobi-PCG over all systems (block-diagonal).
 // Block b owns global rows [b R, (b+1) R); its systems are s_lo(b)..s_hi(b).
-// Per-system dot products: per-(block, local system) partials, summed by
-// every block for its own systems over the blocks that own that system's
-// rows, in block order (deterministic, identical in every block). A system
-// stops when it converges or reaches its own iteration cap; the kernel stops
-// when a round finds every system stopped (a flag summed over blocks).
+// Rows are swept warp by warp (32 consecutive rows per step, steps 256 rows
+// apart, so every lane's system index only moves forward). A warp reduces
+// its step's per-row values by system with a segmented shuffle scan; the
+// head lane of each segment adds the sum to the warp's slot of that system
+// (fixed order: no atomics). One block barrier per phase combines the eight
+// warp slots in order into the block's partial of each local system. After
+// the grid barrier a warp per local system sums that system's partials over
+// the blocks that own its rows, lanes in block order, then a fixed shuffle
+// tree (deterministic and identical in every block). A system stops when it
+// converges or reaches its own iteration cap; the kernel stops when a round
+// finds every system stopped (a flag summed over blocks).
 // ---------------------------------------------------------------------------
 constexpr int kMaxLocalSys = 64;
+constexpr int kBatchWarps = kBatchThreads / 32;
 
 struct BCgCtl {
   GridBarrier bar;
@@ -274,16 +281,25 @@ struct BCgCtl {
   unsigned int flag[3];
 };
 
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  v = warp_sum<double>(v);
-  __syncthreads();
-  if (lane == 0) sh[warp] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-  return s;  // valid in thread 0
+// segmented (by system index j, contiguous in lane order) warp sums of two
+// values; the first lane of each segment adds them to slot[j] of this warp
+__device__ __forceinline__ void warp_seg_add(int j, double a, double b, double (*slot)[2]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int j2 = __shfl_down_sync(0xffffffffu, j, o);
+    const double a2 = __shfl_down_sync(0xffffffffu, a, o);
+    const double b2 = __shfl_down_sync(0xffffffffu, b, o);
+    if (lane + o < 32 && j2 == j) {
+      a += a2;
+      b += b2;
+    }
+  }
+  const int jp = __shfl_up_sync(0xffffffffu, j, 1);
+  if (j >= 0 && (lane == 0 || jp != j)) {
+    slot[j][0] += a;
+    slot[j][1] += b;
+  }
 }
 
 __global__ void __launch_bounds__(kBatchThreads) k_batch_pcg(const BSys* __restrict__ sys, int nsys, int64_t ntot,
@@ -292,61 +308,92 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_pcg(const BSys* __restr
                                                              const int32_t* __restrict__ blk_shi, int maxs,
                                                              double* r, double* z, double* p, double* q, double* part,
                                                              BSysOut* __restrict__ out, BCgCtl* ctl) {
-  __shared__ double sh[kBatchThreads / 32];
   __shared__ double s_rz[kMaxLocalSys], s_bn[kMaxLocalSys], s_beta[kMaxLocalSys], s_alpha[kMaxLocalSys],
       s_rel[kMaxLocalSys];
   __shared__ int s_done[kMaxLocalSys], s_it[kMaxLocalSys], s_conv[kMaxLocalSys];
+  __shared__ int64_t s_off[kMaxLocalSys + 1];
+  __shared__ double s_w[kBatchWarps][kMaxLocalSys][2];
+  __shared__ double s_g[kMaxLocalSys][2];
   __shared__ int s_any;
   const unsigned nb = gridDim.x;
   const int b = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t row0 = (int64_t)b * rows_per_block;
   const int64_t row1 = min(ntot, row0 + rows_per_block);
   const int slo = blk_slo[b], shi = blk_shi[b];
   const int nloc = row0 < row1 ? shi - slo + 1 : 0;
+  for (int j = threadIdx.x; j <= nloc; j += blockDim.x)
+    s_off[j] = j < nloc ? max(row0, sys[slo + j].off) : row1;
 
-  // local system j, row range of this block inside it
-  auto range = [&](int j, int64_t& a, int64_t& e) {
-    const BSys& S = sys[slo + j];
-    a = max(row0, S.off);
-    e = min(row1, S.off + S.n);
+  // clear the warp slots (each warp its own)
+  auto clear_slots = [&]() {
+    for (int j = lane; j < nloc; j += 32) s_w[warp][j][0] = s_w[warp][j][1] = 0.0;
+    __syncwarp();
   };
-  // sum of partial c of system s over its blocks
-  auto gather = [&](int s, int c) {
-    const BSys& S = sys[s];
-    double acc = 0.0;
-    for (int bb = S.blo; bb <= S.bhi; ++bb) acc += __ldcg(part + ((int64_t)bb * maxs + (s - blk_slo[bb])) * 2 + c);
-    return acc;
+  // combine the warp slots in order into this block's partials
+  auto publish = [&]() {
+    __syncthreads();
+    for (int k = threadIdx.x; k < nloc * 2; k += blockDim.x) {
+      const int j = k >> 1, c = k & 1;
+      double t = 0.0;
+      for (int w = 0; w < kBatchWarps; ++w) t += s_w[w][j][c];
+      part[((int64_t)b * maxs + j) * 2 + c] = t;
+    }
+  };
+  // totals of every local system over its blocks -> s_g (warp per system)
+  auto gather_all = [&]() {
+    for (int j = warp; j < nloc; j += kBatchWarps) {
+      const int s = slo + j;
+      const BSys& S = sys[s];
+      double a0 = 0.0, a1 = 0.0;
+      for (int bb = S.blo + lane; bb <= S.bhi; bb += 32) {
+        const double* pp = part + ((int64_t)bb * maxs + (s - blk_slo[bb])) * 2;
+        a0 += __ldcg(pp);
+        a1 += __ldcg(pp + 1);
+      }
+      a0 = warp_sum<double>(a0);
+      a1 = warp_sum<double>(a1);
+      if (lane == 0) {
+        s_g[j][0] = a0;
+        s_g[j][1] = a1;
+      }
+    }
+    __syncthreads();
   };
 
   // init: x = 0, r = b, z = D^-1 r, p = q = 0; partials b.b and r.z
-  for (int j = 0; j < nloc; ++j) {
-    const BSys& S = sys[slo + j];
-    int64_t a, e;
-    range(j, a, e);
-    double bb = 0.0, rzv = 0.0;
-    for (int64_t gr = a + threadIdx.x; gr < e; gr += blockDim.x) {
-      const int64_t i = gr - S.off;
-      const double bi = S.b[i], di = S.dinv[i];
-      S.x[i] = 0.0;
-      r[gr] = bi;
-      z[gr] = di * bi;
-      p[gr] = 0.0;
-      q[gr] = 0.0;
-      bb += bi * bi;
-      rzv += bi * di * bi;
-    }
-    const double t0 = block_sum(bb, sh);
-    const double t1 = block_sum(rzv, sh);
-    if (threadIdx.x == 0) {
-      part[((int64_t)b * maxs + j) * 2] = t0;
-      part[((int64_t)b * maxs + j) * 2 + 1] = t1;
+  clear_slots();
+  __syncthreads();
+  {
+    int j = 0;
+    for (int64_t base = row0 + warp * 32; base < row1; base += kBatchThreads) {
+      const int64_t gr = base + lane;
+      double bb = 0.0, rzv = 0.0;
+      int jj = -1;
+      if (gr < row1) {
+        while (j + 1 < nloc && gr >= s_off[j + 1]) ++j;
+        const BSys& S = sys[slo + j];
+        const int64_t i = gr - S.off;
+        const double bi = S.b[i], di = S.dinv[i];
+        S.x[i] = 0.0;
+        r[gr] = bi;
+        z[gr] = di * bi;
+        p[gr] = 0.0;
+        q[gr] = 0.0;
+        bb = bi * bi;
+        rzv = bi * di * bi;
+        jj = j;
+      }
+      warp_seg_add(jj, bb, rzv, s_w[warp]);
     }
   }
+  publish();
   if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+  gather_all();
   if (threadIdx.x < nloc) {
     const int j = threadIdx.x;
-    s_bn[j] = sqrt(gather(slo + j, 0));
-    s_rz[j] = gather(slo + j, 1);
+    s_bn[j] = sqrt(s_g[j][0]);
+    s_rz[j] = s_g[j][1];
     s_beta[j] = 0.0;
     s_it[j] = 0;
     s_conv[j] = s_bn[j] == 0.0;
@@ -357,71 +404,84 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_pcg(const BSys* __restr
 
   for (int it = 0;; ++it) {
     // phase A: w = M z, p = z + beta p, q = w + beta q, partial p.q
-    for (int j = 0; j < nloc; ++j) {
-      if (s_done[j]) continue;
-      const BSys& S = sys[slo + j];
-      int64_t a, e;
-      range(j, a, e);
-      const double bt = s_beta[j];
-      const double* zs = z + S.off;
-      double pq = 0.0;
-      for (int64_t gr = a + threadIdx.x; gr < e; gr += blockDim.x) {
-        const int64_t i = gr - S.off;
-        double w = 0.0;
-        for (int32_t k = __ldg(S.rp + i); k < __ldg(S.rp + i + 1); ++k) w += __ldg(S.val + k) * __ldcg(zs + __ldg(S.col + k));
-        const double pn = __ldcg(z + gr) + bt * __ldcg(p + gr);
-        const double qn = w + bt * __ldcg(q + gr);
-        p[gr] = pn;
-        q[gr] = qn;
-        pq += pn * qn;
+    clear_slots();
+    {
+      int j = 0;
+      for (int64_t base = row0 + warp * 32; base < row1; base += kBatchThreads) {
+        const int64_t gr = base + lane;
+        double pq = 0.0;
+        int jj = -1;
+        if (gr < row1) {
+          while (j + 1 < nloc && gr >= s_off[j + 1]) ++j;
+          if (!s_done[j]) {
+            const BSys& S = sys[slo + j];
+            const int64_t i = gr - S.off;
+            const double* zs = z + S.off;
+            const int32_t k0 = __ldg(S.rp + i), k1 = __ldg(S.rp + i + 1);
+            double w = 0.0;
+            for (int32_t k = k0; k < k1; ++k) w += __ldg(S.val + k) * __ldcg(zs + __ldg(S.col + k));
+            const double bt = s_beta[j];
+            const double pn = __ldcg(z + gr) + bt * __ldcg(p + gr);
+            const double qn = w + bt * __ldcg(q + gr);
+            p[gr] = pn;
+            q[gr] = qn;
+            pq = pn * qn;
+            jj = j;
+          }
+        }
+        warp_seg_add(jj, pq, 0.0, s_w[warp]);
       }
-      const double t0 = block_sum(pq, sh);
-      if (threadIdx.x == 0) part[((int64_t)b * maxs + j) * 2] = t0;
     }
+    publish();
     if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
     if (it > 0) {
       const unsigned int any = *reinterpret_cast<volatile unsigned int*>(&ctl->flag[(it - 1) % 3]);
       if (any == 0) break;
     }
+    gather_all();
     if (threadIdx.x < nloc) {
       const int j = threadIdx.x;
-      s_alpha[j] = s_done[j] ? 0.0 : s_rz[j] / gather(slo + j, 0);
+      s_alpha[j] = s_done[j] ? 0.0 : s_rz[j] / s_g[j][0];
     }
     __syncthreads();
     // phase B: x += a p, r -= a q, z = D^-1 r, partials r.r and r.z
-    for (int j = 0; j < nloc; ++j) {
-      if (s_done[j]) continue;
-      const BSys& S = sys[slo + j];
-      int64_t a, e;
-      range(j, a, e);
-      const double al = s_alpha[j];
-      double rr = 0.0, rzv = 0.0;
-      for (int64_t gr = a + threadIdx.x; gr < e; gr += blockDim.x) {
-        const int64_t i = gr - S.off;
-        S.x[i] = __ldcg(S.x + i) + al * __ldcg(p + gr);
-        const double ri = __ldcg(r + gr) - al * __ldcg(q + gr);
-        r[gr] = ri;
-        const double zi = S.dinv[i] * ri;
-        z[gr] = zi;
-        rr += ri * ri;
-        rzv += ri * zi;
-      }
-      const double t0 = block_sum(rr, sh);
-      const double t1 = block_sum(rzv, sh);
-      if (threadIdx.x == 0) {
-        part[((int64_t)b * maxs + j) * 2] = t0;
-        part[((int64_t)b * maxs + j) * 2 + 1] = t1;
+    clear_slots();
+    {
+      int j = 0;
+      for (int64_t base = row0 + warp * 32; base < row1; base += kBatchThreads) {
+        const int64_t gr = base + lane;
+        double rr = 0.0, rzv = 0.0;
+        int jj = -1;
+        if (gr < row1) {
+          while (j + 1 < nloc && gr >= s_off[j + 1]) ++j;
+          if (!s_done[j]) {
+            const BSys& S = sys[slo + j];
+            const int64_t i = gr - S.off;
+            const double al = s_alpha[j];
+            S.x[i] = __ldcg(S.x + i) + al * __ldcg(p + gr);
+            const double ri = __ldcg(r + gr) - al * __ldcg(q + gr);
+            r[gr] = ri;
+            const double zi = S.dinv[i] * ri;
+            z[gr] = zi;
+            rr = ri * ri;
+            rzv = ri * zi;
+            jj = j;
+          }
+        }
+        warp_seg_add(jj, rr, rzv, s_w[warp]);
       }
     }
+    publish();
     if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+    gather_all();
     if (threadIdx.x == 0) s_any = 0;
     __syncthreads();
     if (threadIdx.x < nloc) {
       const int j = threadIdx.x;
       if (!s_done[j]) {
         const BSys& S = sys[slo + j];
-        const double rn = sqrt(gather(slo + j, 0));
-        const double rz_new = gather(slo + j, 1);
+        const double rn = sqrt(s_g[j][0]);
+        const double rz_new = s_g[j][1];
         s_it[j] += 1;
         s_rel[j] = rn / s_bn[j];
         if (rn <= S.tol * s_bn[j]) s_conv[j] = 1;

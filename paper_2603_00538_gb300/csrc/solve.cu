@@ -33,18 +33,32 @@ struct PcgCtl {
   int32_t conv[kMaxFields];
 };
 
-// sum the per-block partials [nblocks][nrhs][2] -> tot[nrhs][2] (identical in all blocks)
+// sum the per-block partials [nblocks][nrhs][2] -> tot[nrhs][2], identical
+// in all blocks: thread t sums blocks t, t + 256, ... in order, then warps
+// reduce with a fixed shuffle tree and thread k adds the 8 warp sums in order
 __device__ __forceinline__ void reduce_partials(const double* part, int nblocks, int nrhs, double* sh_tot) {
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    for (int f = 0; f < nrhs; ++f) {
-      for (int c = 0; c < 2; ++c) {
-        double s = 0.0;
-        for (int bidx = lane; bidx < nblocks; bidx += 32) s += __ldcg(part + ((int64_t)bidx * nrhs + f) * 2 + c);
-        s = warp_sum<double>(s);
-        if (lane == 0) sh_tot[f * 2 + c] = s;
-      }
-    }
+  __shared__ double shw[kSolveThreads / 32][kMaxFields * 2];
+  double acc[kMaxFields * 2];
+#pragma unroll
+  for (int k = 0; k < kMaxFields * 2; ++k) acc[k] = 0.0;
+  for (int bidx = threadIdx.x; bidx < nblocks; bidx += blockDim.x) {
+    const double* pb = part + (int64_t)bidx * nrhs * 2;
+#pragma unroll
+    for (int k = 0; k < kMaxFields * 2; ++k)
+      if (k < nrhs * 2) acc[k] += __ldcg(pb + k);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kMaxFields * 2; ++k) {
+    if (k >= nrhs * 2) break;
+    const double w = warp_sum<double>(acc[k]);
+    if (lane == 0) shw[warp][k] = w;
+  }
+  __syncthreads();
+  if (threadIdx.x < nrhs * 2) {
+    double t = 0.0;
+    for (int w = 0; w < kSolveThreads / 32; ++w) t += shw[w][threadIdx.x];
+    sh_tot[threadIdx.x] = t;
   }
   __syncthreads();
 }
