@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_control(const BReq* __r
 // plain FP32 sums of a lane's few samples; the warp combine is compensated.
 // ---------------------------------------------------------------------------
 template <int D, int NF>
-__global__ void __launch_bounds__(kBatchThreads) k_batch_assemble(const BReq* __restrict__ reqs,
+__global__ void __launch_bounds__(kBatchThreads, NF <= 2 ? 4 : (NF <= 4 ? 3 : 2)) k_batch_assemble(const BReq* __restrict__ reqs,
                                                                   const int32_t* __restrict__ greq,
                                                                   const int64_t* __restrict__ goff, int ng,
                                                                   int64_t total, int tile,
