@@ -148,7 +148,10 @@ __global__ void __launch_bounds__(kSolveThreads) k_pcg(const int32_t* __restrict
         if (conv[f]) continue;
         const double* zf = z + (int64_t)f * n;
         double s = 0.0;
-        for (int32_t k = q0 + lane_in_row; k < q1; k += TPR) s += __ldg(val + k) * __ldcg(zf + __ldg(col + k));
+        // z was written by other blocks before the grid barrier; the barrier's
+        // acquire fence makes those writes visible to ordinary (L1-cached)
+        // loads, so neighbouring rows share the gathered lines in L1
+        for (int32_t k = q0 + lane_in_row; k < q1; k += TPR) s += __ldg(val + k) * zf[__ldg(col + k)];
         if constexpr (TPR > 1) {
 #pragma unroll
           for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, TPR);
@@ -238,7 +241,11 @@ sft_status mass_solve(sft_target_s* t, int nrhs, const double* b, double* x, dou
   SFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<1>, kSolveThreads, 0));
   if (per_sm < 1) return fail(SFT_ERR_CUDA, "solver kernel cannot be resident");
   per_sm = std::min(per_sm, 4);
-  const int64_t want = (n + kSolveThreads - 1) / kSolveThreads;
+  // at least ~6 rows per thread: fewer blocks make the two grid barriers and
+  // the partial sums of every iteration cheaper (measured: 4 blocks per SM
+  // for the 1.0 M-row 2D system, about 2 for the 0.5 M-row 3D one)
+  constexpr int64_t kRowsPerThread = 6;
+  const int64_t want = (n + kSolveThreads * kRowsPerThread - 1) / (kSolveThreads * kRowsPerThread);
   const unsigned nblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, want));
 
   double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *part = nullptr;
@@ -377,7 +384,11 @@ extern "C" sft_status sft_mass_solve_static(int64_t n, const int32_t* row_ptr, c
   SFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<1>, kSolveThreads, 0));
   if (per_sm < 1) return fail(SFT_ERR_CUDA, "solver kernel cannot be resident");
   per_sm = std::min(per_sm, 4);
-  const int64_t want = (n + kSolveThreads - 1) / kSolveThreads;
+  // at least ~6 rows per thread: fewer blocks make the two grid barriers and
+  // the partial sums of every iteration cheaper (measured: 4 blocks per SM
+  // for the 1.0 M-row 2D system, about 2 for the 0.5 M-row 3D one)
+  constexpr int64_t kRowsPerThread = 6;
+  const int64_t want = (n + kSolveThreads * kRowsPerThread - 1) / (kSolveThreads * kRowsPerThread);
   const unsigned nblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, want));
   // layout: dinv [n] | r, z, p, q [nrhs][n] | partials [nblocks][nrhs][2] | control block
   const size_t vec = sizeof(double) * (size_t)n * nrhs;
