@@ -419,7 +419,8 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_pcg(const BSys* __restr
             const double* zs = z + S.off;
             const int32_t k0 = __ldg(S.rp + i), k1 = __ldg(S.rp + i + 1);
             double w = 0.0;
-            for (int32_t k = k0; k < k1; ++k) w += __ldg(S.val + k) * __ldcg(zs + __ldg(S.col + k));
+            // z of other blocks is visible to ordinary loads after the grid barrier
+            for (int32_t k = k0; k < k1; ++k) w += __ldg(S.val + k) * zs[__ldg(S.col + k)];
             const double bt = s_beta[j];
             const double pn = __ldcg(z + gr) + bt * __ldcg(p + gr);
             const double qn = w + bt * __ldcg(q + gr);

@@ -1,0 +1,123 @@
+"""Full-size checks of the batched and the surrogate workloads in the launch
+configuration the benchmark times, on samples the oracle can compute one by
+one:
+
+* batch256 (256 requests, 29.9 M target elements): every sampled request of
+  the full plan equals the same request run alone through sft_transfer (b to
+  summation order, 1e-6), and requests on the 2,048-triangle source equal the
+  oracle's transfer (FP32 bound, 1e-5);
+* sur3d (2,958,234 tets x 64 samples against the 3,998,792-triangle source):
+  on sampled elements the fused kernel's network values are the standalone
+  forward's bit for bit and within 1e-2 S of the FP64 oracle network, exact
+  values within FP32 rounding of the oracle's location + evaluation, and every
+  fallback decision consistent with the oracle's margin (unique away from
+  tau, where S is the network's output scale).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2603_00538_gb300 as sft  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def test_batch256_full_plan_samples(orc):
+    srcm, reqs = W.batch_workload()
+    srcs = [sft.mesh_source(m, device=DEV) for m in srcm]
+    tgts = [sft.mesh_target(q["target"], device=DEV) for q in reqs]
+    opts = [dict(samples_per_elem=q["samples_per_elem"], field_count=q["nfields"], seed=r, stream_id=r,
+                 cg_tol=1e-10, cg_max_iter=1000) for r, q in enumerate(reqs)]
+    rsrc = [srcs[q["source"]] for q in reqs]
+    plan = sft.sft_batch_create(rsrc, tgts, opts, autotune=True)
+    _, st = sft.sft_batch_run(plan)
+    assert st["nreq"] == 256 and st["nonconverged"] == 0 and st["empty_queries"] == 0
+    order = np.argsort([q["elems"] for q in reqs])
+    pick = [int(r) for r in order[:3]] + [int(r) for r in order[-2:]]
+    pick += [r for r, q in enumerate(reqs) if q["dim"] == 3][:1]
+    for r in pick:
+        q = reqs[r]
+        nf = q["nfields"]
+        ub, bb = sft.sft_batch_result(plan, r, b_out=np.zeros((nf, q["target"].nnodes)))
+        bs = np.zeros((nf, q["target"].nnodes))
+        _, _, us = sft.sft_transfer(rsrc[r], tgts[r], q["samples_per_elem"], sft.SFT_PREC_FP32, seed=r, stream_id=r,
+                                    cg_tol=1e-10, field_count=nf, b_out=bs)
+        for f in range(nf):
+            assert _rel(bb[f], bs[f]) < 1e-6, (r, f)
+            assert _rel(ub[f], us[f]) < 1e-5, (r, f)
+    # requests on the small source against the oracle (the smallest two)
+    small = [r for r in order if reqs[r]["source"] == 0][:2]
+    for r in small:
+        q = reqs[int(r)]
+        nf = q["nfields"]
+        _, bb = sft.sft_batch_result(plan, int(r), b_out=np.zeros((nf, q["target"].nnodes)))
+        src_nf = W.Mesh(srcm[0].coords, srcm[0].conn, srcm[0].values[:nf])
+        o = orc.transfer(src_nf, q["target"], 1, q["samples_per_elem"], seed=int(r), stream=int(r), cg_tol=1e-10)
+        for f in range(nf):
+            assert _rel(bb[f], o["b"][f]) < 1e-5, (r, f)
+    plan.close()
+
+
+def _gpu_params(orc, p32):
+    p = p32.astype(np.float64)
+    parts = orc.mlp_split(p)
+    for i in (2, 4, 6):
+        parts[i][...] = np.vectorize(orc.bf16_round)(parts[i])
+    return p
+
+
+def test_sur3d_full_size_samples(orc):
+    from oracle import surrogate as OS
+    src, tgt, p = W.config_meshes("sur3d", 1.0)
+    S = sft.mesh_source(src, device=DEV)
+    T = sft.mesh_target(tgt, device=DEV)
+    pts, f, fmax = sft.sft_surrogate_dataset(S, 200_000, seed=1)
+    net = sft.sft_mlp_create(W.mlp_init(0).astype(np.float32))
+    sft.sft_mlp_train(net, pts, f, epochs=3, batch=16384, lr=2e-3, lr_final=1e-3)
+    tau = p["tau_rel"] * fmax
+    N, s = p["samples_per_elem"], p["subsample"]
+    E = tgt.nelems
+    fb = torch.zeros(E, dtype=torch.int32, device=DEV)
+    sf = torch.zeros((E, N), dtype=torch.float32, device=DEV)
+    u = torch.zeros(tgt.nnodes, dtype=torch.float64, device=DEV)
+    _, stats, _ = sft.sft_transfer_surrogate(net, S, T, N, seed=0, cg_tol=p["cg_tol"], subsample=s, tau=tau, u_out=u,
+                                             fallback_out=fb, sample_f_out=sf)
+    torch.cuda.synchronize()
+    assert stats["cg_rel_resid"] <= 1e-10
+    assert stats["net_queries"] == tgt.nnodes + E * N
+    fbh = fb.cpu().numpy().astype(bool)
+    assert stats["fallback_elems"] == int(fbh.sum())
+    rng = np.random.default_rng(2)
+    sel = np.sort(rng.choice(E, 96, replace=False))
+    sfh = sf[torch.as_tensor(sel, device=DEV)].cpu().numpy()
+    params = _gpu_params(orc, sft.sft_mlp_params(net))
+    grid = orc.Grid(1, src.coords, src.conn)
+    X = np.zeros((len(sel), N, 3))
+    for k, t in enumerate(sel):
+        _, X[k] = orc.sample_element(1, 3, 0, 0, int(t), N, tgt.coords[tgt.conn[t]])
+    Xf = X.reshape(-1, 3)
+    y_orc = orc.mlp_forward(params, Xf, act_bf16=True).reshape(len(sel), N)
+    y_gpu = sft.sft_mlp_forward(net, Xf.astype(np.float32)).reshape(len(sel), N)
+    fe, _ = OS._exact_values(grid, src.coords, src.conn, src.values[0], Xf[:, :2])
+    fe = fe.reshape(len(sel), N)
+    Snet = max(np.abs(y_orc).max(), 1e-3)
+    margin = np.abs(y_orc[:, :s] - fe[:, :s]).max(axis=1)
+    near = np.abs(margin - tau) <= 1e-2 * Snet
+    assert np.array_equal(fbh[sel][~near], (margin > tau)[~near])
+    for k in range(len(sel)):
+        if fbh[sel[k]]:
+            assert np.abs(sfh[k] - fe[k]).max() <= 1e-5 * np.abs(src.values[0]).max()
+        else:
+            assert np.array_equal(sfh[k], y_gpu[k])            # fused network = standalone forward
+            assert np.abs(sfh[k] - y_orc[k]).max() <= 1e-2 * Snet
