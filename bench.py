@@ -197,7 +197,7 @@ def run_ours(args):
     cons_last = [None]
 
     def step():
-        s = sft.sft_source_create(sc, sk, sv)
+        s = sft.sft_source_create(sc, sk, sv, args.grid_scale)
         t = sft.sft_target_create(tc, tk)
         _, st, _ = sft.sft_transfer(s, t, N, prec, seed=0, cg_tol=tol, u_out=u)
         cons_last[0] = sft.sft_conservation_error(s, t, u[0])
@@ -254,7 +254,8 @@ def run_ours(args):
             "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}"
                                    + ("" if args.scale == 1.0 else f" (element counts x{args.scale})"),
                        "queries_per_step": queries, "target_elements": tgt.nelems, "samples_per_elem": N,
-                       "source_elements": src.nelems, "l2": "flushed between steps (256 MB write)",
+                       "source_elements": src.nelems, "grid_scale_L": args.grid_scale,
+                       "l2": "flushed between steps (256 MB write)",
                        "accumulation": "FP64 load vector, CG and reductions",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "breakdown_ms": {"assembly_kernel": mean_asm, "solve": float(np.mean(solve_ms)),
@@ -625,7 +626,7 @@ def run_e2e(args, src, tgt, N, tol, prec):
     d2h = u.numel() * u.element_size() + 8
 
     def step():
-        s = sft.sft_source_create(sc, sk, sv)
+        s = sft.sft_source_create(sc, sk, sv, args.grid_scale)
         t = sft.sft_target_create(tc, tk)
         _, st, _ = sft.sft_transfer(s, t, N, prec, seed=0, cg_tol=tol, u_out=u)
         e = sft.sft_conservation_error(s, t, u[0])
@@ -774,6 +775,8 @@ def main():
                     help="fraction of the target elements in the cpu_baseline sample")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--sur-epochs", type=int, default=40, help="training epochs of the surrogate (sur3d)")
+    ap.add_argument("--grid-scale", type=float, default=1.0,
+                    help="source grid cells per axis = int(L * nelems^(1/d)) (tri4m / tet5m)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="element-count scale of the workload (1 = the named workload)")
     args = ap.parse_args()
