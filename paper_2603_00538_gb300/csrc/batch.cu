@@ -595,6 +595,7 @@ struct sft_batch_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool graph_ok = false;
+  int64_t graph_kernels = 0;  // kernels recorded in the graph (counted per replay)
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   int64_t queries = 0;
 };
@@ -953,7 +954,10 @@ static sft_status build_batch(sft_batch_s* B, const sft_options* opts, int autot
   SFT_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
   bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
   if (ok) {
+    const int64_t l0 = launch_count();
     const sft_status e = enqueue_batch(B, cap);
+    B->graph_kernels = launch_count() - l0;  // recorded, not run
+    note_launches(-B->graph_kernels);
     cudaGraph_t g = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(cap, &g);
     ok = e == SFT_OK && ce == cudaSuccess && g;
@@ -1010,6 +1014,7 @@ sft_status sft_batch_run(sft_batch B, void* cuda_stream, sft_batch_stats* stats)
   cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : B->stream;
   if (B->graph_ok) {
     SFT_CUDA(cudaGraphLaunch(B->exec, st));
+    note_launches(B->graph_kernels);
   } else {
     if (sft_status e = enqueue_batch(B, st)) return e;
   }

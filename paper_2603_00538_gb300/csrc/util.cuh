@@ -83,6 +83,10 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned int nblocks
 namespace sft {
 // counts every kernel this library launches (exported as sft_kernel_launches)
 void note_launch();
+// kernels recorded into a graph are counted when the graph is launched:
+// capture subtracts them (note_launches(-k)), every replay adds k
+void note_launches(int64_t n);
+int64_t launch_count();
 // exclusive scan of int32 counts [n] into int64 offsets [n+1] (out[n] = total)
 cudaError_t exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
 // narrow int64 -> int32 (caller checked the range)
