@@ -86,14 +86,17 @@ __global__ void k_inc_rank(const int32_t* __restrict__ inc_start, const int32_t*
   }
 }
 
-// Row i of M: FILL=false writes the row length, FILL=true writes columns,
-// values, the Jacobi inverse diagonal and the lumped mass.
+// Row i of M: FILL=false writes the row length (and, when tmp_col is given,
+// the row itself into a fixed-stride staging array, so that the second pass
+// only copies), FILL=true writes columns, values, the Jacobi inverse diagonal
+// and the lumped mass.
 template <int D, bool FILL>
 __global__ void k_mass_rows(const int32_t* __restrict__ conn, const double2* __restrict__ wfac,
                             const int32_t* __restrict__ inc_start, const int32_t* __restrict__ inc, int64_t nv,
                             int32_t* __restrict__ row_len, const int32_t* __restrict__ row_ptr,
                             int32_t* __restrict__ col, double* __restrict__ val, double* __restrict__ dinv,
-                            double* __restrict__ lumped, int32_t* err) {
+                            double* __restrict__ lumped, int32_t* err, int32_t* __restrict__ tmp_col,
+                            double* __restrict__ tmp_val, double* __restrict__ tmp_lump) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
     int32_t cols[kMaxRow];
     double vals[kMaxRow];
@@ -127,6 +130,13 @@ __global__ void k_mass_rows(const int32_t* __restrict__ conn, const double2* __r
     if (overflow) set_error(err, DEV_VALENCE);
     if (!FILL) {
       row_len[i] = cnt;
+      if (tmp_col) {
+        for (int q = 0; q < cnt; ++q) {
+          tmp_col[i * kMaxRow + q] = cols[q];
+          tmp_val[i * kMaxRow + q] = vals[q];
+        }
+        tmp_lump[i] = lump;
+      }
     } else {
       const int32_t base = row_ptr[i];
       double diag = 0.0;
@@ -138,6 +148,26 @@ __global__ void k_mass_rows(const int32_t* __restrict__ conn, const double2* __r
       dinv[i] = diag > 0.0 ? 1.0 / diag : 0.0;
       lumped[i] = lump;
     }
+  }
+}
+
+// second pass from the staged rows: copy into the CSR arrays
+__global__ void k_mass_copy(const int32_t* __restrict__ tmp_col, const double* __restrict__ tmp_val,
+                            const double* __restrict__ tmp_lump, const int32_t* __restrict__ row_ptr, int64_t nv,
+                            int32_t* __restrict__ col, double* __restrict__ val, double* __restrict__ dinv,
+                            double* __restrict__ lumped) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t base = row_ptr[i], cnt = row_ptr[i + 1] - base;
+    double diag = 0.0;
+    for (int q = 0; q < cnt; ++q) {
+      const int32_t c = tmp_col[i * kMaxRow + q];
+      const double v = tmp_val[i * kMaxRow + q];
+      col[base + q] = c;
+      val[base + q] = v;
+      if (c == i) diag = v;
+    }
+    dinv[i] = diag > 0.0 ? 1.0 / diag : 0.0;
+    lumped[i] = tmp_lump[i];
   }
 }
 
@@ -190,8 +220,25 @@ static sft_status build_target_t(sft_target_s* t, cudaStream_t st, int32_t* d_er
   dfree(inc_raw, st);
   dfree(inc_node, st);
   row_len = inc_count;  // reuse
+  // rows are staged at a fixed stride when that fits comfortably (the
+  // second pass then copies instead of merging the incidence lists again)
+  DevBuf<int32_t> stage_col(st);
+  DevBuf<double> stage_val(st), stage_lump(st);
+  int32_t* tmp_col = nullptr;
+  double *tmp_val = nullptr, *tmp_lump = nullptr;
+  if (t->nv * kMaxRow <= (int64_t)1 << 31) {
+    if (stage_col.alloc((size_t)t->nv * kMaxRow) == cudaSuccess &&
+        stage_val.alloc((size_t)t->nv * kMaxRow) == cudaSuccess && stage_lump.alloc((size_t)t->nv) == cudaSuccess) {
+      tmp_col = stage_col.p;
+      tmp_val = stage_val.p;
+      tmp_lump = stage_lump.p;
+    } else {
+      cudaGetLastError();  // no staging: the second pass merges again
+    }
+  }
   ::sft::note_launch(), k_mass_rows<D, false><<<blocks_for(t->nv), 256, 0, st>>>(t->conn, wfac, inc_start, inc, t->nv, row_len, nullptr,
-                                                           nullptr, nullptr, nullptr, nullptr, d_err);
+                                                           nullptr, nullptr, nullptr, nullptr, d_err, tmp_col,
+                                                           tmp_val, tmp_lump);
   SFT_CUDA(cudaGetLastError());
   SFT_CUDA(exclusive_scan_i32_to_i64(row_len, off64, t->nv, st));
   int64_t nnz = 0;
@@ -207,8 +254,14 @@ static sft_status build_target_t(sft_target_s* t, cudaStream_t st, int32_t* d_er
   SFT_CUDA(dalloc(&t->val, (size_t)nnz, st));
   SFT_CUDA(dalloc(&t->dinv, (size_t)t->nv, st));
   SFT_CUDA(dalloc(&t->lumped, (size_t)t->nv, st));
-  ::sft::note_launch(), k_mass_rows<D, true><<<blocks_for(t->nv), 256, 0, st>>>(t->conn, wfac, inc_start, inc, t->nv, nullptr, t->row_ptr,
-                                                          t->col, t->val, t->dinv, t->lumped, d_err);
+  if (tmp_col) {
+    ::sft::note_launch(), k_mass_copy<<<blocks_for(t->nv), 256, 0, st>>>(tmp_col, tmp_val, tmp_lump, t->row_ptr, t->nv,
+                                                                        t->col, t->val, t->dinv, t->lumped);
+  } else {
+    ::sft::note_launch(), k_mass_rows<D, true><<<blocks_for(t->nv), 256, 0, st>>>(t->conn, wfac, inc_start, inc, t->nv, nullptr, t->row_ptr,
+                                                            t->col, t->val, t->dinv, t->lumped, d_err, nullptr,
+                                                            nullptr, nullptr);
+  }
   SFT_CUDA(cudaGetLastError());
   dfree(off64, st);
   dfree(inc_start, st);
