@@ -313,12 +313,14 @@ __device__ __forceinline__ bool cell_may_hold(const P* r, const P c[D], const P 
 }
 
 // one registration per (element, cell) that passes cell_may_hold: count, or
-// fill the element id and the cell id
+// fill the element id, the cell id and the depth of the cell centre in the
+// element (its min barycentric coordinate there, evaluated exactly as a
+// query at that point would be), which orders the cell's list
 template <int D, typename P, bool FILL>
 __global__ void k_register(const P* __restrict__ x, const int32_t* __restrict__ conn, const P* __restrict__ recs,
                            int64_t nv, int64_t ne, const GridP<P>* __restrict__ gp, int32_t* __restrict__ cell_count,
                            const int32_t* __restrict__ cell_start, int32_t* __restrict__ items,
-                           int32_t* __restrict__ item_cell) {
+                           int32_t* __restrict__ item_cell, P* __restrict__ depth) {
   constexpr int RL = RecLen<D>::value;
   const GridP<P> g = *gp;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
@@ -349,43 +351,24 @@ __global__ void k_register(const P* __restrict__ x, const int32_t* __restrict__ 
           const int64_t c = ((int64_t)iz * g.n[1] + iy) * g.n[0] + ix;
           const int32_t pos = atomicAdd(cell_count + c, 1);
           if (FILL) {
-            items[cell_start[c] + pos] = (int32_t)e;
-            item_cell[cell_start[c] + pos] = (int32_t)c;
+            P mu[D + 1];
+            bary_from_record<D, P>(r, cc, mu);
+            P mn = mu[0];
+#pragma unroll
+            for (int q = 1; q <= D; ++q) mn = mu[q] < mn ? mu[q] : mn;
+            const int64_t at = (int64_t)cell_start[c] + pos;
+            items[at] = (int32_t)e;
+            item_cell[at] = (int32_t)c;
+            depth[at] = mn;
           }
         }
   }
 }
 
 // Order of each cell's list (the atomic fill leaves it arbitrary): decreasing
-// depth of the cell centre in the element (its min barycentric coordinate
-// there), ties by ascending element id. One thread per registration computes
-// its depth, then its rank among the cell's entries, and scatters itself.
-template <int D, typename P>
-__global__ void k_item_depth(const GridP<P>* __restrict__ gp, const int32_t* __restrict__ items,
-                             const int32_t* __restrict__ item_cell, const P* __restrict__ recs, int64_t nitems,
-                             P* __restrict__ depth) {
-  constexpr int L = RecLen<D>::value;
-  const GridP<P> g = *gp;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nitems; p += (int64_t)gridDim.x * blockDim.x) {
-    int64_t rem = item_cell[p];
-    P X[D];
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const int32_t i = (int32_t)(rem % g.n[a]);
-      rem /= g.n[a];
-      X[a] = cell_centre<P>(g, a, i);
-    }
-    P r[L];
-    load_record<D, P>(recs, items[p], r);
-    P mu[D + 1];
-    bary_from_record<D, P>(r, X, mu);
-    P mn = mu[0];
-#pragma unroll
-    for (int q = 1; q <= D; ++q) mn = mu[q] < mn ? mu[q] : mn;
-    depth[p] = mn;
-  }
-}
-
+// depth of the cell centre in the element, ties by ascending element id. One
+// thread per registration computes its rank among the cell's entries and
+// scatters itself.
 template <typename P>
 __global__ void k_item_rank(const int32_t* __restrict__ cell_start, const int32_t* __restrict__ item_cell,
                             const int32_t* __restrict__ items, const P* __restrict__ depth, int64_t nitems,
@@ -458,7 +441,7 @@ static sft_status build_locator_t(sft_source_s* s, int prec, cudaStream_t st, in
   SFT_CUDA(dalloc(&start64, (size_t)L.ncells + 1, st));
   SFT_CUDA(cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * L.ncells, st));
   ::sft::note_launch(), k_register<D, P, false><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, recs, s->nv, s->ne, g, cell_count,
-                                                                               nullptr, nullptr, nullptr);
+                                                                               nullptr, nullptr, nullptr, nullptr);
   SFT_CUDA(cudaGetLastError());
   SFT_CUDA(exclusive_scan_i32_to_i64(cell_count, start64, L.ncells, st));
   int32_t herr = 0;
@@ -486,9 +469,7 @@ static sft_status build_locator_t(sft_source_s* s, int prec, cudaStream_t st, in
   SFT_CUDA(dalloc(&L.cell_items, (size_t)total, st));
   SFT_CUDA(cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * L.ncells, st));
   ::sft::note_launch(), k_register<D, P, true><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, recs, s->nv, s->ne, g, cell_count,
-                                                                              L.cell_start, items, item_cell);
-  SFT_CUDA(cudaGetLastError());
-  ::sft::note_launch(), k_item_depth<D, P><<<grid_for(total), 256, 0, st>>>(g, items, item_cell, recs, total, depth);
+                                                                              L.cell_start, items, item_cell, depth);
   SFT_CUDA(cudaGetLastError());
   ::sft::note_launch(), k_item_rank<P><<<grid_for(total), 256, 0, st>>>(L.cell_start, item_cell, items, depth, total,
                                                                        L.cell_items);
