@@ -234,6 +234,30 @@ sft_status sft_mlp_train(sft_mlp m, int64_t n, const float* pts, const float* ta
                          void* cuda_stream);
 void sft_mlp_destroy(sft_mlp m);
 
+/* ---- Transfer plans: initialization once, online transfers many times ----
+ *
+ * The paper's cost split (Sec. 5.3): the initialization, paid once per pair
+ * of fixed meshes, localizes the target nodes and every sample point; the
+ * online part, paid per coupling iteration, evaluates the integrals with the
+ * source's current values and solves. sft_plan_create runs the transfer of
+ * `opt` once, keeping for every target node and every sample the source
+ * element and barycentric coordinates found (mu_1..d in the path precision;
+ * plan memory (4 + d*sizeof(P)) bytes per node and per sample, see
+ * sft_plan_bytes). The plan refers to src and tgt, which must outlive it;
+ * opt->sample_elem_out is ignored. sft_plan_transfer evaluates steps 1-7
+ * with the source's current nodal values (sft_source_set_values), the
+ * samples' target weights regenerated from the same Philox counters, and
+ * writes u_out, b_out, g_out as sft_transfer with opt would (host or device
+ * per opt->out_device, on opt->cuda_stream). Its result equals that of
+ * sft_transfer with the same options and values up to the order of the
+ * floating-point sums. stats->fallback_queries and empty_queries are those
+ * found at plan creation. */
+typedef struct sft_plan_s* sft_plan;
+sft_status sft_plan_create(sft_source src, sft_target tgt, const sft_options* opt, sft_plan* out);
+sft_status sft_plan_transfer(sft_plan plan, double* u_out, double* b_out, double* g_out, sft_stats* stats);
+int64_t sft_plan_bytes(sft_plan plan);
+void sft_plan_destroy(sft_plan plan);
+
 /* ---- Surrogate source: the network as the black-box query ----
  *
  * The transfer of Sec. 4 (steps 1-7) with the source queried through a

@@ -119,6 +119,10 @@ _SIGS = {
     "sft_mlp_loss_grad": ([_vp, _i64, _vp, _vp, _vp, _vp, _i32, _vp], _i32),
     "sft_mlp_train": ([_vp, _i64, _vp, _vp, _i32, _i32, ctypes.c_float, ctypes.c_float, _vp, _i32, _vp], _i32),
     "sft_transfer_surrogate": ([_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp], _i32),
+    "sft_plan_create": ([_vp, _vp, _vp, _vp], _i32),
+    "sft_plan_transfer": ([_vp, _vp, _vp, _vp, _vp], _i32),
+    "sft_plan_bytes": ([_vp], _i64),
+    "sft_plan_destroy": ([_vp], None),
     "sft_surrogate_dataset": ([_vp, _i32, _i64, ctypes.c_uint64, ctypes.c_uint32, _vp, _vp, _vp, _vp, _vp, _vp],
                               _i32),
     "sft_mass_solve_static": ([_i64, _vp, _vp, _vp, _i32, _vp, _vp, _d, _i32, _vp, _vp, _vp], _i32),
@@ -306,6 +310,44 @@ def sft_transfer(src: Source, tgt: Target, samples_per_elem: int, precision: int
     status = _check(lib().sft_transfer(src.h, tgt.h, ctypes.byref(o), up, bp, gp, ctypes.byref(st)),
                     "sft_transfer", allow)
     return status, st.as_dict(), u_out
+
+
+class Plan(_Handle):
+    pass
+
+
+def sft_plan_create(src: Source, tgt: Target, samples_per_elem: int, precision: int = SFT_PREC_FP32, seed: int = 0,
+                    stream_id: int = 0, alpha: float = 1.0, cg_tol: float = 1e-10, cg_max_iter: int = 1000,
+                    field_count: int = 0, out_device: bool = False, strict_inside: bool = False,
+                    stream=None) -> Plan:
+    """Initialization of a transfer between fixed meshes (node and sample
+    locations recorded); outputs of later transfers go to host arrays, or to
+    CUDA tensors with out_device=True."""
+    o = _options(samples_per_elem, seed, stream_id, alpha, cg_tol, cg_max_iter, field_count, precision)
+    o.out_device = int(bool(out_device))
+    o.strict_inside = int(bool(strict_inside))
+    o.cuda_stream = stream if stream is not None else _current_stream()
+    h = _vp()
+    _check(lib().sft_plan_create(src.h, tgt.h, ctypes.byref(o), ctypes.byref(h)), "sft_plan_create")
+    pl = Plan(h.value, lib().sft_plan_destroy, (src, tgt))
+    pl.nfields = int(field_count) if field_count > 0 else _nf(src)
+    pl.nnodes = _nv(tgt)
+    return pl
+
+
+def sft_plan_transfer(pl: Plan, u_out=None, b_out=None, g_out=None, allow_not_converged: bool = False):
+    """Online transfer with the source's current values. Returns (status, stats dict, u_out)."""
+    if u_out is None:
+        u_out = np.zeros((pl.nfields, pl.nnodes), np.float64)
+    st = sft_stats()
+    allow = (SFT_OK, SFT_ERR_NOT_CONVERGED) if allow_not_converged else (SFT_OK,)
+    status = _check(lib().sft_plan_transfer(pl.h, _ptr(u_out)[0], _ptr(b_out)[0], _ptr(g_out)[0], ctypes.byref(st)),
+                    "sft_plan_transfer", allow)
+    return status, st.as_dict(), u_out
+
+
+def sft_plan_bytes(pl: Plan) -> int:
+    return int(lib().sft_plan_bytes(pl.h))
 
 
 def sft_conservation_error(src: Source, tgt: Target, u, field: int = 0, stream=None):

@@ -31,7 +31,12 @@ struct AsmParams {
   double inv_n;   // 1 / N
 };
 
-template <int D, typename P, int NF, bool DBG>
+// MODE: kAsmPlain; kAsmDebug also writes the source element of every sample
+// (sample_elem); kAsmRecord also writes its barycentric coordinates mu_1..d
+// (pmu, [d][N ne]) for later online transfers; kAsmCached takes element and
+// mu from those arrays instead of locating the sample (the samples' target
+// weights are regenerated from the same Philox counters).
+template <int D, typename P, int NF, int MODE>
 __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) k_assemble(const P* __restrict__ tx, const int32_t* __restrict__ tconn,
                                                   const double* __restrict__ vol, const float* __restrict__ vol32,
                                                   const P* __restrict__ g,
@@ -40,13 +45,15 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) k_assemble(const P* __res
                                                   const int32_t* __restrict__ cell_items,
                                                   const P* __restrict__ recs, const P* __restrict__ vals,
                                                   AsmParams p, double* __restrict__ b,
-                                                  int32_t* __restrict__ sample_elem,
+                                                  int32_t* __restrict__ sample_elem, P* __restrict__ pmu,
                                                   int64_t* __restrict__ counters) {
   using A = Ar<P>;
   constexpr int K = D + 1;
   constexpr int SPU = D == 2 ? 2 : 1;  // samples per Philox call
-  const GridP<P> gr = *gp;
+  GridP<P> gr;
+  if (MODE != kAsmCached) gr = *gp;
   const int lane = threadIdx.x & 31;
+  const int64_t ns = p.ne * (int64_t)p.N;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const P alphaP = (P)p.alpha;
@@ -83,7 +90,7 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) k_assemble(const P* __res
       for (int m = 0; m < K; ++m) {
         v[m] = __ldg(tconn + t * K + m);
 #pragma unroll
-        for (int a = 0; a < D; ++a) xv[m][a] = __ldg(tx + (int64_t)v[m] * D + a);
+        for (int a = 0; a < D; ++a) xv[m][a] = MODE == kAsmCached ? P(0) : __ldg(tx + (int64_t)v[m] * D + a);
 #pragma unroll
         for (int f = 0; f < NF; ++f) gl[f][m] = f < p.nf ? __ldg(g + (int64_t)f * p.nv + v[m]) : P(0);
       }
@@ -102,14 +109,31 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) k_assemble(const P* __res
         } else {
           spacing_weights<P>(w.x, w.y, w.z, lam);
         }
-        P X[D];
-        map_point<D, P>(lam, xv, X);
         P mu[K];
-        int status;
-        const int32_t e = locate_point<D, P>(gr, cell_start, cell_items, recs, X, mu, status);
+        int status = 0;
+        int32_t e;
+        const int64_t idx = t * p.N + j;
+        if constexpr (MODE == kAsmCached) {
+          e = __ldg(sample_elem + idx);
+          P m0 = P(1);
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            mu[a + 1] = __ldg(pmu + a * ns + idx);
+            m0 = A::sub(m0, mu[a + 1]);  // the predicate's mu_0, bit for bit
+          }
+          mu[0] = m0;
+        } else {
+          P X[D];
+          map_point<D, P>(lam, xv, X);
+          e = locate_point<D, P>(gr, cell_start, cell_items, recs, X, mu, status);
+          if (MODE != kAsmPlain) sample_elem[idx] = e;
+          if (MODE == kAsmRecord) {
+#pragma unroll
+            for (int a = 0; a < D; ++a) pmu[a * ns + idx] = mu[a + 1];
+          }
+        }
         n_fallback += status == 1;
         n_empty += status == 2;
-        if (DBG) sample_elem[t * p.N + j] = e;
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
           if (f >= p.nf) break;
@@ -173,10 +197,12 @@ static void launch_t(sft_source_s* s, sft_target_s* t, const AssembleArgs& a, co
     ::sft::note_launch(), kern<<<(unsigned)blocks, threads, 0, st>>>((const P*)t->coordsP[a.prec], t->conn, t->vol, t->vol32, (const P*)a.g,
                                                (const GridP<P>*)L.grid, L.cell_start, L.cell_items,
                                                (const P*)L.recs, (const P*)L.vals, p, a.b, a.sample_elem,
-                                               a.counters);
+                                               (P*)a.pmu, a.counters);
   };
-  if (a.sample_elem) args(k_assemble<D, P, NF, true>);
-  else args(k_assemble<D, P, NF, false>);
+  if (a.mode == kAsmCached) args(k_assemble<D, P, NF, kAsmCached>);
+  else if (a.mode == kAsmRecord) args(k_assemble<D, P, NF, kAsmRecord>);
+  else if (a.sample_elem) args(k_assemble<D, P, NF, kAsmDebug>);
+  else args(k_assemble<D, P, NF, kAsmPlain>);
 }
 
 template <int D, typename P>

@@ -117,13 +117,14 @@ namespace sft {
 sft_status build_locator(sft_source_s* s, int prec, cudaStream_t st, int32_t* d_err);
 sft_status locate_points(sft_source_s* s, int prec, int64_t n, const void* pts, int pts_are_double,
                          int32_t* elem_out, void* val_out, int val_is_double, int64_t val_stride,
-                         int64_t* d_counters, cudaStream_t st, int nf_out = -1);
+                         int64_t* d_counters, cudaStream_t st, int nf_out = -1, void* mu_out = nullptr);
 sft_status source_integrals(sft_source_s* s, cudaStream_t st);
 sft_status refresh_value_copies(sft_source_s* s, cudaStream_t st);
 // target.cu
 sft_status build_target(sft_target_s* t, cudaStream_t st, int32_t* d_err);
 sft_status target_coordsP(sft_target_s* t, int prec, cudaStream_t st);
 // assemble.cu
+enum AsmMode : int { kAsmPlain = 0, kAsmDebug = 1, kAsmRecord = 2, kAsmCached = 3 };
 struct AssembleArgs {
   int prec;
   int nf;
@@ -133,8 +134,10 @@ struct AssembleArgs {
   double alpha;
   const void* g;          // [nf][nv_t] P
   double* b;              // [nf][nv_t] FP64 (accumulated)
-  int32_t* sample_elem;   // optional [ne_t][N]
+  int32_t* sample_elem;   // optional [ne_t][N] (debug, record: written; cached: read)
   int64_t* counters;      // [2]: fallback, empty
+  int mode = kAsmPlain;
+  void* pmu = nullptr;    // record / cached: [d][ne_t N] P, mu_1..d of every sample
 };
 sft_status launch_assembly(sft_source_s* s, sft_target_s* t, const AssembleArgs& a, cudaStream_t st);
 // solve.cu

@@ -535,7 +535,7 @@ __global__ void __launch_bounds__(256) k_locate_points(const TIn* __restrict__ p
                                                        const P* __restrict__ recs, const P* __restrict__ vals,
                                                        int64_t ne, int nf, int32_t* __restrict__ elem_out,
                                                        TOut* __restrict__ val_out, int64_t val_stride,
-                                                       int64_t* __restrict__ counters) {
+                                                       int64_t* __restrict__ counters, P* __restrict__ mu_out) {
   const GridP<P> g = *gp;
   int n_fallback = 0, n_empty = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -551,6 +551,10 @@ __global__ void __launch_bounds__(256) k_locate_points(const TIn* __restrict__ p
     n_fallback += status == 1;
     n_empty += status == 2;
     if (elem_out) elem_out[i] = e;
+    if (mu_out) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) mu_out[a * n + i] = mu[a + 1];
+    }
     if (val_out) {
       for (int f = 0; f < nf; ++f)
         val_out[(int64_t)f * val_stride + i] = e >= 0 ? (TOut)eval_p1<D, P>(vals, ne, f, e, mu) : TOut(0);
@@ -568,7 +572,7 @@ __global__ void __launch_bounds__(256) k_locate_points(const TIn* __restrict__ p
 template <int D, typename P>
 static void launch_locate(sft_source_s* s, const Locator& L, int64_t n, const void* pts, int pts_are_double,
                           int32_t* elem_out, void* val_out, int val_is_double, int64_t val_stride,
-                          int64_t* counters, cudaStream_t st, int nf) {
+                          int64_t* counters, cudaStream_t st, int nf, void* mu_out) {
   const unsigned blocks = grid_for(n);
   const GridP<P>* g = (const GridP<P>*)L.grid;
   const P* recs = (const P*)L.recs;
@@ -576,7 +580,7 @@ static void launch_locate(sft_source_s* s, const Locator& L, int64_t n, const vo
 #define SFT_LOC(TIN, TOUT)                                                                                      \
   ::sft::note_launch(), k_locate_points<D, P, TIN, TOUT><<<blocks, 256, 0, st>>>((const TIN*)pts, n, g, L.cell_start, L.cell_items, \
                                                            recs, vals, s->ne, nf, elem_out, (TOUT*)val_out,  \
-                                                           val_stride, counters)
+                                                           val_stride, counters, (P*)mu_out)
   if (pts_are_double) {
     if (val_is_double) SFT_LOC(double, double); else SFT_LOC(double, P);
   } else {
@@ -587,17 +591,17 @@ static void launch_locate(sft_source_s* s, const Locator& L, int64_t n, const vo
 
 sft_status locate_points(sft_source_s* s, int prec, int64_t n, const void* pts, int pts_are_double,
                          int32_t* elem_out, void* val_out, int val_is_double, int64_t val_stride,
-                         int64_t* d_counters, cudaStream_t st, int nf_out) {
+                         int64_t* d_counters, cudaStream_t st, int nf_out, void* mu_out) {
   const Locator& L = s->loc[prec];
   const int nf = nf_out < 0 ? s->nf : nf_out;
   if (!L.built) return fail(SFT_ERR_ARG, "locator not built");
   if (n <= 0) return SFT_OK;
   if (s->dim == 2) {
-    if (prec == SFT_PREC_FP32) launch_locate<2, float>(s, L, n, pts, pts_are_double, elem_out, val_out, val_is_double, val_stride, d_counters, st, nf);
-    else launch_locate<2, double>(s, L, n, pts, pts_are_double, elem_out, val_out, val_is_double, val_stride, d_counters, st, nf);
+    if (prec == SFT_PREC_FP32) launch_locate<2, float>(s, L, n, pts, pts_are_double, elem_out, val_out, val_is_double, val_stride, d_counters, st, nf, mu_out);
+    else launch_locate<2, double>(s, L, n, pts, pts_are_double, elem_out, val_out, val_is_double, val_stride, d_counters, st, nf, mu_out);
   } else {
-    if (prec == SFT_PREC_FP32) launch_locate<3, float>(s, L, n, pts, pts_are_double, elem_out, val_out, val_is_double, val_stride, d_counters, st, nf);
-    else launch_locate<3, double>(s, L, n, pts, pts_are_double, elem_out, val_out, val_is_double, val_stride, d_counters, st, nf);
+    if (prec == SFT_PREC_FP32) launch_locate<3, float>(s, L, n, pts, pts_are_double, elem_out, val_out, val_is_double, val_stride, d_counters, st, nf, mu_out);
+    else launch_locate<3, double>(s, L, n, pts, pts_are_double, elem_out, val_out, val_is_double, val_stride, d_counters, st, nf, mu_out);
   }
   SFT_CUDA(cudaGetLastError());
   return SFT_OK;
