@@ -39,7 +39,7 @@ struct BReq {
   const float* recs;
   const float* vals;
   int64_t nes;
-  int32_t nf, N, U, G;
+  int32_t nf, N, U, G, LPE;
   int64_t ntasks;
   PhiloxKey key;
   uint32_t stream_id;
@@ -115,8 +115,8 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_control(const BReq* __r
 
 // ---------------------------------------------------------------------------
 // steps 2-6: persistent fused assembly over the tasks of a request group.
-// A task is one warp's share of one request (one element when the element
-// has >= 32 Philox units, else floor(32/U) elements). Per-lane partials are
+// A task is one warp's share of one request: floor(32/LPE) elements, LPE =
+// min(U, 4) lanes per element striding over its Philox units. Per-lane partials are
 // plain FP32 sums of a lane's few samples; the warp combine is compensated.
 // ---------------------------------------------------------------------------
 template <int D, int NF>
@@ -145,15 +145,13 @@ __global__ void __launch_bounds__(kBatchThreads, NF <= 2 ? 4 : (NF <= 4 ? 3 : 2)
       const int gi = find_seg(s_off, ng, task_g);
       const BReq& R = reqs[greq[gi]];
       const int64_t task = task_g - s_off[gi];
-      const int U = R.U, G = R.G, N = R.N, nf = R.nf;
+      const int U = R.U, G = R.G, N = R.N, nf = R.nf, LPE = R.LPE;
       int64_t t;
       int u0, ustep, seg_lo, seg_hi;
       bool active;
-      if (G == 1) {
-        t = task; u0 = lane; ustep = 32; seg_lo = 0; seg_hi = 32; active = true;
-      } else {
-        const int slot = lane / U;
-        t = task * G + slot; u0 = lane - slot * U; ustep = U; seg_lo = slot * U; seg_hi = seg_lo + U;
+      {
+        const int slot = lane / LPE;
+        t = task * G + slot; u0 = lane - slot * LPE; ustep = LPE; seg_lo = slot * LPE; seg_hi = seg_lo + LPE;
         active = slot < G;
       }
       active = active && t < R.ne;
@@ -820,7 +818,8 @@ static sft_status build_batch(sft_batch_s* B, const sft_options* opts, int autot
     R.N = o.samples_per_elem;
     const int spu = t->dim == 2 ? 2 : 1;
     R.U = (R.N + spu - 1) / spu;
-    R.G = R.U >= 32 ? 1 : 32 / R.U;
+    R.LPE = R.U >= 4 ? 4 : R.U;  // lanes per element, as in the single-transfer kernel
+    R.G = 32 / R.LPE;
     R.ntasks = (t->ne + R.G - 1) / R.G;
     R.key.k0 = (uint32_t)o.seed;
     R.key.k1 = (uint32_t)(o.seed >> 32);
