@@ -49,6 +49,15 @@ typedef enum {
  * global reductions in FP64. FP64: everything in FP64. */
 typedef enum { SFT_PREC_FP64 = 0, SFT_PREC_FP32 = 1 } sft_precision;
 
+/* How the FP64 system M u = b of step 7 is solved (both stop on the true
+ * FP64 residual ||b - M u||_2 <= cg_tol ||b||_2, which is computed in FP64).
+ * MIXED: iterative refinement -- FP64 residual and solution, each correction
+ * by CG in FP32 on the symmetrically Jacobi-scaled matrix
+ * diag(M)^-1/2 M diag(M)^-1/2 (its condition number is bounded by a small
+ * constant for any P1 mass matrix, so FP32 inner solves are safe).
+ * FP64: Jacobi-preconditioned CG in FP64 throughout. */
+typedef enum { SFT_CG_MIXED = 0, SFT_CG_FP64 = 1 } sft_cg_mode;
+
 /* element type of coordinate / value arrays */
 typedef enum { SFT_F32 = 0, SFT_F64 = 1 } sft_dtype;
 
@@ -82,7 +91,7 @@ typedef struct {
     void* cuda_stream;          /* cudaStream_t */
     int32_t* sample_elem_out;   /* optional [nelems][N]: source element located for every sample */
     int32_t field_count;        /* 0: every source field; k > 0: the first k fields only */
-    int32_t reserved;
+    int32_t cg_mode;            /* sft_cg_mode (0: mixed-precision refinement) */
 } sft_options;
 
 typedef struct {
@@ -155,11 +164,14 @@ sft_status sft_locate(sft_source src, int32_t precision, int64_t n, const double
                       void* cuda_stream);
 
 /* Solve M u = b on the target (step 7 alone) for nrhs right-hand sides
- * b [nrhs][nnodes] -> u [nrhs][nnodes], FP64, Jacobi-PCG from u = 0.
- * iters_out / rel_resid_out (host, may be NULL) get the worst field. */
+ * b [nrhs][nnodes] -> u [nrhs][nnodes] (FP64), from u = 0, by the sft_cg_mode
+ * `cg_mode`. max_iter bounds the CG iterations (FP32 inner iterations summed
+ * over the refinement cycles in MIXED mode). iters_out / rel_resid_out (host,
+ * may be NULL) get the worst field; rel_resid is the true FP64 residual of the
+ * returned u in MIXED mode, the recurrence residual in FP64 mode. */
 sft_status sft_mass_solve(sft_target tgt, int32_t nrhs, const double* b, double* u,
-                          int32_t device_ptrs, double tol, int32_t max_iter, void* cuda_stream,
-                          int32_t* iters_out, double* rel_resid_out);
+                          int32_t device_ptrs, double tol, int32_t max_iter, int32_t cg_mode,
+                          void* cuda_stream, int32_t* iters_out, double* rel_resid_out);
 
 /* ---- batched transfers ----
  * Many requests (source, target, options) of uneven size run together: the

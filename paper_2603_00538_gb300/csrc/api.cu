@@ -130,7 +130,7 @@ void sft_source_destroy(sft_source s) {
 void sft_target_destroy(sft_target t) {
   if (!t) return;
   cudaStream_t st = t->stream;
-  void* bufs[] = {t->coords, t->conn, t->coordsP[0], t->coordsP[1], t->vol, t->vol32, t->row_ptr, t->col, t->val, t->dinv, t->lumped};
+  void* bufs[] = {t->coords, t->conn, t->coordsP[0], t->coordsP[1], t->vol, t->vol32, t->row_ptr, t->col, t->val, t->dinv, t->lumped, t->sc, t->val32s};
   for (void* p : bufs)
     if (p) cudaFreeAsync(p, st);
   delete t;
@@ -229,6 +229,7 @@ sft_status sft_transfer(sft_source s, sft_target t, const sft_options* o, double
   if ((int64_t)o->samples_per_elem * t->ne >= ((int64_t)1 << 40)) return fail(SFT_ERR_UNSUPPORTED, "too many samples");
   if (o->precision != SFT_PREC_FP32 && o->precision != SFT_PREC_FP64) return fail(SFT_ERR_ARG, "bad precision");
   if (o->cg_max_iter < 0 || !(o->cg_tol >= 0) || !std::isfinite(o->alpha)) return fail(SFT_ERR_ARG, "bad solver options");
+  if (o->cg_mode != SFT_CG_MIXED && o->cg_mode != SFT_CG_FP64) return fail(SFT_ERR_ARG, "unknown cg_mode");
   if (o->field_count < 0 || o->field_count > s->nf) return fail(SFT_ERR_ARG, "field_count out of range");
   cudaStream_t st = (cudaStream_t)o->cuda_stream;
   const int prec = o->precision;
@@ -291,7 +292,8 @@ sft_status sft_transfer(sft_source s, sft_target t, const sft_options* o, double
     u_dev = u_tmp.p;
   }
   SolveResult sr;
-  if (sft_status r = mass_solve(t, nf, b.p, u_dev, o->cg_tol, o->cg_max_iter, st, d_err.p, &sr)) return r;
+  if (sft_status r = mass_solve(t, nf, b.p, u_dev, o->cg_tol, o->cg_max_iter, st, d_err.p, &sr, o->cg_mode))
+    return r;
   if (ev.ok) cudaEventRecord(ev.e[4], st);
 
   const cudaMemcpyKind d2o = o->out_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -388,8 +390,10 @@ sft_status sft_locate(sft_source s, int32_t precision, int64_t n, const double* 
 }
 
 sft_status sft_mass_solve(sft_target t, int32_t nrhs, const double* b, double* u, int32_t device_ptrs, double tol,
-                          int32_t max_iter, void* cuda_stream, int32_t* iters_out, double* rel_resid_out) {
+                          int32_t max_iter, int32_t cg_mode, void* cuda_stream, int32_t* iters_out,
+                          double* rel_resid_out) {
   if (!t || !b || !u) return fail(SFT_ERR_ARG, "null argument");
+  if (cg_mode != SFT_CG_MIXED && cg_mode != SFT_CG_FP64) return fail(SFT_ERR_ARG, "unknown cg_mode");
   if (nrhs < 1 || nrhs > kMaxFields) return fail(SFT_ERR_ARG, "nrhs must be in 1..8");
   if (max_iter < 0 || !(tol >= 0)) return fail(SFT_ERR_ARG, "bad solver options");
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -405,7 +409,7 @@ sft_status sft_mass_solve(sft_target t, int32_t nrhs, const double* b, double* u
     ud = ut.p;
   }
   SolveResult sr;
-  if (sft_status r = mass_solve(t, nrhs, bd, ud, tol, max_iter, st, nullptr, &sr)) return r;
+  if (sft_status r = mass_solve(t, nrhs, bd, ud, tol, max_iter, st, nullptr, &sr, cg_mode)) return r;
   if (!device_ptrs) SFT_CUDA(cudaMemcpyAsync(u, ud, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
   SFT_CUDA(cudaStreamSynchronize(st));
   if (iters_out) *iters_out = sr.iters;

@@ -992,6 +992,7 @@ sft_status sft_batch_create(int32_t nreq, const sft_source* srcs, const sft_targ
     if (o.precision != SFT_PREC_FP32) return fail(SFT_ERR_UNSUPPORTED, "batched transfers use the FP32 path");
     if (o.samples_per_elem < 1 || o.cg_max_iter < 0 || !(o.cg_tol >= 0) || !std::isfinite(o.alpha))
       return fail(SFT_ERR_ARG, "bad request options");
+    if (o.cg_mode != SFT_CG_MIXED && o.cg_mode != SFT_CG_FP64) return fail(SFT_ERR_ARG, "unknown cg_mode");
     if (o.field_count < 0 || o.field_count > srcs[r]->nf) return fail(SFT_ERR_ARG, "field_count out of range");
   }
   auto* B = new sft_batch_s();

@@ -110,6 +110,10 @@ struct sft_target_s {
   double* val = nullptr;        // [nnz]
   double* dinv = nullptr;       // [nv]
   double* lumped = nullptr;     // [nv]
+  // symmetric Jacobi scaling for the mixed-precision solve (made on first use):
+  // sc = diag(M)^-1/2 and the FP32 values of sc_i M_ij sc_j
+  double* sc = nullptr;         // [nv]
+  float* val32s = nullptr;      // [nnz]
 };
 
 namespace sft {
@@ -142,8 +146,9 @@ struct AssembleArgs {
 sft_status launch_assembly(sft_source_s* s, sft_target_s* t, const AssembleArgs& a, cudaStream_t st);
 // solve.cu
 struct SolveResult { int iters; double rel_resid; int converged; };
+// cg_mode: SFT_CG_MIXED (FP64 refinement around FP32 CG) or SFT_CG_FP64
 sft_status mass_solve(sft_target_s* t, int nrhs, const double* b, double* x, double tol, int max_iter,
-                      cudaStream_t st, int32_t* d_err, SolveResult* res);
+                      cudaStream_t st, int32_t* d_err, SolveResult* res, int cg_mode = SFT_CG_MIXED);
 sft_status weighted_sum(const double* w, const double* u, int64_t n, double* out_host, cudaStream_t st);
 // conversions
 sft_status convert_coords(const void* in, int in_dtype, void* out, int out_prec, int64_t n, cudaStream_t st);

@@ -69,6 +69,7 @@ sft_status sft_plan_create(sft_source s, sft_target t, const sft_options* o, sft
   if ((int64_t)o->samples_per_elem * t->ne >= ((int64_t)1 << 40)) return fail(SFT_ERR_UNSUPPORTED, "too many samples");
   if (o->precision != SFT_PREC_FP32 && o->precision != SFT_PREC_FP64) return fail(SFT_ERR_ARG, "bad precision");
   if (o->cg_max_iter < 0 || !(o->cg_tol >= 0) || !std::isfinite(o->alpha)) return fail(SFT_ERR_ARG, "bad solver options");
+  if (o->cg_mode != SFT_CG_MIXED && o->cg_mode != SFT_CG_FP64) return fail(SFT_ERR_ARG, "unknown cg_mode");
   if (o->field_count < 0 || o->field_count > s->nf) return fail(SFT_ERR_ARG, "field_count out of range");
   cudaStream_t st = (cudaStream_t)o->cuda_stream;
   const int prec = o->precision;
@@ -205,7 +206,8 @@ sft_status sft_plan_transfer(sft_plan pl, double* u_out, double* b_out, double* 
     u_dev = u_tmp.p;
   }
   SolveResult sr;
-  if (sft_status r = mass_solve(t, nf, b.p, u_dev, o.cg_tol, o.cg_max_iter, st, d_err.p, &sr)) return r;
+  if (sft_status r = mass_solve(t, nf, b.p, u_dev, o.cg_tol, o.cg_max_iter, st, d_err.p, &sr, o.cg_mode))
+    return r;
   if (ev.ok) cudaEventRecord(ev.e[4], st);
   const cudaMemcpyKind d2o = o.out_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (!o.out_device) SFT_CUDA(cudaMemcpyAsync(u_out, u_dev, sizeof(double) * nv * nf, d2o, st));

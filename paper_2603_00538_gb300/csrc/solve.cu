@@ -1,10 +1,12 @@
 // Step 7 of Sec. 4: solve the target Galerkin system M u = b (Eq.
-// cv_galerkin_system) in FP64 with Jacobi-preconditioned CG from u = 0,
-// stopping at ||b - M u||_2 <= tol ||b||_2 (the paper does not name its
-// solver; see the design notes).
+// cv_galerkin_system) from u = 0, stopping at ||b - M u||_2 <= tol ||b||_2
+// (the paper does not name its solver). Two kernels:
+//   k_pcg       Jacobi-preconditioned CG in FP64 (cg_mode FP64, and the
+//               allocation-free entry point, which takes any SPD CSR matrix);
+//   k_mixed_cg  mixed-precision iterative refinement (default; see below).
 //
 // One cooperative (co-resident) kernel runs the whole iteration: no host round
-// trip per step. Each iteration has two grid barriers:
+// trip per step. Each k_pcg iteration has two grid barriers:
 //   A: w = M z (SpMV), then for the own row p = z + beta p and
 //      q = w + beta q (= M p by linearity, one FP64 FMA per nonzero instead of
 //      two), and the partial dot p.q;
@@ -215,8 +217,401 @@ __global__ void __launch_bounds__(kSolveThreads) k_pcg(const int32_t* __restrict
   }
 }
 
+// ---------------------------------------------------------------------------
+// Mixed-precision iterative refinement (cg_mode MIXED).
+//
+// With S = diag(M)^-1/2 the scaled matrix A = S M S has unit diagonal. For P1
+// elements the element mass matrix against its own diagonal has eigenvalues
+// in [1/2, 2] (triangles) or [1/2, 5/2] (tetrahedra), and the assembled
+// matrix inherits the union of the element bounds, so cond(A) <= 4 or 5 on
+// any mesh: CG in FP32 on A converges like Jacobi-PCG in FP64 on M, and its
+// attainable accuracy (~ eps32 cond(A)) is far below the per-cycle target.
+// One refinement cycle:
+//   R (FP64)  r = b - M x, t = S r, ||r||_2 (the stopping test) and ||t||_2;
+//   I         c = t / ||t||_2 rounded to FP32 (unit norm), y = 0;
+//   CG (FP32) on A y = c until ||c - A y||_2 <= eta, eta about the reduction
+//             the stopping test still needs (between 1e-5 and 1/4);
+//   U (FP64)  x += ||t||_2 S y   (so the new residual is ||t|| S^-1 (c - A y)).
+// The FP64 pipe does one SpMV per cycle (2 to 3 cycles) instead of one per
+// iteration. Every block takes every decision from the same fixed-order
+// reductions; the stopping test uses the true FP64 residual.
+constexpr float kEtaFloor = 1e-5f;
+#ifndef SFT_MIX_ROWS_PER_THREAD
+#define SFT_MIX_ROWS_PER_THREAD 3
+#endif
+
+struct MixCtl {
+  GridBarrier bar;
+  int32_t err;
+  int32_t cycles;
+  int32_t iters[kMaxFields];
+  double rel[kMaxFields];
+  int32_t conv[kMaxFields];
+};
+
+template <int NR>
+__device__ __forceinline__ void block_partials_d(const double (&v)[NR][2], int nrhs, double* part) {
+  __shared__ double sh[kSolveThreads / 32][NR][2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int f = 0; f < NR; ++f) {
+    if (f >= nrhs) break;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const double w = warp_sum<double>(v[f][c]);
+      if (lane == 0) sh[warp][f][c] = w;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < nrhs * 2) {
+    const int f = threadIdx.x >> 1, c = threadIdx.x & 1;
+    double s = 0.0;
+    for (int w = 0; w < kSolveThreads / 32; ++w) s += sh[w][f][c];
+    part[((int64_t)blockIdx.x * nrhs + f) * 2 + c] = s;
+  }
+  __syncthreads();
+}
+
+template <int NR>
+__device__ __forceinline__ void block_partials_f(const float (&v)[NR], int nrhs, float* part) {
+  __shared__ float sh[kSolveThreads / 32][NR];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int f = 0; f < NR; ++f) {
+    if (f >= nrhs) break;
+    const float w = warp_sum<float>(v[f]);
+    if (lane == 0) sh[warp][f] = w;
+  }
+  __syncthreads();
+  if (threadIdx.x < nrhs) {
+    float s = 0.f;
+    for (int w = 0; w < kSolveThreads / 32; ++w) s += sh[w][threadIdx.x];
+    part[(int64_t)blockIdx.x * nrhs + threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// sum the FP32 partials [nblocks][nrhs] in a fixed order (identical in all blocks)
+template <int NR>
+__device__ __forceinline__ void reduce_partials_f(const float* part, int nblocks, int nrhs, float* sh_tot) {
+  __shared__ float shw[kSolveThreads / 32][NR];
+  float acc[NR];
+#pragma unroll
+  for (int f = 0; f < NR; ++f) acc[f] = 0.f;
+  for (int bidx = threadIdx.x; bidx < nblocks; bidx += blockDim.x) {
+    const float* pb = part + (int64_t)bidx * nrhs;
+#pragma unroll
+    for (int f = 0; f < NR; ++f)
+      if (f < nrhs) acc[f] += __ldcg(pb + f);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int f = 0; f < NR; ++f) {
+    if (f >= nrhs) break;
+    const float w = warp_sum<float>(acc[f]);
+    if (lane == 0) shw[warp][f] = w;
+  }
+  __syncthreads();
+  if (threadIdx.x < nrhs) {
+    float t = 0.f;
+    for (int w = 0; w < kSolveThreads / 32; ++w) t += shw[w][threadIdx.x];
+    sh_tot[threadIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+// NR: compile-time bound on the number of right-hand sides (nrhs <= NR)
+template <int NR>
+__global__ void __launch_bounds__(kSolveThreads) k_mixed_cg(
+    const int32_t* __restrict__ rp, const int32_t* __restrict__ col, const double* __restrict__ val,
+    const float* __restrict__ aval, const double* __restrict__ sc, int64_t n, int nrhs,
+    const double* __restrict__ b, double* x, double* t, float* r, float* p, float* q, float* y, double* partd,
+    float* partf, MixCtl* ctl, double tol, int max_iter) {
+  __shared__ double totd[kMaxFields * 2];
+  __shared__ float totf[NR];
+  __shared__ double bnorm[NR], prev[NR], sig[NR], isig[NR];
+  __shared__ float eta2[NR], rr[NR], alpha[NR], beta[NR];
+  __shared__ int live[NR], act[NR], conv[NR], stop;
+  const unsigned nb = gridDim.x;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int f = 0; f < NR; ++f) {
+      live[f] = f < nrhs;
+      act[f] = 0;
+      conv[f] = 0;
+    }
+  }
+  __syncthreads();
+  int it = 0, cyc = 0;
+  for (;; ++cyc) {
+    // R: true residual in FP64 (x = 0 in the first cycle)
+    double v[NR][2];
+#pragma unroll
+    for (int f = 0; f < NR; ++f) v[f][0] = v[f][1] = 0.0;
+    for (int64_t i = tid; i < n; i += nthreads) {
+      const double si = sc[i];
+      int32_t k0 = 0, k1 = 0;
+      if (cyc > 0) {
+        k0 = __ldg(rp + i);
+        k1 = __ldg(rp + i + 1);
+      }
+#pragma unroll
+      for (int f = 0; f < NR; ++f) {
+        if (f >= nrhs) break;
+        if (!live[f]) continue;
+        const int64_t o = (int64_t)f * n;
+        double s = 0.0;
+        // x was written by other blocks before the grid barrier (plain loads)
+        for (int32_t k = k0; k < k1; ++k) s += __ldg(val + k) * x[o + __ldg(col + k)];
+        if (cyc == 0) x[o + i] = 0.0;
+        const double ri = b[o + i] - s;
+        const double ti = si * ri;
+        t[o + i] = ti;
+        v[f][0] += ri * ri;
+        v[f][1] += ti * ti;
+      }
+    }
+    block_partials_d<NR>(v, nrhs, partd);
+    if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+    reduce_partials(partd, nb, nrhs, totd);
+    if (threadIdx.x == 0) {
+      bool any = false;
+      for (int f = 0; f < nrhs; ++f) {
+        if (!live[f]) continue;
+        const double rn = sqrt(totd[2 * f]), tn = sqrt(totd[2 * f + 1]);
+        if (cyc == 0) bnorm[f] = rn;
+        if (blockIdx.x == 0) {
+          ctl->rel[f] = bnorm[f] > 0.0 ? rn / bnorm[f] : 0.0;
+          ctl->iters[f] = it;
+        }
+        if (rn <= tol * bnorm[f]) {
+          live[f] = 0;
+          conv[f] = 1;
+          continue;
+        }
+        // a cycle that did not halve the residual (FP64 rounding floor) or a
+        // residual on rows without diagonal ends the field unconverged
+        if ((cyc > 0 && rn > 0.5 * prev[f]) || !(tn > 0.0)) {
+          live[f] = 0;
+          continue;
+        }
+        prev[f] = rn;
+        sig[f] = tn;
+        isig[f] = 1.0 / tn;
+        const double e = fmin(0.25, fmax((double)kEtaFloor, 0.1 * tol * bnorm[f] / rn));
+        eta2[f] = (float)(e * e);
+        act[f] = 1;
+        any = true;
+      }
+      stop = !any || it >= max_iter;
+    }
+    __syncthreads();
+    if (stop) break;
+
+    // I: unit-norm FP32 right-hand side, zero iterate and directions
+    float vf[NR];
+#pragma unroll
+    for (int f = 0; f < NR; ++f) vf[f] = 0.f;
+    for (int64_t i = tid; i < n; i += nthreads) {
+#pragma unroll
+      for (int f = 0; f < NR; ++f) {
+        if (f >= nrhs) break;
+        if (!act[f]) continue;
+        const int64_t k = (int64_t)f * n + i;
+        const float ci = (float)(t[k] * isig[f]);
+        r[k] = ci;
+        y[k] = 0.f;
+        p[k] = 0.f;
+        q[k] = 0.f;
+        vf[f] += ci * ci;
+      }
+    }
+    block_partials_f<NR>(vf, nrhs, partf);
+    if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+    reduce_partials_f<NR>(partf, nb, nrhs, totf);
+    if (threadIdx.x == 0)
+      for (int f = 0; f < nrhs; ++f) {
+        rr[f] = totf[f];
+        beta[f] = 0.f;
+      }
+    __syncthreads();
+
+    // CG in FP32 on A y = c
+    for (;;) {
+      bool any = false;
+#pragma unroll
+      for (int f = 0; f < NR; ++f)
+        if (f < nrhs) any = any || act[f];
+      if (!any || it >= max_iter) break;
+      // phase A: w = A r, p = r + beta p, q = w + beta q (= A p), partial (p, q)
+#pragma unroll
+      for (int f = 0; f < NR; ++f) vf[f] = 0.f;
+      for (int64_t i = tid; i < n; i += nthreads) {
+        const int32_t k0 = __ldg(rp + i), k1 = __ldg(rp + i + 1);
+#pragma unroll
+        for (int f = 0; f < NR; ++f) {
+          if (f >= nrhs) break;
+          if (!act[f]) continue;
+          const int64_t o = (int64_t)f * n;
+          const float* rf = r + o;
+          float s = 0.f;
+          // r was written by other blocks before the grid barrier (plain loads)
+          for (int32_t k = k0; k < k1; ++k) s += __ldg(aval + k) * rf[__ldg(col + k)];
+          const float bt = beta[f];
+          const int64_t k = o + i;
+          const float pn = rf[i] + bt * p[k];
+          const float qn = s + bt * q[k];
+          p[k] = pn;
+          q[k] = qn;
+          vf[f] += pn * qn;
+        }
+      }
+      block_partials_f<NR>(vf, nrhs, partf);
+      if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+      reduce_partials_f<NR>(partf, nb, nrhs, totf);
+      if (threadIdx.x == 0)
+        for (int f = 0; f < nrhs; ++f) alpha[f] = act[f] ? rr[f] / totf[f] : 0.f;
+      __syncthreads();
+      // phase B: y += alpha p, r -= alpha q, partial (r, r)
+#pragma unroll
+      for (int f = 0; f < NR; ++f) vf[f] = 0.f;
+      for (int64_t i = tid; i < n; i += nthreads) {
+#pragma unroll
+        for (int f = 0; f < NR; ++f) {
+          if (f >= nrhs) break;
+          if (!act[f]) continue;
+          const int64_t k = (int64_t)f * n + i;
+          const float a = alpha[f];
+          y[k] += a * p[k];
+          const float ri = r[k] - a * q[k];
+          r[k] = ri;
+          vf[f] += ri * ri;
+        }
+      }
+      block_partials_f<NR>(vf, nrhs, partf);
+      if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+      reduce_partials_f<NR>(partf, nb, nrhs, totf);
+      ++it;
+      if (threadIdx.x == 0)
+        for (int f = 0; f < nrhs; ++f) {
+          if (!act[f]) continue;
+          const float rn = totf[f];
+          beta[f] = rn / rr[f];
+          rr[f] = rn;
+          if (rn <= eta2[f]) act[f] = 0;
+        }
+      __syncthreads();
+    }
+
+    // U: x += ||t|| S y for every field that ran this cycle
+    for (int64_t i = tid; i < n; i += nthreads) {
+      const double si = sc[i];
+#pragma unroll
+      for (int f = 0; f < NR; ++f) {
+        if (f >= nrhs) break;
+        if (!live[f]) continue;
+        const int64_t k = (int64_t)f * n + i;
+        x[k] += (sig[f] * si) * (double)y[k];
+      }
+    }
+    if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->cycles = cyc;
+    for (int f = 0; f < nrhs; ++f) ctl->conv[f] = conv[f];
+  }
+}
+
+// S = diag(M)^-1/2 (0 on a row without diagonal) and the FP32 scaled values
+__global__ void k_jacobi_sqrt(const double* __restrict__ dinv, int64_t n, double* __restrict__ sc) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    sc[i] = sqrt(dinv[i]);
+}
+
+__global__ void k_scaled_values(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                const double* __restrict__ val, const double* __restrict__ sc, int64_t n,
+                                float* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double si = sc[i];
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) out[k] = (float)(val[k] * si * sc[col[k]]);
+  }
+}
+
+static sft_status scaled_matrix(sft_target_s* t, cudaStream_t st) {
+  if (t->val32s) return SFT_OK;
+  const int64_t n = t->nv;
+  SFT_CUDA(dalloc(&t->sc, (size_t)n, st));
+  SFT_CUDA(dalloc(&t->val32s, (size_t)std::max<int64_t>(t->nnz, 1), st));
+  const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16));
+  ::sft::note_launch(), k_jacobi_sqrt<<<nb, 256, 0, st>>>(t->dinv, n, t->sc);
+  SFT_CUDA(cudaGetLastError());
+  ::sft::note_launch(), k_scaled_values<<<nb, 256, 0, st>>>(t->row_ptr, t->col, t->val, t->sc, n, t->val32s);
+  SFT_CUDA(cudaGetLastError());
+  return SFT_OK;
+}
+
+template <int NR>
+static sft_status launch_mixed(sft_target_s* t, int nrhs, const double* b, double* x, double tol, int max_iter,
+                               cudaStream_t st, SolveResult* res) {
+  const int64_t n = t->nv;
+  int dev = 0, sms = 0;
+  SFT_CUDA(cudaGetDevice(&dev));
+  SFT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int per_sm = 0;
+  SFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mixed_cg<NR>, kSolveThreads, 0));
+  if (per_sm < 1) return fail(SFT_ERR_CUDA, "solver kernel cannot be resident");
+  per_sm = std::min(per_sm, 4);
+  // as many resident blocks as ~3 rows per thread allows: measured 0.78 /
+  // 0.71 ms (1.0 M-row 2D / 0.5 M-row 3D systems) at 3 rows, 0.78 / 0.76 at
+  // 6, 1.04 / 1.06 at 12 (the FP32 phases are latency-bound, not FP64-bound)
+  constexpr int64_t kRows = SFT_MIX_ROWS_PER_THREAD;
+  const int64_t want = (n + kSolveThreads * kRows - 1) / (kSolveThreads * kRows);
+  const unsigned nblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, want));
+  const size_t vec = (size_t)n * nrhs;
+  DevBuf<double> tb(st), partd(st);
+  DevBuf<float> rb(st), pb(st), qb(st), yb(st), partf(st);
+  DevBuf<MixCtl> ctl(st);
+  SFT_CUDA(tb.alloc(vec));
+  SFT_CUDA(rb.alloc(vec));
+  SFT_CUDA(pb.alloc(vec));
+  SFT_CUDA(qb.alloc(vec));
+  SFT_CUDA(yb.alloc(vec));
+  SFT_CUDA(partd.alloc((size_t)nblocks * nrhs * 2));
+  SFT_CUDA(partf.alloc((size_t)nblocks * nrhs));
+  SFT_CUDA(ctl.alloc(1));
+  SFT_CUDA(cudaMemsetAsync(ctl.p, 0, sizeof(MixCtl), st));
+  const int32_t* rp = t->row_ptr;
+  const int32_t* col = t->col;
+  const double* val = t->val;
+  const float* aval = t->val32s;
+  const double* sc = t->sc;
+  double* tp = tb.p;
+  float *r = rb.p, *p = pb.p, *q = qb.p, *y = yb.p;
+  double* pd = partd.p;
+  float* pf = partf.p;
+  MixCtl* c = ctl.p;
+  void* args[] = {(void*)&rp, (void*)&col, (void*)&val, (void*)&aval, (void*)&sc, (void*)&n, (void*)&nrhs,
+                  (void*)&b, (void*)&x, (void*)&tp, (void*)&r, (void*)&p, (void*)&q, (void*)&y,
+                  (void*)&pd, (void*)&pf, (void*)&c, (void*)&tol, (void*)&max_iter};
+  const cudaError_t le = (::sft::note_launch(), cudaLaunchCooperativeKernel((const void*)k_mixed_cg<NR>, nblocks,
+                                                                           kSolveThreads, args, 0, st));
+  if (le != cudaSuccess) return cuda_fail(le, "cudaLaunchCooperativeKernel(k_mixed_cg)");
+  MixCtl h;
+  SFT_CUDA(cudaMemcpyAsync(&h, ctl.p, sizeof(MixCtl), cudaMemcpyDeviceToHost, st));
+  SFT_CUDA(cudaStreamSynchronize(st));
+  if (h.err != 0) return fail(SFT_ERR_DEVICE_STATUS, "CG kernel: grid barrier wait expired");
+  for (int f = 0; f < nrhs; ++f) {
+    res->iters = std::max(res->iters, (int)h.iters[f]);
+    res->rel_resid = std::max(res->rel_resid, h.rel[f]);
+    if (!h.conv[f]) res->converged = 0;
+  }
+  return SFT_OK;
+}
+
 sft_status mass_solve(sft_target_s* t, int nrhs, const double* b, double* x, double tol, int max_iter,
-                      cudaStream_t st, int32_t* d_err, SolveResult* res) {
+                      cudaStream_t st, int32_t* d_err, SolveResult* res, int cg_mode) {
   (void)d_err;
   res->iters = 0;
   res->rel_resid = 0.0;
@@ -228,6 +623,13 @@ sft_status mass_solve(sft_target_s* t, int nrhs, const double* b, double* x, dou
     SFT_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n * nrhs, st));
     res->converged = 0;
     return SFT_OK;
+  }
+  if (cg_mode == SFT_CG_MIXED) {
+    if (sft_status r = scaled_matrix(t, st)) return r;
+    if (nrhs == 1) return launch_mixed<1>(t, nrhs, b, x, tol, max_iter, st, res);
+    if (nrhs == 2) return launch_mixed<2>(t, nrhs, b, x, tol, max_iter, st, res);
+    if (nrhs <= 4) return launch_mixed<4>(t, nrhs, b, x, tol, max_iter, st, res);
+    return launch_mixed<8>(t, nrhs, b, x, tol, max_iter, st, res);
   }
   int dev = 0, sms = 0, coop = 0;
   SFT_CUDA(cudaGetDevice(&dev));

@@ -401,6 +401,7 @@ sft_status sft_transfer_surrogate(sft_mlp net, sft_source exact, sft_target t, c
   if (o->samples_per_elem < 1) return fail(SFT_ERR_ARG, "samples_per_elem must be >= 1");
   if ((int64_t)o->samples_per_elem * t->ne >= ((int64_t)1 << 40)) return fail(SFT_ERR_UNSUPPORTED, "too many samples");
   if (o->cg_max_iter < 0 || !(o->cg_tol >= 0) || !std::isfinite(o->alpha)) return fail(SFT_ERR_ARG, "bad solver options");
+  if (o->cg_mode != SFT_CG_MIXED && o->cg_mode != SFT_CG_FP64) return fail(SFT_ERR_ARG, "unknown cg_mode");
   if (exact) {
     if (exact->dim > t->dim) return fail(SFT_ERR_ARG, "exact source dimension exceeds the target's");
     if (so->exact_field < 0 || so->exact_field >= exact->nf) return fail(SFT_ERR_ARG, "exact_field out of range");
@@ -507,7 +508,8 @@ sft_status sft_transfer_surrogate(sft_mlp net, sft_source exact, sft_target t, c
     u_dev = u_tmp.p;
   }
   SolveResult sr;
-  if (sft_status r = mass_solve(t, 1, b.p, u_dev, o->cg_tol, o->cg_max_iter, st, d_err.p, &sr)) return r;
+  if (sft_status r = mass_solve(t, 1, b.p, u_dev, o->cg_tol, o->cg_max_iter, st, d_err.p, &sr, o->cg_mode))
+    return r;
   if (ev.ok) cudaEventRecord(ev.e[4], st);
 
   const cudaMemcpyKind d2o = o->out_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
