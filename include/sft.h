@@ -179,8 +179,10 @@ sft_status sft_mass_solve(sft_target tgt, int32_t nrhs, const double* b, double*
  * counterpart in the paper. The plan groups requests by dimension and field
  * count, and records one CUDA graph: control values of every request, a
  * persistent fused assembly per group (warps pull (request, element-tile)
- * work items from an atomic counter), and one cooperative FP64 CG over the
- * block-diagonal system of every (request, field) right-hand side. */
+ * work items from an atomic counter), and one cooperative solve over the
+ * block-diagonal system of every (request, field) right-hand side: the
+ * mixed-precision refinement when every request asks for SFT_CG_MIXED, else
+ * the FP64 CG for all. */
 typedef struct {
     int32_t nreq;
     int32_t graph;              /* 1: runs replay a captured CUDA graph; 0: direct launches */

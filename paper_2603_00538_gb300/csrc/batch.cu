@@ -5,8 +5,9 @@
 //   1. control values of every request      (k_batch_control, one per dim)
 //   2. fused assembly of every request      (k_batch_assemble, persistent, one per group:
 //      warps pull (request, element-task) tiles from an atomic work counter)
-//   3. one cooperative CG over the block-diagonal system of every
-//      (request, field) right-hand side     (k_batch_pcg)
+//   3. one cooperative solve of the block-diagonal system of every
+//      (request, field) right-hand side     (k_batch_mixed: mixed-precision
+//      refinement, the default; k_batch_pcg: FP64 CG when a request asks)
 // The tile size of each group is chosen by a small autotuner (timed trial
 // launches, cached per process and optionally in a file).
 #include <algorithm>
@@ -54,6 +55,8 @@ struct BSys {
   const int32_t* col;
   const double* val;
   const double* dinv;
+  const float* aval;  // FP32 values of S M S (mixed mode)
+  const double* sc;   // S = diag(M)^-1/2 (mixed mode)
   const double* b;
   double* x;
   int64_t off;  // first global row
@@ -281,13 +284,15 @@ struct BCgCtl {
 
 // segmented (by system index j, contiguous in lane order) warp sums of two
 // values; the first lane of each segment adds them to slot[j] of this warp
-__device__ __forceinline__ void warp_seg_add(int j, double a, double b, double (*slot)[2]) {
+// (T = float: the shuffle tree runs on the FP32 pipe; the slot stays FP64)
+template <typename T>
+__device__ __forceinline__ void warp_seg_add(int j, T a, T b, double (*slot)[2]) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const int j2 = __shfl_down_sync(0xffffffffu, j, o);
-    const double a2 = __shfl_down_sync(0xffffffffu, a, o);
-    const double b2 = __shfl_down_sync(0xffffffffu, b, o);
+    const T a2 = __shfl_down_sync(0xffffffffu, a, o);
+    const T b2 = __shfl_down_sync(0xffffffffu, b, o);
     if (lane + o < 32 && j2 == j) {
       a += a2;
       b += b2;
@@ -295,8 +300,8 @@ __device__ __forceinline__ void warp_seg_add(int j, double a, double b, double (
   }
   const int jp = __shfl_up_sync(0xffffffffu, j, 1);
   if (j >= 0 && (lane == 0 || jp != j)) {
-    slot[j][0] += a;
-    slot[j][1] += b;
+    slot[j][0] += (double)a;
+    slot[j][1] += (double)b;
   }
 }
 
@@ -382,7 +387,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_pcg(const BSys* __restr
         rzv = bi * di * bi;
         jj = j;
       }
-      warp_seg_add(jj, bb, rzv, s_w[warp]);
+      warp_seg_add<double>(jj, bb, rzv, s_w[warp]);
     }
   }
   publish();
@@ -428,7 +433,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_pcg(const BSys* __restr
             jj = j;
           }
         }
-        warp_seg_add(jj, pq, 0.0, s_w[warp]);
+        warp_seg_add<double>(jj, pq, 0.0, s_w[warp]);
       }
     }
     publish();
@@ -467,7 +472,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_pcg(const BSys* __restr
             jj = j;
           }
         }
-        warp_seg_add(jj, rr, rzv, s_w[warp]);
+        warp_seg_add<double>(jj, rr, rzv, s_w[warp]);
       }
     }
     publish();
@@ -497,6 +502,301 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_pcg(const BSys* __restr
     }
   }
   // results: written by the first block of each system
+  if (threadIdx.x < nloc) {
+    const int j = threadIdx.x;
+    const int s = slo + j;
+    if (sys[s].blo == b) {
+      out[s].iters = s_it[j];
+      out[s].conv = s_conv[j];
+      out[s].rel = s_rel[j];
+    }
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched mixed-precision iterative refinement (the cg_mode MIXED solve of
+// every (request, field) system at once; see the single-system k_mixed_cg):
+// per refinement cycle an FP64 residual pass R, the FP32 right-hand side
+// pass I, FP32 CG on S M S (phases A and B) and the FP64 update U. All
+// systems step through the same phases; a system whose inner solve reached
+// its target (or that converged) skips the row work of the phase. Whether
+// any system still works is a flag summed over blocks, read after the next
+// grid barrier (three rotating flags: the one of decision d is cleared at
+// decision d + 2, when every block has read it).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBatchThreads) k_batch_mixed(const BSys* __restrict__ sys, int nsys, int64_t ntot,
+                                                               int64_t rows_per_block,
+                                                               const int32_t* __restrict__ blk_slo,
+                                                               const int32_t* __restrict__ blk_shi, int maxs,
+                                                               double* t, float* r, float* p, float* q, float* y,
+                                                               double* part, BSysOut* __restrict__ out, BCgCtl* ctl) {
+  __shared__ double s_bn[kMaxLocalSys], s_prev[kMaxLocalSys], s_sig[kMaxLocalSys], s_isig[kMaxLocalSys],
+      s_rel[kMaxLocalSys];
+  __shared__ float s_eta2[kMaxLocalSys], s_rr[kMaxLocalSys], s_alpha[kMaxLocalSys], s_beta[kMaxLocalSys];
+  __shared__ int s_live[kMaxLocalSys], s_act[kMaxLocalSys], s_conv[kMaxLocalSys], s_it[kMaxLocalSys];
+  __shared__ int64_t s_off[kMaxLocalSys + 1];
+  __shared__ double s_w[kBatchWarps][kMaxLocalSys][2];
+  __shared__ double s_g[kMaxLocalSys][2];
+  __shared__ int s_any;
+  const unsigned nb = gridDim.x;
+  const int b = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row0 = (int64_t)b * rows_per_block;
+  const int64_t row1 = min(ntot, row0 + rows_per_block);
+  const int slo = blk_slo[b], shi = blk_shi[b];
+  const int nloc = row0 < row1 ? shi - slo + 1 : 0;
+  for (int j = threadIdx.x; j <= nloc; j += blockDim.x)
+    s_off[j] = j < nloc ? max(row0, sys[slo + j].off) : row1;
+  for (int j = threadIdx.x; j < nloc; j += blockDim.x) {
+    s_live[j] = sys[slo + j].n > 0;
+    s_act[j] = 0;
+    s_conv[j] = sys[slo + j].n == 0;
+    s_it[j] = 0;
+    s_rel[j] = 0.0;
+  }
+
+  auto clear_slots = [&]() {
+    for (int j = lane; j < nloc; j += 32) s_w[warp][j][0] = s_w[warp][j][1] = 0.0;
+    __syncwarp();
+  };
+  auto publish = [&]() {
+    __syncthreads();
+    for (int k = threadIdx.x; k < nloc * 2; k += blockDim.x) {
+      const int j = k >> 1, c = k & 1;
+      double v = 0.0;
+      for (int w = 0; w < kBatchWarps; ++w) v += s_w[w][j][c];
+      part[((int64_t)b * maxs + j) * 2 + c] = v;
+    }
+  };
+  auto gather_all = [&]() {
+    for (int j = warp; j < nloc; j += kBatchWarps) {
+      const int s = slo + j;
+      const BSys& S = sys[s];
+      double a0 = 0.0, a1 = 0.0;
+      for (int bb = S.blo + lane; bb <= S.bhi; bb += 32) {
+        const double* pp = part + ((int64_t)bb * maxs + (s - blk_slo[bb])) * 2;
+        a0 += __ldcg(pp);
+        a1 += __ldcg(pp + 1);
+      }
+      a0 = warp_sum<double>(a0);
+      a1 = warp_sum<double>(a1);
+      if (lane == 0) {
+        s_g[j][0] = a0;
+        s_g[j][1] = a1;
+      }
+    }
+    __syncthreads();
+  };
+  int dcount = 0;
+  // block's vote for decision dcount (s_any set by the per-system threads)
+  auto post = [&]() {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (b == 0) atomicExch(&ctl->flag[(dcount + 1) % 3], 0u);
+      if (s_any) atomicAdd(&ctl->flag[dcount % 3], 1u);
+    }
+    ++dcount;
+  };
+  auto voted = [&]() -> bool {
+    return *reinterpret_cast<volatile unsigned int*>(&ctl->flag[(dcount - 1) % 3]) != 0u;
+  };
+  __syncthreads();
+
+  for (int cyc = 0;; ++cyc) {
+    // R: r = b - M x in FP64 (x = 0 in the first cycle), t = S r; partials r.r, t.t
+    clear_slots();
+    {
+      int j = 0;
+      for (int64_t base = row0 + warp * 32; base < row1; base += kBatchThreads) {
+        const int64_t gr = base + lane;
+        double rr = 0.0, tt = 0.0;
+        int jj = -1;
+        if (gr < row1) {
+          while (j + 1 < nloc && gr >= s_off[j + 1]) ++j;
+          if (s_live[j]) {
+            const BSys& S = sys[slo + j];
+            const int64_t i = gr - S.off;
+            double w = 0.0;
+            if (cyc > 0) {
+              const int32_t k0 = __ldg(S.rp + i), k1 = __ldg(S.rp + i + 1);
+              // x of other blocks is visible to ordinary loads after the grid barrier
+              for (int32_t k = k0; k < k1; ++k) w += __ldg(S.val + k) * S.x[__ldg(S.col + k)];
+            } else {
+              S.x[i] = 0.0;
+            }
+            const double ri = S.b[i] - w;
+            const double ti = S.sc[i] * ri;
+            t[gr] = ti;
+            rr = ri * ri;
+            tt = ti * ti;
+            jj = j;
+          }
+        }
+        warp_seg_add<double>(jj, rr, tt, s_w[warp]);
+      }
+    }
+    publish();
+    if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+    gather_all();
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    if (threadIdx.x < nloc) {
+      const int j = threadIdx.x;
+      if (s_live[j]) {
+        const BSys& S = sys[slo + j];
+        const double rn = sqrt(s_g[j][0]), tn = sqrt(s_g[j][1]);
+        if (cyc == 0) s_bn[j] = rn;
+        s_rel[j] = s_bn[j] > 0.0 ? rn / s_bn[j] : 0.0;
+        if (rn <= S.tol * s_bn[j]) {
+          s_live[j] = 0;
+          s_conv[j] = 1;
+        } else if ((cyc > 0 && rn > 0.5 * s_prev[j]) || !(tn > 0.0) || s_it[j] >= S.max_iter) {
+          s_live[j] = 0;  // stagnated, no scaled residual, or out of iterations: unconverged
+        } else {
+          s_prev[j] = rn;
+          s_sig[j] = tn;
+          s_isig[j] = 1.0 / tn;
+          const double e = fmin(0.25, fmax(1e-5, 0.1 * S.tol * s_bn[j] / rn));
+          s_eta2[j] = (float)(e * e);
+          s_act[j] = 1;
+          atomicOr(&s_any, 1);
+        }
+      }
+    }
+    post();
+    // I: c = t / ||t|| in FP32, y = p = q = 0; partial c.c
+    clear_slots();
+    __syncthreads();
+    {
+      int j = 0;
+      for (int64_t base = row0 + warp * 32; base < row1; base += kBatchThreads) {
+        const int64_t gr = base + lane;
+        float cc = 0.f;
+        int jj = -1;
+        if (gr < row1) {
+          while (j + 1 < nloc && gr >= s_off[j + 1]) ++j;
+          if (s_act[j]) {
+            const float ci = (float)(t[gr] * s_isig[j]);
+            r[gr] = ci;
+            y[gr] = 0.f;
+            p[gr] = 0.f;
+            q[gr] = 0.f;
+            cc = ci * ci;
+            jj = j;
+          }
+        }
+        warp_seg_add<float>(jj, cc, 0.f, s_w[warp]);
+      }
+    }
+    publish();
+    if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+    if (!voted()) break;  // no system left to refine
+    gather_all();
+    if (threadIdx.x < nloc) {
+      const int j = threadIdx.x;
+      s_rr[j] = (float)s_g[j][0];
+      s_beta[j] = 0.f;
+    }
+    __syncthreads();
+
+    // FP32 CG on S M S y = c
+    for (int inner = 0;; ++inner) {
+      // A: w = A r, p = r + beta p, q = w + beta q; partial p.q
+      clear_slots();
+      {
+        int j = 0;
+        for (int64_t base = row0 + warp * 32; base < row1; base += kBatchThreads) {
+          const int64_t gr = base + lane;
+          float pq = 0.f;
+          int jj = -1;
+          if (gr < row1) {
+            while (j + 1 < nloc && gr >= s_off[j + 1]) ++j;
+            if (s_act[j]) {
+              const BSys& S = sys[slo + j];
+              const int64_t i = gr - S.off;
+              const float* rs = r + S.off;
+              const int32_t k0 = __ldg(S.rp + i), k1 = __ldg(S.rp + i + 1);
+              float w = 0.f;
+              for (int32_t k = k0; k < k1; ++k) w += __ldg(S.aval + k) * rs[__ldg(S.col + k)];
+              const float bt = s_beta[j];
+              const float pn = r[gr] + bt * p[gr];
+              const float qn = w + bt * q[gr];
+              p[gr] = pn;
+              q[gr] = qn;
+              pq = pn * qn;
+              jj = j;
+            }
+          }
+          warp_seg_add<float>(jj, pq, 0.f, s_w[warp]);
+        }
+      }
+      publish();
+      if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+      if (inner > 0 && !voted()) break;  // every inner solve reached its target
+      gather_all();
+      if (threadIdx.x < nloc) {
+        const int j = threadIdx.x;
+        s_alpha[j] = s_act[j] ? s_rr[j] / (float)s_g[j][0] : 0.f;
+      }
+      __syncthreads();
+      // B: y += alpha p, r -= alpha q; partial r.r
+      clear_slots();
+      {
+        int j = 0;
+        for (int64_t base = row0 + warp * 32; base < row1; base += kBatchThreads) {
+          const int64_t gr = base + lane;
+          float rr = 0.f;
+          int jj = -1;
+          if (gr < row1) {
+            while (j + 1 < nloc && gr >= s_off[j + 1]) ++j;
+            if (s_act[j]) {
+              const float al = s_alpha[j];
+              y[gr] += al * p[gr];
+              const float ri = r[gr] - al * q[gr];
+              r[gr] = ri;
+              rr = ri * ri;
+              jj = j;
+            }
+          }
+          warp_seg_add<float>(jj, rr, 0.f, s_w[warp]);
+        }
+      }
+      publish();
+      if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+      gather_all();
+      if (threadIdx.x == 0) s_any = 0;
+      __syncthreads();
+      if (threadIdx.x < nloc) {
+        const int j = threadIdx.x;
+        if (s_act[j]) {
+          const float rn = (float)s_g[j][0];
+          s_it[j] += 1;
+          s_beta[j] = rn / s_rr[j];
+          s_rr[j] = rn;
+          if (rn <= s_eta2[j] || s_it[j] >= sys[slo + j].max_iter) s_act[j] = 0;
+          else atomicOr(&s_any, 1);
+        }
+      }
+      post();
+    }
+    // U: x += ||t|| S y for every system that refined in this cycle
+    {
+      int j = 0;
+      for (int64_t base = row0 + warp * 32; base < row1; base += kBatchThreads) {
+        const int64_t gr = base + lane;
+        if (gr < row1) {
+          while (j + 1 < nloc && gr >= s_off[j + 1]) ++j;
+          if (s_live[j]) {
+            const BSys& S = sys[slo + j];
+            const int64_t i = gr - S.off;
+            S.x[i] += (s_sig[j] * S.sc[i]) * (double)y[gr];
+          }
+        }
+      }
+    }
+    if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+  }
   if (threadIdx.x < nloc) {
     const int j = threadIdx.x;
     const int s = slo + j;
@@ -586,6 +886,7 @@ struct sft_batch_s {
   int nblocks = 0, maxs = 1;
   int32_t *blk_slo = nullptr, *blk_shi = nullptr;
   double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *part = nullptr;
+  bool mixed = true;  // every request asked for cg_mode MIXED (else the FP64 CG for all)
   sft::BSysOut* sysout = nullptr;
   sft::BCgCtl* cgctl = nullptr;
   std::vector<int> sys_first;  // first system of each request
@@ -660,9 +961,18 @@ static sft_status enqueue_batch(sft_batch_s* B, cudaStream_t st) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     ::sft::note_launch();
-    SFT_CUDA(cudaLaunchKernelEx(&cfg, k_batch_pcg, (const BSys*)B->dsys, B->nsys, B->ntot, B->rows_per_block,
-                                (const int32_t*)B->blk_slo, (const int32_t*)B->blk_shi, B->maxs, B->r, B->z, B->p,
-                                B->q, B->part, B->sysout, B->cgctl));
+    if (B->mixed) {
+      // FP32 work vectors packed into the FP64 ones: r | y in r, p | q in p; t in z
+      float* r32 = reinterpret_cast<float*>(B->r);
+      float* p32 = reinterpret_cast<float*>(B->p);
+      SFT_CUDA(cudaLaunchKernelEx(&cfg, k_batch_mixed, (const BSys*)B->dsys, B->nsys, B->ntot, B->rows_per_block,
+                                  (const int32_t*)B->blk_slo, (const int32_t*)B->blk_shi, B->maxs, B->z, r32, p32,
+                                  p32 + B->ntot, r32 + B->ntot, B->part, B->sysout, B->cgctl));
+    } else {
+      SFT_CUDA(cudaLaunchKernelEx(&cfg, k_batch_pcg, (const BSys*)B->dsys, B->nsys, B->ntot, B->rows_per_block,
+                                  (const int32_t*)B->blk_slo, (const int32_t*)B->blk_shi, B->maxs, B->r, B->z, B->p,
+                                  B->q, B->part, B->sysout, B->cgctl));
+    }
   }
   SFT_CUDA(cudaEventRecordWithFlags(B->ev[3], st, cudaEventRecordExternal));
   return SFT_OK;
@@ -857,16 +1167,21 @@ static sft_status build_batch(sft_batch_s* B, const sft_options* opts, int autot
   if (sft_status e = upload(&B->dreq, B->hreq, st)) return e;
   // systems of the batched CG
   B->sys_first.resize(nreq + 1);
+  for (int r = 0; r < nreq; ++r) B->mixed = B->mixed && opts[r].cg_mode == SFT_CG_MIXED;
   int64_t off = 0;
   for (int r = 0; r < nreq; ++r) {
     B->sys_first[r] = (int)B->hsys.size();
     sft_target t = B->tgts[r];
+    if (B->mixed)
+      if (sft_status e = scaled_matrix(t, st)) return e;
     for (int f = 0; f < B->hreq[r].nf; ++f) {
       BSys S;
       S.rp = t->row_ptr;
       S.col = t->col;
       S.val = t->val;
       S.dinv = t->dinv;
+      S.aval = t->val32s;
+      S.sc = t->sc;
       S.b = B->b + B->vec_off[r] + (int64_t)f * t->nv;
       S.x = B->u + B->vec_off[r] + (int64_t)f * t->nv;
       S.off = off;
@@ -883,7 +1198,10 @@ static sft_status build_batch(sft_batch_s* B, const sft_options* opts, int autot
   int dev = 0, sms = 0, per_sm = 0;
   SFT_CUDA(cudaGetDevice(&dev));
   SFT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  SFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_pcg, kBatchThreads, 0));
+  if (B->mixed)
+    SFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_mixed, kBatchThreads, 0));
+  else
+    SFT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_pcg, kBatchThreads, 0));
   if (per_sm < 1) return fail(SFT_ERR_CUDA, "batched CG kernel cannot be resident");
   B->nblocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::min(per_sm, 4) * sms,
                                                            (B->ntot + kBatchThreads - 1) / kBatchThreads));

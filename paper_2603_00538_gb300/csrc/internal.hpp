@@ -149,6 +149,8 @@ struct SolveResult { int iters; double rel_resid; int converged; };
 // cg_mode: SFT_CG_MIXED (FP64 refinement around FP32 CG) or SFT_CG_FP64
 sft_status mass_solve(sft_target_s* t, int nrhs, const double* b, double* x, double tol, int max_iter,
                       cudaStream_t st, int32_t* d_err, SolveResult* res, int cg_mode = SFT_CG_MIXED);
+// S = diag(M)^-1/2 and the FP32 values of S M S on the target (made once, cached)
+sft_status scaled_matrix(sft_target_s* t, cudaStream_t st);
 sft_status weighted_sum(const double* w, const double* u, int64_t n, double* out_host, cudaStream_t st);
 // conversions
 sft_status convert_coords(const void* in, int in_dtype, void* out, int out_prec, int64_t n, cudaStream_t st);

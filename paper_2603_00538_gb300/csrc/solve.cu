@@ -539,7 +539,7 @@ __global__ void k_scaled_values(const int32_t* __restrict__ rp, const int32_t* _
   }
 }
 
-static sft_status scaled_matrix(sft_target_s* t, cudaStream_t st) {
+sft_status scaled_matrix(sft_target_s* t, cudaStream_t st) {
   if (t->val32s) return SFT_OK;
   const int64_t n = t->nv;
   SFT_CUDA(dalloc(&t->sc, (size_t)n, st));

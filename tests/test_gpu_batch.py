@@ -98,3 +98,37 @@ def test_batch_rejects_fp64_requests(batch_setup):
     with pytest.raises(sft.SftError) as ei:
         sft.sft_batch_create(S["srcs"][:2], S["tgts"][:2], opts)
     assert ei.value.status == 8
+
+
+def _spmv(rp, col, val, x):
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    return np.bincount(rows, weights=val * x[col], minlength=len(rp) - 1)
+
+
+@pytest.mark.parametrize("modes", ["mixed", "fp64", "one_fp64"])
+def test_batch_cg_modes(batch_setup, orc, modes):
+    """The batched solve in either CG mode: every (request, field) system's
+    u has the true residual ||b - M u|| <= tol ||b|| (MIXED stops on it; the
+    FP64 CG's recurrence residual may drift from it by rounding, 1e-11), and
+    u equals the single transfer's in the same mode to the solve accuracy.
+    One FP64 request makes the whole batch use the FP64 CG."""
+    S = batch_setup
+    reqs = S["reqs"][:8]
+    mode = {"mixed": [0] * 8, "fp64": [1] * 8, "one_fp64": [0] * 7 + [1]}[modes]
+    opts = [dict(o, cg_tol=1e-12, cg_mode=m) for (_, _, o), m in zip(reqs, mode)]
+    b = sft.sft_batch_create(S["srcs"][:8], S["tgts"][:8], opts, autotune=False)
+    _, st = sft.sft_batch_run(b)
+    assert st["nonconverged"] == 0
+    for r, (dim, tgt, opt) in enumerate(reqs):
+        nf = opt["field_count"]
+        ub, bb = sft.sft_batch_result(b, r, b_out=np.zeros((nf, tgt.nnodes)))
+        rp, col, val = orc.mass_csr(tgt.coords, tgt.conn)
+        for f in range(nf):
+            res = np.linalg.norm(bb[f] - _spmv(rp, col, val, ub[f])) / np.linalg.norm(bb[f])
+            assert res <= (2e-12 if modes == "mixed" else 1e-11), (r, f, res)
+        _, _, us = sft.sft_transfer(S["srcs"][r], S["tgts"][r], opt["samples_per_elem"], sft.SFT_PREC_FP32,
+                                    seed=opt["seed"], stream_id=opt["stream_id"], alpha=opt["alpha"],
+                                    cg_tol=1e-12, cg_max_iter=2000, field_count=nf, cg_mode=mode[r])
+        for f in range(nf):
+            assert _rel(ub[f], us[f]) < 1e-5, (r, f)
+    b.close()
