@@ -113,7 +113,8 @@ typedef struct {
  * uniform-grid point-location structure (Sec. 5.3: nx = ny = int(L sqrt(#elements)),
  * extended to 3D with the cube root) for the precision matching `dtype`
  * (F32 -> FP32 location, F64 -> FP64 location); the other precision is built
- * on first use. Also computes int f^s (exact P1 integral) per field.
+ * on first use. The exact P1 integral int f^s of every field is computed on
+ * the first sft_conservation_error call (and again after new values).
  * Errors: SFT_ERR_ARG (null/size/dim/nfields), SFT_ERR_MESH (index out of
  * range, non-positive element, non-finite coordinate), SFT_ERR_OOM, SFT_ERR_CUDA. */
 sft_status sft_source_create(const sft_mesh_desc* desc, sft_source* out);
@@ -127,8 +128,8 @@ sft_status sft_target_create(const sft_mesh_desc* desc, sft_target* out);
 /* Replace the nodal values of every field of a source (same shape and dtype
  * as at create: [nfields][nnodes]; device pointer if device_ptrs) keeping its
  * mesh and location grid: the per-coupling-step update of a fixed mesh
- * (the paper's online cost, Sec. 5.3). Ordered on cuda_stream; synchronises
- * it to refresh the source integrals. */
+ * (the paper's online cost, Sec. 5.3). Ordered on cuda_stream; does not
+ * synchronise it. */
 sft_status sft_source_set_values(sft_source src, const void* values, int32_t device_ptrs, void* cuda_stream);
 
 void sft_source_destroy(sft_source src);
@@ -150,7 +151,9 @@ sft_status sft_transfer(sft_source src, sft_target tgt, const sft_options* opt,
  * field u [nnodes_target] (FP64; device pointer if u_on_device):
  *   out3[0] = |int f^s - int f^t| / |int f^s|, out3[1] = int f^s (field `field`
  *   of the source, exact P1 integral), out3[2] = int f^t = sum_i m_i u_i.
- * out3 is a host array of 3 doubles. Synchronises `cuda_stream`. */
+ * out3 is a host array of 3 doubles. Synchronises `cuda_stream`. Computes the
+ * source integrals when the values changed since they were last computed, so
+ * it must not run concurrently with other calls on the same source. */
 sft_status sft_conservation_error(sft_source src, sft_target tgt, const double* u,
                                   int32_t u_on_device, int32_t field, void* cuda_stream,
                                   double* out3);

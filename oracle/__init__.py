@@ -62,7 +62,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("samples_per_elem", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("stream", ctypes.c_uint32),
                 ("alpha", ctypes.c_double), ("grid_scale_L", ctypes.c_double),
-                ("cg_tol", ctypes.c_double), ("cg_max_iter", ctypes.c_int)]
+                ("cg_tol", ctypes.c_double), ("cg_max_iter", ctypes.c_int), ("sampling", ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):
@@ -78,6 +78,10 @@ def _declare(L):
     L.orc_u01_f64.restype = ctypes.c_double
     L.orc_sample_element.argtypes = [_int, _int, ctypes.c_uint64, ctypes.c_uint32, _i64,
                                      ctypes.c_int32, _f64p, _f64p, _f64p]
+    L.orc_sample_element_s.argtypes = [_int, _int, ctypes.c_uint64, ctypes.c_uint32, _i64,
+                                       ctypes.c_int32, _int, _f64p, _f64p, _f64p]
+    L.orc_strata_per_axis.argtypes = [_int, ctypes.c_int32]
+    L.orc_strata_per_axis.restype = _int
     L.orc_grid_build.argtypes = [_int, _int, _i64, _f64p, _i64, _i32p, ctypes.c_double]
     L.orc_grid_build.restype = _vp
     L.orc_grid_free.argtypes = [_vp]
@@ -132,11 +136,17 @@ def u01(x: int, prec: int) -> float:
     return float(lib().orc_u01_f32(x) if prec == 1 else lib().orc_u01_f64(x))
 
 
-def sample_element(prec, dim, seed, stream, t, nsamp, node_xyz):
+def sample_element(prec, dim, seed, stream, t, nsamp, node_xyz, sampling=0):
+    """Barycentric weights [nsamp, dim+1] and points [nsamp, dim] of the samples
+    of target element t (sampling 0 uniform, 1 stratified)."""
     lam = np.zeros((nsamp, dim + 1))
     X = np.zeros((nsamp, dim))
-    lib().orc_sample_element(prec, dim, seed, stream, t, nsamp, _f64(node_xyz), lam, X)
+    lib().orc_sample_element_s(prec, dim, seed, stream, t, nsamp, sampling, _f64(node_xyz), lam, X)
     return lam, X
+
+
+def strata_per_axis(dim, nsamp) -> int:
+    return int(lib().orc_strata_per_axis(dim, nsamp))
 
 
 class Grid:
@@ -229,13 +239,13 @@ def pcg(rp, col, val, b, tol=1e-12, max_iter=1000):
 
 
 def transfer(src, tgt, prec, samples_per_elem, seed=0, stream=0, alpha=1.0, grid_scale_L=1.0,
-             cg_tol=1e-12, cg_max_iter=1000, want_sample_elem=False):
+             cg_tol=1e-12, cg_max_iter=1000, want_sample_elem=False, sampling=0):
     """Steps 1-7 of Sec. 4 on the CPU; returns a dict of FP64 arrays."""
     sc, sconn, sv = _f64(src.coords), _i32(src.conn), _f64(src.values)
     tc, tconn = _f64(tgt.coords), _i32(tgt.conn)
     dim, nf = sc.shape[1], sv.shape[0]
     nvt, net = tc.shape[0], tconn.shape[0]
-    p = _Params(prec, samples_per_elem, seed, stream, alpha, grid_scale_L, cg_tol, cg_max_iter)
+    p = _Params(prec, samples_per_elem, seed, stream, alpha, grid_scale_L, cg_tol, cg_max_iter, sampling)
     st = _Stats()
     out = {k: np.zeros((nf, nvt)) for k in ("g", "b_g", "b_res", "b", "u")}
     se = np.zeros((net, samples_per_elem), np.int32) if want_sample_elem else None

@@ -37,6 +37,15 @@ double orc_u01_f64(uint32_t x);
  * lam_out [N][k] (barycentric weights), X_out [N][d]. */
 void orc_sample_element(int prec, int dim, uint64_t seed, uint32_t stream, int64_t t,
                         int32_t nsamp, const double* node_xyz, double* lam_out, double* X_out);
+/* The same with a sampling scheme: 0 uniform (as above), 1 stratified (the
+ * uniforms of sample j < m^d, m = largest integer with m^d <= nsamp, are
+ * confined to cell j of an m^d grid on the unit square / cube before the map;
+ * see rng_sample.c). */
+void orc_sample_element_s(int prec, int dim, uint64_t seed, uint32_t stream, int64_t t,
+                          int32_t nsamp, int sampling, const double* node_xyz, double* lam_out,
+                          double* X_out);
+/* strata per axis for nsamp samples in dimension dim: largest m with m^dim <= nsamp */
+int orc_strata_per_axis(int dim, int32_t nsamp);
 
 /* ---- point location in a uniform-grid-bucketed source mesh ---- */
 typedef struct orc_grid orc_grid;
@@ -83,6 +92,7 @@ typedef struct {
     double grid_scale_L;
     double cg_tol;
     int cg_max_iter;
+    int sampling;         /* 0 uniform, 1 stratified (orc_sample_element_s) */
 } orc_params;
 
 typedef struct {

@@ -17,6 +17,17 @@
  *     take the spacings (v1, v2 - v1, v3 - v2, 1 - v3), which are uniformly
  *     distributed on the simplex (order statistics of uniforms);
  *   - X = sum_m lambda_m x_m, added left to right, one rounding per operation.
+ *
+ * Stratified sampling (an instance of the general density p_t of Eq.
+ * mc_element_integral_operator_general with equal-measure strata; the paper
+ * names better sampling schemes as future work): with m the largest integer
+ * such that m^d <= N, sample j < m^d replaces each uniform U_a by
+ * u_a = (c_a + U_a) / m, where c_a is digit a of j in base m (least
+ * significant first), computed in the path's precision with one rounding per
+ * operation. Both maps push the uniform measure of the unit square / cube to
+ * the uniform measure of the simplex, so the m^d grid cells map to regions of
+ * equal measure |T| / m^d and every sample keeps the weight |T| / N: the
+ * estimator stays unbiased. Samples j >= m^d keep their plain uniforms.
  */
 #include "oracle.h"
 #include <math.h>
@@ -68,23 +79,61 @@ static void draw_words(uint64_t seed, uint32_t c0, int64_t t, uint32_t stream, u
     orc_philox4x32_10(ctr, key, w);
 }
 
+int orc_strata_per_axis(int dim, int32_t nsamp)
+{
+    int m = 1;
+    for (;;) {
+        int64_t p = 1;
+        for (int a = 0; a < dim; ++a) p *= (int64_t)(m + 1);
+        if (p > nsamp) return m;
+        ++m;
+    }
+}
+
+/* cell coordinate of sample j along axis a (base-m digit a of j) */
+static int stratum_digit(int32_t j, int m, int a)
+{
+    int32_t q = j;
+    for (int i = 0; i < a; ++i) q /= m;
+    return (int)(q % m);
+}
+
 void orc_sample_element(int prec, int dim, uint64_t seed, uint32_t stream, int64_t t,
                         int32_t nsamp, const double* node_xyz, double* lam_out, double* X_out)
 {
+    orc_sample_element_s(prec, dim, seed, stream, t, nsamp, 0, node_xyz, lam_out, X_out);
+}
+
+void orc_sample_element_s(int prec, int dim, uint64_t seed, uint32_t stream, int64_t t,
+                          int32_t nsamp, int sampling, const double* node_xyz, double* lam_out,
+                          double* X_out)
+{
     const int k = dim + 1;
+    const int m = sampling == 1 ? orc_strata_per_axis(dim, nsamp) : 1;
+    int32_t nstrata = 1;
+    for (int a = 0; a < dim; ++a) nstrata *= m;
     for (int32_t j = 0; j < nsamp; ++j) {
         uint32_t w[4];
         double lam[4];
+        const int strat = sampling == 1 && m > 1 && j < nstrata;
         if (dim == 2) {
             draw_words(seed, (uint32_t)(j >> 1), t, stream, w);
             const uint32_t wx = w[2 * (j & 1)], wy = w[2 * (j & 1) + 1];
             if (prec == 1) {
-                const float xi = orc_u01_f32(wx), eta = orc_u01_f32(wy);
+                float xi = orc_u01_f32(wx), eta = orc_u01_f32(wy);
+                if (strat) {
+                    xi = ((float)stratum_digit(j, m, 0) + xi) / (float)m;
+                    eta = ((float)stratum_digit(j, m, 1) + eta) / (float)m;
+                }
                 const float s = sqrtf(xi);
                 const float l0 = 1.0f - s, l1 = s * (1.0f - eta), l2 = s * eta;
                 lam[0] = l0; lam[1] = l1; lam[2] = l2;
             } else {
-                const double xi = orc_u01_f64(wx), eta = orc_u01_f64(wy);
+                double xi = orc_u01_f64(wx), eta = orc_u01_f64(wy);
+                if (strat) {
+                    xi = ((double)stratum_digit(j, m, 0) + xi) / (double)m;
+                    eta = ((double)stratum_digit(j, m, 1) + eta) / (double)m;
+                }
                 const double s = sqrt(xi);
                 lam[0] = 1.0 - s; lam[1] = s * (1.0 - eta); lam[2] = s * eta;
             }
@@ -92,6 +141,8 @@ void orc_sample_element(int prec, int dim, uint64_t seed, uint32_t stream, int64
             draw_words(seed, (uint32_t)j, t, stream, w);
             if (prec == 1) {
                 float v[3] = {orc_u01_f32(w[0]), orc_u01_f32(w[1]), orc_u01_f32(w[2])};
+                if (strat)
+                    for (int a = 0; a < 3; ++a) v[a] = ((float)stratum_digit(j, m, a) + v[a]) / (float)m;
                 /* three-comparator sorting network (0,1), (1,2), (0,1) */
                 if (v[1] < v[0]) { float s = v[0]; v[0] = v[1]; v[1] = s; }
                 if (v[2] < v[1]) { float s = v[1]; v[1] = v[2]; v[2] = s; }
@@ -99,6 +150,8 @@ void orc_sample_element(int prec, int dim, uint64_t seed, uint32_t stream, int64
                 lam[0] = v[0]; lam[1] = v[1] - v[0]; lam[2] = v[2] - v[1]; lam[3] = 1.0f - v[2];
             } else {
                 double v[3] = {orc_u01_f64(w[0]), orc_u01_f64(w[1]), orc_u01_f64(w[2])};
+                if (strat)
+                    for (int a = 0; a < 3; ++a) v[a] = ((double)stratum_digit(j, m, a) + v[a]) / (double)m;
                 if (v[1] < v[0]) { double s = v[0]; v[0] = v[1]; v[1] = s; }
                 if (v[2] < v[1]) { double s = v[1]; v[1] = v[2]; v[2] = s; }
                 if (v[1] < v[0]) { double s = v[0]; v[0] = v[1]; v[1] = s; }

@@ -252,7 +252,7 @@ void orc_transfer(int dim, const orc_params* p,
         }
     }
 
-    /* Steps 3-5: per target element, N uniform samples; locate each sample in
+    /* Steps 3-5: per target element, N samples (uniform or stratified); locate each sample in
      * the source, evaluate f^s and g there, and accumulate the residual
      * estimate |T|/N sum_j (f^s - alpha g)(X_j) psi_i(X_j) */
     double* lam = (double*)malloc(sizeof(double) * (size_t)(N * k));
@@ -264,7 +264,7 @@ void orc_transfer(int dim, const orc_params* p,
         double xyz[12];
         for (int m = 0; m < k; ++m)
             for (int a = 0; a < dim; ++a) xyz[m * dim + a] = tcoord[(int64_t)v[m] * dim + a];
-        orc_sample_element(p->prec, dim, p->seed, p->stream, t, N, xyz, lam, X);
+        orc_sample_element_s(p->prec, dim, p->seed, p->stream, t, N, p->sampling, xyz, lam, X);
         for (int i = 0; i < nf * k; ++i) acc[i] = 0.0;
         for (int j = 0; j < N; ++j) {
             int32_t e, st;

@@ -163,7 +163,6 @@ sft_status sft_source_create(const sft_mesh_desc* d, sft_source* out) {
     if (e != cudaSuccess) { r = cuda_fail(e, "memset"); break; }
     const int prec = d->dtype == SFT_F64 ? SFT_PREC_FP64 : SFT_PREC_FP32;
     if ((r = build_locator(s, prec, st, d_err))) break;
-    if ((r = source_integrals(s, st))) break;
   } while (0);
   if (d_err) cudaFreeAsync(d_err, st);
   if (r != SFT_OK) {
@@ -180,8 +179,8 @@ sft_status sft_source_set_values(sft_source s, const void* values, int32_t devic
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const size_t esz = s->dtype == SFT_F64 ? 8 : 4;
   SFT_CUDA(cudaMemcpyAsync(s->values, values, esz * s->nv * s->nf, cudaMemcpyDefault, st));
-  if (sft_status r = refresh_value_copies(s, st)) return r;
-  return source_integrals(s, st);
+  s->integral_valid = false;
+  return refresh_value_copies(s, st);
 }
 
 sft_status sft_target_create(const sft_mesh_desc* d, sft_target* out) {
@@ -351,6 +350,10 @@ sft_status sft_conservation_error(sft_source s, sft_target t, const double* u, i
   }
   double it = 0.0;
   if (sft_status r = weighted_sum(t->lumped, ud, t->nv, &it, st)) return r;
+  if (!s->integral_valid) {
+    if (sft_status r = source_integrals(s, st)) return r;
+    s->integral_valid = true;
+  }
   const double is = s->integral[field];
   out3[0] = std::fabs(is - it) / std::fabs(is);
   out3[1] = is;

@@ -90,6 +90,7 @@ struct sft_source_s {
   int32_t* conn = nullptr;      // [ne][dim+1]
   void* values = nullptr;       // [nf][nv] input dtype
   double integral[sft::kMaxFields] = {0};
+  bool integral_valid = false;  // integral[] matches the current values (made on first use)
   sft::Locator loc[2];          // index = sft_precision (0 FP64, 1 FP32)
 };
 

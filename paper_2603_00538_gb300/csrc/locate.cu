@@ -691,7 +691,7 @@ __global__ void k_p1_integral_partial(const TI* __restrict__ x, const int32_t* _
 }
 
 sft_status source_integrals(sft_source_s* s, cudaStream_t st) {
-  const unsigned nb = 256;
+  const unsigned nb = 152 * 8;
   double* part = nullptr;
   SFT_CUDA(dalloc(&part, (size_t)nb * kMaxFields, st));
   if (s->dim == 2) {

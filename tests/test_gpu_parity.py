@@ -297,6 +297,9 @@ def test_set_values_equals_recreate(orc):
     s = sft.mesh_source(src, device=DEV)
     t = sft.mesh_target(tgt, device=DEV)
     new = W.as_precision(W.with_values(src, [W.paper_f3], np.float64), np.float32)
+    # the source integral of the old values is computed (and cached) first
+    _, i_old, _ = sft.sft_conservation_error(s, t, np.ones(tgt.nnodes))
+    assert i_old == pytest.approx(orc.integral_p1(src.coords, src.conn, src.values[0]), rel=1e-6)
     sft.sft_source_set_values(s, torch.as_tensor(new.values).to(DEV))
     _, _, u1 = sft.sft_transfer(s, t, 16, FP32, cg_tol=1e-12)
     s2 = sft.mesh_source(new, device=DEV)
@@ -305,3 +308,4 @@ def test_set_values_equals_recreate(orc):
     e1 = sft.sft_conservation_error(s, t, u1[0])
     e2 = sft.sft_conservation_error(s2, t, u2[0])
     assert e1 == e2
+    assert e1[1] == pytest.approx(orc.integral_p1(new.coords, new.conn, new.values[0]), rel=1e-6)
