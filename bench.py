@@ -203,7 +203,7 @@ def run_ours(args):
     def step():
         s = sft.sft_source_create(sc, sk, sv, args.grid_scale)
         t = sft.sft_target_create(tc, tk)
-        _, st, _ = sft.sft_transfer(s, t, N, prec, seed=0, cg_tol=tol, u_out=u)
+        _, st, _ = sft.sft_transfer(s, t, N, prec, seed=0, cg_tol=tol, u_out=u, sampling=_sampling(args))
         cons_last[0] = sft.sft_conservation_error(s, t, u[0])
         stats_last.update(st)
         s.close()
@@ -258,7 +258,7 @@ def run_ours(args):
             "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}"
                                    + ("" if args.scale == 1.0 else f" (element counts x{args.scale})"),
                        "queries_per_step": queries, "target_elements": tgt.nelems, "samples_per_elem": N,
-                       "source_elements": src.nelems, "grid_scale_L": args.grid_scale,
+                       "source_elements": src.nelems, "grid_scale_L": args.grid_scale, "sampling": args.sampling,
                        "l2": "flushed between steps (256 MB write)",
                        "accumulation": "FP64 load vector, CG and reductions",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -443,7 +443,8 @@ def run_online(args):
             torch.as_tensor(np.ascontiguousarray(src.values * np.float32(0.5) + np.float32(0.25))).to(dev)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    plan = sft.sft_plan_create(S, T, N, sft.SFT_PREC_FP32, seed=0, cg_tol=tol, out_device=True)
+    plan = sft.sft_plan_create(S, T, N, sft.SFT_PREC_FP32, seed=0, cg_tol=tol, out_device=True,
+                               sampling=_sampling(args))
     torch.cuda.synchronize()
     plan_s = time.perf_counter() - t0
     u = torch.zeros((src.nfields, tgt.nnodes), dtype=torch.float64, device=dev)
@@ -484,7 +485,8 @@ def run_online(args):
     # end to end: new values from pinned host memory, u back to pinned memory
     pin_vals = torch.as_tensor(np.ascontiguousarray(src.values)).pin_memory()
     u_h = torch.zeros((src.nfields, tgt.nnodes), dtype=torch.float64).pin_memory()
-    plan_h = sft.sft_plan_create(S, T, N, sft.SFT_PREC_FP32, seed=0, cg_tol=tol, out_device=False)
+    plan_h = sft.sft_plan_create(S, T, N, sft.SFT_PREC_FP32, seed=0, cg_tol=tol, out_device=False,
+                                 sampling=_sampling(args))
 
     def e2e_step():
         sft.sft_source_set_values(S, pin_vals)
@@ -756,7 +758,7 @@ def run_e2e(args, src, tgt, N, tol, prec):
     def step():
         s = sft.sft_source_create(sc, sk, sv, args.grid_scale)
         t = sft.sft_target_create(tc, tk)
-        _, st, _ = sft.sft_transfer(s, t, N, prec, seed=0, cg_tol=tol, u_out=u)
+        _, st, _ = sft.sft_transfer(s, t, N, prec, seed=0, cg_tol=tol, u_out=u, sampling=_sampling(args))
         e = sft.sft_conservation_error(s, t, u[0])
         s.close()
         t.close()
@@ -816,17 +818,23 @@ def _sample_target(tgt, frac):
     return W.Mesh(tgt.coords[used], remap[conn].astype(np.int32))
 
 
-def oracle_step(src, tgt_s, p):
+def oracle_step(src, tgt_s, p, sampling=0):
     import oracle
     t0 = time.perf_counter()
-    r = oracle.transfer(src, tgt_s, 1, p["samples_per_elem"], seed=0, cg_tol=p["cg_tol"], cg_max_iter=1000)
+    r = oracle.transfer(src, tgt_s, 1, p["samples_per_elem"], seed=0, cg_tol=p["cg_tol"], cg_max_iter=1000,
+                        sampling=sampling)
     dt = time.perf_counter() - t0
     return (tgt_s.nelems * p["samples_per_elem"] + tgt_s.nnodes) / dt, dt, r
 
 
+def _sampling(args) -> int:
+    """sft_sampling value of --sampling (1 stratified, 0 uniform)."""
+    return 1 if getattr(args, "sampling", "uniform") == "stratified" else 0
+
+
 def cpu_baseline(args, src, tgt, p, frac):
     tgt_s = _sample_target(tgt, frac)
-    v, dt, _ = oracle_step(src, tgt_s, p)
+    v, dt, _ = oracle_step(src, tgt_s, p, _sampling(args))
     return {"value": v, "unit": "queries/s", "cores": 1, "kind": "oracle",
             "seconds": dt,
             "sample": f"full source mesh (grid build included) and the first {tgt_s.nelems} target "
@@ -870,7 +878,7 @@ def run_reference(args):
         tgt_s = _sample_target(tgt, args.cpu_frac)
 
         def one():
-            return oracle_step(src, tgt_s, p)[1]
+            return oracle_step(src, tgt_s, p, _sampling(args))[1]
         q = tgt_s.nelems * p["samples_per_elem"] + tgt_s.nnodes
         sample = (f"full source mesh and the first {tgt_s.nelems} target elements (Morton order, "
                   f"{args.cpu_frac:.3g} of the workload) per step")
@@ -905,6 +913,8 @@ def main():
     ap.add_argument("--sur-epochs", type=int, default=40, help="training epochs of the surrogate (sur3d)")
     ap.add_argument("--grid-scale", type=float, default=1.0,
                     help="source grid cells per axis = int(L * nelems^(1/d)) (tri4m / tet5m)")
+    ap.add_argument("--sampling", choices=["uniform", "stratified"], default="uniform",
+                    help="sample scheme of the mesh-source workloads (tri4m, tet5m and their online forms)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="element-count scale of the workload (1 = the named workload)")
     args = ap.parse_args()

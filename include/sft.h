@@ -58,6 +58,16 @@ typedef enum { SFT_PREC_FP64 = 0, SFT_PREC_FP32 = 1 } sft_precision;
  * FP64: Jacobi-preconditioned CG in FP64 throughout. */
 typedef enum { SFT_CG_MIXED = 0, SFT_CG_FP64 = 1 } sft_cg_mode;
 
+/* Where the N samples of a target element are drawn (Sec. 4 step 3). UNIFORM:
+ * N independent uniform points (the paper's scheme). STRATIFIED: the element
+ * is cut into m^d equal-measure strata, m the largest integer with
+ * m^d <= N (the images of the cells of an m^d grid on the unit square / cube
+ * under the uniform-to-simplex map), one uniform point in each, plus N - m^d
+ * uniform points; every sample keeps the weight |T| / N, so the estimator
+ * stays unbiased (Eq. mc_element_integral_operator_general) and its error
+ * falls like N^-1 instead of N^-1/2 for a Lipschitz residual in 2D. */
+typedef enum { SFT_SAMPLING_UNIFORM = 0, SFT_SAMPLING_STRATIFIED = 1 } sft_sampling;
+
 /* element type of coordinate / value arrays */
 typedef enum { SFT_F32 = 0, SFT_F64 = 1 } sft_dtype;
 
@@ -92,6 +102,8 @@ typedef struct {
     int32_t* sample_elem_out;   /* optional [nelems][N]: source element located for every sample */
     int32_t field_count;        /* 0: every source field; k > 0: the first k fields only */
     int32_t cg_mode;            /* sft_cg_mode (0: mixed-precision refinement) */
+    int32_t sampling;           /* sft_sampling (0: uniform) */
+    int32_t reserved;           /* must be 0 */
 } sft_options;
 
 typedef struct {

@@ -54,9 +54,10 @@ def surrogate_dataset(coords, conn, values, n, seed=0, stream_id=0, box_lo=(0, 0
 
 
 def surrogate_transfer(params, tgt_coords, tgt_conn, N, seed=0, stream=0, alpha=1.0, exact=None, tau=0.0, s=4,
-                       cg_tol=1e-12, cg_max_iter=2000):
+                       cg_tol=1e-12, cg_max_iter=2000, sampling=0):
     """params: the network the GPU computes with (FP64 vector) or None (every
-    query exact); exact: (coords, conn, values of one field) or None.
+    query exact); exact: (coords, conn, values of one field) or None;
+    sampling: 0 uniform, 1 stratified (as the mesh-source transfer).
     Returns a dict: g, b, u, fallback [E] bool, margin [E], f [E, N]."""
     tc = np.asarray(tgt_coords, np.float64)
     tconn = np.asarray(tgt_conn, np.int32)
@@ -79,7 +80,7 @@ def surrogate_transfer(params, tgt_coords, tgt_conn, N, seed=0, stream=0, alpha=
     lam = np.zeros((E, N, K))
     X = np.zeros((E, N, d))
     for t in range(E):
-        lam[t], X[t] = sample_element(1, d, seed, stream, t, N, tc[tconn[t]])
+        lam[t], X[t] = sample_element(1, d, seed, stream, t, N, tc[tconn[t]], sampling=sampling)
     Xf = X.reshape(-1, d)
     # step 4: the query
     fallback = np.zeros(E, bool)

@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libsft.so")
  SFT_ERR_DEVICE_STATUS, SFT_ERR_UNSUPPORTED) = range(9)
 SFT_PREC_FP64, SFT_PREC_FP32 = 0, 1
 SFT_CG_MIXED, SFT_CG_FP64 = 0, 1
+SFT_SAMPLING_UNIFORM, SFT_SAMPLING_STRATIFIED = 0, 1
 SFT_F32, SFT_F64 = 0, 1
 
 
@@ -48,7 +49,7 @@ class sft_options(ctypes.Structure):
                 ("alpha", ctypes.c_double), ("cg_tol", ctypes.c_double), ("strict_inside", ctypes.c_int32),
                 ("out_device", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
                 ("sample_elem_out", ctypes.c_void_p), ("field_count", ctypes.c_int32),
-                ("cg_mode", ctypes.c_int32)]
+                ("cg_mode", ctypes.c_int32), ("sampling", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class sft_stats(ctypes.Structure):
@@ -280,7 +281,7 @@ def sft_transfer(src: Source, tgt: Target, samples_per_elem: int, precision: int
                  seed: int = 0, stream_id: int = 0, alpha: float = 1.0, cg_tol: float = 1e-10,
                  cg_max_iter: int = 1000, strict_inside: bool = False, u_out=None, b_out=None, g_out=None,
                  sample_elem_out=None, stream=None, allow_not_converged: bool = False, field_count: int = 0,
-                 cg_mode: int = SFT_CG_MIXED):
+                 cg_mode: int = SFT_CG_MIXED, sampling: int = SFT_SAMPLING_UNIFORM):
     """Run one transfer. Outputs are caller-provided arrays (numpy for host,
     torch CUDA tensors for device); when u_out is None a host array
     [nfields, nnodes] is allocated. Returns (status, stats dict, u_out)."""
@@ -308,6 +309,7 @@ def sft_transfer(src: Source, tgt: Target, samples_per_elem: int, precision: int
     o.sample_elem_out = sp
     o.field_count = int(field_count)
     o.cg_mode = int(cg_mode)
+    o.sampling = int(sampling)
     st = sft_stats()
     allow = (SFT_OK, SFT_ERR_NOT_CONVERGED) if allow_not_converged else (SFT_OK,)
     status = _check(lib().sft_transfer(src.h, tgt.h, ctypes.byref(o), up, bp, gp, ctypes.byref(st)),
@@ -322,11 +324,12 @@ class Plan(_Handle):
 def sft_plan_create(src: Source, tgt: Target, samples_per_elem: int, precision: int = SFT_PREC_FP32, seed: int = 0,
                     stream_id: int = 0, alpha: float = 1.0, cg_tol: float = 1e-10, cg_max_iter: int = 1000,
                     field_count: int = 0, out_device: bool = False, strict_inside: bool = False,
-                    stream=None, cg_mode: int = SFT_CG_MIXED) -> Plan:
+                    stream=None, cg_mode: int = SFT_CG_MIXED, sampling: int = SFT_SAMPLING_UNIFORM) -> Plan:
     """Initialization of a transfer between fixed meshes (node and sample
     locations recorded); outputs of later transfers go to host arrays, or to
     CUDA tensors with out_device=True."""
-    o = _options(samples_per_elem, seed, stream_id, alpha, cg_tol, cg_max_iter, field_count, precision, cg_mode)
+    o = _options(samples_per_elem, seed, stream_id, alpha, cg_tol, cg_max_iter, field_count, precision, cg_mode,
+                 sampling)
     o.out_device = int(bool(out_device))
     o.strict_inside = int(bool(strict_inside))
     o.cuda_stream = stream if stream is not None else _current_stream()
@@ -417,7 +420,7 @@ class Batch(_Handle):
 
 
 def _options(samples_per_elem, seed=0, stream_id=0, alpha=1.0, cg_tol=1e-10, cg_max_iter=1000,
-             field_count=0, precision=SFT_PREC_FP32, cg_mode=SFT_CG_MIXED):
+             field_count=0, precision=SFT_PREC_FP32, cg_mode=SFT_CG_MIXED, sampling=SFT_SAMPLING_UNIFORM):
     o = sft_options()
     o.samples_per_elem = int(samples_per_elem)
     o.precision = int(precision)
@@ -428,6 +431,7 @@ def _options(samples_per_elem, seed=0, stream_id=0, alpha=1.0, cg_tol=1e-10, cg_
     o.cg_tol = float(cg_tol)
     o.field_count = int(field_count)
     o.cg_mode = int(cg_mode)
+    o.sampling = int(sampling)
     return o
 
 
@@ -560,7 +564,8 @@ def sft_transfer_surrogate(net, exact, tgt: Target, samples_per_elem: int, seed:
                            alpha: float = 1.0, cg_tol: float = 1e-10, cg_max_iter: int = 1000, subsample: int = 4,
                            tau: float = 0.0, exact_field: int = 0, u_out=None, b_out=None, g_out=None,
                            fallback_out=None, sample_f_out=None, strict_inside: bool = False, stream=None,
-                           allow_not_converged: bool = False, cg_mode: int = SFT_CG_MIXED):
+                           allow_not_converged: bool = False, cg_mode: int = SFT_CG_MIXED,
+                           sampling: int = SFT_SAMPLING_UNIFORM):
     """Transfer with the surrogate network `net` (Mlp or None) backed by the
     exact source `exact` (Source or None). Outputs as sft_transfer (numpy for
     host, CUDA tensors for device). Returns (status, stats dict, u_out)."""
@@ -571,7 +576,7 @@ def sft_transfer_surrogate(net, exact, tgt: Target, samples_per_elem: int, seed:
     for p, dv, _ in ptrs:
         if p is not None and dv != udev:
             raise ValueError("all outputs must be host arrays or all device tensors")
-    o = _options(samples_per_elem, seed, stream_id, alpha, cg_tol, cg_max_iter, cg_mode=cg_mode)
+    o = _options(samples_per_elem, seed, stream_id, alpha, cg_tol, cg_max_iter, cg_mode=cg_mode, sampling=sampling)
     o.strict_inside = int(bool(strict_inside))
     o.out_device = int(udev)
     o.cuda_stream = stream if stream is not None else _current_stream()

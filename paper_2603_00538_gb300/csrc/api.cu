@@ -229,6 +229,10 @@ sft_status sft_transfer(sft_source s, sft_target t, const sft_options* o, double
   if (o->precision != SFT_PREC_FP32 && o->precision != SFT_PREC_FP64) return fail(SFT_ERR_ARG, "bad precision");
   if (o->cg_max_iter < 0 || !(o->cg_tol >= 0) || !std::isfinite(o->alpha)) return fail(SFT_ERR_ARG, "bad solver options");
   if (o->cg_mode != SFT_CG_MIXED && o->cg_mode != SFT_CG_FP64) return fail(SFT_ERR_ARG, "unknown cg_mode");
+  if (o->sampling != SFT_SAMPLING_UNIFORM && o->sampling != SFT_SAMPLING_STRATIFIED)
+    return fail(SFT_ERR_ARG, "unknown sampling scheme");
+  if (o->sampling == SFT_SAMPLING_STRATIFIED && o->samples_per_elem > kMaxStratifiedN)
+    return fail(SFT_ERR_UNSUPPORTED, "stratified sampling supports at most 2^20 samples per element");
   if (o->field_count < 0 || o->field_count > s->nf) return fail(SFT_ERR_ARG, "field_count out of range");
   cudaStream_t st = (cudaStream_t)o->cuda_stream;
   const int prec = o->precision;
@@ -281,6 +285,7 @@ sft_status sft_transfer(sft_source s, sft_target t, const sft_options* o, double
   a.b = b.p;
   a.sample_elem = se;
   a.counters = counters.p;
+  a.sampling = o->sampling;
   if (sft_status r = launch_assembly(s, t, a, st)) return r;
   if (ev.ok) cudaEventRecord(ev.e[3], st);
 

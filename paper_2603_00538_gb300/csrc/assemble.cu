@@ -29,6 +29,7 @@ struct AsmParams {
   double alpha;
   double c_det;   // alpha / ((d+1)(d+2)): exact P1 mass factor of the control term
   double inv_n;   // 1 / N
+  Strat st;       // sampling scheme (st.n = 0: uniform)
 };
 
 // MODE: kAsmPlain; kAsmDebug also writes the source element of every sample
@@ -98,12 +99,7 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) k_assemble(const P* __res
         const int j = SPU * u + s;
         if (j >= p.N) break;
         P lam[K];
-        if constexpr (D == 2) {
-          if (s == 0) osada_weights<P>(w.x, w.y, lam);
-          else osada_weights<P>(w.z, w.w, lam);
-        } else {
-          spacing_weights<P>(w.x, w.y, w.z, lam);
-        }
+        sample_lambda<D, P>(w, j, p.st, lam);
         P mu[K];
         int status = 0;
         int32_t e;
@@ -231,6 +227,7 @@ sft_status launch_assembly(sft_source_s* s, sft_target_s* t, const AssembleArgs&
   p.alpha = a.alpha;
   p.c_det = a.alpha / (double)((t->dim + 1) * (t->dim + 2));
   p.inv_n = 1.0 / (double)a.N;
+  p.st = strat_for(t->dim, a.N, a.sampling);
   if (t->dim == 2) {
     if (a.prec == SFT_PREC_FP32) launch_nf<2, float>(s, t, a, p, st);
     else launch_nf<2, double>(s, t, a, p, st);

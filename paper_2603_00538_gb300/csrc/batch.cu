@@ -45,6 +45,7 @@ struct BReq {
   PhiloxKey key;
   uint32_t stream_id;
   float alpha, c_det, inv_n;
+  Strat st;   // sampling scheme
   float* g;   // [nf][nv]
   double* b;  // [nf][nv]
 };
@@ -181,12 +182,7 @@ __global__ void __launch_bounds__(kBatchThreads, NF <= 2 ? 4 : (NF <= 4 ? 3 : 2)
           const int j = SPU * u + s;
           if (j >= N) break;
           float lam[K];
-          if constexpr (D == 2) {
-            if (s == 0) osada_weights<float>(w.x, w.y, lam);
-            else osada_weights<float>(w.z, w.w, lam);
-          } else {
-            spacing_weights<float>(w.x, w.y, w.z, lam);
-          }
+          sample_lambda<D, float>(w, j, R.st, lam);
           float X[D];
           map_point<D, float>(lam, xv, X);
           float mu[K];
@@ -1137,6 +1133,7 @@ static sft_status build_batch(sft_batch_s* B, const sft_options* opts, int autot
     R.alpha = (float)o.alpha;
     R.c_det = (float)(o.alpha / (double)((t->dim + 1) * (t->dim + 2)));
     R.inv_n = (float)(1.0 / (double)R.N);
+    R.st = strat_for(t->dim, R.N, opts[r].sampling);
     R.g = B->g + B->vec_off[r];
     R.b = B->b + B->vec_off[r];
     B->queries += t->nv + t->ne * (int64_t)R.N;
@@ -1311,6 +1308,10 @@ sft_status sft_batch_create(int32_t nreq, const sft_source* srcs, const sft_targ
     if (o.samples_per_elem < 1 || o.cg_max_iter < 0 || !(o.cg_tol >= 0) || !std::isfinite(o.alpha))
       return fail(SFT_ERR_ARG, "bad request options");
     if (o.cg_mode != SFT_CG_MIXED && o.cg_mode != SFT_CG_FP64) return fail(SFT_ERR_ARG, "unknown cg_mode");
+    if (o.sampling != SFT_SAMPLING_UNIFORM && o.sampling != SFT_SAMPLING_STRATIFIED)
+      return fail(SFT_ERR_ARG, "unknown sampling scheme");
+    if (o.sampling == SFT_SAMPLING_STRATIFIED && o.samples_per_elem > kMaxStratifiedN)
+      return fail(SFT_ERR_UNSUPPORTED, "stratified sampling supports at most 2^20 samples per element");
     if (o.field_count < 0 || o.field_count > srcs[r]->nf) return fail(SFT_ERR_ARG, "field_count out of range");
   }
   auto* B = new sft_batch_s();

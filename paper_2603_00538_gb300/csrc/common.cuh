@@ -59,6 +59,7 @@ template <> struct Ar<float> {
   static __device__ __forceinline__ float u01(uint32_t x) { return u01f(x); }
   static __device__ __forceinline__ float from_d(double x) { return __double2float_rn(x); }
   static __device__ __forceinline__ float floor(float x) { return floorf(x); }
+  static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
 };
 template <> struct Ar<double> {
   static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
@@ -69,6 +70,7 @@ template <> struct Ar<double> {
   static __device__ __forceinline__ double u01(uint32_t x) { return u01d(x); }
   static __device__ __forceinline__ double from_d(double x) { return x; }
   static __device__ __forceinline__ double floor(double x) { return ::floor(x); }
+  static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
 };
 
 // ---------------------------------------------------------------------------
@@ -79,27 +81,94 @@ template <> struct Ar<double> {
 // (q, t, stream, 0), sample j uses words 2(j%2), 2(j%2)+1; 3D one call per
 // sample, counter (j, t, stream, 0), words 0..2.
 // ---------------------------------------------------------------------------
-template <typename P>
-__device__ __forceinline__ void osada_weights(uint32_t wx, uint32_t wy, P lam[3]) {
-  using A = Ar<P>;
-  const P xi = A::u01(wx), eta = A::u01(wy);
-  const P s = A::sqrt(xi);
-  lam[0] = A::sub(P(1), s);
-  lam[1] = A::mul(s, A::sub(P(1), eta));
-  lam[2] = A::mul(s, eta);
+// Sampling scheme. Uniform: the maps above. Stratified (the general density
+// p_t of Eq. mc_element_integral_operator_general with equal-measure strata):
+// with m the largest integer such that m^D <= N, sample j < m^D replaces
+// each uniform U_a by (c_a + U_a) / m, c_a the base-m digit a of j (least
+// significant first), one rounding per operation; both maps carry the
+// uniform measure of the unit square / cube to that of the simplex, so the
+// m^D cells become equal-measure strata and the weights |T| / N stay
+// unbiased. Samples j >= m^D keep their uniforms. n = 0 selects uniform.
+struct Strat {
+  int m;           // strata per axis
+  int n;           // m^D (0: uniform sampling)
+  uint32_t magic;  // ceil(2^32 / m): j / m = umulhi(j, magic) exactly while j m < 2^32
+  float mf;        // m in FP32 and FP64
+  double md;
+};
+
+// largest N for which the stratified digits are exact (j m <= N^(1+1/d) < 2^32)
+constexpr int kMaxStratifiedN = 1 << 20;
+
+// strata for N samples per element in dimension d (sampling 1 = stratified)
+inline Strat strat_for(int d, int N, int sampling) {
+  Strat st{0, 0, 0u, 1.f, 1.0};
+  if (sampling != 1) return st;
+  int m = 1;
+  for (;;) {
+    int64_t q = 1;
+    for (int a = 0; a < d; ++a) q *= (int64_t)(m + 1);
+    if (q > N) break;
+    ++m;
+  }
+  st.m = m;
+  st.n = m > 1 ? (d == 2 ? m * m : m * m * m) : 0;
+  st.magic = m > 1 ? (uint32_t)((((uint64_t)1 << 32) + (uint64_t)m - 1) / (uint64_t)m) : 0u;
+  st.mf = (float)m;
+  st.md = (double)m;
+  return st;
+}
+
+// small non-negative integer c (< 2^23) as P, from its bit pattern (no
+// conversion instruction: conversions use the narrow FP64 pipe here)
+__device__ __forceinline__ float small_int_f(uint32_t c) {
+  return __fsub_rn(__uint_as_float(0x4B000000u | c), 8388608.0f);
+}
+__device__ __forceinline__ double small_int_d(uint32_t c) {
+  return __dsub_rn(__longlong_as_double((long long)(0x4330000000000000ull | c)), 4503599627370496.0);
 }
 
 template <typename P>
-__device__ __forceinline__ void spacing_weights(uint32_t w0, uint32_t w1, uint32_t w2, P lam[4]) {
+__device__ __forceinline__ P strat_u(P u, uint32_t c, const Strat& st) {
   using A = Ar<P>;
-  P v0 = A::u01(w0), v1 = A::u01(w1), v2 = A::u01(w2), s;
-  if (v1 < v0) { s = v0; v0 = v1; v1 = s; }
-  if (v2 < v1) { s = v1; v1 = v2; v2 = s; }
-  if (v1 < v0) { s = v0; v0 = v1; v1 = s; }
-  lam[0] = v0;
-  lam[1] = A::sub(v1, v0);
-  lam[2] = A::sub(v2, v1);
-  lam[3] = A::sub(P(1), v2);
+  if constexpr (sizeof(P) == 4) return A::div(A::add(small_int_f(c), u), st.mf);
+  else return A::div(A::add(small_int_d(c), u), st.md);
+}
+
+// barycentric weights of sample j from its Philox block w (2D: words
+// 2(j%2), 2(j%2)+1; 3D: words 0..2)
+template <int D, typename P>
+__device__ __forceinline__ void sample_lambda(const uint4& w, int j, const Strat& st, P lam[D + 1]) {
+  using A = Ar<P>;
+  if constexpr (D == 2) {
+    P xi = A::u01((j & 1) ? w.z : w.x), eta = A::u01((j & 1) ? w.w : w.y);
+    if (j < st.n) {
+      const uint32_t c1 = __umulhi((uint32_t)j, st.magic), c0 = (uint32_t)j - c1 * (uint32_t)st.m;
+      xi = strat_u<P>(xi, c0, st);
+      eta = strat_u<P>(eta, c1, st);
+    }
+    const P s = A::sqrt(xi);
+    lam[0] = A::sub(P(1), s);
+    lam[1] = A::mul(s, A::sub(P(1), eta));
+    lam[2] = A::mul(s, eta);
+  } else {
+    P v0 = A::u01(w.x), v1 = A::u01(w.y), v2 = A::u01(w.z), s;
+    if (j < st.n) {
+      const uint32_t m = (uint32_t)st.m;
+      const uint32_t q = __umulhi((uint32_t)j, st.magic), c0 = (uint32_t)j - q * m;
+      const uint32_t c2 = __umulhi(q, st.magic), c1 = q - c2 * m;
+      v0 = strat_u<P>(v0, c0, st);
+      v1 = strat_u<P>(v1, c1, st);
+      v2 = strat_u<P>(v2, c2, st);
+    }
+    if (v1 < v0) { s = v0; v0 = v1; v1 = s; }
+    if (v2 < v1) { s = v1; v1 = v2; v2 = s; }
+    if (v1 < v0) { s = v0; v0 = v1; v1 = s; }
+    lam[0] = v0;
+    lam[1] = A::sub(v1, v0);
+    lam[2] = A::sub(v2, v1);
+    lam[3] = A::sub(P(1), v2);
+  }
 }
 
 // X = sum_m lam_m x_m, accumulated left to right, one rounding per operation

@@ -143,6 +143,7 @@ struct AssembleArgs {
   int64_t* counters;      // [2]: fallback, empty
   int mode = kAsmPlain;
   void* pmu = nullptr;    // record / cached: [d][ne_t N] P, mu_1..d of every sample
+  int sampling = SFT_SAMPLING_UNIFORM;  // sft_sampling
 };
 sft_status launch_assembly(sft_source_s* s, sft_target_s* t, const AssembleArgs& a, cudaStream_t st);
 // solve.cu

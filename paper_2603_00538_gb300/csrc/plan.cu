@@ -70,6 +70,10 @@ sft_status sft_plan_create(sft_source s, sft_target t, const sft_options* o, sft
   if (o->precision != SFT_PREC_FP32 && o->precision != SFT_PREC_FP64) return fail(SFT_ERR_ARG, "bad precision");
   if (o->cg_max_iter < 0 || !(o->cg_tol >= 0) || !std::isfinite(o->alpha)) return fail(SFT_ERR_ARG, "bad solver options");
   if (o->cg_mode != SFT_CG_MIXED && o->cg_mode != SFT_CG_FP64) return fail(SFT_ERR_ARG, "unknown cg_mode");
+  if (o->sampling != SFT_SAMPLING_UNIFORM && o->sampling != SFT_SAMPLING_STRATIFIED)
+    return fail(SFT_ERR_ARG, "unknown sampling scheme");
+  if (o->sampling == SFT_SAMPLING_STRATIFIED && o->samples_per_elem > kMaxStratifiedN)
+    return fail(SFT_ERR_UNSUPPORTED, "stratified sampling supports at most 2^20 samples per element");
   if (o->field_count < 0 || o->field_count > s->nf) return fail(SFT_ERR_ARG, "field_count out of range");
   cudaStream_t st = (cudaStream_t)o->cuda_stream;
   const int prec = o->precision;
@@ -123,6 +127,7 @@ sft_status sft_plan_create(sft_source s, sft_target t, const sft_options* o, sft
     a.counters = counters.p;
     a.mode = kAsmRecord;
     a.pmu = pl->samp_mu;
+    a.sampling = o->sampling;
     if ((r = launch_assembly(s, t, a, st))) break;
     int64_t hc[2] = {0, 0};
     int32_t herr = 0;
@@ -197,6 +202,7 @@ sft_status sft_plan_transfer(sft_plan pl, double* u_out, double* b_out, double* 
   a.counters = nullptr;
   a.mode = kAsmCached;
   a.pmu = pl->samp_mu;
+  a.sampling = o.sampling;
   if (sft_status r = launch_assembly(s, t, a, st)) return r;
   if (ev.ok) cudaEventRecord(ev.e[3], st);
   // step 7

@@ -34,6 +34,7 @@ struct SurParams {
   PhiloxKey key;
   uint32_t stream_id;
   float alpha, tau, cdet, cmc;
+  Strat st;              // sampling scheme
 };
 
 // shared memory: [network tile (NET only)] + per-row partial pieces +
@@ -122,14 +123,9 @@ __global__ void __launch_bounds__(NET ? kTPR * kTileM : kTileM, NET ? 2 : 8) k_s
 #pragma unroll
           for (int a = 0; a < DT; ++a) xv[m][a] = __ldg(tx + (int64_t)v[m] * DT + a);
         }
-        if constexpr (DT == 2) {
-          const uint4 w = philox4x32_10(make_uint4((uint32_t)(j >> 1), (uint32_t)t, p.stream_id, 0u), p.key);
-          if (j & 1) osada_weights<float>(w.z, w.w, lam);
-          else osada_weights<float>(w.x, w.y, lam);
-        } else {
-          const uint4 w = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)t, p.stream_id, 0u), p.key);
-          spacing_weights<float>(w.x, w.y, w.z, lam);
-        }
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)(DT == 2 ? (j >> 1) : j), (uint32_t)t, p.stream_id, 0u),
+                                      p.key);
+        sample_lambda<DT, float>(w, j, p.st, lam);
         map_point<DT, float>(lam, xv, X);
       }
       // exact subsample (or every query when the network is off)
@@ -402,6 +398,10 @@ sft_status sft_transfer_surrogate(sft_mlp net, sft_source exact, sft_target t, c
   if ((int64_t)o->samples_per_elem * t->ne >= ((int64_t)1 << 40)) return fail(SFT_ERR_UNSUPPORTED, "too many samples");
   if (o->cg_max_iter < 0 || !(o->cg_tol >= 0) || !std::isfinite(o->alpha)) return fail(SFT_ERR_ARG, "bad solver options");
   if (o->cg_mode != SFT_CG_MIXED && o->cg_mode != SFT_CG_FP64) return fail(SFT_ERR_ARG, "unknown cg_mode");
+  if (o->sampling != SFT_SAMPLING_UNIFORM && o->sampling != SFT_SAMPLING_STRATIFIED)
+    return fail(SFT_ERR_ARG, "unknown sampling scheme");
+  if (o->sampling == SFT_SAMPLING_STRATIFIED && o->samples_per_elem > kMaxStratifiedN)
+    return fail(SFT_ERR_UNSUPPORTED, "stratified sampling supports at most 2^20 samples per element");
   if (exact) {
     if (exact->dim > t->dim) return fail(SFT_ERR_ARG, "exact source dimension exceeds the target's");
     if (so->exact_field < 0 || so->exact_field >= exact->nf) return fail(SFT_ERR_ARG, "exact_field out of range");
@@ -477,6 +477,7 @@ sft_status sft_transfer_surrogate(sft_mlp net, sft_source exact, sft_target t, c
   p.tau = so->tau;
   p.cdet = (float)(o->alpha / (double)((t->dim + 1) * (t->dim + 2)));
   p.cmc = (float)(1.0 / (double)N);
+  p.st = strat_for(t->dim, N, o->sampling);
   int32_t* fb = nullptr;
   float* sf = nullptr;
   if (so->fallback_out) {
