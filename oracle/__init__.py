@@ -284,6 +284,51 @@ def l2_error_2d(src, tgt, tgt_values, field=0):
     return e.value, n.value
 
 
+def roundtrip(mesh1, mesh2, f_ref, iters, prec, samples_per_elem, seeds=(0, 1), alpha=1.0, cg_tol=1e-12,
+              cg_max_iter=1000, sampling=0, exact=False):
+    """Repeated round trips mesh1 -> mesh2 -> mesh1 of a nodal field (the
+    iterative analysis of Sec. 5): transfer i of the first leg uses
+    seeds[0], of the second leg seeds[1], so every round trip draws the same
+    samples (the fixed-sample online mode). exact=True replaces the Monte
+    Carlo load vector by the mesh-intersection one (2D only), i.e. repeated
+    exact Galerkin projections. Returns (errors, field): errors[k] =
+    (E_l2, E_mass) after round trip k + 1, E_l2 the discrete l2 error of the
+    nodal values and E_mass the conservation error of the P1 integral on
+    mesh 1 (exact quadrature: sum_i m_i f_i with the lumped masses), both
+    relative to f_ref."""
+    f_ref = _f64(f_ref)
+    m1 = lumped_mass(mesh1.coords, mesh1.conn)
+    i_ref = float(m1 @ f_ref)
+    if exact:
+        csr1, csr2 = mass_csr(mesh2.coords, mesh2.conn), mass_csr(mesh1.coords, mesh1.conn)
+
+    def leg(src_mesh, tgt_mesh, vals, seed, csr):
+        src = _Mesh(src_mesh.coords, src_mesh.conn, vals[None, :])
+        if exact:
+            b = mi_load_vector_2d(src, tgt_mesh)
+            u, _, _ = pcg(*csr, b, tol=cg_tol, max_iter=cg_max_iter)
+            return u
+        return transfer(src, tgt_mesh, prec, samples_per_elem, seed=seed, stream=0, alpha=alpha, cg_tol=cg_tol,
+                        cg_max_iter=cg_max_iter, sampling=sampling)["u"][0]
+
+    f = f_ref.copy()
+    errors = []
+    for _ in range(iters):
+        g = leg(mesh1, mesh2, f, seeds[0], csr1 if exact else None)
+        f = leg(mesh2, mesh1, g, seeds[1], csr2 if exact else None)
+        e_l2 = float(np.linalg.norm(f - f_ref) / np.linalg.norm(f_ref))
+        e_mass = abs(float(m1 @ f) - i_ref) / abs(i_ref)
+        errors.append((e_l2, e_mass))
+    return errors, f
+
+
+class _Mesh:
+    """coords, conn, values: the attributes transfer() reads from a mesh."""
+
+    def __init__(self, coords, conn, values):
+        self.coords, self.conn, self.values = coords, conn, values
+
+
 def _declare_mlp(L):
     L.orc_mlp_nparam.restype = _i64
     L.orc_bf16_round.argtypes = [ctypes.c_double]

@@ -495,6 +495,44 @@ def test_error_decays_as_inverse_sqrt_N(orc):
     assert -0.56 < slope < -0.44
 
 
+def test_roundtrip_exact_projection_conserves_and_linear_fields_survive(orc):
+    """Round trips (the iterative analysis of Sec. 5): repeated exact Galerkin
+    projections (mesh-intersection load vectors) conserve the integral, since
+    both P1 spaces contain the constants (test function sum_i psi_i = 1), so
+    E_mass stays at rounding level; a linear field is reproduced by every
+    projection, exactly (MI) and by the control-variate estimate with
+    alpha = 1 (the residual f - g vanishes)."""
+    a = W.delaunay_tri_mesh(120, 8, 3)
+    b = W.jittered_tri_mesh(5, 4)
+    f = W.paper_f2(a.coords)
+    errs, _ = orc.roundtrip(a, b, f, 3, 0, 8, exact=True, cg_tol=1e-14)
+    assert all(em < 1e-12 for _, em in errs)
+    assert 0 < errs[0][0] < errs[-1][0]          # projection errors do accumulate in l2
+    lin = W.linear_field([0.3, -1.2, 2.0])(a.coords)
+    for exact in (True, False):
+        errs, _ = orc.roundtrip(a, b, lin, 2, 0, 8, exact=exact, cg_tol=1e-14)
+        assert all(el < 1e-11 and em < 1e-11 for el, em in errs), errs
+
+
+def test_roundtrip_monte_carlo_is_unbiased_for_the_exact_round_trip(orc):
+    """One round trip with independent samples in its two legs is unbiased
+    for the exact (mesh-intersection) round trip: each leg is linear in its
+    input values and unbiased (Eq. cv_load_unbiased), and the legs draw
+    independent samples, so E[A2 A1 f] = E[A2] E[A1] f. The mean over 150
+    seed pairs approaches the exact round trip within a few standard errors."""
+    a = W.delaunay_tri_mesh(60, 6, 5)
+    b = W.jittered_tri_mesh(4, 6)
+    f = W.paper_f2(a.coords)
+    _, f_mi = orc.roundtrip(a, b, f, 1, 0, 8, exact=True, cg_tol=1e-14)
+    runs = np.stack([orc.roundtrip(a, b, f, 1, 0, 8, seeds=(sd, 1000 + sd), cg_tol=1e-14)[1]
+                     for sd in range(150)])
+    mean, se = runs.mean(0), runs.std(0, ddof=1) / math.sqrt(runs.shape[0])
+    se = np.sqrt(se ** 2 + (1e-12 * np.abs(f_mi).max()) ** 2)
+    z = (mean - f_mi) / se
+    assert np.abs(z).max() < 5.0
+    assert abs(z.mean()) < 5.0 / math.sqrt(z.size)
+
+
 def test_alpha_reduces_error(orc):
     """Both errors decrease as alpha goes from 0 to 1 (Sec. 5.1, alpha study)."""
     s, t = _pair(2, ns=8)
