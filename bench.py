@@ -55,7 +55,11 @@ WORKLOADS = {
     "batch256": "256 batched requests, 2D/3D 50/50, 1e4..5e5 target elements (log-uniform, seeded), 1..8 fields, "
                 "N in {8,16,32,64,128}; 2D sources: 2,048- and 3,998,792-triangle meshes, 3D source: "
                 "4,983,504 tets, 8 fields each; one graph-replayed plan per step (control, persistent "
-                "assembly, one batched FP64 CG to 1e-10)",
+                "assembly, one batched solve to 1e-10: FP64 residuals, FP32 CG on the scaled matrices)",
+    "roundtrip": "round trips (the paper's iterative analysis): f2 on a 2,000,000-triangle Delaunay mesh "
+                 "(1,002,001 nodes) -> 199,712-triangle jittered mesh -> back, N = 20, FP32 sampling, FP64 "
+                 "values and CG to 1e-10; two plans built once, a step is one round trip (two online "
+                 "transfers, each leg's solution the next leg's source values)",
 }
 # algorithmic HBM bytes of the assembly kernel (minimum a black-box P1 query
 # and a target element must move): per query cell range 8 B + one candidate
@@ -549,6 +553,120 @@ SUR_KERNEL_FILES = ["paper_2603_00538_gb300/csrc/surrogate.cu", "paper_2603_0053
                     "paper_2603_00538_gb300/csrc/tc.cuh"]
 
 
+def run_roundtrip(args):
+    """Round-trip workload: plans mesh 1 -> mesh 2 and mesh 2 -> mesh 1 built
+    once; the field starts at the reference f2 after the warm-up; a step is
+    one round trip. Reports the discrete l2 and conservation errors on mesh 1
+    after the timed round trips and, from an untimed run, after each of the
+    first ten."""
+    import torch
+    import paper_2603_00538_gb300 as sft
+
+    rank, world, local = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    m1, m2, p = W.config_meshes("roundtrip", args.scale)
+    N, tol = p["samples_per_elem"], p["cg_tol"]
+    stream = torch.cuda.current_stream()
+    s1, t1 = sft.mesh_source(m1, device=dev), sft.mesh_target(m1, device=dev)
+    s2, t2 = sft.mesh_source(m2, device=dev), sft.mesh_target(m2, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rt = sft.RoundTrip(s1, t1, s2, t2, N, seeds=(0, 1), cg_tol=tol, sampling=_sampling(args))
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t0
+    ref = torch.as_tensor(np.ascontiguousarray(m1.values)).to(dev)
+    f = ref.clone()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    lump = torch.as_tensor(sft.sft_target_mass(t1)[3]).to(dev)
+
+    def errors(x):
+        e_l2 = float(torch.linalg.norm(x[0] - ref[0]) / torch.linalg.norm(ref[0]))
+        i_ref = float(lump @ ref[0])
+        return e_l2, abs(float(lump @ x[0]) - i_ref) / abs(i_ref)
+
+    curve = []
+    for _ in range(10):
+        rt.run(f, 1)
+        curve.append(errors(f))
+    for _ in range(args.warmup):
+        rt.run(f, 1)
+    f.copy_(ref)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            rt.run(f, 1)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    final = errors(f)
+    queries = int(rt.queries)
+    total_ms, all_queries = aggregate(float(sum(step_ms)), queries * args.steps, world, dev)
+    if world > 1:
+        torch.distributed.barrier()
+    ms_per_step = total_ms / args.steps
+    value = all_queries / (total_ms / 1e3)
+    launches = count_launches(lambda: rt.run(f, 1))
+    # end to end: the field from pinned host memory, the round trip, the field back
+    f_h = torch.as_tensor(np.ascontiguousarray(m1.values)).pin_memory()
+    k_e2e = max(1, min(args.steps, 5))
+
+    def e2e_step():
+        f.copy_(f_h, non_blocking=True)
+        rt.run(f, 1)
+        f_h.copy_(f, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    e2e_step()
+    t1w = time.perf_counter()
+    for _ in range(k_e2e):
+        e2e_step()
+    e2e_ms = (time.perf_counter() - t1w) * 1e3 / k_e2e
+    if rank == 0:
+        hbm, which = peaks()
+        cpu = None
+        if not args.skip_cpu:
+            import oracle
+            ms1, ms2, _ = W.config_meshes("roundtrip", 0.1)
+            t0c = time.perf_counter()
+            oracle.roundtrip(ms1, ms2, ms1.values[0], 1, 1, N, cg_tol=tol, sampling=_sampling(args))
+            dt = time.perf_counter() - t0c
+            qc = (ms2.nnodes + ms2.nelems * N) + (ms1.nnodes + ms1.nelems * N)
+            cpu = {"value": qc / dt, "unit": "queries/s", "cores": 1, "kind": "oracle", "seconds": dt,
+                   "sample": f"one oracle round trip on the same generators at 1/10 of the element counts "
+                             f"({ms1.nelems} and {ms2.nelems} triangles, grid builds included)"}
+        line = {
+            "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"roundtrip: {WORKLOADS['roundtrip']}", "queries_per_step": queries,
+                       "mesh1_elements": m1.nelems, "mesh2_elements": m2.nelems, "samples_per_elem": N,
+                       "sampling": args.sampling, "plan_create_s": plan_s,
+                       "l2": "flushed between steps (256 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "breakdown_ms": {"round_trip_min": min(step_ms), "round_trip_max": max(step_ms)},
+            "accuracy": {"after_timed_round_trips": {"round_trips": args.steps, "E_l2": final[0],
+                                                     "E_mass": final[1]},
+                         "per_round_trip_first_10": [{"E_l2": a, "E_mass": b} for a, b in curve]},
+            "roofline": None,
+            "cpu_baseline": cpu,
+            "e2e": {"value": queries / (e2e_ms / 1e3), "unit": "queries/s", "ms_per_step": e2e_ms, "steps": k_e2e,
+                    "h2d_bytes_per_step": int(f_h.numel() * f_h.element_size()),
+                    "d2h_bytes_per_step": int(f_h.numel() * f_h.element_size()),
+                    "timing": "host wall clock: field H2D, one round trip, field D2H"},
+            "clocks": clk.summary(),
+            "gpu_launches": launches * args.steps if launches else None,
+        }
+        print(json.dumps(line), flush=True)
+    rt.close()
+
+
 def run_surrogate(args):
     """Surrogate workload: the network is trained once (timed separately); a
     step is one sft_transfer_surrogate (control at the target nodes from the
@@ -873,6 +991,18 @@ def run_reference(args):
         q = tgt_s.nelems * p["samples_per_elem"] + tgt_s.nnodes
         sample = (f"the first {tgt_s.nelems} target elements (Morton order) per step, the initial network "
                   f"weights, the full exact source (grid build included)")
+    elif args.workload == "roundtrip":
+        import oracle
+        ms1, ms2, p = W.config_meshes("roundtrip", 0.01 * args.scale)
+
+        def one():
+            t0 = time.perf_counter()
+            oracle.roundtrip(ms1, ms2, ms1.values[0], 1, 1, p["samples_per_elem"], cg_tol=p["cg_tol"],
+                             sampling=_sampling(args))
+            return time.perf_counter() - t0
+        q = (ms2.nnodes + ms2.nelems * p["samples_per_elem"]) + (ms1.nnodes + ms1.nelems * p["samples_per_elem"])
+        sample = (f"one oracle round trip per step on the same generators at 1/100 of the element counts "
+                  f"({ms1.nelems} and {ms2.nelems} triangles)")
     else:
         src, tgt, p = make_workload(args.workload, args.scale)
         tgt_s = _sample_target(tgt, args.cpu_frac)
@@ -926,6 +1056,8 @@ def main():
         run_batch(args)
     elif args.workload == "sur3d":
         run_surrogate(args)
+    elif args.workload == "roundtrip":
+        run_roundtrip(args)
     elif args.workload.endswith("_online"):
         run_online(args)
     else:

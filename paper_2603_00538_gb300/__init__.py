@@ -473,6 +473,43 @@ def sft_batch_destroy(batch: Batch):
     batch.close()
 
 
+class RoundTrip:
+    """Repeated round trips mesh 1 -> mesh 2 -> mesh 1 of one nodal field (the
+    iterative analysis of Sec. 5) through two transfer plans (initialization
+    once; every round trip reuses the recorded samples). src1/tgt1 and
+    src2/tgt2 are the same meshes as sources (one FP64 field) and targets.
+    run(f, iters) maps the CUDA tensor f [1, nnodes1] (float64) in place."""
+
+    def __init__(self, src1: Source, tgt1: Target, src2: Source, tgt2: Target, samples_per_elem: int,
+                 precision: int = SFT_PREC_FP32, seeds=(0, 1), alpha: float = 1.0, cg_tol: float = 1e-10,
+                 cg_max_iter: int = 1000, sampling: int = SFT_SAMPLING_UNIFORM, cg_mode: int = SFT_CG_MIXED):
+        import torch
+        if _nf(src1) != 1 or _nf(src2) != 1:
+            raise ValueError("round-trip sources carry exactly one field")
+        kw = dict(alpha=alpha, cg_tol=cg_tol, cg_max_iter=cg_max_iter, out_device=True, sampling=sampling,
+                  cg_mode=cg_mode)
+        self.src1, self.src2 = src1, src2
+        self.p12 = sft_plan_create(src1, tgt2, samples_per_elem, precision, seed=seeds[0], **kw)
+        self.p21 = sft_plan_create(src2, tgt1, samples_per_elem, precision, seed=seeds[1], **kw)
+        self.g = torch.zeros((1, _nv(tgt2)), dtype=torch.float64, device=torch.device("cuda",
+                                                                                       torch.cuda.current_device()))
+        self.queries = 0
+
+    def run(self, f, iters: int = 1):
+        for _ in range(iters):
+            sft_source_set_values(self.src1, f)
+            _, st, _ = sft_plan_transfer(self.p12, u_out=self.g)
+            q = st["queries"]
+            sft_source_set_values(self.src2, self.g)
+            _, st, _ = sft_plan_transfer(self.p21, u_out=f)
+            self.queries = q + st["queries"]
+        return f
+
+    def close(self):
+        self.p12.close()
+        self.p21.close()
+
+
 class Mlp(_Handle):
     pass
 

@@ -282,6 +282,9 @@ def config_meshes(name: str, scale: float = 1.0):
       float32 coords; 2,000,000-triangle Delaunay target; N = 64.
     * ``tet5m``:   4,983,504-tet source (94^3 x 6), 8 Gaussians + jump;
       2,958,234-tet target (79^3 x 6, independent jitter); N = 32; float32.
+    * ``roundtrip``: (mesh 1, mesh 2, params) of the round-trip analysis: f2 on
+      a 2,000,000-triangle Delaunay mesh, a 199,712-triangle jittered mesh,
+      N = 20, float64 values.
     * ``sur3d``:   the tri4m source field extruded along z, F(x,y,z) = f(x,y),
       learned by the surrogate network from 2,000,000 seeded points, onto the
       tet5m target with N = 64; exact fallback subsample s = 4,
@@ -316,6 +319,17 @@ def config_meshes(name: str, scale: float = 1.0):
         tgt = as_precision(morton_reorder(jittered_kuhn_mesh(nt, seed=1)), np.float32)
         return src, tgt, dict(samples_per_elem=64, dtype="float32", cg_tol=1e-10,
                               train_points=max(4096, int(round(2_000_000 * scale))), subsample=4, tau_rel=1e-2)
+    if name == "roundtrip":
+        # the iterative analysis (Sec. 5) at scale: the reference field f2 on a
+        # fine 2,000,000-triangle Delaunay mesh (mesh 1) carried through a
+        # 10x coarser 199,712-triangle jittered mesh (mesh 2) and back,
+        # N = 20 samples per element as in the paper; FP64 values (each leg's
+        # FP64 solution is the next leg's source)
+        side = max(2, int(round(1000 * math.sqrt(scale))))
+        m1 = with_values(delaunay_tri_mesh((side - 1) ** 2, side - 1, seed=1), [paper_f2], np.float64)
+        n2 = max(2, int(round(316 * math.sqrt(scale))))
+        m2 = with_values(jittered_tri_mesh(n2, seed=2), [lambda x: 0.0 * x[:, 0]], np.float64)
+        return m1, m2, dict(samples_per_elem=20, dtype="float64", cg_tol=1e-10)
     raise KeyError(name)
 
 
