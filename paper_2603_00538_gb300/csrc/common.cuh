@@ -41,6 +41,18 @@ __device__ __forceinline__ float u01f(uint32_t x) {
   const float one_m = __uint_as_float(0x3F800000u | (x >> 9));  // 1 + (x>>9) 2^-23
   return __fadd_rn(__fsub_rn(one_m, 1.0f), 0x1p-24f);           // (2 (x>>9) + 1) 2^-24
 }
+// float -> double without a conversion instruction (exact): a normal float's
+// sign, rebiased exponent and mantissa placed in the double's fields; zero,
+// subnormal, infinite and NaN inputs take the conversion instruction
+__device__ __forceinline__ double f2d(float x) {
+  const uint32_t b = __float_as_uint(x);
+  const uint32_t e = (b >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) return (double)x;
+  const uint64_t bits = ((uint64_t)(b >> 31) << 63) | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(b & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ double f2d(double x) { return x; }
+
 __device__ __forceinline__ double u01d(uint32_t x) {
   const double one_m = __longlong_as_double((long long)(0x3FF0000000000000ull | ((uint64_t)x << 20)));
   return __dadd_rn(__dsub_rn(one_m, 1.0), 0x1p-33);              // (2x + 1) 2^-33

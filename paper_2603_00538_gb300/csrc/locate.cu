@@ -656,7 +656,7 @@ __global__ void k_p1_integral_partial(const TI* __restrict__ x, const int32_t* _
     for (int m = 0; m <= D; ++m) {
       v[m] = conn[e * (D + 1) + m];
 #pragma unroll
-      for (int a = 0; a < D; ++a) xv[m][a] = (double)x[(int64_t)v[m] * D + a];
+      for (int a = 0; a < D; ++a) xv[m][a] = f2d(x[(int64_t)v[m] * D + a]);
     }
     double vol;
     if constexpr (D == 2) {
@@ -665,15 +665,17 @@ __global__ void k_p1_integral_partial(const TI* __restrict__ x, const int32_t* _
       double e1[3], e2[3], e3[3];
       for (int a = 0; a < 3; ++a) { e1[a] = xv[1][a] - xv[0][a]; e2[a] = xv[2][a] - xv[0][a]; e3[a] = xv[3][a] - xv[0][a]; }
       vol = (e1[0] * (e2[1] * e3[2] - e2[2] * e3[1]) - e1[1] * (e2[0] * e3[2] - e2[2] * e3[0]) +
-             e1[2] * (e2[0] * e3[1] - e2[1] * e3[0])) / 6.0;
+             e1[2] * (e2[0] * e3[1] - e2[1] * e3[0])) * (1.0 / 6.0);
     }
+    // sum |e| (f_0 + ... + f_d); the 1 / (d + 1) is applied once per thread
     for (int f = 0; f < nf; ++f) {
       double m = 0.0;
 #pragma unroll
-      for (int q = 0; q <= D; ++q) m += (double)values[(int64_t)f * nv + v[q]];
-      acc[f] += vol * m / (double)(D + 1);
+      for (int q = 0; q <= D; ++q) m += f2d(values[(int64_t)f * nv + v[q]]);
+      acc[f] = fma(vol, m, acc[f]);
     }
   }
+  for (int f = 0; f < nf; ++f) acc[f] *= 1.0 / (D + 1);
   __shared__ double sh[kMaxFields][8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int f = 0; f < nf; ++f) {
