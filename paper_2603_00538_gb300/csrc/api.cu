@@ -208,8 +208,6 @@ sft_status sft_target_create(const sft_mesh_desc* d, sft_target* out) {
     if ((r = build_target(t, st, d_err))) break;
     const int prec = d->dtype == SFT_F64 ? SFT_PREC_FP64 : SFT_PREC_FP32;
     if ((r = target_coordsP(t, prec, st))) break;
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) { r = cuda_fail(e, "sync"); break; }
   } while (0);
   if (d_err) cudaFreeAsync(d_err, st);
   if (r != SFT_OK) {
@@ -296,7 +294,8 @@ sft_status sft_transfer(sft_source s, sft_target t, const sft_options* o, double
     u_dev = u_tmp.p;
   }
   SolveResult sr;
-  if (sft_status r = mass_solve(t, nf, b.p, u_dev, o->cg_tol, o->cg_max_iter, st, d_err.p, &sr, o->cg_mode))
+  SolveLate late(st);  // the solve's status is read with the final readback below
+  if (sft_status r = mass_solve(t, nf, b.p, u_dev, o->cg_tol, o->cg_max_iter, st, d_err.p, &sr, o->cg_mode, &late))
     return r;
   if (ev.ok) cudaEventRecord(ev.e[4], st);
 
@@ -320,8 +319,10 @@ sft_status sft_transfer(sft_source s, sft_target t, const sft_options* o, double
   int32_t herr = 0;
   SFT_CUDA(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
   SFT_CUDA(cudaMemcpyAsync(&herr, d_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  if (late.pending) SFT_CUDA(cudaMemcpyAsync(late.host, late.buf.p, late.bytes, cudaMemcpyDeviceToHost, st));
   if (ev.ok) cudaEventRecord(ev.e[5], st);
   SFT_CUDA(cudaStreamSynchronize(st));
+  if (sft_status r = finish_solve(late, &sr)) return r;
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
     stats->cg_iters = sr.iters;
@@ -353,12 +354,18 @@ sft_status sft_conservation_error(sft_source s, sft_target t, const double* u, i
     SFT_CUDA(cudaMemcpyAsync(tmp.p, u, sizeof(double) * t->nv, cudaMemcpyHostToDevice, st));
     ud = tmp.p;
   }
-  double it = 0.0;
-  if (sft_status r = weighted_sum(t->lumped, ud, t->nv, &it, st)) return r;
-  if (!s->integral_valid) {
-    if (sft_status r = source_integrals(s, st)) return r;
-    s->integral_valid = true;
-  }
+  // both reductions read back together (one wait on the stream)
+  const size_t ni = s->integral_valid ? 0 : (size_t)kIntegralBlocks * kMaxFields;
+  DevBuf<double> part(st);
+  SFT_CUDA(part.alloc(ni + kWsumBlocks));
+  if (ni)
+    if (sft_status r = source_integrals_launch(s, part.p, st)) return r;
+  if (sft_status r = weighted_sum_launch(t->lumped, ud, t->nv, part.p + ni, st)) return r;
+  std::vector<double> h(ni + kWsumBlocks);
+  SFT_CUDA(cudaMemcpyAsync(h.data(), part.p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
+  SFT_CUDA(cudaStreamSynchronize(st));
+  if (ni) source_integrals_finish(s, h.data());
+  const double it = weighted_sum_finish(h.data() + ni);
   const double is = s->integral[field];
   out3[0] = std::fabs(is - it) / std::fabs(is);
   out3[1] = is;

@@ -124,6 +124,11 @@ sft_status locate_points(sft_source_s* s, int prec, int64_t n, const void* pts, 
                          int32_t* elem_out, void* val_out, int val_is_double, int64_t val_stride,
                          int64_t* d_counters, cudaStream_t st, int nf_out = -1, void* mu_out = nullptr);
 sft_status source_integrals(sft_source_s* s, cudaStream_t st);
+// the same split in launch (partials [kIntegralBlocks][kMaxFields] on the
+// device) and the host's fixed-order sum of the copied partials
+constexpr unsigned kIntegralBlocks = 152 * 8;
+sft_status source_integrals_launch(sft_source_s* s, double* part, cudaStream_t st);
+void source_integrals_finish(sft_source_s* s, const double* hpart);
 sft_status refresh_value_copies(sft_source_s* s, cudaStream_t st);
 // target.cu
 sft_status build_target(sft_target_s* t, cudaStream_t st, int32_t* d_err);
@@ -148,12 +153,28 @@ struct AssembleArgs {
 sft_status launch_assembly(sft_source_s* s, sft_target_s* t, const AssembleArgs& a, cudaStream_t st);
 // solve.cu
 struct SolveResult { int iters; double rel_resid; int converged; };
+// Deferred solve status: with a SolveLate, mass_solve returns without waiting
+// for the kernel (mixed mode); the caller copies `bytes` from buf to host in
+// its own final readback and then calls finish_solve.
+struct SolveLate {
+  explicit SolveLate(cudaStream_t st) : buf(st) {}
+  DevBuf<unsigned char> buf;
+  alignas(16) unsigned char host[256];
+  size_t bytes = 0;
+  int nrhs = 0;
+  bool pending = false;
+};
+sft_status finish_solve(const SolveLate& late, SolveResult* res);
 // cg_mode: SFT_CG_MIXED (FP64 refinement around FP32 CG) or SFT_CG_FP64
 sft_status mass_solve(sft_target_s* t, int nrhs, const double* b, double* x, double tol, int max_iter,
-                      cudaStream_t st, int32_t* d_err, SolveResult* res, int cg_mode = SFT_CG_MIXED);
+                      cudaStream_t st, int32_t* d_err, SolveResult* res, int cg_mode = SFT_CG_MIXED,
+                      SolveLate* late = nullptr);
 // S = diag(M)^-1/2 and the FP32 values of S M S on the target (made once, cached)
 sft_status scaled_matrix(sft_target_s* t, cudaStream_t st);
 sft_status weighted_sum(const double* w, const double* u, int64_t n, double* out_host, cudaStream_t st);
+constexpr unsigned kWsumBlocks = 304;
+sft_status weighted_sum_launch(const double* w, const double* u, int64_t n, double* part, cudaStream_t st);
+double weighted_sum_finish(const double* hpart);
 // conversions
 sft_status convert_coords(const void* in, int in_dtype, void* out, int out_prec, int64_t n, cudaStream_t st);
 }  // namespace sft

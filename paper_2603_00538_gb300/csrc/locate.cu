@@ -692,10 +692,8 @@ __global__ void k_p1_integral_partial(const TI* __restrict__ x, const int32_t* _
   }
 }
 
-sft_status source_integrals(sft_source_s* s, cudaStream_t st) {
-  const unsigned nb = 152 * 8;
-  double* part = nullptr;
-  SFT_CUDA(dalloc(&part, (size_t)nb * kMaxFields, st));
+sft_status source_integrals_launch(sft_source_s* s, double* part, cudaStream_t st) {
+  const unsigned nb = kIntegralBlocks;
   if (s->dim == 2) {
     if (s->dtype == SFT_F64) ::sft::note_launch(), k_p1_integral_partial<2, double><<<nb, 256, 0, st>>>((const double*)s->coords, s->conn, (const double*)s->values, s->nv, s->ne, s->nf, part);
     else ::sft::note_launch(), k_p1_integral_partial<2, float><<<nb, 256, 0, st>>>((const float*)s->coords, s->conn, (const float*)s->values, s->nv, s->ne, s->nf, part);
@@ -704,15 +702,26 @@ sft_status source_integrals(sft_source_s* s, cudaStream_t st) {
     else ::sft::note_launch(), k_p1_integral_partial<3, float><<<nb, 256, 0, st>>>((const float*)s->coords, s->conn, (const float*)s->values, s->nv, s->ne, s->nf, part);
   }
   SFT_CUDA(cudaGetLastError());
-  std::vector<double> h((size_t)nb * kMaxFields);
-  SFT_CUDA(cudaMemcpyAsync(h.data(), part, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
-  SFT_CUDA(cudaStreamSynchronize(st));
-  dfree(part, st);
+  return SFT_OK;
+}
+
+void source_integrals_finish(sft_source_s* s, const double* hpart) {
   for (int f = 0; f < s->nf; ++f) {
     double t = 0.0;
-    for (unsigned b = 0; b < nb; ++b) t += h[(size_t)b * kMaxFields + f];
+    for (unsigned b = 0; b < kIntegralBlocks; ++b) t += hpart[(size_t)b * kMaxFields + f];
     s->integral[f] = t;
   }
+  s->integral_valid = true;
+}
+
+sft_status source_integrals(sft_source_s* s, cudaStream_t st) {
+  DevBuf<double> part(st);
+  SFT_CUDA(part.alloc((size_t)kIntegralBlocks * kMaxFields));
+  if (sft_status r = source_integrals_launch(s, part.p, st)) return r;
+  std::vector<double> h((size_t)kIntegralBlocks * kMaxFields);
+  SFT_CUDA(cudaMemcpyAsync(h.data(), part.p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
+  SFT_CUDA(cudaStreamSynchronize(st));
+  source_integrals_finish(s, h.data());
   return SFT_OK;
 }
 

@@ -18,6 +18,7 @@
 // same convergence decision. The barrier wait is bounded (error flag on
 // timeout; the kernel then returns).
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 #include <vector>
 #include "internal.hpp"
@@ -556,9 +557,28 @@ sft_status scaled_matrix(sft_target_s* t, cudaStream_t st) {
   return SFT_OK;
 }
 
+static_assert(sizeof(MixCtl) <= sizeof(SolveLate::host), "status block larger than its host copy");
+
+static void mix_result(const MixCtl& h, int nrhs, SolveResult* res) {
+  for (int f = 0; f < nrhs; ++f) {
+    res->iters = std::max(res->iters, (int)h.iters[f]);
+    res->rel_resid = std::max(res->rel_resid, h.rel[f]);
+    if (!h.conv[f]) res->converged = 0;
+  }
+}
+
+sft_status finish_solve(const SolveLate& late, SolveResult* res) {
+  if (!late.pending) return SFT_OK;
+  MixCtl h;
+  std::memcpy(&h, late.host, sizeof(MixCtl));
+  if (h.err != 0) return fail(SFT_ERR_DEVICE_STATUS, "CG kernel: grid barrier wait expired");
+  mix_result(h, late.nrhs, res);
+  return SFT_OK;
+}
+
 template <int NR>
 static sft_status launch_mixed(sft_target_s* t, int nrhs, const double* b, double* x, double tol, int max_iter,
-                               cudaStream_t st, SolveResult* res) {
+                               cudaStream_t st, SolveResult* res, SolveLate* late) {
   const int64_t n = t->nv;
   int dev = 0, sms = 0;
   SFT_CUDA(cudaGetDevice(&dev));
@@ -584,8 +604,15 @@ static sft_status launch_mixed(sft_target_s* t, int nrhs, const double* b, doubl
   SFT_CUDA(yb.alloc(vec));
   SFT_CUDA(partd.alloc((size_t)nblocks * nrhs * 2));
   SFT_CUDA(partf.alloc((size_t)nblocks * nrhs));
-  SFT_CUDA(ctl.alloc(1));
-  SFT_CUDA(cudaMemsetAsync(ctl.p, 0, sizeof(MixCtl), st));
+  MixCtl* c = nullptr;
+  if (late) {
+    SFT_CUDA(late->buf.alloc(sizeof(MixCtl)));
+    c = reinterpret_cast<MixCtl*>(late->buf.p);
+  } else {
+    SFT_CUDA(ctl.alloc(1));
+    c = ctl.p;
+  }
+  SFT_CUDA(cudaMemsetAsync(c, 0, sizeof(MixCtl), st));
   const int32_t* rp = t->row_ptr;
   const int32_t* col = t->col;
   const double* val = t->val;
@@ -595,27 +622,28 @@ static sft_status launch_mixed(sft_target_s* t, int nrhs, const double* b, doubl
   float *r = rb.p, *p = pb.p, *q = qb.p, *y = yb.p;
   double* pd = partd.p;
   float* pf = partf.p;
-  MixCtl* c = ctl.p;
   void* args[] = {(void*)&rp, (void*)&col, (void*)&val, (void*)&aval, (void*)&sc, (void*)&n, (void*)&nrhs,
                   (void*)&b, (void*)&x, (void*)&tp, (void*)&r, (void*)&p, (void*)&q, (void*)&y,
                   (void*)&pd, (void*)&pf, (void*)&c, (void*)&tol, (void*)&max_iter};
   const cudaError_t le = (::sft::note_launch(), cudaLaunchCooperativeKernel((const void*)k_mixed_cg<NR>, nblocks,
                                                                            kSolveThreads, args, 0, st));
   if (le != cudaSuccess) return cuda_fail(le, "cudaLaunchCooperativeKernel(k_mixed_cg)");
+  if (late) {
+    late->bytes = sizeof(MixCtl);
+    late->nrhs = nrhs;
+    late->pending = true;
+    return SFT_OK;  // the work buffers are freed in stream order
+  }
   MixCtl h;
   SFT_CUDA(cudaMemcpyAsync(&h, ctl.p, sizeof(MixCtl), cudaMemcpyDeviceToHost, st));
   SFT_CUDA(cudaStreamSynchronize(st));
   if (h.err != 0) return fail(SFT_ERR_DEVICE_STATUS, "CG kernel: grid barrier wait expired");
-  for (int f = 0; f < nrhs; ++f) {
-    res->iters = std::max(res->iters, (int)h.iters[f]);
-    res->rel_resid = std::max(res->rel_resid, h.rel[f]);
-    if (!h.conv[f]) res->converged = 0;
-  }
+  mix_result(h, nrhs, res);
   return SFT_OK;
 }
 
 sft_status mass_solve(sft_target_s* t, int nrhs, const double* b, double* x, double tol, int max_iter,
-                      cudaStream_t st, int32_t* d_err, SolveResult* res, int cg_mode) {
+                      cudaStream_t st, int32_t* d_err, SolveResult* res, int cg_mode, SolveLate* late) {
   (void)d_err;
   res->iters = 0;
   res->rel_resid = 0.0;
@@ -630,10 +658,10 @@ sft_status mass_solve(sft_target_s* t, int nrhs, const double* b, double* x, dou
   }
   if (cg_mode == SFT_CG_MIXED) {
     if (sft_status r = scaled_matrix(t, st)) return r;
-    if (nrhs == 1) return launch_mixed<1>(t, nrhs, b, x, tol, max_iter, st, res);
-    if (nrhs == 2) return launch_mixed<2>(t, nrhs, b, x, tol, max_iter, st, res);
-    if (nrhs <= 4) return launch_mixed<4>(t, nrhs, b, x, tol, max_iter, st, res);
-    return launch_mixed<8>(t, nrhs, b, x, tol, max_iter, st, res);
+    if (nrhs == 1) return launch_mixed<1>(t, nrhs, b, x, tol, max_iter, st, res, late);
+    if (nrhs == 2) return launch_mixed<2>(t, nrhs, b, x, tol, max_iter, st, res, late);
+    if (nrhs <= 4) return launch_mixed<4>(t, nrhs, b, x, tol, max_iter, st, res, late);
+    return launch_mixed<8>(t, nrhs, b, x, tol, max_iter, st, res, late);
   }
   int dev = 0, sms = 0, coop = 0;
   SFT_CUDA(cudaGetDevice(&dev));
@@ -704,19 +732,26 @@ __global__ void k_wsum_partial(const double* __restrict__ w, const double* __res
   }
 }
 
-sft_status weighted_sum(const double* w, const double* u, int64_t n, double* out_host, cudaStream_t st) {
-  const unsigned nb = 304;
-  double* part = nullptr;
-  SFT_CUDA(dalloc(&part, nb, st));
-  ::sft::note_launch(), k_wsum_partial<<<nb, 256, 0, st>>>(w, u, n, part);
+sft_status weighted_sum_launch(const double* w, const double* u, int64_t n, double* part, cudaStream_t st) {
+  ::sft::note_launch(), k_wsum_partial<<<kWsumBlocks, 256, 0, st>>>(w, u, n, part);
   SFT_CUDA(cudaGetLastError());
-  std::vector<double> h(nb);
-  SFT_CUDA(cudaMemcpyAsync(h.data(), part, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
-  SFT_CUDA(cudaStreamSynchronize(st));
-  dfree(part, st);
+  return SFT_OK;
+}
+
+double weighted_sum_finish(const double* hpart) {
   double t = 0.0;
-  for (unsigned k = 0; k < nb; ++k) t += h[k];
-  *out_host = t;
+  for (unsigned k = 0; k < kWsumBlocks; ++k) t += hpart[k];
+  return t;
+}
+
+sft_status weighted_sum(const double* w, const double* u, int64_t n, double* out_host, cudaStream_t st) {
+  DevBuf<double> part(st);
+  SFT_CUDA(part.alloc(kWsumBlocks));
+  if (sft_status r = weighted_sum_launch(w, u, n, part.p, st)) return r;
+  std::vector<double> h(kWsumBlocks);
+  SFT_CUDA(cudaMemcpyAsync(h.data(), part.p, sizeof(double) * kWsumBlocks, cudaMemcpyDeviceToHost, st));
+  SFT_CUDA(cudaStreamSynchronize(st));
+  *out_host = weighted_sum_finish(h.data());
   return SFT_OK;
 }
 

@@ -64,9 +64,19 @@ __global__ void k_volumes(const TI* __restrict__ x, const int32_t* __restrict__ 
 // node -> element incidence, filled in arbitrary order (atomic cursor) with
 // the node of every entry, then put in ascending element order by rank
 template <int D>
-__global__ void k_inc_fill(const int32_t* __restrict__ conn, int64_t ne, const int32_t* __restrict__ inc_start,
+__global__ void k_inc_fill(const int32_t* __restrict__ conn, int64_t ne, int64_t nv,
+                           const int32_t* __restrict__ inc_start,
                            int32_t* __restrict__ cursor, int32_t* __restrict__ inc, int32_t* __restrict__ inc_node) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+    // elements with an index out of range were not counted (k_volumes) and
+    // are skipped here too: the error is reported after the counting pass
+    bool ok = true;
+#pragma unroll
+    for (int m = 0; m <= D; ++m) {
+      const int32_t v = conn[e * (D + 1) + m];
+      ok = ok && v >= 0 && v < nv;
+    }
+    if (!ok) continue;
 #pragma unroll
     for (int m = 0; m <= D; ++m) {
       const int32_t v = conn[e * (D + 1) + m];
@@ -77,8 +87,10 @@ __global__ void k_inc_fill(const int32_t* __restrict__ conn, int64_t ne, const i
   }
 }
 
+// positions [0, inc_start[nv]) were filled (skipped elements leave the tail unused)
 __global__ void k_inc_rank(const int32_t* __restrict__ inc_start, const int32_t* __restrict__ inc,
-                           const int32_t* __restrict__ inc_node, int64_t n, int32_t* __restrict__ out) {
+                           const int32_t* __restrict__ inc_node, int64_t nv, int32_t* __restrict__ out) {
+  const int64_t n = inc_start[nv];
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
     const int32_t v = inc_node[p];
     const int32_t p0 = inc_start[v], p1 = inc_start[v + 1];
@@ -197,14 +209,9 @@ static sft_status build_target_t(sft_target_s* t, cudaStream_t st, int32_t* d_er
     ::sft::note_launch(), k_volumes<D, float><<<blocks_for(t->ne), 256, 0, st>>>((const float*)t->coords, t->conn, t->nv, t->ne, t->vol, t->vol32, wfac, inc_count, d_err);
   SFT_CUDA(cudaGetLastError());
   int32_t herr = 0;
-  SFT_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  SFT_CUDA(cudaStreamSynchronize(st));
-  if (herr) {
-    dfree(inc_count, st);
-    dfree(wfac, st);
-    return fail(SFT_ERR_MESH, herr == DEV_BAD_INDEX ? "target connectivity index out of range"
-                                                    : "target mesh has a non-positive element");
-  }
+  // no host check here: every later kernel only follows connectivity of
+  // elements whose indices are all in range, and the error flag is read with
+  // the row count below
   SFT_CUDA(dalloc(&off64, (size_t)t->nv + 1, st));
   SFT_CUDA(dalloc(&inc_start, (size_t)t->nv + 1, st));
   SFT_CUDA(dalloc(&inc, (size_t)t->ne * (D + 1), st));
@@ -214,11 +221,11 @@ static sft_status build_target_t(sft_target_s* t, cudaStream_t st, int32_t* d_er
   SFT_CUDA(exclusive_scan_i32_to_i64(inc_count, off64, t->nv, st));
   SFT_CUDA(narrow_i64_to_i32(off64, inc_start, t->nv + 1, st));
   SFT_CUDA(cudaMemsetAsync(inc_count, 0, sizeof(int32_t) * t->nv, st));
-  ::sft::note_launch(), k_inc_fill<D><<<blocks_for(t->ne), 256, 0, st>>>(t->conn, t->ne, inc_start, inc_count, inc_raw,
-                                                                       inc_node);
+  ::sft::note_launch(), k_inc_fill<D><<<blocks_for(t->ne), 256, 0, st>>>(t->conn, t->ne, t->nv, inc_start, inc_count,
+                                                                       inc_raw, inc_node);
   SFT_CUDA(cudaGetLastError());
-  ::sft::note_launch(), k_inc_rank<<<blocks_for(t->ne * (D + 1)), 256, 0, st>>>(inc_start, inc_raw, inc_node,
-                                                                               t->ne * (D + 1), inc);
+  ::sft::note_launch(), k_inc_rank<<<blocks_for(t->ne * (D + 1)), 256, 0, st>>>(inc_start, inc_raw, inc_node, t->nv,
+                                                                               inc);
   SFT_CUDA(cudaGetLastError());
   dfree(inc_raw, st);
   dfree(inc_node, st);
@@ -248,8 +255,17 @@ static sft_status build_target_t(sft_target_s* t, cudaStream_t st, int32_t* d_er
   SFT_CUDA(cudaMemcpyAsync(&nnz, off64 + t->nv, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   SFT_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   SFT_CUDA(cudaStreamSynchronize(st));
-  if (herr) return fail(SFT_ERR_MESH, "target node belongs to more elements than supported");
-  if (nnz >= (int64_t)INT32_MAX) return fail(SFT_ERR_UNSUPPORTED, "mass matrix nnz exceeds 2^31");
+  if (herr || nnz >= (int64_t)INT32_MAX) {
+    dfree(off64, st);
+    dfree(inc_start, st);
+    dfree(inc, st);
+    dfree(inc_count, st);
+    dfree(wfac, st);
+    if (herr == DEV_BAD_INDEX) return fail(SFT_ERR_MESH, "target connectivity index out of range");
+    if (herr == DEV_BAD_ELEMENT) return fail(SFT_ERR_MESH, "target mesh has a non-positive element");
+    if (herr) return fail(SFT_ERR_MESH, "target node belongs to more elements than supported");
+    return fail(SFT_ERR_UNSUPPORTED, "mass matrix nnz exceeds 2^31");
+  }
   t->nnz = nnz;
   SFT_CUDA(dalloc(&t->row_ptr, (size_t)t->nv + 1, st));
   SFT_CUDA(narrow_i64_to_i32(off64, t->row_ptr, t->nv + 1, st));

@@ -254,6 +254,17 @@ def test_invalid_meshes_rejected():
     with pytest.raises(sft.SftError) as ei:
         sft.sft_source_create(nanc, m.conn, m.values)
     assert ei.value.status == 2
+    # a target index out of range: the setup skips the element in every pass
+    # and reports the error once the row counts are read back
+    for v in (m.nnodes, m.nnodes + 1000, -1):
+        badt = m.conn.copy()
+        badt[5, 2] = v
+        with pytest.raises(sft.SftError) as ei:
+            sft.sft_target_create(m.coords, badt)
+        assert ei.value.status == 2
+    # a valid target afterwards on the same stream
+    t = sft.sft_target_create(m.coords, m.conn)
+    t.close()
 
 
 # --------------------------------------------------------------------------
