@@ -212,7 +212,8 @@ sft_status sft_plan_transfer(sft_plan pl, double* u_out, double* b_out, double* 
     u_dev = u_tmp.p;
   }
   SolveResult sr;
-  if (sft_status r = mass_solve(t, nf, b.p, u_dev, o.cg_tol, o.cg_max_iter, st, d_err.p, &sr, o.cg_mode))
+  SolveLate late(st);  // the solve's status is read with the final readback
+  if (sft_status r = mass_solve(t, nf, b.p, u_dev, o.cg_tol, o.cg_max_iter, st, d_err.p, &sr, o.cg_mode, &late))
     return r;
   if (ev.ok) cudaEventRecord(ev.e[4], st);
   const cudaMemcpyKind d2o = o.out_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -230,8 +231,10 @@ sft_status sft_plan_transfer(sft_plan pl, double* u_out, double* b_out, double* 
   }
   int32_t herr = 0;
   SFT_CUDA(cudaMemcpyAsync(&herr, d_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  if (late.pending) SFT_CUDA(cudaMemcpyAsync(late.host, late.buf.p, late.bytes, cudaMemcpyDeviceToHost, st));
   if (ev.ok) cudaEventRecord(ev.e[5], st);
   SFT_CUDA(cudaStreamSynchronize(st));
+  if (sft_status r = finish_solve(late, &sr)) return r;
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
     stats->cg_iters = sr.iters;

@@ -509,7 +509,8 @@ sft_status sft_transfer_surrogate(sft_mlp net, sft_source exact, sft_target t, c
     u_dev = u_tmp.p;
   }
   SolveResult sr;
-  if (sft_status r = mass_solve(t, 1, b.p, u_dev, o->cg_tol, o->cg_max_iter, st, d_err.p, &sr, o->cg_mode))
+  SolveLate late(st);  // the solve's status is read with the final readback
+  if (sft_status r = mass_solve(t, 1, b.p, u_dev, o->cg_tol, o->cg_max_iter, st, d_err.p, &sr, o->cg_mode, &late))
     return r;
   if (ev.ok) cudaEventRecord(ev.e[4], st);
 
@@ -528,8 +529,10 @@ sft_status sft_transfer_surrogate(sft_mlp net, sft_source exact, sft_target t, c
   int32_t herr = 0;
   SFT_CUDA(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
   SFT_CUDA(cudaMemcpyAsync(&herr, d_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  if (late.pending) SFT_CUDA(cudaMemcpyAsync(late.host, late.buf.p, late.bytes, cudaMemcpyDeviceToHost, st));
   if (ev.ok) cudaEventRecord(ev.e[5], st);
   SFT_CUDA(cudaStreamSynchronize(st));
+  if (sft_status r = finish_solve(late, &sr)) return r;
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
     stats->cg_iters = sr.iters;
