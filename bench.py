@@ -495,6 +495,7 @@ def run_online(args):
     def e2e_step():
         sft.sft_source_set_values(S, pin_vals)
         sft.sft_plan_transfer(plan_h, u_out=u_h)
+        sft.sft_conservation_error(S, T, u_h[0])
 
     e2e_step()
     torch.cuda.synchronize()
@@ -536,7 +537,8 @@ def run_online(args):
             "e2e": {"value": queries / (e2e_ms / 1e3), "unit": "queries/s", "ms_per_step": e2e_ms, "steps": k_e2e,
                     "h2d_bytes_per_step": int(pin_vals.numel() * pin_vals.element_size()),
                     "d2h_bytes_per_step": int(u_h.numel() * u_h.element_size()),
-                    "timing": "host wall clock: new source values H2D, online transfer, u D2H"},
+                    "timing": "host wall clock: new source values H2D, online transfer, u D2H, conservation error "
+                              "(the timed step's calls)"},
             "clocks": clk.summary(),
             "gpu_launches": launches * args.steps if launches else None,
         }
