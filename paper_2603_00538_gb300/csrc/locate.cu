@@ -312,6 +312,12 @@ __device__ __forceinline__ bool cell_may_hold(const P* r, const P c[D], const P 
   return !(A::add(A::sub(P(1), tsum), S) < -eps);
 }
 
+// one filled registration: the element and the depth of the cell centre in it,
+// stored together so that the fill writes one scattered entry, not two
+template <typename P> struct RegEntry;
+template <> struct alignas(8) RegEntry<float> { int32_t id; float depth; };
+template <> struct alignas(16) RegEntry<double> { int32_t id; int32_t pad; double depth; };
+
 // one registration per (element, cell) that passes cell_may_hold: count, or
 // fill the element id and the depth of the cell centre in the
 // element (its min barycentric coordinate there, evaluated exactly as a
@@ -319,8 +325,7 @@ __device__ __forceinline__ bool cell_may_hold(const P* r, const P c[D], const P 
 template <int D, typename P, bool FILL>
 __global__ void k_register(const P* __restrict__ x, const int32_t* __restrict__ conn, const P* __restrict__ recs,
                            int64_t nv, int64_t ne, const GridP<P>* __restrict__ gp, int32_t* __restrict__ cell_count,
-                           const int32_t* __restrict__ cell_start, int32_t* __restrict__ items,
-                           P* __restrict__ depth) {
+                           const int32_t* __restrict__ cell_start, RegEntry<P>* __restrict__ reg) {
   constexpr int RL = RecLen<D>::value;
   const GridP<P> g = *gp;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
@@ -356,9 +361,11 @@ __global__ void k_register(const P* __restrict__ x, const int32_t* __restrict__ 
             P mn = mu[0];
 #pragma unroll
             for (int q = 1; q <= D; ++q) mn = mu[q] < mn ? mu[q] : mn;
-            const int64_t at = (int64_t)cell_start[c] + pos;
-            items[at] = (int32_t)e;
-            depth[at] = mn;
+            RegEntry<P> en;
+            if constexpr (sizeof(P) == 8) en.pad = 0;
+            en.id = (int32_t)e;
+            en.depth = mn;
+            reg[(int64_t)cell_start[c] + pos] = en;
           }
         }
   }
@@ -373,8 +380,8 @@ __global__ void k_register(const P* __restrict__ x, const int32_t* __restrict__ 
 // entries), W = 16 the denser ones of 3D grids (measured on the 4,983,504-tet
 // source: source build 3.04 ms against 3.11 with W = 32; W = 4 in 2D: no change).
 template <typename P, int W>
-__global__ void k_cell_rank(const int32_t* __restrict__ cell_start, const int32_t* __restrict__ items,
-                            const P* __restrict__ depth, int64_t ncells, int32_t* __restrict__ out) {
+__global__ void k_cell_rank(const int32_t* __restrict__ cell_start, const RegEntry<P>* __restrict__ reg,
+                            int64_t ncells, int32_t* __restrict__ out) {
   const int lane = threadIdx.x & (W - 1);
   const int64_t grp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
   const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
@@ -390,8 +397,9 @@ __global__ void k_cell_rank(const int32_t* __restrict__ cell_start, const int32_
     P d = P(0);
     int32_t id = 0;
     if (small && lane < n) {
-      d = depth[p0 + lane];
-      id = items[p0 + lane];
+      const RegEntry<P> en = reg[p0 + lane];
+      d = en.depth;
+      id = en.id;
     }
     int32_t rank = 0;
     // every lane of the warp takes part in every shuffle: loop to the largest
@@ -406,13 +414,13 @@ __global__ void k_cell_rank(const int32_t* __restrict__ cell_start, const int32_
       if (lane < n) out[p0 + rank] = id;
     } else {
       for (int32_t p = p0 + lane; p < p1; p += W) {
-        const P dp = depth[p];
-        const int32_t ip = items[p];
+        const RegEntry<P> ep = reg[p];
+        const P dp = ep.depth;
+        const int32_t ip = ep.id;
         int32_t rk = 0;
         for (int32_t q = p0; q < p1; ++q) {
-          const P dq = depth[q];
-          const int32_t iq = items[q];
-          rk += (dq > dp) || (dq == dp && iq < ip);
+          const RegEntry<P> eq = reg[q];
+          rk += (eq.depth > dp) || (eq.depth == dp && eq.id < ip);
         }
         out[p0 + rk] = ip;
       }
@@ -473,7 +481,7 @@ static sft_status build_locator_t(sft_source_s* s, int prec, cudaStream_t st, in
   SFT_CUDA(dalloc(&start64, (size_t)L.ncells + 1, st));
   SFT_CUDA(cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * L.ncells, st));
   ::sft::note_launch(), k_register<D, P, false><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, recs, s->nv, s->ne, g, cell_count,
-                                                                               nullptr, nullptr, nullptr);
+                                                                               nullptr, nullptr);
   SFT_CUDA(cudaGetLastError());
   SFT_CUDA(exclusive_scan_i32_to_i64(cell_count, start64, L.ncells, st));
   int32_t herr = 0;
@@ -493,25 +501,22 @@ static sft_status build_locator_t(sft_source_s* s, int prec, cudaStream_t st, in
   SFT_CUDA(narrow_i64_to_i32(start64, L.cell_start, L.ncells + 1, st));
   dfree(start64, st);
   // fill (arbitrary order within a cell), then order each cell
-  int32_t* items = nullptr;
-  P* depth = nullptr;
-  SFT_CUDA(dalloc(&items, (size_t)total, st));
-  SFT_CUDA(dalloc(&depth, (size_t)total, st));
+  RegEntry<P>* reg = nullptr;
+  SFT_CUDA(dalloc(&reg, (size_t)total, st));
   SFT_CUDA(dalloc(&L.cell_items, (size_t)total, st));
   SFT_CUDA(cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * L.ncells, st));
   ::sft::note_launch(), k_register<D, P, true><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, recs, s->nv, s->ne, g, cell_count,
-                                                                              L.cell_start, items, depth);
+                                                                              L.cell_start, reg);
   SFT_CUDA(cudaGetLastError());
-  if (D == 3)  // measured: 32 lanes per cell in 3D, 8 in 2D
-    ::sft::note_launch(), k_cell_rank<P, 16><<<grid_for(L.ncells * 16), 256, 0, st>>>(L.cell_start, items, depth,
-                                                                                     L.ncells, L.cell_items);
+  if (D == 3)  // measured: 16 lanes per cell in 3D, 8 in 2D
+    ::sft::note_launch(), k_cell_rank<P, 16><<<grid_for(L.ncells * 16), 256, 0, st>>>(L.cell_start, reg, L.ncells,
+                                                                                     L.cell_items);
   else
-    ::sft::note_launch(), k_cell_rank<P, 8><<<grid_for(L.ncells * 8), 256, 0, st>>>(L.cell_start, items, depth,
-                                                                                   L.ncells, L.cell_items);
+    ::sft::note_launch(), k_cell_rank<P, 8><<<grid_for(L.ncells * 8), 256, 0, st>>>(L.cell_start, reg, L.ncells,
+                                                                                   L.cell_items);
   SFT_CUDA(cudaGetLastError());
   dfree(cell_count, st);
-  dfree(items, st);
-  dfree(depth, st);
+  dfree(reg, st);
   L.built = true;
   return SFT_OK;
 }
