@@ -118,15 +118,33 @@ __global__ void k_mass_rows(const int32_t* __restrict__ conn, const double2* __r
     int cnt = 0;
     bool overflow = false;
     double lump = 0.0;
-    for (int32_t p = inc_start[i]; p < inc_start[i + 1]; ++p) {
-      const int32_t e = inc[p];
-      const double2 wf = __ldg(wfac + e);
+    // incident elements in chunks of kPre: their connectivity and factors are
+    // loaded first (independent loads in flight together), then merged in
+    // incidence order (the same sums as one element at a time)
+    constexpr int kPre = 4;
+    const int32_t p_end = inc_start[i + 1];
+    for (int32_t p0 = inc_start[i]; p0 < p_end; p0 += kPre) {
+      int32_t ce[kPre][D + 1];
+      double2 wv[kPre];
+#pragma unroll
+      for (int u = 0; u < kPre; ++u) {
+        if (p0 + u < p_end) {
+          const int32_t e = __ldg(inc + p0 + u);
+          wv[u] = __ldg(wfac + e);
+#pragma unroll
+          for (int m = 0; m <= D; ++m) ce[u][m] = __ldg(conn + (int64_t)e * (D + 1) + m);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kPre; ++u) {
+      if (p0 + u >= p_end) break;
+      const double2 wf = wv[u];
       lump += wf.y;
       // 2 RN(w/den) == RN(2w/den): same values as dividing each entry
       const double wd = wf.x;
 #pragma unroll
       for (int m = 0; m <= D; ++m) {
-        const int32_t j = conn[(int64_t)e * (D + 1) + m];
+        const int32_t j = ce[u][m];
         const double c = j == i ? 2.0 * wd : wd;
         int q = 0;
         while (q < cnt && cols[q] < j) ++q;
@@ -140,6 +158,7 @@ __global__ void k_mass_rows(const int32_t* __restrict__ conn, const double2* __r
         } else {
           overflow = true;
         }
+      }
       }
     }
     if (overflow) set_error(err, DEV_VALENCE);
