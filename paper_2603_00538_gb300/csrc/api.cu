@@ -124,6 +124,7 @@ void sft_source_destroy(sft_source s) {
   if (s->coords) cudaFreeAsync(s->coords, st);
   if (s->conn) cudaFreeAsync(s->conn, st);
   if (s->values) cudaFreeAsync(s->values, st);
+  if (s->evol) cudaFreeAsync(s->evol, st);
   delete s;
 }
 

@@ -89,6 +89,7 @@ struct sft_source_s {
   void* coords = nullptr;       // [nv][dim] input dtype
   int32_t* conn = nullptr;      // [ne][dim+1]
   void* values = nullptr;       // [nf][nv] input dtype
+  double* evol = nullptr;       // [ne] FP64 element measures (made with the first locator)
   double integral[sft::kMaxFields] = {0};
   bool integral_valid = false;  // integral[] matches the current values (made on first use)
   sft::Locator loc[2];          // index = sft_precision (0 FP64, 1 FP32)

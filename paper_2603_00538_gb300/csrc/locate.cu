@@ -238,7 +238,8 @@ __device__ __forceinline__ bool record_map(const P xv[D + 1][D], P* r) {
 
 template <int D, typename P, typename TV>
 __global__ void k_records(const P* __restrict__ x, const int32_t* __restrict__ conn, const TV* __restrict__ values,
-                          int64_t nv, int64_t ne, int nf, P* __restrict__ recs, P* __restrict__ vals, int32_t* err) {
+                          int64_t nv, int64_t ne, int nf, P* __restrict__ recs, P* __restrict__ vals, int32_t* err,
+                          double* __restrict__ evol) {
   constexpr int L = RecLen<D>::value;
   
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
@@ -263,6 +264,25 @@ __global__ void k_records(const P* __restrict__ x, const int32_t* __restrict__ c
     if (!record_map<D, P>(xv, r)) set_error(err, DEV_BAD_ELEMENT);
 #pragma unroll
     for (int q = 0; q < L; ++q) recs[e * L + q] = r[q];
+    if (evol) {
+      // FP64 measure of the element (exact differences of the stored coordinates)
+      double xd[D + 1][D];
+#pragma unroll
+      for (int m = 0; m <= D; ++m)
+#pragma unroll
+        for (int a = 0; a < D; ++a) xd[m][a] = f2d(xv[m][a]);
+      double vol;
+      if constexpr (D == 2) {
+        vol = 0.5 * ((xd[1][0] - xd[0][0]) * (xd[2][1] - xd[0][1]) - (xd[2][0] - xd[0][0]) * (xd[1][1] - xd[0][1]));
+      } else {
+        double e1[3], e2[3], e3[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) { e1[a] = xd[1][a] - xd[0][a]; e2[a] = xd[2][a] - xd[0][a]; e3[a] = xd[3][a] - xd[0][a]; }
+        vol = (e1[0] * (e2[1] * e3[2] - e2[2] * e3[1]) - e1[1] * (e2[0] * e3[2] - e2[2] * e3[0]) +
+               e1[2] * (e2[0] * e3[1] - e2[1] * e3[0])) * (1.0 / 6.0);
+      }
+      evol[e] = vol;
+    }
     for (int f = 0; f < nf; ++f) {
 #pragma unroll
       for (int m = 0; m < 4; ++m)
@@ -467,12 +487,19 @@ static sft_status build_locator_t(sft_source_s* s, int prec, cudaStream_t st, in
   SFT_CUDA(dalloc(&vals, (size_t)s->nf * s->ne * 4, st));
   L.recs = recs;
   L.vals = vals;
+  // the first locator (the source's own precision, at create) also records
+  // every element's FP64 measure for the source integrals
+  double* evol = nullptr;
+  if (!s->evol) {
+    SFT_CUDA(dalloc(&s->evol, (size_t)s->ne, st));
+    evol = s->evol;
+  }
   if (s->dtype == SFT_F64)
     ::sft::note_launch(), k_records<D, P, double><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, (const double*)s->values, s->nv, s->ne,
-                                                             s->nf, recs, vals, d_err);
+                                                             s->nf, recs, vals, d_err, evol);
   else
     ::sft::note_launch(), k_records<D, P, float><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, (const float*)s->values, s->nv, s->ne,
-                                                            s->nf, recs, vals, d_err);
+                                                            s->nf, recs, vals, d_err, evol);
   SFT_CUDA(cudaGetLastError());
   // count registrations per cell, then total (int64) -> int32 offsets must suffice
   int32_t* cell_count = nullptr;
@@ -650,29 +677,16 @@ sft_status locate_points(sft_source_s* s, int prec, int64_t n, const void* pts, 
 // exact P1 integral of every source field: sum_e |e| mean(f over vertices)
 // ---------------------------------------------------------------------------
 template <int D, typename TI>
-__global__ void k_p1_integral_partial(const TI* __restrict__ x, const int32_t* __restrict__ conn,
+__global__ void k_p1_integral_partial(const double* __restrict__ evol, const int32_t* __restrict__ conn,
                                       const TI* __restrict__ values, int64_t nv, int64_t ne, int nf,
                                       double* __restrict__ part) {
   double acc[kMaxFields];
   for (int f = 0; f < kMaxFields; ++f) acc[f] = 0.0;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
-    double xv[D + 1][D];
     int32_t v[D + 1];
 #pragma unroll
-    for (int m = 0; m <= D; ++m) {
-      v[m] = conn[e * (D + 1) + m];
-#pragma unroll
-      for (int a = 0; a < D; ++a) xv[m][a] = f2d(x[(int64_t)v[m] * D + a]);
-    }
-    double vol;
-    if constexpr (D == 2) {
-      vol = 0.5 * ((xv[1][0] - xv[0][0]) * (xv[2][1] - xv[0][1]) - (xv[2][0] - xv[0][0]) * (xv[1][1] - xv[0][1]));
-    } else {
-      double e1[3], e2[3], e3[3];
-      for (int a = 0; a < 3; ++a) { e1[a] = xv[1][a] - xv[0][a]; e2[a] = xv[2][a] - xv[0][a]; e3[a] = xv[3][a] - xv[0][a]; }
-      vol = (e1[0] * (e2[1] * e3[2] - e2[2] * e3[1]) - e1[1] * (e2[0] * e3[2] - e2[2] * e3[0]) +
-             e1[2] * (e2[0] * e3[1] - e2[1] * e3[0])) * (1.0 / 6.0);
-    }
+    for (int m = 0; m <= D; ++m) v[m] = __ldg(conn + e * (D + 1) + m);
+    const double vol = __ldg(evol + e);
     // sum |e| (f_0 + ... + f_d); the 1 / (d + 1) is applied once per thread
     for (int f = 0; f < nf; ++f) {
       double m = 0.0;
@@ -700,12 +714,13 @@ __global__ void k_p1_integral_partial(const TI* __restrict__ x, const int32_t* _
 
 sft_status source_integrals_launch(sft_source_s* s, double* part, cudaStream_t st) {
   const unsigned nb = kIntegralBlocks;
+  if (!s->evol) return fail(SFT_ERR_ARG, "source has no element measures");
   if (s->dim == 2) {
-    if (s->dtype == SFT_F64) ::sft::note_launch(), k_p1_integral_partial<2, double><<<nb, 256, 0, st>>>((const double*)s->coords, s->conn, (const double*)s->values, s->nv, s->ne, s->nf, part);
-    else ::sft::note_launch(), k_p1_integral_partial<2, float><<<nb, 256, 0, st>>>((const float*)s->coords, s->conn, (const float*)s->values, s->nv, s->ne, s->nf, part);
+    if (s->dtype == SFT_F64) ::sft::note_launch(), k_p1_integral_partial<2, double><<<nb, 256, 0, st>>>(s->evol, s->conn, (const double*)s->values, s->nv, s->ne, s->nf, part);
+    else ::sft::note_launch(), k_p1_integral_partial<2, float><<<nb, 256, 0, st>>>(s->evol, s->conn, (const float*)s->values, s->nv, s->ne, s->nf, part);
   } else {
-    if (s->dtype == SFT_F64) ::sft::note_launch(), k_p1_integral_partial<3, double><<<nb, 256, 0, st>>>((const double*)s->coords, s->conn, (const double*)s->values, s->nv, s->ne, s->nf, part);
-    else ::sft::note_launch(), k_p1_integral_partial<3, float><<<nb, 256, 0, st>>>((const float*)s->coords, s->conn, (const float*)s->values, s->nv, s->ne, s->nf, part);
+    if (s->dtype == SFT_F64) ::sft::note_launch(), k_p1_integral_partial<3, double><<<nb, 256, 0, st>>>(s->evol, s->conn, (const double*)s->values, s->nv, s->ne, s->nf, part);
+    else ::sft::note_launch(), k_p1_integral_partial<3, float><<<nb, 256, 0, st>>>(s->evol, s->conn, (const float*)s->values, s->nv, s->ne, s->nf, part);
   }
   SFT_CUDA(cudaGetLastError());
   return SFT_OK;
