@@ -236,7 +236,14 @@ __global__ void __launch_bounds__(kSolveThreads) k_pcg(const int32_t* __restrict
 // The FP64 pipe does one SpMV per cycle (2 to 3 cycles) instead of one per
 // iteration. Every block takes every decision from the same fixed-order
 // reductions; the stopping test uses the true FP64 residual.
-constexpr float kEtaFloor = 1e-5f;
+// smallest inner reduction asked of one FP32 solve (measured: 1e-5 gives
+// 0.71 / 0.68 ms on the 1.0 M-row 2D / 0.5 M-row 3D systems, 3e-6 and 1e-6
+// 0.74 / 0.71 ms: deeper FP32 solves cost more iterations than the extra
+// refinement cycle they save)
+#ifndef SFT_MIX_ETA_FLOOR
+#define SFT_MIX_ETA_FLOOR 1e-5f
+#endif
+constexpr float kEtaFloor = SFT_MIX_ETA_FLOOR;
 #ifndef SFT_MIX_ROWS_PER_THREAD
 #define SFT_MIX_ROWS_PER_THREAD 3
 #endif
