@@ -105,7 +105,10 @@ __global__ void k_inc_rank(const int32_t* __restrict__ inc_start, const int32_t*
 // the row itself into a fixed-stride staging array, so that the second pass
 // only copies), FILL=true writes columns, values, the Jacobi inverse diagonal
 // and the lumped mass.
-template <int D, bool FILL>
+// CAP bounds the row buffers (local memory per thread); a counting pass with
+// CAP < kMaxRow marks the rows that do not fit (row_len = -1) and a second
+// pass with REDO = true and CAP = kMaxRow builds exactly those.
+template <int D, bool FILL, int CAP = kMaxRow, bool REDO = false>
 __global__ void k_mass_rows(const int32_t* __restrict__ conn, const double2* __restrict__ wfac,
                             const int32_t* __restrict__ inc_start, const int32_t* __restrict__ inc, int64_t nv,
                             int32_t* __restrict__ row_len, const int32_t* __restrict__ row_ptr,
@@ -113,8 +116,9 @@ __global__ void k_mass_rows(const int32_t* __restrict__ conn, const double2* __r
                             double* __restrict__ lumped, int32_t* err, int32_t* __restrict__ tmp_col,
                             double* __restrict__ tmp_val, double* __restrict__ tmp_lump) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
-    int32_t cols[kMaxRow];
-    double vals[kMaxRow];
+    if (REDO && row_len[i] >= 0) continue;
+    int32_t cols[CAP];
+    double vals[CAP];
     int cnt = 0;
     bool overflow = false;
     double lump = 0.0;
@@ -150,7 +154,7 @@ __global__ void k_mass_rows(const int32_t* __restrict__ conn, const double2* __r
         while (q < cnt && cols[q] < j) ++q;
         if (q < cnt && cols[q] == j) {
           vals[q] += c;
-        } else if (cnt < kMaxRow) {
+        } else if (cnt < CAP) {
           for (int r = cnt; r > q; --r) { cols[r] = cols[r - 1]; vals[r] = vals[r - 1]; }
           cols[q] = j;
           vals[q] = c;
@@ -161,7 +165,13 @@ __global__ void k_mass_rows(const int32_t* __restrict__ conn, const double2* __r
       }
       }
     }
-    if (overflow) set_error(err, DEV_VALENCE);
+    if (overflow) {
+      if (CAP < kMaxRow) {  // this row is built again with the full buffers
+        row_len[i] = -1;
+        continue;
+      }
+      set_error(err, DEV_VALENCE);
+    }
     if (!FILL) {
       row_len[i] = cnt;
       if (tmp_col) {
@@ -265,7 +275,14 @@ static sft_status build_target_t(sft_target_s* t, cudaStream_t st, int32_t* d_er
       cudaGetLastError();  // no staging: the second pass merges again
     }
   }
-  ::sft::note_launch(), k_mass_rows<D, false><<<blocks_for(t->nv), 256, 0, st>>>(t->conn, wfac, inc_start, inc, t->nv, row_len, nullptr,
+  // rows of up to 16 (2D) / 32 (3D) entries in small buffers, the rest again
+  // with the full ones (measured: the full-size buffers spill to L2)
+  constexpr int kCapSmall = D == 2 ? 16 : 32;
+  ::sft::note_launch(), k_mass_rows<D, false, kCapSmall><<<blocks_for(t->nv), 256, 0, st>>>(t->conn, wfac, inc_start, inc, t->nv, row_len, nullptr,
+                                                           nullptr, nullptr, nullptr, nullptr, d_err, tmp_col,
+                                                           tmp_val, tmp_lump);
+  SFT_CUDA(cudaGetLastError());
+  ::sft::note_launch(), k_mass_rows<D, false, kMaxRow, true><<<blocks_for(t->nv), 256, 0, st>>>(t->conn, wfac, inc_start, inc, t->nv, row_len, nullptr,
                                                            nullptr, nullptr, nullptr, nullptr, d_err, tmp_col,
                                                            tmp_val, tmp_lump);
   SFT_CUDA(cudaGetLastError());

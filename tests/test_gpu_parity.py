@@ -108,6 +108,57 @@ def test_mass_matrix_parity(orc, dim):
     assert np.max(np.abs(lump - orc.lumped_mass(m.coords, m.conn))) <= 1e-15
 
 
+def _fan_2d(k=24):
+    ang = 2 * np.pi * np.arange(k) / k
+    coords = np.vstack([[0.0, 0.0], np.stack([np.cos(ang), np.sin(ang)], 1)])
+    conn = np.array([[0, 1 + i, 1 + (i + 1) % k] for i in range(k)], np.int32)
+    return W.Mesh(coords, conn, None)
+
+
+def _star_3d():
+    """Tetrahedra joining the centre to the faces of a once-subdivided
+    icosahedron (80 faces, 42 surface nodes): the centre's row has 43 entries."""
+    t = (1 + 5 ** 0.5) / 2
+    v = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t), (0, -1, -t), (0, 1, -t),
+         (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    v = [np.array(p, float) / np.linalg.norm(p) for p in v]
+    f = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2), (10, 7, 6),
+         (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10),
+         (8, 6, 7), (9, 8, 1)]
+    mid = {}
+
+    def m(a, b):
+        key = (min(a, b), max(a, b))
+        if key not in mid:
+            p = v[a] + v[b]
+            v.append(p / np.linalg.norm(p))
+            mid[key] = len(v) - 1
+        return mid[key]
+    faces = []
+    for a, b, c in f:
+        ab, bc, ca = m(a, b), m(b, c), m(c, a)
+        faces += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+    coords = np.vstack([[0.0, 0.0, 0.0], np.array(v)])
+    conn = np.array([[0, 1 + a, 1 + b, 1 + c] for a, b, c in faces], np.int32)
+    mesh = W.Mesh(coords, conn, None)
+    W._fix_orientation(mesh)
+    return mesh
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_mass_matrix_high_valence(orc, dim):
+    """Rows longer than the small per-thread buffers of the first counting
+    pass (16 entries in 2D, 32 in 3D) are built again with the full ones."""
+    m = _fan_2d() if dim == 2 else _star_3d()
+    rp_o, col_o, val_o = orc.mass_csr(m.coords, m.conn)
+    assert np.diff(rp_o).max() > (16 if dim == 2 else 32)
+    t = sft.mesh_target(m, device=DEV)
+    rp, col, val, lump = sft.sft_target_mass(t)
+    assert np.array_equal(rp, rp_o) and np.array_equal(col, col_o)
+    assert np.max(np.abs(val - val_o)) <= 1e-15 * np.max(np.abs(val_o))
+    assert np.max(np.abs(lump - orc.lumped_mass(m.coords, m.conn))) <= 1e-15
+
+
 @pytest.mark.parametrize("dim,nrhs", [(2, 1), (2, 3), (3, 2)])
 def test_mass_solve_parity(orc, dim, nrhs):
     """Given the same b, the FP64 CG solutions agree to 1e-10 (tol 1e-13)."""
