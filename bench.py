@@ -574,7 +574,8 @@ def run_roundtrip(args):
     s2, t2 = sft.mesh_source(m2, device=dev), sft.mesh_target(m2, device=dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    rt = sft.RoundTrip(s1, t1, s2, t2, N, seeds=(0, 1), cg_tol=tol, sampling=_sampling(args))
+    rt = sft.RoundTrip(s1, t1, s2, t2, N, seeds=(0, 1), cg_tol=tol, sampling=_sampling(args),
+                       warm_start=not args.cold_start)
     torch.cuda.synchronize()
     plan_s = time.perf_counter() - t0
     ref = torch.as_tensor(np.ascontiguousarray(m1.values)).to(dev)
@@ -650,6 +651,7 @@ def run_roundtrip(args):
             "config": {"workload": f"roundtrip: {WORKLOADS['roundtrip']}", "queries_per_step": queries,
                        "mesh1_elements": m1.nelems, "mesh2_elements": m2.nelems, "samples_per_elem": N,
                        "sampling": args.sampling, "plan_create_s": plan_s,
+                       "solve_start": "zero" if args.cold_start else "each leg's previous result (warm start)",
                        "l2": "flushed between steps (256 MB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "breakdown_ms": {"round_trip_min": min(step_ms), "round_trip_max": max(step_ms)},
@@ -1047,6 +1049,8 @@ def main():
                     help="source grid cells per axis = int(L * nelems^(1/d)) (tri4m / tet5m)")
     ap.add_argument("--sampling", choices=["uniform", "stratified"], default="uniform",
                     help="sample scheme of the mesh-source workloads (tri4m, tet5m and their online forms)")
+    ap.add_argument("--cold-start", action="store_true",
+                    help="roundtrip: start every solve from 0 instead of the leg's previous result")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="element-count scale of the workload (1 = the named workload)")
     args = ap.parse_args()

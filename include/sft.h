@@ -103,7 +103,10 @@ typedef struct {
     int32_t field_count;        /* 0: every source field; k > 0: the first k fields only */
     int32_t cg_mode;            /* sft_cg_mode (0: mixed-precision refinement) */
     int32_t sampling;           /* sft_sampling (0: uniform) */
-    int32_t reserved;           /* must be 0 */
+    int32_t cg_warm_start;      /* 1: the solve starts from the values u_out holds (the previous
+                                   transfer's result, say) instead of 0; needs cg_mode MIXED.
+                                   The stopping test is unchanged (true FP64 residual relative
+                                   to ||b||), so the result meets the same tolerance. */
 } sft_options;
 
 typedef struct {

@@ -49,7 +49,7 @@ class sft_options(ctypes.Structure):
                 ("alpha", ctypes.c_double), ("cg_tol", ctypes.c_double), ("strict_inside", ctypes.c_int32),
                 ("out_device", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
                 ("sample_elem_out", ctypes.c_void_p), ("field_count", ctypes.c_int32),
-                ("cg_mode", ctypes.c_int32), ("sampling", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("cg_mode", ctypes.c_int32), ("sampling", ctypes.c_int32), ("cg_warm_start", ctypes.c_int32)]
 
 
 class sft_stats(ctypes.Structure):
@@ -281,7 +281,7 @@ def sft_transfer(src: Source, tgt: Target, samples_per_elem: int, precision: int
                  seed: int = 0, stream_id: int = 0, alpha: float = 1.0, cg_tol: float = 1e-10,
                  cg_max_iter: int = 1000, strict_inside: bool = False, u_out=None, b_out=None, g_out=None,
                  sample_elem_out=None, stream=None, allow_not_converged: bool = False, field_count: int = 0,
-                 cg_mode: int = SFT_CG_MIXED, sampling: int = SFT_SAMPLING_UNIFORM):
+                 cg_mode: int = SFT_CG_MIXED, sampling: int = SFT_SAMPLING_UNIFORM, cg_warm_start: bool = False):
     """Run one transfer. Outputs are caller-provided arrays (numpy for host,
     torch CUDA tensors for device); when u_out is None a host array
     [nfields, nnodes] is allocated. Returns (status, stats dict, u_out)."""
@@ -310,6 +310,7 @@ def sft_transfer(src: Source, tgt: Target, samples_per_elem: int, precision: int
     o.field_count = int(field_count)
     o.cg_mode = int(cg_mode)
     o.sampling = int(sampling)
+    o.cg_warm_start = int(bool(cg_warm_start))
     st = sft_stats()
     allow = (SFT_OK, SFT_ERR_NOT_CONVERGED) if allow_not_converged else (SFT_OK,)
     status = _check(lib().sft_transfer(src.h, tgt.h, ctypes.byref(o), up, bp, gp, ctypes.byref(st)),
@@ -324,12 +325,13 @@ class Plan(_Handle):
 def sft_plan_create(src: Source, tgt: Target, samples_per_elem: int, precision: int = SFT_PREC_FP32, seed: int = 0,
                     stream_id: int = 0, alpha: float = 1.0, cg_tol: float = 1e-10, cg_max_iter: int = 1000,
                     field_count: int = 0, out_device: bool = False, strict_inside: bool = False,
-                    stream=None, cg_mode: int = SFT_CG_MIXED, sampling: int = SFT_SAMPLING_UNIFORM) -> Plan:
+                    stream=None, cg_mode: int = SFT_CG_MIXED, sampling: int = SFT_SAMPLING_UNIFORM,
+                    cg_warm_start: bool = False) -> Plan:
     """Initialization of a transfer between fixed meshes (node and sample
     locations recorded); outputs of later transfers go to host arrays, or to
     CUDA tensors with out_device=True."""
     o = _options(samples_per_elem, seed, stream_id, alpha, cg_tol, cg_max_iter, field_count, precision, cg_mode,
-                 sampling)
+                 sampling, cg_warm_start)
     o.out_device = int(bool(out_device))
     o.strict_inside = int(bool(strict_inside))
     o.cuda_stream = stream if stream is not None else _current_stream()
@@ -420,7 +422,8 @@ class Batch(_Handle):
 
 
 def _options(samples_per_elem, seed=0, stream_id=0, alpha=1.0, cg_tol=1e-10, cg_max_iter=1000,
-             field_count=0, precision=SFT_PREC_FP32, cg_mode=SFT_CG_MIXED, sampling=SFT_SAMPLING_UNIFORM):
+             field_count=0, precision=SFT_PREC_FP32, cg_mode=SFT_CG_MIXED, sampling=SFT_SAMPLING_UNIFORM,
+             cg_warm_start=False):
     o = sft_options()
     o.samples_per_elem = int(samples_per_elem)
     o.precision = int(precision)
@@ -432,6 +435,7 @@ def _options(samples_per_elem, seed=0, stream_id=0, alpha=1.0, cg_tol=1e-10, cg_
     o.field_count = int(field_count)
     o.cg_mode = int(cg_mode)
     o.sampling = int(sampling)
+    o.cg_warm_start = int(bool(cg_warm_start))
     return o
 
 
@@ -478,16 +482,19 @@ class RoundTrip:
     iterative analysis of Sec. 5) through two transfer plans (initialization
     once; every round trip reuses the recorded samples). src1/tgt1 and
     src2/tgt2 are the same meshes as sources (one FP64 field) and targets.
-    run(f, iters) maps the CUDA tensor f [1, nnodes1] (float64) in place."""
+    run(f, iters) maps the CUDA tensor f [1, nnodes1] (float64) in place.
+    warm_start: each leg's solve starts from that leg's previous result (the
+    field it is about to overwrite) instead of 0."""
 
     def __init__(self, src1: Source, tgt1: Target, src2: Source, tgt2: Target, samples_per_elem: int,
                  precision: int = SFT_PREC_FP32, seeds=(0, 1), alpha: float = 1.0, cg_tol: float = 1e-10,
-                 cg_max_iter: int = 1000, sampling: int = SFT_SAMPLING_UNIFORM, cg_mode: int = SFT_CG_MIXED):
+                 cg_max_iter: int = 1000, sampling: int = SFT_SAMPLING_UNIFORM, cg_mode: int = SFT_CG_MIXED,
+                 warm_start: bool = False):
         import torch
         if _nf(src1) != 1 or _nf(src2) != 1:
             raise ValueError("round-trip sources carry exactly one field")
         kw = dict(alpha=alpha, cg_tol=cg_tol, cg_max_iter=cg_max_iter, out_device=True, sampling=sampling,
-                  cg_mode=cg_mode)
+                  cg_mode=cg_mode, cg_warm_start=warm_start)
         self.src1, self.src2 = src1, src2
         self.p12 = sft_plan_create(src1, tgt2, samples_per_elem, precision, seed=seeds[0], **kw)
         self.p21 = sft_plan_create(src2, tgt1, samples_per_elem, precision, seed=seeds[1], **kw)
@@ -602,7 +609,7 @@ def sft_transfer_surrogate(net, exact, tgt: Target, samples_per_elem: int, seed:
                            tau: float = 0.0, exact_field: int = 0, u_out=None, b_out=None, g_out=None,
                            fallback_out=None, sample_f_out=None, strict_inside: bool = False, stream=None,
                            allow_not_converged: bool = False, cg_mode: int = SFT_CG_MIXED,
-                           sampling: int = SFT_SAMPLING_UNIFORM):
+                           sampling: int = SFT_SAMPLING_UNIFORM, cg_warm_start: bool = False):
     """Transfer with the surrogate network `net` (Mlp or None) backed by the
     exact source `exact` (Source or None). Outputs as sft_transfer (numpy for
     host, CUDA tensors for device). Returns (status, stats dict, u_out)."""
@@ -613,7 +620,8 @@ def sft_transfer_surrogate(net, exact, tgt: Target, samples_per_elem: int, seed:
     for p, dv, _ in ptrs:
         if p is not None and dv != udev:
             raise ValueError("all outputs must be host arrays or all device tensors")
-    o = _options(samples_per_elem, seed, stream_id, alpha, cg_tol, cg_max_iter, cg_mode=cg_mode, sampling=sampling)
+    o = _options(samples_per_elem, seed, stream_id, alpha, cg_tol, cg_max_iter, cg_mode=cg_mode, sampling=sampling,
+                 cg_warm_start=cg_warm_start)
     o.strict_inside = int(bool(strict_inside))
     o.out_device = int(udev)
     o.cuda_stream = stream if stream is not None else _current_stream()

@@ -1310,6 +1310,7 @@ sft_status sft_batch_create(int32_t nreq, const sft_source* srcs, const sft_targ
     if (o.cg_mode != SFT_CG_MIXED && o.cg_mode != SFT_CG_FP64) return fail(SFT_ERR_ARG, "unknown cg_mode");
     if (o.sampling != SFT_SAMPLING_UNIFORM && o.sampling != SFT_SAMPLING_STRATIFIED)
       return fail(SFT_ERR_ARG, "unknown sampling scheme");
+    if (o.cg_warm_start) return fail(SFT_ERR_UNSUPPORTED, "batched transfers start every solve from 0");
     if (o.sampling == SFT_SAMPLING_STRATIFIED && o.samples_per_elem > kMaxStratifiedN)
       return fail(SFT_ERR_UNSUPPORTED, "stratified sampling supports at most 2^20 samples per element");
     if (o.field_count < 0 || o.field_count > srcs[r]->nf) return fail(SFT_ERR_ARG, "field_count out of range");

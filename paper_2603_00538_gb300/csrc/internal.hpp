@@ -169,7 +169,7 @@ sft_status finish_solve(const SolveLate& late, SolveResult* res);
 // cg_mode: SFT_CG_MIXED (FP64 refinement around FP32 CG) or SFT_CG_FP64
 sft_status mass_solve(sft_target_s* t, int nrhs, const double* b, double* x, double tol, int max_iter,
                       cudaStream_t st, int32_t* d_err, SolveResult* res, int cg_mode = SFT_CG_MIXED,
-                      SolveLate* late = nullptr);
+                      SolveLate* late = nullptr, int warm = 0);
 // S = diag(M)^-1/2 and the FP32 values of S M S on the target (made once, cached)
 sft_status scaled_matrix(sft_target_s* t, cudaStream_t st);
 sft_status weighted_sum(const double* w, const double* u, int64_t n, double* out_host, cudaStream_t st);

@@ -72,6 +72,8 @@ sft_status sft_plan_create(sft_source s, sft_target t, const sft_options* o, sft
   if (o->cg_mode != SFT_CG_MIXED && o->cg_mode != SFT_CG_FP64) return fail(SFT_ERR_ARG, "unknown cg_mode");
   if (o->sampling != SFT_SAMPLING_UNIFORM && o->sampling != SFT_SAMPLING_STRATIFIED)
     return fail(SFT_ERR_ARG, "unknown sampling scheme");
+  if (o->cg_warm_start != 0 && o->cg_warm_start != 1) return fail(SFT_ERR_ARG, "cg_warm_start must be 0 or 1");
+  if (o->cg_warm_start && o->cg_mode != SFT_CG_MIXED) return fail(SFT_ERR_UNSUPPORTED, "a warm start needs cg_mode MIXED");
   if (o->sampling == SFT_SAMPLING_STRATIFIED && o->samples_per_elem > kMaxStratifiedN)
     return fail(SFT_ERR_UNSUPPORTED, "stratified sampling supports at most 2^20 samples per element");
   if (o->field_count < 0 || o->field_count > s->nf) return fail(SFT_ERR_ARG, "field_count out of range");
@@ -210,10 +212,13 @@ sft_status sft_plan_transfer(sft_plan pl, double* u_out, double* b_out, double* 
   if (!o.out_device) {
     SFT_CUDA(u_tmp.alloc((size_t)nv * nf));
     u_dev = u_tmp.p;
+    if (o.cg_warm_start)
+      SFT_CUDA(cudaMemcpyAsync(u_dev, u_out, sizeof(double) * nv * nf, cudaMemcpyHostToDevice, st));
   }
   SolveResult sr;
   SolveLate late(st);  // the solve's status is read with the final readback
-  if (sft_status r = mass_solve(t, nf, b.p, u_dev, o.cg_tol, o.cg_max_iter, st, d_err.p, &sr, o.cg_mode, &late))
+  if (sft_status r = mass_solve(t, nf, b.p, u_dev, o.cg_tol, o.cg_max_iter, st, d_err.p, &sr, o.cg_mode, &late,
+                                o.cg_warm_start))
     return r;
   if (ev.ok) cudaEventRecord(ev.e[4], st);
   const cudaMemcpyKind d2o = o.out_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;

@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) k_mixed_cg(
     const int32_t* __restrict__ rp, const int32_t* __restrict__ col, const double* __restrict__ val,
     const float* __restrict__ aval, const double* __restrict__ sc, int64_t n, int nrhs,
     const double* __restrict__ b, double* x, double* t, float* r, float* p, float* q, float* y, double* partd,
-    float* partf, MixCtl* ctl, double tol, int max_iter) {
+    float* partf, MixCtl* ctl, double tol, int max_iter, int warm) {
   __shared__ double totd[kMaxFields * 2];
   __shared__ float totf[NR];
   __shared__ double bnorm[NR], prev[NR], sig[NR], isig[NR];
@@ -357,15 +357,35 @@ __global__ void __launch_bounds__(kSolveThreads, 4) k_mixed_cg(
   }
   __syncthreads();
   int it = 0, cyc = 0;
+  if (warm) {
+    // warm start from the x given: ||b|| for the stopping test first
+    double v[NR][2];
+#pragma unroll
+    for (int f = 0; f < NR; ++f) v[f][0] = v[f][1] = 0.0;
+    for (int64_t i = tid; i < n; i += nthreads) {
+#pragma unroll
+      for (int f = 0; f < NR; ++f) {
+        if (f >= nrhs) break;
+        const double bi = b[(int64_t)f * n + i];
+        v[f][0] += bi * bi;
+      }
+    }
+    block_partials_d<NR>(v, nrhs, partd);
+    if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+    reduce_partials(partd, nb, nrhs, totd);
+    if (threadIdx.x == 0)
+      for (int f = 0; f < nrhs; ++f) bnorm[f] = sqrt(totd[2 * f]);
+    __syncthreads();
+  }
   for (;; ++cyc) {
-    // R: true residual in FP64 (x = 0 in the first cycle)
+    // R: true residual in FP64 (x = 0 in the first cycle unless warm)
     double v[NR][2];
 #pragma unroll
     for (int f = 0; f < NR; ++f) v[f][0] = v[f][1] = 0.0;
     for (int64_t i = tid; i < n; i += nthreads) {
       const double si = sc[i];
       int32_t k0 = 0, k1 = 0;
-      if (cyc > 0) {
+      if (cyc > 0 || warm) {
         k0 = __ldg(rp + i);
         k1 = __ldg(rp + i + 1);
       }
@@ -377,7 +397,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) k_mixed_cg(
         double s = 0.0;
         // x was written by other blocks before the grid barrier (plain loads)
         for (int32_t k = k0; k < k1; ++k) s += __ldg(val + k) * x[o + __ldg(col + k)];
-        if (cyc == 0) x[o + i] = 0.0;
+        if (cyc == 0 && !warm) x[o + i] = 0.0;
         const double ri = b[o + i] - s;
         const double ti = si * ri;
         t[o + i] = ti;
@@ -393,7 +413,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) k_mixed_cg(
       for (int f = 0; f < nrhs; ++f) {
         if (!live[f]) continue;
         const double rn = sqrt(totd[2 * f]), tn = sqrt(totd[2 * f + 1]);
-        if (cyc == 0) bnorm[f] = rn;
+        if (cyc == 0 && !warm) bnorm[f] = rn;
         if (blockIdx.x == 0) {
           ctl->rel[f] = bnorm[f] > 0.0 ? rn / bnorm[f] : 0.0;
           ctl->iters[f] = it;
@@ -585,7 +605,7 @@ sft_status finish_solve(const SolveLate& late, SolveResult* res) {
 
 template <int NR>
 static sft_status launch_mixed(sft_target_s* t, int nrhs, const double* b, double* x, double tol, int max_iter,
-                               cudaStream_t st, SolveResult* res, SolveLate* late) {
+                               cudaStream_t st, SolveResult* res, SolveLate* late, int warm) {
   const int64_t n = t->nv;
   int dev = 0, sms = 0;
   SFT_CUDA(cudaGetDevice(&dev));
@@ -631,7 +651,7 @@ static sft_status launch_mixed(sft_target_s* t, int nrhs, const double* b, doubl
   float* pf = partf.p;
   void* args[] = {(void*)&rp, (void*)&col, (void*)&val, (void*)&aval, (void*)&sc, (void*)&n, (void*)&nrhs,
                   (void*)&b, (void*)&x, (void*)&tp, (void*)&r, (void*)&p, (void*)&q, (void*)&y,
-                  (void*)&pd, (void*)&pf, (void*)&c, (void*)&tol, (void*)&max_iter};
+                  (void*)&pd, (void*)&pf, (void*)&c, (void*)&tol, (void*)&max_iter, (void*)&warm};
   const cudaError_t le = (::sft::note_launch(), cudaLaunchCooperativeKernel((const void*)k_mixed_cg<NR>, nblocks,
                                                                            kSolveThreads, args, 0, st));
   if (le != cudaSuccess) return cuda_fail(le, "cudaLaunchCooperativeKernel(k_mixed_cg)");
@@ -650,7 +670,7 @@ static sft_status launch_mixed(sft_target_s* t, int nrhs, const double* b, doubl
 }
 
 sft_status mass_solve(sft_target_s* t, int nrhs, const double* b, double* x, double tol, int max_iter,
-                      cudaStream_t st, int32_t* d_err, SolveResult* res, int cg_mode, SolveLate* late) {
+                      cudaStream_t st, int32_t* d_err, SolveResult* res, int cg_mode, SolveLate* late, int warm) {
   (void)d_err;
   res->iters = 0;
   res->rel_resid = 0.0;
@@ -663,12 +683,13 @@ sft_status mass_solve(sft_target_s* t, int nrhs, const double* b, double* x, dou
     res->converged = 0;
     return SFT_OK;
   }
+  if (warm && cg_mode != SFT_CG_MIXED) return fail(SFT_ERR_UNSUPPORTED, "a warm start needs cg_mode MIXED");
   if (cg_mode == SFT_CG_MIXED) {
     if (sft_status r = scaled_matrix(t, st)) return r;
-    if (nrhs == 1) return launch_mixed<1>(t, nrhs, b, x, tol, max_iter, st, res, late);
-    if (nrhs == 2) return launch_mixed<2>(t, nrhs, b, x, tol, max_iter, st, res, late);
-    if (nrhs <= 4) return launch_mixed<4>(t, nrhs, b, x, tol, max_iter, st, res, late);
-    return launch_mixed<8>(t, nrhs, b, x, tol, max_iter, st, res, late);
+    if (nrhs == 1) return launch_mixed<1>(t, nrhs, b, x, tol, max_iter, st, res, late, warm);
+    if (nrhs == 2) return launch_mixed<2>(t, nrhs, b, x, tol, max_iter, st, res, late, warm);
+    if (nrhs <= 4) return launch_mixed<4>(t, nrhs, b, x, tol, max_iter, st, res, late, warm);
+    return launch_mixed<8>(t, nrhs, b, x, tol, max_iter, st, res, late, warm);
   }
   int dev = 0, sms = 0, coop = 0;
   SFT_CUDA(cudaGetDevice(&dev));

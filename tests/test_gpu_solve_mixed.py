@@ -113,3 +113,38 @@ def test_transfer_modes_agree(orc):
         assert st["cg_rel_resid"] <= 1e-13
         for f in range(u.shape[0]):
             assert _rel(u[f], o["u"][f]) < 1e-10
+
+
+def test_warm_start(orc):
+    """cg_warm_start: the solve starts from the values in u_out. From the
+    converged solution it stops after the first residual check (0 inner
+    iterations, u unchanged to the tolerance); from a poor start it reaches
+    the cold-start solution within the solve tolerance; FP64 mode and batched
+    plans reject it."""
+    src, tgt, _ = W.config_meshes("tri2k", 1.0)
+    s, t = sft.mesh_source(src, device=DEV), sft.mesh_target(tgt, device=DEV)
+    u = torch.zeros((1, tgt.nnodes), dtype=torch.float64, device=DEV)
+    _, st0, _ = sft.sft_transfer(s, t, 16, sft.SFT_PREC_FP64, seed=2, cg_tol=1e-12, u_out=u)
+    u0 = u.cpu().numpy().copy()
+    _, st1, _ = sft.sft_transfer(s, t, 16, sft.SFT_PREC_FP64, seed=2, cg_tol=1e-12, u_out=u, cg_warm_start=True)
+    assert st1["cg_iters"] == 0 and st1["cg_rel_resid"] <= 1e-12
+    assert _rel(u.cpu().numpy(), u0) < 1e-12
+    # poor start (host buffers: the start is copied in)
+    rng = np.random.default_rng(3)
+    uh = rng.standard_normal((1, tgt.nnodes))
+    _, st2, _ = sft.sft_transfer(s, t, 16, sft.SFT_PREC_FP64, seed=2, cg_tol=1e-12, u_out=uh, cg_warm_start=True)
+    assert st2["cg_rel_resid"] <= 1e-12 and st2["cg_iters"] > 0
+    assert _rel(uh, u0) < 1e-10
+    # a second transfer with other samples starts close: fewer iterations than cold
+    u2 = u.clone()
+    _, st3, _ = sft.sft_transfer(s, t, 16, sft.SFT_PREC_FP64, seed=9, cg_tol=1e-12, u_out=u2, cg_warm_start=True)
+    u3 = torch.zeros_like(u)
+    _, st4, _ = sft.sft_transfer(s, t, 16, sft.SFT_PREC_FP64, seed=9, cg_tol=1e-12, u_out=u3)
+    assert st3["cg_iters"] <= st4["cg_iters"]
+    assert _rel(u2.cpu().numpy(), u3.cpu().numpy()) < 1e-10
+    with pytest.raises(sft.SftError) as e:
+        sft.sft_transfer(s, t, 16, sft.SFT_PREC_FP64, u_out=u, cg_warm_start=True, cg_mode=sft.SFT_CG_FP64)
+    assert e.value.status == sft.SFT_ERR_UNSUPPORTED
+    with pytest.raises(sft.SftError) as e:
+        sft.sft_batch_create([s], [t], [dict(samples_per_elem=8, cg_warm_start=True)])
+    assert e.value.status == sft.SFT_ERR_UNSUPPORTED
