@@ -1,6 +1,7 @@
 // Step 7 of Sec. 4: solve the target Galerkin system M u = b (Eq.
-// cv_galerkin_system) from u = 0, stopping at ||b - M u||_2 <= tol ||b||_2
-// (the paper does not name its solver). Two kernels:
+// cv_galerkin_system) from u = 0 (or, in the mixed mode on request, from the
+// u the caller holds), stopping at ||b - M u||_2 <= tol ||b||_2 (the paper
+// does not name its solver). Two kernels:
 //   k_pcg       Jacobi-preconditioned CG in FP64 (cg_mode FP64, and the
 //               allocation-free entry point, which takes any SPD CSR matrix);
 //   k_mixed_cg  mixed-precision iterative refinement (default; see below).
@@ -233,6 +234,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_pcg(const int32_t* __restrict
 //   CG (FP32) on A y = c until ||c - A y||_2 <= eta, eta about the reduction
 //             the stopping test still needs (between 1e-5 and 1/4);
 //   U (FP64)  x += ||t||_2 S y   (so the new residual is ||t|| S^-1 (c - A y)).
+// A warm start takes x as given (||b|| is then reduced separately first) and
+// skips nothing else: the first R phase checks whether x already converged.
 // The FP64 pipe does one SpMV per cycle (2 to 3 cycles) instead of one per
 // iteration. Every block takes every decision from the same fixed-order
 // reductions; the stopping test uses the true FP64 residual.
