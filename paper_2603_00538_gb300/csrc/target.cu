@@ -102,7 +102,7 @@ __global__ void k_inc_rank(const int32_t* __restrict__ inc_start, const int32_t*
 }
 
 // Row i of M: FILL=false writes the row length (and, when tmp_col is given,
-// the row itself into a fixed-stride staging array, so that the second pass
+// the row itself into an entry-major staging array [kMaxRow][nv], so that the second pass
 // only copies), FILL=true writes columns, values, the Jacobi inverse diagonal
 // and the lumped mass.
 // CAP bounds the row buffers (local memory per thread); a counting pass with
@@ -176,8 +176,9 @@ __global__ void k_mass_rows(const int32_t* __restrict__ conn, const double2* __r
       row_len[i] = cnt;
       if (tmp_col) {
         for (int q = 0; q < cnt; ++q) {
-          tmp_col[i * kMaxRow + q] = cols[q];
-          tmp_val[i * kMaxRow + q] = vals[q];
+          // entry q of every row contiguous ([q][nv]): coalesced across a warp's rows
+          tmp_col[(int64_t)q * nv + i] = cols[q];
+          tmp_val[(int64_t)q * nv + i] = vals[q];
         }
         tmp_lump[i] = lump;
       }
@@ -204,8 +205,8 @@ __global__ void k_mass_copy(const int32_t* __restrict__ tmp_col, const double* _
     const int32_t base = row_ptr[i], cnt = row_ptr[i + 1] - base;
     double diag = 0.0;
     for (int q = 0; q < cnt; ++q) {
-      const int32_t c = tmp_col[i * kMaxRow + q];
-      const double v = tmp_val[i * kMaxRow + q];
+      const int32_t c = tmp_col[(int64_t)q * nv + i];
+      const double v = tmp_val[(int64_t)q * nv + i];
       col[base + q] = c;
       val[base + q] = v;
       if (c == i) diag = v;
