@@ -161,6 +161,32 @@ def test_stratified_samples_lie_in_their_strata(orc, dim, prec, N):
                 assert c[a] / m - tol <= u[a] <= (c[a] + 1) / m + tol, (t, j, a, u[a], c[a])
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("sampling", [0, 1])
+def test_sampling_unbiased_for_dirichlet_moments(orc, dim, sampling):
+    """Both sampling schemes are unbiased element quadratures: the mean over
+    seeds of |T|/N sum_j lam_1(X_j)^2 lam_0(X_j) approaches the closed form
+    int_T lam_1^2 lam_0 = d! |T| 2! 1! / (3 + d)! (Dirichlet moments of the
+    barycentric coordinates), within 5 standard errors; stratification
+    lowers the spread of the estimate."""
+    vol = 0.5 if dim == 2 else 1.0 / 6.0
+    exact = math.factorial(dim) * vol * 2 / math.factorial(3 + dim)
+    N = 16 if dim == 2 else 27
+    est = []
+    for t in range(400):
+        lam, _ = orc.sample_element(0, dim, 7, 1, t, N, REF[dim], sampling=sampling)
+        est.append(vol / N * np.sum(lam[:, 1] ** 2 * lam[:, 0]))
+    est = np.array(est)
+    se = est.std(ddof=1) / math.sqrt(est.size)
+    assert abs(est.mean() - exact) < 5 * se
+    if sampling == 1:
+        unif = []
+        for t in range(400):
+            lam, _ = orc.sample_element(0, dim, 7, 1, t, N, REF[dim], sampling=0)
+            unif.append(vol / N * np.sum(lam[:, 1] ** 2 * lam[:, 0]))
+        assert est.std() < 0.7 * np.std(unif)
+
+
 def test_stratified_strata_cover_each_cell_once(orc):
     """With N = m^2 every cell of the m x m grid of (xi, eta) holds exactly one
     sample of each element (a permutation check of the recovered cells)."""
