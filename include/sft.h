@@ -4,7 +4,7 @@
  * approximation of the Galerkin projection (paper Sec. 4), with the source
  * field queried pointwise as a black box (here: P1 point location in a
  * uniform-grid-bucketed source mesh, Sec. 5.3) and the target mass-matrix
- * system solved in FP64.
+ * system solved to an FP64 residual tolerance (sft_cg_mode).
  *
  * Conventions shared by every entry point
  *  - Plain pointers and sizes only. A pointer is device memory when the
@@ -153,8 +153,10 @@ void sft_target_destroy(sft_target tgt);
 /* One transfer, Sec. 4 steps 1-7 (Eqs. cv_load_expanded and cv_galerkin_system):
  *   g   = source evaluated at the target nodes (step 1);
  *   b_i = alpha int g psi_i  +  sum_t |T|/N sum_j (f^s - alpha g)(X_tj) psi_i(X_tj)
- *         with X_tj uniform in t from Philox4x32-10 (steps 2-6);
- *   M u = b by Jacobi-preconditioned CG from u = 0 (step 7).
+ *         with X_tj uniform in t from Philox4x32-10 (steps 2-6; stratified
+ *         with opt->sampling = SFT_SAMPLING_STRATIFIED);
+ *   M u = b by the sft_cg_mode of opt->cg_mode, from u = 0 or, with
+ *         opt->cg_warm_start, from the values u_out holds (step 7).
  * nfields = opt->field_count if > 0, else the source's field count.
  * u_out [nfields][nnodes_target] FP64 (required); b_out, g_out same shape,
  * optional (NULL). u_out is written on SFT_OK and SFT_ERR_NOT_CONVERGED.
@@ -352,8 +354,8 @@ sft_status sft_surrogate_dataset(sft_source src, int32_t field, int64_t n, uint6
  * memory at solve time (for example a coupled code whose memory pool owns
  * the device, or a time-stepping loop that must not call cudaMalloc/cudaFree,
  * which synchronise the device and can fail mid-run). The paper has no
- * counterpart; this is the step-7 solve of sft_mass_solve with the caller's
- * CSR matrix and its work vectors kept in a fixed 32 MiB device array that
+ * counterpart; this is the FP64 Jacobi-PCG of sft_mass_solve (cg_mode
+ * SFT_CG_FP64: it takes any SPD matrix) with the caller's CSR matrix and its work vectors kept in a fixed 32 MiB device array that
  * the library reserves on every device it is loaded on, until process exit.
  * All pointers are device memory: row_ptr [n+1], col / val [row_ptr[n]]
  * (FP64, symmetric positive definite, diagonal present), b and u
