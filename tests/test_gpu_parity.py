@@ -366,8 +366,11 @@ def test_set_values_equals_recreate(orc):
     _, _, u1 = sft.sft_transfer(s, t, 16, FP32, cg_tol=1e-12)
     s2 = sft.mesh_source(new, device=DEV)
     _, _, u2 = sft.sft_transfer(s2, t, 16, FP32, cg_tol=1e-12)
-    assert np.array_equal(u1, u2)
+    # same samples, locations and values: the load vectors differ only by the
+    # order of the FP64 atomic sums
+    assert _rel(u1, u2) < 1e-12
     e1 = sft.sft_conservation_error(s, t, u1[0])
     e2 = sft.sft_conservation_error(s2, t, u2[0])
-    assert e1 == e2
+    assert e1[1] == e2[1]                      # the same source integral
+    assert e1[2] == pytest.approx(e2[2], rel=1e-12)
     assert e1[1] == pytest.approx(orc.integral_p1(new.coords, new.conn, new.values[0]), rel=1e-6)
