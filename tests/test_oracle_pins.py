@@ -388,6 +388,40 @@ def test_mass_matrix_closed_forms(orc, dim):
     assert u @ A @ u == pytest.approx(exact, rel=1e-12)
 
 
+def test_scaled_mass_matrix_eigenvalue_bounds(orc):
+    """The mixed-precision solve relies on cond(S M S) being a small constant
+    for S = diag(M)^-1/2: each P1 element mass matrix against its own diagonal
+    has eigenvalues in [1/2, 2] (triangles) or [1/2, 5/2] (tetrahedra), and the
+    assembled scaled matrix's Rayleigh quotients stay in the union of the
+    element intervals. Checked by dense eigenvalues on quasi-uniform, Delaunay,
+    strongly graded, high-valence and sliver meshes."""
+    meshes = [W.jittered_tri_mesh(9, 1), W.delaunay_tri_mesh(150, 9, 2)]
+    g = W.delaunay_tri_mesh(150, 9, 3)
+    c = g.coords.copy()
+    c[:, 0] = c[:, 0] ** 4
+    g = W.Mesh(c, g.conn.copy(), None)
+    W._fix_orientation(g)
+    meshes.append(g)
+    k = 40                                          # fan: one node with 40 triangles
+    ang = 2 * np.pi * np.arange(k) / k
+    meshes.append(W.Mesh(np.vstack([[0.0, 0.0], np.stack([np.cos(ang), np.sin(ang)], 1)]),
+                         np.array([[0, 1 + i, 1 + (i + 1) % k] for i in range(k)], np.int32), None))
+    sl = W.jittered_tri_mesh(6, 4)
+    meshes.append(W.Mesh(sl.coords * np.array([1.0, 1e-3]), sl.conn, None))   # slivers
+    meshes += [W.jittered_kuhn_mesh(3, 5), W.morton_reorder(W.jittered_kuhn_mesh(4, 6))]
+    for m in meshes:
+        d = m.coords.shape[1]
+        rp, col, val = orc.mass_csr(m.coords, m.conn)
+        n = len(rp) - 1
+        A = np.zeros((n, n))
+        for i in range(n):
+            A[i, col[rp[i]:rp[i + 1]]] = val[rp[i]:rp[i + 1]]
+        s = 1.0 / np.sqrt(np.diag(A))
+        ev = np.linalg.eigvalsh(A * s[:, None] * s[None, :])
+        hi = 2.0 if d == 2 else 2.5
+        assert ev.min() >= 0.5 - 1e-12 and ev.max() <= hi + 1e-12, (d, ev.min(), ev.max())
+
+
 def test_pcg_matches_dense_solve(orc):
     m = W.delaunay_tri_mesh(150, 6, 5)
     rp, col, val = orc.mass_csr(m.coords, m.conn)
