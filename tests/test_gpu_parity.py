@@ -2,9 +2,11 @@
 
 Bar: integer results (grid cells, located elements, per-sample source
 elements, CSR pattern) bit-exact; FP64 paths within rounding; FP32 paths:
-b within 1e-5 relative (2-norm), the rest within the bounds derived in the
-design notes (FP32 evaluation error ~1e-7 relative, amplified at most by the
-mass matrix condition number)."""
+b within 1e-5 relative, the rest within the bounds derived in the design
+notes (FP32 evaluation error ~1e-7 relative, amplified at most by the mass
+matrix condition number). Floating-point vectors are held to each bound both
+as a 2-norm ratio and entry by entry (max_i |a_i - b_i| against max_i |b_i|),
+so a few wrong entries cannot hide under the norm of a long vector."""
 import numpy as np
 import pytest
 
@@ -24,6 +26,16 @@ FP64, FP32 = sft.SFT_PREC_FP64, sft.SFT_PREC_FP32
 
 def _rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def _rel_max(a, b):
+    """largest entry-wise difference relative to the largest entry of b"""
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _close(a, b, lim):
+    return _rel(a, b) < lim and _rel_max(a, b) < lim
 
 
 def _run(src, tgt, prec, N, seed=0, alpha=1.0, tol=1e-13, device=True, stream_id=0, L=1.0, maxit=2000):
@@ -205,14 +217,10 @@ def test_transfer_parity(orc, name, scale, prec, N):
     assert np.array_equal(r["sample_elem"], o["sample_elem"])
     assert r["stats"]["fallback_queries"] == o["fallback_queries"]
     assert r["stats"]["empty_queries"] == o["empty_queries"] == 0
-    if prec == FP64:
-        assert _rel(r["g"], o["g"]) < 1e-13
-        assert _rel(r["b"], o["b"]) < 1e-13
-        assert _rel(r["u"], o["u"]) < 1e-10
-    else:
-        assert _rel(r["g"], o["g"]) < 2e-6
-        assert _rel(r["b"], o["b"]) < 1e-5
-        assert _rel(r["u"], o["u"]) < 1e-4
+    lim = dict(g=1e-13, b=1e-13, u=1e-10) if prec == FP64 else dict(g=2e-6, b=1e-5, u=1e-4)
+    for f in range(src.nfields):
+        for k in ("g", "b", "u"):
+            assert _close(r[k][f], o[k][f], lim[k]), (k, f, _rel(r[k][f], o[k][f]), _rel_max(r[k][f], o[k][f]))
 
 
 @pytest.mark.parametrize("dim,N,nf,alpha", [
@@ -237,8 +245,8 @@ def test_transfer_edge_shapes(orc, dim, N, nf, alpha):
         assert np.array_equal(r["sample_elem"], o["sample_elem"])
         lim_b = 1e-13 if prec == FP64 else 1e-5
         for f in range(nf):
-            assert _rel(r["b"][f], o["b"][f]) < lim_b
-            assert _rel(r["u"][f], o["u"][f]) < (1e-10 if prec == FP64 else 1e-4)
+            assert _close(r["b"][f], o["b"][f], lim_b), (prec, f, _rel_max(r["b"][f], o["b"][f]))
+            assert _close(r["u"][f], o["u"][f], 1e-10 if prec == FP64 else 1e-4), (prec, f)
 
 
 def test_host_buffers_equal_device_buffers():
@@ -319,37 +327,38 @@ def test_invalid_meshes_rejected():
 
 
 # --------------------------------------------------------------------------
-# full size, in the benchmark's launch configuration: sampled outputs
+# full size, in the benchmark's launch configuration: every output
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("name", ["tri4m", "tet5m"])
-def test_full_size_sampled(orc, name):
+def test_full_size_elementwise(orc, name):
+    """The benchmark's workloads at full size (4.0 M -> 2.0 M triangles x 64
+    samples; 5.0 M -> 3.0 M tetrahedra x 32 samples), FP32 path, against the
+    oracle run on the whole workload: the source element of every one of the
+    128 M / 95 M samples bit for bit, g, b and u entry by entry within the
+    FP32 bounds, plus properties that hold at any size."""
     src, tgt, p = W.config_meshes(name)
     N = p["samples_per_elem"]
     r = _run(src, tgt, FP32, N, tol=p["cg_tol"])
     # every sample lands in an element (the meshes cover the same domain)
     assert r["stats"]["empty_queries"] == 0
     assert (r["sample_elem"] >= 0).all()
-    # sampled target elements: samples and their source elements, one by one
-    rng = np.random.default_rng(0)
-    pick = np.sort(rng.choice(tgt.nelems, 400, replace=False))
-    grid = orc.Grid(1, src.coords, src.conn)
-    d = tgt.dim
-    for e in pick:
-        xyz = tgt.coords[tgt.conn[e]].astype(np.float64)
-        lam, X = orc.sample_element(1, d, 0, 0, int(e), N, xyz)
-        el, _ = grid.locate(X)
-        assert np.array_equal(el, r["sample_elem"][e])
-    # control values at sampled nodes
-    nodes = rng.choice(tgt.nnodes, 2000, replace=False)
-    X = tgt.coords[nodes].astype(np.float64)
-    el, _ = grid.locate(X)
-    gref = np.array([orc.eval_p1(src.coords, src.conn, src.values, e, x)[0] for e, x in zip(el, X)])
-    assert np.max(np.abs(r["g"][0][nodes] - gref)) <= 2e-6 * np.max(np.abs(gref))
     # properties: partition of unity of the control term and convergence of M u = b
     e_mass, i_s, i_t = sft.sft_conservation_error(r["s"], r["t"], r["u"][0])
     assert i_t == pytest.approx(r["b"][0].sum(), rel=1e-8)
     assert r["stats"]["cg_rel_resid"] <= p["cg_tol"]
     assert e_mass < 1e-3
+    gpu_se = r.pop("sample_elem")
+    r["s"].close()
+    r["t"].close()
+    o = orc.transfer(src, tgt, 1, N, cg_tol=p["cg_tol"], want_sample_elem=True)
+    assert o["empty_queries"] == 0 and o["cg_rel_resid"] <= p["cg_tol"]
+    assert r["stats"]["fallback_queries"] == o["fallback_queries"]
+    bad = np.count_nonzero(gpu_se != o["sample_elem"])
+    assert bad == 0, f"{bad} of {gpu_se.size} samples located in another element"
+    del gpu_se, o["sample_elem"]
+    lim = dict(g=2e-6, b=1e-5, u=1e-4)
+    for k in ("g", "b", "u"):
+        assert _close(r[k][0], o[k][0], lim[k]), (k, _rel(r[k][0], o[k][0]), _rel_max(r[k][0], o[k][0]))
 
 
 def test_set_values_equals_recreate(orc):
