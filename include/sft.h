@@ -193,6 +193,15 @@ sft_status sft_mass_solve(sft_target tgt, int32_t nrhs, const double* b, double*
                           int32_t device_ptrs, double tol, int32_t max_iter, int32_t cg_mode,
                           void* cuda_stream, int32_t* iters_out, double* rel_resid_out);
 
+/* Limit of every device wait in the solves on this target (the grid barriers
+ * of the cooperative CG kernels of step 7, Eq. cv_galerkin_system, reached
+ * through sft_transfer, sft_plan_transfer and sft_mass_solve): a wait that
+ * runs past it sets the kernel's error word, every block of the launch
+ * returns, and the call reports SFT_ERR_DEVICE_STATUS; the stream and the
+ * context stay usable. Default 2 s; `seconds` in (0, 3600], else SFT_ERR_ARG.
+ * The paper has no counterpart (failure detection of the device path). */
+sft_status sft_target_set_wait_limit(sft_target tgt, double seconds);
+
 /* ---- batched transfers ----
  * Many requests (source, target, options) of uneven size run together: the
  * paper's per-request method (Sec. 4 steps 1-7) is unchanged; batching has no
@@ -364,7 +373,9 @@ sft_status sft_surrogate_dataset(sft_source src, int32_t field, int64_t n, uint6
  * partials must fit in 32 MiB (n (1 + 4 nrhs) below about 4.1e6);
  * larger problems are rejected with SFT_ERR_ARG before any device work.
  * The first call on a device looks up the array's device address once (make
- * that first call before any stream capture). Every call uses the same
+ * that first call before any stream capture) and keeps it, so resetting the
+ * device (cudaDeviceReset) while the library is loaded is not supported.
+ * A row without a positive diagonal entry gives SFT_ERR_ARG. Every call uses the same
  * array, so calls that overlap on the GPU (other streams, other threads)
  * race and must be serialised by the caller. Nothing is allocated or freed;
  * the stream is synchronised before returning. iters_out / rel_resid_out are
@@ -379,6 +390,14 @@ sft_status sft_mass_solve_static(int64_t n, const int32_t* row_ptr, const int32_
 sft_status sft_source_grid(sft_source src, int32_t precision, int32_t n_out[3],
                            int64_t* ncells_out, int64_t* nitems_out,
                            int64_t* start_out, int32_t* items_out);
+/* Face neighbours of the source mesh used by the location walk (Sec. 4,
+ * step 4: localizing each sample in the source mesh): adj_out [nelems][dim+1]
+ * host or device memory, adj_out[e][m] = the other element holding every
+ * vertex of the face of e opposite its local vertex m (the smallest id if
+ * several), -1 on the boundary. Built with the source's first location
+ * structure (of either precision; `precision` selects which one to build if
+ * none exists yet). SFT_ERR_ARG for a null source or output. */
+sft_status sft_source_adjacency(sft_source src, int32_t precision, int32_t* adj_out);
 /* Target mass matrix: nnz, row_ptr [nnodes+1] (int64), col [nnz], val [nnz],
  * lumped masses [nnodes]. */
 sft_status sft_target_mass(sft_target tgt, int64_t* nnz_out, int64_t* row_ptr_out,

@@ -89,6 +89,7 @@ def _declare(L):
     L.orc_grid_csr.argtypes = [_vp, _i64p, _i32p]
     L.orc_grid_locate.argtypes = [_vp, _i64, _f64p, _i32p, _i32p]
     L.orc_grid_depths.argtypes = [_vp, _f64p]
+    L.orc_grid_adjacency.argtypes = [_vp, _i32p]
     L.orc_brute_locate.argtypes = [_int, _int, _i64, _f64p, _i64, _i32p, _i64, _f64p,
                                    _i32p, _i32p]
     L.orc_eval_p1.argtypes = [_int, _f64p, _i32p, _int, _i64, _f64p, ctypes.c_int32,
@@ -183,6 +184,12 @@ class Grid:
         out = np.zeros(max(ni, 1))
         lib().orc_grid_depths(self._h, out)
         return out[:ni]
+
+    def adjacency(self):
+        """[ne][dim+1] face neighbours: across the face opposite local vertex m, or -1"""
+        out = np.zeros((self.conn.shape[0], self.dim + 1), np.int32)
+        lib().orc_grid_adjacency(self._h, out)
+        return out
 
     def locate(self, pts):
         pts = _f64(pts).reshape(-1, self.dim)

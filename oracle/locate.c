@@ -22,14 +22,31 @@
  *     map, formed in P from the vertex coordinates (one reciprocal of the
  *     determinant; FP32 uses Kahan's 2x2 determinant); mu is evaluated in P
  *     with fused multiply-adds in a fixed order. Accepted when all mu >= 0;
- *   - the first accepting candidate in the cell's order wins; if none
- *     accepts, the candidate with the largest min(mu) wins (ties to the
- *     earlier one); an empty cell yields -1.
+ *   - search: a walk through face neighbours, started at the first element
+ *     of the point's cell (the one deepest at the cell centre). At element e
+ *     the predicate's mu is evaluated; all mu >= 0 accepts e; otherwise the
+ *     walk moves to the element across the face opposite the vertex with the
+ *     smallest mu (the first such vertex on ties), the face where the point
+ *     lies farthest outside. It gives up at a boundary face (no neighbour)
+ *     or after ORC_WALK_STEPS evaluations;
+ *   - neighbour across the face of e opposite its local vertex m: the other
+ *     element whose vertices include the face's vertices (the smallest id if
+ *     several; none on the boundary);
+ *   - when the walk gives up, the cell's list is scanned: the first
+ *     accepting candidate in the cell's order wins; if none accepts, the
+ *     candidate with the largest min(mu) wins (ties to the earlier one); an
+ *     empty cell yields -1.
+ * A point inside exactly one element (the usual case) gets that element
+ * whatever the search; the rule only fixes which element wins where the
+ * rounded predicate accepts several (points on shared faces).
  */
 #include "oracle.h"
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* predicate evaluations of the walk before the cell's list is scanned */
+#define ORC_WALK_STEPS 12
 
 struct orc_grid {
     int prec, dim;
@@ -44,6 +61,7 @@ struct orc_grid {
     int64_t nv, ne;
     double* coords;
     const int32_t* conn;
+    int32_t* adj;      /* [ne][dim+1]: neighbour across the face opposite vertex m, or -1 */
 };
 
 static double to_prec(int prec, double x) { return prec == 1 ? (double)(float)x : x; }
@@ -324,6 +342,48 @@ static void order_cells(orc_grid* g)
     free(sc);
 }
 
+/* does element e2 have every vertex of element e except its local vertex m? */
+static int holds_face(int k, const int32_t* conn, int64_t e, int m, int64_t e2)
+{
+    for (int q = 0; q < k; ++q) {
+        if (q == m) continue;
+        int found = 0;
+        for (int r = 0; r < k; ++r) found |= conn[e2 * k + r] == conn[e * k + q];
+        if (!found) return 0;
+    }
+    return 1;
+}
+
+/* face neighbours by their definition: for each element e and local vertex m,
+ * the smallest id e2 != e among the elements incident to the face's first
+ * vertex that hold every vertex of the face; -1 if there is none */
+static int32_t* build_adjacency(int dim, int64_t nv, int64_t ne, const int32_t* conn)
+{
+    const int k = dim + 1;
+    int64_t* first = (int64_t*)calloc((size_t)nv + 1, sizeof(int64_t));
+    for (int64_t i = 0; i < ne * k; ++i) first[conn[i] + 1]++;
+    for (int64_t v = 0; v < nv; ++v) first[v + 1] += first[v];
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nv + 1));
+    memcpy(fill, first, sizeof(int64_t) * (size_t)(nv + 1));
+    int32_t* inc = (int32_t*)malloc(sizeof(int32_t) * (size_t)(ne * k > 0 ? ne * k : 1));
+    for (int64_t e = 0; e < ne; ++e)
+        for (int m = 0; m < k; ++m) inc[fill[conn[e * k + m]]++] = (int32_t)e;
+    int32_t* adj = (int32_t*)malloc(sizeof(int32_t) * (size_t)(ne * k > 0 ? ne * k : 1));
+    for (int64_t e = 0; e < ne; ++e)
+        for (int m = 0; m < k; ++m) {
+            const int32_t v = conn[e * k + (m == 0 ? 1 : 0)];   /* a vertex of the face */
+            int32_t best = -1;
+            for (int64_t p = first[v]; p < first[v + 1]; ++p) {
+                const int32_t e2 = inc[p];
+                if (e2 == e || !holds_face(k, conn, e, m, e2)) continue;
+                if (best < 0 || e2 < best) best = e2;
+            }
+            adj[e * k + m] = best;
+        }
+    free(first); free(fill); free(inc);
+    return adj;
+}
+
 orc_grid* orc_grid_build(int prec, int dim, int64_t nv, const double* coords,
                          int64_t ne, const int32_t* conn, double grid_scale_L)
 {
@@ -388,13 +448,14 @@ orc_grid* orc_grid_build(int prec, int dim, int64_t nv, const double* coords,
     }
     free(count);
     order_cells(g);
+    g->adj = build_adjacency(dim, nv, ne, conn);
     return g;
 }
 
 void orc_grid_free(orc_grid* g)
 {
     if (!g) return;
-    free(g->start); free(g->items); free(g->coords); free(g);
+    free(g->start); free(g->items); free(g->coords); free(g->adj); free(g);
 }
 
 void orc_grid_shape(const orc_grid* g, int32_t n_out[3], int64_t* ncells, int64_t* nitems)
@@ -428,8 +489,29 @@ static int locate_one(const orc_grid* g, const double* Xin, int32_t* elem)
     int32_t ci[3] = {0, 0, 0};
     for (int a = 0; a < g->dim; ++a) ci[a] = cell_axis(g, a, X[a]);
     const int64_t cell = ((int64_t)ci[2] * g->n[1] + ci[1]) * g->n[0] + ci[0];
+    if (g->start[cell + 1] > g->start[cell]) {
+        /* the walk from the element deepest at the cell centre */
+        int32_t e = g->items[g->start[cell]];
+        for (int s = 0; s < ORC_WALK_STEPS; ++s) {
+            double mu[4];
+            predicate_mu(g->prec, g->dim, g->coords, g->conn, e, X, mu);
+            double mn = mu[0];
+            int am = 0;
+            for (int m = 1; m <= g->dim; ++m)
+                if (mu[m] < mn) { mn = mu[m]; am = m; }
+            if (mn >= 0.0) { *elem = e; return 0; }
+            const int32_t next = g->adj[(int64_t)e * (g->dim + 1) + am];
+            if (next < 0) break;
+            e = next;
+        }
+    }
     return scan_candidates(g->prec, g->dim, g->coords, g->conn, g->items + g->start[cell],
                            g->start[cell + 1] - g->start[cell], X, elem);
+}
+
+void orc_grid_adjacency(const orc_grid* g, int32_t* out)
+{
+    memcpy(out, g->adj, sizeof(int32_t) * (size_t)(g->ne * (g->dim + 1)));
 }
 
 void orc_grid_locate(const orc_grid* g, int64_t npts, const double* pts,

@@ -58,9 +58,12 @@ void orc_grid_shape(const orc_grid* g, int32_t n_out[3], int64_t* ncells, int64_
 void orc_grid_csr(const orc_grid* g, int64_t* start, int32_t* items);
 /* depth of each cell's centre in each listed element (min barycentric), [nitems] */
 void orc_grid_depths(const orc_grid* g, double* out);
-/* elem_out: containing element (first accepting candidate in the cell order),
- * the best-scoring candidate when none accepts, or -1 for an empty cell.
- * status_out: 0 accepted, 1 fallback, 2 empty cell. */
+/* face neighbours [ne][dim+1]: across the face opposite local vertex m, or -1 */
+void orc_grid_adjacency(const orc_grid* g, int32_t* out);
+/* elem_out: containing element (the walk through face neighbours from the
+ * cell's first element, else the first accepting candidate in the cell
+ * order), the best-scoring candidate when none accepts, or -1 for an empty
+ * cell. status_out: 0 accepted, 1 fallback, 2 empty cell. */
 void orc_grid_locate(const orc_grid* g, int64_t npts, const double* pts,
                      int32_t* elem_out, int32_t* status_out);
 /* same predicate, scanning every element (no grid) */

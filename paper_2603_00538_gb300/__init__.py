@@ -105,6 +105,8 @@ _SIGS = {
     "sft_locate": ([_vp, _i32, _i64, _vp, _i32, _vp, _vp, _vp], _i32),
     "sft_mass_solve": ([_vp, _i32, _vp, _vp, _i32, _d, _i32, _i32, _vp, _vp, _vp], _i32),
     "sft_source_grid": ([_vp, _i32, _vp, _vp, _vp, _vp, _vp], _i32),
+    "sft_source_adjacency": ([_vp, _i32, _vp], _i32),
+    "sft_target_set_wait_limit": ([_vp, ctypes.c_double], _i32),
     "sft_target_mass": ([_vp, _vp, _vp, _vp, _vp, _vp], _i32),
     "sft_status_str": ([_i32], ctypes.c_char_p),
     "sft_last_error": ([], ctypes.c_char_p),
@@ -402,12 +404,39 @@ def sft_mass_solve(tgt: Target, b, tol=1e-12, max_iter=1000, u_out=None, stream=
 def sft_mass_solve_static(row_ptr, col, val, b, u_out, tol=1e-12, max_iter=1000, stream=None):
     """Allocation-free solve of M u = b (all arguments CUDA tensors: row_ptr
     int32 [n+1], col int32, val float64, b and u_out float64 [nrhs, n]).
-    Returns (iters, rel_resid)."""
+    Returns (iters, rel_resid).
+
+    The arguments are checked here before any pointer reaches the library,
+    which trusts them: dtypes (an int64 row_ptr read as int32 would give a
+    wrong answer), shapes (a b or u_out shorter than nrhs x n would be read
+    or written past its end), one device, a contiguous u_out (a copy would
+    receive the solution and drop it) and col / val holding row_ptr[n]
+    entries. ValueError / TypeError otherwise."""
+    import torch
+    args = dict(row_ptr=row_ptr, col=col, val=val, b=b, u_out=u_out)
+    for name, x in args.items():
+        if not (_is_torch(x) and x.is_cuda):
+            raise ValueError(f"sft_mass_solve_static: {name} must be a CUDA tensor")
+    want = dict(row_ptr=torch.int32, col=torch.int32, val=torch.float64, b=torch.float64, u_out=torch.float64)
+    for name, dt in want.items():
+        if args[name].dtype != dt:
+            raise TypeError(f"sft_mass_solve_static: {name} must be {dt}, got {args[name].dtype}")
+    if len({x.device for x in args.values()}) != 1:
+        raise ValueError("sft_mass_solve_static: all tensors must be on one device")
+    if row_ptr.dim() != 1 or row_ptr.shape[0] < 2 or col.dim() != 1 or val.dim() != 1:
+        raise ValueError("sft_mass_solve_static: row_ptr [n+1] (n >= 1), col and val must be 1-D")
     n = int(row_ptr.shape[0]) - 1
+    if b.shape != u_out.shape or b.dim() not in (1, 2) or b.shape[-1] != n:
+        raise ValueError(f"sft_mass_solve_static: b and u_out must both be [nrhs, {n}] or [{n}], "
+                         f"got {tuple(b.shape)} and {tuple(u_out.shape)}")
+    if not u_out.is_contiguous():
+        raise ValueError("sft_mass_solve_static: u_out must be contiguous (the solution is written in place)")
+    nnz = int(row_ptr[-1])
+    if int(row_ptr[0]) != 0 or nnz < 0 or col.numel() < nnz or val.numel() < nnz:
+        raise ValueError(f"sft_mass_solve_static: row_ptr[0] must be 0 and col / val hold row_ptr[n] = {nnz} "
+                         f"entries, got {col.numel()} / {val.numel()}")
     nrhs = int(b.shape[0]) if b.dim() == 2 else 1
     ptrs = [_ptr(x) for x in (row_ptr, col, val, b, u_out)]
-    if not all(dev for _, dev, _ in ptrs):
-        raise ValueError("sft_mass_solve_static takes device tensors only")
     it = ctypes.c_int32()
     rr = ctypes.c_double()
     _check(lib().sft_mass_solve_static(n, ptrs[0][0], ptrs[1][0], ptrs[2][0], nrhs, ptrs[3][0], ptrs[4][0],
@@ -651,6 +680,19 @@ def sft_source_grid(src: Source, precision: int):
     _check(lib().sft_source_grid(src.h, int(precision), None, None, None, start.ctypes.data, items.ctypes.data),
            "sft_source_grid")
     return np.array(list(n)), start, items[:ni.value]
+
+
+def sft_target_set_wait_limit(tgt: Target, seconds: float) -> None:
+    """Limit of the device waits of the solves on this target (default 2 s)."""
+    _check(lib().sft_target_set_wait_limit(tgt.h, float(seconds)), "sft_target_set_wait_limit")
+
+
+def sft_source_adjacency(src: Source, precision: int) -> np.ndarray:
+    """[nelems][dim+1] int32 face neighbours of the source mesh (-1 on the boundary)."""
+    conn = src._keep[1]
+    out = np.zeros((int(conn.shape[0]), int(conn.shape[1])), np.int32)
+    _check(lib().sft_source_adjacency(src.h, int(precision), out.ctypes.data), "sft_source_adjacency")
+    return out
 
 
 def sft_target_mass(tgt: Target):

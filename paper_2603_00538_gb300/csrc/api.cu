@@ -125,6 +125,7 @@ void sft_source_destroy(sft_source s) {
   if (s->conn) cudaFreeAsync(s->conn, st);
   if (s->values) cudaFreeAsync(s->values, st);
   if (s->evol) cudaFreeAsync(s->evol, st);
+  if (s->adj) cudaFreeAsync(s->adj, st);
   delete s;
 }
 
@@ -460,6 +461,27 @@ sft_status sft_source_grid(sft_source s, int32_t precision, int32_t n_out[3], in
     for (size_t i = 0; i < h.size(); ++i) start_out[i] = h[i];
   }
   if (items_out) SFT_CUDA(cudaMemcpyAsync(items_out, L.cell_items, sizeof(int32_t) * L.nitems, cudaMemcpyDeviceToHost, st));
+  SFT_CUDA(cudaStreamSynchronize(st));
+  return SFT_OK;
+}
+
+sft_status sft_target_set_wait_limit(sft_target t, double seconds) {
+  if (!t) return fail(SFT_ERR_ARG, "null target");
+  if (!(seconds > 0.0) || !(seconds <= 3600.0)) return fail(SFT_ERR_ARG, "wait limit must be in (0, 3600] s");
+  const double ns = seconds * 1e9;
+  t->wait_ns = ns < 1.0 ? 1ull : (uint64_t)ns;
+  return SFT_OK;
+}
+
+sft_status sft_source_adjacency(sft_source s, int32_t precision, int32_t* adj_out) {
+  if (!s || !adj_out) return fail(SFT_ERR_ARG, "null source or output");
+  if (precision != SFT_PREC_FP32 && precision != SFT_PREC_FP64) return fail(SFT_ERR_ARG, "bad precision");
+  cudaStream_t st = s->stream;
+  DevBuf<int32_t> d_err(st);
+  SFT_CUDA(d_err.alloc(1));
+  SFT_CUDA(cudaMemsetAsync(d_err.p, 0, sizeof(int32_t), st));
+  if (sft_status r = build_locator(s, precision, st, d_err.p)) return r;
+  SFT_CUDA(cudaMemcpyAsync(adj_out, s->adj, sizeof(int32_t) * (size_t)s->ne * (s->dim + 1), cudaMemcpyDefault, st));
   SFT_CUDA(cudaStreamSynchronize(st));
   return SFT_OK;
 }

@@ -24,7 +24,7 @@ struct AsmParams {
   int64_t nv, ne, nes;
   int nf, N, U, G, LPE;
   int64_t ntasks;
-  PhiloxKey key;
+  PhiloxRoundKeys rk;
   uint32_t stream_id;
   double alpha;
   double c_det;   // alpha / ((d+1)(d+2)): exact P1 mass factor of the control term
@@ -47,7 +47,8 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const P* __restrict__ tx, c
                                                   const GridP<P>* __restrict__ gp,
                                                   const int32_t* __restrict__ cell_start,
                                                   const int32_t* __restrict__ cell_items,
-                                                  const P* __restrict__ recs, const P* __restrict__ vals,
+                                                  const P* __restrict__ recs, const int32_t* __restrict__ adj,
+                                                  const P* __restrict__ vals,
                                                   AsmParams p, double* __restrict__ b,
                                                   int32_t* __restrict__ sample_elem, P* __restrict__ pmu,
                                                   int64_t* __restrict__ counters) {
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const P* __restrict__ tx, c
     }
 
     for (int u = u0; active && u < p.U; u += ustep) {
-      const uint4 w = philox4x32_10(make_uint4((uint32_t)u, (uint32_t)t, p.stream_id, 0u), p.key);
+      const uint4 w = philox4x32_10(make_uint4((uint32_t)u, (uint32_t)t, p.stream_id, 0u), p.rk);
 #pragma unroll
       for (int s = 0; s < SPU; ++s) {
         const int j = SPU * u + s;
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const P* __restrict__ tx, c
         } else {
           P X[D];
           map_point<D, P>(lam, xv, X);
-          e = locate_point<D, P>(gr, cell_start, cell_items, recs, X, mu, status);
+          e = locate_point<D, P>(gr, cell_start, cell_items, recs, adj, X, mu, status);
           if (MODE != kAsmPlain) sample_elem[idx] = e;
           if (MODE == kAsmRecord) {
 #pragma unroll
@@ -143,8 +144,8 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const P* __restrict__ tx, c
     }
 
     // segmented suffix combine: lane seg_lo ends with its element's totals
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
+    // (log2 LPE rounds: a segment spans LPE lanes)
+    for (int o = 1; o < p.LPE; o <<= 1) {
       const bool take = lane + o < seg_hi;
 #pragma unroll
       for (int f = 0; f < NF; ++f)
@@ -190,7 +191,7 @@ static void launch_t(sft_source_s* s, sft_target_s* t, const AssembleArgs& a, co
   auto args = [&](auto kern) {
     ::sft::note_launch(), kern<<<(unsigned)blocks, threads, 0, st>>>((const P*)t->coordsP[a.prec], t->conn, t->vol, t->vol32, (const P*)a.g,
                                                (const GridP<P>*)L.grid, L.cell_start, L.cell_items,
-                                               (const P*)L.recs, (const P*)L.vals, p, a.b, a.sample_elem,
+                                               (const P*)L.recs, L.adj, (const P*)L.vals, p, a.b, a.sample_elem,
                                                (P*)a.pmu, a.counters);
   };
   if (a.mode == kAsmCached) args(k_assemble<D, P, NF, kAsmCached>);
@@ -224,8 +225,7 @@ sft_status launch_assembly(sft_source_s* s, sft_target_s* t, const AssembleArgs&
   p.LPE = p.U >= 4 ? 4 : p.U;
   p.G = 32 / p.LPE;
   p.ntasks = (t->ne + p.G - 1) / p.G;
-  p.key.k0 = (uint32_t)a.seed;
-  p.key.k1 = (uint32_t)(a.seed >> 32);
+  p.rk = philox_round_keys(a.seed);
   p.stream_id = a.stream_id;
   p.alpha = a.alpha;
   p.c_det = a.alpha / (double)((t->dim + 1) * (t->dim + 2));

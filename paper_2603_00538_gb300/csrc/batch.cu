@@ -38,6 +38,7 @@ struct BReq {
   const int32_t* cell_start;
   const int32_t* cell_items;
   const float* recs;
+  const int32_t* adj;
   const float* vals;
   int64_t nes;
   int32_t nf, N, U, G, LPE;
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_control(const BReq* __r
     for (int a = 0; a < D; ++a) X[a] = R.tx[i * D + a];
     float mu[D + 1];
     int status;
-    const int32_t e = locate_point<D, float>(gr, R.cell_start, R.cell_items, R.recs, X, mu, status);
+    const int32_t e = locate_point<D, float>(gr, R.cell_start, R.cell_items, R.recs, R.adj, X, mu, status);
     n_fb += status == 1;
     n_em += status == 2;
     for (int f = 0; f < R.nf; ++f) R.g[(int64_t)f * R.nv + i] = e >= 0 ? eval_p1<D, float>(R.vals, R.nes, f, e, mu) : 0.f;
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(kBatchThreads, NF <= 2 ? 4 : (NF <= 4 ? 3 : 2)
           map_point<D, float>(lam, xv, X);
           float mu[K];
           int status;
-          const int32_t e = locate_point<D, float>(gr, R.cell_start, R.cell_items, R.recs, X, mu, status);
+          const int32_t e = locate_point<D, float>(gr, R.cell_start, R.cell_items, R.recs, R.adj, X, mu, status);
           n_fb += status == 1;
           n_em += status == 2;
 #pragma unroll
@@ -1118,6 +1119,7 @@ static sft_status build_batch(sft_batch_s* B, const sft_options* opts, int autot
     R.cell_start = L.cell_start;
     R.cell_items = L.cell_items;
     R.recs = (const float*)L.recs;
+    R.adj = L.adj;
     R.vals = (const float*)L.vals;
     R.nes = s->ne;
     R.nf = o.field_count > 0 ? o.field_count : s->nf;

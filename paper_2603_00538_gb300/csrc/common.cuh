@@ -19,27 +19,58 @@ namespace sft {
 // ---------------------------------------------------------------------------
 struct PhiloxKey { uint32_t k0, k1; };
 
+// One round: the two 32x32 -> 64-bit products (one wide multiply each gives
+// both halves), their high halves mixed with the other two words and the
+// round key.
+__device__ __forceinline__ uint4 philox_round(uint4 c, uint32_t k0, uint32_t k1) {
+  const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+  const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+  return make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
+}
+
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, PhiloxKey k) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-    c = make_uint4(hi1 ^ c.y ^ k.k0, lo1, hi0 ^ c.w ^ k.k1, lo0);
+    c = philox_round(c, k.k0, k.k1);
     k.k0 += 0x9E3779B9u;
     k.k1 += 0xBB67AE85u;
   }
   return c;
 }
 
+// The ten round keys of one key (key + r (0x9E3779B9, 0xBB67AE85) mod 2^32),
+// formed once on the host: passed in a kernel's parameters they are operands
+// of the round's XOR, so the hot loop spends no instruction on the schedule.
+struct PhiloxRoundKeys { uint32_t k0[10], k1[10]; };
+
+inline PhiloxRoundKeys philox_round_keys(uint64_t seed) {
+  PhiloxRoundKeys rk;
+  uint32_t a = (uint32_t)seed, b = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    rk.k0[r] = a;
+    rk.k1[r] = b;
+    a += 0x9E3779B9u;
+    b += 0xBB67AE85u;
+  }
+  return rk;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxRoundKeys& rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) c = philox_round(c, rk.k0[r], rk.k1[r]);
+  return c;
+}
+
 // Uniform(0,1) from one 32-bit word, exact in the target precision:
 // FP32 odd multiples of 2^-24, u = ((x >> 8) | 1) 2^-24; FP64 (x + 1/2) 2^-32.
-// Formed from the bit pattern (1 + m 2^-23 has mantissa m) with exact
-// subtract/add, so no int->float conversion instruction is issued: on this
-// GPU conversions share the narrow FP64 pipe. Value-identical to the
-// definition above.
+// Formed from the bit pattern (1 + m 2^-23 has mantissa m) and one exact
+// addition, so no int->float conversion instruction is issued: on this GPU
+// conversions share the narrow FP64 pipe. Value-identical to the definition
+// above: (1 + k 2^-23) + (2^-24 - 1) = (2k + 1) 2^-24 has 24 significant bits,
+// so the sum is exact, and (x >> 8) | 1 = 2 (x >> 9) + 1.
 __device__ __forceinline__ float u01f(uint32_t x) {
   const float one_m = __uint_as_float(0x3F800000u | (x >> 9));  // 1 + (x>>9) 2^-23
-  return __fadd_rn(__fsub_rn(one_m, 1.0f), 0x1p-24f);           // (2 (x>>9) + 1) 2^-24
+  return __fadd_rn(one_m, -0x1.fffffep-1f);                      // (2 (x>>9) + 1) 2^-24
 }
 // float -> double without a conversion instruction (exact): a normal float's
 // sign, rebiased exponent and mantissa placed in the double's fields; zero,
@@ -55,7 +86,7 @@ __device__ __forceinline__ double f2d(double x) { return x; }
 
 __device__ __forceinline__ double u01d(uint32_t x) {
   const double one_m = __longlong_as_double((long long)(0x3FF0000000000000ull | ((uint64_t)x << 20)));
-  return __dadd_rn(__dsub_rn(one_m, 1.0), 0x1p-33);              // (2x + 1) 2^-33
+  return __dadd_rn(one_m, -0x1.ffffffffp-1);                     // (2x + 1) 2^-33, exact
 }
 
 // ---------------------------------------------------------------------------
@@ -295,23 +326,55 @@ __device__ __forceinline__ void load_record(const P* __restrict__ recs, int32_t 
   }
 }
 
-// Locate X: scan the candidates of its cell in list order (decreasing depth
-// of the cell centre in the element, ties ascending id), return the first
-// whose predicate accepts; if none accepts, the candidate with the largest
-// min(mu) (the earlier one on ties); -1 for an empty cell.
+// predicate evaluations of the walk before the cell's list is scanned
+constexpr int kWalkSteps = 12;
+
+// Locate X. A walk through face neighbours starts at the first element of
+// X's cell (the one deepest at the cell centre): at element e the predicate's
+// mu is evaluated; all mu >= 0 accepts e, otherwise the walk moves to the
+// element across the face opposite the vertex with the smallest mu (the
+// first on ties: the face X lies farthest outside of). adj[e][m] is that
+// neighbour, -1 on the boundary. The walk gives up at a boundary face or
+// after kWalkSteps evaluations; the cell's list is then scanned in order
+// (decreasing depth of the cell centre, ties ascending id): the first
+// accepting candidate wins, if none accepts the candidate with the largest
+// min(mu) (the earlier one on ties), -1 for an empty cell.
 // status: 0 accepted, 1 nearest candidate, 2 empty cell. mu is the returned
-// element's barycentric vector. The first pass only tests acceptance; the
-// nearest-candidate pass runs only when nothing accepted (rare: points on
-// the domain boundary within rounding), so the common path carries no
-// bookkeeping for it. The result is that of a single scan with both rules.
+// element's barycentric vector. A point inside one element gets that element
+// whichever way it is found; the order of the search decides only between
+// elements that all accept a point on their shared face.
 template <int D, typename P>
 __device__ __forceinline__ int32_t locate_point(const GridP<P>& g, const int32_t* __restrict__ cell_start,
                                                 const int32_t* __restrict__ cell_items,
-                                                const P* __restrict__ recs, const P X[D], P mu[D + 1],
-                                                int& status) {
+                                                const P* __restrict__ recs, const int32_t* __restrict__ adj,
+                                                const P X[D], P mu[D + 1], int& status) {
   constexpr int L = RecLen<D>::value;
   const int32_t c = cell_of<D, P>(g, X);
   const int32_t p0 = __ldg(cell_start + c), p1 = __ldg(cell_start + c + 1);
+  if (p0 < p1) {
+    int32_t e = __ldg(cell_items + p0);
+    for (int s = 0; s < kWalkSteps; ++s) {
+      P r[L];
+      load_record<D, P>(recs, e, r);
+      P m[D + 1];
+      bary_from_record<D, P>(r, X, m);
+      P mn = m[0];
+      int am = 0;
+#pragma unroll
+      for (int q = 1; q <= D; ++q)
+        if (m[q] < mn) { mn = m[q]; am = q; }
+      if (mn >= P(0)) {
+#pragma unroll
+        for (int q = 0; q <= D; ++q) mu[q] = m[q];
+        status = 0;
+        return e;
+      }
+      const int32_t nx = __ldg(adj + (int64_t)e * (D + 1) + am);
+      if (nx < 0) break;
+      e = nx;
+    }
+  }
+  // the walk gave up (boundary or step limit): the cell's list in order
   int32_t best = -1;
   P best_score = P(0);
   for (int32_t p = p0; p < p1; ++p) {
@@ -382,7 +445,8 @@ enum DevErr : int32_t {
   DEV_BAD_INDEX = 2,
   DEV_VALENCE = 3,
   DEV_BAD_ELEMENT = 4,
-  DEV_NONFINITE = 5
+  DEV_NONFINITE = 5,
+  DEV_BAD_DIAGONAL = 6
 };
 
 }  // namespace sft

@@ -76,6 +76,7 @@ struct Locator {
   void* recs = nullptr;           // [ne][RecLen] P
   void* vals = nullptr;           // [nf][ne][4] P
   void* coordsP = nullptr;        // [nv][dim] P
+  const int32_t* adj = nullptr;   // the source's face neighbours (sft_source_s::adj)
 };
 
 }  // namespace sft
@@ -90,6 +91,8 @@ struct sft_source_s {
   int32_t* conn = nullptr;      // [ne][dim+1]
   void* values = nullptr;       // [nf][nv] input dtype
   double* evol = nullptr;       // [ne] FP64 element measures (made with the first locator)
+  int32_t* adj = nullptr;       // [ne][dim+1] neighbour across the face opposite vertex m, -1 on
+                                // the boundary (made with the first locator)
   double integral[sft::kMaxFields] = {0};
   bool integral_valid = false;  // integral[] matches the current values (made on first use)
   sft::Locator loc[2];          // index = sft_precision (0 FP64, 1 FP32)
@@ -116,6 +119,8 @@ struct sft_target_s {
   // sc = diag(M)^-1/2 and the FP32 values of sc_i M_ij sc_j
   double* sc = nullptr;         // [nv]
   float* val32s = nullptr;      // [nnz]
+  // limit of the solves' device waits (grid barriers), nanoseconds
+  uint64_t wait_ns = 2000000000ull;
 };
 
 namespace sft {

@@ -448,6 +448,66 @@ __global__ void k_cell_rank(const int32_t* __restrict__ cell_start, const RegEnt
   }
 }
 
+// Face neighbours of every element for the location walk: adj[e][m] = the
+// other element holding every vertex of the face opposite local vertex m
+// (the smallest id if several), -1 on the boundary. Found through the grid:
+// an element holding vertex v has v in its closure, and registration keeps
+// every cell a point of the element can fall in, so it is listed in the cell
+// of v. Faces m != 0 hold vertex 0 and are matched against the list of
+// cell(x_0); face 0 holds vertex 1 and is matched against the list of
+// cell(x_1). One thread per element.
+template <int D, typename P>
+__global__ void k_adjacency(const P* __restrict__ x, const int32_t* __restrict__ conn, int64_t nv, int64_t ne,
+                            const GridP<P>* __restrict__ gp, const int32_t* __restrict__ cell_start,
+                            const int32_t* __restrict__ cell_items, int32_t* __restrict__ adj) {
+  constexpr int K = D + 1;
+  const GridP<P> g = *gp;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v[K];
+    bool ok = true;
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+      v[m] = __ldg(conn + e * K + m);
+      ok = ok && v[m] >= 0 && v[m] < nv;
+    }
+    int32_t best[K];
+#pragma unroll
+    for (int m = 0; m < K; ++m) best[m] = INT32_MAX;
+    if (ok) {
+#pragma unroll
+      for (int pass = 0; pass < 2; ++pass) {
+        P X[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) X[a] = __ldg(x + (int64_t)v[pass] * D + a);
+        const int32_t c = cell_of<D, P>(g, X);
+        const int32_t p1 = __ldg(cell_start + c + 1);
+        for (int32_t p = __ldg(cell_start + c); p < p1; ++p) {
+          const int32_t e2 = __ldg(cell_items + p);
+          if (e2 == (int32_t)e) continue;
+          int32_t w[K];
+#pragma unroll
+          for (int r = 0; r < K; ++r) w[r] = __ldg(conn + (int64_t)e2 * K + r);
+          int shared = 0, miss = 0;
+#pragma unroll
+          for (int m = 0; m < K; ++m) {
+            bool in = false;
+#pragma unroll
+            for (int r = 0; r < K; ++r) in = in || w[r] == v[m];
+            shared += in;
+            miss = in ? miss : m;
+          }
+          if (shared != D || (pass == 0) == (miss == 0)) continue;
+#pragma unroll
+          for (int m = 0; m < K; ++m)
+            if (m == miss && e2 < best[m]) best[m] = e2;
+        }
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < K; ++m) adj[e * K + m] = best[m] == INT32_MAX ? -1 : best[m];
+  }
+}
+
 static unsigned grid_for(int64_t n, int threads = 256) {
   int64_t b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -544,6 +604,14 @@ static sft_status build_locator_t(sft_source_s* s, int prec, cudaStream_t st, in
   SFT_CUDA(cudaGetLastError());
   dfree(cell_count, st);
   dfree(reg, st);
+  // face neighbours for the location walk (one array per source mesh)
+  if (!s->adj) {
+    SFT_CUDA(dalloc(&s->adj, (size_t)s->ne * (D + 1), st));
+    ::sft::note_launch(), k_adjacency<D, P><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, s->nv, s->ne, g, L.cell_start,
+                                                                           L.cell_items, s->adj);
+    SFT_CUDA(cudaGetLastError());
+  }
+  L.adj = s->adj;
   L.built = true;
   return SFT_OK;
 }
@@ -598,7 +666,8 @@ __global__ void __launch_bounds__(256) k_locate_points(const TIn* __restrict__ p
                                                        const GridP<P>* __restrict__ gp,
                                                        const int32_t* __restrict__ cell_start,
                                                        const int32_t* __restrict__ cell_items,
-                                                       const P* __restrict__ recs, const P* __restrict__ vals,
+                                                       const P* __restrict__ recs, const int32_t* __restrict__ adj,
+                                                       const P* __restrict__ vals,
                                                        int64_t ne, int nf, int32_t* __restrict__ elem_out,
                                                        TOut* __restrict__ val_out, int64_t val_stride,
                                                        int64_t* __restrict__ counters, P* __restrict__ mu_out) {
@@ -613,7 +682,7 @@ __global__ void __launch_bounds__(256) k_locate_points(const TIn* __restrict__ p
     }
     P mu[D + 1];
     int status;
-    const int32_t e = locate_point<D, P>(g, cell_start, cell_items, recs, X, mu, status);
+    const int32_t e = locate_point<D, P>(g, cell_start, cell_items, recs, adj, X, mu, status);
     n_fallback += status == 1;
     n_empty += status == 2;
     if (elem_out) elem_out[i] = e;
@@ -645,7 +714,8 @@ static void launch_locate(sft_source_s* s, const Locator& L, int64_t n, const vo
   const P* vals = (const P*)L.vals;
 #define SFT_LOC(TIN, TOUT)                                                                                      \
   ::sft::note_launch(), k_locate_points<D, P, TIN, TOUT><<<blocks, 256, 0, st>>>((const TIN*)pts, n, g, L.cell_start, L.cell_items, \
-                                                           recs, vals, s->ne, nf, elem_out, (TOUT*)val_out,  \
+                                                           recs, L.adj, vals, s->ne, nf, elem_out,          \
+                                                           (TOUT*)val_out,                                   \
                                                            val_stride, counters, (P*)mu_out)
   if (pts_are_double) {
     if (val_is_double) SFT_LOC(double, double); else SFT_LOC(double, P);

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_pcg(const int32_t* __restrict
                                                        int64_t n, int nrhs, const double* __restrict__ b,
                                                        double* __restrict__ x, double* r, double* z, double* p,
                                                        double* q, double* part, PcgCtl* ctl, double tol,
-                                                       int max_iter) {
+                                                       int max_iter, uint64_t wait_ns) {
   __shared__ double tot[kMaxFields * 2];
   __shared__ double bnorm[kMaxFields], rz[kMaxFields], beta[kMaxFields], alpha[kMaxFields];
   __shared__ int conv[kMaxFields];
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_pcg(const int32_t* __restrict
     }
   }
   block_partials(v, nrhs, part);
-  if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+  if (!grid_sync(&ctl->bar, nb, &ctl->err, wait_ns)) return;
   reduce_partials(part, nb, nrhs, tot);
   if (threadIdx.x == 0) {
     for (int f = 0; f < nrhs; ++f) {
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_pcg(const int32_t* __restrict
       }
     }
     block_partials(v, nrhs, part);
-    if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+    if (!grid_sync(&ctl->bar, nb, &ctl->err, wait_ns)) return;
     reduce_partials(part, nb, nrhs, tot);
     if (threadIdx.x == 0)
       for (int f = 0; f < nrhs; ++f) alpha[f] = conv[f] ? 0.0 : rz[f] / tot[f * 2];
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_pcg(const int32_t* __restrict
       }
     }
     block_partials(v, nrhs, part);
-    if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+    if (!grid_sync(&ctl->bar, nb, &ctl->err, wait_ns)) return;
     reduce_partials(part, nb, nrhs, tot);
     ++it;
     if (threadIdx.x == 0) {
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) k_mixed_cg(
     const int32_t* __restrict__ rp, const int32_t* __restrict__ col, const double* __restrict__ val,
     const float* __restrict__ aval, const double* __restrict__ sc, int64_t n, int nrhs,
     const double* __restrict__ b, double* x, double* t, float* r, float* p, float* q, float* y, double* partd,
-    float* partf, MixCtl* ctl, double tol, int max_iter, int warm) {
+    float* partf, MixCtl* ctl, double tol, int max_iter, int warm, uint64_t wait_ns) {
   __shared__ double totd[kMaxFields * 2];
   __shared__ float totf[NR];
   __shared__ double bnorm[NR], prev[NR], sig[NR], isig[NR];
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) k_mixed_cg(
       }
     }
     block_partials_d<NR>(v, nrhs, partd);
-    if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+    if (!grid_sync(&ctl->bar, nb, &ctl->err, wait_ns)) return;
     reduce_partials(partd, nb, nrhs, totd);
     if (threadIdx.x == 0)
       for (int f = 0; f < nrhs; ++f) bnorm[f] = sqrt(totd[2 * f]);
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) k_mixed_cg(
       }
     }
     block_partials_d<NR>(v, nrhs, partd);
-    if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+    if (!grid_sync(&ctl->bar, nb, &ctl->err, wait_ns)) return;
     reduce_partials(partd, nb, nrhs, totd);
     if (threadIdx.x == 0) {
       bool any = false;
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) k_mixed_cg(
       }
     }
     block_partials_f<NR>(vf, nrhs, partf);
-    if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+    if (!grid_sync(&ctl->bar, nb, &ctl->err, wait_ns)) return;
     reduce_partials_f<NR>(partf, nb, nrhs, totf);
     if (threadIdx.x == 0)
       for (int f = 0; f < nrhs; ++f) {
@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) k_mixed_cg(
         }
       }
       block_partials_f<NR>(vf, nrhs, partf);
-      if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+      if (!grid_sync(&ctl->bar, nb, &ctl->err, wait_ns)) return;
       reduce_partials_f<NR>(partf, nb, nrhs, totf);
       if (threadIdx.x == 0)
         for (int f = 0; f < nrhs; ++f) alpha[f] = act[f] ? rr[f] / totf[f] : 0.f;
@@ -526,7 +526,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) k_mixed_cg(
         }
       }
       block_partials_f<NR>(vf, nrhs, partf);
-      if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+      if (!grid_sync(&ctl->bar, nb, &ctl->err, wait_ns)) return;
       reduce_partials_f<NR>(partf, nb, nrhs, totf);
       ++it;
       if (threadIdx.x == 0)
@@ -551,7 +551,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) k_mixed_cg(
         x[k] += (sig[f] * si) * (double)y[k];
       }
     }
-    if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+    if (!grid_sync(&ctl->bar, nb, &ctl->err, wait_ns)) return;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl->cycles = cyc;
@@ -654,7 +654,8 @@ static sft_status launch_mixed(sft_target_s* t, int nrhs, const double* b, doubl
   float* pf = partf.p;
   void* args[] = {(void*)&rp, (void*)&col, (void*)&val, (void*)&aval, (void*)&sc, (void*)&n, (void*)&nrhs,
                   (void*)&b, (void*)&x, (void*)&tp, (void*)&r, (void*)&p, (void*)&q, (void*)&y,
-                  (void*)&pd, (void*)&pf, (void*)&c, (void*)&tol, (void*)&max_iter, (void*)&warm};
+                  (void*)&pd, (void*)&pf, (void*)&c, (void*)&tol, (void*)&max_iter, (void*)&warm,
+                  (void*)&t->wait_ns};
   const cudaError_t le = (::sft::note_launch(), cudaLaunchCooperativeKernel((const void*)k_mixed_cg<NR>, nblocks,
                                                                            kSolveThreads, args, 0, st));
   if (le != cudaSuccess) return cuda_fail(le, "cudaLaunchCooperativeKernel(k_mixed_cg)");
@@ -729,7 +730,7 @@ sft_status mass_solve(sft_target_s* t, int nrhs, const double* b, double* x, dou
   const double* dinv = t->dinv;
   void* args[] = {(void*)&rp, (void*)&col, (void*)&val, (void*)&dinv, (void*)&n, (void*)&nrhs, (void*)&b,
                   (void*)&x, (void*)&r, (void*)&z, (void*)&p, (void*)&q, (void*)&part,
-                  (void*)&ctl, (void*)&tol, (void*)&max_iter};
+                  (void*)&ctl, (void*)&tol, (void*)&max_iter, (void*)&t->wait_ns};
   cudaError_t le;
   le = (::sft::note_launch(), cudaLaunchCooperativeKernel((const void*)k_pcg<1>, nblocks, kSolveThreads, args, 0, st));
   if (le != cudaSuccess) return cuda_fail(le, "cudaLaunchCooperativeKernel(k_pcg)");
@@ -824,12 +825,18 @@ static sft_status static_scratch(void** out) {
   return SFT_OK;
 }
 
+// Jacobi inverse of the caller's matrix; a row without a positive diagonal
+// entry (the matrix cannot be SPD) sets DEV_BAD_DIAGONAL, reported as
+// SFT_ERR_ARG (the CG kernel sees the error word and leaves at its first
+// barrier)
 __global__ void k_jacobi_inverse(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                 const double* __restrict__ val, int64_t n, double* __restrict__ dinv) {
+                                 const double* __restrict__ val, int64_t n, double* __restrict__ dinv,
+                                 int32_t* err) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double d = 0.0;
     for (int32_t k = rp[i]; k < rp[i + 1]; ++k)
       if (col[k] == i) d = val[k];
+    if (!(d > 0.0)) set_error(err, DEV_BAD_DIAGONAL);
     dinv[i] = d > 0.0 ? 1.0 / d : 0.0;
   }
 }
@@ -889,18 +896,20 @@ extern "C" sft_status sft_mass_solve_static(int64_t n, const int32_t* row_ptr, c
   // region is written by the kernels before it is read
   SFT_CUDA(cudaMemsetAsync(ctl, 0, sizeof(PcgCtl), st));
   ::sft::note_launch(), k_jacobi_inverse<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(
-      row_ptr, col, val, n, dinv);
+      row_ptr, col, val, n, dinv, &ctl->err);
   SFT_CUDA(cudaGetLastError());
   const double* dinv_c = dinv;
+  const uint64_t wait_ns = kDefaultWaitNs;
   void* args[] = {(void*)&row_ptr, (void*)&col, (void*)&val, (void*)&dinv_c, (void*)&n, (void*)&nrhs, (void*)&b,
                   (void*)&u, (void*)&r, (void*)&z, (void*)&p, (void*)&q, (void*)&part,
-                  (void*)&ctl, (void*)&tol, (void*)&max_iter};
+                  (void*)&ctl, (void*)&tol, (void*)&max_iter, (void*)&wait_ns};
   const cudaError_t le =
       (::sft::note_launch(), cudaLaunchCooperativeKernel((const void*)k_pcg<1>, nblocks, kSolveThreads, args, 0, st));
   if (le != cudaSuccess) return cuda_fail(le, "cudaLaunchCooperativeKernel(k_pcg, static scratch)");
   PcgCtl h;
   SFT_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
   SFT_CUDA(cudaStreamSynchronize(st));
+  if (h.err == DEV_BAD_DIAGONAL) return fail(SFT_ERR_ARG, "a row has no positive diagonal entry (matrix not SPD)");
   if (h.err != 0) return fail(SFT_ERR_DEVICE_STATUS, "CG kernel: grid barrier wait expired");
   int it = 0, conv = 1;
   double rel = 0.0;

@@ -37,16 +37,22 @@ __device__ __forceinline__ T warp_inclusive_scan(T v, int lane) {
   return v;
 }
 
+// limit of a device wait (grid barrier, mbarrier phase) unless the caller
+// sets another (sft_target_set_wait_limit for the solves on a target)
+constexpr uint64_t kDefaultWaitNs = 2000000000ull;
+
 // Grid-wide barrier for a cooperative launch (all blocks co-resident).
 // Sense by generation counter; the wait gives up after `timeout_ns`, sets
-// DEV_BARRIER_TIMEOUT in *err and returns false (callers then return).
+// DEV_BARRIER_TIMEOUT in *err and returns false (callers then return). A
+// block that finds the error word set while it waits leaves at once, so after
+// one expired wait every block leaves at the next barrier it waits at.
 struct GridBarrier {
   unsigned int count;
   unsigned int gen;
 };
 
 __device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned int nblocks, int32_t* err,
-                                          uint64_t timeout_ns = 2000000000ull) {
+                                          uint64_t timeout_ns = kDefaultWaitNs) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {

@@ -96,6 +96,25 @@ def test_locate_bit_exact(orc, dim, prec):
     assert np.max(np.abs(v_gpu[:, :3000] - ref)) <= tol * np.max(np.abs(ref))
 
 
+@pytest.mark.parametrize("dim,prec", [(2, FP64), (2, FP32), (3, FP64), (3, FP32)])
+def test_adjacency_bit_exact(orc, dim, prec):
+    """Face neighbours of the location walk, built on the GPU through the
+    grid, equal the oracle's (built from their definition) entry for entry,
+    on a jittered mesh and on a Delaunay / graded one."""
+    meshes = ([W.jittered_tri_mesh(29, 5), W.delaunay_tri_mesh(700, 9, 5)] if dim == 2 else
+              [W.jittered_kuhn_mesh(7, 5), W.morton_reorder(W.jittered_kuhn_mesh(5, 6))])
+    for m in meshes:
+        if dim == 3 and m is meshes[1]:
+            m = W.Mesh(m.coords ** 2, m.conn, None)    # graded towards the origin
+        m = W.with_values(m, [W.paper_f2] if dim == 2 else [lambda x: x[:, 0]])
+        if prec == FP32:
+            m = W.as_precision(m, np.float32)
+        s = sft.mesh_source(m, device=DEV)
+        adj = sft.sft_source_adjacency(s, prec)
+        ref = orc.Grid(1 if prec == FP32 else 0, m.coords, m.conn).adjacency()
+        assert np.array_equal(adj, ref)
+
+
 def test_locate_host_pointers_match_device(orc):
     m = W.with_values(W.jittered_tri_mesh(12, 1), [W.paper_f3])
     pts = np.random.default_rng(0).random((777, 2))

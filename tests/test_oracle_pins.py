@@ -300,6 +300,76 @@ def test_grid_locate_equals_brute_force_and_exact_containment(orc, dim, prec):
     assert mism <= pts.shape[0] // 50
 
 
+@pytest.mark.parametrize("mesh", ["tri", "delaunay", "kuhn", "star"])
+def test_face_neighbours_brute_force(orc, mesh):
+    """The walk's face neighbours: for every element and local vertex m, the
+    other element holding all vertices of the face opposite m, found by a scan
+    of every element; each interior face pairs two elements both ways, and the
+    number of boundary faces is that of the domain's boundary."""
+    if mesh == "tri":
+        m = W.jittered_tri_mesh(6, 4)
+    elif mesh == "delaunay":
+        m = W.delaunay_tri_mesh(60, 5, 4)
+    elif mesh == "kuhn":
+        m = W.jittered_kuhn_mesh(3, 4)
+    else:   # every tetrahedron shares the centre vertex 0
+        c = np.array([[0.5, 0.5, 0.5]] + [[x, y, z] for z in (0, 1) for y in (0, 1) for x in (0, 1)], float)
+        faces = [(1, 2, 4), (1, 4, 3), (5, 6, 8), (5, 8, 7), (1, 2, 6), (1, 6, 5), (3, 4, 8), (3, 8, 7),
+                 (1, 3, 7), (1, 7, 5), (2, 4, 8), (2, 8, 6)]
+        m = W.Mesh(c, np.array([[0, *f] for f in faces], np.int32), None)
+        W._fix_orientation(m)
+    k = m.dim + 1
+    adj = orc.Grid(0, m.coords, m.conn).adjacency()
+    sets = [set(r.tolist()) for r in m.conn]
+    nb = 0
+    for e in range(m.nelems):
+        for q in range(k):
+            face = sets[e] - {int(m.conn[e, q])}
+            others = [e2 for e2 in range(m.nelems) if e2 != e and face <= sets[e2]]
+            assert adj[e, q] == (min(others) if others else -1), (e, q)
+            if others:
+                e2 = adj[e, q]
+                back = [r for r in range(k) if int(m.conn[e2, r]) not in face]
+                assert len(back) == 1 and adj[e2, back[0]] == e
+            else:
+                nb += 1
+    if mesh == "tri":
+        assert nb == 4 * 6                       # 6 edges per side of the square
+    elif mesh == "kuhn":
+        assert nb == 6 * 3 * 3 * 2               # 2 triangles per cube face, 6 sides
+    elif mesh == "star":
+        assert nb == 12                          # the cube's surface triangles
+
+
+@pytest.mark.parametrize("dim,prec", [(2, 0), (2, 1), (3, 0), (3, 1)])
+def test_walk_locates_interior_points_exactly(orc, dim, prec):
+    """A point inside exactly one element, by a margin above the predicate's
+    rounding, is located in that element whatever the search path: the walk
+    agrees with a scan of every element, including from starting cells far
+    from the point's element (graded mesh)."""
+    src = W.jittered_tri_mesh(9, 8) if dim == 2 else W.jittered_kuhn_mesh(4, 8)
+    coords = src.coords.astype(np.float32).astype(np.float64) if prec else src.coords
+    # grade the mesh towards the origin: cells then hold very different elements
+    coords = coords ** 2
+    if prec:
+        coords = coords.astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(11)
+    e_true = rng.integers(0, src.nelems, 4000)
+    w = rng.dirichlet(np.ones(dim + 1), 4000)
+    pts = np.einsum("qk,qkd->qd", w, coords[src.conn[e_true]])
+    if prec:
+        pts = pts.astype(np.float32).astype(np.float64)
+    g = orc.Grid(prec, coords, src.conn)
+    eg, sg = g.locate(pts)
+    checked = 0
+    for i in range(pts.shape[0]):
+        mu = _exact_bary(coords, src.conn, e_true[i], pts[i])
+        if min(mu) > (1e-4 if prec else 1e-9):
+            assert eg[i] == e_true[i] and sg[i] == 0, (i, eg[i], e_true[i])
+            checked += 1
+    assert checked > 3000
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 def test_grid_structure(orc, dim):
     src = W.jittered_tri_mesh(9, 2) if dim == 2 else W.jittered_kuhn_mesh(3, 2)
