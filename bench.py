@@ -67,6 +67,11 @@ WORKLOADS = {
 # element conn + coords + g + b read-modify-write (2D 72 B, 3D 112 B)
 BYTES_PER_QUERY = {2: 48, 3: 76}
 BYTES_PER_ELEM = {2: 72, 3: 112}
+# the same minimum with FP64 records, values, coordinates and control values
+# (the all-FP64 path): per query 8 + 4 + 2 x (2D 36, 3D 64); per element
+# conn 4k + coords 8kd + g 8k + b read-modify-write 16k
+BYTES_PER_QUERY_FP64 = {2: 84, 3: 140}
+BYTES_PER_ELEM_FP64 = {2: 132, 3: 208}
 KERNEL_FILES = ["paper_2603_00538_gb300/csrc/assemble.cu", "paper_2603_00538_gb300/csrc/common.cuh",
                 "paper_2603_00538_gb300/csrc/accum.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "assemble_traffic.txt")
@@ -104,13 +109,17 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples (every 100 ms) while the timed region runs."""
+    """nvidia-smi samples (every 100 ms) while the timed region runs. The
+    sampler process is started, and its first sample awaited, before the
+    region begins, so that nvidia-smi's own start-up does not land inside a
+    timed step; the summary uses the samples taken inside the region."""
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.rows = []
         self._stop = threading.Event()
         self._proc = None
+        self.t0 = None
 
     def __enter__(self):
         q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
@@ -121,15 +130,19 @@ class ClockSampler:
                                            "--format=csv,noheader,nounits", "-lms", "100"],
                                           stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             threading.Thread(target=self._read, daemon=True).start()
+            deadline = time.time() + 5.0
+            while not self.rows and time.time() < deadline and self._proc.poll() is None:
+                time.sleep(0.01)
         except (OSError, FileNotFoundError):
             self._proc = None
+        self.t0 = time.time()
         return self
 
     def _read(self):
         for line in self._proc.stdout:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) >= 7:
-                self.rows.append(parts)
+                self.rows.append([time.time()] + parts)
 
     def __exit__(self, *a):
         if self._proc:
@@ -141,14 +154,16 @@ class ClockSampler:
                 self._proc.kill()
 
     def summary(self):
-        if not self.rows:
+        inside = [r[1:] for r in self.rows if self.t0 is not None and r[0] >= self.t0]
+        rows = inside or [r[1:] for r in self.rows]   # a region shorter than one sample period
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(rows)}
 
 
 def dist_init():
@@ -194,7 +209,7 @@ def run_ours(args):
     src, tgt, p = make_workload(args.workload, args.scale)
     N, tol = p["samples_per_elem"], p["cg_tol"]
     dim = src.dim
-    prec = sft.SFT_PREC_FP32
+    prec = sft.SFT_PREC_FP64 if args.precision == "fp64" else sft.SFT_PREC_FP32
     stream = torch.cuda.current_stream()
     sc, sk, sv = (torch.as_tensor(np.ascontiguousarray(a)).to(dev) for a in (src.coords, src.conn, src.values))
     tc, tk = (torch.as_tensor(np.ascontiguousarray(a)).to(dev) for a in (tgt.coords, tgt.conn))
@@ -247,22 +262,31 @@ def run_ours(args):
     # errors at which the throughput is measured
     e_mass = cons_last[0][0]
     e_l2, e_l2_se = estimate_l2(src, tgt, u[0].cpu().numpy(), dev) if rank == 0 else (None, None)
+    # the FP32 path against an all-FP64 run of the same workload (untimed)
+    prec_cmp = precision_comparison(args, sc, sk, sv, tc, tk, N, tol) if rank == 0 else None
+    # exact judge and comparison method (2D): mesh intersection (untimed)
+    mi = mesh_intersection_leg(args, sc, sk, sv, tc, tk, u[0], N, tol) if rank == 0 and dim == 2 else None
 
     if rank == 0:
         hbm, which = peaks()
         mean_asm = float(np.mean(asm_ms))
-        alg_bytes = BYTES_PER_QUERY[dim] * tgt.nelems * N + BYTES_PER_ELEM[dim] * tgt.nelems
+        bq, be = (BYTES_PER_QUERY_FP64, BYTES_PER_ELEM_FP64) if args.precision == "fp64" else \
+            (BYTES_PER_QUERY, BYTES_PER_ELEM)
+        alg_bytes = bq[dim] * tgt.nelems * N + be[dim] * tgt.nelems
         achieved = alg_bytes / (mean_asm / 1e3) / 1e9
-        traffic = measured_traffic(args.workload)
+        traffic = measured_traffic(args.workload) if args.precision == "fp32" else None
         cpu = cpu_baseline(args, src, tgt, p, args.cpu_frac_baseline) if not args.skip_cpu else None
         line = {
             "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}"
-                                   + ("" if args.scale == 1.0 else f" (element counts x{args.scale})"),
+                                   + ("" if args.scale == 1.0 else f" (element counts x{args.scale})")
+                                   + (" [all-FP64 run: FP64 sampling, location and evaluation]"
+                                      if args.precision == "fp64" else ""),
                        "queries_per_step": queries, "target_elements": tgt.nelems, "samples_per_elem": N,
                        "source_elements": src.nelems, "grid_scale_L": args.grid_scale, "sampling": args.sampling,
+                       "precision": args.precision,
                        "l2": "flushed between steps (256 MB write)",
                        "accumulation": "FP64 load vector, CG and reductions",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -272,7 +296,10 @@ def run_ours(args):
             "assembly_queries_per_s": tgt.nelems * N / (mean_asm / 1e3),
             "accuracy": {"E_mass": e_mass, "E_L2_estimate": e_l2, "E_L2_stderr": e_l2_se,
                          "cg_iters": stats_last["cg_iters"], "cg_rel_resid": stats_last["cg_rel_resid"],
-                         "fallback_queries": stats_last["fallback_queries"]},
+                         "fallback_queries": stats_last["fallback_queries"],
+                         "fp32_vs_fp64": prec_cmp,
+                         "E_L2_exact": mi["E_L2"] if mi else None},
+            "mesh_intersection": mi,
             "roofline": {"kernel": "sft::k_assemble", "bound": "hbm", "achieved": achieved, "peak": hbm,
                          "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                          "peak_source": which, "algorithmic_bytes": alg_bytes},
@@ -398,6 +425,7 @@ def run_batch(args):
                        "queries_per_step": queries, "target_elements": int(sum(q["elems"] for q in reqs)),
                        "l2": "flushed between steps (256 MB write)", "plan_build_s": plan_s,
                        "graph": stats["graph"], "tiles": stats["tile"],
+                       "autotuned_groups": sft.sft_batch_groups(plan),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "breakdown_ms": {"control": stats["ms_control"], "assembly": stats["ms_assembly"],
                              "solve": stats["ms_solve"], "cg_max_iters": stats["max_cg_iters"]},
@@ -868,6 +896,75 @@ def count_launches(step):
     return sft.sft_kernel_launches() - n0
 
 
+def mesh_intersection_leg(args, sc, sk, sv, tc, tk, u, N, tol):
+    """The exact judge at full size (2D): the supermesh L2 error of the
+    benchmark's solution u, and the mesh-intersection load vector (the
+    paper's comparison method) timed with CUDA events against the Monte
+    Carlo assembly of the same source and target; the Monte Carlo load
+    vector's distance from the exact one."""
+    import torch
+    import paper_2603_00538_gb300 as sft
+    s = sft.sft_source_create(sc, sk, sv, args.grid_scale)
+    t = sft.sft_target_create(tc, tk)
+    stream = torch.cuda.current_stream()
+    b = torch.zeros(tc.shape[0], dtype=torch.float64, device=sc.device)
+    sft.sft_mi_load_vector(s, t, 0, b_out=b)            # builds the FP64 location structure once
+    ms = []
+    for _ in range(3):
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sft.sft_mi_load_vector(s, t, 0, b_out=b)
+        z.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(z))
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    e, n = sft.sft_mi_l2_error(s, t, u, 0)
+    z.record(stream)
+    torch.cuda.synchronize()
+    bmc = torch.zeros((sv.shape[0], tc.shape[0]), dtype=torch.float64, device=sc.device)
+    umc = torch.zeros_like(bmc)
+    _, st, _ = sft.sft_transfer(s, t, N, sft.SFT_PREC_FP32, seed=0, cg_tol=tol, u_out=umc, b_out=bmc,
+                                sampling=_sampling(args))
+    bx = b.cpu().numpy()
+    bm = bmc[0].cpu().numpy()
+    s.close()
+    t.close()
+    return {"E_L2": e / n, "load_vector_ms": float(np.median(ms)), "l2_error_ms": a.elapsed_time(z),
+            "mc_assembly_ms": st["ms_assembly"],
+            "b_mc_vs_exact_rel_l2": float(np.linalg.norm(bm - bx) / np.linalg.norm(bx)),
+            "method": "2D clipping of every overlapping (target, source) triangle pair, FP64, edge-midpoint rule"}
+
+
+def precision_comparison(args, sc, sk, sv, tc, tk, N, tol):
+    """One FP32-path transfer and one all-FP64 transfer of the same workload
+    (same Philox streams: the FP32 uniforms are the FP64 ones rounded to 24
+    bits), outside the timed region: the FP32 path's load vector and solution
+    against the FP64 run (2-norm ratio and largest entry against the largest
+    entry), each run's conservation error and assembly time."""
+    import torch
+    import paper_2603_00538_gb300 as sft
+    out, res = {}, {}
+    s = sft.sft_source_create(sc, sk, sv, args.grid_scale)
+    t = sft.sft_target_create(tc, tk)
+    for name, prec in (("fp32", sft.SFT_PREC_FP32), ("fp64", sft.SFT_PREC_FP64)):
+        u = torch.zeros((sv.shape[0], tc.shape[0]), dtype=torch.float64, device=sc.device)
+        b = torch.zeros_like(u)
+        sft.sft_transfer(s, t, N, prec, seed=0, cg_tol=tol, u_out=u, b_out=b, sampling=_sampling(args))
+        _, st, _ = sft.sft_transfer(s, t, N, prec, seed=0, cg_tol=tol, u_out=u, b_out=b, sampling=_sampling(args))
+        e = sft.sft_conservation_error(s, t, u[0])[0]
+        res[name] = (b[0].cpu().numpy(), u[0].cpu().numpy())
+        out[f"E_mass_{name}"] = e
+        out[f"assembly_ms_{name}"] = st["ms_assembly"]
+    s.close()
+    t.close()
+    for k, i in (("b", 0), ("u", 1)):
+        a, r = res["fp32"][i], res["fp64"][i]
+        out[f"{k}_rel_l2"] = float(np.linalg.norm(a - r) / np.linalg.norm(r))
+        out[f"{k}_rel_max"] = float(np.max(np.abs(a - r)) / np.max(np.abs(r)))
+    return out
+
+
 def run_e2e(args, src, tgt, N, tol, prec):
     import torch
     import paper_2603_00538_gb300 as sft
@@ -1052,6 +1149,9 @@ def main():
                     help="sample scheme of the mesh-source workloads (tri4m, tet5m and their online forms)")
     ap.add_argument("--cold-start", action="store_true",
                     help="roundtrip: start every solve from 0 instead of the leg's previous result")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
+                    help="tri4m / tet5m: arithmetic of sampling, location and evaluation (fp32: compensated "
+                         "FP32 partials, FP64 load vector / CG / reductions; fp64: all FP64)")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="element-count scale of the workload (1 = the named workload)")
     args = ap.parse_args()

@@ -164,6 +164,29 @@ void sft_target_destroy(sft_target tgt);
 sft_status sft_transfer(sft_source src, sft_target tgt, const sft_options* opt,
                         double* u_out, double* b_out, double* g_out, sft_stats* stats);
 
+/* ---- mesh intersection (2D): the exact judge ----
+ * Sec. 3, Intersection-Based Galerkin Projection: every target triangle is
+ * partitioned by the source triangles it overlaps (Eq. partition_ts); each
+ * piece is clipped (Sutherland-Hodgman), split into a fan from its first
+ * vertex and integrated with the edge-midpoint rule, exact for the products
+ * of two functions linear on the piece; all arithmetic FP64. A target
+ * triangle's pieces are found by a walk over source face neighbours from
+ * the source triangle holding its centroid (at most 256 source triangles
+ * visited per target triangle, else SFT_ERR_UNSUPPORTED).
+ * sft_mi_load_vector: the exact P1 load vector b_i = int psi_i f^s of source
+ * field `field` (Eq. galerkin_system's right-hand side), b_out [nnodes_target]
+ * FP64, a device pointer if out_device. sft_mi_l2_error: the supermesh L2
+ * error of a target field u [nnodes_target] (FP64, device pointer if
+ * u_on_device) against source field `field` (Eq. relative_L2_error):
+ * out2[0] = ||f^s - f^t||_L2, out2[1] = ||f^s||_L2 (host array of 2).
+ * Both need 2D meshes (SFT_ERR_UNSUPPORTED otherwise), return
+ * SFT_ERR_OUTSIDE if a target centroid lies in no source triangle, and
+ * synchronise `cuda_stream`. */
+sft_status sft_mi_load_vector(sft_source src, sft_target tgt, int32_t field, double* b_out,
+                              int32_t out_device, void* cuda_stream);
+sft_status sft_mi_l2_error(sft_source src, sft_target tgt, int32_t field, const double* u,
+                           int32_t u_on_device, void* cuda_stream, double* out2);
+
 /* Relative conservation error (Eq. relative_conservation_error) of a target
  * field u [nnodes_target] (FP64; device pointer if u_on_device):
  *   out3[0] = |int f^s - int f^t| / |int f^s|, out3[1] = int f^s (field `field`
@@ -243,6 +266,13 @@ sft_status sft_batch_run(sft_batch b, void* cuda_stream, sft_batch_stats* stats)
  * of the last run to u_out / b_out (device pointers if out_device). */
 sft_status sft_batch_result(sft_batch b, int32_t req, double* u_out, double* b_out, int32_t out_device,
                             void* cuda_stream);
+/* The plan's request groups and their tuned launch shape: out [6][5] host
+ * int32, per group (dimension 2 then 3; field-count classes <= 2, <= 4,
+ * <= 8): request count, dimension, largest field count of the class, tile
+ * (tasks a warp takes per atomic work claim) and lanes per element (a
+ * warp holds 32 / lanes elements; each element's lanes share its samples),
+ * as chosen by the autotuner (or the defaults without autotuning). */
+sft_status sft_batch_groups(sft_batch plan, int32_t* out);
 void sft_batch_destroy(sft_batch b);
 
 /* ---- learned surrogate source (spec item 4; no counterpart in the
@@ -315,7 +345,13 @@ typedef struct {
                               queried exactly; 0 disables the fallback */
     float tau;             /* >= 0: an element whose subsample has max |f_net - f_exact| > tau
                               (or a non-finite difference) uses exact queries for all N samples */
-    int32_t reserved;
+    int32_t exact_cost;    /* >= 0: stand-in cost of a costly black-box source: every exact
+                              query (subsample, fallback and, without a network, control and
+                              samples) runs this many dependent FP32 fused multiply-adds after
+                              its mesh location, which leave its value unchanged; 0 = the mesh
+                              query alone. It measures the query cost above which the surrogate
+                              pays off (the paper's motivating case); the paper has no such
+                              parameter. */
     int32_t* fallback_out; /* optional [nelems]: 1 where the element used exact queries */
     float* sample_f_out;   /* optional [nelems][N]: the source value used at every sample */
 } sft_surrogate_opts;
@@ -324,7 +360,8 @@ typedef struct {
     int32_t cg_iters;
     int32_t reserved;
     double cg_rel_resid;
-    int64_t net_queries;     /* network evaluations: target nodes + nelems * N */
+    int64_t net_queries;     /* network evaluations: target nodes + nelems * s (the subsample)
+                                + N for every element that keeps the network */
     int64_t exact_queries;   /* exact mesh queries (subsample + fallback elements) */
     int64_t fallback_elems;  /* elements that used exact queries */
     int64_t empty_queries;   /* exact queries that landed in an empty grid cell (value 0) */
@@ -402,6 +439,14 @@ sft_status sft_source_adjacency(sft_source src, int32_t precision, int32_t* adj_
  * lumped masses [nnodes]. */
 sft_status sft_target_mass(sft_target tgt, int64_t* nnz_out, int64_t* row_ptr_out,
                            int32_t* col_out, double* val_out, double* lumped_out);
+
+/* Device memory: every buffer of this library comes from its own
+ * stream-ordered memory pool on each device, which keeps blocks freed by
+ * *_destroy and by finished calls for later calls instead of returning them
+ * to the driver at each synchronisation (creating and destroying meshes in a
+ * loop then maps no new memory). This returns the pools' unused blocks to
+ * the driver; memory in use is untouched. The paper has no counterpart. */
+sft_status sft_trim_memory(void);
 
 const char* sft_status_str(sft_status s);
 /* Message of the last error on the calling thread (empty if none). */

@@ -79,7 +79,7 @@ class sft_batch_stats(ctypes.Structure):
 
 class sft_surrogate_opts(ctypes.Structure):
     _fields_ = [("exact_field", ctypes.c_int32), ("subsample", ctypes.c_int32), ("tau", ctypes.c_float),
-                ("reserved", ctypes.c_int32), ("fallback_out", ctypes.c_void_p), ("sample_f_out", ctypes.c_void_p)]
+                ("exact_cost", ctypes.c_int32), ("fallback_out", ctypes.c_void_p), ("sample_f_out", ctypes.c_void_p)]
 
 
 class sft_surrogate_stats(ctypes.Structure):
@@ -107,6 +107,10 @@ _SIGS = {
     "sft_source_grid": ([_vp, _i32, _vp, _vp, _vp, _vp, _vp], _i32),
     "sft_source_adjacency": ([_vp, _i32, _vp], _i32),
     "sft_target_set_wait_limit": ([_vp, ctypes.c_double], _i32),
+    "sft_trim_memory": ([], _i32),
+    "sft_batch_groups": ([_vp, _vp], _i32),
+    "sft_mi_load_vector": ([_vp, _vp, _i32, _vp, _i32, _vp], _i32),
+    "sft_mi_l2_error": ([_vp, _vp, _i32, _vp, _i32, _vp, _vp], _i32),
     "sft_target_mass": ([_vp, _vp, _vp, _vp, _vp, _vp], _i32),
     "sft_status_str": ([_i32], ctypes.c_char_p),
     "sft_last_error": ([], ctypes.c_char_p),
@@ -368,6 +372,25 @@ def sft_conservation_error(src: Source, tgt: Target, u, field: int = 0, stream=N
                                         stream if stream is not None else _current_stream(), out),
            "sft_conservation_error")
     return out[0], out[1], out[2]
+
+
+def sft_mi_load_vector(src: Source, tgt: Target, field: int = 0, b_out=None, stream=None):
+    """Exact load vector int psi_i f^s by 2D mesh intersection (FP64 [nnodes])."""
+    if b_out is None:
+        b_out = np.zeros(_nv(tgt), np.float64)
+    p, dev, _ = _ptr(b_out)
+    _check(lib().sft_mi_load_vector(src.h, tgt.h, int(field), p, int(dev),
+                                    stream if stream is not None else _current_stream()), "sft_mi_load_vector")
+    return b_out
+
+
+def sft_mi_l2_error(src: Source, tgt: Target, u, field: int = 0, stream=None):
+    """(||f^s - f^t||_L2, ||f^s||_L2) on the supermesh (2D) for a target field u [nnodes]."""
+    p, dev, _ = _ptr(u)
+    out = (ctypes.c_double * 2)()
+    _check(lib().sft_mi_l2_error(src.h, tgt.h, int(field), p, int(dev),
+                                 stream if stream is not None else _current_stream(), out), "sft_mi_l2_error")
+    return out[0], out[1]
 
 
 def sft_locate(src: Source, pts, precision: int = SFT_PREC_FP32, elem_out=None, val_out=None, stream=None):
@@ -638,10 +661,13 @@ def sft_transfer_surrogate(net, exact, tgt: Target, samples_per_elem: int, seed:
                            tau: float = 0.0, exact_field: int = 0, u_out=None, b_out=None, g_out=None,
                            fallback_out=None, sample_f_out=None, strict_inside: bool = False, stream=None,
                            allow_not_converged: bool = False, cg_mode: int = SFT_CG_MIXED,
-                           sampling: int = SFT_SAMPLING_UNIFORM, cg_warm_start: bool = False):
+                           sampling: int = SFT_SAMPLING_UNIFORM, cg_warm_start: bool = False,
+                           exact_cost: int = 0):
     """Transfer with the surrogate network `net` (Mlp or None) backed by the
     exact source `exact` (Source or None). Outputs as sft_transfer (numpy for
-    host, CUDA tensors for device). Returns (status, stats dict, u_out)."""
+    host, CUDA tensors for device). exact_cost: dependent FMAs added to every
+    exact query (a stand-in for a costly black-box source). Returns (status,
+    stats dict, u_out)."""
     if u_out is None:
         u_out = np.zeros(_nv(tgt), np.float64)
     up, udev, _ = _ptr(u_out)
@@ -658,6 +684,7 @@ def sft_transfer_surrogate(net, exact, tgt: Target, samples_per_elem: int, seed:
     so.exact_field = int(exact_field)
     so.subsample = int(subsample)
     so.tau = float(tau)
+    so.exact_cost = int(exact_cost)
     so.fallback_out = ptrs[2][0]
     so.sample_f_out = ptrs[3][0]
     st = sft_surrogate_stats()
@@ -680,6 +707,19 @@ def sft_source_grid(src: Source, precision: int):
     _check(lib().sft_source_grid(src.h, int(precision), None, None, None, start.ctypes.data, items.ctypes.data),
            "sft_source_grid")
     return np.array(list(n)), start, items[:ni.value]
+
+
+def sft_batch_groups(plan) -> list:
+    """Per non-empty request group: dict(requests, dim, max_fields, tile, lanes_per_element)."""
+    out = np.zeros((6, 5), np.int32)
+    _check(lib().sft_batch_groups(plan.h, out.ctypes.data), "sft_batch_groups")
+    keys = ("requests", "dim", "max_fields", "tile", "lanes_per_element")
+    return [dict(zip(keys, (int(v) for v in row))) for row in out if row[0] > 0]
+
+
+def sft_trim_memory() -> None:
+    """Return the unused blocks of the library's device memory pools to the driver."""
+    _check(lib().sft_trim_memory(), "sft_trim_memory")
 
 
 def sft_target_set_wait_limit(tgt: Target, seconds: float) -> None:

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsft.so")
-SOURCES = ["api.cu", "locate.cu", "target.cu", "assemble.cu", "solve.cu", "util.cu", "batch.cu", "mlp.cu", "surrogate.cu", "plan.cu"]
+SOURCES = ["api.cu", "locate.cu", "target.cu", "assemble.cu", "solve.cu", "util.cu", "batch.cu", "mlp.cu", "surrogate.cu", "plan.cu", "intersect.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xcompiler", "-Wall", f"-I{os.path.join(ROOT, 'include')}"]

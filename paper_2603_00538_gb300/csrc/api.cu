@@ -77,7 +77,7 @@ static sft_status check_desc(const sft_mesh_desc* d, bool source) {
 }
 
 static sft_status copy_in(void** dst, const void* src, size_t bytes, cudaStream_t st) {
-  SFT_CUDA(cudaMallocAsync(dst, bytes ? bytes : 1, st));
+  SFT_CUDA(pool_alloc(dst, bytes ? bytes : 1, st));
   if (bytes) SFT_CUDA(cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyDefault, st));
   return SFT_OK;
 }
@@ -116,6 +116,11 @@ const char* sft_status_str(sft_status s) {
 const char* sft_last_error(void) { return g_last_error.c_str(); }
 
 int64_t sft_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+sft_status sft_trim_memory(void) {
+  trim_pools();
+  return SFT_OK;
+}
 
 void sft_source_destroy(sft_source s) {
   if (!s) return;

@@ -120,9 +120,10 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_control(const BReq* __r
 
 // ---------------------------------------------------------------------------
 // steps 2-6: persistent fused assembly over the tasks of a request group.
-// A task is one warp's share of one request: floor(32/LPE) elements, LPE =
-// min(U, 4) lanes per element striding over its Philox units. Per-lane partials are
-// plain FP32 sums of a lane's few samples; the warp combine is compensated.
+// A task is one warp's share of one request: 32/LPE elements, LPE lanes per
+// element (1, 2, 4 or 8, chosen per group by the autotuner; default min(U, 4))
+// striding over its Philox units. Per-lane partials are plain FP32 sums of a
+// lane's few samples; the warp combine is compensated.
 // ---------------------------------------------------------------------------
 template <int D, int NF>
 __global__ void __launch_bounds__(kBatchThreads, NF <= 2 ? 4 : (NF <= 4 ? 3 : 2)) k_batch_assemble(const BReq* __restrict__ reqs,
@@ -212,8 +213,7 @@ __global__ void __launch_bounds__(kBatchThreads, NF <= 2 ? 4 : (NF <= 4 ? 3 : 2)
 #pragma unroll
         for (int i = 0; i < K; ++i) {
           float s = acc[f][i], e = 0.f;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
+          for (int o = 1; o < LPE; o <<= 1) {  // log2 LPE rounds: a segment spans LPE lanes
             const float s2 = __shfl_down_sync(0xffffffffu, s, o);
             const float e2 = __shfl_down_sync(0xffffffffu, e, o);
             if (lane + o < seg_hi) {
@@ -809,8 +809,9 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_mixed(const BSys* __res
 // autotune cache: (dim, field class, log2 mean N, log2 tasks) -> tile
 // ---------------------------------------------------------------------------
 using TuneKey = std::tuple<int, int, int, int>;
+using TuneVal = std::pair<int, int>;  // (tile, lanes per element; 0 = the default min(U, 4))
 static std::mutex g_tune_mu;
-static std::map<TuneKey, int> g_tune;
+static std::map<TuneKey, TuneVal> g_tune;
 static bool g_tune_loaded = false;
 
 static const char* tune_file() { return std::getenv("SFT_AUTOTUNE_CACHE"); }
@@ -822,18 +823,20 @@ static void tune_load_locked() {
   if (!path) return;
   FILE* fh = std::fopen(path, "r");
   if (!fh) return;
-  int d, c, n, t, tile;
-  while (std::fscanf(fh, "%d %d %d %d %d", &d, &c, &n, &t, &tile) == 5) g_tune[TuneKey(d, c, n, t)] = tile;
+  int d, c, n, t, tile, lpe;
+  while (std::fscanf(fh, "%d %d %d %d %d %d", &d, &c, &n, &t, &tile, &lpe) == 6)
+    g_tune[TuneKey(d, c, n, t)] = TuneVal(tile, lpe);
   std::fclose(fh);
 }
 
-static void tune_store_locked(const TuneKey& k, int tile) {
-  g_tune[k] = tile;
+static void tune_store_locked(const TuneKey& k, TuneVal v) {
+  g_tune[k] = v;
   const char* path = tune_file();
   if (!path) return;
   FILE* fh = std::fopen(path, "a");
   if (!fh) return;
-  std::fprintf(fh, "%d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k), tile);
+  std::fprintf(fh, "%d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k), v.first,
+               v.second);
   std::fclose(fh);
 }
 
@@ -859,6 +862,7 @@ struct sft_batch_s {
     int64_t* doff = nullptr;
     int64_t total = 0;
     int tile = 4;
+    int lpe = 0;  // lanes per element of every request in the group (0: min(U, 4) per request)
     unsigned long long* work = nullptr;
   } grp[6];
   struct CtlGroup {
@@ -975,6 +979,32 @@ static sft_status enqueue_batch(sft_batch_s* B, cudaStream_t st) {
   return SFT_OK;
 }
 
+// lanes per element of a request: the group's choice, or min(U, 4)
+static int request_lpe(const BReq& R, int lpe) { return lpe > 0 ? lpe : (R.U >= 4 ? 4 : R.U); }
+
+// apply lanes per element `lpe` to every request of group gi: elements per
+// task, task counts, the group's task offsets (host and device copies)
+static sft_status set_group_lpe(sft_batch_s* B, int gi, int lpe, cudaStream_t st) {
+  auto& G = B->grp[gi];
+  G.lpe = lpe;
+  G.off.assign(1, 0);
+  for (int32_t r : G.req) {
+    BReq& R = B->hreq[r];
+    R.LPE = request_lpe(R, lpe);
+    R.G = 32 / R.LPE;
+    R.ntasks = (R.ne + R.G - 1) / R.G;
+    G.off.push_back(G.off.back() + R.ntasks);
+  }
+  G.total = G.off.back();
+  if (G.doff) SFT_CUDA(cudaMemcpyAsync(G.doff, G.off.data(), sizeof(int64_t) * G.off.size(), cudaMemcpyHostToDevice, st));
+  if (B->dreq)
+    SFT_CUDA(cudaMemcpyAsync(B->dreq, B->hreq.data(), sizeof(BReq) * B->hreq.size(), cudaMemcpyHostToDevice, st));
+  return SFT_OK;
+}
+
+// Timed trials of the group's assembly over lanes per element {1, 2, 4, 8}
+// x tiles {1, 2, 4, 8, 16} (tasks a warp takes per atomic); the fastest pair
+// is kept and cached per (dimension, field class, log2 mean N, log2 tasks).
 static sft_status autotune_group(sft_batch_s* B, int gi, cudaStream_t st) {
   auto& G = B->grp[gi];
   const int dim = gi < 3 ? 2 : 3;
@@ -987,8 +1017,8 @@ static sft_status autotune_group(sft_batch_s* B, int gi, cudaStream_t st) {
     tune_load_locked();
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      G.tile = it->second;
-      return SFT_OK;
+      G.tile = it->second.first;
+      return set_group_lpe(B, gi, it->second.second, st);
     }
   }
   // control values must exist before trial assemblies
@@ -999,46 +1029,51 @@ static sft_status autotune_group(sft_batch_s* B, int gi, cudaStream_t st) {
   SFT_CUDA(cudaEventCreate(&e0));
   SFT_CUDA(cudaEventCreate(&e1));
   const int tiles[] = {1, 2, 4, 8, 16};
+  const int lpes[] = {1, 2, 4, 8};
   float best = 1e30f;
-  int best_tile = 4;
-  const unsigned blocks = (unsigned)std::max<int64_t>(
-      1, std::min<int64_t>((int64_t)sms * 4, (G.total + (kBatchThreads / 32) - 1) / (kBatchThreads / 32)));
+  TuneVal best_v(4, 0);
   const int ng = (int)G.req.size();
-  for (int tile : tiles) {
-    float tsum = 0.f;
-    for (int rep = 0; rep < 2; ++rep) {
-      SFT_CUDA(cudaMemsetAsync(G.work, 0, sizeof(unsigned long long), st));
-      SFT_CUDA(cudaEventRecord(e0, st));
+  for (int lpe : lpes) {
+    if (sft_status e = set_group_lpe(B, gi, lpe, st)) return e;
+    const unsigned blocks = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)sms * 4, (G.total + (kBatchThreads / 32) - 1) / (kBatchThreads / 32)));
+    for (int tile : tiles) {
+      float tsum = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {
+        SFT_CUDA(cudaMemsetAsync(G.work, 0, sizeof(unsigned long long), st));
+        SFT_CUDA(cudaEventRecord(e0, st));
 #define SFT_BA(DD, NN)                                                                                          \
   ::sft::note_launch(), k_batch_assemble<DD, NN><<<blocks, kBatchThreads, sizeof(int64_t) * (ng + 1), st>>>(B->dreq, G.dreq, G.doff, ng, \
                                                                                    G.total, tile, G.work,     \
                                                                                    B->counters)
-      switch (gi) {
-        case 0: SFT_BA(2, 2); break;
-        case 1: SFT_BA(2, 4); break;
-        case 2: SFT_BA(2, 8); break;
-        case 3: SFT_BA(3, 2); break;
-        case 4: SFT_BA(3, 4); break;
-        default: SFT_BA(3, 8); break;
-      }
+        switch (gi) {
+          case 0: SFT_BA(2, 2); break;
+          case 1: SFT_BA(2, 4); break;
+          case 2: SFT_BA(2, 8); break;
+          case 3: SFT_BA(3, 2); break;
+          case 4: SFT_BA(3, 4); break;
+          default: SFT_BA(3, 8); break;
+        }
 #undef SFT_BA
-      SFT_CUDA(cudaGetLastError());
-      SFT_CUDA(cudaEventRecord(e1, st));
-      SFT_CUDA(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      SFT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      if (rep > 0) tsum += ms;
-    }
-    if (tsum < best) {
-      best = tsum;
-      best_tile = tile;
+        SFT_CUDA(cudaGetLastError());
+        SFT_CUDA(cudaEventRecord(e1, st));
+        SFT_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        SFT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) tsum += ms;
+      }
+      if (tsum < best) {
+        best = tsum;
+        best_v = TuneVal(tile, lpe);
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  G.tile = best_tile;
+  G.tile = best_v.first;
+  if (sft_status e = set_group_lpe(B, gi, best_v.second, st)) return e;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  tune_store_locked(key, best_tile);
+  tune_store_locked(key, best_v);
   return SFT_OK;
 }
 
@@ -1126,7 +1161,7 @@ static sft_status build_batch(sft_batch_s* B, const sft_options* opts, int autot
     R.N = o.samples_per_elem;
     const int spu = t->dim == 2 ? 2 : 1;
     R.U = (R.N + spu - 1) / spu;
-    R.LPE = R.U >= 4 ? 4 : R.U;  // lanes per element, as in the single-transfer kernel
+    R.LPE = request_lpe(R, 0);  // lanes per element, as in the single-transfer kernel (until tuned)
     R.G = 32 / R.LPE;
     R.ntasks = (t->ne + R.G - 1) / R.G;
     R.key.k0 = (uint32_t)o.seed;
@@ -1392,6 +1427,22 @@ sft_status sft_batch_result(sft_batch B, int32_t req, double* u_out, double* b_o
   SFT_CUDA(cudaMemcpyAsync(u_out, B->u + B->vec_off[req], bytes, k, st));
   if (b_out) SFT_CUDA(cudaMemcpyAsync(b_out, B->b + B->vec_off[req], bytes, k, st));
   SFT_CUDA(cudaStreamSynchronize(st));
+  return SFT_OK;
+}
+
+sft_status sft_batch_groups(sft_batch B, int32_t* out) {
+  if (!B || !out) return fail(SFT_ERR_ARG, "null argument");
+  for (int gi = 0; gi < 6; ++gi) {
+    const auto& G = B->grp[gi];
+    int32_t* o = out + gi * 5;
+    o[0] = (int32_t)G.req.size();
+    o[1] = gi < 3 ? 2 : 3;
+    o[2] = gi % 3 == 0 ? 2 : (gi % 3 == 1 ? 4 : 8);
+    o[3] = G.tile;
+    int lpe = 0;
+    for (int32_t r : G.req) lpe = std::max(lpe, B->hreq[r].LPE);
+    o[4] = G.req.empty() ? 0 : (G.lpe > 0 ? G.lpe : lpe);
+  }
   return SFT_OK;
 }
 

@@ -21,12 +21,18 @@ sft_status cuda_fail(cudaError_t e, const char* what);
     if (_e != cudaSuccess) return ::sft::cuda_fail(_e, #call);           \
   } while (0)
 
-// stream-ordered device allocation
+// Stream-ordered device allocation from the library's memory pool of the
+// current device (util.cu). The pool keeps freed blocks for reuse instead of
+// returning them to the driver at each synchronisation, so repeated creates,
+// transfers and destroys do not map fresh memory every time;
+// sft_trim_memory hands the unused part back.
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s);
+void trim_pools();
 template <typename T>
 cudaError_t dalloc(T** p, size_t count, cudaStream_t s) {
   *p = nullptr;
   if (count == 0) count = 1;
-  return cudaMallocAsync(reinterpret_cast<void**>(p), sizeof(T) * count, s);
+  return pool_alloc(reinterpret_cast<void**>(p), sizeof(T) * count, s);
 }
 template <typename T>
 void dfree(T*& p, cudaStream_t s) {
@@ -139,6 +145,9 @@ sft_status refresh_value_copies(sft_source_s* s, cudaStream_t st);
 // target.cu
 sft_status build_target(sft_target_s* t, cudaStream_t st, int32_t* d_err);
 sft_status target_coordsP(sft_target_s* t, int prec, cudaStream_t st);
+// intersect.cu: exact load vector (u == nullptr) or L2 error of u (2D)
+sft_status mesh_intersection_2d(sft_source_s* s, sft_target_s* t, int field, const double* u, double* b,
+                                double* err_out, double* norm_out, cudaStream_t st);
 // assemble.cu
 enum AsmMode : int { kAsmPlain = 0, kAsmDebug = 1, kAsmRecord = 2, kAsmCached = 3 };
 struct AssembleArgs {

@@ -97,9 +97,9 @@ sft_status sft_plan_create(sft_source s, sft_target t, const sft_options* o, sft
   sft_status r = SFT_OK;
   do {
     cudaError_t e = dalloc(&pl->node_elem, (size_t)nv, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&pl->node_mu, psz * d * (size_t)nv, st);
+    if (e == cudaSuccess) e = pool_alloc(&pl->node_mu, psz * d * (size_t)nv, st);
     if (e == cudaSuccess) e = dalloc(&pl->samp_elem, (size_t)ns, st);
-    if (e == cudaSuccess) e = cudaMallocAsync(&pl->samp_mu, psz * d * (size_t)ns, st);
+    if (e == cudaSuccess) e = pool_alloc(&pl->samp_mu, psz * d * (size_t)ns, st);
     if (e != cudaSuccess) { r = cuda_fail(e, "plan arrays"); break; }
     pl->bytes = sizeof(int32_t) * (size_t)(nv + ns) + psz * d * (size_t)(nv + ns);
     DevBuf<char> g(st);

@@ -335,7 +335,7 @@ sft_status target_coordsP(sft_target_s* t, int prec, cudaStream_t st) {
   if (t->coordsP[prec]) return SFT_OK;
   const size_t esz = prec == SFT_PREC_FP32 ? 4 : 8;
   void* p = nullptr;
-  SFT_CUDA(cudaMallocAsync(&p, esz * (size_t)(t->nv * t->dim > 0 ? t->nv * t->dim : 1), st));
+  SFT_CUDA(pool_alloc(&p, esz * (size_t)(t->nv * t->dim > 0 ? t->nv * t->dim : 1), st));
   t->coordsP[prec] = p;
   return convert_coords(t->coords, t->dtype, p, prec, t->nv * t->dim, st);
 }

@@ -2,7 +2,52 @@
 // the block totals, add-back) and small conversion kernels.
 #include "util.cuh"
 
+#include <cstdint>
+#include <mutex>
+#include "internal.hpp"
+
 namespace sft {
+
+// one memory pool per device, made on first use with a release threshold of
+// "never": blocks freed in stream order stay with the pool for the next
+// allocation (the default pool returns them to the driver at every
+// synchronisation, and remapping them costs tenths of a millisecond per call)
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64] = {};
+
+static cudaMemPool_t library_pool(int dev) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;  // the device's default pool then
+    }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pool[dev] = pool;
+  }
+  return g_pool[dev];
+}
+
+cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  cudaMemPool_t pool = dev >= 0 && dev < 64 ? library_pool(dev) : nullptr;
+  if (!pool) return cudaMallocAsync(p, bytes, s);
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+void trim_pools() {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  for (auto& pool : g_pool)
+    if (pool) cudaMemPoolTrimTo(pool, 0);
+}
 
 namespace {
 constexpr int kScanThreads = 512;
@@ -58,7 +103,7 @@ cudaError_t scan_rec(const TIn* in, int64_t* out, int64_t n, cudaStream_t s) {
   const int64_t tiles = (n + kScanTile - 1) / kScanTile;
   if (tiles == 0) return cudaMemsetAsync(out, 0, sizeof(int64_t), s);
   int64_t* sums = nullptr;
-  cudaError_t e = cudaMallocAsync(&sums, sizeof(int64_t) * (tiles + 1), s);
+  cudaError_t e = pool_alloc(reinterpret_cast<void**>(&sums), sizeof(int64_t) * (tiles + 1), s);
   if (e != cudaSuccess) return e;
   ::sft::note_launch(), k_scan_tiles<TIn><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, sums);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -67,7 +112,7 @@ cudaError_t scan_rec(const TIn* in, int64_t* out, int64_t n, cudaStream_t s) {
     e = cudaMemcpyAsync(out + n, sums, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
   } else {
     int64_t* sums_scan = nullptr;
-    e = cudaMallocAsync(&sums_scan, sizeof(int64_t) * (tiles + 1), s);
+    e = pool_alloc(reinterpret_cast<void**>(&sums_scan), sizeof(int64_t) * (tiles + 1), s);
     if (e != cudaSuccess) return e;
     e = scan_rec<int64_t>(sums, sums_scan, tiles, s);
     if (e == cudaSuccess) {

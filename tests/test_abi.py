@@ -60,15 +60,19 @@ def test_ctypes_layout_matches_header(tmp_path):
     import paper_2603_00538_gb300 as sft
     src = tmp_path / "lay.c"
     src.write_text(f'#include <stdio.h>\n#include <stddef.h>\n#include "{HEADER}"\n'
-                   "int main(){printf(\"%zu %zu %zu %zu %zu %zu\\n\", sizeof(sft_mesh_desc), sizeof(sft_options),"
-                   " sizeof(sft_stats), offsetof(sft_options, cuda_stream), offsetof(sft_stats, ms_setup),"
-                   " offsetof(sft_mesh_desc, grid_scale_L));}\n")
+                   "int main(){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(sft_mesh_desc),"
+                   " sizeof(sft_options), sizeof(sft_stats), offsetof(sft_options, cuda_stream),"
+                   " offsetof(sft_stats, ms_setup), offsetof(sft_mesh_desc, grid_scale_L),"
+                   " sizeof(sft_surrogate_opts), offsetof(sft_surrogate_opts, exact_cost),"
+                   " offsetof(sft_surrogate_opts, sample_f_out), sizeof(sft_surrogate_stats));}\n")
     exe = tmp_path / "lay"
     subprocess.run(["gcc", str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     want = [ctypes.sizeof(sft.sft_mesh_desc), ctypes.sizeof(sft.sft_options), ctypes.sizeof(sft.sft_stats),
             sft.sft_options.cuda_stream.offset, sft.sft_stats.ms_setup.offset,
-            sft.sft_mesh_desc.grid_scale_L.offset]
+            sft.sft_mesh_desc.grid_scale_L.offset, ctypes.sizeof(sft.sft_surrogate_opts),
+            sft.sft_surrogate_opts.exact_cost.offset, sft.sft_surrogate_opts.sample_f_out.offset,
+            ctypes.sizeof(sft.sft_surrogate_stats)]
     assert got == want
 
 

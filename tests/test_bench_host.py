@@ -12,9 +12,11 @@ if ROOT not in sys.path:
 import bench  # noqa: E402
 
 
-def _sampler(rows):
+def _sampler(rows, t0=0.0, times=None):
     c = bench.ClockSampler(0)
-    c.rows = [[p.strip() for p in r.split(",")] for r in rows]
+    c.t0 = t0
+    times = times or [1.0] * len(rows)
+    c.rows = [[t] + [p.strip() for p in r.split(",")] for t, r in zip(times, rows)]
     return c.summary()
 
 
@@ -28,6 +30,18 @@ def test_clock_summary_reasons_and_median():
     assert s["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
     s = _sampler(["[N/A], [N/A], [N/A], Not Active, Not Active, Not Active, Not Active"])
     assert s["sm_mhz"] is None and s["reasons"] == []
+
+
+def test_clock_summary_uses_the_timed_region():
+    """Samples taken before the timed region began (sampler start-up, idle
+    clocks) are left out when the region has samples of its own."""
+    rows = ["1200, 2070, 200, Not Active, Not Active, Not Active, Not Active",
+            "2070, 2070, 900, Not Active, Not Active, Not Active, Not Active",
+            "2070, 2070, 950, Not Active, Not Active, Not Active, Active"]
+    s = _sampler(rows, t0=10.0, times=[9.0, 10.5, 10.6])
+    assert s["samples"] == 2 and s["sm_mhz"] == 2070.0 and s["reasons"] == ["sw_power_cap"]
+    s = _sampler(rows[:1], t0=10.0, times=[9.0])        # region shorter than one period
+    assert s["samples"] == 1 and s["sm_mhz"] == 1200.0
 
 
 def test_clock_summary_unsampled():

@@ -95,8 +95,8 @@ def test_sur3d_full_size_samples(orc):
                                              fallback_out=fb, sample_f_out=sf)
     torch.cuda.synchronize()
     assert stats["cg_rel_resid"] <= 1e-10
-    assert stats["net_queries"] == tgt.nnodes + E * N
     fbh = fb.cpu().numpy().astype(bool)
+    assert stats["net_queries"] == tgt.nnodes + E * s + (E - int(fbh.sum())) * N
     assert stats["fallback_elems"] == int(fbh.sum())
     rng = np.random.default_rng(2)
     sel = np.sort(rng.choice(E, 96, replace=False))

@@ -315,6 +315,28 @@ def test_empty_cells_and_strict_mode():
     assert ei.value.status == 6
 
 
+def test_memory_pool_reuse_and_trim():
+    """Meshes created and destroyed in a loop reuse the library pool's blocks
+    (the device's free memory does not move on the second round), and
+    sft_trim_memory returns them to the driver."""
+    src, tgt, _ = W.config_meshes("tri4m", 0.05)
+    free = lambda: (torch.cuda.synchronize(), torch.cuda.mem_get_info(DEV)[0])[1]  # noqa: E731
+    sft.sft_trim_memory()
+    f0 = free()
+    after = []
+    for _ in range(2):
+        s = sft.mesh_source(src)           # host inputs: only the library allocates
+        t = sft.mesh_target(tgt)
+        sft.sft_transfer(s, t, 8, FP32, cg_tol=1e-10)
+        s.close()
+        t.close()
+        after.append(free())
+    assert after[0] < f0                   # the pool kept the freed blocks
+    assert after[1] == after[0]            # and the second round reused them
+    sft.sft_trim_memory()
+    assert free() > after[1]
+
+
 def test_invalid_meshes_rejected():
     m = W.with_values(W.jittered_tri_mesh(4, 0), [W.paper_f1])
     bad = m.conn.copy()

@@ -107,7 +107,9 @@ def test_surrogate_transfer_matches_oracle(orc, dt, n_tgt, N):
     bound = 1.5 * (1 + 2 * alpha) * EPS * Snet * m + 1e-5 * np.abs(ref["b"]).max()
     assert np.all(np.abs(b - ref["b"])[~touched] <= bound[~touched])
     # statistics
-    assert stats["net_queries"] == nv + E * N
+    # the network runs on the target nodes, the subsample of every element,
+    # and all N samples of the elements that keep it
+    assert stats["net_queries"] == nv + E * s + (E - fb.sum()) * N
     assert stats["fallback_elems"] == fb.sum()
     assert stats["exact_queries"] == E * s + fb.sum() * (N - s)
     assert stats["cg_rel_resid"] <= 1e-10

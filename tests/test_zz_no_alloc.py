@@ -143,7 +143,7 @@ def test_static_solve_wrapper_checks_arguments():
     with pytest.raises(ValueError):
         sft.sft_mass_solve_static(rp_d, col_d, val_d, b, torch.zeros((1, 99), dtype=torch.float64, device=DEV))
     with pytest.raises(ValueError):
-        sft.sft_mass_solve_static(rp_d, col_d, val_d, b, torch.zeros((100, 1), dtype=torch.float64, device=DEV).t())
+        sft.sft_mass_solve_static(rp_d, col_d, val_d, b, torch.zeros((1, 200), dtype=torch.float64, device=DEV)[:, ::2])
     with pytest.raises(ValueError):
         sft.sft_mass_solve_static(rp_d, col_d[:10], val_d, b, u)
     with pytest.raises(ValueError):
