@@ -65,8 +65,19 @@ typedef enum { SFT_CG_MIXED = 0, SFT_CG_FP64 = 1 } sft_cg_mode;
  * under the uniform-to-simplex map), one uniform point in each, plus N - m^d
  * uniform points; every sample keeps the weight |T| / N, so the estimator
  * stays unbiased (Eq. mc_element_integral_operator_general) and its error
- * falls like N^-1 instead of N^-1/2 for a Lipschitz residual in 2D. */
-typedef enum { SFT_SAMPLING_UNIFORM = 0, SFT_SAMPLING_STRATIFIED = 1 } sft_sampling;
+ * falls like N^-1 instead of N^-1/2 for a Lipschitz residual in 2D.
+ * IMPORTANCE: the samples follow the non-uniform density p_t = (1/4 +
+ * sum_{a<b} pi_e (d+1)(d+2) lambda_a lambda_b) / |T| (pi_e = 1/4 in 2D, 1/8
+ * in 3D), a mixture of the uniform density and the edge-bubble densities
+ * that the control-variate residual of a smooth field follows, and every
+ * sample is weighted by 1 / (|T| p_t) <= 4 (Eq.
+ * mc_element_integral_operator_general). Philox counters (j, t, stream, 6)
+ * and (j, t, stream, 7) per sample. sft_transfer only (plain mode). */
+typedef enum {
+    SFT_SAMPLING_UNIFORM = 0,
+    SFT_SAMPLING_STRATIFIED = 1,
+    SFT_SAMPLING_IMPORTANCE = 2
+} sft_sampling;
 
 /* element type of coordinate / value arrays */
 typedef enum { SFT_F32 = 0, SFT_F64 = 1 } sft_dtype;
@@ -107,13 +118,23 @@ typedef struct {
                                    transfer's result, say) instead of 0; needs cg_mode MIXED.
                                    The stopping test is unchanged (true FP64 residual relative
                                    to ||b||), so the result meets the same tolerance. */
+    double adapt_ref_measure;   /* > 0: per-element sample counts N_t = min(8 N, max(1,
+                                   ceil(N D_t / D_ref))), D_t = d! |T| (the edge determinant of
+                                   the element's vertices in the path precision, in FP64) and
+                                   D_ref = d! adapt_ref_measure: samples in proportion to the
+                                   element's measure, N per reference measure (for a residual of
+                                   uniform variance per unit measure the global sum's variance
+                                   is lowest so); weights |T| / N_t. 0: N for every element.
+                                   sft_transfer only (uniform or importance sampling);
+                                   sample_elem_out is then [nelems][8 N], -1 past N_t. */
 } sft_options;
 
 typedef struct {
     int32_t cg_iters;           /* largest iteration count over the fields */
     int32_t reserved;
     double cg_rel_resid;        /* largest final ||r||/||b|| over the fields */
-    int64_t queries;            /* source queries issued: nodes (control) + nelems * N */
+    int64_t queries;            /* source queries issued: nodes (control) + the samples
+                                   (nelems * N, or sum_t N_t with adapt_ref_measure) */
     int64_t fallback_queries;   /* queries no candidate accepted (nearest candidate used) */
     int64_t empty_queries;      /* queries that landed in an empty cell (value 0) */
     float ms_setup;             /* lazily built source/target structures inside this call */

@@ -62,12 +62,14 @@ class _Params(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("samples_per_elem", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("stream", ctypes.c_uint32),
                 ("alpha", ctypes.c_double), ("grid_scale_L", ctypes.c_double),
-                ("cg_tol", ctypes.c_double), ("cg_max_iter", ctypes.c_int), ("sampling", ctypes.c_int)]
+                ("cg_tol", ctypes.c_double), ("cg_max_iter", ctypes.c_int), ("sampling", ctypes.c_int),
+                ("adapt_ref_measure", ctypes.c_double)]
 
 
 class _Stats(ctypes.Structure):
     _fields_ = [("cg_iters", ctypes.c_int), ("cg_rel_resid", ctypes.c_double),
-                ("fallback_queries", ctypes.c_int64), ("empty_queries", ctypes.c_int64)]
+                ("fallback_queries", ctypes.c_int64), ("empty_queries", ctypes.c_int64),
+                ("samples", ctypes.c_int64)]
 
 
 def _declare(L):
@@ -78,6 +80,12 @@ def _declare(L):
     L.orc_u01_f64.restype = ctypes.c_double
     L.orc_sample_element.argtypes = [_int, _int, ctypes.c_uint64, ctypes.c_uint32, _i64,
                                      ctypes.c_int32, _f64p, _f64p, _f64p]
+    L.orc_sample_element_w.argtypes = [_int, _int, ctypes.c_uint64, ctypes.c_uint32, _i64,
+                                       ctypes.c_int32, _int, _f64p, _f64p, _f64p, _f64p]
+    L.orc_adaptive_samples.argtypes = [_int, _f64p, ctypes.c_int32, ctypes.c_double]
+    L.orc_adaptive_samples.restype = ctypes.c_int32
+    L.orc_importance_weight.argtypes = [_int, _f64p]
+    L.orc_importance_weight.restype = ctypes.c_double
     L.orc_sample_element_s.argtypes = [_int, _int, ctypes.c_uint64, ctypes.c_uint32, _i64,
                                        ctypes.c_int32, _int, _f64p, _f64p, _f64p]
     L.orc_strata_per_axis.argtypes = [_int, ctypes.c_int32]
@@ -135,6 +143,24 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 
 def u01(x: int, prec: int) -> float:
     return float(lib().orc_u01_f32(x) if prec == 1 else lib().orc_u01_f64(x))
+
+
+def sample_element_w(prec, dim, seed, stream, t, nsamp, node_xyz, sampling=0):
+    """(lam [N][d+1], X [N][d], w [N]) of one element under any sampling scheme."""
+    k = dim + 1
+    lam = np.zeros((nsamp, k))
+    X = np.zeros((nsamp, dim))
+    w = np.zeros(nsamp)
+    lib().orc_sample_element_w(prec, dim, seed, stream, t, nsamp, sampling, _f64(node_xyz).ravel(), lam, X, w)
+    return lam, X, w
+
+
+def adaptive_samples(dim, node_xyz, nsamp, ref_measure) -> int:
+    return int(lib().orc_adaptive_samples(dim, _f64(node_xyz).ravel(), nsamp, float(ref_measure)))
+
+
+def importance_weight(dim, lam) -> float:
+    return float(lib().orc_importance_weight(dim, _f64(lam)))
 
 
 def sample_element(prec, dim, seed, stream, t, nsamp, node_xyz, sampling=0):
@@ -246,22 +272,26 @@ def pcg(rp, col, val, b, tol=1e-12, max_iter=1000):
 
 
 def transfer(src, tgt, prec, samples_per_elem, seed=0, stream=0, alpha=1.0, grid_scale_L=1.0,
-             cg_tol=1e-12, cg_max_iter=1000, want_sample_elem=False, sampling=0):
-    """Steps 1-7 of Sec. 4 on the CPU; returns a dict of FP64 arrays."""
+             cg_tol=1e-12, cg_max_iter=1000, want_sample_elem=False, sampling=0, adapt_ref_measure=0.0):
+    """Steps 1-7 of Sec. 4 on the CPU; returns a dict of FP64 arrays.
+    sampling: 0 uniform, 1 stratified, 2 importance; adapt_ref_measure > 0:
+    per-element sample counts (sample_elem is then [E][8 N], -1 padded)."""
     sc, sconn, sv = _f64(src.coords), _i32(src.conn), _f64(src.values)
     tc, tconn = _f64(tgt.coords), _i32(tgt.conn)
     dim, nf = sc.shape[1], sv.shape[0]
     nvt, net = tc.shape[0], tconn.shape[0]
-    p = _Params(prec, samples_per_elem, seed, stream, alpha, grid_scale_L, cg_tol, cg_max_iter, sampling)
+    p = _Params(prec, samples_per_elem, seed, stream, alpha, grid_scale_L, cg_tol, cg_max_iter, sampling,
+                adapt_ref_measure)
     st = _Stats()
     out = {k: np.zeros((nf, nvt)) for k in ("g", "b_g", "b_res", "b", "u")}
-    se = np.zeros((net, samples_per_elem), np.int32) if want_sample_elem else None
+    nmax = samples_per_elem * (8 if adapt_ref_measure > 0 else 1)
+    se = np.zeros((net, nmax), np.int32) if want_sample_elem else None
     lib().orc_transfer(dim, ctypes.byref(p), sc.shape[0], sc, sconn.shape[0], sconn, nf, sv,
                        nvt, tc, net, tconn, out["g"], out["b_g"], out["b_res"], out["b"],
                        out["u"], None if se is None else se.ctypes.data_as(_vp),
                        ctypes.byref(st))
     out.update(cg_iters=st.cg_iters, cg_rel_resid=st.cg_rel_resid,
-               fallback_queries=st.fallback_queries, empty_queries=st.empty_queries)
+               fallback_queries=st.fallback_queries, empty_queries=st.empty_queries, samples=st.samples)
     if se is not None:
         out["sample_elem"] = se
     return out

@@ -46,6 +46,17 @@ void orc_sample_element_s(int prec, int dim, uint64_t seed, uint32_t stream, int
                           double* X_out);
 /* strata per axis for nsamp samples in dimension dim: largest m with m^dim <= nsamp */
 int orc_strata_per_axis(int dim, int32_t nsamp);
+/* The same with importance sampling (sampling 2, see rng_sample.c) as well:
+ * w_out [N] gets each sample's weight 1 / (|T| p_t(X_j)) (1 for schemes 0, 1). */
+void orc_sample_element_w(int prec, int dim, uint64_t seed, uint32_t stream, int64_t t,
+                          int32_t nsamp, int sampling, const double* node_xyz, double* lam_out,
+                          double* X_out, double* w_out);
+/* weight 1 / (|T| p_t) of importance sampling at lambda [d+1]:
+ * 1 / (1/4 + 3 sum_{a<b} lambda_a lambda_b) in 2D, 1 / (1/4 + 5/2 sum ...) in 3D */
+double orc_importance_weight(int dim, const double* lam);
+/* samples of an element under the adaptive count: min(8 N, max(1, ceil(N D / D_ref)))
+ * with D = d! |T| the edge determinant of node_xyz and D_ref = d! ref_measure */
+int32_t orc_adaptive_samples(int dim, const double* node_xyz, int32_t nsamp, double ref_measure);
 
 /* ---- point location in a uniform-grid-bucketed source mesh ---- */
 typedef struct orc_grid orc_grid;
@@ -95,7 +106,8 @@ typedef struct {
     double grid_scale_L;
     double cg_tol;
     int cg_max_iter;
-    int sampling;         /* 0 uniform, 1 stratified (orc_sample_element_s) */
+    int sampling;         /* 0 uniform, 1 stratified, 2 importance (orc_sample_element_w) */
+    double adapt_ref_measure; /* > 0: N_t = orc_adaptive_samples(...) per element; 0: N */
 } orc_params;
 
 typedef struct {
@@ -103,10 +115,12 @@ typedef struct {
     double cg_rel_resid;
     int64_t fallback_queries;   /* queries no candidate accepted */
     int64_t empty_queries;      /* queries landing in an empty cell */
+    int64_t samples;            /* sum over elements of the samples drawn */
 } orc_stats;
 
 /* g_out [nf][Vt]; bg_out, bres_out, b_out, u_out [nf][Vt]; sample_elem_out
- * [Et][N] (may be NULL). */
+ * [Et][Nmax] (may be NULL; Nmax = N, or 8 N with the adaptive count; -1 past
+ * an element's count). */
 void orc_transfer(int dim, const orc_params* p,
                   int64_t nvs, const double* src_coords, int64_t nes, const int32_t* src_conn,
                   int nf, const double* src_values,

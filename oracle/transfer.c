@@ -252,11 +252,15 @@ void orc_transfer(int dim, const orc_params* p,
         }
     }
 
-    /* Steps 3-5: per target element, N samples (uniform or stratified); locate each sample in
-     * the source, evaluate f^s and g there, and accumulate the residual
-     * estimate |T|/N sum_j (f^s - alpha g)(X_j) psi_i(X_j) */
-    double* lam = (double*)malloc(sizeof(double) * (size_t)(N * k));
-    double* X = (double*)malloc(sizeof(double) * (size_t)(N * dim));
+    /* Steps 3-5: per target element, N_t samples (uniform, stratified or
+     * importance; N_t = N, or the adaptive count); locate each sample in the
+     * source, evaluate f^s and g there, and accumulate the residual estimate
+     * |T|/N_t sum_j w_j (f^s - alpha g)(X_j) psi_i(X_j), w_j = 1 / (|T| p_t(X_j)) */
+    const int adapt = p->adapt_ref_measure > 0.0;
+    const int Nmax = adapt ? 8 * N : N;
+    double* lam = (double*)malloc(sizeof(double) * (size_t)(Nmax * k));
+    double* X = (double*)malloc(sizeof(double) * (size_t)(Nmax * dim));
+    double* w = (double*)malloc(sizeof(double) * (size_t)Nmax);
     double* acc = (double*)malloc(sizeof(double) * (size_t)(nf * k));
     for (int64_t t = 0; t < net; ++t) {
         const int32_t* v = tgt_conn + t * k;
@@ -264,13 +268,17 @@ void orc_transfer(int dim, const orc_params* p,
         double xyz[12];
         for (int m = 0; m < k; ++m)
             for (int a = 0; a < dim; ++a) xyz[m * dim + a] = tcoord[(int64_t)v[m] * dim + a];
-        orc_sample_element_s(p->prec, dim, p->seed, p->stream, t, N, p->sampling, xyz, lam, X);
+        const int32_t Nt = adapt ? orc_adaptive_samples(dim, xyz, N, p->adapt_ref_measure) : N;
+        stats->samples += Nt;
+        orc_sample_element_w(p->prec, dim, p->seed, p->stream, t, Nt, p->sampling, xyz, lam, X, w);
         for (int i = 0; i < nf * k; ++i) acc[i] = 0.0;
-        for (int j = 0; j < N; ++j) {
+        if (sample_elem_out)
+            for (int j = Nt; j < Nmax; ++j) sample_elem_out[t * Nmax + j] = -1;
+        for (int j = 0; j < Nt; ++j) {
             int32_t e, st;
             orc_grid_locate(grid, 1, X + (int64_t)j * dim, &e, &st);
             if (st == 1) stats->fallback_queries++;
-            if (sample_elem_out) sample_elem_out[t * N + j] = e;
+            if (sample_elem_out) sample_elem_out[t * Nmax + j] = e;
             double fs[64];
             if (e < 0) {
                 stats->empty_queries++;
@@ -283,15 +291,15 @@ void orc_transfer(int dim, const orc_params* p,
                 double gX = 0.0;     /* g is P1 on the target element: sum_m g_m psi_m(X) */
                 for (int m = 0; m < k; ++m) gX += g_out[(int64_t)q * nvt + v[m]] * lj[m];
                 const double r = fs[q] - alpha * gX;
-                for (int i = 0; i < k; ++i) acc[q * k + i] += r * lj[i];
+                for (int i = 0; i < k; ++i) acc[q * k + i] += w[j] * r * lj[i];
             }
         }
         /* Step 6 (residual part): scatter the element-local estimate */
         for (int q = 0; q < nf; ++q)
             for (int i = 0; i < k; ++i)
-                bres_out[(int64_t)q * nvt + v[i]] += vol / (double)N * acc[q * k + i];
+                bres_out[(int64_t)q * nvt + v[i]] += vol / (double)Nt * acc[q * k + i];
     }
-    free(lam); free(X); free(acc);
+    free(lam); free(X); free(w); free(acc);
 
     /* Step 6: b = b_g + b_res */
     for (int64_t i = 0; i < nvt * nf; ++i) b_out[i] = bg_out[i] + bres_out[i];

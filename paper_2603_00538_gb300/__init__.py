@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libsft.so")
  SFT_ERR_DEVICE_STATUS, SFT_ERR_UNSUPPORTED) = range(9)
 SFT_PREC_FP64, SFT_PREC_FP32 = 0, 1
 SFT_CG_MIXED, SFT_CG_FP64 = 0, 1
-SFT_SAMPLING_UNIFORM, SFT_SAMPLING_STRATIFIED = 0, 1
+SFT_SAMPLING_UNIFORM, SFT_SAMPLING_STRATIFIED, SFT_SAMPLING_IMPORTANCE = 0, 1, 2
 SFT_F32, SFT_F64 = 0, 1
 
 
@@ -49,7 +49,8 @@ class sft_options(ctypes.Structure):
                 ("alpha", ctypes.c_double), ("cg_tol", ctypes.c_double), ("strict_inside", ctypes.c_int32),
                 ("out_device", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p),
                 ("sample_elem_out", ctypes.c_void_p), ("field_count", ctypes.c_int32),
-                ("cg_mode", ctypes.c_int32), ("sampling", ctypes.c_int32), ("cg_warm_start", ctypes.c_int32)]
+                ("cg_mode", ctypes.c_int32), ("sampling", ctypes.c_int32), ("cg_warm_start", ctypes.c_int32),
+                ("adapt_ref_measure", ctypes.c_double)]
 
 
 class sft_stats(ctypes.Structure):
@@ -287,10 +288,12 @@ def sft_transfer(src: Source, tgt: Target, samples_per_elem: int, precision: int
                  seed: int = 0, stream_id: int = 0, alpha: float = 1.0, cg_tol: float = 1e-10,
                  cg_max_iter: int = 1000, strict_inside: bool = False, u_out=None, b_out=None, g_out=None,
                  sample_elem_out=None, stream=None, allow_not_converged: bool = False, field_count: int = 0,
-                 cg_mode: int = SFT_CG_MIXED, sampling: int = SFT_SAMPLING_UNIFORM, cg_warm_start: bool = False):
+                 cg_mode: int = SFT_CG_MIXED, sampling: int = SFT_SAMPLING_UNIFORM, cg_warm_start: bool = False,
+                 adapt_ref_measure: float = 0.0):
     """Run one transfer. Outputs are caller-provided arrays (numpy for host,
     torch CUDA tensors for device); when u_out is None a host array
-    [nfields, nnodes] is allocated. Returns (status, stats dict, u_out)."""
+    [nfields, nnodes] is allocated. sample_elem_out is [nelems, N], or
+    [nelems, 8 N] with adapt_ref_measure > 0. Returns (status, stats dict, u_out)."""
     nf = int(field_count) if field_count > 0 else _nf(src)
     if u_out is None:
         u_out = np.zeros((nf, _nv(tgt)), np.float64)
@@ -317,6 +320,7 @@ def sft_transfer(src: Source, tgt: Target, samples_per_elem: int, precision: int
     o.cg_mode = int(cg_mode)
     o.sampling = int(sampling)
     o.cg_warm_start = int(bool(cg_warm_start))
+    o.adapt_ref_measure = float(adapt_ref_measure)
     st = sft_stats()
     allow = (SFT_OK, SFT_ERR_NOT_CONVERGED) if allow_not_converged else (SFT_OK,)
     status = _check(lib().sft_transfer(src.h, tgt.h, ctypes.byref(o), up, bp, gp, ctypes.byref(st)),
@@ -475,7 +479,7 @@ class Batch(_Handle):
 
 def _options(samples_per_elem, seed=0, stream_id=0, alpha=1.0, cg_tol=1e-10, cg_max_iter=1000,
              field_count=0, precision=SFT_PREC_FP32, cg_mode=SFT_CG_MIXED, sampling=SFT_SAMPLING_UNIFORM,
-             cg_warm_start=False):
+             cg_warm_start=False, adapt_ref_measure=0.0):
     o = sft_options()
     o.samples_per_elem = int(samples_per_elem)
     o.precision = int(precision)
@@ -488,6 +492,7 @@ def _options(samples_per_elem, seed=0, stream_id=0, alpha=1.0, cg_tol=1e-10, cg_
     o.cg_mode = int(cg_mode)
     o.sampling = int(sampling)
     o.cg_warm_start = int(bool(cg_warm_start))
+    o.adapt_ref_measure = float(adapt_ref_measure)
     return o
 
 

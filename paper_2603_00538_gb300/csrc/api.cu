@@ -234,13 +234,22 @@ sft_status sft_transfer(sft_source s, sft_target t, const sft_options* o, double
   if (o->precision != SFT_PREC_FP32 && o->precision != SFT_PREC_FP64) return fail(SFT_ERR_ARG, "bad precision");
   if (o->cg_max_iter < 0 || !(o->cg_tol >= 0) || !std::isfinite(o->alpha)) return fail(SFT_ERR_ARG, "bad solver options");
   if (o->cg_mode != SFT_CG_MIXED && o->cg_mode != SFT_CG_FP64) return fail(SFT_ERR_ARG, "unknown cg_mode");
-  if (o->sampling != SFT_SAMPLING_UNIFORM && o->sampling != SFT_SAMPLING_STRATIFIED)
+  if (o->sampling != SFT_SAMPLING_UNIFORM && o->sampling != SFT_SAMPLING_STRATIFIED &&
+      o->sampling != SFT_SAMPLING_IMPORTANCE)
     return fail(SFT_ERR_ARG, "unknown sampling scheme");
   if (o->cg_warm_start != 0 && o->cg_warm_start != 1) return fail(SFT_ERR_ARG, "cg_warm_start must be 0 or 1");
   if (o->cg_warm_start && o->cg_mode != SFT_CG_MIXED) return fail(SFT_ERR_UNSUPPORTED, "a warm start needs cg_mode MIXED");
   if (o->sampling == SFT_SAMPLING_STRATIFIED && o->samples_per_elem > kMaxStratifiedN)
     return fail(SFT_ERR_UNSUPPORTED, "stratified sampling supports at most 2^20 samples per element");
+  if (!(o->adapt_ref_measure >= 0.0) || !std::isfinite(o->adapt_ref_measure))
+    return fail(SFT_ERR_ARG, "adapt_ref_measure must be finite and >= 0");
+  const bool adapt = o->adapt_ref_measure > 0.0;
+  if (adapt && o->sampling == SFT_SAMPLING_STRATIFIED)
+    return fail(SFT_ERR_UNSUPPORTED, "adaptive sample counts need uniform or importance sampling");
+  if (adapt && (int64_t)o->samples_per_elem * 8 * t->ne >= ((int64_t)1 << 40))
+    return fail(SFT_ERR_UNSUPPORTED, "too many samples");
   if (o->field_count < 0 || o->field_count > s->nf) return fail(SFT_ERR_ARG, "field_count out of range");
+  const int64_t nmax = (int64_t)o->samples_per_elem * (adapt ? 8 : 1);   // sample_elem row length
   cudaStream_t st = (cudaStream_t)o->cuda_stream;
   const int prec = o->precision;
   const int nf = o->field_count > 0 ? o->field_count : s->nf;
@@ -261,9 +270,9 @@ sft_status sft_transfer(sft_source s, sft_target t, const sft_options* o, double
   DevBuf<int32_t> se_tmp(st);
   SFT_CUDA(g.alloc(psz * nv * nf));
   SFT_CUDA(b.alloc((size_t)nv * nf));
-  SFT_CUDA(counters.alloc(2));
+  SFT_CUDA(counters.alloc(3));
   SFT_CUDA(cudaMemsetAsync(b.p, 0, sizeof(double) * nv * nf, st));
-  SFT_CUDA(cudaMemsetAsync(counters.p, 0, sizeof(int64_t) * 2, st));
+  SFT_CUDA(cudaMemsetAsync(counters.p, 0, sizeof(int64_t) * 3, st));
 
   // step 1: control values g = f^s at the target nodes
   if (sft_status r = locate_points(s, prec, nv, t->coordsP[prec], prec == SFT_PREC_FP64, nullptr, g.p,
@@ -277,7 +286,7 @@ sft_status sft_transfer(sft_source s, sft_target t, const sft_options* o, double
     if (o->out_device) {
       se = o->sample_elem_out;
     } else {
-      SFT_CUDA(se_tmp.alloc((size_t)ne * o->samples_per_elem));
+      SFT_CUDA(se_tmp.alloc((size_t)(ne * nmax)));
       se = se_tmp.p;
     }
   }
@@ -293,6 +302,7 @@ sft_status sft_transfer(sft_source s, sft_target t, const sft_options* o, double
   a.sample_elem = se;
   a.counters = counters.p;
   a.sampling = o->sampling;
+  a.adapt_ref = o->adapt_ref_measure;
   if (sft_status r = launch_assembly(s, t, a, st)) return r;
   if (ev.ok) cudaEventRecord(ev.e[3], st);
 
@@ -326,8 +336,8 @@ sft_status sft_transfer(sft_source s, sft_target t, const sft_options* o, double
     }
   }
   if (se && !o->out_device)
-    SFT_CUDA(cudaMemcpyAsync(o->sample_elem_out, se, sizeof(int32_t) * ne * o->samples_per_elem, d2o, st));
-  int64_t hc[2] = {0, 0};
+    SFT_CUDA(cudaMemcpyAsync(o->sample_elem_out, se, sizeof(int32_t) * ne * nmax, d2o, st));
+  int64_t hc[3] = {0, 0, 0};
   int32_t herr = 0;
   SFT_CUDA(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
   SFT_CUDA(cudaMemcpyAsync(&herr, d_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -339,7 +349,8 @@ sft_status sft_transfer(sft_source s, sft_target t, const sft_options* o, double
     std::memset(stats, 0, sizeof(*stats));
     stats->cg_iters = sr.iters;
     stats->cg_rel_resid = sr.rel_resid;
-    stats->queries = nv + ne * (int64_t)o->samples_per_elem;
+    stats->queries = nv + (adapt || o->sampling == SFT_SAMPLING_IMPORTANCE ? hc[2]
+                                                                            : ne * (int64_t)o->samples_per_elem);
     stats->fallback_queries = hc[0];
     stats->empty_queries = hc[1];
     stats->ms_setup = ev.ms(0, 1);

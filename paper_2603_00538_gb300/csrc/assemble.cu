@@ -30,7 +30,43 @@ struct AsmParams {
   double c_det;   // alpha / ((d+1)(d+2)): exact P1 mass factor of the control term
   double inv_n;   // 1 / N
   Strat st;       // sampling scheme (st.n = 0: uniform)
+  int imp;        // importance sampling (the EXT kernel)
+  int adapt;      // per-element sample counts (the EXT kernel)
+  double dref;    // d! x the reference measure of the adaptive count
+  int nmax;       // samples per element at most (row length of sample_elem)
 };
+
+// Adaptive sample count of an element (the EXT kernel): N_t = min(8 N,
+// max(1, ceil(N D / dref))) with D = d! |T| the edge determinant of its
+// vertices in P, evaluated in FP64 left to right (the oracle's order).
+template <int D, typename P>
+__device__ __forceinline__ int adaptive_count(const P xv[D + 1][D], int N, double dref) {
+  double x[D + 1][D];
+#pragma unroll
+  for (int m = 0; m <= D; ++m)
+#pragma unroll
+    for (int a = 0; a < D; ++a) x[m][a] = f2d(xv[m][a]);
+  double det;
+  if constexpr (D == 2) {
+    det = __dsub_rn(__dmul_rn(__dsub_rn(x[1][0], x[0][0]), __dsub_rn(x[2][1], x[0][1])),
+                    __dmul_rn(__dsub_rn(x[2][0], x[0][0]), __dsub_rn(x[1][1], x[0][1])));
+  } else {
+    double e1[3], e2[3], e3[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      e1[a] = __dsub_rn(x[1][a], x[0][a]);
+      e2[a] = __dsub_rn(x[2][a], x[0][a]);
+      e3[a] = __dsub_rn(x[3][a], x[0][a]);
+    }
+    const double t0 = __dmul_rn(e1[0], __dsub_rn(__dmul_rn(e2[1], e3[2]), __dmul_rn(e2[2], e3[1])));
+    const double t1 = __dmul_rn(e1[1], __dsub_rn(__dmul_rn(e2[0], e3[2]), __dmul_rn(e2[2], e3[0])));
+    const double t2 = __dmul_rn(e1[2], __dsub_rn(__dmul_rn(e2[0], e3[1]), __dmul_rn(e2[1], e3[0])));
+    det = __dadd_rn(__dsub_rn(t0, t1), t2);
+  }
+  const double q = ceil(__ddiv_rn(__dmul_rn((double)N, det), dref));
+  const double cap = 8.0 * (double)N;
+  return (int)(q < 1.0 ? 1.0 : (q > cap ? cap : q));
+}
 
 // MODE: kAsmPlain; kAsmDebug also writes the source element of every sample
 // (sample_elem); kAsmRecord also writes its barycentric coordinates mu_1..d
@@ -40,7 +76,9 @@ struct AsmParams {
 // Four resident blocks per SM in both dimensions (64 registers a thread). In
 // 3D that leaves 32 bytes of spill, yet the extra warps hide the longer
 // location chains: tet5m launch 4.165 -> 3.724 ms against three blocks.
-template <int D, typename P, int NF, int MODE>
+// EXT: the kernel with importance sampling (p.imp) and per-element sample
+// counts (p.adapt); without it the kernel is the uniform / stratified one.
+template <int D, typename P, int NF, int MODE, bool EXT>
 __global__ void __launch_bounds__(256, 4) k_assemble(const P* __restrict__ tx, const int32_t* __restrict__ tconn,
                                                   const double* __restrict__ vol, const float* __restrict__ vol32,
                                                   const P* __restrict__ g,
@@ -85,6 +123,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const P* __restrict__ tx, c
     P xv[K][D];
     P gl[NF][K];
     Acc<P> acc[NF][K];
+    int Nt = p.N;   // this element's samples
     if (active) {
 #pragma unroll
       for (int m = 0; m < K; ++m) {
@@ -94,20 +133,34 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const P* __restrict__ tx, c
 #pragma unroll
         for (int f = 0; f < NF; ++f) gl[f][m] = f < p.nf ? __ldg(g + (int64_t)f * p.nv + v[m]) : P(0);
       }
+      if (EXT && p.adapt) Nt = adaptive_count<D, P>(xv, p.N, p.dref);
     }
+    // importance sampling draws one sample per unit (two Philox blocks)
+    const int spu = EXT && p.imp ? 1 : SPU;
+    const int Ut = EXT ? (Nt + spu - 1) / spu : p.U;
+    if (EXT && MODE == kAsmDebug && active && lane == seg_lo)
+      for (int j = Nt; j < p.nmax; ++j) sample_elem[t * p.nmax + j] = -1;
 
-    for (int u = u0; active && u < p.U; u += ustep) {
-      const uint4 w = philox4x32_10(make_uint4((uint32_t)u, (uint32_t)t, p.stream_id, 0u), p.rk);
+    for (int u = u0; active && u < Ut; u += ustep) {
+      uint4 w, wb;
+      if (EXT && p.imp) {
+        w = philox4x32_10(make_uint4((uint32_t)u, (uint32_t)t, p.stream_id, 6u), p.rk);
+        wb = philox4x32_10(make_uint4((uint32_t)u, (uint32_t)t, p.stream_id, 7u), p.rk);
+      } else {
+        w = philox4x32_10(make_uint4((uint32_t)u, (uint32_t)t, p.stream_id, 0u), p.rk);
+      }
 #pragma unroll
       for (int s = 0; s < SPU; ++s) {
-        const int j = SPU * u + s;
-        if (j >= p.N) break;
+        const int j = EXT && p.imp ? u : SPU * u + s;
+        if ((EXT && p.imp && s > 0) || j >= Nt) break;
         P lam[K];
-        sample_lambda<D, P>(w, j, p.st, lam);
+        P wgt = P(1);
+        if (EXT && p.imp) wgt = importance_lambda<D, P>(w, wb, lam);
+        else sample_lambda<D, P>(w, j, p.st, lam);
         P mu[K];
         int status = 0;
         int32_t e;
-        const int64_t idx = t * p.N + j;
+        const int64_t idx = t * (EXT ? p.nmax : p.N) + j;
         if constexpr (MODE == kAsmCached) {
           e = __ldg(sample_elem + idx);
           P m0 = P(1);
@@ -136,7 +189,8 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const P* __restrict__ tx, c
           P gX = A::mul(gl[f][0], lam[0]);
 #pragma unroll
           for (int m = 1; m < K; ++m) gX = A::fma(gl[f][m], lam[m], gX);
-          const P r = A::sub(fs, A::mul(alphaP, gX));
+          P r = A::sub(fs, A::mul(alphaP, gX));
+          if (EXT && p.imp) r = A::mul(wgt, r);   // w_j (f^s - alpha g): the density's weight
 #pragma unroll
           for (int i = 0; i < K; ++i) acc[f][i].add(A::mul(r, lam[i]));
         }
@@ -160,7 +214,9 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const P* __restrict__ tx, c
     if (active && lane == seg_lo) {
       const double w = sizeof(P) == 8 ? __ldg(vol + t) : 0.0;
       const float wf = sizeof(P) == 4 ? __ldg(vol32 + t) : 0.f;
-      const P cdet = (P)p.c_det, cmc = (P)p.inv_n;
+      const P cdet = (P)p.c_det;
+      const P cmc = EXT && p.adapt ? (P)__drcp_rn((double)Nt) : (P)p.inv_n;   // 1 / N_t
+      if (EXT && counters) atomicAdd(reinterpret_cast<unsigned long long*>(counters + 2), (unsigned long long)Nt);
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         if (f >= p.nf) break;
@@ -194,10 +250,16 @@ static void launch_t(sft_source_s* s, sft_target_s* t, const AssembleArgs& a, co
                                                (const P*)L.recs, L.adj, (const P*)L.vals, p, a.b, a.sample_elem,
                                                (P*)a.pmu, a.counters);
   };
-  if (a.mode == kAsmCached) args(k_assemble<D, P, NF, kAsmCached>);
-  else if (a.mode == kAsmRecord) args(k_assemble<D, P, NF, kAsmRecord>);
-  else if (a.sample_elem) args(k_assemble<D, P, NF, kAsmDebug>);
-  else args(k_assemble<D, P, NF, kAsmPlain>);
+  const bool ext = p.imp || p.adapt;  // only with the plain and debug modes (checked by the callers)
+  if (a.mode == kAsmCached) args(k_assemble<D, P, NF, kAsmCached, false>);
+  else if (a.mode == kAsmRecord) args(k_assemble<D, P, NF, kAsmRecord, false>);
+  else if (a.sample_elem) {
+    if (ext) args(k_assemble<D, P, NF, kAsmDebug, true>);
+    else args(k_assemble<D, P, NF, kAsmDebug, false>);
+  } else {
+    if (ext) args(k_assemble<D, P, NF, kAsmPlain, true>);
+    else args(k_assemble<D, P, NF, kAsmPlain, false>);
+  }
 }
 
 template <int D, typename P>
@@ -231,6 +293,10 @@ sft_status launch_assembly(sft_source_s* s, sft_target_s* t, const AssembleArgs&
   p.c_det = a.alpha / (double)((t->dim + 1) * (t->dim + 2));
   p.inv_n = 1.0 / (double)a.N;
   p.st = strat_for(t->dim, a.N, a.sampling);
+  p.imp = a.sampling == SFT_SAMPLING_IMPORTANCE ? 1 : 0;
+  p.adapt = a.adapt_ref > 0.0 ? 1 : 0;
+  p.dref = a.adapt_ref * (t->dim == 2 ? 2.0 : 6.0);
+  p.nmax = p.adapt ? 8 * a.N : a.N;
   if (t->dim == 2) {
     if (a.prec == SFT_PREC_FP32) launch_nf<2, float>(s, t, a, p, st);
     else launch_nf<2, double>(s, t, a, p, st);

@@ -1345,6 +1345,8 @@ sft_status sft_batch_create(int32_t nreq, const sft_source* srcs, const sft_targ
     if (o.samples_per_elem < 1 || o.cg_max_iter < 0 || !(o.cg_tol >= 0) || !std::isfinite(o.alpha))
       return fail(SFT_ERR_ARG, "bad request options");
     if (o.cg_mode != SFT_CG_MIXED && o.cg_mode != SFT_CG_FP64) return fail(SFT_ERR_ARG, "unknown cg_mode");
+    if (o.sampling == SFT_SAMPLING_IMPORTANCE || o.adapt_ref_measure != 0.0)
+      return fail(SFT_ERR_UNSUPPORTED, "importance sampling and adaptive sample counts: sft_transfer only");
     if (o.sampling != SFT_SAMPLING_UNIFORM && o.sampling != SFT_SAMPLING_STRATIFIED)
       return fail(SFT_ERR_ARG, "unknown sampling scheme");
     if (o.cg_warm_start) return fail(SFT_ERR_UNSUPPORTED, "batched transfers start every solve from 0");

@@ -214,6 +214,97 @@ __device__ __forceinline__ void sample_lambda(const uint4& w, int j, const Strat
   }
 }
 
+// ---------------------------------------------------------------------------
+// Importance sampling (Eq. mc_element_integral_operator_general with a
+// non-uniform p_t): a mixture of the uniform density and the edge-bubble
+// densities (d+1)(d+2) lambda_a lambda_b / |T| (Dirichlet with 2 at the
+// edge's vertices a, b and 1 elsewhere), which follow the P1 interpolation
+// error that the control-variate residual is at alpha = 1. Component
+// probabilities: 2D uniform 1/4, each of the 3 edges 1/4; 3D uniform 1/4,
+// each of the 6 edges 1/8; so |T| p_t = 1/4 + 3 sum_{a<b} lambda_a lambda_b
+// (2D) or 1/4 + 5/2 sum (3D), and the sample weight w = 1 / (|T| p_t) <= 4.
+// Sample j: Philox blocks (j, t, stream, 6) = a and (j, t, stream, 7) = b.
+// The top bits of a.x pick the component (2D: a.x >> 30, 0 uniform, 1..3 the
+// edges (0,1), (0,2), (1,2); 3D: a.x >> 29, 0..1 uniform, 2..7 the edges
+// (0,1), (0,2), (0,3), (1,2), (1,3), (2,3)). Uniform: the Osada map of
+// a.y, a.z (2D) or the sorted spacings of a.y, a.z, a.w (3D). Edge (ea, eb):
+// the d + 2 uniforms a.y, a.z, a.w, b.x (, b.y) sorted, spacings s_0..s_{d+2}
+// (s_0 = v_0, s_i = v_i - v_{i-1}, s_{d+2} = 1 - v_{d+1}); lambda_ea =
+// s_0 + s_1, lambda_eb = s_2 + s_3, the other vertices in increasing order
+// s_4 (, s_5). One rounding per operation in P.
+// ---------------------------------------------------------------------------
+template <typename P>
+__device__ __forceinline__ void cswap(P& x, P& y) {
+  const P lo = y < x ? y : x, hi = y < x ? x : y;
+  x = lo;
+  y = hi;
+}
+
+template <int D, typename P>
+__device__ __forceinline__ P importance_lambda(const uint4& a, const uint4& b, P lam[D + 1]) {
+  using A = Ar<P>;
+  const uint32_t c = D == 2 ? (a.x >> 30) : (a.x >> 29);
+  if (D == 2 ? c == 0u : c < 2u) {
+    if constexpr (D == 2) {
+      const P s = A::sqrt(A::u01(a.y)), eta = A::u01(a.z);
+      lam[0] = A::sub(P(1), s);
+      lam[1] = A::mul(s, A::sub(P(1), eta));
+      lam[2] = A::mul(s, eta);
+    } else {
+      P v0 = A::u01(a.y), v1 = A::u01(a.z), v2 = A::u01(a.w);
+      cswap(v0, v1); cswap(v1, v2); cswap(v0, v1);
+      lam[0] = v0;
+      lam[1] = A::sub(v1, v0);
+      lam[2] = A::sub(v2, v1);
+      lam[3] = A::sub(P(1), v2);
+    }
+  } else {
+    P v[D + 2];
+    v[0] = A::u01(a.y); v[1] = A::u01(a.z); v[2] = A::u01(a.w); v[3] = A::u01(b.x);
+    if constexpr (D == 2) {
+      cswap(v[0], v[1]); cswap(v[2], v[3]); cswap(v[0], v[2]); cswap(v[1], v[3]); cswap(v[1], v[2]);
+    } else {
+      v[4] = A::u01(b.y);
+      cswap(v[0], v[1]); cswap(v[3], v[4]); cswap(v[2], v[4]); cswap(v[2], v[3]); cswap(v[0], v[3]);
+      cswap(v[0], v[2]); cswap(v[1], v[4]); cswap(v[1], v[3]); cswap(v[1], v[2]);
+    }
+    P sp[D + 3];
+    sp[0] = v[0];
+#pragma unroll
+    for (int i = 1; i < D + 2; ++i) sp[i] = A::sub(v[i], v[i - 1]);
+    sp[D + 2] = A::sub(P(1), v[D + 1]);
+    const P la = A::add(sp[0], sp[1]), lb = A::add(sp[2], sp[3]);
+    // the edge's vertices (ea < eb) and the others in increasing order
+    int ea, eb;
+    if constexpr (D == 2) {
+      ea = c == 3u ? 1 : 0;
+      eb = c == 1u ? 1 : 2;
+    } else {
+      const int e = (int)c - 2;   // (0,1) (0,2) (0,3) (1,2) (1,3) (2,3)
+      ea = e < 3 ? 0 : (e < 5 ? 1 : 2);
+      eb = e < 3 ? e + 1 : (e < 5 ? e - 1 : 3);
+    }
+    // the vertices off the edge, in increasing order: o1 (and o2 in 3D)
+    const int o1 = ea > 0 ? 0 : (eb > 1 ? 1 : 2);
+    const int o2 = D == 2 ? o1 : 6 - ea - eb - o1;
+#pragma unroll
+    for (int m = 0; m <= D; ++m) {
+      P x = sp[4];
+      if constexpr (D == 3) x = m == o2 ? sp[5] : x;
+      x = m == o1 ? sp[4] : x;
+      x = m == eb ? lb : x;
+      lam[m] = m == ea ? la : x;
+    }
+  }
+  P bub = P(0);
+#pragma unroll
+  for (int x = 0; x <= D; ++x)
+#pragma unroll
+    for (int y = x + 1; y <= D; ++y) bub = A::add(bub, A::mul(lam[x], lam[y]));
+  const P tp = A::add(P(0.25), A::mul(D == 2 ? P(3) : P(2.5), bub));
+  return A::div(P(1), tp);
+}
+
 // X = sum_m lam_m x_m, accumulated left to right, one rounding per operation
 template <int D, typename P>
 __device__ __forceinline__ void map_point(const P lam[D + 1], const P xv[D + 1][D], P X[D]) {

@@ -164,6 +164,7 @@ struct AssembleArgs {
   int mode = kAsmPlain;
   void* pmu = nullptr;    // record / cached: [d][ne_t N] P, mu_1..d of every sample
   int sampling = SFT_SAMPLING_UNIFORM;  // sft_sampling
+  double adapt_ref = 0.0;  // > 0: per-element sample counts against this reference measure
 };
 sft_status launch_assembly(sft_source_s* s, sft_target_s* t, const AssembleArgs& a, cudaStream_t st);
 // solve.cu

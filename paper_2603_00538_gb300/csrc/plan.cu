@@ -70,6 +70,8 @@ sft_status sft_plan_create(sft_source s, sft_target t, const sft_options* o, sft
   if (o->precision != SFT_PREC_FP32 && o->precision != SFT_PREC_FP64) return fail(SFT_ERR_ARG, "bad precision");
   if (o->cg_max_iter < 0 || !(o->cg_tol >= 0) || !std::isfinite(o->alpha)) return fail(SFT_ERR_ARG, "bad solver options");
   if (o->cg_mode != SFT_CG_MIXED && o->cg_mode != SFT_CG_FP64) return fail(SFT_ERR_ARG, "unknown cg_mode");
+  if (o->sampling == SFT_SAMPLING_IMPORTANCE || o->adapt_ref_measure != 0.0)
+    return fail(SFT_ERR_UNSUPPORTED, "importance sampling and adaptive sample counts: sft_transfer only");
   if (o->sampling != SFT_SAMPLING_UNIFORM && o->sampling != SFT_SAMPLING_STRATIFIED)
     return fail(SFT_ERR_ARG, "unknown sampling scheme");
   if (o->cg_warm_start != 0 && o->cg_warm_start != 1) return fail(SFT_ERR_ARG, "cg_warm_start must be 0 or 1");

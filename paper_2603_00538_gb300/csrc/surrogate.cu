@@ -493,6 +493,8 @@ sft_status sft_transfer_surrogate(sft_mlp net, sft_source exact, sft_target t, c
   if ((int64_t)o->samples_per_elem * t->ne >= ((int64_t)1 << 40)) return fail(SFT_ERR_UNSUPPORTED, "too many samples");
   if (o->cg_max_iter < 0 || !(o->cg_tol >= 0) || !std::isfinite(o->alpha)) return fail(SFT_ERR_ARG, "bad solver options");
   if (o->cg_mode != SFT_CG_MIXED && o->cg_mode != SFT_CG_FP64) return fail(SFT_ERR_ARG, "unknown cg_mode");
+  if (o->sampling == SFT_SAMPLING_IMPORTANCE || o->adapt_ref_measure != 0.0)
+    return fail(SFT_ERR_UNSUPPORTED, "importance sampling and adaptive sample counts: sft_transfer only");
   if (o->sampling != SFT_SAMPLING_UNIFORM && o->sampling != SFT_SAMPLING_STRATIFIED)
     return fail(SFT_ERR_ARG, "unknown sampling scheme");
   if (o->cg_warm_start != 0 && o->cg_warm_start != 1) return fail(SFT_ERR_ARG, "cg_warm_start must be 0 or 1");

@@ -225,6 +225,131 @@ def test_stratified_unbiased_and_faster_than_uniform(orc):
     assert all(r1 < r0 for r0, r1 in zip(rms[0], rms[1]))
 
 
+@pytest.mark.parametrize("dim,prec", [(2, 0), (2, 1), (3, 0), (3, 1)])
+def test_importance_density_closed_forms(orc, dim, prec):
+    """Importance sampling (Eq. mc_element_integral_operator_general with the
+    mixture p_t = (pi_u + sum_{a<b} pi_e (d+1)(d+2) lambda_a lambda_b) / |T|):
+    every sample lies in the element, the weights lie in (0, 4], and the
+    weighted sample means E_p[w h] equal the plain averages int_T h / |T| of
+    closed forms: h = 1 (the normalisation, which a wrong constant or
+    component probability breaks), h = lambda_i lambda_j ((1 + delta_ij) /
+    ((d+1)(d+2))) and h = prod lambda (d! / (2d+1)!), within 4 standard
+    errors."""
+    k = dim + 1
+    xyz = np.vstack([np.zeros(dim), np.eye(dim)]) * 0.7 + 0.1        # a scaled reference simplex
+    n = 200_000
+    lam, X, w = orc.sample_element_w(prec, dim, 3, 1, 5, n, xyz, sampling=2)
+    assert (lam >= 0).all()
+    assert np.abs(lam.sum(1) - 1).max() <= (4e-7 if prec else 1e-15)
+    assert np.allclose(X, lam @ xyz, atol=1e-6 if prec else 1e-15)
+    assert np.all((w > 0) & (w <= 4.0))
+
+    def check(vals, exact):
+        m, se = vals.mean(), vals.std(ddof=1) / math.sqrt(vals.size)
+        assert abs(m - exact) <= 4 * se + 1e-12, (m, exact, se)
+    check(w, 1.0)
+    for i in range(k):
+        for j in range(i, k):
+            check(w * lam[:, i] * lam[:, j], (2.0 if i == j else 1.0) / ((dim + 1) * (dim + 2)))
+    check(w * np.prod(lam, axis=1), math.factorial(dim) / math.factorial(2 * dim + 1))
+    assert orc.importance_weight(dim, lam[0]) == w[0]
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_importance_lowers_the_variance_of_a_bubble_residual(orc, dim):
+    """The control-variate residual of a smooth field at alpha = 1 is the P1
+    interpolation error, a sum of edge bubbles; for the isotropic one
+    (sum_{a<b} lambda_a lambda_b) the weighted integrands w r psi_i have a
+    smaller variance under p_t than r psi_i under uniform sampling, for every
+    basis function: by 8 % in 2D, by 1 % only in 3D, where these integrands
+    spread almost evenly over the tetrahedron (2,000,000 samples each, so the
+    ratio is known to about 0.2 %)."""
+    xyz = np.vstack([np.zeros(dim), np.eye(dim)])
+    n = 2_000_000
+    lam_u, _, _ = orc.sample_element_w(0, dim, 11, 0, 0, n, xyz, sampling=0)
+    lam_p, _, w = orc.sample_element_w(0, dim, 11, 0, 0, n, xyz, sampling=2)
+
+    def bubble(lam):
+        return sum(lam[:, a] * lam[:, b] for a in range(dim + 1) for b in range(a + 1, dim + 1))
+    for i in range(dim + 1):
+        hu = bubble(lam_u) * lam_u[:, i]
+        hp = w * bubble(lam_p) * lam_p[:, i]
+        assert abs(hu.mean() - hp.mean()) <= 4 * hp.std() / math.sqrt(n)
+        assert hp.var() < (0.95 if dim == 2 else 0.998) * hu.var(), (i, hp.var() / hu.var())
+
+
+def test_importance_unbiased_against_mesh_intersection(orc):
+    """The importance-sampled estimate stays unbiased against the exact
+    mesh-intersection load vector: the mean over 300 seeds lies within 5
+    standard errors, at alpha = 0 and alpha = 1."""
+    s, t = _pair(2, ns=5)
+    s = W.with_values(s, [W.field_sincos])
+    b_mi = orc.mi_load_vector_2d(s, t)
+    for alpha in (0.0, 1.0):
+        bs = np.stack([orc.transfer(s, t, 0, 8, seed=sd, alpha=alpha, cg_max_iter=1, sampling=2)["b"][0]
+                       for sd in range(300)])
+        mean, se = bs.mean(0), bs.std(0, ddof=1) / math.sqrt(bs.shape[0])
+        se = np.sqrt(se ** 2 + (1e-13 * np.abs(b_mi).max()) ** 2)
+        z = (mean - b_mi) / se
+        assert np.abs(z).max() < 5.0
+        assert abs(z.mean()) < 5.0 / math.sqrt(z.size)
+
+
+def test_adaptive_counts(orc):
+    """Per-element sample counts N_t = min(8N, max(1, ceil(N |T| / A_ref))):
+    equal elements with A_ref just above their measure get N each; on a
+    graded mesh the counts follow the measures, so the total is N |Omega| /
+    A_ref up to one sample per element; the cap and the floor hold."""
+    m = W.jittered_tri_mesh(6, 0, jitter=0.0)                      # equal right triangles
+    area = 0.5 / 36
+    for e in range(m.nelems):
+        assert orc.adaptive_samples(2, m.coords[m.conn[e]], 12, area * (1 + 1e-9)) == 12
+    g = W.jittered_tri_mesh(8, 1)
+    g = W.Mesh(g.coords ** 2, g.conn, None)                         # graded towards the origin
+    meas = W._signed_measure(g.coords, g.conn)
+    ref = meas.sum() / g.nelems
+    counts = np.array([orc.adaptive_samples(2, g.coords[g.conn[e]], 10, ref) for e in range(g.nelems)])
+    assert counts.min() >= 1 and counts.max() <= 80
+    assert np.all(np.diff(counts[np.argsort(meas)]) >= 0)            # monotone in the measure
+    assert 10 * g.nelems <= counts.sum() <= 10 * g.nelems + g.nelems
+    kuhn = W.jittered_kuhn_mesh(2, 0, jitter=0.0)
+    vol = 1.0 / (6 * 8)
+    assert orc.adaptive_samples(3, kuhn.coords[kuhn.conn[0]], 5, vol * (1 + 1e-9)) == 5
+    assert orc.adaptive_samples(3, kuhn.coords[kuhn.conn[0]], 5, vol / 100) == 40   # the cap, 8 N
+    assert orc.adaptive_samples(3, kuhn.coords[kuhn.conn[0]], 5, vol * 100) == 1    # the floor
+
+
+def test_adaptive_counts_unbiased_and_steadier_conservation_sum(orc):
+    """With per-element counts the estimate stays unbiased against mesh
+    intersection, and on a graded target (element measures spanning two
+    orders of magnitude) the total sum_i b_i, an estimate of int f^s, spreads
+    less over seeds than with the same total number of samples spread evenly
+    (alpha = 0: the residual is f itself, whose spread over an element grows
+    with its size, so the large elements need the samples)."""
+    s = W.with_values(W.jittered_tri_mesh(12, 3), [W.field_sincos])
+    t = W.delaunay_tri_mesh(60, 5, 4)
+    t = W.Mesh(t.coords ** 2, t.conn, None)
+    W._fix_orientation(t)
+    meas = W._signed_measure(t.coords, t.conn)
+    assert meas.max() / meas.min() > 100
+    ref = meas.sum() / t.nelems
+    b_mi = orc.mi_load_vector_2d(s, t)
+    N = 6
+    runs = [orc.transfer(s, t, 0, N, seed=sd, alpha=0.0, cg_max_iter=1, adapt_ref_measure=ref)
+            for sd in range(200)]
+    bs = np.stack([r["b"][0] for r in runs])
+    total = runs[0]["samples"]
+    assert all(r["samples"] == total for r in runs)
+    mean, se = bs.mean(0), bs.std(0, ddof=1) / math.sqrt(bs.shape[0])
+    se = np.sqrt(se ** 2 + (1e-13 * np.abs(b_mi).max()) ** 2)
+    z = (mean - b_mi) / se
+    assert np.abs(z).max() < 5.0
+    # the same budget without adaptation: N' per element with N' E >= total
+    Nu = -(-total // t.nelems)
+    sums_u = [orc.transfer(s, t, 0, Nu, seed=sd, alpha=0.0, cg_max_iter=1)["b"][0].sum() for sd in range(200)]
+    assert bs.sum(1).std() < 0.8 * np.std(sums_u)
+
+
 # --------------------------------------------------------------------------
 # point location
 # --------------------------------------------------------------------------
