@@ -444,10 +444,17 @@ sft_status sft_mass_solve_static(int64_t n, const int32_t* row_ptr, const int32_
 
 /* Inspection of the built structures (host copies; any output may be NULL).
  * Source grid for `precision`: cells per axis n[3], cell count, registration
- * count, CSR start [ncells+1] and items [nitems]. */
+ * count, CSR start [ncells+1] and items [nitems] (within a cell in no
+ * particular order: no rule depends on it). */
 sft_status sft_source_grid(sft_source src, int32_t precision, int32_t n_out[3],
                            int64_t* ncells_out, int64_t* nitems_out,
                            int64_t* start_out, int32_t* items_out);
+/* Start element of the location walk in every cell of the source grid for
+ * `precision` (Sec. 4, step 4; Sec. 5.3 grid): first_out [ncells] host or
+ * device memory, the element of the cell's list deepest at the cell centre
+ * (largest min barycentric coordinate there, ties to the lowest id), -1 for an
+ * empty cell. SFT_ERR_ARG for a null source or output. */
+sft_status sft_source_cell_first(sft_source src, int32_t precision, int32_t* first_out);
 /* Face neighbours of the source mesh used by the location walk (Sec. 4,
  * step 4: localizing each sample in the source mesh): adj_out [nelems][dim+1]
  * host or device memory, adj_out[e][m] = the other element holding every

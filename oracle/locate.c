@@ -32,10 +32,11 @@
  *   - neighbour across the face of e opposite its local vertex m: the other
  *     element whose vertices include the face's vertices (the smallest id if
  *     several; none on the boundary);
- *   - when the walk gives up, the cell's list is scanned: the first
- *     accepting candidate in the cell's order wins; if none accepts, the
- *     candidate with the largest min(mu) wins (ties to the earlier one); an
- *     empty cell yields -1.
+ *   - when the walk gives up, every candidate of the cell is tested and the
+ *     one with the largest min(mu) wins (ties to the lowest id): an
+ *     accepting one whenever any accepts (status 0), else the nearest
+ *     (status 1); the result does not depend on the list's order. An empty
+ *     cell yields -1.
  * A point inside exactly one element (the usual case) gets that element
  * whatever the search; the rule only fixes which element wins where the
  * rounded predicate accepts several (points on shared faces).
@@ -265,7 +266,8 @@ static int cell_may_hold(const orc_grid* g, int32_t e, const double* c, const do
     }
 }
 
-/* scan candidates in the given order; returns status 0/1/2 */
+/* the candidate with the largest min(mu), ties to the lowest id; returns
+ * status 0 (it accepts), 1 (none accepts: the nearest) or 2 (no candidate) */
 static int scan_candidates(int prec, int dim, const double* coords, const int32_t* conn,
                            const int32_t* cand, int64_t ncand, const double* X, int32_t* elem)
 {
@@ -277,11 +279,10 @@ static int scan_candidates(int prec, int dim, const double* coords, const int32_
         predicate_mu(prec, dim, coords, conn, e, X, mu);
         double mn = mu[0];
         for (int m = 1; m <= dim; ++m) if (mu[m] < mn) mn = mu[m];
-        if (mn >= 0.0) { *elem = e; return 0; }
-        if (best < 0 || mn > best_score) { best = e; best_score = mn; }
+        if (best < 0 || mn > best_score || (mn == best_score && e < best)) { best = e; best_score = mn; }
     }
     *elem = best;
-    return best < 0 ? 2 : 1;
+    return best < 0 ? 2 : (best_score >= 0.0 ? 0 : 1);
 }
 
 static double* rounded_coords(int prec, int dim, int64_t nv, const double* coords)

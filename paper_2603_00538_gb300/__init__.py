@@ -107,6 +107,7 @@ _SIGS = {
     "sft_mass_solve": ([_vp, _i32, _vp, _vp, _i32, _d, _i32, _i32, _vp, _vp, _vp], _i32),
     "sft_source_grid": ([_vp, _i32, _vp, _vp, _vp, _vp, _vp], _i32),
     "sft_source_adjacency": ([_vp, _i32, _vp], _i32),
+    "sft_source_cell_first": ([_vp, _i32, _vp], _i32),
     "sft_target_set_wait_limit": ([_vp, ctypes.c_double], _i32),
     "sft_trim_memory": ([], _i32),
     "sft_batch_groups": ([_vp, _vp], _i32),
@@ -730,6 +731,14 @@ def sft_trim_memory() -> None:
 def sft_target_set_wait_limit(tgt: Target, seconds: float) -> None:
     """Limit of the device waits of the solves on this target (default 2 s)."""
     _check(lib().sft_target_set_wait_limit(tgt.h, float(seconds)), "sft_target_set_wait_limit")
+
+
+def sft_source_cell_first(src: Source, precision: int) -> np.ndarray:
+    """[ncells] int32 start element of the location walk per grid cell (-1: empty)."""
+    n, _, _ = sft_source_grid(src, precision)
+    out = np.zeros(int(np.prod(n)), np.int32)
+    _check(lib().sft_source_cell_first(src.h, int(precision), out.ctypes.data), "sft_source_cell_first")
+    return out
 
 
 def sft_source_adjacency(src: Source, precision: int) -> np.ndarray:

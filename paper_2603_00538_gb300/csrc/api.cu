@@ -86,6 +86,7 @@ static void free_locator(Locator& L, cudaStream_t st) {
   if (L.grid) cudaFreeAsync(L.grid, st);
   if (L.cell_start) cudaFreeAsync(L.cell_start, st);
   if (L.cell_items) cudaFreeAsync(L.cell_items, st);
+  if (L.cell_first) cudaFreeAsync(L.cell_first, st);
   if (L.recs) cudaFreeAsync(L.recs, st);
   if (L.vals) cudaFreeAsync(L.vals, st);
   if (L.coordsP) cudaFreeAsync(L.coordsP, st);
@@ -477,6 +478,20 @@ sft_status sft_source_grid(sft_source s, int32_t precision, int32_t n_out[3], in
     for (size_t i = 0; i < h.size(); ++i) start_out[i] = h[i];
   }
   if (items_out) SFT_CUDA(cudaMemcpyAsync(items_out, L.cell_items, sizeof(int32_t) * L.nitems, cudaMemcpyDeviceToHost, st));
+  SFT_CUDA(cudaStreamSynchronize(st));
+  return SFT_OK;
+}
+
+sft_status sft_source_cell_first(sft_source s, int32_t precision, int32_t* first_out) {
+  if (!s || !first_out) return fail(SFT_ERR_ARG, "null source or output");
+  if (precision != SFT_PREC_FP32 && precision != SFT_PREC_FP64) return fail(SFT_ERR_ARG, "bad precision");
+  cudaStream_t st = s->stream;
+  DevBuf<int32_t> d_err(st);
+  SFT_CUDA(d_err.alloc(1));
+  SFT_CUDA(cudaMemsetAsync(d_err.p, 0, sizeof(int32_t), st));
+  if (sft_status r = build_locator(s, precision, st, d_err.p)) return r;
+  const Locator& L = s->loc[precision];
+  SFT_CUDA(cudaMemcpyAsync(first_out, L.cell_first, sizeof(int32_t) * (size_t)L.ncells, cudaMemcpyDefault, st));
   SFT_CUDA(cudaStreamSynchronize(st));
   return SFT_OK;
 }

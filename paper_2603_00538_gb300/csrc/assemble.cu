@@ -73,9 +73,12 @@ __device__ __forceinline__ int adaptive_count(const P xv[D + 1][D], int N, doubl
 // (pmu, [d][N ne]) for later online transfers; kAsmCached takes element and
 // mu from those arrays instead of locating the sample (the samples' target
 // weights are regenerated from the same Philox counters).
-// Four resident blocks per SM in both dimensions (64 registers a thread). In
-// 3D that leaves 32 bytes of spill, yet the extra warps hide the longer
-// location chains: tet5m launch 4.165 -> 3.724 ms against three blocks.
+// Four resident blocks per SM (64 registers a thread) in both dimensions:
+// the kernel is bound by the latency of its dependent cache loads (cell ->
+// start element -> record -> neighbour -> record), and more resident warps
+// would hide more of it, but at five or six blocks the register cap spills
+// inside the walk. Measured on tri4m: 1.265 ms at four blocks, 1.406 at five;
+// tet5m 2.110 at four, 2.219 at five, 2.132 at six.
 // EXT: the kernel with importance sampling (p.imp) and per-element sample
 // counts (p.adapt); without it the kernel is the uniform / stratified one.
 template <int D, typename P, int NF, int MODE, bool EXT>
@@ -85,6 +88,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const P* __restrict__ tx, c
                                                   const GridP<P>* __restrict__ gp,
                                                   const int32_t* __restrict__ cell_start,
                                                   const int32_t* __restrict__ cell_items,
+                                                  const int32_t* __restrict__ cell_first,
                                                   const P* __restrict__ recs, const int32_t* __restrict__ adj,
                                                   const P* __restrict__ vals,
                                                   AsmParams p, double* __restrict__ b,
@@ -173,7 +177,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const P* __restrict__ tx, c
         } else {
           P X[D];
           map_point<D, P>(lam, xv, X);
-          e = locate_point<D, P>(gr, cell_start, cell_items, recs, adj, X, mu, status);
+          e = locate_point<D, P>(gr, cell_start, cell_items, cell_first, recs, adj, X, mu, status);
           if (MODE != kAsmPlain) sample_elem[idx] = e;
           if (MODE == kAsmRecord) {
 #pragma unroll
@@ -246,7 +250,7 @@ static void launch_t(sft_source_s* s, sft_target_s* t, const AssembleArgs& a, co
   if (blocks < 1) blocks = 1;
   auto args = [&](auto kern) {
     ::sft::note_launch(), kern<<<(unsigned)blocks, threads, 0, st>>>((const P*)t->coordsP[a.prec], t->conn, t->vol, t->vol32, (const P*)a.g,
-                                               (const GridP<P>*)L.grid, L.cell_start, L.cell_items,
+                                               (const GridP<P>*)L.grid, L.cell_start, L.cell_items, L.cell_first,
                                                (const P*)L.recs, L.adj, (const P*)L.vals, p, a.b, a.sample_elem,
                                                (P*)a.pmu, a.counters);
   };

@@ -37,6 +37,7 @@ struct BReq {
   const GridP<float>* grid;
   const int32_t* cell_start;
   const int32_t* cell_items;
+  const int32_t* cell_first;
   const float* recs;
   const int32_t* adj;
   const float* vals;
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_control(const BReq* __r
     for (int a = 0; a < D; ++a) X[a] = R.tx[i * D + a];
     float mu[D + 1];
     int status;
-    const int32_t e = locate_point<D, float>(gr, R.cell_start, R.cell_items, R.recs, R.adj, X, mu, status);
+    const int32_t e = locate_point<D, float>(gr, R.cell_start, R.cell_items, R.cell_first, R.recs, R.adj, X, mu, status);
     n_fb += status == 1;
     n_em += status == 2;
     for (int f = 0; f < R.nf; ++f) R.g[(int64_t)f * R.nv + i] = e >= 0 ? eval_p1<D, float>(R.vals, R.nes, f, e, mu) : 0.f;
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(kBatchThreads, NF <= 2 ? 4 : (NF <= 4 ? 3 : 2)
           map_point<D, float>(lam, xv, X);
           float mu[K];
           int status;
-          const int32_t e = locate_point<D, float>(gr, R.cell_start, R.cell_items, R.recs, R.adj, X, mu, status);
+          const int32_t e = locate_point<D, float>(gr, R.cell_start, R.cell_items, R.cell_first, R.recs, R.adj, X, mu, status);
           n_fb += status == 1;
           n_em += status == 2;
 #pragma unroll
@@ -1153,6 +1154,7 @@ static sft_status build_batch(sft_batch_s* B, const sft_options* opts, int autot
     R.grid = (const GridP<float>*)L.grid;
     R.cell_start = L.cell_start;
     R.cell_items = L.cell_items;
+    R.cell_first = L.cell_first;
     R.recs = (const float*)L.recs;
     R.adj = L.adj;
     R.vals = (const float*)L.vals;

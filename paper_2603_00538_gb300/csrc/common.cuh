@@ -420,52 +420,26 @@ __device__ __forceinline__ void load_record(const P* __restrict__ recs, int32_t 
 // predicate evaluations of the walk before the cell's list is scanned
 constexpr int kWalkSteps = 12;
 
-// Locate X. A walk through face neighbours starts at the first element of
-// X's cell (the one deepest at the cell centre): at element e the predicate's
-// mu is evaluated; all mu >= 0 accepts e, otherwise the walk moves to the
-// element across the face opposite the vertex with the smallest mu (the
-// first on ties: the face X lies farthest outside of). adj[e][m] is that
-// neighbour, -1 on the boundary. The walk gives up at a boundary face or
-// after kWalkSteps evaluations; the cell's list is then scanned in order
-// (decreasing depth of the cell centre, ties ascending id): the first
-// accepting candidate wins, if none accepts the candidate with the largest
-// min(mu) (the earlier one on ties), -1 for an empty cell.
-// status: 0 accepted, 1 nearest candidate, 2 empty cell. mu is the returned
-// element's barycentric vector. A point inside one element gets that element
-// whichever way it is found; the order of the search decides only between
-// elements that all accept a point on their shared face.
+// The fallback of the location below: every candidate of cell c is tested
+// at X = (x0, x1, x2) and the one with the largest min(mu) wins, ties to the
+// lowest id (an accepting one whenever any accepts, else the nearest); -1 for
+// an empty list. Kept out of line and fed by value: the walk almost always
+// succeeds, and inlining this loop into the callers raised their register
+// pressure (more spills in the assembly kernel) for a path a few queries in a
+// thousand take.
+template <typename P>
+struct ScanHit {
+  int32_t e;
+  int status;
+  P mu[4];
+};
+
 template <int D, typename P>
-__device__ __forceinline__ int32_t locate_point(const GridP<P>& g, const int32_t* __restrict__ cell_start,
-                                                const int32_t* __restrict__ cell_items,
-                                                const P* __restrict__ recs, const int32_t* __restrict__ adj,
-                                                const P X[D], P mu[D + 1], int& status) {
+__device__ __noinline__ ScanHit<P> scan_cell(int32_t c, P x0, P x1, P x2, const int32_t* __restrict__ cell_start,
+                                             const int32_t* __restrict__ cell_items, const P* __restrict__ recs) {
   constexpr int L = RecLen<D>::value;
-  const int32_t c = cell_of<D, P>(g, X);
+  const P X[3] = {x0, x1, x2};
   const int32_t p0 = __ldg(cell_start + c), p1 = __ldg(cell_start + c + 1);
-  if (p0 < p1) {
-    int32_t e = __ldg(cell_items + p0);
-    for (int s = 0; s < kWalkSteps; ++s) {
-      P r[L];
-      load_record<D, P>(recs, e, r);
-      P m[D + 1];
-      bary_from_record<D, P>(r, X, m);
-      P mn = m[0];
-      int am = 0;
-#pragma unroll
-      for (int q = 1; q <= D; ++q)
-        if (m[q] < mn) { mn = m[q]; am = q; }
-      if (mn >= P(0)) {
-#pragma unroll
-        for (int q = 0; q <= D; ++q) mu[q] = m[q];
-        status = 0;
-        return e;
-      }
-      const int32_t nx = __ldg(adj + (int64_t)e * (D + 1) + am);
-      if (nx < 0) break;
-      e = nx;
-    }
-  }
-  // the walk gave up (boundary or step limit): the cell's list in order
   int32_t best = -1;
   P best_score = P(0);
   for (int32_t p = p0; p < p1; ++p) {
@@ -477,25 +451,76 @@ __device__ __forceinline__ int32_t locate_point(const GridP<P>& g, const int32_t
     P mn = m[0];
 #pragma unroll
     for (int q = 1; q <= D; ++q) mn = m[q] < mn ? m[q] : mn;
+    if (best < 0 || mn > best_score || (mn == best_score && e < best)) { best = e; best_score = mn; }
+  }
+  ScanHit<P> h;
+  h.e = best;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) h.mu[q] = P(0);
+  if (best < 0) {  // an empty list (cell_first is -1 there; kept safe)
+    h.status = 2;
+    return h;
+  }
+  h.status = best_score >= P(0) ? 0 : 1;
+  P r[L];
+  load_record<D, P>(recs, best, r);
+  bary_from_record<D, P>(r, X, h.mu);
+  return h;
+}
+
+// Locate X. A walk through face neighbours starts at the element deepest at
+// the centre of X's cell (cell_first, ties to the lowest id): at element e
+// the predicate's mu is evaluated; all mu >= 0 accepts e, otherwise the walk
+// moves to the element across the face opposite the vertex with the smallest
+// mu (the first on ties: the face X lies farthest outside of). adj[e][m] is
+// that neighbour, -1 on the boundary. The walk gives up at a boundary face or
+// after kWalkSteps evaluations and hands over to scan_cell. No rule depends on
+// the order of the cell's list.
+// status: 0 accepted, 1 nearest candidate, 2 empty cell. mu is the returned
+// element's barycentric vector. A point inside one element gets that element
+// whichever way it is found; the walk decides only between elements that all
+// accept a point on their shared face.
+template <int D, typename P>
+__device__ __forceinline__ int32_t locate_point(const GridP<P>& g, const int32_t* __restrict__ cell_start,
+                                                const int32_t* __restrict__ cell_items,
+                                                const int32_t* __restrict__ cell_first,
+                                                const P* __restrict__ recs, const int32_t* __restrict__ adj,
+                                                const P X[D], P mu[D + 1], int& status) {
+  constexpr int L = RecLen<D>::value;
+  const int32_t c = cell_of<D, P>(g, X);
+  int32_t e = __ldg(cell_first + c);
+  if (e < 0) {  // an empty cell
+    status = 2;
+#pragma unroll
+    for (int q = 0; q <= D; ++q) mu[q] = P(0);
+    return -1;
+  }
+  for (int s = 0; s < kWalkSteps; ++s) {
+    P r[L];
+    load_record<D, P>(recs, e, r);
+    P m[D + 1];
+    bary_from_record<D, P>(r, X, m);
+    P mn = m[0];
+    int am = 0;
+#pragma unroll
+    for (int q = 1; q <= D; ++q)
+      if (m[q] < mn) { mn = m[q]; am = q; }
     if (mn >= P(0)) {
 #pragma unroll
       for (int q = 0; q <= D; ++q) mu[q] = m[q];
       status = 0;
       return e;
     }
-    if (best < 0 || mn > best_score) { best = e; best_score = mn; }
+    const int32_t nx = __ldg(adj + (int64_t)e * (D + 1) + am);
+    if (nx < 0) break;
+    e = nx;
   }
-  if (best < 0) {
-    status = 2;
+  // the walk gave up (boundary or step limit)
+  const ScanHit<P> h = scan_cell<D, P>(c, X[0], X[1], D == 3 ? X[D - 1] : P(0), cell_start, cell_items, recs);
+  status = h.status;
 #pragma unroll
-    for (int q = 0; q <= D; ++q) mu[q] = P(0);
-    return -1;
-  }
-  status = 1;
-  P r[L];
-  load_record<D, P>(recs, best, r);
-  bary_from_record<D, P>(r, X, mu);
-  return best;
+  for (int q = 0; q <= D; ++q) mu[q] = h.mu[q];
+  return h.e;
 }
 
 // P1 value of field f in element e from the per-element copy of its nodal

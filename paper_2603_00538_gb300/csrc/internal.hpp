@@ -78,7 +78,8 @@ struct Locator {
   int64_t ncells = 0, nitems = 0;
   void* grid = nullptr;          // device GridP<P>
   int32_t* cell_start = nullptr;  // [ncells + 1]
-  int32_t* cell_items = nullptr;  // [nitems]
+  int32_t* cell_items = nullptr;  // [nitems] (in no particular order within a cell)
+  int32_t* cell_first = nullptr;  // [ncells] start element of the location walk, -1: empty cell
   void* recs = nullptr;           // [ne][RecLen] P
   void* vals = nullptr;           // [nf][ne][4] P
   void* coordsP = nullptr;        // [nv][dim] P

@@ -65,8 +65,8 @@ template <bool L2>
 __global__ void __launch_bounds__(kMiThreads) k_mi_2d(
     const double* __restrict__ sx, const int32_t* __restrict__ sconn, const int32_t* __restrict__ adj,
     const double* __restrict__ svals, int64_t nes, int field, const GridP<double>* __restrict__ gp,
-    const int32_t* __restrict__ cell_start, const int32_t* __restrict__ cell_items, const double* __restrict__ recs,
-    const double* __restrict__ tx, const int32_t* __restrict__ tconn, int64_t net, const double* __restrict__ u,
+    const int32_t* __restrict__ cell_start, const int32_t* __restrict__ cell_items,
+    const int32_t* __restrict__ cell_first, const double* __restrict__ recs, const double* __restrict__ tx, const int32_t* __restrict__ tconn, int64_t net, const double* __restrict__ u,
     double* __restrict__ b, double* __restrict__ part, int32_t* err) {
   const GridP<double> g = *gp;
   double e2 = 0.0, n2 = 0.0;
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kMiThreads) k_mi_2d(
                    __ddiv_rn(__dadd_rn(__dadd_rn(tv[0].y, tv[1].y), tv[2].y), 3.0)};
     double mu0[3];
     int status = 0;
-    const int32_t s0 = locate_point<2, double>(g, cell_start, cell_items, recs, adj, c, mu0, status);
+    const int32_t s0 = locate_point<2, double>(g, cell_start, cell_items, cell_first, recs, adj, c, mu0, status);
     if (s0 < 0) {
       set_error(err, DEV_BAD_INDEX);
       continue;
@@ -210,7 +210,7 @@ sft_status mesh_intersection_2d(sft_source_s* s, sft_target_s* t, int field, con
   auto launch = [&](auto kern) {
     ::sft::note_launch(), kern<<<blocks, kMiThreads, 0, st>>>(
         (const double*)L.coordsP, s->conn, L.adj, (const double*)L.vals, s->ne, field, (const GridP<double>*)L.grid,
-        L.cell_start, L.cell_items, (const double*)L.recs, (const double*)t->coordsP[SFT_PREC_FP64], t->conn,
+        L.cell_start, L.cell_items, L.cell_first, (const double*)L.recs, (const double*)t->coordsP[SFT_PREC_FP64], t->conn,
         t->ne, u, b, part.p, d_err.p);
   };
   if (l2) launch(k_mi_2d<true>);

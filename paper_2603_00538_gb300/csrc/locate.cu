@@ -7,10 +7,11 @@
 // Layout in HBM per precision P:
 //   recs  [ne][8 | 12] P  : first vertex + inverse affine map (16-B aligned rows)
 //   vals  [nf][ne][4]  P  : per-element copy of the nodal values (one 16/32-B load)
-//   cell_start [ncells+1], cell_items [nitems] int32: elements of each cell,
-//   ordered by decreasing depth of the cell centre in them (min barycentric
-//   coordinate), ties by ascending id: the element holding most of the cell
-//   is scanned first, and the first accepting candidate in this order wins.
+//   cell_start [ncells+1], cell_items [nitems] int32: elements of each cell
+//   (in no particular order); cell_first [ncells] int32: the element deepest
+//   at the cell centre (largest min barycentric coordinate there, ties to the
+//   lowest id), where the location walk starts; -1 for an empty cell;
+//   adj [ne][d+1] int32: face neighbours (one array per source).
 #include <cmath>
 #include <vector>
 #include "internal.hpp"
@@ -342,10 +343,18 @@ template <> struct alignas(16) RegEntry<double> { int32_t id; int32_t pad; doubl
 // fill the element id and the depth of the cell centre in the
 // element (its min barycentric coordinate there, evaluated exactly as a
 // query at that point would be), which orders the cell's list
+// The count pass records which cells of the element's bounding box passed
+// the test as a bit mask (bit k: the k-th box cell in x-fastest order) when
+// the box has at most kMaskCells cells; the fill pass then registers exactly
+// those without testing again. Larger boxes (bit 31 set) are tested again.
+constexpr int kMaskCells = 31;
+constexpr uint32_t kMaskRetest = 0x80000000u;
+
 template <int D, typename P, bool FILL>
 __global__ void k_register(const P* __restrict__ x, const int32_t* __restrict__ conn, const P* __restrict__ recs,
                            int64_t nv, int64_t ne, const GridP<P>* __restrict__ gp, int32_t* __restrict__ cell_count,
-                           const int32_t* __restrict__ cell_start, RegEntry<P>* __restrict__ reg) {
+                           const int32_t* __restrict__ cell_start, RegEntry<P>* __restrict__ reg,
+                           uint32_t* __restrict__ mask) {
   constexpr int RL = RecLen<D>::value;
   const GridP<P> g = *gp;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
@@ -359,20 +368,30 @@ __global__ void k_register(const P* __restrict__ x, const int32_t* __restrict__ 
     P xv[D + 1][D];
     elem_vertices<D, P>(x, conn, e, xv);
     int32_t c0[3], c1[3];
-    elem_cell_range<D, P>(g, xv, c0, c1);
+    const int64_t nbox = elem_cell_range<D, P>(g, xv, c0, c1);
     P r[RL];
     load_record<D, P>(recs, (int32_t)e, r);
     P w[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) w[a] = Ar<P>::mul(g.h[a], P(0.5));
+    const bool use_mask = nbox <= kMaskCells;
+    const uint32_t have = FILL ? __ldg(mask + e) : 0u;
+    const bool retest = !FILL || (have & kMaskRetest) != 0u;
+    uint32_t bits = 0u;
+    int k = 0;
     for (int32_t iz = c0[2]; iz <= c1[2]; ++iz)
       for (int32_t iy = c0[1]; iy <= c1[1]; ++iy)
-        for (int32_t ix = c0[0]; ix <= c1[0]; ++ix) {
+        for (int32_t ix = c0[0]; ix <= c1[0]; ++ix, ++k) {
           const int32_t idx[3] = {ix, iy, iz};
           P cc[D];
 #pragma unroll
           for (int a = 0; a < D; ++a) cc[a] = cell_centre<P>(g, a, idx[a]);
-          if (!cell_may_hold<D, P>(r, cc, w)) continue;
+          if (retest) {
+            if (!cell_may_hold<D, P>(r, cc, w)) continue;
+          } else if (!((have >> k) & 1u)) {
+            continue;
+          }
+          if (!FILL && use_mask) bits |= 1u << k;
           const int64_t c = ((int64_t)iz * g.n[1] + iy) * g.n[0] + ix;
           const int32_t pos = atomicAdd(cell_count + c, 1);
           if (FILL) {
@@ -388,63 +407,32 @@ __global__ void k_register(const P* __restrict__ x, const int32_t* __restrict__ 
             reg[(int64_t)cell_start[c] + pos] = en;
           }
         }
+    if (!FILL) mask[e] = use_mask ? bits : kMaskRetest;
   }
 }
 
-// Order of each cell's list (the atomic fill leaves it arbitrary): decreasing
-// depth of the cell centre in the element, ties by ascending element id. A
-// group of W lanes takes one cell at a time; a cell of up to W entries is
-// ranked in registers (each lane holds one entry and compares it with the
-// others by shuffles), a longer one entry by entry from memory. Each entry is
-// scattered to its rank. W = 8 suits the sparse cells of 2D grids (a few
-// entries), W = 16 the denser ones of 3D grids (measured on the 4,983,504-tet
-// source: source build 3.04 ms against 3.11 with W = 32; W = 4 in 2D: no change).
-template <typename P, int W>
-__global__ void k_cell_rank(const int32_t* __restrict__ cell_start, const RegEntry<P>* __restrict__ reg,
-                            int64_t ncells, int32_t* __restrict__ out) {
-  const int lane = threadIdx.x & (W - 1);
-  const int64_t grp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / W;
-  const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / W;
-  // groups of a warp loop the same number of times (ncells is rounded up per
-  // warp) so that the shuffles below always see all 32 lanes
-  const int64_t per_warp = 32 / W;
-  const int64_t ncells_r = (ncells + per_warp - 1) / per_warp * per_warp;
-  for (int64_t c = grp0; c < ncells_r; c += ngrp) {
-    const bool real = c < ncells;
-    const int32_t p0 = real ? __ldg(cell_start + c) : 0, p1 = real ? __ldg(cell_start + c + 1) : 0;
-    const int32_t n = p1 - p0;
-    const bool small = n <= W;
-    P d = P(0);
-    int32_t id = 0;
-    if (small && lane < n) {
-      const RegEntry<P> en = reg[p0 + lane];
-      d = en.depth;
-      id = en.id;
-    }
-    int32_t rank = 0;
-    // every lane of the warp takes part in every shuffle: loop to the largest
-    // register-ranked cell among the warp's groups
-    const int kmax = (int)__reduce_max_sync(0xffffffffu, small ? (unsigned)n : 0u);
-    for (int k = 0; k < kmax; ++k) {
-      const P dk = __shfl_sync(0xffffffffu, d, k, W);
-      const int32_t ik = __shfl_sync(0xffffffffu, id, k, W);
-      if (k < n) rank += (dk > d) || (dk == d && ik < id);
-    }
-    if (small) {
-      if (lane < n) out[p0 + rank] = id;
-    } else {
-      for (int32_t p = p0 + lane; p < p1; p += W) {
-        const RegEntry<P> ep = reg[p];
-        const P dp = ep.depth;
-        const int32_t ip = ep.id;
-        int32_t rk = 0;
-        for (int32_t q = p0; q < p1; ++q) {
-          const RegEntry<P> eq = reg[q];
-          rk += (eq.depth > dp) || (eq.depth == dp && eq.id < ip);
-        }
-        out[p0 + rk] = ip;
+// Start element of each cell and its list of ids: the fill leaves a cell's
+// entries in arbitrary order, which no rule depends on (the walk starts at
+// the element deepest at the cell centre, ties to the lowest id; the
+// fallback takes the best-scoring candidate whatever the order). One thread
+// per cell: the argmax of (depth, -id) over its entries, and the ids copied
+// into the cell's list.
+template <typename P>
+__global__ void k_cell_first(const int32_t* __restrict__ cell_start, const RegEntry<P>* __restrict__ reg,
+                             int64_t ncells, int32_t* __restrict__ items, int32_t* __restrict__ first) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t p0 = __ldg(cell_start + c), p1 = __ldg(cell_start + c + 1);
+    int32_t best = -1;
+    P bd = P(0);
+    for (int32_t p = p0; p < p1; ++p) {
+      const RegEntry<P> en = reg[p];
+      if (best < 0 || en.depth > bd || (en.depth == bd && en.id < best)) {
+        best = en.id;
+        bd = en.depth;
       }
+      items[p] = en.id;
     }
+    first[c] = best;
   }
 }
 
@@ -455,14 +443,17 @@ __global__ void k_cell_rank(const int32_t* __restrict__ cell_start, const RegEnt
 // every cell a point of the element can fall in, so it is listed in the cell
 // of v. Faces m != 0 hold vertex 0 and are matched against the list of
 // cell(x_0); face 0 holds vertex 1 and is matched against the list of
-// cell(x_1). One thread per element.
+// cell(x_1). Two threads per element, one per list (they write different
+// entries of the element's row).
 template <int D, typename P>
 __global__ void k_adjacency(const P* __restrict__ x, const int32_t* __restrict__ conn, int64_t nv, int64_t ne,
                             const GridP<P>* __restrict__ gp, const int32_t* __restrict__ cell_start,
                             const int32_t* __restrict__ cell_items, int32_t* __restrict__ adj) {
   constexpr int K = D + 1;
   const GridP<P> g = *gp;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < 2 * ne; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i >> 1;
+    const int pass = (int)(i & 1);
     int32_t v[K];
     bool ok = true;
 #pragma unroll
@@ -474,37 +465,38 @@ __global__ void k_adjacency(const P* __restrict__ x, const int32_t* __restrict__
 #pragma unroll
     for (int m = 0; m < K; ++m) best[m] = INT32_MAX;
     if (ok) {
+      P X[D];
+      const int32_t vp = pass == 0 ? v[0] : v[1];
 #pragma unroll
-      for (int pass = 0; pass < 2; ++pass) {
-        P X[D];
+      for (int a = 0; a < D; ++a) X[a] = __ldg(x + (int64_t)vp * D + a);
+      const int32_t c = cell_of<D, P>(g, X);
+      const int32_t p1 = __ldg(cell_start + c + 1);
+#pragma unroll 2
+      for (int32_t p = __ldg(cell_start + c); p < p1; ++p) {
+        const int32_t e2 = __ldg(cell_items + p);
+        if (e2 == (int32_t)e) continue;
+        int32_t w[K];
 #pragma unroll
-        for (int a = 0; a < D; ++a) X[a] = __ldg(x + (int64_t)v[pass] * D + a);
-        const int32_t c = cell_of<D, P>(g, X);
-        const int32_t p1 = __ldg(cell_start + c + 1);
-        for (int32_t p = __ldg(cell_start + c); p < p1; ++p) {
-          const int32_t e2 = __ldg(cell_items + p);
-          if (e2 == (int32_t)e) continue;
-          int32_t w[K];
+        for (int r = 0; r < K; ++r) w[r] = __ldg(conn + (int64_t)e2 * K + r);
+        int shared = 0, miss = 0;
 #pragma unroll
-          for (int r = 0; r < K; ++r) w[r] = __ldg(conn + (int64_t)e2 * K + r);
-          int shared = 0, miss = 0;
+        for (int m = 0; m < K; ++m) {
+          bool in = false;
 #pragma unroll
-          for (int m = 0; m < K; ++m) {
-            bool in = false;
-#pragma unroll
-            for (int r = 0; r < K; ++r) in = in || w[r] == v[m];
-            shared += in;
-            miss = in ? miss : m;
-          }
-          if (shared != D || (pass == 0) == (miss == 0)) continue;
-#pragma unroll
-          for (int m = 0; m < K; ++m)
-            if (m == miss && e2 < best[m]) best[m] = e2;
+          for (int r = 0; r < K; ++r) in = in || w[r] == v[m];
+          shared += in;
+          miss = in ? miss : m;
         }
+        if (shared != D || (pass == 0) == (miss == 0)) continue;
+#pragma unroll
+        for (int m = 0; m < K; ++m)
+          if (m == miss && e2 < best[m]) best[m] = e2;
       }
     }
+    // pass 0 owns faces 1..D, pass 1 face 0
 #pragma unroll
-    for (int m = 0; m < K; ++m) adj[e * K + m] = best[m] == INT32_MAX ? -1 : best[m];
+    for (int m = 0; m < K; ++m)
+      if ((m == 0) == (pass == 1)) adj[e * K + m] = best[m] == INT32_MAX ? -1 : best[m];
   }
 }
 
@@ -562,52 +554,46 @@ static sft_status build_locator_t(sft_source_s* s, int prec, cudaStream_t st, in
                                                             s->nf, recs, vals, d_err, evol);
   SFT_CUDA(cudaGetLastError());
   // count registrations per cell, then total (int64) -> int32 offsets must suffice
-  int32_t* cell_count = nullptr;
-  int64_t* start64 = nullptr;
-  SFT_CUDA(dalloc(&cell_count, (size_t)L.ncells, st));
-  SFT_CUDA(dalloc(&start64, (size_t)L.ncells + 1, st));
-  SFT_CUDA(cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * L.ncells, st));
-  ::sft::note_launch(), k_register<D, P, false><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, recs, s->nv, s->ne, g, cell_count,
-                                                                               nullptr, nullptr);
+  // (temporaries freed in stream order on every return)
+  DevBuf<int32_t> cell_count(st);
+  DevBuf<int64_t> start64(st);
+  DevBuf<uint32_t> mask(st);
+  DevBuf<RegEntry<P>> reg(st);
+  SFT_CUDA(cell_count.alloc((size_t)L.ncells));
+  SFT_CUDA(start64.alloc((size_t)L.ncells + 1));
+  SFT_CUDA(mask.alloc((size_t)s->ne));
+  SFT_CUDA(cudaMemsetAsync(cell_count.p, 0, sizeof(int32_t) * L.ncells, st));
+  ::sft::note_launch(), k_register<D, P, false><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, recs, s->nv, s->ne, g,
+                                                                               cell_count.p, nullptr, nullptr, mask.p);
   SFT_CUDA(cudaGetLastError());
-  SFT_CUDA(exclusive_scan_i32_to_i64(cell_count, start64, L.ncells, st));
+  SFT_CUDA(exclusive_scan_i32_to_i64(cell_count.p, start64.p, L.ncells, st));
   int32_t herr = 0;
   int64_t total = 0;
   SFT_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  SFT_CUDA(cudaMemcpyAsync(&total, start64 + L.ncells, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  SFT_CUDA(cudaMemcpyAsync(&total, start64.p + L.ncells, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   SFT_CUDA(cudaStreamSynchronize(st));
-  if (herr != 0) {
-    dfree(cell_count, st);
-    dfree(start64, st);
+  if (herr != 0)
     return fail(SFT_ERR_MESH, herr == DEV_BAD_INDEX ? "source connectivity index out of range"
                                                     : "source mesh has a non-positive element or a degenerate box");
-  }
   if (total >= (int64_t)INT32_MAX) return fail(SFT_ERR_UNSUPPORTED, "grid registrations exceed 2^31");
   L.nitems = total;
   SFT_CUDA(dalloc(&L.cell_start, (size_t)L.ncells + 1, st));
-  SFT_CUDA(narrow_i64_to_i32(start64, L.cell_start, L.ncells + 1, st));
-  dfree(start64, st);
-  // fill (arbitrary order within a cell), then order each cell
-  RegEntry<P>* reg = nullptr;
-  SFT_CUDA(dalloc(&reg, (size_t)total, st));
+  SFT_CUDA(narrow_i64_to_i32(start64.p, L.cell_start, L.ncells + 1, st));
+  // fill (arbitrary order within a cell), then each cell's start element
+  SFT_CUDA(reg.alloc((size_t)total));
   SFT_CUDA(dalloc(&L.cell_items, (size_t)total, st));
-  SFT_CUDA(cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * L.ncells, st));
-  ::sft::note_launch(), k_register<D, P, true><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, recs, s->nv, s->ne, g, cell_count,
-                                                                              L.cell_start, reg);
+  SFT_CUDA(cudaMemsetAsync(cell_count.p, 0, sizeof(int32_t) * L.ncells, st));
+  ::sft::note_launch(), k_register<D, P, true><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, recs, s->nv, s->ne, g,
+                                                                              cell_count.p, L.cell_start, reg.p, mask.p);
   SFT_CUDA(cudaGetLastError());
-  if (D == 3)  // measured: 16 lanes per cell in 3D, 8 in 2D
-    ::sft::note_launch(), k_cell_rank<P, 16><<<grid_for(L.ncells * 16), 256, 0, st>>>(L.cell_start, reg, L.ncells,
-                                                                                     L.cell_items);
-  else
-    ::sft::note_launch(), k_cell_rank<P, 8><<<grid_for(L.ncells * 8), 256, 0, st>>>(L.cell_start, reg, L.ncells,
-                                                                                   L.cell_items);
+  SFT_CUDA(dalloc(&L.cell_first, (size_t)L.ncells, st));
+  ::sft::note_launch(), k_cell_first<P><<<grid_for(L.ncells), 256, 0, st>>>(L.cell_start, reg.p, L.ncells, L.cell_items,
+                                                                           L.cell_first);
   SFT_CUDA(cudaGetLastError());
-  dfree(cell_count, st);
-  dfree(reg, st);
   // face neighbours for the location walk (one array per source mesh)
   if (!s->adj) {
     SFT_CUDA(dalloc(&s->adj, (size_t)s->ne * (D + 1), st));
-    ::sft::note_launch(), k_adjacency<D, P><<<grid_for(s->ne), 256, 0, st>>>(xP, s->conn, s->nv, s->ne, g, L.cell_start,
+    ::sft::note_launch(), k_adjacency<D, P><<<grid_for(2 * s->ne), 256, 0, st>>>(xP, s->conn, s->nv, s->ne, g, L.cell_start,
                                                                            L.cell_items, s->adj);
     SFT_CUDA(cudaGetLastError());
   }
@@ -666,6 +652,7 @@ __global__ void __launch_bounds__(256) k_locate_points(const TIn* __restrict__ p
                                                        const GridP<P>* __restrict__ gp,
                                                        const int32_t* __restrict__ cell_start,
                                                        const int32_t* __restrict__ cell_items,
+                                                       const int32_t* __restrict__ cell_first,
                                                        const P* __restrict__ recs, const int32_t* __restrict__ adj,
                                                        const P* __restrict__ vals,
                                                        int64_t ne, int nf, int32_t* __restrict__ elem_out,
@@ -682,7 +669,7 @@ __global__ void __launch_bounds__(256) k_locate_points(const TIn* __restrict__ p
     }
     P mu[D + 1];
     int status;
-    const int32_t e = locate_point<D, P>(g, cell_start, cell_items, recs, adj, X, mu, status);
+    const int32_t e = locate_point<D, P>(g, cell_start, cell_items, cell_first, recs, adj, X, mu, status);
     n_fallback += status == 1;
     n_empty += status == 2;
     if (elem_out) elem_out[i] = e;
@@ -714,6 +701,7 @@ static void launch_locate(sft_source_s* s, const Locator& L, int64_t n, const vo
   const P* vals = (const P*)L.vals;
 #define SFT_LOC(TIN, TOUT)                                                                                      \
   ::sft::note_launch(), k_locate_points<D, P, TIN, TOUT><<<blocks, 256, 0, st>>>((const TIN*)pts, n, g, L.cell_start, L.cell_items, \
+                                                           L.cell_first,                                    \
                                                            recs, L.adj, vals, s->ne, nf, elem_out,          \
                                                            (TOUT*)val_out,                                   \
                                                            val_stride, counters, (P*)mu_out)

@@ -54,7 +54,8 @@ constexpr uint32_t kSmemSur = kSmemFwd + kSmemPieces;
 
 template <int DS>
 __device__ __forceinline__ float exact_value(const GridP<float>& gr, const int32_t* __restrict__ cell_start,
-                                             const int32_t* __restrict__ cell_items, const float* __restrict__ recs,
+                                             const int32_t* __restrict__ cell_items,
+                                             const int32_t* __restrict__ cell_first, const float* __restrict__ recs,
                                              const int32_t* __restrict__ adj,
                                              const float* __restrict__ vals, int64_t nes, int field, const float* X,
                                              int& n_empty, int cost = 0) {
@@ -63,7 +64,7 @@ __device__ __forceinline__ float exact_value(const GridP<float>& gr, const int32
   for (int a = 0; a < DS; ++a) Xs[a] = X[a];
   float mu[DS + 1];
   int status;
-  const int32_t e = locate_point<DS, float>(gr, cell_start, cell_items, recs, adj, Xs, mu, status);
+  const int32_t e = locate_point<DS, float>(gr, cell_start, cell_items, cell_first, recs, adj, Xs, mu, status);
   n_empty += status == 2;
   float v = e >= 0 ? eval_p1<DS, float>(vals, nes, field, e, mu) : 0.f;
   if (cost > 0) {
@@ -83,7 +84,8 @@ __global__ void __launch_bounds__(NET ? kTPR * kTileM : kTileM, NET ? 2 : 8) k_s
     const float* __restrict__ P, const unsigned char* __restrict__ W2, const unsigned char* __restrict__ W3,
     const unsigned char* __restrict__ W4, const float* __restrict__ tx, const int32_t* __restrict__ tconn,
     const float* __restrict__ vol32, const float* __restrict__ g, const GridP<float>* __restrict__ gp,
-    const int32_t* __restrict__ cell_start, const int32_t* __restrict__ cell_items, const float* __restrict__ recs,
+    const int32_t* __restrict__ cell_start, const int32_t* __restrict__ cell_items,
+    const int32_t* __restrict__ cell_first, const float* __restrict__ recs,
     const int32_t* __restrict__ adj, const float* __restrict__ vals, SurParams p, double* __restrict__ b, int32_t* __restrict__ fb_out,
     float* __restrict__ sample_f, int64_t* __restrict__ counters, int32_t* err) {
   constexpr int K = DT + 1;
@@ -156,7 +158,7 @@ __global__ void __launch_bounds__(NET ? kTPR * kTileM : kTileM, NET ? 2 : 8) k_s
         if (!NET && p.sub_f && j < p.s) {
           fe = __ldg(p.sub_f + t * p.s + j);
         } else {
-          fe = exact_value<DS>(gr, cell_start, cell_items, recs, adj, vals, p.nes, p.exact_field, X, n_empty,
+          fe = exact_value<DS>(gr, cell_start, cell_items, cell_first, recs, adj, vals, p.nes, p.exact_field, X, n_empty,
                                p.exact_cost);
           ++n_exact;
         }
@@ -171,7 +173,7 @@ __global__ void __launch_bounds__(NET ? kTPR * kTileM : kTileM, NET ? 2 : 8) k_s
         __syncthreads();
         const bool fb = s_flag[el] != 0;
         if (fb && lead && valid && !sub) {
-          fe = exact_value<DS>(gr, cell_start, cell_items, recs, adj, vals, p.nes, p.exact_field, X, n_empty, p.exact_cost);
+          fe = exact_value<DS>(gr, cell_start, cell_items, cell_first, recs, adj, vals, p.nes, p.exact_field, X, n_empty, p.exact_cost);
           ++n_exact;
         }
         f = fb ? fe : y;
@@ -294,6 +296,7 @@ template <int DT, int DS>
 __global__ void k_sub_points(const float* __restrict__ tx, const int32_t* __restrict__ tconn, int64_t ne, int s,
                              PhiloxKey key, uint32_t stream_id, Strat st, const GridP<float>* __restrict__ gp,
                              const int32_t* __restrict__ cell_start, const int32_t* __restrict__ cell_items,
+                             const int32_t* __restrict__ cell_first,
                              const float* __restrict__ recs, const int32_t* __restrict__ adj,
                              const float* __restrict__ vals, int64_t nes, int field, int cost,
                              float* __restrict__ pts3, float* __restrict__ fe, int64_t* __restrict__ counters) {
@@ -316,7 +319,7 @@ __global__ void k_sub_points(const float* __restrict__ tx, const int32_t* __rest
     pts3[i * 3] = X[0];
     pts3[i * 3 + 1] = X[1];
     pts3[i * 3 + 2] = DT == 3 ? X[DT - 1] : 0.f;
-    fe[i] = exact_value<DS>(gr, cell_start, cell_items, recs, adj, vals, nes, field, X, n_empty, cost);
+    fe[i] = exact_value<DS>(gr, cell_start, cell_items, cell_first, recs, adj, vals, nes, field, X, n_empty, cost);
     ++n_exact;
   }
   const int e1 = warp_sum<int>(n_exact), m1 = warp_sum<int>(n_empty);
@@ -358,6 +361,7 @@ __global__ void k_pad3(const float* __restrict__ x, int64_t nv, int d, float* __
 template <int DS>
 __global__ void k_exact_nodes(const float* __restrict__ x, int64_t nv, int d, const GridP<float>* __restrict__ gp,
                               const int32_t* __restrict__ cell_start, const int32_t* __restrict__ cell_items,
+                              const int32_t* __restrict__ cell_first,
                               const float* __restrict__ recs, const int32_t* __restrict__ adj,
                               const float* __restrict__ vals, int64_t nes, int field, int cost,
                               float* __restrict__ out, int64_t* __restrict__ counters) {
@@ -365,7 +369,7 @@ __global__ void k_exact_nodes(const float* __restrict__ x, int64_t nv, int d, co
   int n_empty = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
     float X[3] = {x[i * d], x[i * d + 1], d == 3 ? x[i * d + 2] : 0.f};
-    out[i] = exact_value<DS>(gr, cell_start, cell_items, recs, adj, vals, nes, field, X, n_empty, cost);
+    out[i] = exact_value<DS>(gr, cell_start, cell_items, cell_first, recs, adj, vals, nes, field, X, n_empty, cost);
   }
   const int m1 = warp_sum<int>(n_empty);
   if ((threadIdx.x & 31) == 0 && m1) atomicAdd(reinterpret_cast<unsigned long long*>(counters + 2), (unsigned long long)m1);
@@ -377,8 +381,8 @@ __global__ void k_exact_nodes(const float* __restrict__ x, int64_t nv, int d, co
 template <int DS>
 __global__ void k_dataset(int64_t n, PhiloxKey key, uint32_t stream_id, float3 lo, float3 w,
                           const GridP<float>* __restrict__ gp, const int32_t* __restrict__ cell_start,
-                          const int32_t* __restrict__ cell_items, const float* __restrict__ recs,
-                          const int32_t* __restrict__ adj,
+                          const int32_t* __restrict__ cell_items, const int32_t* __restrict__ cell_first,
+                          const float* __restrict__ recs, const int32_t* __restrict__ adj,
                           const float* __restrict__ vals, int64_t nes, int field, float* __restrict__ pts,
                           float* __restrict__ f, unsigned int* __restrict__ maxabs, int64_t* __restrict__ counters) {
   const GridP<float> gr = *gp;
@@ -390,7 +394,7 @@ __global__ void k_dataset(int64_t n, PhiloxKey key, uint32_t stream_id, float3 l
     X[0] = __fadd_rn(lo.x, __fmul_rn(u01f(r.x), w.x));
     X[1] = __fadd_rn(lo.y, __fmul_rn(u01f(r.y), w.y));
     X[2] = __fadd_rn(lo.z, __fmul_rn(u01f(r.z), w.z));
-    const float v = exact_value<DS>(gr, cell_start, cell_items, recs, adj, vals, nes, field, X, n_empty);
+    const float v = exact_value<DS>(gr, cell_start, cell_items, cell_first, recs, adj, vals, nes, field, X, n_empty);
     pts[j * 3] = X[0];
     pts[j * 3 + 1] = X[1];
     pts[j * 3 + 2] = X[2];
@@ -425,7 +429,8 @@ static sft_status launch_sur(sft_mlp_s* m, sft_source_s* s, sft_target_s* t, con
   ::sft::note_launch(), k_surrogate_assemble<DT, DS, NET><<<grid, NET ? kTPR * kTileM : kTileM, NET ? kSmemSur : kSmemPieces, st>>>(
       m ? m->P : nullptr, m ? m->Wc[0] : nullptr, m ? m->Wc[1] : nullptr, m ? m->Wc[2] : nullptr,
       (const float*)t->coordsP[SFT_PREC_FP32], t->conn, t->vol32, g, L ? (const GridP<float>*)L->grid : nullptr,
-      L ? L->cell_start : nullptr, L ? L->cell_items : nullptr, L ? (const float*)L->recs : nullptr,
+      L ? L->cell_start : nullptr, L ? L->cell_items : nullptr, L ? L->cell_first : nullptr,
+      L ? (const float*)L->recs : nullptr,
       L ? L->adj : nullptr, L ? (const float*)L->vals : nullptr, p, b, fb, sf, counters, err);
   SFT_CUDA(cudaGetLastError());
   return SFT_OK;
@@ -465,7 +470,8 @@ sft_status sft_surrogate_dataset(sft_source s, int32_t field, int64_t n, uint64_
     const unsigned blocks = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16);
 #define SFT_DS(DSV)                                                                                               \
   ::sft::note_launch(), k_dataset<DSV><<<blocks, 256, 0, st>>>(n, key, stream_id, lo, w, (const GridP<float>*)L.grid, \
-                                                              L.cell_start, L.cell_items, (const float*)L.recs,   \
+                                                              L.cell_start, L.cell_items, L.cell_first,           \
+                                                              (const float*)L.recs,                               \
                                                               L.adj, (const float*)L.vals, s->ne, field, pts_out, \
                                                               f_out,                                              \
                                                               mx.p, counters.p)
@@ -543,7 +549,8 @@ sft_status sft_transfer_surrogate(sft_mlp net, sft_source exact, sft_target t, c
     const Locator& L = exact->loc[SFT_PREC_FP32];
 #define SFT_EN(DSV)                                                                                             \
   ::sft::note_launch(), k_exact_nodes<DSV><<<nb, 256, 0, st>>>(tx, nv, t->dim, (const GridP<float>*)L.grid,     \
-                                                              L.cell_start, L.cell_items, (const float*)L.recs, \
+                                                              L.cell_start, L.cell_items, L.cell_first,         \
+                                                              (const float*)L.recs,                             \
                                                               L.adj, (const float*)L.vals, exact->ne,           \
                                                               so->exact_field, so->exact_cost,                  \
                                                               g.p, counters.p)
@@ -620,7 +627,7 @@ sft_status sft_transfer_surrogate(sft_mlp net, sft_source exact, sft_target t, c
 #define SFT_SP(DTV, DSV)                                                                                             \
   ::sft::note_launch(), k_sub_points<DTV, DSV><<<nbs, 128, 0, st>>>(                                                  \
       tx, t->conn, ne, sub, p.key, p.stream_id, p.st, (const GridP<float>*)L.grid, L.cell_start, L.cell_items,     \
-      (const float*)L.recs, L.adj, (const float*)L.vals, exact->ne, so->exact_field, so->exact_cost, s_pts.p,      \
+      L.cell_first, (const float*)L.recs, L.adj, (const float*)L.vals, exact->ne, so->exact_field, so->exact_cost, s_pts.p,      \
       s_fe.p, counters.p)
     if (t->dim == 2) SFT_SP(2, 2);
     else if (ds == 2) SFT_SP(3, 2);
