@@ -209,6 +209,8 @@ def run_ours(args):
     src, tgt, p = make_workload(args.workload, args.scale)
     N, tol = p["samples_per_elem"], p["cg_tol"]
     dim = src.dim
+    if args.adaptive:
+        args.adapt_ref = _mean_measure(tgt)
     prec = sft.SFT_PREC_FP64 if args.precision == "fp64" else sft.SFT_PREC_FP32
     stream = torch.cuda.current_stream()
     sc, sk, sv = (torch.as_tensor(np.ascontiguousarray(a)).to(dev) for a in (src.coords, src.conn, src.values))
@@ -222,7 +224,7 @@ def run_ours(args):
     def step():
         s = sft.sft_source_create(sc, sk, sv, args.grid_scale)
         t = sft.sft_target_create(tc, tk)
-        _, st, _ = sft.sft_transfer(s, t, N, prec, seed=0, cg_tol=tol, u_out=u, sampling=_sampling(args))
+        _, st, _ = sft.sft_transfer(s, t, N, prec, seed=0, cg_tol=tol, u_out=u, **_xfer(args))
         cons_last[0] = sft.sft_conservation_error(s, t, u[0])
         stats_last.update(st)
         s.close()
@@ -272,7 +274,8 @@ def run_ours(args):
         mean_asm = float(np.mean(asm_ms))
         bq, be = (BYTES_PER_QUERY_FP64, BYTES_PER_ELEM_FP64) if args.precision == "fp64" else \
             (BYTES_PER_QUERY, BYTES_PER_ELEM)
-        alg_bytes = bq[dim] * tgt.nelems * N + be[dim] * tgt.nelems
+        n_samples = queries - tgt.nnodes          # samples drawn (N per element unless --adaptive)
+        alg_bytes = bq[dim] * n_samples + be[dim] * tgt.nelems
         achieved = alg_bytes / (mean_asm / 1e3) / 1e9
         traffic = measured_traffic(args.workload) if args.precision == "fp32" else None
         cpu = cpu_baseline(args, src, tgt, p, args.cpu_frac_baseline) if not args.skip_cpu else None
@@ -286,6 +289,8 @@ def run_ours(args):
                                       if args.precision == "fp64" else ""),
                        "queries_per_step": queries, "target_elements": tgt.nelems, "samples_per_elem": N,
                        "source_elements": src.nelems, "grid_scale_L": args.grid_scale, "sampling": args.sampling,
+                       "adaptive_counts": (f"N_t = min(8N, max(1, ceil(N |T| / {args.adapt_ref:.6g})))"
+                                           if args.adaptive else "off"),
                        "precision": args.precision,
                        "l2": "flushed between steps (256 MB write)",
                        "accumulation": "FP64 load vector, CG and reductions",
@@ -293,7 +298,7 @@ def run_ours(args):
             "breakdown_ms": {"assembly_kernel": mean_asm, "solve": float(np.mean(solve_ms)),
                              "step_min": min(step_ms), "step_max": max(step_ms),
                              "transfer_call": stats_last["ms_total"], "control": stats_last["ms_control"]},
-            "assembly_queries_per_s": tgt.nelems * N / (mean_asm / 1e3),
+            "assembly_queries_per_s": n_samples / (mean_asm / 1e3),
             "accuracy": {"E_mass": e_mass, "E_L2_estimate": e_l2, "E_L2_stderr": e_l2_se,
                          "cg_iters": stats_last["cg_iters"], "cg_rel_resid": stats_last["cg_rel_resid"],
                          "fallback_queries": stats_last["fallback_queries"],
@@ -925,7 +930,7 @@ def mesh_intersection_leg(args, sc, sk, sv, tc, tk, u, N, tol):
     bmc = torch.zeros((sv.shape[0], tc.shape[0]), dtype=torch.float64, device=sc.device)
     umc = torch.zeros_like(bmc)
     _, st, _ = sft.sft_transfer(s, t, N, sft.SFT_PREC_FP32, seed=0, cg_tol=tol, u_out=umc, b_out=bmc,
-                                sampling=_sampling(args))
+                                **_xfer(args))
     bx = b.cpu().numpy()
     bm = bmc[0].cpu().numpy()
     s.close()
@@ -950,8 +955,8 @@ def precision_comparison(args, sc, sk, sv, tc, tk, N, tol):
     for name, prec in (("fp32", sft.SFT_PREC_FP32), ("fp64", sft.SFT_PREC_FP64)):
         u = torch.zeros((sv.shape[0], tc.shape[0]), dtype=torch.float64, device=sc.device)
         b = torch.zeros_like(u)
-        sft.sft_transfer(s, t, N, prec, seed=0, cg_tol=tol, u_out=u, b_out=b, sampling=_sampling(args))
-        _, st, _ = sft.sft_transfer(s, t, N, prec, seed=0, cg_tol=tol, u_out=u, b_out=b, sampling=_sampling(args))
+        sft.sft_transfer(s, t, N, prec, seed=0, cg_tol=tol, u_out=u, b_out=b, **_xfer(args))
+        _, st, _ = sft.sft_transfer(s, t, N, prec, seed=0, cg_tol=tol, u_out=u, b_out=b, **_xfer(args))
         e = sft.sft_conservation_error(s, t, u[0])[0]
         res[name] = (b[0].cpu().numpy(), u[0].cpu().numpy())
         out[f"E_mass_{name}"] = e
@@ -977,7 +982,7 @@ def run_e2e(args, src, tgt, N, tol, prec):
     def step():
         s = sft.sft_source_create(sc, sk, sv, args.grid_scale)
         t = sft.sft_target_create(tc, tk)
-        _, st, _ = sft.sft_transfer(s, t, N, prec, seed=0, cg_tol=tol, u_out=u, sampling=_sampling(args))
+        _, st, _ = sft.sft_transfer(s, t, N, prec, seed=0, cg_tol=tol, u_out=u, **_xfer(args))
         e = sft.sft_conservation_error(s, t, u[0])
         s.close()
         t.close()
@@ -1037,23 +1042,38 @@ def _sample_target(tgt, frac):
     return W.Mesh(tgt.coords[used], remap[conn].astype(np.int32))
 
 
-def oracle_step(src, tgt_s, p, sampling=0):
+def oracle_step(src, tgt_s, p, sampling=0, adapt_ref_measure=0.0):
     import oracle
     t0 = time.perf_counter()
     r = oracle.transfer(src, tgt_s, 1, p["samples_per_elem"], seed=0, cg_tol=p["cg_tol"], cg_max_iter=1000,
-                        sampling=sampling)
+                        sampling=sampling, adapt_ref_measure=adapt_ref_measure)
     dt = time.perf_counter() - t0
-    return (tgt_s.nelems * p["samples_per_elem"] + tgt_s.nnodes) / dt, dt, r
+    return (int(r["samples"]) + tgt_s.nnodes) / dt, dt, r
 
 
 def _sampling(args) -> int:
-    """sft_sampling value of --sampling (1 stratified, 0 uniform)."""
-    return 1 if getattr(args, "sampling", "uniform") == "stratified" else 0
+    """sft_sampling value of --sampling (0 uniform, 1 stratified, 2 importance)."""
+    return {"uniform": 0, "stratified": 1, "importance": 2}[getattr(args, "sampling", "uniform")]
+
+
+def _xfer(args) -> dict:
+    """Sampling options of one sft_transfer / oracle.transfer call: the scheme
+    and, with --adaptive, per-element sample counts against the mean target
+    element measure (adapt_ref_measure; 0 = N everywhere)."""
+    return {"sampling": _sampling(args), "adapt_ref_measure": float(getattr(args, "adapt_ref", 0.0))}
+
+
+def _mean_measure(mesh) -> float:
+    """Mean element measure of a simplicial mesh (FP64, host)."""
+    x = mesh.coords.astype(np.float64)[mesh.conn.astype(np.int64)]     # [E, d+1, d]
+    J = x[:, 1:, :] - x[:, :1, :]
+    d = J.shape[1]
+    return float(np.abs(np.linalg.det(J)).mean() / (2.0 if d == 2 else 6.0))
 
 
 def cpu_baseline(args, src, tgt, p, frac):
     tgt_s = _sample_target(tgt, frac)
-    v, dt, _ = oracle_step(src, tgt_s, p, _sampling(args))
+    v, dt, _ = oracle_step(src, tgt_s, p, **_xfer(args))
     return {"value": v, "unit": "queries/s", "cores": 1, "kind": "oracle",
             "seconds": dt,
             "sample": f"full source mesh (grid build included) and the first {tgt_s.nelems} target "
@@ -1108,14 +1128,22 @@ def run_reference(args):
         src, tgt, p = make_workload(args.workload, args.scale)
         tgt_s = _sample_target(tgt, args.cpu_frac)
 
+        if args.adaptive:
+            args.adapt_ref = _mean_measure(tgt)
+        seen = {}
+
         def one():
-            return oracle_step(src, tgt_s, p, _sampling(args))[1]
-        q = tgt_s.nelems * p["samples_per_elem"] + tgt_s.nnodes
+            _, dt, r = oracle_step(src, tgt_s, p, **_xfer(args))
+            seen["q"] = int(r["samples"]) + tgt_s.nnodes   # queries of the step (adaptive counts included)
+            return dt
+        q = None
         sample = (f"full source mesh and the first {tgt_s.nelems} target elements (Morton order, "
                   f"{args.cpu_frac:.3g} of the workload) per step")
     for _ in range(args.warmup):
         one()
     times = [one() for _ in range(args.steps)]
+    if q is None:
+        q = seen["q"]
     ms = 1e3 * float(np.mean(times))
     value = q / (ms / 1e3)
     print(json.dumps({
@@ -1145,8 +1173,12 @@ def main():
     ap.add_argument("--sur-epochs", type=int, default=40, help="training epochs of the surrogate (sur3d)")
     ap.add_argument("--grid-scale", type=float, default=1.0,
                     help="source grid cells per axis = int(L * nelems^(1/d)) (tri4m / tet5m)")
-    ap.add_argument("--sampling", choices=["uniform", "stratified"], default="uniform",
-                    help="sample scheme of the mesh-source workloads (tri4m, tet5m and their online forms)")
+    ap.add_argument("--sampling", choices=["uniform", "stratified", "importance"], default="uniform",
+                    help="sample scheme of the mesh-source workloads (tri4m, tet5m and their online forms; "
+                         "importance: tri4m / tet5m only)")
+    ap.add_argument("--adaptive", action="store_true",
+                    help="tri4m / tet5m: per-element sample counts proportional to the element measure "
+                         "(reference measure = the mean target element measure)")
     ap.add_argument("--cold-start", action="store_true",
                     help="roundtrip: start every solve from 0 instead of the leg's previous result")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
@@ -1155,6 +1187,9 @@ def main():
     ap.add_argument("--scale", type=float, default=1.0,
                     help="element-count scale of the workload (1 = the named workload)")
     args = ap.parse_args()
+    args.adapt_ref = 0.0
+    if (args.sampling == "importance" or args.adaptive) and args.workload not in ("tri4m", "tet5m"):
+        ap.error("--sampling importance and --adaptive apply to tri4m and tet5m only")
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

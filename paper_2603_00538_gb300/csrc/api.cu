@@ -60,19 +60,8 @@ static sft_status check_desc(const sft_mesh_desc* d, bool source) {
     if (d->nfields < 1 || d->nfields > kMaxFields) return fail(SFT_ERR_ARG, "nfields must be in 1..8");
     if (!d->values) return fail(SFT_ERR_ARG, "null source values");
   }
-  if (!d->device_ptrs) {
-    // host inputs: reject non-finite coordinates before copying
-    const int64_t n = d->nnodes * d->dim;
-    if (d->dtype == SFT_F64) {
-      const double* c = (const double*)d->coords;
-      for (int64_t i = 0; i < n; ++i)
-        if (!std::isfinite(c[i])) return fail(SFT_ERR_MESH, "non-finite coordinate");
-    } else {
-      const float* c = (const float*)d->coords;
-      for (int64_t i = 0; i < n; ++i)
-        if (!std::isfinite(c[i])) return fail(SFT_ERR_MESH, "non-finite coordinate");
-    }
-  }
+  // non-finite coordinates (host or device inputs) are found on the device
+  // after the copy (check_finite), before the first kernel that reads them
   return SFT_OK;
 }
 
@@ -169,6 +158,8 @@ sft_status sft_source_create(const sft_mesh_desc* d, sft_source* out) {
     if (e != cudaSuccess) { r = cuda_fail(e, "alloc"); break; }
     e = cudaMemsetAsync(d_err, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) { r = cuda_fail(e, "memset"); break; }
+    e = check_finite(s->coords, s->nv * s->dim, d->dtype == SFT_F64, d_err, DEV_NONFINITE, st);
+    if (e != cudaSuccess) { r = cuda_fail(e, "check_finite"); break; }
     const int prec = d->dtype == SFT_F64 ? SFT_PREC_FP64 : SFT_PREC_FP32;
     if ((r = build_locator(s, prec, st, d_err))) break;
   } while (0);
@@ -213,6 +204,8 @@ sft_status sft_target_create(const sft_mesh_desc* d, sft_target* out) {
     if (e != cudaSuccess) { r = cuda_fail(e, "alloc"); break; }
     e = cudaMemsetAsync(d_err, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) { r = cuda_fail(e, "memset"); break; }
+    e = check_finite(t->coords, t->nv * t->dim, d->dtype == SFT_F64, d_err, DEV_NONFINITE, st);
+    if (e != cudaSuccess) { r = cuda_fail(e, "check_finite"); break; }
     if ((r = build_target(t, st, d_err))) break;
     const int prec = d->dtype == SFT_F64 ? SFT_PREC_FP64 : SFT_PREC_FP32;
     if ((r = target_coordsP(t, prec, st))) break;

@@ -34,6 +34,7 @@ struct AsmParams {
   int adapt;      // per-element sample counts (the EXT kernel)
   double dref;    // d! x the reference measure of the adaptive count
   int nmax;       // samples per element at most (row length of sample_elem)
+  const int32_t* nt;  // per-element sample counts (p.adapt; k_adaptive_counts)
 };
 
 // Adaptive sample count of an element (the EXT kernel): N_t = min(8 N,
@@ -66,6 +67,26 @@ __device__ __forceinline__ int adaptive_count(const P xv[D + 1][D], int N, doubl
   const double q = ceil(__ddiv_rn(__dmul_rn((double)N, det), dref));
   const double cap = 8.0 * (double)N;
   return (int)(q < 1.0 ? 1.0 : (q > cap ? cap : q));
+}
+
+// The adaptive count of every target element, once per assembly: the FP64
+// determinant runs with every lane of a warp busy (inside the assembly only
+// the 8 lanes that count the warp's 8 elements would be: tet5m assembly
+// 2.67 ms with the counts inline).
+template <int D, typename P>
+__global__ void k_adaptive_counts(const P* __restrict__ tx, const int32_t* __restrict__ tconn, int64_t ne, int N,
+                                  double dref, int32_t* __restrict__ nt) {
+  constexpr int K = D + 1;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+    P xv[K][D];
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+      const int32_t vm = __ldg(tconn + e * K + m);
+#pragma unroll
+      for (int a = 0; a < D; ++a) xv[m][a] = __ldg(tx + (int64_t)vm * D + a);
+    }
+    nt[e] = adaptive_count<D, P>(xv, N, dref);
+  }
 }
 
 // MODE: kAsmPlain; kAsmDebug also writes the source element of every sample
@@ -106,11 +127,43 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const P* __restrict__ tx, c
   const P alphaP = (P)p.alpha;
   int n_fallback = 0, n_empty = 0;
 
+  // importance sampling draws one sample per unit (two Philox blocks)
+  const int spu = EXT && p.imp ? 1 : SPU;
   for (int64_t task = warp0; task < p.ntasks; task += nwarps) {
     int64_t t;
     int u0, ustep, seg_lo, seg_hi;
     bool active;
-    {
+    int Nt = p.N;   // this element's samples
+    int span = p.LPE;
+    if (EXT && p.adapt) {
+      // per-element counts: the G elements of the task share the 32 lanes in
+      // proportion to their units (each at least one lane), so a warp runs
+      // as long as its mean element, not its largest. Lane s < G reads the
+      // count of element s; slot s starts at lane s + floor((32 - G) C_s / C),
+      // C_s the units of the slots before it and C the task's total.
+      const int64_t ts = task * p.G + lane;
+      const int Ns = lane < p.G && ts < p.ne ? __ldg(p.nt + ts) : 0;
+      const int Us = (Ns + spu - 1) / spu;
+      int cum = Us;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, cum, o);
+        if (lane >= o) cum += y;
+      }
+      const int tot = __shfl_sync(0xffffffffu, cum, 31);
+      const int start = lane + (tot > 0 ? (int)((int64_t)(32 - p.G) * (cum - Us) / tot) : lane * (32 / p.G - 1));
+      int slot = 0;
+      for (int q = 1; q < p.G; ++q) slot += __shfl_sync(0xffffffffu, start, q) <= lane;
+      seg_lo = __shfl_sync(0xffffffffu, start, slot);
+      const int nxt = __shfl_sync(0xffffffffu, start, slot + 1 < p.G ? slot + 1 : slot);
+      seg_hi = slot + 1 < p.G ? nxt : 32;
+      Nt = __shfl_sync(0xffffffffu, Ns, slot);
+      span = (int)__reduce_max_sync(0xffffffffu, (unsigned)(seg_hi - seg_lo));
+      t = task * p.G + slot;
+      u0 = lane - seg_lo;
+      ustep = seg_hi - seg_lo;
+      active = true;
+    } else {
       // G elements per warp, LPE = lanes per element; lanes stride over the
       // element's units
       const int slot = lane / p.LPE;
@@ -127,7 +180,6 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const P* __restrict__ tx, c
     P xv[K][D];
     P gl[NF][K];
     Acc<P> acc[NF][K];
-    int Nt = p.N;   // this element's samples
     if (active) {
 #pragma unroll
       for (int m = 0; m < K; ++m) {
@@ -137,10 +189,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const P* __restrict__ tx, c
 #pragma unroll
         for (int f = 0; f < NF; ++f) gl[f][m] = f < p.nf ? __ldg(g + (int64_t)f * p.nv + v[m]) : P(0);
       }
-      if (EXT && p.adapt) Nt = adaptive_count<D, P>(xv, p.N, p.dref);
     }
-    // importance sampling draws one sample per unit (two Philox blocks)
-    const int spu = EXT && p.imp ? 1 : SPU;
     const int Ut = EXT ? (Nt + spu - 1) / spu : p.U;
     if (EXT && MODE == kAsmDebug && active && lane == seg_lo)
       for (int j = Nt; j < p.nmax; ++j) sample_elem[t * p.nmax + j] = -1;
@@ -202,8 +251,9 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const P* __restrict__ tx, c
     }
 
     // segmented suffix combine: lane seg_lo ends with its element's totals
-    // (log2 LPE rounds: a segment spans LPE lanes)
-    for (int o = 1; o < p.LPE; o <<= 1) {
+    // (log2 of the longest segment rounds: LPE lanes, or with per-element
+    // counts the task's widest lane range)
+    for (int o = 1; o < span; o <<= 1) {
       const bool take = lane + o < seg_hi;
 #pragma unroll
       for (int f = 0; f < NF; ++f)
@@ -301,6 +351,27 @@ sft_status launch_assembly(sft_source_s* s, sft_target_s* t, const AssembleArgs&
   p.adapt = a.adapt_ref > 0.0 ? 1 : 0;
   p.dref = a.adapt_ref * (t->dim == 2 ? 2.0 : 6.0);
   p.nmax = p.adapt ? 8 * a.N : a.N;
+  p.nt = nullptr;
+  DevBuf<int32_t> nt(st);  // freed in stream order after the launches
+  if (p.adapt) {
+    SFT_CUDA(nt.alloc((size_t)t->ne));
+    int dev = 0, sms = 1;
+    SFT_CUDA(cudaGetDevice(&dev));
+    SFT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t want = (t->ne + 255) / 256;
+    const unsigned nb = (unsigned)(want < 16LL * sms ? want : 16LL * sms);
+    const void* tx = t->coordsP[a.prec];
+    if (t->dim == 2 && a.prec == SFT_PREC_FP32)
+      ::sft::note_launch(), k_adaptive_counts<2, float><<<nb, 256, 0, st>>>((const float*)tx, t->conn, t->ne, a.N, p.dref, nt.p);
+    else if (t->dim == 2)
+      ::sft::note_launch(), k_adaptive_counts<2, double><<<nb, 256, 0, st>>>((const double*)tx, t->conn, t->ne, a.N, p.dref, nt.p);
+    else if (a.prec == SFT_PREC_FP32)
+      ::sft::note_launch(), k_adaptive_counts<3, float><<<nb, 256, 0, st>>>((const float*)tx, t->conn, t->ne, a.N, p.dref, nt.p);
+    else
+      ::sft::note_launch(), k_adaptive_counts<3, double><<<nb, 256, 0, st>>>((const double*)tx, t->conn, t->ne, a.N, p.dref, nt.p);
+    SFT_CUDA(cudaGetLastError());
+    p.nt = nt.p;
+  }
   if (t->dim == 2) {
     if (a.prec == SFT_PREC_FP32) launch_nf<2, float>(s, t, a, p, st);
     else launch_nf<2, double>(s, t, a, p, st);

@@ -423,10 +423,10 @@ constexpr int kWalkSteps = 12;
 // The fallback of the location below: every candidate of cell c is tested
 // at X = (x0, x1, x2) and the one with the largest min(mu) wins, ties to the
 // lowest id (an accepting one whenever any accepts, else the nearest); -1 for
-// an empty list. Kept out of line and fed by value: the walk almost always
-// succeeds, and inlining this loop into the callers raised their register
-// pressure (more spills in the assembly kernel) for a path a few queries in a
-// thousand take.
+// an empty list. In 3D it runs out of line (scan_cell, fed by value): the
+// walk almost always succeeds, and the inlined loop raised the register
+// pressure of the 3D assembly kernel (tet5m launch 2.110 ms inlined, 1.858
+// out of line); in 2D the inlined form is faster (tri4m 1.276 against 1.327).
 template <typename P>
 struct ScanHit {
   int32_t e;
@@ -435,8 +435,10 @@ struct ScanHit {
 };
 
 template <int D, typename P>
-__device__ __noinline__ ScanHit<P> scan_cell(int32_t c, P x0, P x1, P x2, const int32_t* __restrict__ cell_start,
-                                             const int32_t* __restrict__ cell_items, const P* __restrict__ recs) {
+__device__ __forceinline__ ScanHit<P> scan_cell_body(int32_t c, P x0, P x1, P x2,
+                                                     const int32_t* __restrict__ cell_start,
+                                                     const int32_t* __restrict__ cell_items,
+                                                     const P* __restrict__ recs) {
   constexpr int L = RecLen<D>::value;
   const P X[3] = {x0, x1, x2};
   const int32_t p0 = __ldg(cell_start + c), p1 = __ldg(cell_start + c + 1);
@@ -466,6 +468,12 @@ __device__ __noinline__ ScanHit<P> scan_cell(int32_t c, P x0, P x1, P x2, const 
   load_record<D, P>(recs, best, r);
   bary_from_record<D, P>(r, X, h.mu);
   return h;
+}
+
+template <int D, typename P>
+__device__ __noinline__ ScanHit<P> scan_cell(int32_t c, P x0, P x1, P x2, const int32_t* __restrict__ cell_start,
+                                             const int32_t* __restrict__ cell_items, const P* __restrict__ recs) {
+  return scan_cell_body<D, P>(c, x0, x1, x2, cell_start, cell_items, recs);
 }
 
 // Locate X. A walk through face neighbours starts at the element deepest at
@@ -498,25 +506,42 @@ __device__ __forceinline__ int32_t locate_point(const GridP<P>& g, const int32_t
   for (int s = 0; s < kWalkSteps; ++s) {
     P r[L];
     load_record<D, P>(recs, e, r);
+    // 3D: the element's neighbour row (16 B) is loaded beside its record, so
+    // a step waits for one cache latency instead of two (record, then the
+    // neighbour it selects): tet5m launch 1.858 -> 1.755 ms. In 2D the row is
+    // 12 B and the extra loads cost more than they hide (1.276 -> 1.292 ms).
+    int32_t nb[D + 1];
+    if constexpr (D == 3) {
+      const int4 a4 = __ldg(reinterpret_cast<const int4*>(adj) + e);
+      nb[0] = a4.x; nb[1] = a4.y; nb[2] = a4.z; nb[3] = a4.w;
+    }
     P m[D + 1];
     bary_from_record<D, P>(r, X, m);
     P mn = m[0];
     int am = 0;
+    int32_t nx = 0;
+    if constexpr (D == 3) nx = nb[0];
 #pragma unroll
     for (int q = 1; q <= D; ++q)
-      if (m[q] < mn) { mn = m[q]; am = q; }
+      if (m[q] < mn) {
+        mn = m[q];
+        am = q;
+        if constexpr (D == 3) nx = nb[q];
+      }
     if (mn >= P(0)) {
 #pragma unroll
       for (int q = 0; q <= D; ++q) mu[q] = m[q];
       status = 0;
       return e;
     }
-    const int32_t nx = __ldg(adj + (int64_t)e * (D + 1) + am);
+    if constexpr (D == 2) nx = __ldg(adj + (int64_t)e * (D + 1) + am);
     if (nx < 0) break;
     e = nx;
   }
   // the walk gave up (boundary or step limit)
-  const ScanHit<P> h = scan_cell<D, P>(c, X[0], X[1], D == 3 ? X[D - 1] : P(0), cell_start, cell_items, recs);
+  ScanHit<P> h;
+  if constexpr (D == 2) h = scan_cell_body<D, P>(c, X[0], X[1], P(0), cell_start, cell_items, recs);
+  else h = scan_cell<D, P>(c, X[0], X[1], X[D - 1], cell_start, cell_items, recs);
   status = h.status;
 #pragma unroll
   for (int q = 0; q <= D; ++q) mu[q] = h.mu[q];

@@ -27,6 +27,9 @@ sft_status cuda_fail(cudaError_t e, const char* what);
 // transfers and destroys do not map fresh memory every time;
 // sft_trim_memory hands the unused part back.
 cudaError_t pool_alloc(void** p, size_t bytes, cudaStream_t s);
+// *err <- code (first error wins) if any of the n values at x (device
+// memory, FP64 or FP32) is not finite (util.cu)
+cudaError_t check_finite(const void* x, int64_t n, bool is_double, int32_t* err, int32_t code, cudaStream_t s);
 void trim_pools();
 template <typename T>
 cudaError_t dalloc(T** p, size_t count, cudaStream_t s) {

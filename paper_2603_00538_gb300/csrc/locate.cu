@@ -573,8 +573,9 @@ static sft_status build_locator_t(sft_source_s* s, int prec, cudaStream_t st, in
   SFT_CUDA(cudaMemcpyAsync(&total, start64.p + L.ncells, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   SFT_CUDA(cudaStreamSynchronize(st));
   if (herr != 0)
-    return fail(SFT_ERR_MESH, herr == DEV_BAD_INDEX ? "source connectivity index out of range"
-                                                    : "source mesh has a non-positive element or a degenerate box");
+    return fail(SFT_ERR_MESH, herr == DEV_NONFINITE  ? "non-finite source coordinate"
+                              : herr == DEV_BAD_INDEX ? "source connectivity index out of range"
+                                                      : "source mesh has a non-positive element or a degenerate box");
   if (total >= (int64_t)INT32_MAX) return fail(SFT_ERR_UNSUPPORTED, "grid registrations exceed 2^31");
   L.nitems = total;
   SFT_CUDA(dalloc(&L.cell_start, (size_t)L.ncells + 1, st));

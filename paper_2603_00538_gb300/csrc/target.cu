@@ -298,6 +298,7 @@ static sft_status build_target_t(sft_target_s* t, cudaStream_t st, int32_t* d_er
     dfree(inc, st);
     dfree(inc_count, st);
     dfree(wfac, st);
+    if (herr == DEV_NONFINITE) return fail(SFT_ERR_MESH, "non-finite target coordinate");
     if (herr == DEV_BAD_INDEX) return fail(SFT_ERR_MESH, "target connectivity index out of range");
     if (herr == DEV_BAD_ELEMENT) return fail(SFT_ERR_MESH, "target mesh has a non-positive element");
     if (herr) return fail(SFT_ERR_MESH, "target node belongs to more elements than supported");

@@ -132,6 +132,31 @@ cudaError_t exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n
   return scan_rec<int32_t>(in, out, n, s);
 }
 
+// err <- code (first error wins) when any of x[0..n) is not finite: one
+// coalesced pass on the device (a host loop over the coordinates of a
+// multi-million-node mesh took milliseconds per create)
+template <typename T>
+__global__ void k_check_finite(const T* __restrict__ x, int64_t n, int32_t* __restrict__ err, int32_t code) {
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    bad = bad || !isfinite(__ldg(x + i));
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) set_error(err, code);
+}
+
+cudaError_t check_finite(const void* x, int64_t n, bool is_double, int32_t* err, int32_t code, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (n + 255) / 256;
+  const unsigned blocks = (unsigned)(want < 8LL * sms ? want : 8LL * sms);
+  if (is_double)
+    ::sft::note_launch(), k_check_finite<double><<<blocks, 256, 0, s>>>((const double*)x, n, err, code);
+  else
+    ::sft::note_launch(), k_check_finite<float><<<blocks, 256, 0, s>>>((const float*)x, n, err, code);
+  return cudaGetLastError();
+}
+
 cudaError_t narrow_i64_to_i32(const int64_t* in, int32_t* out, int64_t n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   ::sft::note_launch(), k_narrow<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, out, n);

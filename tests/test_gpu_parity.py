@@ -362,6 +362,27 @@ def test_invalid_meshes_rejected():
     with pytest.raises(sft.SftError) as ei:
         sft.sft_source_create(nanc, m.conn, m.values)
     assert ei.value.status == 2
+    assert "non-finite" in str(ei.value)
+    # non-finite coordinates are found on the device: device inputs too, and
+    # in a node no element uses
+    for bad_val in (np.inf, -np.inf, np.nan):
+        c2 = np.concatenate([m.coords, [[bad_val, 0.5]]])
+        for dev in (False, True):
+            cc = torch.as_tensor(c2).to(DEV) if dev else c2
+            kk = torch.as_tensor(m.conn).to(DEV) if dev else m.conn
+            with pytest.raises(sft.SftError) as ei:
+                sft.sft_target_create(cc, kk)
+            assert ei.value.status == 2 and "non-finite" in str(ei.value)
+            vv = np.concatenate([m.values, np.zeros((m.values.shape[0], 1))], axis=1)
+            vv = torch.as_tensor(vv).to(DEV) if dev else vv
+            with pytest.raises(sft.SftError) as ei:
+                sft.sft_source_create(cc, kk, vv)
+            assert ei.value.status == 2 and "non-finite" in str(ei.value)
+    # the library stays usable after the rejections
+    s = sft.sft_source_create(m.coords, m.conn, m.values)
+    t = sft.sft_target_create(m.coords, m.conn)
+    s.close()
+    t.close()
     # a target index out of range: the setup skips the element in every pass
     # and reports the error once the row counts are read back
     for v in (m.nnodes, m.nnodes + 1000, -1):
