@@ -808,7 +808,10 @@ def run_surrogate(args):
 
     if rank == 0:
         mean_asm = float(np.mean(asm_ms))
-        flops = NET_FLOP_PER_QUERY * tgt.nelems * N
+        # network work actually done: every sample of the elements that keep
+        # the network, plus the decision subsample of every element
+        net_queries = (tgt.nelems - int(stats_sur["fallback_elems"])) * N + tgt.nelems * int(p["subsample"])
+        flops = NET_FLOP_PER_QUERY * net_queries
         achieved = flops / (mean_asm / 1e3) / 1e12
         peak, which = tensor_peak()
         cpu = None if args.skip_cpu else sur_cpu_baseline(src, tgt, p, net, tau)
@@ -835,9 +838,12 @@ def run_surrogate(args):
             "exact_path": {"ms_per_step": float(np.mean(ex_ms)), "assembly_ms": ex["ms_assembly"],
                            "queries_per_s": (tgt.nelems * N + tgt.nnodes) / (float(np.mean(ex_ms)) / 1e3),
                            "surrogate_over_exact_time": ms_per_step / float(np.mean(ex_ms))},
-            "roofline": {"kernel": "sft::k_surrogate_assemble", "bound": "tensor", "achieved": achieved,
+            "roofline": {"kernel": "sft::k_surrogate_net (with the decision and exact passes)", "bound": "tensor", "achieved": achieved,
                          "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "peak_source": which, "algorithmic_flops": flops},
+                         "peak_source": which, "algorithmic_flops": flops, "network_queries": net_queries,
+                         "flop_model": "0.395 MFLOP per network query: N per element that keeps the network "
+                                       "+ the s-sample decision subsample of every element; time = the whole "
+                                       "assembly (decision, network pass, exact pass of the fallbacks)"},
             "cpu_baseline": cpu,
             "e2e": {"value": queries / (e2e_ms / 1e3), "unit": "queries/s", "ms_per_step": e2e_ms, "steps": k_e2e,
                     "h2d_bytes_per_step": int(tc_h.numel() * tc_h.element_size() + tk_h.numel() * tk_h.element_size()),

@@ -67,6 +67,41 @@ constexpr float kNegLog2e = -1.4426950408889634f;
 __device__ __forceinline__ float sigmoid_f(float z) { return rcp_sfu(1.0f + ex2_sfu(kNegLog2e * z)); }
 // SiLU z sigma(z): two special-function operations per activation
 __device__ __forceinline__ float silu_f(float z) { return z * sigmoid_f(z); }
+
+// Packed FP32 pairs (sm_100 family f32x2 instructions): each lane is rounded
+// exactly as the scalar operation (round to nearest, no flush), so the pair
+// forms below give the scalar results bit for bit with half the instructions.
+__device__ __forceinline__ uint64_t f2_pack(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t r, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// silu_f of both lanes of z2 (the same operations in the same order)
+__device__ __forceinline__ void silu_pair(uint64_t z2, float& h0, float& h1) {
+  float t0, t1;
+  f2_unpack(f2_mul(z2, f2_pack(kNegLog2e, kNegLog2e)), t0, t1);
+  float d0, d1;
+  f2_unpack(f2_add(f2_pack(1.0f, 1.0f), f2_pack(ex2_sfu(t0), ex2_sfu(t1))), d0, d1);
+  f2_unpack(f2_mul(z2, f2_pack(rcp_sfu(d0), rcp_sfu(d1))), h0, h1);
+}
 // d silu / dz = sigma(z) (1 + z (1 - sigma(z)))
 __device__ __forceinline__ float silu_grad(float z) {
   const float sg = sigmoid_f(z);
@@ -79,6 +114,31 @@ __device__ __forceinline__ void store_bf16x8(unsigned char* dst, const float* v)
 #pragma unroll
   for (int i = 0; i < 8; ++i) h[i] = __float2bfloat16_rn(v[i]);
   *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(h);
+}
+
+// The first layer in shared memory, pair-interleaved for the packed FMAs:
+// outputs 2m and 2m + 1 take entries 2m = {W1[2m][0], W1[2m+1][0], W1[2m][1],
+// W1[2m+1][1]} and 2m + 1 = {W1[2m][2], W1[2m+1][2], c1[2m], c1[2m+1]}.
+__device__ __forceinline__ void w1_table_entry(float4* w1, const float* __restrict__ P, int o) {
+  const int m = o >> 1, odd = o & 1;
+  float* e0 = reinterpret_cast<float*>(w1 + 2 * m);
+  float* e1 = reinterpret_cast<float*>(w1 + 2 * m + 1);
+  e0[odd] = __ldg(P + kOffW1 + o * 3);
+  e0[2 + odd] = __ldg(P + kOffW1 + o * 3 + 1);
+  e1[odd] = __ldg(P + kOffW1 + o * 3 + 2);
+  e1[2 + odd] = __ldg(P + kOffC1 + o);
+}
+// first-layer outputs o .. o + 7 (o even) of the point x: SiLU(W1 x + c1),
+// the FMAs in the order fma(w2, x2, fma(w1, x1, fma(w0, x0, c)))
+__device__ __forceinline__ void layer1_outputs8(const float4* w1, int o, const float x[3], float h[8]) {
+  const uint64_t X0 = f2_pack(x[0], x[0]), X1 = f2_pack(x[1], x[1]), X2 = f2_pack(x[2], x[2]);
+#pragma unroll
+  for (int q = 0; q < 8; q += 2) {
+    const float4 a = w1[o + q], b = w1[o + q + 1];
+    const uint64_t z = f2_fma(f2_pack(b.x, b.y), X2, f2_fma(f2_pack(a.z, a.w), X1,
+                                                           f2_fma(f2_pack(a.x, a.y), X0, f2_pack(b.z, b.w))));
+    silu_pair(z, h[q], h[q + 1]);
+  }
 }
 
 // The weight stream of a forward CTA: chunk g (g = 0, 1, ... over the
@@ -144,7 +204,7 @@ __device__ __forceinline__ bool tc_layer_issue(WStream& ws, unsigned char* A, un
 struct MlpSmem {
   unsigned char* A;   // activation tile [128][256] BF16, K-major core matrices
   unsigned char* B;   // kStages weight chunk buffers [256][kKF] BF16
-  float4* w1;         // first layer: {W1[o][0], W1[o][1], W1[o][2], c1[o]}
+  float4* w1;         // first layer, pair-interleaved (w1_table_entry)
   float* bias;        // [4][256]: c2, c3, c4 and the output weights w5
   float* ypart;       // [kTPR][128] partial outputs of the column halves
   uint64_t* full;     // [kStages] chunk landed (bulk-copy transaction bytes)
@@ -188,8 +248,7 @@ __device__ __forceinline__ uint32_t mlp_setup(const MlpSmem& S, const float* __r
     while (ws.next_copy < ws.total && ws.next_copy < kStages - 1) ws_copy(ws, S.B, S.full, Wc);
   }
   for (int o = threadIdx.x; o < kH; o += blockDim.x) {
-    S.w1[o] = make_float4(__ldg(P + kOffW1 + o * 3), __ldg(P + kOffW1 + o * 3 + 1), __ldg(P + kOffW1 + o * 3 + 2),
-                          __ldg(P + kOffC1 + o));
+    w1_table_entry(S.w1, P, o);
     S.bias[o] = __ldg(P + kOffC2 + o);
     S.bias[kH + o] = __ldg(P + kOffC3 + o);
     S.bias[2 * kH + o] = __ldg(P + kOffC4 + o);
@@ -221,23 +280,24 @@ __device__ __forceinline__ int64_t cta_tiles(int64_t ntiles) {
 // 32 columns cc .. cc+31 of hidden layer l (accumulators in r) for this
 // thread's row: bias + SiLU, then into the activation tile (l < 2) or the
 // output dot product y
-__device__ __forceinline__ void tile_columns(const MlpSmem& S, int l, int row, int cc, const uint32_t (&r)[32],
-                                             float& y) {
-  const float4* b4 = reinterpret_cast<const float4*>(S.bias + l * kH + cc);
+__device__ __forceinline__ void tile_columns_a(unsigned char* A, const float* bias, int l, int row, int cc,
+                                               const uint32_t (&r)[32], float& y) {
+  const float4* b4 = reinterpret_cast<const float4*>(bias + l * kH + cc);
   float v[32];
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const float4 b = b4[i];
-    v[4 * i] = silu_f(__uint_as_float(r[4 * i]) + b.x);
-    v[4 * i + 1] = silu_f(__uint_as_float(r[4 * i + 1]) + b.y);
-    v[4 * i + 2] = silu_f(__uint_as_float(r[4 * i + 2]) + b.z);
-    v[4 * i + 3] = silu_f(__uint_as_float(r[4 * i + 3]) + b.w);
+    // silu_f(acc + bias) on pairs of columns
+    silu_pair(f2_add(f2_pack(__uint_as_float(r[4 * i]), __uint_as_float(r[4 * i + 1])), f2_pack(b.x, b.y)),
+              v[4 * i], v[4 * i + 1]);
+    silu_pair(f2_add(f2_pack(__uint_as_float(r[4 * i + 2]), __uint_as_float(r[4 * i + 3])), f2_pack(b.z, b.w)),
+              v[4 * i + 2], v[4 * i + 3]);
   }
   if (l < 2) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) store_bf16x8(S.A + tc::kmajor_offset(row, cc + q * 8, kH), v + q * 8);
+    for (int q = 0; q < 4; ++q) store_bf16x8(A + tc::kmajor_offset(row, cc + q * 8, kH), v + q * 8);
   } else {
-    const float4* w4 = reinterpret_cast<const float4*>(S.bias + 3 * kH + cc);
+    const float4* w4 = reinterpret_cast<const float4*>(bias + 3 * kH + cc);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const float4 w = w4[i];
@@ -247,6 +307,11 @@ __device__ __forceinline__ void tile_columns(const MlpSmem& S, int l, int row, i
       y = __fmaf_rn(bf16r(v[4 * i + 3]), w.w, y);
     }
   }
+}
+
+__device__ __forceinline__ void tile_columns(const MlpSmem& S, int l, int row, int cc, const uint32_t (&r)[32],
+                                             float& y) {
+  tile_columns_a(S.A, S.bias, l, row, cc, r, y);
 }
 
 // The whole network on one 128-row tile with kTPR * 128 threads: thread t
@@ -266,11 +331,7 @@ __device__ __forceinline__ bool mlp_tile(const MlpSmem& S, const float* __restri
   const uint32_t trow = taddr + ((uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16);
   for (int o = c0; o < c0 + kCols; o += 8) {
     float h[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const float4 w = S.w1[o + q];
-      h[q] = silu_f(__fmaf_rn(w.z, x[2], __fmaf_rn(w.y, x[1], __fmaf_rn(w.x, x[0], w.w))));
-    }
+    layer1_outputs8(S.w1, o, x, h);
     store_bf16x8(S.A + tc::kmajor_offset(row, o, kH), h);
   }
   tc::fence_async_smem();
@@ -305,6 +366,312 @@ __device__ __forceinline__ bool mlp_tile(const MlpSmem& S, const float* __restri
   float yy = S.ypart[row];
 #pragma unroll
   for (int h = 1; h < kTPR; ++h) yy += S.ypart[h * kTileM + row];
+  y_out = yy + __ldg(P + kOffC5);
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Two-group forward tile (the fused surrogate assembly): one CTA per SM,
+// 2 x 256 threads. Group g (threads 256 g .. 256 g + 255) runs its own
+// 128-row tiles exactly as mlp_tile does one (same arithmetic, bit-identical
+// outputs), with its own activation tile, TMEM accumulator (columns
+// 256 g .. +255) and named barrier. The two groups' layers take turns on the
+// tensor cores in a fixed order - tile pair j: T0 L1, T1 L1, T0 L2, T1 L2,
+// T0 L3, T1 L3; a group without a partner tile at the end runs its layers
+// alone - so one group's epilogue overlaps the other's MMAs, and both read
+// one ring of kStagesPP weight chunks fed in that order (chunk c = 16 s + k:
+// K-slice k of the layer of slot s). Per slot 1 + kCopiers threads of its
+// group work at once: thread 0 issues the 16 MMAs as their chunks land
+// (descriptors formed once, so an MMA costs a few adds), and kCopiers
+// threads each refill one class of buffers (chunk c mod kCopiers) as soon as
+// the MMA that read a buffer completes (the chunk kStagesPP ahead). One
+// thread doing both spent about 1,000 cycles per chunk on issue work, five
+// times the MMA's own time (sur3d fused kernel 258 ms against 132 ms for two
+// independent CTAs per SM); with one copier 132 ms, two 122 ms. Turn counters in shared memory
+// (bounded waits) keep the slots' MMA issue and their copies each in slot
+// order; the copies of slot s wait for slot s - 1's copier, so every
+// mbarrier phase is waited only after the phase before it completed.
+// ---------------------------------------------------------------------------
+constexpr int kStagesPP = 8;                    // power of two
+constexpr int kGroupThreads = kTPR * kTileM;    // 256
+constexpr int kCopiers = 4;      // ring refill threads per group: 32 (1 + p) handles chunks = p (mod kCopiers)
+constexpr int kCopierLane = 32;
+constexpr uint32_t kSmemBarPP = 256;            // mbarriers, TMEM slot, flags, turn counters, stream state
+constexpr uint32_t kSmemPP = 2 * kSmemA + kStagesPP * kSmemBF + kSmemW1 + kSmemBias + 2 * kSmemY + kSmemBarPP;
+static_assert((kStagesPP & (kStagesPP - 1)) == 0 && kStagesPP <= kChunksPerLayer, "ring size");
+static_assert(kStagesPP % kCopiers == 0 && kCopierLane * kCopiers < kGroupThreads, "copier classes");
+
+struct StreamPP {
+  int32_t total;         // chunks of the CTA's stream
+  int32_t tail0;         // first slot of the unpaired tiles (6 x the paired tiles of a group)
+  int32_t next_use;      // chunks whose MMA was issued
+  int32_t next_copy[kCopiers];  // chunk c of class c % kCopiers was copied iff c < next_copy[c % kCopiers]
+};
+
+struct MlpSmemPP {
+  unsigned char* A[2];
+  unsigned char* B;   // kStagesPP weight chunk buffers [256][kKF] BF16
+  float4* w1;
+  float* bias;
+  float* ypart[2];
+  uint64_t* full;     // [kStagesPP]
+  uint64_t* mdone;    // [kStagesPP]
+  uint64_t* lbar;     // [2]: all MMAs of a group's layer completed
+  uint32_t* slot;     // TMEM base address
+  int* s_ok;          // [2]: MMA issue of the group's current slot succeeded
+  int* s_okc;         // [2][kCopiers]: its copies of each class succeeded
+  volatile int* issued;  // layer slots whose MMAs were issued
+  volatile int* copied;  // [kCopiers]: layer slots whose copies of each class were issued
+  StreamPP* st;
+};
+__device__ __forceinline__ MlpSmemPP mlp_smem_pp(unsigned char* sm) {
+  MlpSmemPP S;
+  S.A[0] = sm;
+  S.A[1] = sm + kSmemA;
+  S.B = sm + 2 * kSmemA;
+  unsigned char* q = S.B + kStagesPP * kSmemBF;
+  S.w1 = reinterpret_cast<float4*>(q);
+  q += kSmemW1;
+  S.bias = reinterpret_cast<float*>(q);
+  q += kSmemBias;
+  S.ypart[0] = reinterpret_cast<float*>(q);
+  S.ypart[1] = reinterpret_cast<float*>(q + kSmemY);
+  q += 2 * kSmemY;
+  S.full = reinterpret_cast<uint64_t*>(q);
+  S.mdone = S.full + kStagesPP;
+  S.lbar = S.mdone + kStagesPP;
+  S.slot = reinterpret_cast<uint32_t*>(S.lbar + 2);
+  S.s_ok = reinterpret_cast<int*>(S.slot + 1);
+  S.s_okc = S.s_ok + 2;
+  S.issued = reinterpret_cast<volatile int*>(S.s_okc + 2 * kCopiers);
+  S.copied = S.issued + 1;
+  S.st = reinterpret_cast<StreamPP*>(q + 224);
+  return S;
+}
+static_assert(2 * kStagesPP * 8 + 2 * 8 + 4 + 8 + 8 * kCopiers + 4 + 4 * kCopiers <= 224,
+              "barrier block overlaps the stream state");
+static_assert(224 + sizeof(StreamPP) <= kSmemBarPP, "stream state outside its block");
+
+__device__ __forceinline__ void group_sync(int grp) {
+  asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(kGroupThreads) : "memory");
+}
+
+// bounded wait until *ctr == v (false and *err set if it did not come)
+__device__ __forceinline__ bool turn_wait(volatile int* ctr, int v, int32_t* err,
+                                          uint64_t timeout_ns = 2000000000ull) {
+  if (*ctr == v) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (*ctr != v) {
+    if (globaltimer_ns() - t0 > timeout_ns) {
+      set_error(err, DEV_BARRIER_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+// layer of slot s in the two-group order
+__device__ __forceinline__ int slot_layer(int s, int tail0) { return s < tail0 ? (s % 6) >> 1 : (s - tail0) % 3; }
+
+// the weights of layer l (a select, not an indexed local array)
+__device__ __forceinline__ const unsigned char* layer_weights(const unsigned char* const Wc[3], int l) {
+  return l == 0 ? Wc[0] : (l == 1 ? Wc[1] : Wc[2]);
+}
+__device__ __forceinline__ void copy_chunk_pp(const MlpSmemPP& S, const unsigned char* layer_w, int c) {
+  const int b = c & (kStagesPP - 1);
+  tc::mbar_arrive_expect_tx(S.full + b, kSmemBF);
+  tc::bulk_g2s(S.B + (size_t)b * kSmemBF, layer_w + (size_t)(c & (kChunksPerLayer - 1)) * kSmemBF, kSmemBF,
+               S.full + b);
+}
+
+// Setup over the CTA's `units` work units of `nsub` tiles each, split between
+// the groups (group 0 the even ones): TMEM (512 columns), mbarriers, the
+// stream state and its first kStagesPP copies, the first-layer table.
+// Every thread calls it.
+__device__ __forceinline__ uint32_t mlp_setup_pp(const MlpSmemPP& S, const float* __restrict__ P,
+                                                 const unsigned char* const Wc[3], int64_t units, int nsub) {
+  if ((threadIdx.x >> 5) == 0) {
+    tc::tmem_alloc(S.slot, 2 * kH);
+    tc::tmem_relinquish();
+  }
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < kStagesPP; ++b) {
+      tc::mbar_init(S.full + b, 1);
+      tc::mbar_init(S.mdone + b, 1);
+    }
+    tc::mbar_init(S.lbar, 1);
+    tc::mbar_init(S.lbar + 1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    StreamPP& st = *S.st;
+    st.total = (int32_t)(units * nsub * 3 * kChunksPerLayer);
+    st.tail0 = (int32_t)(6 * (units / 2) * nsub);
+    st.next_use = 0;
+    *S.issued = 0;
+    S.s_ok[0] = S.s_ok[1] = 1;
+    for (int q2 = 0; q2 < 2 * kCopiers; ++q2) S.s_okc[q2] = 1;
+    const unsigned char* w0 = layer_weights(Wc, slot_layer(0, st.tail0));
+    int c = 0;
+    for (; c < st.total && c < kStagesPP; ++c) copy_chunk_pp(S, w0, c);
+    for (int q2 = 0; q2 < kCopiers; ++q2) {
+      S.copied[q2] = 0;
+      st.next_copy[q2] = c + ((q2 - c) % kCopiers + kCopiers) % kCopiers;  // first chunk of class q2 not copied
+    }
+  }
+  for (int o = threadIdx.x; o < kH; o += blockDim.x) {
+    w1_table_entry(S.w1, P, o);
+    S.bias[o] = __ldg(P + kOffC2 + o);
+    S.bias[kH + o] = __ldg(P + kOffC3 + o);
+    S.bias[2 * kH + o] = __ldg(P + kOffC4 + o);
+    S.bias[3 * kH + o] = __ldg(P + kOffW5 + o);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  return *S.slot;
+}
+
+// End of both groups' tile loops (every thread calls it): thread 0 waits
+// (bounded) for copies that no MMA consumed, then TMEM is released.
+__device__ __forceinline__ void mlp_teardown_pp(const MlpSmemPP& S, uint32_t taddr, int32_t* err) {
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (threadIdx.x == 0) {
+    const StreamPP& st = *S.st;
+    int hi = st.next_copy[0];
+    for (int q2 = 1; q2 < kCopiers; ++q2) hi = st.next_copy[q2] > hi ? st.next_copy[q2] : hi;
+    for (int c = st.next_use; c < hi; ++c)
+      if (c < st.next_copy[c % kCopiers] &&
+          !tc::mbar_wait(S.full + (c & (kStagesPP - 1)), ((uint32_t)c / kStagesPP) & 1u, err, 200000000ull))
+        break;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(taddr, 2 * kH);
+}
+
+// MMAs of layer slot `slot` (group grp's thread 0): after the previous slot's
+// MMAs were issued, one MMA per chunk as it lands, a commit per chunk
+// (mdone: its buffer may be refilled) and one for the layer (lbar[grp]); the
+// turn is handed on before the bounded wait for the layer's MMAs.
+__device__ __forceinline__ bool tc_layer_issue_pp(const MlpSmemPP& S, int grp, uint32_t taddr_g, int slot,
+                                                  uint32_t& lphase, int32_t* err) {
+  if (!turn_wait(S.issued, slot, err)) return false;
+  __threadfence_block();
+  tc::fence_after_sync();
+  const uint64_t a0 = tc::smem_desc(tc::smem_addr(S.A[grp]), 128u, (uint32_t)kH * 16u);
+  const uint64_t b0 = tc::smem_desc(tc::smem_addr(S.B), 128u, (uint32_t)kKF * 16u);
+  const int c0 = slot * kChunksPerLayer;
+  for (int kc = 0; kc < kChunksPerLayer; ++kc) {
+    const int c = c0 + kc;
+    const int b = c & (kStagesPP - 1);
+    if (!tc::mbar_wait(S.full + b, ((uint32_t)c / kStagesPP) & 1u, err)) return false;
+    // descriptor start address in 16-byte units: K-slice kc of A is 256 bytes
+    // on, buffer b of the ring kSmemBF bytes on
+    tc::mma_bf16(taddr_g, a0 + (uint64_t)(kc * (kKF * 16 / 16)), b0 + (uint64_t)(b * (kSmemBF / 16)), kIdesc,
+                 kc != 0);
+    tc::mma_commit(S.mdone + b);
+  }
+  tc::mma_commit(S.lbar + grp);
+  S.st->next_use = c0 + kChunksPerLayer;
+  __threadfence_block();
+  *S.issued = slot + 1;
+  const bool ok = tc::mbar_wait(S.lbar + grp, lphase, err);
+  lphase ^= 1u;
+  return ok;
+}
+
+// Copies of layer slot `slot`, chunks of class par = c mod kCopiers (group
+// grp's thread kCopierLane (1 + par)): after the same class's copier of the
+// previous slot, chunk u + kStagesPP into buffer u's slot as soon as MMA u
+// (u in this slot) completed. A class's chunks live in its own buffers only,
+// so each buffer sees its mbarrier phases in order.
+__device__ __forceinline__ bool copy_slot_pp(const MlpSmemPP& S, const unsigned char* const Wc[3], int slot, int par,
+                                             int32_t* err) {
+  if (!turn_wait(S.copied + par, slot, err)) return false;
+  __threadfence_block();
+  StreamPP& st = *S.st;
+  const int c0 = slot * kChunksPerLayer;
+  const int total = st.total;
+  // chunks c0 + kStagesPP .. c0 + 15 belong to this slot's layer, the rest
+  // to the next slot's
+  const unsigned char* w_this = layer_weights(Wc, slot_layer(slot, st.tail0));
+  const unsigned char* w_next = layer_weights(Wc, slot_layer(slot + 1, st.tail0));
+  for (int kc = par; kc < kChunksPerLayer; kc += kCopiers) {
+    const int u = c0 + kc;  // the MMA whose buffer the next chunk reuses
+    const int c = u + kStagesPP;
+    if (c >= total) break;
+    if (!tc::mbar_wait(S.mdone + (u & (kStagesPP - 1)), ((uint32_t)u / kStagesPP) & 1u, err)) return false;
+    copy_chunk_pp(S, kc + kStagesPP < kChunksPerLayer ? w_this : w_next, c);
+    st.next_copy[par] = c + kCopiers;
+  }
+  __threadfence_block();
+  S.copied[par] = slot + 1;
+  return true;
+}
+
+// The network on group grp's 128-row tile (lt = thread index in the group):
+// the arithmetic of mlp_tile, layer slots slot0, slot0 + step, slot0 + 2 step.
+// hook(lt) runs on the group's other threads while the first layer's MMAs
+// are issued and computed (the caller's prefetch of its next tile).
+template <class Hook>
+__device__ __forceinline__ bool mlp_tile_pp(const MlpSmemPP& S, const float* __restrict__ P,
+                                            const unsigned char* const Wc[3], int grp, int lt, const float x[3],
+                                            uint32_t taddr, uint32_t& lphase, int64_t slot0, int step,
+                                            int32_t* err, float& y_out, Hook&& hook) {
+  constexpr int kCols = kH / kTPR;
+  const int row = lt & (kTileM - 1);
+  const int half = lt / kTileM;
+  const int c0 = half * kCols;
+  const uint32_t tcol = taddr + (uint32_t)(grp * kH);
+  const uint32_t trow = tcol + ((uint32_t)(32 * ((lt >> 5) & 3)) << 16);
+  unsigned char* A = S.A[grp];
+  for (int o = c0; o < c0 + kCols; o += 8) {
+    float h[8];
+    layer1_outputs8(S.w1, o, x, h);
+    store_bf16x8(A + tc::kmajor_offset(row, o, kH), h);
+  }
+  tc::fence_async_smem();
+  group_sync(grp);
+  float y = 0.f;
+  for (int l = 0; l < 3; ++l) {
+    const int slot = (int)(slot0 + (int64_t)l * step);
+    if (lt == 0) {
+      S.s_ok[grp] = tc_layer_issue_pp(S, grp, tcol, slot, lphase, err);
+    } else if (lt % kCopierLane == 0 && lt <= kCopierLane * kCopiers) {
+      const int par = lt / kCopierLane - 1;
+      S.s_okc[grp * kCopiers + par] = copy_slot_pp(S, Wc, slot, par, err);
+    } else if (l == 0) {
+      hook(lt);
+    }
+    group_sync(grp);
+    tc::fence_after_sync();
+    bool good = S.s_ok[grp];
+#pragma unroll
+    for (int q = 0; q < kCopiers; ++q) good = good && S.s_okc[grp * kCopiers + q];
+    if (!good) return false;
+    uint32_t ra[32], rb[32];
+    tc::tmem_ld32_issue(trow + (uint32_t)c0, ra);
+    tc::tmem_ld_wait();
+#pragma unroll 1
+    for (int cc = c0; cc < c0 + kCols; cc += 64) {
+      tc::tmem_ld32_issue(trow + (uint32_t)(cc + 32), rb);
+      tile_columns_a(A, S.bias, l, row, cc, ra, y);
+      tc::tmem_ld_wait();
+      if (cc + 64 < c0 + kCols) tc::tmem_ld32_issue(trow + (uint32_t)(cc + 64), ra);
+      tile_columns_a(A, S.bias, l, row, cc + 32, rb, y);
+      tc::tmem_ld_wait();
+    }
+    if (l == 2) S.ypart[grp][half * kTileM + row] = y;
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    group_sync(grp);
+    tc::fence_after_sync();
+  }
+  float yy = S.ypart[grp][row];
+#pragma unroll
+  for (int h = 1; h < kTPR; ++h) yy += S.ypart[grp][h * kTileM + row];
   y_out = yy + __ldg(P + kOffC5);
   return true;
 }

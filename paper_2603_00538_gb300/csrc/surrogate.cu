@@ -3,24 +3,26 @@
 // surrogate network instead of a mesh location, plus a per-element exact
 // fallback, and the training set drawn from the exact source.
 //
-// Fused assembly kernel, one 128-thread CTA per SM, persistent over tiles of
-// 128 samples (thread r owns sample row r):
+// Fused assembly kernels, persistent over tiles of 128 samples (a row per
+// sample):
 //   Philox -> barycentrics -> X (FP32)  ->  network on the tensor cores
-//   (tcgen05, FP32 accumulation in tensor memory)  ->  exact subsample test
-//   ->  residual r = f - alpha sum_m g_m lambda_m  ->  r lambda_i partials
-//   ->  warp-segmented compensated sums  ->  per-element epilogue + FP64
-//   atomics into b.
+//   (tcgen05, FP32 accumulation in tensor memory) or an exact query  ->
+//   residual r = f - alpha sum_m g_m lambda_m  ->  r lambda_i partials  ->
+//   warp-segmented compensated sums  ->  per-element epilogue + FP64 atomics
+//   into b.
+// k_surrogate_net (one CTA of two 256-thread groups per SM) runs the network
+// tiles, k_surrogate_exact (128 threads, many CTAs per SM) the exact ones.
 // Tiles hold EPB = floor(128/N) whole elements when N <= 128; an element with
-// N > 128 samples spans ceil(N/128) consecutive tiles of one CTA.
+// N > 128 samples spans ceil(N/128) consecutive tiles of one group or CTA.
 //
 // Fallback: the first s samples of every element are also queried exactly
 // (a location of X's first d_s coordinates in the exact source mesh). If any
 // of them differs from the network by more than tau (or is not finite), the
 // whole element uses exact queries for all N samples. The decision is taken
 // first, for all elements (k_sub_points, the standalone network forward,
-// k_decide, k_split); the fused kernel then runs twice over element lists:
-// with the network over the elements that keep it, and with exact queries
-// alone over the elements that fall back (their s subsample values reused).
+// k_decide, k_split); then k_surrogate_net runs over the elements that keep
+// the network and k_surrogate_exact over the elements that fall back (their
+// s subsample values reused).
 // So no network tile is spent on a sample whose value is thrown away, and
 // the exact queries of the fallbacks run at the full width of the GPU.
 #include <algorithm>
@@ -47,10 +49,8 @@ struct SurParams {
   Strat st;              // sampling scheme
 };
 
-// shared memory: [network tile (NET only)] + per-row partial pieces +
-// per-element fallback flags
-constexpr uint32_t kSmemPieces = kTileM * 8 * 4 + kTileM * 4;
-constexpr uint32_t kSmemSur = kSmemFwd + kSmemPieces;
+// shared memory of the exact-query pass: per-row partial pieces
+constexpr uint32_t kSmemPieces = kTileM * 8 * 4;
 
 template <int DS>
 __device__ __forceinline__ float exact_value(const GridP<float>& gr, const int32_t* __restrict__ cell_start,
@@ -77,12 +77,13 @@ __device__ __forceinline__ float exact_value(const GridP<float>& gr, const int32
   return v;
 }
 
-// NET = false: every query exact (the plain mesh-query transfer on the same
-// sampler and launch shape, the comparison point of the surrogate).
-template <int DT, int DS, bool NET>
-__global__ void __launch_bounds__(NET ? kTPR * kTileM : kTileM, NET ? 2 : 8) k_surrogate_assemble(
-    const float* __restrict__ P, const unsigned char* __restrict__ W2, const unsigned char* __restrict__ W3,
-    const unsigned char* __restrict__ W4, const float* __restrict__ tx, const int32_t* __restrict__ tconn,
+// The exact-query pass: the elements that fall back (their decision
+// subsample's values reused), or every element when there is no network (the
+// plain mesh-query transfer on the same sampler, the comparison point of the
+// surrogate). One thread per sample row of a 128-row tile.
+template <int DT, int DS>
+__global__ void __launch_bounds__(kTileM, 8) k_surrogate_exact(
+    const float* __restrict__ tx, const int32_t* __restrict__ tconn,
     const float* __restrict__ vol32, const float* __restrict__ g, const GridP<float>* __restrict__ gp,
     const int32_t* __restrict__ cell_start, const int32_t* __restrict__ cell_items,
     const int32_t* __restrict__ cell_first, const float* __restrict__ recs,
@@ -90,31 +91,18 @@ __global__ void __launch_bounds__(NET ? kTPR * kTileM : kTileM, NET ? 2 : 8) k_s
     float* __restrict__ sample_f, int64_t* __restrict__ counters, int32_t* err) {
   constexpr int K = DT + 1;
   extern __shared__ __align__(1024) unsigned char sm[];
-  MlpSmem S = mlp_smem(sm);
-  constexpr uint32_t off = NET ? kSmemFwd : 0;
-  float(*piece)[8] = reinterpret_cast<float(*)[8]>(sm + off);  // [row][s_i, e_i]
-  int* s_flag = reinterpret_cast<int*>(sm + off + kTileM * 8 * 4);
+  float(*piece)[8] = reinterpret_cast<float(*)[8]>(sm);  // [row][s_i, e_i]
   const int lane = threadIdx.x & 31;
-  uint32_t taddr = 0;
-  const unsigned char* const Wc[3] = {W2, W3, W4};
-  WStream ws;
-  if (NET) taddr = mlp_setup(S, P, Wc, cta_tiles(p.nunits) * p.nsub, ws);
   GridP<float> gr;
   if (p.has_exact) gr = *gp;
-  uint32_t phase = 0;
-  bool ok = true;
-  int64_t n_exact = 0, n_fb = 0;
+  int64_t n_exact = 0;
   int n_empty = 0;
   Acc<float> acc_long;  // N > 128: thread i < K carries node i's sum over the element's tiles
-  // with the network on, threads 128..255 only help with the network (the
-  // second column half); the sample rows belong to threads 0..127
   const int row = threadIdx.x & (kTileM - 1);
   const bool lead = threadIdx.x < kTileM;
 
-  for (int64_t unit = blockIdx.x; ok && unit < p.nunits; unit += gridDim.x) {
-    if (lead) s_flag[row] = NET ? 0 : 1;
+  for (int64_t unit = blockIdx.x; unit < p.nunits; unit += gridDim.x) {
     acc_long = Acc<float>();
-    __syncthreads();
     for (int c = 0; c < p.nsub; ++c) {
       int el, j;
       int64_t t;
@@ -150,12 +138,12 @@ __global__ void __launch_bounds__(NET ? kTPR * kTileM : kTileM, NET ? 2 : 8) k_s
         sample_lambda<DT, float>(w, j, p.st, lam);
         map_point<DT, float>(lam, xv, X);
       }
-      // exact subsample (or every query when the network is off; the
-      // fallback pass takes the subsample's values from the decision pass)
+      // exact queries (the fallback pass takes the subsample's values from
+      // the decision pass)
       float fe = 0.f;
-      const bool sub = lead && p.has_exact && valid && (!NET || j < p.s);
+      const bool sub = lead && p.has_exact && valid;
       if (sub) {
-        if (!NET && p.sub_f && j < p.s) {
+        if (p.sub_f && j < p.s) {
           fe = __ldg(p.sub_f + t * p.s + j);
         } else {
           fe = exact_value<DS>(gr, cell_start, cell_items, cell_first, recs, adj, vals, p.nes, p.exact_field, X, n_empty,
@@ -163,27 +151,8 @@ __global__ void __launch_bounds__(NET ? kTPR * kTileM : kTileM, NET ? 2 : 8) k_s
           ++n_exact;
         }
       }
-      float f = fe;
-      if (NET) {
-        const float x3[3] = {X[0], X[1], DT == 3 ? X[DT - 1] : 0.f};
-        float y = 0.f;
-        ok = mlp_tile(S, P, Wc, ws, x3, taddr, phase, err, y);
-        if (!ok) break;
-        if (sub && !(fabsf(y - fe) <= p.tau)) s_flag[el] = 1;
-        __syncthreads();
-        const bool fb = s_flag[el] != 0;
-        if (fb && lead && valid && !sub) {
-          fe = exact_value<DS>(gr, cell_start, cell_items, cell_first, recs, adj, vals, p.nes, p.exact_field, X, n_empty, p.exact_cost);
-          ++n_exact;
-        }
-        f = fb ? fe : y;
-        if (lead && valid && c == 0 && j == 0) {
-          n_fb += fb;
-          if (fb_out) fb_out[t] = fb ? 1 : 0;
-        }
-      } else if (valid && c == 0 && j == 0 && fb_out) {
-        fb_out[t] = 1;
-      }
+      const float f = fe;
+      if (valid && c == 0 && j == 0 && fb_out) fb_out[t] = 1;
       if (lead && valid && sample_f) sample_f[t * p.N + j] = f;
 
       // residual against the P1 control and its basis-weighted partials
@@ -268,19 +237,17 @@ __global__ void __launch_bounds__(NET ? kTPR * kTileM : kTileM, NET ? 2 : 8) k_s
           atomicAdd(b + vv[i], Epi<float>::contrib(__ldg(vol32 + tu), 0.0, p.cdet, p.cmc, gsum, gv[i], acc_long));
         }
       }
-      __syncthreads();  // pieces and flags are reused by the next tile
+      __syncthreads();  // pieces are reused by the next tile
     }
   }
   if (counters) {
-    const int64_t e1 = warp_sum<int64_t>(n_exact), f1 = warp_sum<int64_t>(n_fb);
+    const int64_t e1 = warp_sum<int64_t>(n_exact);
     const int m1 = warp_sum<int>(n_empty);
     if (lane == 0) {
       if (e1) atomicAdd(reinterpret_cast<unsigned long long*>(counters), (unsigned long long)e1);
-      if (f1) atomicAdd(reinterpret_cast<unsigned long long*>(counters + 1), (unsigned long long)f1);
       if (m1) atomicAdd(reinterpret_cast<unsigned long long*>(counters + 2), (unsigned long long)m1);
     }
   }
-  if (NET) mlp_teardown(S, taddr, ws, err);
 }
 
 // Fallback decision, before any network tile of the assembly runs:
@@ -409,31 +376,285 @@ __global__ void k_dataset(int64_t n, PhiloxKey key, uint32_t stream_id, float3 l
   }
 }
 
+// The network pass (the elements that keep the network; no exact queries):
+// one CTA per SM, two groups of 256 threads, each running the tile loop over
+// its share of the CTA's units (group 0 the even ones) with the two-group
+// forward tile (mlp_tile_pp): the groups' layers alternate on the tensor
+// cores, so one group's sampling, epilogues and scatter overlap the other's
+// MMAs. The network values are those of the standalone forward bit for bit;
+// partials and epilogue follow k_surrogate_exact's with the network value in
+// place of the exact one.
+constexpr uint32_t kSmemPiecesPP = 2 * kTileM * 8 * 4;
+// An element's inputs to its tile rows and its scatter, fetched by one
+// thread while the group waits for the previous tile's first-layer MMAs
+// (the dependent loads list -> connectivity -> vertices / control values no
+// longer stall the group). Used when a tile holds at most kPfMax elements.
+struct EPre {
+  int32_t t;        // element, -1: none
+  int32_t v[4];
+  float xv[4][3];
+  float gv[4];
+  float vol;
+  int32_t pad[2];
+};
+constexpr int kPfMax = 8;
+constexpr int kPfLane = 192;  // group threads 192 .. 192 + EPB - 1 (warp 6: no issuer, no copier)
+static_assert(kPfLane % 32 == 0 && kPfLane > kCopierLane * kCopiers && kPfLane + kPfMax <= kGroupThreads,
+              "prefetch threads");
+constexpr uint32_t kSmemPrePP = 2 * 2 * kPfMax * sizeof(EPre);
+constexpr uint32_t kSmemSurPP = kSmemPP + kSmemPiecesPP + kSmemPrePP;
+
+template <int DT>
+__device__ __forceinline__ void pf_element(EPre& e, const SurParams& p, int64_t unit, int el,
+                                           const int32_t* __restrict__ tconn, const float* __restrict__ tx,
+                                           const float* __restrict__ g, const float* __restrict__ vol32) {
+  constexpr int K = DT + 1;
+  const int64_t k = unit * p.EPB + el;
+  if (unit >= p.nunits || k >= p.nlist) {
+    e.t = -1;
+    return;
+  }
+  const int64_t t = p.elist ? (int64_t)__ldg(p.elist + k) : k;
+  int32_t v[K];
+#pragma unroll
+  for (int m = 0; m < K; ++m) v[m] = __ldg(tconn + t * K + m);
+#pragma unroll
+  for (int m = 0; m < K; ++m) {
+#pragma unroll
+    for (int a = 0; a < DT; ++a) e.xv[m][a] = __ldg(tx + (int64_t)v[m] * DT + a);
+    e.gv[m] = __ldg(g + v[m]);
+    e.v[m] = v[m];
+  }
+  e.vol = __ldg(vol32 + t);
+  e.t = (int32_t)t;
+}
+static_assert(kSmemSurPP <= 227u * 1024u, "two-group tile exceeds the shared memory of one CTA");
+
+template <int DT>
+__global__ void __launch_bounds__(2 * kGroupThreads, 1) k_surrogate_net(
+    const float* __restrict__ P, const unsigned char* __restrict__ W2, const unsigned char* __restrict__ W3,
+    const unsigned char* __restrict__ W4, const float* __restrict__ tx, const int32_t* __restrict__ tconn,
+    const float* __restrict__ vol32, const float* __restrict__ g, SurParams p, double* __restrict__ b,
+    int32_t* __restrict__ fb_out, float* __restrict__ sample_f, int32_t* err) {
+  constexpr int K = DT + 1;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const MlpSmemPP S = mlp_smem_pp(sm);
+  const int grp = threadIdx.x / kGroupThreads;
+  const int lt = threadIdx.x - grp * kGroupThreads;
+  float(*piece)[8] = reinterpret_cast<float(*)[8]>(sm + kSmemPP + (uint32_t)grp * kTileM * 8 * 4);
+  const int lane = threadIdx.x & 31;
+  const unsigned char* const Wc[3] = {W2, W3, W4};
+  const int64_t units = cta_tiles(p.nunits);
+  const uint32_t taddr = mlp_setup_pp(S, P, Wc, units, p.nsub);
+  uint32_t lphase = 0;
+  bool ok = true;
+  Acc<float> acc_long;  // N > 128: thread i < K of the group carries node i's sum over the element's tiles
+  const int row = lt & (kTileM - 1);
+  const bool lead = lt < kTileM;
+  const int64_t J1 = (units / 2) * p.nsub;  // tiles of each group that have a partner
+  const bool usepf = p.nsub == 1 && p.EPB <= kPfMax;
+  EPre* pre = reinterpret_cast<EPre*>(sm + kSmemPP + kSmemPiecesPP) + grp * 2 * kPfMax;  // [2][kPfMax]
+  if (usepf) {  // the group's first tile
+    if (lt >= kPfLane && lt < kPfLane + p.EPB)
+      pf_element<DT>(pre[lt - kPfLane], p, blockIdx.x + (int64_t)grp * gridDim.x, lt - kPfLane, tconn, tx, g, vol32);
+    group_sync(grp);
+  }
+
+  for (int64_t kk = grp; ok && kk < units; kk += 2) {
+    const int64_t unit = blockIdx.x + kk * gridDim.x;
+    acc_long = Acc<float>();
+    for (int c = 0; c < p.nsub; ++c) {
+      const int64_t jt = (kk / 2) * p.nsub + c;
+      const int64_t slot0 = jt < J1 ? 6 * jt + grp : 6 * J1 + 3 * (jt - J1);
+      const int step = jt < J1 ? 2 : 1;
+      const int cur = (int)(jt & 1);
+      int el, j;
+      int64_t t;
+      bool valid;
+      const EPre* ep = nullptr;
+      if (usepf) {
+        el = row / p.N;
+        j = row - el * p.N;
+        ep = pre + cur * kPfMax + (el < p.EPB ? el : 0);
+        valid = el < p.EPB && ep->t >= 0;
+        t = ep->t;
+      } else if (p.nsub == 1) {
+        el = row / p.N;
+        j = row - el * p.N;
+        const int64_t k = unit * p.EPB + el;
+        valid = el < p.EPB && k < p.nlist;
+        t = valid && p.elist ? (int64_t)__ldg(p.elist + k) : k;
+      } else {
+        el = 0;
+        j = c * kTileM + row;
+        t = p.elist ? (int64_t)__ldg(p.elist + unit) : unit;
+        valid = j < p.N;
+      }
+      float lam[K], X[DT];
+      int32_t v[K];
+#pragma unroll
+      for (int m = 0; m < K; ++m) { lam[m] = 0.f; v[m] = 0; }
+#pragma unroll
+      for (int a = 0; a < DT; ++a) X[a] = 0.f;
+      float gvr[K];
+      if (valid) {
+        float xv[K][DT];
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+          if (usepf) {
+            v[m] = ep->v[m];
+            gvr[m] = ep->gv[m];
+#pragma unroll
+            for (int a = 0; a < DT; ++a) xv[m][a] = ep->xv[m][a];
+          } else {
+            v[m] = __ldg(tconn + t * K + m);
+            gvr[m] = __ldg(g + v[m]);
+#pragma unroll
+            for (int a = 0; a < DT; ++a) xv[m][a] = __ldg(tx + (int64_t)v[m] * DT + a);
+          }
+        }
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)(DT == 2 ? (j >> 1) : j), (uint32_t)t, p.stream_id, 0u),
+                                      p.key);
+        sample_lambda<DT, float>(w, j, p.st, lam);
+        map_point<DT, float>(lam, xv, X);
+      }
+      const float x3[3] = {X[0], X[1], DT == 3 ? X[DT - 1] : 0.f};
+      float f = 0.f;
+      // while the first layer's MMAs run, threads kPfLane.. fetch the
+      // elements of the group's next tile into the other buffer
+      const int64_t unit_next = blockIdx.x + (kk + 2) * gridDim.x;
+      EPre* nxt = pre + (cur ^ 1) * kPfMax;
+      ok = mlp_tile_pp(S, P, Wc, grp, lt, x3, taddr, lphase, slot0, step, err, f, [&](int q) {
+        if (usepf && q >= kPfLane && q < kPfLane + p.EPB)
+          pf_element<DT>(nxt[q - kPfLane], p, unit_next, q - kPfLane, tconn, tx, g, vol32);
+      });
+      if (!ok) break;
+      if (fb_out && lead && valid && c == 0 && j == 0) fb_out[t] = 0;
+      if (lead && valid && sample_f) sample_f[t * p.N + j] = f;
+
+      // residual against the P1 control and its basis-weighted partials
+      Acc<float> a[K];
+      const bool mine = lead && valid;
+      if (mine) {
+        float gX = __fmul_rn(gvr[0], lam[0]);
+#pragma unroll
+        for (int m = 1; m < K; ++m) gX = __fmaf_rn(gvr[m], lam[m], gX);
+        const float r = __fsub_rn(f, __fmul_rn(p.alpha, gX));
+#pragma unroll
+        for (int i = 0; i < K; ++i) a[i].add(__fmul_rn(r, lam[i]));
+      }
+      // warp-segmented suffix combine over rows of the same element
+      const int seg = mine ? el : -1;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int seg2 = __shfl_down_sync(0xffffffffu, seg, o);
+        const bool take = lane + o < 32 && seg2 == seg;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          const float s2 = __shfl_down_sync(0xffffffffu, a[i].s, o);
+          const float e2 = __shfl_down_sync(0xffffffffu, a[i].e, o);
+          if (take) a[i].combine(s2, e2);
+        }
+      }
+      const int seg_prev = __shfl_up_sync(0xffffffffu, seg, 1);
+      const bool head = mine && (lane == 0 || seg_prev != seg);
+      if (head) {
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          piece[row][2 * i] = a[i].s;
+          piece[row][2 * i + 1] = a[i].e;
+        }
+      }
+      group_sync(grp);
+      // combine the pieces of each element (heads at its first row and at
+      // every warp boundary inside it), in row order
+      if (p.nsub == 1) {
+        for (int q = lt; q < p.EPB * K; q += kGroupThreads) {
+          const int e2 = q / K, i = q - e2 * K;
+          const int64_t k2 = unit * p.EPB + e2;
+          if (k2 >= p.nlist) continue;
+          const EPre& e = pre[cur * kPfMax + (e2 < kPfMax ? e2 : 0)];
+          const int64_t t2 = usepf ? (int64_t)e.t : (p.elist ? (int64_t)__ldg(p.elist + k2) : k2);
+          const int r0 = e2 * p.N, r1 = r0 + p.N;
+          Acc<float> acc;
+          for (int hr = r0; hr < r1; hr = (hr & ~31) + 32) acc.combine(piece[hr][2 * i], piece[hr][2 * i + 1]);
+          int32_t vv[K];
+          float gv[K];
+#pragma unroll
+          for (int m = 0; m < K; ++m) {
+            vv[m] = usepf ? e.v[m] : __ldg(tconn + t2 * K + m);
+            gv[m] = usepf ? e.gv[m] : __ldg(g + vv[m]);
+          }
+          float gsum = gv[0];
+#pragma unroll
+          for (int m = 1; m < K; ++m) gsum = __fadd_rn(gsum, gv[m]);
+          float gi = gv[0];
+#pragma unroll
+          for (int m = 1; m < K; ++m) gi = i == m ? gv[m] : gi;
+          int32_t vi = vv[0];
+#pragma unroll
+          for (int m = 1; m < K; ++m) vi = i == m ? vv[m] : vi;
+          atomicAdd(b + vi, Epi<float>::contrib(usepf ? e.vol : __ldg(vol32 + t2), 0.0, p.cdet, p.cmc, gsum, gi, acc));
+        }
+      } else if (lt < K) {
+        const int i = lt;
+        const int nrow = min(kTileM, p.N - c * kTileM);
+        for (int hr = 0; hr < nrow; hr += 32) acc_long.combine(piece[hr][2 * i], piece[hr][2 * i + 1]);
+        if (c == p.nsub - 1) {
+          const int64_t tu = p.elist ? (int64_t)__ldg(p.elist + unit) : unit;
+          int32_t vv[K];
+          float gv[K];
+#pragma unroll
+          for (int m = 0; m < K; ++m) {
+            vv[m] = __ldg(tconn + tu * K + m);
+            gv[m] = __ldg(g + vv[m]);
+          }
+          float gsum = gv[0];
+#pragma unroll
+          for (int m = 1; m < K; ++m) gsum = __fadd_rn(gsum, gv[m]);
+          atomicAdd(b + vv[i], Epi<float>::contrib(__ldg(vol32 + tu), 0.0, p.cdet, p.cmc, gsum, gv[i], acc_long));
+        }
+      }
+      group_sync(grp);  // pieces are reused by the group's next tile
+    }
+  }
+  mlp_teardown_pp(S, taddr, err);
+}
+
 template <int DT, int DS, bool NET>
 static sft_status launch_sur(sft_mlp_s* m, sft_source_s* s, sft_target_s* t, const SurParams& p, const float* g,
                              double* b, int32_t* fb, float* sf, int64_t* counters, int32_t* err, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    SFT_CUDA(cudaFuncSetAttribute(k_surrogate_assemble<DT, DS, NET>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kSmemSur));
-    attr = true;
-  }
   int dev = 0, sms = 0;
   SFT_CUDA(cudaGetDevice(&dev));
   SFT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  // network on: two CTAs per SM (about 106 KB of shared memory and 256 TMEM
-  // columns each);
-  // exact queries only: latency-bound location work, many CTAs per SM
-  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(p.nunits, (int64_t)sms * (NET ? 2 : 16)));
-  const Locator* L = s ? &s->loc[SFT_PREC_FP32] : nullptr;
-  ::sft::note_launch(), k_surrogate_assemble<DT, DS, NET><<<grid, NET ? kTPR * kTileM : kTileM, NET ? kSmemSur : kSmemPieces, st>>>(
-      m ? m->P : nullptr, m ? m->Wc[0] : nullptr, m ? m->Wc[1] : nullptr, m ? m->Wc[2] : nullptr,
-      (const float*)t->coordsP[SFT_PREC_FP32], t->conn, t->vol32, g, L ? (const GridP<float>*)L->grid : nullptr,
-      L ? L->cell_start : nullptr, L ? L->cell_items : nullptr, L ? L->cell_first : nullptr,
-      L ? (const float*)L->recs : nullptr,
-      L ? L->adj : nullptr, L ? (const float*)L->vals : nullptr, p, b, fb, sf, counters, err);
-  SFT_CUDA(cudaGetLastError());
-  return SFT_OK;
+  if constexpr (NET) {
+    // the network pass: one two-group CTA per SM (about 218 KB of shared
+    // memory and all 512 TMEM columns)
+    static bool attr = false;
+    if (!attr) {
+      SFT_CUDA(cudaFuncSetAttribute(k_surrogate_net<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kSmemSurPP));
+      attr = true;
+    }
+    if (p.has_exact) return fail(SFT_ERR_UNSUPPORTED, "network pass with exact queries");
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(p.nunits, (int64_t)sms));
+    ::sft::note_launch(), k_surrogate_net<DT><<<grid, 2 * kGroupThreads, kSmemSurPP, st>>>(
+        m->P, m->Wc[0], m->Wc[1], m->Wc[2], (const float*)t->coordsP[SFT_PREC_FP32], t->conn, t->vol32, g, p, b, fb,
+        sf, err);
+    SFT_CUDA(cudaGetLastError());
+    return SFT_OK;
+  } else {
+    // exact queries only: latency-bound location work, many CTAs per SM
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(p.nunits, (int64_t)sms * 16));
+    const Locator* L = s ? &s->loc[SFT_PREC_FP32] : nullptr;
+    ::sft::note_launch(), k_surrogate_exact<DT, DS><<<grid, kTileM, kSmemPieces, st>>>(
+        (const float*)t->coordsP[SFT_PREC_FP32], t->conn, t->vol32, g,
+        L ? (const GridP<float>*)L->grid : nullptr, L ? L->cell_start : nullptr, L ? L->cell_items : nullptr,
+        L ? L->cell_first : nullptr, L ? (const float*)L->recs : nullptr, L ? L->adj : nullptr,
+        L ? (const float*)L->vals : nullptr, p, b, fb, sf, counters, err);
+    SFT_CUDA(cudaGetLastError());
+    return SFT_OK;
+  }
 }
 
 }  // namespace sft

@@ -51,15 +51,18 @@ def test_clock_summary_unsampled():
 def test_traffic_record_tracks_kernel_sources():
     h = bench.kernel_hash()
     assert len(h) == 16
-    rec = {}
+    recs = {}
     for line in open(bench.TRAFFIC_FILE):
         if line.startswith("workload="):
             rec = dict(kv.split("=", 1) for kv in line.split())
-    t = bench.measured_traffic("tri4m")
-    if rec.get("kernel_hash") == h:
-        assert t == float(rec["dram_bytes_per_launch"])
-    else:
-        assert t is None                          # stale record: reported as null
+            recs[rec["workload"]] = rec
+    assert {"tri4m", "tet5m"} <= set(recs)
+    for w, rec in recs.items():
+        t = bench.measured_traffic(w)
+        if rec.get("kernel_hash") == h:
+            assert t == float(rec["dram_bytes_per_launch"])
+        else:
+            assert t is None                      # stale record: reported as null
     assert bench.measured_traffic("no-such-workload") is None
 
 
