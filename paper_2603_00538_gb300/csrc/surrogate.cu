@@ -384,7 +384,6 @@ __global__ void k_dataset(int64_t n, PhiloxKey key, uint32_t stream_id, float3 l
 // MMAs. The network values are those of the standalone forward bit for bit;
 // partials and epilogue follow k_surrogate_exact's with the network value in
 // place of the exact one.
-constexpr uint32_t kSmemPiecesPP = 2 * kTileM * 8 * 4;
 // An element's inputs to its tile rows and its scatter, fetched by one
 // thread while the group waits for the previous tile's first-layer MMAs
 // (the dependent loads list -> connectivity -> vertices / control values no
@@ -402,7 +401,7 @@ constexpr int kPfLane = 192;  // group threads 192 .. 192 + EPB - 1 (warp 6: no 
 static_assert(kPfLane % 32 == 0 && kPfLane > kCopierLane * kCopiers && kPfLane + kPfMax <= kGroupThreads,
               "prefetch threads");
 constexpr uint32_t kSmemPrePP = 2 * 2 * kPfMax * sizeof(EPre);
-constexpr uint32_t kSmemSurPP = kSmemPP + kSmemPiecesPP + kSmemPrePP;
+constexpr uint32_t kSmemSurPP = kSmemPP + kSmemPrePP;
 
 template <int DT>
 __device__ __forceinline__ void pf_element(EPre& e, const SurParams& p, int64_t unit, int el,
@@ -441,19 +440,17 @@ __global__ void __launch_bounds__(2 * kGroupThreads, 1) k_surrogate_net(
   const MlpSmemPP S = mlp_smem_pp(sm);
   const int grp = threadIdx.x / kGroupThreads;
   const int lt = threadIdx.x - grp * kGroupThreads;
-  float(*piece)[8] = reinterpret_cast<float(*)[8]>(sm + kSmemPP + (uint32_t)grp * kTileM * 8 * 4);
   const int lane = threadIdx.x & 31;
   const unsigned char* const Wc[3] = {W2, W3, W4};
   const int64_t units = cta_tiles(p.nunits);
   const uint32_t taddr = mlp_setup_pp(S, P, Wc, units, p.nsub);
   uint32_t lphase = 0;
   bool ok = true;
-  Acc<float> acc_long;  // N > 128: thread i < K of the group carries node i's sum over the element's tiles
   const int row = lt & (kTileM - 1);
   const bool lead = lt < kTileM;
   const int64_t J1 = (units / 2) * p.nsub;  // tiles of each group that have a partner
   const bool usepf = p.nsub == 1 && p.EPB <= kPfMax;
-  EPre* pre = reinterpret_cast<EPre*>(sm + kSmemPP + kSmemPiecesPP) + grp * 2 * kPfMax;  // [2][kPfMax]
+  EPre* pre = reinterpret_cast<EPre*>(sm + kSmemPP) + grp * 2 * kPfMax;  // [2][kPfMax]
   if (usepf) {  // the group's first tile
     if (lt >= kPfLane && lt < kPfLane + p.EPB)
       pf_element<DT>(pre[lt - kPfLane], p, blockIdx.x + (int64_t)grp * gridDim.x, lt - kPfLane, tconn, tx, g, vol32);
@@ -462,7 +459,6 @@ __global__ void __launch_bounds__(2 * kGroupThreads, 1) k_surrogate_net(
 
   for (int64_t kk = grp; ok && kk < units; kk += 2) {
     const int64_t unit = blockIdx.x + kk * gridDim.x;
-    acc_long = Acc<float>();
     for (int c = 0; c < p.nsub; ++c) {
       const int64_t jt = (kk / 2) * p.nsub + c;
       const int64_t slot0 = jt < J1 ? 6 * jt + grp : 6 * J1 + 3 * (jt - J1);
@@ -558,64 +554,23 @@ __global__ void __launch_bounds__(2 * kGroupThreads, 1) k_surrogate_net(
       }
       const int seg_prev = __shfl_up_sync(0xffffffffu, seg, 1);
       const bool head = mine && (lane == 0 || seg_prev != seg);
+      // each warp segment's head adds its share |T| / N sum_j r_j lambda_i
+      // into b; the head of the element's first sample also adds the control
+      // term (the FP32 epilogue of the exact pass, split over the segments:
+      // no shared-memory pieces and no block barrier between tiles)
       if (head) {
+        const float volf = usepf ? ep->vol : __ldg(vol32 + t);
+        float gsum = gvr[0];
+#pragma unroll
+        for (int m = 1; m < K; ++m) gsum = __fadd_rn(gsum, gvr[m]);
+        const float wc = __fmul_rn(volf, p.cmc);
 #pragma unroll
         for (int i = 0; i < K; ++i) {
-          piece[row][2 * i] = a[i].s;
-          piece[row][2 * i + 1] = a[i].e;
+          const double add = j == 0 ? Epi<float>::contrib(volf, 0.0, p.cdet, p.cmc, gsum, gvr[i], a[i])
+                                    : (double)__fmul_rn(wc, __fadd_rn(a[i].s, a[i].e));
+          atomicAdd(b + v[i], add);
         }
       }
-      group_sync(grp);
-      // combine the pieces of each element (heads at its first row and at
-      // every warp boundary inside it), in row order
-      if (p.nsub == 1) {
-        for (int q = lt; q < p.EPB * K; q += kGroupThreads) {
-          const int e2 = q / K, i = q - e2 * K;
-          const int64_t k2 = unit * p.EPB + e2;
-          if (k2 >= p.nlist) continue;
-          const EPre& e = pre[cur * kPfMax + (e2 < kPfMax ? e2 : 0)];
-          const int64_t t2 = usepf ? (int64_t)e.t : (p.elist ? (int64_t)__ldg(p.elist + k2) : k2);
-          const int r0 = e2 * p.N, r1 = r0 + p.N;
-          Acc<float> acc;
-          for (int hr = r0; hr < r1; hr = (hr & ~31) + 32) acc.combine(piece[hr][2 * i], piece[hr][2 * i + 1]);
-          int32_t vv[K];
-          float gv[K];
-#pragma unroll
-          for (int m = 0; m < K; ++m) {
-            vv[m] = usepf ? e.v[m] : __ldg(tconn + t2 * K + m);
-            gv[m] = usepf ? e.gv[m] : __ldg(g + vv[m]);
-          }
-          float gsum = gv[0];
-#pragma unroll
-          for (int m = 1; m < K; ++m) gsum = __fadd_rn(gsum, gv[m]);
-          float gi = gv[0];
-#pragma unroll
-          for (int m = 1; m < K; ++m) gi = i == m ? gv[m] : gi;
-          int32_t vi = vv[0];
-#pragma unroll
-          for (int m = 1; m < K; ++m) vi = i == m ? vv[m] : vi;
-          atomicAdd(b + vi, Epi<float>::contrib(usepf ? e.vol : __ldg(vol32 + t2), 0.0, p.cdet, p.cmc, gsum, gi, acc));
-        }
-      } else if (lt < K) {
-        const int i = lt;
-        const int nrow = min(kTileM, p.N - c * kTileM);
-        for (int hr = 0; hr < nrow; hr += 32) acc_long.combine(piece[hr][2 * i], piece[hr][2 * i + 1]);
-        if (c == p.nsub - 1) {
-          const int64_t tu = p.elist ? (int64_t)__ldg(p.elist + unit) : unit;
-          int32_t vv[K];
-          float gv[K];
-#pragma unroll
-          for (int m = 0; m < K; ++m) {
-            vv[m] = __ldg(tconn + tu * K + m);
-            gv[m] = __ldg(g + vv[m]);
-          }
-          float gsum = gv[0];
-#pragma unroll
-          for (int m = 1; m < K; ++m) gsum = __fadd_rn(gsum, gv[m]);
-          atomicAdd(b + vv[i], Epi<float>::contrib(__ldg(vol32 + tu), 0.0, p.cdet, p.cmc, gsum, gv[i], acc_long));
-        }
-      }
-      group_sync(grp);  // pieces are reused by the group's next tile
     }
   }
   mlp_teardown_pp(S, taddr, err);

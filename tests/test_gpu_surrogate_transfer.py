@@ -58,7 +58,11 @@ def _run(net, src_h, tgt_h, tgt, N, seed, tau, s, alpha=1.0):
     return u, b, g, fb.astype(bool), sf, stats
 
 
-@pytest.mark.parametrize("dt,n_tgt,N", [(3, 4, 16), (3, 3, 50), (3, 2, 200), (2, 10, 16)])
+# (3, 4, 8) and (2, 40, 8): 16 elements per tile (no prefetch of element data);
+# (2, 40, 8) and (2, 40, 16) have more work units than SMs, so CTAs run paired
+# tiles (with and without the prefetch); (3, 2, 200):
+# an element spans two tiles
+@pytest.mark.parametrize("dt,n_tgt,N", [(3, 4, 16), (3, 3, 50), (3, 2, 200), (2, 10, 16), (3, 4, 8), (2, 40, 8), (2, 40, 16)])
 def test_surrogate_transfer_matches_oracle(orc, dt, n_tgt, N):
     from oracle import surrogate as S
     src, tgt = _meshes(dt, n_tgt)
