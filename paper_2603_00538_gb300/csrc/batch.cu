@@ -69,6 +69,15 @@ struct BSys {
   int32_t blo, bhi;  // blocks owning its rows
 };
 
+// a block's share of the mixed-precision batched solve: matrix rows [i0, i1)
+// of one request with all its nf field systems s0 .. s0 + nf - 1 (the
+// fields of a matrix row are visited back to back, so the row's matrix
+// entries are read once from memory and again from cache for the others)
+struct BPiece {
+  int32_t s0, nf;
+  int64_t i0, i1;
+};
+
 struct BSysOut {
   int32_t iters;
   int32_t conv;
@@ -523,8 +532,9 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_pcg(const BSys* __restr
 // grid barrier (three rotating flags: the one of decision d is cleared at
 // decision d + 2, when every block has read it).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBatchThreads) k_batch_mixed(const BSys* __restrict__ sys, int nsys, int64_t ntot,
-                                                               int64_t rows_per_block,
+__global__ void __launch_bounds__(kBatchThreads) k_batch_mixed(const BSys* __restrict__ sys,
+                                                               const BPiece* __restrict__ pcs,
+                                                               const int32_t* __restrict__ blk_pc,
                                                                const int32_t* __restrict__ blk_slo,
                                                                const int32_t* __restrict__ blk_shi, int maxs,
                                                                double* t, float* r, float* p, float* q, float* y,
@@ -533,19 +543,15 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_mixed(const BSys* __res
       s_rel[kMaxLocalSys];
   __shared__ float s_eta2[kMaxLocalSys], s_rr[kMaxLocalSys], s_alpha[kMaxLocalSys], s_beta[kMaxLocalSys];
   __shared__ int s_live[kMaxLocalSys], s_act[kMaxLocalSys], s_conv[kMaxLocalSys], s_it[kMaxLocalSys];
-  __shared__ int64_t s_off[kMaxLocalSys + 1];
   __shared__ double s_w[kBatchWarps][kMaxLocalSys][2];
   __shared__ double s_g[kMaxLocalSys][2];
   __shared__ int s_any;
   const unsigned nb = gridDim.x;
   const int b = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t row0 = (int64_t)b * rows_per_block;
-  const int64_t row1 = min(ntot, row0 + rows_per_block);
+  const int pc0 = blk_pc[b], pc1 = blk_pc[b + 1];
   const int slo = blk_slo[b], shi = blk_shi[b];
-  const int nloc = row0 < row1 ? shi - slo + 1 : 0;
-  for (int j = threadIdx.x; j <= nloc; j += blockDim.x)
-    s_off[j] = j < nloc ? max(row0, sys[slo + j].off) : row1;
+  const int nloc = pc0 < pc1 ? shi - slo + 1 : 0;
   for (int j = threadIdx.x; j < nloc; j += blockDim.x) {
     s_live[j] = sys[slo + j].n > 0;
     s_act[j] = 0;
@@ -604,17 +610,17 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_mixed(const BSys* __res
   for (int cyc = 0;; ++cyc) {
     // R: r = b - M x in FP64 (x = 0 in the first cycle), t = S r; partials r.r, t.t
     clear_slots();
-    {
-      int j = 0;
-      for (int64_t base = row0 + warp * 32; base < row1; base += kBatchThreads) {
-        const int64_t gr = base + lane;
-        double rr = 0.0, tt = 0.0;
-        int jj = -1;
-        if (gr < row1) {
-          while (j + 1 < nloc && gr >= s_off[j + 1]) ++j;
-          if (s_live[j]) {
-            const BSys& S = sys[slo + j];
-            const int64_t i = gr - S.off;
+    for (int pc = pc0; pc < pc1; ++pc) {
+      const BPiece P = pcs[pc];
+      for (int64_t base = P.i0 + warp * 32; base < P.i1; base += kBatchThreads) {
+        const int64_t i = base + lane;
+        for (int f = 0; f < P.nf; ++f) {
+          const int j = P.s0 + f - slo;
+          double rr = 0.0, tt = 0.0;
+          int jj = -1;
+          if (i < P.i1 && s_live[j]) {
+            const BSys& S = sys[P.s0 + f];
+            const int64_t gr = S.off + i;
             double w = 0.0;
             if (cyc > 0) {
               const int32_t k0 = __ldg(S.rp + i), k1 = __ldg(S.rp + i + 1);
@@ -630,8 +636,8 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_mixed(const BSys* __res
             tt = ti * ti;
             jj = j;
           }
+          warp_seg_add<double>(jj, rr, tt, s_w[warp]);
         }
-        warp_seg_add<double>(jj, rr, tt, s_w[warp]);
       }
     }
     publish();
@@ -666,15 +672,16 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_mixed(const BSys* __res
     // I: c = t / ||t|| in FP32, y = p = q = 0; partial c.c
     clear_slots();
     __syncthreads();
-    {
-      int j = 0;
-      for (int64_t base = row0 + warp * 32; base < row1; base += kBatchThreads) {
-        const int64_t gr = base + lane;
-        float cc = 0.f;
-        int jj = -1;
-        if (gr < row1) {
-          while (j + 1 < nloc && gr >= s_off[j + 1]) ++j;
-          if (s_act[j]) {
+    for (int pc = pc0; pc < pc1; ++pc) {
+      const BPiece P = pcs[pc];
+      for (int64_t base = P.i0 + warp * 32; base < P.i1; base += kBatchThreads) {
+        const int64_t i = base + lane;
+        for (int f = 0; f < P.nf; ++f) {
+          const int j = P.s0 + f - slo;
+          float cc = 0.f;
+          int jj = -1;
+          if (i < P.i1 && s_act[j]) {
+            const int64_t gr = sys[P.s0 + f].off + i;
             const float ci = (float)(t[gr] * s_isig[j]);
             r[gr] = ci;
             y[gr] = 0.f;
@@ -683,8 +690,8 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_mixed(const BSys* __res
             cc = ci * ci;
             jj = j;
           }
+          warp_seg_add<float>(jj, cc, 0.f, s_w[warp]);
         }
-        warp_seg_add<float>(jj, cc, 0.f, s_w[warp]);
       }
     }
     publish();
@@ -702,17 +709,17 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_mixed(const BSys* __res
     for (int inner = 0;; ++inner) {
       // A: w = A r, p = r + beta p, q = w + beta q; partial p.q
       clear_slots();
-      {
-        int j = 0;
-        for (int64_t base = row0 + warp * 32; base < row1; base += kBatchThreads) {
-          const int64_t gr = base + lane;
-          float pq = 0.f;
-          int jj = -1;
-          if (gr < row1) {
-            while (j + 1 < nloc && gr >= s_off[j + 1]) ++j;
-            if (s_act[j]) {
-              const BSys& S = sys[slo + j];
-              const int64_t i = gr - S.off;
+      for (int pc = pc0; pc < pc1; ++pc) {
+        const BPiece P = pcs[pc];
+        for (int64_t base = P.i0 + warp * 32; base < P.i1; base += kBatchThreads) {
+          const int64_t i = base + lane;
+          for (int f = 0; f < P.nf; ++f) {
+            const int j = P.s0 + f - slo;
+            float pq = 0.f;
+            int jj = -1;
+            if (i < P.i1 && s_act[j]) {
+              const BSys& S = sys[P.s0 + f];
+              const int64_t gr = S.off + i;
               const float* rs = r + S.off;
               const int32_t k0 = __ldg(S.rp + i), k1 = __ldg(S.rp + i + 1);
               float w = 0.f;
@@ -725,8 +732,8 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_mixed(const BSys* __res
               pq = pn * qn;
               jj = j;
             }
+            warp_seg_add<float>(jj, pq, 0.f, s_w[warp]);
           }
-          warp_seg_add<float>(jj, pq, 0.f, s_w[warp]);
         }
       }
       publish();
@@ -740,15 +747,16 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_mixed(const BSys* __res
       __syncthreads();
       // B: y += alpha p, r -= alpha q; partial r.r
       clear_slots();
-      {
-        int j = 0;
-        for (int64_t base = row0 + warp * 32; base < row1; base += kBatchThreads) {
-          const int64_t gr = base + lane;
-          float rr = 0.f;
-          int jj = -1;
-          if (gr < row1) {
-            while (j + 1 < nloc && gr >= s_off[j + 1]) ++j;
-            if (s_act[j]) {
+      for (int pc = pc0; pc < pc1; ++pc) {
+        const BPiece P = pcs[pc];
+        for (int64_t base = P.i0 + warp * 32; base < P.i1; base += kBatchThreads) {
+          const int64_t i = base + lane;
+          for (int f = 0; f < P.nf; ++f) {
+            const int j = P.s0 + f - slo;
+            float rr = 0.f;
+            int jj = -1;
+            if (i < P.i1 && s_act[j]) {
+              const int64_t gr = sys[P.s0 + f].off + i;
               const float al = s_alpha[j];
               y[gr] += al * p[gr];
               const float ri = r[gr] - al * q[gr];
@@ -756,8 +764,8 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_mixed(const BSys* __res
               rr = ri * ri;
               jj = j;
             }
+            warp_seg_add<float>(jj, rr, 0.f, s_w[warp]);
           }
-          warp_seg_add<float>(jj, rr, 0.f, s_w[warp]);
         }
       }
       publish();
@@ -779,17 +787,16 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_mixed(const BSys* __res
       post();
     }
     // U: x += ||t|| S y for every system that refined in this cycle
-    {
-      int j = 0;
-      for (int64_t base = row0 + warp * 32; base < row1; base += kBatchThreads) {
-        const int64_t gr = base + lane;
-        if (gr < row1) {
-          while (j + 1 < nloc && gr >= s_off[j + 1]) ++j;
-          if (s_live[j]) {
-            const BSys& S = sys[slo + j];
-            const int64_t i = gr - S.off;
-            S.x[i] += (s_sig[j] * S.sc[i]) * (double)y[gr];
-          }
+    for (int pc = pc0; pc < pc1; ++pc) {
+      const BPiece P = pcs[pc];
+      for (int64_t base = P.i0 + warp * 32; base < P.i1; base += kBatchThreads) {
+        const int64_t i = base + lane;
+        if (i >= P.i1) continue;
+        for (int f = 0; f < P.nf; ++f) {
+          const int j = P.s0 + f - slo;
+          if (!s_live[j]) continue;
+          const BSys& S = sys[P.s0 + f];
+          S.x[i] += (s_sig[j] * S.sc[i]) * (double)y[S.off + i];
         }
       }
     }
@@ -887,6 +894,8 @@ struct sft_batch_s {
   int64_t ntot = 0, rows_per_block = 0;
   int nblocks = 0, maxs = 1;
   int32_t *blk_slo = nullptr, *blk_shi = nullptr;
+  sft::BPiece* pcs = nullptr;     // mixed mode: the blocks' pieces
+  int32_t* blk_pc = nullptr;      // [nblocks + 1]: block b owns pcs[blk_pc[b] .. blk_pc[b + 1])
   double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *part = nullptr;
   bool mixed = true;  // every request asked for cg_mode MIXED (else the FP64 CG for all)
   sft::BSysOut* sysout = nullptr;
@@ -967,9 +976,10 @@ static sft_status enqueue_batch(sft_batch_s* B, cudaStream_t st) {
       // FP32 work vectors packed into the FP64 ones: r | y in r, p | q in p; t in z
       float* r32 = reinterpret_cast<float*>(B->r);
       float* p32 = reinterpret_cast<float*>(B->p);
-      SFT_CUDA(cudaLaunchKernelEx(&cfg, k_batch_mixed, (const BSys*)B->dsys, B->nsys, B->ntot, B->rows_per_block,
-                                  (const int32_t*)B->blk_slo, (const int32_t*)B->blk_shi, B->maxs, B->z, r32, p32,
-                                  p32 + B->ntot, r32 + B->ntot, B->part, B->sysout, B->cgctl));
+      SFT_CUDA(cudaLaunchKernelEx(&cfg, k_batch_mixed, (const BSys*)B->dsys, (const BPiece*)B->pcs,
+                                  (const int32_t*)B->blk_pc, (const int32_t*)B->blk_slo, (const int32_t*)B->blk_shi,
+                                  B->maxs, B->z, r32, p32, p32 + B->ntot, r32 + B->ntot, B->part, B->sysout,
+                                  B->cgctl));
     } else {
       SFT_CUDA(cudaLaunchKernelEx(&cfg, k_batch_pcg, (const BSys*)B->dsys, B->nsys, B->ntot, B->rows_per_block,
                                   (const int32_t*)B->blk_slo, (const int32_t*)B->blk_shi, B->maxs, B->r, B->z, B->p,
@@ -1101,6 +1111,8 @@ static void free_batch(sft_batch_s* B) {
   dfree(B->dsys, st);
   dfree(B->blk_slo, st);
   dfree(B->blk_shi, st);
+  dfree(B->pcs, st);
+  dfree(B->blk_pc, st);
   dfree(B->r, st);
   dfree(B->z, st);
   dfree(B->p, st);
@@ -1243,7 +1255,58 @@ static sft_status build_batch(sft_batch_s* B, const sft_options* opts, int autot
                                                            (B->ntot + kBatchThreads - 1) / kBatchThreads));
   B->rows_per_block = (B->ntot + B->nblocks - 1) / B->nblocks;
   std::vector<int32_t> slo(B->nblocks), shi(B->nblocks);
-  {
+  if (B->mixed) {
+    // pieces: whole matrix rows of one request with all its fields, about
+    // rows x fields = ntot / nblocks per block, in request order (so a
+    // request's systems are owned by consecutive blocks)
+    std::vector<BPiece> hp;
+    std::vector<int32_t> hbpc(B->nblocks + 1);
+    int r = 0;
+    int64_t i = 0;
+    for (int b = 0; b < B->nblocks; ++b) {
+      hbpc[b] = (int32_t)hp.size();
+      int64_t budget = b == B->nblocks - 1 ? INT64_MAX : B->rows_per_block;
+      while (budget > 0 && r < nreq) {
+        const int64_t nv = B->tgts[r]->nv;
+        const int nf = B->hreq[r].nf;
+        if (i >= nv || nf < 1) {
+          ++r;
+          i = 0;
+          continue;
+        }
+        const int64_t take = std::min(nv - i, (budget + nf - 1) / nf);
+        hp.push_back(BPiece{B->sys_first[r], nf, i, i + take});
+        i += take;
+        budget = budget == INT64_MAX ? budget : budget - take * nf;
+      }
+    }
+    hbpc[B->nblocks] = (int32_t)hp.size();
+    for (int s = 0; s < B->nsys; ++s) {
+      B->hsys[s].blo = INT32_MAX;
+      B->hsys[s].bhi = -1;
+    }
+    for (int b = 0; b < B->nblocks; ++b) {
+      if (hbpc[b] == hbpc[b + 1]) {
+        slo[b] = shi[b] = B->nsys - 1;
+        continue;
+      }
+      const BPiece& first = hp[hbpc[b]];
+      const BPiece& last = hp[hbpc[b + 1] - 1];
+      slo[b] = first.s0;
+      shi[b] = last.s0 + last.nf - 1;
+      B->maxs = std::max(B->maxs, shi[b] - slo[b] + 1);
+      for (int q = hbpc[b]; q < hbpc[b + 1]; ++q)
+        for (int f = 0; f < hp[q].nf; ++f) {
+          BSys& S = B->hsys[hp[q].s0 + f];
+          S.blo = std::min(S.blo, (int32_t)b);
+          S.bhi = std::max(S.bhi, (int32_t)b);
+        }
+    }
+    for (int s = 0; s < B->nsys; ++s)
+      if (B->hsys[s].bhi < 0) B->hsys[s].blo = B->hsys[s].bhi = 0;  // no rows
+    if (sft_status e = upload(&B->pcs, hp, st)) return e;
+    if (sft_status e = upload(&B->blk_pc, hbpc, st)) return e;
+  } else {
     int s = 0;
     for (int b = 0; b < B->nblocks; ++b) {
       const int64_t r0 = (int64_t)b * B->rows_per_block;
@@ -1259,14 +1322,14 @@ static sft_status build_batch(sft_batch_s* B, const sft_options* opts, int autot
       shi[b] = e;
       B->maxs = std::max(B->maxs, e - s + 1);
     }
+    for (int s2 = 0; s2 < B->nsys; ++s2) {
+      BSys& S = B->hsys[s2];
+      if (S.n == 0) { S.blo = S.bhi = 0; continue; }
+      S.blo = (int32_t)(S.off / B->rows_per_block);
+      S.bhi = (int32_t)((S.off + S.n - 1) / B->rows_per_block);
+    }
   }
   if (B->maxs > kMaxLocalSys) return fail(SFT_ERR_UNSUPPORTED, "too many small systems per CG block");
-  for (int s = 0; s < B->nsys; ++s) {
-    BSys& S = B->hsys[s];
-    if (S.n == 0) { S.blo = S.bhi = 0; continue; }
-    S.blo = (int32_t)(S.off / B->rows_per_block);
-    S.bhi = (int32_t)((S.off + S.n - 1) / B->rows_per_block);
-  }
   if (sft_status e = upload(&B->dsys, B->hsys, st)) return e;
   if (sft_status e = upload(&B->blk_slo, slo, st)) return e;
   if (sft_status e = upload(&B->blk_shi, shi, st)) return e;
