@@ -21,7 +21,7 @@
 namespace sft {
 
 struct AsmParams {
-  int64_t nv, ne, nes;
+  int64_t nv, ne, snf;  // snf: the source's field count (stride of its value copies)
   int nf, N, U, G, LPE;
   int64_t ntasks;
   PhiloxRoundKeys rk;
@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const P* __restrict__ tx, c
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const P alphaP = (P)p.alpha;
+  const int snf = NF == 1 ? 1 : (int)p.snf;  // value-copy stride (NF = 1: one-field sources only)
   int n_fallback = 0, n_empty = 0;
 
   // importance sampling draws one sample per unit (two Philox blocks)
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const P* __restrict__ tx, c
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
           if (f >= p.nf) break;
-          const P fs = e >= 0 ? eval_p1<D, P>(vals, p.nes, f, e, mu) : P(0);
+          const P fs = e >= 0 ? eval_p1<D, P>(vals, snf, f, e, mu) : P(0);
           P gX = A::mul(gl[f][0], lam[0]);
 #pragma unroll
           for (int m = 1; m < K; ++m) gX = A::fma(gl[f][m], lam[m], gX);
@@ -316,9 +317,11 @@ static void launch_t(sft_source_s* s, sft_target_s* t, const AssembleArgs& a, co
   }
 }
 
+// NF = 1 only for a one-field source (the kernel then takes the value-copy
+// stride as the constant 1); one field of a multi-field source goes to NF = 2
 template <int D, typename P>
 static void launch_nf(sft_source_s* s, sft_target_s* t, const AssembleArgs& a, const AsmParams& p, cudaStream_t st) {
-  if (a.nf <= 1) launch_t<D, P, 1>(s, t, a, p, st);
+  if (a.nf <= 1 && s->nf == 1) launch_t<D, P, 1>(s, t, a, p, st);
   else if (a.nf <= 2) launch_t<D, P, 2>(s, t, a, p, st);
   else if (a.nf <= 4) launch_t<D, P, 4>(s, t, a, p, st);
   else launch_t<D, P, 8>(s, t, a, p, st);
@@ -329,7 +332,7 @@ sft_status launch_assembly(sft_source_s* s, sft_target_s* t, const AssembleArgs&
   AsmParams p;
   p.nv = t->nv;
   p.ne = t->ne;
-  p.nes = s->ne;
+  p.snf = s->nf;
   p.nf = a.nf;
   p.N = a.N;
   const int spu = t->dim == 2 ? 2 : 1;

@@ -41,7 +41,7 @@ struct BReq {
   const float* recs;
   const int32_t* adj;
   const float* vals;
-  int64_t nes;
+  int32_t snf;  // the source's field count (stride of its value copies)
   int32_t nf, N, U, G, LPE;
   int64_t ntasks;
   PhiloxKey key;
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_control(const BReq* __r
     const int32_t e = locate_point<D, float>(gr, R.cell_start, R.cell_items, R.cell_first, R.recs, R.adj, X, mu, status);
     n_fb += status == 1;
     n_em += status == 2;
-    for (int f = 0; f < R.nf; ++f) R.g[(int64_t)f * R.nv + i] = e >= 0 ? eval_p1<D, float>(R.vals, R.nes, f, e, mu) : 0.f;
+    for (int f = 0; f < R.nf; ++f) R.g[(int64_t)f * R.nv + i] = e >= 0 ? eval_p1<D, float>(R.vals, R.snf, f, e, mu) : 0.f;
   }
   const int fb = warp_sum<int>(n_fb), em = warp_sum<int>(n_em);
   if ((threadIdx.x & 31) == 0) {
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kBatchThreads, NF <= 2 ? 4 : (NF <= 4 ? 3 : 2)
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
             if (f >= nf) break;
-            const float fs = e >= 0 ? eval_p1<D, float>(R.vals, R.nes, f, e, mu) : 0.f;
+            const float fs = e >= 0 ? eval_p1<D, float>(R.vals, R.snf, f, e, mu) : 0.f;
             const float* gf = R.g + (int64_t)f * R.nv;
             float gX = A::mul(__ldg(gf + v[0]), lam[0]);
 #pragma unroll
@@ -522,6 +522,232 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_pcg(const BSys* __restr
 
 
 // ---------------------------------------------------------------------------
+// Row phases of one piece of the batched mixed-precision solve. The piece's
+// field f is system P.s0 + f; the fields of one request share the matrix and
+// lie at stride S.n (S = the first field's system) in b, x and the work
+// vectors, so a row's matrix entries are loaded once for all fields. NFC
+// (1, 2, 4, 8) bounds the piece's field count; bit f of m marks the fields
+// that work in the phase. A thread sums its rows' dot-product terms per
+// field, and the warp adds them to its shared slots once per piece.
+// ---------------------------------------------------------------------------
+template <int NFC>
+__device__ __forceinline__ void piece_flush(const double (&a)[NFC], const double (&c)[NFC], unsigned m,
+                                            double (*slot)[2], int j0) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int f = 0; f < NFC; ++f) {
+    if (!((m >> f) & 1u)) continue;
+    const double u = warp_sum<double>(a[f]), v = warp_sum<double>(c[f]);
+    if (lane == 0) {
+      slot[j0 + f][0] += u;
+      slot[j0 + f][1] += v;
+    }
+  }
+}
+
+template <int NFC>
+__device__ __forceinline__ void piece_flush_f(const float (&a)[NFC], unsigned m, double (*slot)[2], int j0) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int f = 0; f < NFC; ++f) {
+    if (!((m >> f) & 1u)) continue;
+    const float u = warp_sum<float>(a[f]);
+    if (lane == 0) slot[j0 + f][0] += (double)u;
+  }
+}
+
+// R: r = b - M x in FP64 (x = 0 in cycle 0), t = S r; terms r.r, t.t
+template <int NFC>
+__device__ __forceinline__ void piece_R(const BPiece P, const BSys& S, unsigned m, int cyc, double* t,
+                                        double (*slot)[2], int j0) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t n = S.n;
+  double a0[NFC], a1[NFC];
+#pragma unroll
+  for (int f = 0; f < NFC; ++f) a0[f] = a1[f] = 0.0;
+  for (int64_t base = P.i0 + warp * 32; base < P.i1; base += kBatchThreads) {
+    const int64_t i = base + lane;
+    if (i >= P.i1) continue;
+    double w[NFC];
+#pragma unroll
+    for (int f = 0; f < NFC; ++f) w[f] = 0.0;
+    if (cyc > 0) {
+      const int32_t k0 = __ldg(S.rp + i), k1 = __ldg(S.rp + i + 1);
+      // x of other blocks is visible to ordinary loads after the grid barrier
+      for (int32_t k = k0; k < k1; ++k) {
+        const double v = __ldg(S.val + k);
+        const int64_t c = __ldg(S.col + k);
+#pragma unroll
+        for (int f = 0; f < NFC; ++f)
+          if ((m >> f) & 1u) w[f] += v * S.x[f * n + c];
+      }
+    }
+    const double si = S.sc[i];
+#pragma unroll
+    for (int f = 0; f < NFC; ++f) {
+      if (!((m >> f) & 1u)) continue;
+      const int64_t o = f * n + i;
+      if (cyc == 0) S.x[o] = 0.0;
+      const double ri = S.b[o] - w[f];
+      const double ti = si * ri;
+      t[S.off + o] = ti;
+      a0[f] += ri * ri;
+      a1[f] += ti * ti;
+    }
+  }
+  piece_flush<NFC>(a0, a1, m, slot, j0);
+}
+
+// I: c = t / ||t|| in FP32, y = p = q = 0; term c.c
+template <int NFC>
+__device__ __forceinline__ void piece_I(const BPiece P, const BSys& S, unsigned m, const double* t, float* r,
+                                        float* p, float* q, float* y, const double* isig, double (*slot)[2],
+                                        int j0) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t n = S.n;
+  float a[NFC];
+  double is[NFC];
+#pragma unroll
+  for (int f = 0; f < NFC; ++f) {
+    a[f] = 0.f;
+    is[f] = (m >> f) & 1u ? isig[j0 + f] : 0.0;
+  }
+  for (int64_t base = P.i0 + warp * 32; base < P.i1; base += kBatchThreads) {
+    const int64_t i = base + lane;
+    if (i >= P.i1) continue;
+#pragma unroll
+    for (int f = 0; f < NFC; ++f) {
+      if (!((m >> f) & 1u)) continue;
+      const int64_t gr = S.off + f * n + i;
+      const float ci = (float)(t[gr] * is[f]);
+      r[gr] = ci;
+      y[gr] = 0.f;
+      p[gr] = 0.f;
+      q[gr] = 0.f;
+      a[f] += ci * ci;
+    }
+  }
+  piece_flush_f<NFC>(a, m, slot, j0);
+}
+
+// A: w = A r, p = r + beta p, q = w + beta q (= A p); term p.q
+template <int NFC>
+__device__ __forceinline__ void piece_A(const BPiece P, const BSys& S, unsigned m, float* r, float* p, float* q,
+                                        const float* beta, double (*slot)[2], int j0) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t n = S.n;
+  const float* rs = r + S.off;
+  float a[NFC], bt[NFC];
+#pragma unroll
+  for (int f = 0; f < NFC; ++f) {
+    a[f] = 0.f;
+    bt[f] = (m >> f) & 1u ? beta[j0 + f] : 0.f;
+  }
+  for (int64_t base = P.i0 + warp * 32; base < P.i1; base += kBatchThreads) {
+    const int64_t i = base + lane;
+    if (i >= P.i1) continue;
+    const int32_t k0 = __ldg(S.rp + i), k1 = __ldg(S.rp + i + 1);
+    float w[NFC];
+#pragma unroll
+    for (int f = 0; f < NFC; ++f) w[f] = 0.f;
+    // r was written by other blocks before the grid barrier (plain loads)
+    for (int32_t k = k0; k < k1; ++k) {
+      const float v = __ldg(S.aval + k);
+      const int64_t c = __ldg(S.col + k);
+#pragma unroll
+      for (int f = 0; f < NFC; ++f)
+        if ((m >> f) & 1u) w[f] += v * rs[f * n + c];
+    }
+#pragma unroll
+    for (int f = 0; f < NFC; ++f) {
+      if (!((m >> f) & 1u)) continue;
+      const int64_t gr = S.off + f * n + i;
+      const float pn = r[gr] + bt[f] * p[gr];
+      const float qn = w[f] + bt[f] * q[gr];
+      p[gr] = pn;
+      q[gr] = qn;
+      a[f] += pn * qn;
+    }
+  }
+  piece_flush_f<NFC>(a, m, slot, j0);
+}
+
+// B: y += alpha p, r -= alpha q; term r.r
+template <int NFC>
+__device__ __forceinline__ void piece_B(const BPiece P, const BSys& S, unsigned m, float* r, const float* p,
+                                        const float* q, float* y, const float* alpha, double (*slot)[2], int j0) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t n = S.n;
+  float a[NFC], al[NFC];
+#pragma unroll
+  for (int f = 0; f < NFC; ++f) {
+    a[f] = 0.f;
+    al[f] = (m >> f) & 1u ? alpha[j0 + f] : 0.f;
+  }
+  for (int64_t base = P.i0 + warp * 32; base < P.i1; base += kBatchThreads) {
+    const int64_t i = base + lane;
+    if (i >= P.i1) continue;
+#pragma unroll
+    for (int f = 0; f < NFC; ++f) {
+      if (!((m >> f) & 1u)) continue;
+      const int64_t gr = S.off + f * n + i;
+      y[gr] += al[f] * p[gr];
+      const float ri = r[gr] - al[f] * q[gr];
+      r[gr] = ri;
+      a[f] += ri * ri;
+    }
+  }
+  piece_flush_f<NFC>(a, m, slot, j0);
+}
+
+// U: x += ||t|| S y
+template <int NFC>
+__device__ __forceinline__ void piece_U(const BPiece P, const BSys& S, unsigned m, const float* y,
+                                        const double* sig, int j0) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t n = S.n;
+  double sg[NFC];
+#pragma unroll
+  for (int f = 0; f < NFC; ++f) sg[f] = (m >> f) & 1u ? sig[j0 + f] : 0.0;
+  for (int64_t base = P.i0 + warp * 32; base < P.i1; base += kBatchThreads) {
+    const int64_t i = base + lane;
+    if (i >= P.i1) continue;
+    const double si = S.sc[i];
+#pragma unroll
+    for (int f = 0; f < NFC; ++f) {
+      if (!((m >> f) & 1u)) continue;
+      const int64_t o = f * n + i;
+      S.x[o] += (sg[f] * si) * (double)y[S.off + o];
+    }
+  }
+}
+
+// the piece's field class and its mask of working fields (flags[j0 + f])
+__device__ __forceinline__ unsigned piece_mask(const BPiece& P, const int* flags, int j0) {
+  unsigned m = 0u;
+  for (int f = 0; f < P.nf; ++f) m |= flags[j0 + f] ? 1u << f : 0u;
+  return m;
+}
+
+// run phase PH on piece P (locals P, m, j0, sys) by its field class; with
+// MAXF = 4 a piece of more fields runs as two halves (field 4's system
+// starts the second), which bounds the registers the unrolled fields take
+#define SFT_PIECE_RUN(PH, MAXF, ...)                                             \
+  do {                                                                           \
+    if (P.nf <= 1) PH<1>(P, sys[P.s0], m, __VA_ARGS__, j0);                      \
+    else if (P.nf <= 2) PH<2>(P, sys[P.s0], m, __VA_ARGS__, j0);                 \
+    else if (P.nf <= 4) PH<4>(P, sys[P.s0], m, __VA_ARGS__, j0);                 \
+    else if ((MAXF) == 8) PH<8>(P, sys[P.s0], m, __VA_ARGS__, j0);               \
+    else {                                                                       \
+      const BPiece H{P.s0 + 4, P.nf - 4, P.i0, P.i1};                            \
+      if (m & 0xfu) PH<4>(P, sys[P.s0], m & 0xfu, __VA_ARGS__, j0);              \
+      if (m >> 4) PH<4>(H, sys[H.s0], m >> 4, __VA_ARGS__, j0 + 4);              \
+    }                                                                            \
+  } while (0)
+// field bound of the FP64 phase R and of the FP32 phases
+constexpr int kPieceFieldsR = 4, kPieceFields = 8;
+
+// ---------------------------------------------------------------------------
 // Batched mixed-precision iterative refinement (the cg_mode MIXED solve of
 // every (request, field) system at once; see the single-system k_mixed_cg):
 // per refinement cycle an FP64 residual pass R, the FP32 right-hand side
@@ -532,7 +758,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_pcg(const BSys* __restr
 // grid barrier (three rotating flags: the one of decision d is cleared at
 // decision d + 2, when every block has read it).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kBatchThreads) k_batch_mixed(const BSys* __restrict__ sys,
+__global__ void __launch_bounds__(kBatchThreads, 4) k_batch_mixed(const BSys* __restrict__ sys,
                                                                const BPiece* __restrict__ pcs,
                                                                const int32_t* __restrict__ blk_pc,
                                                                const int32_t* __restrict__ blk_slo,
@@ -612,33 +838,10 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_mixed(const BSys* __res
     clear_slots();
     for (int pc = pc0; pc < pc1; ++pc) {
       const BPiece P = pcs[pc];
-      for (int64_t base = P.i0 + warp * 32; base < P.i1; base += kBatchThreads) {
-        const int64_t i = base + lane;
-        for (int f = 0; f < P.nf; ++f) {
-          const int j = P.s0 + f - slo;
-          double rr = 0.0, tt = 0.0;
-          int jj = -1;
-          if (i < P.i1 && s_live[j]) {
-            const BSys& S = sys[P.s0 + f];
-            const int64_t gr = S.off + i;
-            double w = 0.0;
-            if (cyc > 0) {
-              const int32_t k0 = __ldg(S.rp + i), k1 = __ldg(S.rp + i + 1);
-              // x of other blocks is visible to ordinary loads after the grid barrier
-              for (int32_t k = k0; k < k1; ++k) w += __ldg(S.val + k) * S.x[__ldg(S.col + k)];
-            } else {
-              S.x[i] = 0.0;
-            }
-            const double ri = S.b[i] - w;
-            const double ti = S.sc[i] * ri;
-            t[gr] = ti;
-            rr = ri * ri;
-            tt = ti * ti;
-            jj = j;
-          }
-          warp_seg_add<double>(jj, rr, tt, s_w[warp]);
-        }
-      }
+      const int j0 = P.s0 - slo;
+      const unsigned m = piece_mask(P, s_live, j0);
+      if (!m) continue;
+      SFT_PIECE_RUN(piece_R, kPieceFieldsR, cyc, t, s_w[warp]);
     }
     publish();
     if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
@@ -674,25 +877,10 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_mixed(const BSys* __res
     __syncthreads();
     for (int pc = pc0; pc < pc1; ++pc) {
       const BPiece P = pcs[pc];
-      for (int64_t base = P.i0 + warp * 32; base < P.i1; base += kBatchThreads) {
-        const int64_t i = base + lane;
-        for (int f = 0; f < P.nf; ++f) {
-          const int j = P.s0 + f - slo;
-          float cc = 0.f;
-          int jj = -1;
-          if (i < P.i1 && s_act[j]) {
-            const int64_t gr = sys[P.s0 + f].off + i;
-            const float ci = (float)(t[gr] * s_isig[j]);
-            r[gr] = ci;
-            y[gr] = 0.f;
-            p[gr] = 0.f;
-            q[gr] = 0.f;
-            cc = ci * ci;
-            jj = j;
-          }
-          warp_seg_add<float>(jj, cc, 0.f, s_w[warp]);
-        }
-      }
+      const int j0 = P.s0 - slo;
+      const unsigned m = piece_mask(P, s_act, j0);
+      if (!m) continue;
+      SFT_PIECE_RUN(piece_I, kPieceFields, t, r, p, q, y, s_isig, s_w[warp]);
     }
     publish();
     if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
@@ -711,30 +899,10 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_mixed(const BSys* __res
       clear_slots();
       for (int pc = pc0; pc < pc1; ++pc) {
         const BPiece P = pcs[pc];
-        for (int64_t base = P.i0 + warp * 32; base < P.i1; base += kBatchThreads) {
-          const int64_t i = base + lane;
-          for (int f = 0; f < P.nf; ++f) {
-            const int j = P.s0 + f - slo;
-            float pq = 0.f;
-            int jj = -1;
-            if (i < P.i1 && s_act[j]) {
-              const BSys& S = sys[P.s0 + f];
-              const int64_t gr = S.off + i;
-              const float* rs = r + S.off;
-              const int32_t k0 = __ldg(S.rp + i), k1 = __ldg(S.rp + i + 1);
-              float w = 0.f;
-              for (int32_t k = k0; k < k1; ++k) w += __ldg(S.aval + k) * rs[__ldg(S.col + k)];
-              const float bt = s_beta[j];
-              const float pn = r[gr] + bt * p[gr];
-              const float qn = w + bt * q[gr];
-              p[gr] = pn;
-              q[gr] = qn;
-              pq = pn * qn;
-              jj = j;
-            }
-            warp_seg_add<float>(jj, pq, 0.f, s_w[warp]);
-          }
-        }
+        const int j0 = P.s0 - slo;
+        const unsigned m = piece_mask(P, s_act, j0);
+        if (!m) continue;
+        SFT_PIECE_RUN(piece_A, kPieceFields, r, p, q, s_beta, s_w[warp]);
       }
       publish();
       if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
@@ -749,24 +917,10 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_mixed(const BSys* __res
       clear_slots();
       for (int pc = pc0; pc < pc1; ++pc) {
         const BPiece P = pcs[pc];
-        for (int64_t base = P.i0 + warp * 32; base < P.i1; base += kBatchThreads) {
-          const int64_t i = base + lane;
-          for (int f = 0; f < P.nf; ++f) {
-            const int j = P.s0 + f - slo;
-            float rr = 0.f;
-            int jj = -1;
-            if (i < P.i1 && s_act[j]) {
-              const int64_t gr = sys[P.s0 + f].off + i;
-              const float al = s_alpha[j];
-              y[gr] += al * p[gr];
-              const float ri = r[gr] - al * q[gr];
-              r[gr] = ri;
-              rr = ri * ri;
-              jj = j;
-            }
-            warp_seg_add<float>(jj, rr, 0.f, s_w[warp]);
-          }
-        }
+        const int j0 = P.s0 - slo;
+        const unsigned m = piece_mask(P, s_act, j0);
+        if (!m) continue;
+        SFT_PIECE_RUN(piece_B, kPieceFields, r, p, q, y, s_alpha, s_w[warp]);
       }
       publish();
       if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
@@ -789,16 +943,10 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_mixed(const BSys* __res
     // U: x += ||t|| S y for every system that refined in this cycle
     for (int pc = pc0; pc < pc1; ++pc) {
       const BPiece P = pcs[pc];
-      for (int64_t base = P.i0 + warp * 32; base < P.i1; base += kBatchThreads) {
-        const int64_t i = base + lane;
-        if (i >= P.i1) continue;
-        for (int f = 0; f < P.nf; ++f) {
-          const int j = P.s0 + f - slo;
-          if (!s_live[j]) continue;
-          const BSys& S = sys[P.s0 + f];
-          S.x[i] += (s_sig[j] * S.sc[i]) * (double)y[S.off + i];
-        }
-      }
+      const int j0 = P.s0 - slo;
+      const unsigned m = piece_mask(P, s_live, j0);
+      if (!m) continue;
+      SFT_PIECE_RUN(piece_U, kPieceFields, y, s_sig);
     }
     if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
   }
@@ -1170,7 +1318,7 @@ static sft_status build_batch(sft_batch_s* B, const sft_options* opts, int autot
     R.recs = (const float*)L.recs;
     R.adj = L.adj;
     R.vals = (const float*)L.vals;
-    R.nes = s->ne;
+    R.snf = s->nf;
     R.nf = o.field_count > 0 ? o.field_count : s->nf;
     R.N = o.samples_per_elem;
     const int spu = t->dim == 2 ? 2 : 1;

@@ -549,11 +549,12 @@ __device__ __forceinline__ int32_t locate_point(const GridP<P>& g, const int32_t
 }
 
 // P1 value of field f in element e from the per-element copy of its nodal
-// values (vals: [nf][ne][4] in P; slot 3 unused in 2D)
+// values (vals: [ne][snf][4] in P, snf = the source's field count, so the
+// fields of one element are contiguous; slot 3 unused in 2D)
 template <int D, typename P>
-__device__ __forceinline__ P eval_p1(const P* __restrict__ vals, int64_t ne, int f, int32_t e, const P mu[D + 1]) {
+__device__ __forceinline__ P eval_p1(const P* __restrict__ vals, int snf, int f, int32_t e, const P mu[D + 1]) {
   using A = Ar<P>;
-  const P* v = vals + ((int64_t)f * ne + e) * 4;
+  const P* v = vals + ((int64_t)e * snf + f) * 4;
   P fv[4];
   if constexpr (sizeof(P) == 4) {
     const float4 q = __ldg(reinterpret_cast<const float4*>(v));

@@ -84,7 +84,7 @@ struct Locator {
   int32_t* cell_items = nullptr;  // [nitems] (in no particular order within a cell)
   int32_t* cell_first = nullptr;  // [ncells] start element of the location walk, -1: empty cell
   void* recs = nullptr;           // [ne][RecLen] P
-  void* vals = nullptr;           // [nf][ne][4] P
+  void* vals = nullptr;           // [ne][nf][4] P
   void* coordsP = nullptr;        // [nv][dim] P
   const int32_t* adj = nullptr;   // the source's face neighbours (sft_source_s::adj)
 };

@@ -64,7 +64,7 @@ __device__ __forceinline__ void bary2(const P2 v[3], P2 x, double mu[3]) {
 template <bool L2>
 __global__ void __launch_bounds__(kMiThreads) k_mi_2d(
     const double* __restrict__ sx, const int32_t* __restrict__ sconn, const int32_t* __restrict__ adj,
-    const double* __restrict__ svals, int64_t nes, int field, const GridP<double>* __restrict__ gp,
+    const double* __restrict__ svals, int snf, int field, const GridP<double>* __restrict__ gp,
     const int32_t* __restrict__ cell_start, const int32_t* __restrict__ cell_items,
     const int32_t* __restrict__ cell_first, const double* __restrict__ recs, const double* __restrict__ tx, const int32_t* __restrict__ tconn, int64_t net, const double* __restrict__ u,
     double* __restrict__ b, double* __restrict__ part, int32_t* err) {
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kMiThreads) k_mi_2d(
       for (int m = 0; m < 3; ++m) {
         const int32_t v = __ldg(sconn + (int64_t)s * 3 + m);
         sv[m] = P2{__ldg(sx + (int64_t)v * 2), __ldg(sx + (int64_t)v * 2 + 1)};
-        fv[m] = __ldg(svals + ((int64_t)field * nes + s) * 4 + m);
+        fv[m] = __ldg(svals + ((int64_t)s * snf + field) * 4 + m);
       }
       P2 poly[12], tmp[12];
       int k = 3;
@@ -209,7 +209,7 @@ sft_status mesh_intersection_2d(sft_source_s* s, sft_target_s* t, int field, con
   if (!l2) SFT_CUDA(cudaMemsetAsync(b, 0, sizeof(double) * t->nv, st));
   auto launch = [&](auto kern) {
     ::sft::note_launch(), kern<<<blocks, kMiThreads, 0, st>>>(
-        (const double*)L.coordsP, s->conn, L.adj, (const double*)L.vals, s->ne, field, (const GridP<double>*)L.grid,
+        (const double*)L.coordsP, s->conn, L.adj, (const double*)L.vals, s->nf, field, (const GridP<double>*)L.grid,
         L.cell_start, L.cell_items, L.cell_first, (const double*)L.recs, (const double*)t->coordsP[SFT_PREC_FP64], t->conn,
         t->ne, u, b, part.p, d_err.p);
   };

@@ -6,7 +6,7 @@
 //
 // Layout in HBM per precision P:
 //   recs  [ne][8 | 12] P  : first vertex + inverse affine map (16-B aligned rows)
-//   vals  [nf][ne][4]  P  : per-element copy of the nodal values (one 16/32-B load)
+//   vals  [ne][nf][4]  P  : per-element copy of the nodal values (one 16/32-B load)
 //   cell_start [ncells+1], cell_items [nitems] int32: elements of each cell
 //   (in no particular order); cell_first [ncells] int32: the element deepest
 //   at the cell centre (largest min barycentric coordinate there, ties to the
@@ -287,7 +287,7 @@ __global__ void k_records(const P* __restrict__ x, const int32_t* __restrict__ c
     for (int f = 0; f < nf; ++f) {
 #pragma unroll
       for (int m = 0; m < 4; ++m)
-        vals[((int64_t)f * ne + e) * 4 + m] = m <= D ? P(values[(int64_t)f * nv + v[m]]) : P(0);
+        vals[((int64_t)e * nf + f) * 4 + m] = m <= D ? P(values[(int64_t)f * nv + v[m]]) : P(0);
     }
   }
 }
@@ -620,7 +620,7 @@ __global__ void k_value_copies(const int32_t* __restrict__ conn, const TV* __res
     for (int m = 0; m <= D; ++m) v[m] = conn[e * (D + 1) + m];
     for (int f = 0; f < nf; ++f)
 #pragma unroll
-      for (int m = 0; m < 4; ++m) vals[((int64_t)f * ne + e) * 4 + m] = m <= D ? P(values[(int64_t)f * nv + v[m]]) : P(0);
+      for (int m = 0; m < 4; ++m) vals[((int64_t)e * nf + f) * 4 + m] = m <= D ? P(values[(int64_t)f * nv + v[m]]) : P(0);
   }
 }
 
@@ -656,7 +656,7 @@ __global__ void __launch_bounds__(256) k_locate_points(const TIn* __restrict__ p
                                                        const int32_t* __restrict__ cell_first,
                                                        const P* __restrict__ recs, const int32_t* __restrict__ adj,
                                                        const P* __restrict__ vals,
-                                                       int64_t ne, int nf, int32_t* __restrict__ elem_out,
+                                                       int snf, int nf, int32_t* __restrict__ elem_out,
                                                        TOut* __restrict__ val_out, int64_t val_stride,
                                                        int64_t* __restrict__ counters, P* __restrict__ mu_out) {
   const GridP<P> g = *gp;
@@ -680,7 +680,7 @@ __global__ void __launch_bounds__(256) k_locate_points(const TIn* __restrict__ p
     }
     if (val_out) {
       for (int f = 0; f < nf; ++f)
-        val_out[(int64_t)f * val_stride + i] = e >= 0 ? (TOut)eval_p1<D, P>(vals, ne, f, e, mu) : TOut(0);
+        val_out[(int64_t)f * val_stride + i] = e >= 0 ? (TOut)eval_p1<D, P>(vals, snf, f, e, mu) : TOut(0);
     }
   }
   if (counters) {
@@ -703,7 +703,7 @@ static void launch_locate(sft_source_s* s, const Locator& L, int64_t n, const vo
 #define SFT_LOC(TIN, TOUT)                                                                                      \
   ::sft::note_launch(), k_locate_points<D, P, TIN, TOUT><<<blocks, 256, 0, st>>>((const TIN*)pts, n, g, L.cell_start, L.cell_items, \
                                                            L.cell_first,                                    \
-                                                           recs, L.adj, vals, s->ne, nf, elem_out,          \
+                                                           recs, L.adj, vals, s->nf, nf, elem_out,          \
                                                            (TOUT*)val_out,                                   \
                                                            val_stride, counters, (P*)mu_out)
   if (pts_are_double) {

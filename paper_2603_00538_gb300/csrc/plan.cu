@@ -38,7 +38,7 @@ namespace sft {
 // control values g[f][i] = f^s at target node i from its recorded location
 template <int D, typename P>
 __global__ void k_plan_control(const int32_t* __restrict__ node_elem, const P* __restrict__ node_mu, int64_t nv,
-                               const P* __restrict__ vals, int64_t nes, int nf, P* __restrict__ g) {
+                               const P* __restrict__ vals, int snf, int nf, P* __restrict__ g) {
   using A = Ar<P>;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t e = __ldg(node_elem + i);
@@ -50,7 +50,7 @@ __global__ void k_plan_control(const int32_t* __restrict__ node_elem, const P* _
       m0 = A::sub(m0, mu[a + 1]);
     }
     mu[0] = m0;
-    for (int f = 0; f < nf; ++f) g[(int64_t)f * nv + i] = e >= 0 ? eval_p1<D, P>(vals, nes, f, e, mu) : P(0);
+    for (int f = 0; f < nf; ++f) g[(int64_t)f * nv + i] = e >= 0 ? eval_p1<D, P>(vals, snf, f, e, mu) : P(0);
   }
 }
 
@@ -178,17 +178,17 @@ sft_status sft_plan_transfer(sft_plan pl, double* u_out, double* b_out, double* 
   if (t->dim == 2) {
     if (prec == SFT_PREC_FP32)
       ::sft::note_launch(), k_plan_control<2, float><<<nb, 256, 0, st>>>(pl->node_elem, (const float*)pl->node_mu, nv,
-                                                                        (const float*)L.vals, s->ne, nf, (float*)g.p);
+                                                                        (const float*)L.vals, s->nf, nf, (float*)g.p);
     else
       ::sft::note_launch(), k_plan_control<2, double><<<nb, 256, 0, st>>>(pl->node_elem, (const double*)pl->node_mu, nv,
-                                                                         (const double*)L.vals, s->ne, nf, (double*)g.p);
+                                                                         (const double*)L.vals, s->nf, nf, (double*)g.p);
   } else {
     if (prec == SFT_PREC_FP32)
       ::sft::note_launch(), k_plan_control<3, float><<<nb, 256, 0, st>>>(pl->node_elem, (const float*)pl->node_mu, nv,
-                                                                        (const float*)L.vals, s->ne, nf, (float*)g.p);
+                                                                        (const float*)L.vals, s->nf, nf, (float*)g.p);
     else
       ::sft::note_launch(), k_plan_control<3, double><<<nb, 256, 0, st>>>(pl->node_elem, (const double*)pl->node_mu, nv,
-                                                                         (const double*)L.vals, s->ne, nf, (double*)g.p);
+                                                                         (const double*)L.vals, s->nf, nf, (double*)g.p);
   }
   SFT_CUDA(cudaGetLastError());
   if (ev.ok) cudaEventRecord(ev.e[2], st);

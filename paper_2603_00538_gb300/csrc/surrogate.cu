@@ -34,7 +34,8 @@
 namespace sft {
 
 struct SurParams {
-  int64_t nv, ne, nes;   // target nodes, target elements, exact-source elements
+  int64_t nv, ne;
+  int snf;               // field count of the exact source (stride of its value copies)
   int64_t nlist;         // elements this launch processes: elist[0..nlist) (all ne without a list)
   const int32_t* elist;  // optional element list (the survivors or the fallbacks of the decision)
   const float* sub_f;    // optional [ne][s] exact values of the subsample, reused by the fallback pass
@@ -57,7 +58,7 @@ __device__ __forceinline__ float exact_value(const GridP<float>& gr, const int32
                                              const int32_t* __restrict__ cell_items,
                                              const int32_t* __restrict__ cell_first, const float* __restrict__ recs,
                                              const int32_t* __restrict__ adj,
-                                             const float* __restrict__ vals, int64_t nes, int field, const float* X,
+                                             const float* __restrict__ vals, int snf, int field, const float* X,
                                              int& n_empty, int cost = 0) {
   float Xs[DS];
 #pragma unroll
@@ -66,7 +67,7 @@ __device__ __forceinline__ float exact_value(const GridP<float>& gr, const int32
   int status;
   const int32_t e = locate_point<DS, float>(gr, cell_start, cell_items, cell_first, recs, adj, Xs, mu, status);
   n_empty += status == 2;
-  float v = e >= 0 ? eval_p1<DS, float>(vals, nes, field, e, mu) : 0.f;
+  float v = e >= 0 ? eval_p1<DS, float>(vals, snf, field, e, mu) : 0.f;
   if (cost > 0) {
     // the stand-in black-box cost: a dependent chain of `cost` FMAs (it
     // settles at 0.1, finite), folded in as v + 0 * z, which keeps v
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(kTileM, 8) k_surrogate_exact(
         if (p.sub_f && j < p.s) {
           fe = __ldg(p.sub_f + t * p.s + j);
         } else {
-          fe = exact_value<DS>(gr, cell_start, cell_items, cell_first, recs, adj, vals, p.nes, p.exact_field, X, n_empty,
+          fe = exact_value<DS>(gr, cell_start, cell_items, cell_first, recs, adj, vals, p.snf, p.exact_field, X, n_empty,
                                p.exact_cost);
           ++n_exact;
         }
@@ -265,7 +266,7 @@ __global__ void k_sub_points(const float* __restrict__ tx, const int32_t* __rest
                              const int32_t* __restrict__ cell_start, const int32_t* __restrict__ cell_items,
                              const int32_t* __restrict__ cell_first,
                              const float* __restrict__ recs, const int32_t* __restrict__ adj,
-                             const float* __restrict__ vals, int64_t nes, int field, int cost,
+                             const float* __restrict__ vals, int snf, int field, int cost,
                              float* __restrict__ pts3, float* __restrict__ fe, int64_t* __restrict__ counters) {
   constexpr int K = DT + 1;
   const GridP<float> gr = *gp;
@@ -286,7 +287,7 @@ __global__ void k_sub_points(const float* __restrict__ tx, const int32_t* __rest
     pts3[i * 3] = X[0];
     pts3[i * 3 + 1] = X[1];
     pts3[i * 3 + 2] = DT == 3 ? X[DT - 1] : 0.f;
-    fe[i] = exact_value<DS>(gr, cell_start, cell_items, cell_first, recs, adj, vals, nes, field, X, n_empty, cost);
+    fe[i] = exact_value<DS>(gr, cell_start, cell_items, cell_first, recs, adj, vals, snf, field, X, n_empty, cost);
     ++n_exact;
   }
   const int e1 = warp_sum<int>(n_exact), m1 = warp_sum<int>(n_empty);
@@ -330,13 +331,13 @@ __global__ void k_exact_nodes(const float* __restrict__ x, int64_t nv, int d, co
                               const int32_t* __restrict__ cell_start, const int32_t* __restrict__ cell_items,
                               const int32_t* __restrict__ cell_first,
                               const float* __restrict__ recs, const int32_t* __restrict__ adj,
-                              const float* __restrict__ vals, int64_t nes, int field, int cost,
+                              const float* __restrict__ vals, int snf, int field, int cost,
                               float* __restrict__ out, int64_t* __restrict__ counters) {
   const GridP<float> gr = *gp;
   int n_empty = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
     float X[3] = {x[i * d], x[i * d + 1], d == 3 ? x[i * d + 2] : 0.f};
-    out[i] = exact_value<DS>(gr, cell_start, cell_items, cell_first, recs, adj, vals, nes, field, X, n_empty, cost);
+    out[i] = exact_value<DS>(gr, cell_start, cell_items, cell_first, recs, adj, vals, snf, field, X, n_empty, cost);
   }
   const int m1 = warp_sum<int>(n_empty);
   if ((threadIdx.x & 31) == 0 && m1) atomicAdd(reinterpret_cast<unsigned long long*>(counters + 2), (unsigned long long)m1);
@@ -350,7 +351,7 @@ __global__ void k_dataset(int64_t n, PhiloxKey key, uint32_t stream_id, float3 l
                           const GridP<float>* __restrict__ gp, const int32_t* __restrict__ cell_start,
                           const int32_t* __restrict__ cell_items, const int32_t* __restrict__ cell_first,
                           const float* __restrict__ recs, const int32_t* __restrict__ adj,
-                          const float* __restrict__ vals, int64_t nes, int field, float* __restrict__ pts,
+                          const float* __restrict__ vals, int snf, int field, float* __restrict__ pts,
                           float* __restrict__ f, unsigned int* __restrict__ maxabs, int64_t* __restrict__ counters) {
   const GridP<float> gr = *gp;
   int n_empty = 0;
@@ -361,7 +362,7 @@ __global__ void k_dataset(int64_t n, PhiloxKey key, uint32_t stream_id, float3 l
     X[0] = __fadd_rn(lo.x, __fmul_rn(u01f(r.x), w.x));
     X[1] = __fadd_rn(lo.y, __fmul_rn(u01f(r.y), w.y));
     X[2] = __fadd_rn(lo.z, __fmul_rn(u01f(r.z), w.z));
-    const float v = exact_value<DS>(gr, cell_start, cell_items, cell_first, recs, adj, vals, nes, field, X, n_empty);
+    const float v = exact_value<DS>(gr, cell_start, cell_items, cell_first, recs, adj, vals, snf, field, X, n_empty);
     pts[j * 3] = X[0];
     pts[j * 3 + 1] = X[1];
     pts[j * 3 + 2] = X[2];
@@ -648,7 +649,7 @@ sft_status sft_surrogate_dataset(sft_source s, int32_t field, int64_t n, uint64_
   ::sft::note_launch(), k_dataset<DSV><<<blocks, 256, 0, st>>>(n, key, stream_id, lo, w, (const GridP<float>*)L.grid, \
                                                               L.cell_start, L.cell_items, L.cell_first,           \
                                                               (const float*)L.recs,                               \
-                                                              L.adj, (const float*)L.vals, s->ne, field, pts_out, \
+                                                              L.adj, (const float*)L.vals, s->nf, field, pts_out, \
                                                               f_out,                                              \
                                                               mx.p, counters.p)
     if (s->dim == 2) SFT_DS(2); else SFT_DS(3);
@@ -727,7 +728,7 @@ sft_status sft_transfer_surrogate(sft_mlp net, sft_source exact, sft_target t, c
   ::sft::note_launch(), k_exact_nodes<DSV><<<nb, 256, 0, st>>>(tx, nv, t->dim, (const GridP<float>*)L.grid,     \
                                                               L.cell_start, L.cell_items, L.cell_first,         \
                                                               (const float*)L.recs,                             \
-                                                              L.adj, (const float*)L.vals, exact->ne,           \
+                                                              L.adj, (const float*)L.vals, exact->nf,           \
                                                               so->exact_field, so->exact_cost,                  \
                                                               g.p, counters.p)
     if (exact->dim == 2) SFT_EN(2); else SFT_EN(3);
@@ -740,7 +741,7 @@ sft_status sft_transfer_surrogate(sft_mlp net, sft_source exact, sft_target t, c
   SurParams p{};
   p.nv = nv;
   p.ne = ne;
-  p.nes = exact ? exact->ne : 0;
+  p.snf = exact ? exact->nf : 0;
   p.N = N;
   if (N <= kTileM) {
     p.EPB = kTileM / N;
@@ -803,7 +804,7 @@ sft_status sft_transfer_surrogate(sft_mlp net, sft_source exact, sft_target t, c
 #define SFT_SP(DTV, DSV)                                                                                             \
   ::sft::note_launch(), k_sub_points<DTV, DSV><<<nbs, 128, 0, st>>>(                                                  \
       tx, t->conn, ne, sub, p.key, p.stream_id, p.st, (const GridP<float>*)L.grid, L.cell_start, L.cell_items,     \
-      L.cell_first, (const float*)L.recs, L.adj, (const float*)L.vals, exact->ne, so->exact_field, so->exact_cost, s_pts.p,      \
+      L.cell_first, (const float*)L.recs, L.adj, (const float*)L.vals, exact->nf, so->exact_field, so->exact_cost, s_pts.p,      \
       s_fe.p, counters.p)
     if (t->dim == 2) SFT_SP(2, 2);
     else if (ds == 2) SFT_SP(3, 2);
