@@ -426,7 +426,7 @@ def run_batch(args):
             "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"batch256: {WORKLOADS['batch256']}", "requests": len(reqs),
+            "config": {"workload": f"batch256: {WORKLOADS['batch256']}" + ("" if args.scale == 1.0 else f" (element counts x{args.scale})"), "requests": len(reqs),
                        "queries_per_step": queries, "target_elements": int(sum(q["elems"] for q in reqs)),
                        "l2": "flushed between steps (256 MB write)", "plan_build_s": plan_s,
                        "graph": stats["graph"], "tiles": stats["tile"],
@@ -681,7 +681,7 @@ def run_roundtrip(args):
             "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"roundtrip: {WORKLOADS['roundtrip']}", "queries_per_step": queries,
+            "config": {"workload": f"roundtrip: {WORKLOADS['roundtrip']}" + ("" if args.scale == 1.0 else f" (element counts x{args.scale})"), "queries_per_step": queries,
                        "mesh1_elements": m1.nelems, "mesh2_elements": m2.nelems, "samples_per_elem": N,
                        "sampling": args.sampling, "plan_create_s": plan_s,
                        "solve_start": "zero" if args.cold_start else "each leg's previous result (warm start)",

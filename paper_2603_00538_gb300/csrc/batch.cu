@@ -1404,17 +1404,34 @@ static sft_status build_batch(sft_batch_s* B, const sft_options* opts, int autot
   B->rows_per_block = (B->ntot + B->nblocks - 1) / B->nblocks;
   std::vector<int32_t> slo(B->nblocks), shi(B->nblocks);
   if (B->mixed) {
-    // pieces: whole matrix rows of one request with all its fields, about
-    // rows x fields = ntot / nblocks per block, in request order (so a
-    // request's systems are owned by consecutive blocks)
+    // pieces: whole matrix rows of one request with all its fields, in
+    // request order (so a request's systems are owned by consecutive
+    // blocks), an equal share of the estimated row cost per block. A row of
+    // a request with z matrix entries per row and nf fields costs about
+    // 8 z (its FP32 entries and columns, loaded once for all fields) +
+    // nf (44 + 4 z) (per field the CG vectors of the two FP32 phases and
+    // the z gathered entries of r): 3D rows (z ~ 15) cost about twice 2D
+    // rows (z ~ 7), and a field of an 8-field row 0.6 of a lone field.
     std::vector<BPiece> hp;
     std::vector<int32_t> hbpc(B->nblocks + 1);
+    std::vector<double> rcost(nreq, 0.0);
+    double total = 0.0;
+    for (int q = 0; q < nreq; ++q) {
+      const sft_target tq = B->tgts[q];
+      const int nf = B->hreq[q].nf;
+      if (tq->nv <= 0 || nf < 1) continue;
+      const double z = (double)tq->nnz / (double)tq->nv;
+      rcost[q] = 8.0 * z + nf * (44.0 + 4.0 * z);
+      total += rcost[q] * (double)tq->nv;
+    }
+    const double share = total / B->nblocks;
     int r = 0;
     int64_t i = 0;
     for (int b = 0; b < B->nblocks; ++b) {
       hbpc[b] = (int32_t)hp.size();
-      int64_t budget = b == B->nblocks - 1 ? INT64_MAX : B->rows_per_block;
-      while (budget > 0 && r < nreq) {
+      const bool last = b == B->nblocks - 1;
+      double budget = share;
+      while ((last || budget > 0.0) && r < nreq) {
         const int64_t nv = B->tgts[r]->nv;
         const int nf = B->hreq[r].nf;
         if (i >= nv || nf < 1) {
@@ -1422,10 +1439,11 @@ static sft_status build_batch(sft_batch_s* B, const sft_options* opts, int autot
           i = 0;
           continue;
         }
-        const int64_t take = std::min(nv - i, (budget + nf - 1) / nf);
+        int64_t take = nv - i;
+        if (!last) take = std::min<int64_t>(take, std::max<int64_t>(1, (int64_t)std::ceil(budget / rcost[r])));
         hp.push_back(BPiece{B->sys_first[r], nf, i, i + take});
         i += take;
-        budget = budget == INT64_MAX ? budget : budget - take * nf;
+        budget -= (double)take * rcost[r];
       }
     }
     hbpc[B->nblocks] = (int32_t)hp.size();

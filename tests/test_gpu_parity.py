@@ -276,6 +276,36 @@ def test_transfer_edge_shapes(orc, dim, N, nf, alpha):
             assert _close(r["u"][f], o["u"][f], 1e-10 if prec == FP64 else 1e-4), (prec, f)
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_transfer_field_subset(orc, dim):
+    """The first k fields of a 5-field source (the per-element value copies
+    hold all five per element; k = 1 runs a multi-field kernel width)."""
+    fields = [W.paper_f1, W.paper_f2, W.paper_f3, W.field_sincos, W.linear_field([1, 2, 3, 4])]
+    if dim == 2:
+        src = W.with_values(W.jittered_tri_mesh(9, 11), fields)
+        tgt = W.delaunay_tri_mesh(53, 5, 12)
+    else:
+        src = W.with_values(W.jittered_kuhn_mesh(4, 11), [lambda x, f=f: f(x[:, :2]) + x[:, 2] for f in fields])
+        tgt = W.morton_reorder(W.jittered_kuhn_mesh(3, 12))
+    N = 12
+    for prec in (FP64, FP32):
+        o = orc.transfer(src, tgt, 1 if prec == FP32 else 0, N, seed=4, cg_tol=1e-13, cg_max_iter=2000,
+                         want_sample_elem=True)
+        s = sft.mesh_source(src, device=DEV)
+        t = sft.mesh_target(tgt, device=DEV)
+        for k in (1, 2, 3, 5):
+            u = torch.zeros((k, tgt.nnodes), dtype=torch.float64, device=DEV)
+            b = torch.zeros_like(u)
+            se = torch.zeros((tgt.nelems, N), dtype=torch.int32, device=DEV)
+            sft.sft_transfer(s, t, N, prec, seed=4, cg_tol=1e-13, cg_max_iter=2000, field_count=k,
+                             u_out=u, b_out=b, sample_elem_out=se)
+            assert np.array_equal(se.cpu().numpy(), o["sample_elem"])
+            bb, uu = b.cpu().numpy(), u.cpu().numpy()
+            for f in range(k):
+                assert _close(bb[f], o["b"][f], 1e-13 if prec == FP64 else 1e-5), (prec, k, f)
+                assert _close(uu[f], o["u"][f], 1e-10 if prec == FP64 else 1e-4), (prec, k, f)
+
+
 def test_host_buffers_equal_device_buffers():
     src, tgt, _ = W.config_meshes("tri2k")
     a = _run(src, tgt, FP64, 16, device=True)
