@@ -251,6 +251,7 @@ constexpr float kEtaFloor = SFT_MIX_ETA_FLOOR;
 #define SFT_MIX_ROWS_PER_THREAD 3
 #endif
 
+
 struct MixCtl {
   GridBarrier bar;
   int32_t err;
@@ -341,12 +342,13 @@ __global__ void __launch_bounds__(kSolveThreads, 4) k_mixed_cg(
     const int32_t* __restrict__ rp, const int32_t* __restrict__ col, const double* __restrict__ val,
     const float* __restrict__ aval, const double* __restrict__ sc, int64_t n, int nrhs,
     const double* __restrict__ b, double* x, double* t, float* r, float* p, float* q, float* y, double* partd,
-    float* partf, MixCtl* ctl, double tol, int max_iter, int warm, uint64_t wait_ns) {
+    float* partf, MixCtl* ctl, double tol, int max_iter, int warm, uint64_t wait_ns, float lmax) {
   __shared__ double totd[kMaxFields * 2];
   __shared__ float totf[NR];
   __shared__ double bnorm[NR], prev[NR], sig[NR], isig[NR];
   __shared__ float eta2[NR], rr[NR], alpha[NR], beta[NR];
-  __shared__ int live[NR], act[NR], conv[NR], stop;
+  __shared__ int live[NR], act[NR], conv[NR], ksteps[NR], stop;
+  const ChebCoef ch = cheb_coef(lmax);
   const unsigned nb = gridDim.x;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
@@ -414,6 +416,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) k_mixed_cg(
     if (threadIdx.x == 0) {
       bool any = false;
       for (int f = 0; f < nrhs; ++f) {
+        act[f] = 0;
         if (!live[f]) continue;
         const double rn = sqrt(totd[2 * f]), tn = sqrt(totd[2 * f + 1]);
         if (cyc == 0 && !warm) bnorm[f] = rn;
@@ -437,6 +440,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) k_mixed_cg(
         isig[f] = 1.0 / tn;
         const double e = fmin(0.25, fmax((double)kEtaFloor, 0.1 * tol * bnorm[f] / rn));
         eta2[f] = (float)(e * e);
+        ksteps[f] = cheb_steps(e, ch.s1);
         act[f] = 1;
         any = true;
       }
@@ -445,71 +449,68 @@ __global__ void __launch_bounds__(kSolveThreads, 4) k_mixed_cg(
     __syncthreads();
     if (stop) break;
 
-    // I: unit-norm FP32 right-hand side, zero iterate and directions
-    float vf[NR];
-#pragma unroll
-    for (int f = 0; f < NR; ++f) vf[f] = 0.f;
-    for (int64_t i = tid; i < n; i += nthreads) {
-#pragma unroll
-      for (int f = 0; f < NR; ++f) {
-        if (f >= nrhs) break;
-        if (!act[f]) continue;
-        const int64_t k = (int64_t)f * n + i;
-        const float ci = (float)(t[k] * isig[f]);
-        r[k] = ci;
-        y[k] = 0.f;
-        p[k] = 0.f;
-        q[k] = 0.f;
-        vf[f] += ci * ci;
-      }
-    }
-    block_partials_f<NR>(vf, nrhs, partf);
-    if (!grid_sync(&ctl->bar, nb, &ctl->err, wait_ns)) return;
-    reduce_partials_f<NR>(partf, nb, nrhs, totf);
-    if (threadIdx.x == 0)
-      for (int f = 0; f < nrhs; ++f) {
-        rr[f] = totf[f];
-        beta[f] = 0.f;
-      }
-    __syncthreads();
-
-    // CG in FP32 on A y = c
-    for (;;) {
-      bool any = false;
-#pragma unroll
-      for (int f = 0; f < NR; ++f)
-        if (f < nrhs) any = any || act[f];
-      if (!any || it >= max_iter) break;
-      // phase A: w = A r, p = r + beta p, q = w + beta q (= A p), partial (p, q)
-#pragma unroll
-      for (int f = 0; f < NR; ++f) vf[f] = 0.f;
+    if constexpr (kMixCheb) {
+      // I: c = t / ||t|| in FP32, r = c, y = 0, d = c / theta (in p)
+      const float ith = 1.f / ch.theta;
       for (int64_t i = tid; i < n; i += nthreads) {
-        const int32_t k0 = __ldg(rp + i), k1 = __ldg(rp + i + 1);
 #pragma unroll
         for (int f = 0; f < NR; ++f) {
           if (f >= nrhs) break;
           if (!act[f]) continue;
-          const int64_t o = (int64_t)f * n;
-          const float* rf = r + o;
-          float s = 0.f;
-          // r was written by other blocks before the grid barrier (plain loads)
-          for (int32_t k = k0; k < k1; ++k) s += __ldg(aval + k) * rf[__ldg(col + k)];
-          const float bt = beta[f];
-          const int64_t k = o + i;
-          const float pn = rf[i] + bt * p[k];
-          const float qn = s + bt * q[k];
-          p[k] = pn;
-          q[k] = qn;
-          vf[f] += pn * qn;
+          const int64_t k = (int64_t)f * n + i;
+          const float ci = (float)(t[k] * isig[f]);
+          r[k] = ci;
+          y[k] = 0.f;
+          p[k] = ci * ith;
         }
       }
-      block_partials_f<NR>(vf, nrhs, partf);
       if (!grid_sync(&ctl->bar, nb, &ctl->err, wait_ns)) return;
-      reduce_partials_f<NR>(partf, nb, nrhs, totf);
-      if (threadIdx.x == 0)
-        for (int f = 0; f < nrhs; ++f) alpha[f] = act[f] ? rr[f] / totf[f] : 0.f;
-      __syncthreads();
-      // phase B: y += alpha p, r -= alpha q, partial (r, r)
+      // Chebyshev steps; d alternates between p and q (the SpMV of a step
+      // reads the d every block wrote in the step before)
+      float rho = 1.f / ch.s1;
+      const float idl = 2.f / ch.delta;
+      auto steps_left = [&](int s) {  // fields that take step s
+        unsigned mm = 0u;
+#pragma unroll
+        for (int f = 0; f < NR; ++f)
+          if (f < nrhs && act[f] && s < ksteps[f]) mm |= 1u << f;
+        return it < max_iter ? mm : 0u;
+      };
+      for (int s = 0;; ++s) {
+        const unsigned m = steps_left(s);
+        if (!m) break;
+        const float rn1 = 1.f / (2.f * ch.s1 - rho);
+        const float c1 = rn1 * rho, c2 = rn1 * idl;
+        const float* dc = (s & 1) ? q : p;
+        float* dn = (s & 1) ? p : q;
+        for (int64_t i = tid; i < n; i += nthreads) {
+          const int32_t k0 = __ldg(rp + i), k1 = __ldg(rp + i + 1);
+#pragma unroll
+          for (int f = 0; f < NR; ++f) {
+            if (f >= nrhs) break;
+            if (!((m >> f) & 1u)) continue;
+            const int64_t o = (int64_t)f * n;
+            const float* df = dc + o;
+            float w = 0.f;
+            // d was written by other blocks before the grid barrier (plain loads)
+            for (int32_t k = k0; k < k1; ++k) w += __ldg(aval + k) * df[__ldg(col + k)];
+            const float di = df[i];
+            y[o + i] += di;
+            const float ri = r[o + i] - w;
+            r[o + i] = ri;
+            dn[o + i] = c1 * di + c2 * ri;
+          }
+        }
+        rho = rn1;
+        ++it;
+        // the next step's SpMV reads the d of other blocks; after the last
+        // step U touches only the thread's own rows, so no barrier
+        if (!steps_left(s + 1)) break;
+        if (!grid_sync(&ctl->bar, nb, &ctl->err, wait_ns)) return;
+      }
+    } else {
+      // I: unit-norm FP32 right-hand side, zero iterate and directions
+      float vf[NR];
 #pragma unroll
       for (int f = 0; f < NR; ++f) vf[f] = 0.f;
       for (int64_t i = tid; i < n; i += nthreads) {
@@ -518,26 +519,90 @@ __global__ void __launch_bounds__(kSolveThreads, 4) k_mixed_cg(
           if (f >= nrhs) break;
           if (!act[f]) continue;
           const int64_t k = (int64_t)f * n + i;
-          const float a = alpha[f];
-          y[k] += a * p[k];
-          const float ri = r[k] - a * q[k];
-          r[k] = ri;
-          vf[f] += ri * ri;
+          const float ci = (float)(t[k] * isig[f]);
+          r[k] = ci;
+          y[k] = 0.f;
+          p[k] = 0.f;
+          q[k] = 0.f;
+          vf[f] += ci * ci;
         }
       }
       block_partials_f<NR>(vf, nrhs, partf);
       if (!grid_sync(&ctl->bar, nb, &ctl->err, wait_ns)) return;
       reduce_partials_f<NR>(partf, nb, nrhs, totf);
-      ++it;
       if (threadIdx.x == 0)
         for (int f = 0; f < nrhs; ++f) {
-          if (!act[f]) continue;
-          const float rn = totf[f];
-          beta[f] = rn / rr[f];
-          rr[f] = rn;
-          if (rn <= eta2[f]) act[f] = 0;
+          rr[f] = totf[f];
+          beta[f] = 0.f;
         }
       __syncthreads();
+
+      // CG in FP32 on A y = c
+      for (;;) {
+        bool any = false;
+#pragma unroll
+        for (int f = 0; f < NR; ++f)
+          if (f < nrhs) any = any || act[f];
+        if (!any || it >= max_iter) break;
+        // phase A: w = A r, p = r + beta p, q = w + beta q (= A p), partial (p, q)
+#pragma unroll
+        for (int f = 0; f < NR; ++f) vf[f] = 0.f;
+        for (int64_t i = tid; i < n; i += nthreads) {
+          const int32_t k0 = __ldg(rp + i), k1 = __ldg(rp + i + 1);
+#pragma unroll
+          for (int f = 0; f < NR; ++f) {
+            if (f >= nrhs) break;
+            if (!act[f]) continue;
+            const int64_t o = (int64_t)f * n;
+            const float* rf = r + o;
+            float s = 0.f;
+            // r was written by other blocks before the grid barrier (plain loads)
+            for (int32_t k = k0; k < k1; ++k) s += __ldg(aval + k) * rf[__ldg(col + k)];
+            const float bt = beta[f];
+            const int64_t k = o + i;
+            const float pn = rf[i] + bt * p[k];
+            const float qn = s + bt * q[k];
+            p[k] = pn;
+            q[k] = qn;
+            vf[f] += pn * qn;
+          }
+        }
+        block_partials_f<NR>(vf, nrhs, partf);
+        if (!grid_sync(&ctl->bar, nb, &ctl->err, wait_ns)) return;
+        reduce_partials_f<NR>(partf, nb, nrhs, totf);
+        if (threadIdx.x == 0)
+          for (int f = 0; f < nrhs; ++f) alpha[f] = act[f] ? rr[f] / totf[f] : 0.f;
+        __syncthreads();
+        // phase B: y += alpha p, r -= alpha q, partial (r, r)
+#pragma unroll
+        for (int f = 0; f < NR; ++f) vf[f] = 0.f;
+        for (int64_t i = tid; i < n; i += nthreads) {
+#pragma unroll
+          for (int f = 0; f < NR; ++f) {
+            if (f >= nrhs) break;
+            if (!act[f]) continue;
+            const int64_t k = (int64_t)f * n + i;
+            const float a = alpha[f];
+            y[k] += a * p[k];
+            const float ri = r[k] - a * q[k];
+            r[k] = ri;
+            vf[f] += ri * ri;
+          }
+        }
+        block_partials_f<NR>(vf, nrhs, partf);
+        if (!grid_sync(&ctl->bar, nb, &ctl->err, wait_ns)) return;
+        reduce_partials_f<NR>(partf, nb, nrhs, totf);
+        ++it;
+        if (threadIdx.x == 0)
+          for (int f = 0; f < nrhs; ++f) {
+            if (!act[f]) continue;
+            const float rn = totf[f];
+            beta[f] = rn / rr[f];
+            rr[f] = rn;
+            if (rn <= eta2[f]) act[f] = 0;
+          }
+        __syncthreads();
+      }
     }
 
     // U: x += ||t|| S y for every field that ran this cycle
@@ -610,6 +675,8 @@ template <int NR>
 static sft_status launch_mixed(sft_target_s* t, int nrhs, const double* b, double* x, double tol, int max_iter,
                                cudaStream_t st, SolveResult* res, SolveLate* late, int warm) {
   const int64_t n = t->nv;
+  // largest eigenvalue bound of S M S: 2 for triangles, 5/2 for tetrahedra
+  float lmax = t->dim == 2 ? 2.f : 2.5f;
   int dev = 0, sms = 0;
   SFT_CUDA(cudaGetDevice(&dev));
   SFT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -655,7 +722,7 @@ static sft_status launch_mixed(sft_target_s* t, int nrhs, const double* b, doubl
   void* args[] = {(void*)&rp, (void*)&col, (void*)&val, (void*)&aval, (void*)&sc, (void*)&n, (void*)&nrhs,
                   (void*)&b, (void*)&x, (void*)&tp, (void*)&r, (void*)&p, (void*)&q, (void*)&y,
                   (void*)&pd, (void*)&pf, (void*)&c, (void*)&tol, (void*)&max_iter, (void*)&warm,
-                  (void*)&t->wait_ns};
+                  (void*)&t->wait_ns, (void*)&lmax};
   const cudaError_t le = (::sft::note_launch(), cudaLaunchCooperativeKernel((const void*)k_mixed_cg<NR>, nblocks,
                                                                            kSolveThreads, args, 0, st));
   if (le != cudaSuccess) return cuda_fail(le, "cudaLaunchCooperativeKernel(k_mixed_cg)");

@@ -37,6 +37,41 @@ __device__ __forceinline__ T warp_inclusive_scan(T v, int lane) {
   return v;
 }
 
+// inner FP32 solver of the mixed-precision solves: 1 = Chebyshev iteration
+// on the proven spectrum bounds of A (one SpMV and one grid barrier per step,
+// no dot products), 0 = CG (two grid barriers and two reductions per step)
+#ifndef SFT_MIX_CHEBYSHEV
+#define SFT_MIX_CHEBYSHEV 1
+#endif
+constexpr bool kMixCheb = SFT_MIX_CHEBYSHEV != 0;
+
+// Chebyshev iteration on A y = c (A the Jacobi-scaled P1 mass matrix) with
+// the spectrum of A inside [a, b] (a = 1/2, b = 2 or 5/2, widened by 1e-3
+// relative for the FP32 rounding of A's entries): theta = (a + b) / 2,
+// delta = (b - a) / 2, s1 = theta / delta.
+// From y0 = 0, r0 = c, d0 = c / theta, rho0 = 1 / s1, each step takes
+//   y += d, r -= A d, rho' = 1 / (2 s1 - rho), d' = rho' rho d + (2 rho' / delta) r
+// and leaves r_k = P_k(A) c with max |P_k| on [a, b] = 1 / T_k(s1) (the
+// scaled Chebyshev polynomial of degree k; Saad, Iterative Methods for Sparse
+// Linear Systems, Sec. 12.3). So ||r_k|| <= eta ||c|| after
+// k = ceil(acosh(1 / eta) / acosh(s1)) steps: 12 for eta = 1e-5 on
+// triangles, 13 on tetrahedra.
+struct ChebCoef {
+  float theta, delta, s1;
+};
+__host__ __device__ inline ChebCoef cheb_coef(float lmax) {
+  const float a = 0.5f * (1.f - 1e-3f), b = lmax * (1.f + 1e-3f);
+  ChebCoef c;
+  c.theta = 0.5f * (a + b);
+  c.delta = 0.5f * (b - a);
+  c.s1 = c.theta / c.delta;
+  return c;
+}
+__device__ inline int cheb_steps(double eta, float s1) {
+  const int k = (int)ceil(acosh(1.0 / eta) / acosh((double)s1));
+  return k < 1 ? 1 : k;
+}
+
 // limit of a device wait (grid barrier, mbarrier phase) unless the caller
 // sets another (sft_target_set_wait_limit for the solves on a target)
 constexpr uint64_t kDefaultWaitNs = 2000000000ull;
