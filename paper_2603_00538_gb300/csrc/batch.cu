@@ -67,6 +67,7 @@ struct BSys {
   double tol;
   int32_t max_iter;
   int32_t blo, bhi;  // blocks owning its rows
+  float lmax;        // spectrum bound of the scaled matrix: 2 (triangles), 5/2 (tetrahedra)
 };
 
 // a block's share of the mixed-precision batched solve: matrix rows [i0, i1)
@@ -700,6 +701,67 @@ __device__ __forceinline__ void piece_B(const BPiece P, const BSys& S, unsigned 
   piece_flush_f<NFC>(a, m, slot, j0);
 }
 
+// Chebyshev I: c = t / ||t|| in FP32, r = c, y = 0, d = c / theta (in p)
+template <int NFC>
+__device__ __forceinline__ void piece_Ic(const BPiece P, const BSys& S, unsigned m, const double* t, float* r,
+                                         float* p, float* y, const double* isig, float ith, int j0) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t n = S.n;
+  double is[NFC];
+#pragma unroll
+  for (int f = 0; f < NFC; ++f) is[f] = (m >> f) & 1u ? isig[j0 + f] : 0.0;
+  for (int64_t base = P.i0 + warp * 32; base < P.i1; base += kBatchThreads) {
+    const int64_t i = base + lane;
+    if (i >= P.i1) continue;
+#pragma unroll
+    for (int f = 0; f < NFC; ++f) {
+      if (!((m >> f) & 1u)) continue;
+      const int64_t gr = S.off + f * n + i;
+      const float ci = (float)(t[gr] * is[f]);
+      r[gr] = ci;
+      y[gr] = 0.f;
+      p[gr] = ci * ith;
+    }
+  }
+}
+
+// Chebyshev step: w = A d, y += d, r -= w, d' = c1 d + c2 r (d' in the
+// other buffer: the SpMV reads the d every block wrote in the step before)
+template <int NFC>
+__device__ __forceinline__ void piece_C(const BPiece P, const BSys& S, unsigned m, const float* dc, float* dn,
+                                        float* r, float* y, float c1, float c2, int j0) {
+  (void)j0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t n = S.n;
+  const float* ds = dc + S.off;
+  for (int64_t base = P.i0 + warp * 32; base < P.i1; base += kBatchThreads) {
+    const int64_t i = base + lane;
+    if (i >= P.i1) continue;
+    const int32_t k0 = __ldg(S.rp + i), k1 = __ldg(S.rp + i + 1);
+    float w[NFC];
+#pragma unroll
+    for (int f = 0; f < NFC; ++f) w[f] = 0.f;
+    // d was written by other blocks before the grid barrier (plain loads)
+    for (int32_t k = k0; k < k1; ++k) {
+      const float v = __ldg(S.aval + k);
+      const int64_t c = __ldg(S.col + k);
+#pragma unroll
+      for (int f = 0; f < NFC; ++f)
+        if ((m >> f) & 1u) w[f] += v * ds[f * n + c];
+    }
+#pragma unroll
+    for (int f = 0; f < NFC; ++f) {
+      if (!((m >> f) & 1u)) continue;
+      const int64_t gr = S.off + f * n + i;
+      const float di = dc[gr];
+      y[gr] += di;
+      const float ri = r[gr] - w[f];
+      r[gr] = ri;
+      dn[gr] = c1 * di + c2 * ri;
+    }
+  }
+}
+
 // U: x += ||t|| S y
 template <int NFC>
 __device__ __forceinline__ void piece_U(const BPiece P, const BSys& S, unsigned m, const float* y,
@@ -751,9 +813,12 @@ constexpr int kPieceFieldsR = 4, kPieceFields = 8;
 // Batched mixed-precision iterative refinement (the cg_mode MIXED solve of
 // every (request, field) system at once; see the single-system k_mixed_cg):
 // per refinement cycle an FP64 residual pass R, the FP32 right-hand side
-// pass I, FP32 CG on S M S (phases A and B) and the FP64 update U. All
-// systems step through the same phases; a system whose inner solve reached
-// its target (or that converged) skips the row work of the phase. Whether
+// pass I, the FP32 inner solve on S M S and the FP64 update U. The inner
+// solve is the Chebyshev iteration (one step phase per step; each system
+// takes the step count its spectrum interval fixes for its target), or CG
+// (phases A and B) when built with the CG alternative. All systems step
+// through the same phases; a system whose inner solve reached its target
+// (or that converged) skips the row work of the phase. Whether
 // any system still works is a flag summed over blocks, read after the next
 // grid barrier (three rotating flags: the one of decision d is cleared at
 // decision d + 2, when every block has read it).
@@ -769,6 +834,7 @@ __global__ void __launch_bounds__(kBatchThreads, 4) k_batch_mixed(const BSys* __
       s_rel[kMaxLocalSys];
   __shared__ float s_eta2[kMaxLocalSys], s_rr[kMaxLocalSys], s_alpha[kMaxLocalSys], s_beta[kMaxLocalSys];
   __shared__ int s_live[kMaxLocalSys], s_act[kMaxLocalSys], s_conv[kMaxLocalSys], s_it[kMaxLocalSys];
+  __shared__ int s_ks[kMaxLocalSys];  // Chebyshev steps of the cycle
   __shared__ double s_w[kBatchWarps][kMaxLocalSys][2];
   __shared__ double s_g[kMaxLocalSys][2];
   __shared__ int s_any;
@@ -866,12 +932,58 @@ __global__ void __launch_bounds__(kBatchThreads, 4) k_batch_mixed(const BSys* __
           s_isig[j] = 1.0 / tn;
           const double e = fmin(0.25, fmax(1e-5, 0.1 * S.tol * s_bn[j] / rn));
           s_eta2[j] = (float)(e * e);
+          s_ks[j] = cheb_steps(e, cheb_coef(S.lmax).s1);
           s_act[j] = 1;
           atomicOr(&s_any, 1);
         }
       }
     }
     post();
+    if (kMixCheb) {
+      // I: r = c, y = 0, d = c / theta; the barrier makes d whole for the first step
+      for (int pc = pc0; pc < pc1; ++pc) {
+        const BPiece P = pcs[pc];
+        const int j0 = P.s0 - slo;
+        const unsigned m = piece_mask(P, s_act, j0);
+        if (!m) continue;
+        const float ith = 1.f / cheb_coef(sys[P.s0].lmax).theta;
+        SFT_PIECE_RUN(piece_Ic, kPieceFields, t, r, p, y, s_isig, ith);
+      }
+      if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+      if (!voted()) break;  // no system left to refine
+      const ChebCoef c2d = cheb_coef(2.f), c3d = cheb_coef(2.5f);
+      float rho2 = 1.f / c2d.s1, rho3 = 1.f / c3d.s1;
+      for (int s = 0;; ++s) {
+        const float n2 = 1.f / (2.f * c2d.s1 - rho2), n3 = 1.f / (2.f * c3d.s1 - rho3);
+        const float a2 = n2 * rho2, b2 = n2 * (2.f / c2d.delta), a3 = n3 * rho3, b3 = n3 * (2.f / c3d.delta);
+        const float* dc = (s & 1) ? q : p;
+        float* dn = (s & 1) ? p : q;
+        for (int pc = pc0; pc < pc1; ++pc) {
+          const BPiece P = pcs[pc];
+          const int j0 = P.s0 - slo;
+          unsigned m = 0u;
+          for (int f = 0; f < P.nf; ++f) m |= s_act[j0 + f] && s < s_ks[j0 + f] ? 1u << f : 0u;
+          if (!m) continue;
+          const bool d3 = sys[P.s0].lmax > 2.25f;
+          SFT_PIECE_RUN(piece_C, kPieceFields, dc, dn, r, y, d3 ? a3 : a2, d3 ? b3 : b2);
+        }
+        rho2 = n2;
+        rho3 = n3;
+        if (threadIdx.x == 0) s_any = 0;
+        __syncthreads();
+        if (threadIdx.x < nloc) {
+          const int j = threadIdx.x;
+          if (s_act[j] && s < s_ks[j]) {
+            s_it[j] += 1;
+            if (s + 1 < s_ks[j] && s_it[j] < sys[slo + j].max_iter) atomicOr(&s_any, 1);
+            else s_act[j] = 0;
+          }
+        }
+        post();
+        if (!grid_sync(&ctl->bar, nb, &ctl->err)) return;
+        if (!voted()) break;  // every system took its steps
+      }
+    } else {
     // I: c = t / ||t|| in FP32, y = p = q = 0; partial c.c
     clear_slots();
     __syncthreads();
@@ -939,6 +1051,7 @@ __global__ void __launch_bounds__(kBatchThreads, 4) k_batch_mixed(const BSys* __
         }
       }
       post();
+    }
     }
     // U: x += ||t|| S y for every system that refined in this cycle
     for (int pc = pc0; pc < pc1; ++pc) {
@@ -1384,6 +1497,7 @@ static sft_status build_batch(sft_batch_s* B, const sft_options* opts, int autot
       S.n = t->nv;
       S.tol = opts[r].cg_tol;
       S.max_iter = std::max(1, opts[r].cg_max_iter);
+      S.lmax = t->dim == 2 ? 2.f : 2.5f;
       off += t->nv;
       B->hsys.push_back(S);
     }
