@@ -245,8 +245,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble(const P* __restrict__ tx, c
           for (int m = 1; m < K; ++m) gX = A::fma(gl[f][m], lam[m], gX);
           P r = A::sub(fs, A::mul(alphaP, gX));
           if (EXT && p.imp) r = A::mul(wgt, r);   // w_j (f^s - alpha g): the density's weight
-#pragma unroll
-          for (int i = 0; i < K; ++i) acc[f][i].add(A::mul(r, lam[i]));
+          acc_add_sample<K>(acc[f], r, lam);
         }
       }
     }

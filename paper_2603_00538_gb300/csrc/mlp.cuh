@@ -68,32 +68,7 @@ __device__ __forceinline__ float sigmoid_f(float z) { return rcp_sfu(1.0f + ex2_
 // SiLU z sigma(z): two special-function operations per activation
 __device__ __forceinline__ float silu_f(float z) { return z * sigmoid_f(z); }
 
-// Packed FP32 pairs (sm_100 family f32x2 instructions): each lane is rounded
-// exactly as the scalar operation (round to nearest, no flush), so the pair
-// forms below give the scalar results bit for bit with half the instructions.
-__device__ __forceinline__ uint64_t f2_pack(float a, float b) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ void f2_unpack(uint64_t r, float& a, float& b) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-}
-__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
-  uint64_t d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
-  uint64_t d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
+// (packed FP32 pair helpers f2_*: common.cuh)
 // silu_f of both lanes of z2 (the same operations in the same order)
 __device__ __forceinline__ void silu_pair(uint64_t z2, float& h0, float& h1) {
   float t0, t1;
