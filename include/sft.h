@@ -52,9 +52,11 @@ typedef enum { SFT_PREC_FP64 = 0, SFT_PREC_FP32 = 1 } sft_precision;
 /* How the FP64 system M u = b of step 7 is solved (both stop on the true
  * FP64 residual ||b - M u||_2 <= cg_tol ||b||_2, which is computed in FP64).
  * MIXED: iterative refinement -- FP64 residual and solution, each correction
- * by CG in FP32 on the symmetrically Jacobi-scaled matrix
- * diag(M)^-1/2 M diag(M)^-1/2 (its condition number is bounded by a small
- * constant for any P1 mass matrix, so FP32 inner solves are safe).
+ * by the Chebyshev iteration in FP32 on the symmetrically Jacobi-scaled
+ * matrix diag(M)^-1/2 M diag(M)^-1/2, whose spectrum lies in [1/2, 2]
+ * (triangles) or [1/2, 5/2] (tetrahedra) for any P1 mass matrix: the interval
+ * fixes the step count for each cycle's target, and FP32 inner solves are
+ * safe.
  * FP64: Jacobi-preconditioned CG in FP64 throughout. */
 typedef enum { SFT_CG_MIXED = 0, SFT_CG_FP64 = 1 } sft_cg_mode;
 
@@ -229,8 +231,8 @@ sft_status sft_locate(sft_source src, int32_t precision, int64_t n, const double
 
 /* Solve M u = b on the target (step 7 alone) for nrhs right-hand sides
  * b [nrhs][nnodes] -> u [nrhs][nnodes] (FP64), from u = 0, by the sft_cg_mode
- * `cg_mode`. max_iter bounds the CG iterations (FP32 inner iterations summed
- * over the refinement cycles in MIXED mode). iters_out / rel_resid_out (host,
+ * `cg_mode`. max_iter bounds the iterations (FP32 inner Chebyshev steps
+ * summed over the refinement cycles in MIXED mode). iters_out / rel_resid_out (host,
  * may be NULL) get the worst field; rel_resid is the true FP64 residual of the
  * returned u in MIXED mode, the recurrence residual in FP64 mode. */
 sft_status sft_mass_solve(sft_target tgt, int32_t nrhs, const double* b, double* u,

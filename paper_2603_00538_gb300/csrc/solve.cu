@@ -226,13 +226,17 @@ __global__ void __launch_bounds__(kSolveThreads) k_pcg(const int32_t* __restrict
 // elements the element mass matrix against its own diagonal has eigenvalues
 // in [1/2, 2] (triangles) or [1/2, 5/2] (tetrahedra), and the assembled
 // matrix inherits the union of the element bounds, so cond(A) <= 4 or 5 on
-// any mesh: CG in FP32 on A converges like Jacobi-PCG in FP64 on M, and its
-// attainable accuracy (~ eps32 cond(A)) is far below the per-cycle target.
+// any mesh: an FP32 solve on A converges like Jacobi-PCG in FP64 on M, and
+// its attainable accuracy (~ eps32 cond(A)) is far below the per-cycle target.
 // One refinement cycle:
 //   R (FP64)  r = b - M x, t = S r, ||r||_2 (the stopping test) and ||t||_2;
 //   I         c = t / ||t||_2 rounded to FP32 (unit norm), y = 0;
-//   CG (FP32) on A y = c until ||c - A y||_2 <= eta, eta about the reduction
-//             the stopping test still needs (between 1e-5 and 1/4);
+//   inner (FP32) on A y = c to ||c - A y||_2 <= eta, eta about the reduction
+//             the stopping test still needs (between 1e-5 and 1/4): the
+//             Chebyshev iteration over the spectrum interval (the step count
+//             the interval fixes for eta; util.cuh), or CG until its
+//             recurrence residual reaches eta when built with
+//             SFT_MIX_CHEBYSHEV=0;
 //   U (FP64)  x += ||t||_2 S y   (so the new residual is ||t|| S^-1 (c - A y)).
 // A warm start takes x as given (||b|| is then reduced separately first) and
 // skips nothing else: the first R phase checks whether x already converged.
