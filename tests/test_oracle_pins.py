@@ -617,6 +617,66 @@ def test_scaled_mass_matrix_eigenvalue_bounds(orc):
         assert ev.min() >= 0.5 - 1e-12 and ev.max() <= hi + 1e-12, (d, ev.min(), ev.max())
 
 
+def test_chebyshev_step_count_meets_target(orc):
+    """The mixed solve's inner FP32 solver is the Chebyshev iteration over the
+    spectrum interval pinned above ([1/2, 2] or [1/2, 5/2], widened by 1e-3),
+    run for k = ceil(acosh(1/eta) / acosh(s1)) steps with s1 = theta / delta:
+    the residual polynomial's maximum on the interval is 1 / T_k(s1) <= eta
+    (Saad, Iterative Methods for Sparse Linear Systems, Sec. 12.3). Replayed
+    here in FP32 on scaled mass matrices from the oracle (graded and sliver
+    meshes included) for several targets: ||c - A y|| <= eta ||c|| after k
+    steps, the recurrence residual tracks the true one, and k - 2 steps do
+    not always suffice (the count is not slack by more than a step)."""
+    g = W.delaunay_tri_mesh(600, 12, 3)
+    c = g.coords.copy()
+    c[:, 0] = c[:, 0] ** 3
+    g = W.Mesh(c, g.conn.copy(), None)
+    W._fix_orientation(g)
+    sl = W.jittered_tri_mesh(12, 4)
+    meshes = [W.delaunay_tri_mesh(1500, 15, 2), g, W.Mesh(sl.coords * np.array([1.0, 1e-3]), sl.conn, None),
+              W.morton_reorder(W.jittered_kuhn_mesh(6, 9))]
+    rng = np.random.default_rng(5)
+    short_ok = []
+    for m in meshes:
+        d = m.coords.shape[1]
+        rp, col, val = orc.mass_csr(m.coords, m.conn)
+        n = len(rp) - 1
+        rows = np.repeat(np.arange(n), np.diff(rp))
+        s = 1.0 / np.sqrt(val[col == rows])
+        av = (val * s[rows] * s[col]).astype(np.float32)
+
+        def apply(x):
+            return np.bincount(rows, weights=av.astype(np.float64) * x[col], minlength=n).astype(np.float32)
+
+        a, b = 0.5 * (1 - 1e-3), (2.0 if d == 2 else 2.5) * (1 + 1e-3)
+        theta, delta = (a + b) / 2, (b - a) / 2
+        s1 = theta / delta
+        for eta in (1e-5, 1e-3, 0.25):
+            k = max(1, int(np.ceil(np.arccosh(1 / eta) / np.arccosh(s1))))
+            cvec = rng.standard_normal(n).astype(np.float32)
+            cvec /= np.linalg.norm(cvec)
+            res = []
+            for steps in (k, max(1, k - 2)):
+                y = np.zeros(n, np.float32)
+                r = cvec.copy()
+                dv = (cvec / np.float32(theta)).astype(np.float32)
+                rho = np.float32(1 / s1)
+                for _ in range(steps):
+                    w = apply(dv)
+                    y += dv
+                    r = (r - w).astype(np.float32)
+                    rn = np.float32(1 / (2 * s1 - rho))
+                    dv = (rn * rho * dv + (2 * rn / delta) * r).astype(np.float32)
+                    rho = rn
+                true_r = float(np.linalg.norm(cvec - apply(y)))
+                res.append(true_r)
+                if steps == k:
+                    assert true_r <= eta, (d, eta, k, true_r)
+                    assert abs(float(np.linalg.norm(r)) - true_r) <= 1e-5 + 1e-3 * true_r
+            short_ok.append(res[1] <= eta)
+    assert not all(short_ok)
+
+
 def test_pcg_matches_dense_solve(orc):
     m = W.delaunay_tri_mesh(150, 6, 5)
     rp, col, val = orc.mass_csr(m.coords, m.conn)
