@@ -147,6 +147,11 @@ __global__ void __launch_bounds__(kBatchThreads, NF <= 2 ? 4 : (NF <= 4 ? 3 : 2)
   constexpr int SPU = D == 2 ? 2 : 1;
   using A = Ar<float>;
   extern __shared__ int64_t s_off[];  // [ng + 1]
+  // each slot's control values at its element's vertices, one float4 per
+  // field (w = 0 in 2D), staged once per task: the sample loop reads them
+  // with one shared load per field instead of K global loads (slot stride
+  // NF + 1 float4 keeps the slots of a load phase on different banks)
+  __shared__ float4 s_g[kBatchThreads / 32][32 * (NF + 1)];
   for (int i = threadIdx.x; i <= ng; i += blockDim.x) s_off[i] = goff[i];
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -187,6 +192,21 @@ __global__ void __launch_bounds__(kBatchThreads, NF <= 2 ? 4 : (NF <= 4 ? 3 : 2)
           for (int a = 0; a < D; ++a) xv[m][a] = __ldg(R.tx + (int64_t)v[m] * D + a);
         }
       }
+      float4* sg = s_g[threadIdx.x >> 5] + (lane / LPE) * (NF + 1);
+      __syncwarp();  // the previous task's reads of the slots are done
+      if (active) {
+        for (int f = lane - seg_lo; f < nf && f < NF; f += seg_hi - seg_lo) {
+          const float* gf = R.g + (int64_t)f * R.nv;
+          float4 q;
+          q.x = __ldg(gf + v[0]);
+          q.y = __ldg(gf + v[1]);
+          q.z = __ldg(gf + v[2]);
+          if constexpr (K == 4) q.w = __ldg(gf + v[3]);
+          else q.w = 0.f;
+          sg[f] = q;
+        }
+      }
+      __syncwarp();
       const GridP<float> gr = *R.grid;
       for (int u = u0; active && u < U; u += ustep) {
         const uint4 w = philox4x32_10(make_uint4((uint32_t)u, (uint32_t)t, R.stream_id, 0u), R.key);
@@ -207,10 +227,11 @@ __global__ void __launch_bounds__(kBatchThreads, NF <= 2 ? 4 : (NF <= 4 ? 3 : 2)
           for (int f = 0; f < NF; ++f) {
             if (f >= nf) break;
             const float fs = e >= 0 ? eval_p1<D, float>(R.vals, R.snf, f, e, mu) : 0.f;
-            const float* gf = R.g + (int64_t)f * R.nv;
-            float gX = A::mul(__ldg(gf + v[0]), lam[0]);
-#pragma unroll
-            for (int m = 1; m < K; ++m) gX = A::fma(__ldg(gf + v[m]), lam[m], gX);
+            const float4 gq = sg[f];
+            float gX = A::mul(gq.x, lam[0]);
+            gX = A::fma(gq.y, lam[1], gX);
+            gX = A::fma(gq.z, lam[2], gX);
+            if constexpr (K == 4) gX = A::fma(gq.w, lam[3], gX);
             const float r = A::sub(fs, A::mul(R.alpha, gX));
 #pragma unroll
             for (int i = 0; i < K; ++i) acc[f][i] = A::fma(r, lam[i], acc[f][i]);
@@ -241,14 +262,11 @@ __global__ void __launch_bounds__(kBatchThreads, NF <= 2 ? 4 : (NF <= 4 ? 3 : 2)
         const float wv = __ldg(R.vol32 + t);
         const float cd = __fmul_rn(wv, R.c_det), cm = __fmul_rn(wv, R.inv_n);
         for (int f = 0; f < nf && f < NF; ++f) {
-          const float* gf = R.g + (int64_t)f * R.nv;
-          float gl[K];
+          const float4 gq = sg[f];
+          const float gl[4] = {gq.x, gq.y, gq.z, gq.w};
           float gsum = 0.f;
 #pragma unroll
-          for (int m = 0; m < K; ++m) {
-            gl[m] = __ldg(gf + v[m]);
-            gsum = __fadd_rn(gsum, gl[m]);
-          }
+          for (int m = 0; m < K; ++m) gsum = __fadd_rn(gsum, gl[m]);
 #pragma unroll
           for (int i = 0; i < K; ++i) {
             const float c = __fmaf_rn(cd, __fadd_rn(gsum, gl[i]), __fmul_rn(cm, acc[f][i]));
