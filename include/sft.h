@@ -432,9 +432,9 @@ sft_status sft_surrogate_dataset(sft_source src, int32_t field, int64_t n, uint6
  * Limits: 1 <= nrhs <= 8 and 8 n (1 + 4 nrhs) bytes plus small per-block
  * partials must fit in 32 MiB (n (1 + 4 nrhs) below about 4.1e6);
  * larger problems are rejected with SFT_ERR_ARG before any device work.
- * The first call on a device looks up the array's device address once (make
- * that first call before any stream capture) and keeps it, so resetting the
- * device (cudaDeviceReset) while the library is loaded is not supported.
+ * The first call on a device looks up the array's device address once and
+ * keeps it, so resetting the device (cudaDeviceReset) while the library is
+ * loaded is not supported.
  * A row without a positive diagonal entry gives SFT_ERR_ARG. Every call uses the same
  * array, so calls that overlap on the GPU (other streams, other threads)
  * race and must be serialised by the caller. Nothing is allocated or freed;
