@@ -37,7 +37,8 @@ typedef enum {
     SFT_ERR_MESH = 2,           /* invalid mesh: connectivity, orientation, non-finite value */
     SFT_ERR_CUDA = 3,           /* a CUDA runtime call failed */
     SFT_ERR_OOM = 4,            /* device allocation failed */
-    SFT_ERR_NOT_CONVERGED = 5,  /* CG reached cg_max_iter; u is the last iterate */
+    SFT_ERR_NOT_CONVERGED = 5,  /* the solve reached cg_max_iter iterations (FP32 inner
+                                   steps in MIXED mode) or stagnated; u is the last iterate */
     SFT_ERR_OUTSIDE = 6,        /* strict mode: a query fell in an empty grid cell */
     SFT_ERR_DEVICE_STATUS = 7,  /* a kernel reported an error (bounded wait expired, bad index) */
     SFT_ERR_UNSUPPORTED = 8     /* valid request this build does not implement */
@@ -106,7 +107,9 @@ typedef struct {
     int32_t precision;          /* sft_precision */
     uint64_t seed;              /* Philox key */
     uint32_t stream_id;         /* Philox counter word 2 (independent sample streams) */
-    int32_t cg_max_iter;        /* >= 0; 0 skips the solve (u = 0) */
+    int32_t cg_max_iter;        /* >= 0; bound on the solve's iterations (in MIXED mode the
+                                   FP32 inner steps summed over the cycles); 0 skips the
+                                   solve (u = 0) */
     double alpha;               /* control-variate parameter (Eq. cv_centered_integrand); 1 recommended */
     double cg_tol;              /* stop when ||b - M u||_2 <= cg_tol ||b||_2 */
     int32_t strict_inside;      /* 1: SFT_ERR_OUTSIDE when a query lands in an empty grid cell */
@@ -132,7 +135,8 @@ typedef struct {
 } sft_options;
 
 typedef struct {
-    int32_t cg_iters;           /* largest iteration count over the fields */
+    int32_t cg_iters;           /* largest iteration count over the fields (MIXED: FP32
+                                   inner steps summed over the cycles) */
     int32_t reserved;
     double cg_rel_resid;        /* largest final ||r||/||b|| over the fields */
     int64_t queries;            /* source queries issued: nodes (control) + the samples
